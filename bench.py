@@ -1,0 +1,393 @@
+#!/usr/bin/env python3
+"""Benchmark: adaptive s-step CG on one GB300, through the libascg C ABI.
+
+One step = one full solve of the 3D Poisson 7-point problem on a 128^3 grid
+(n = 2,097,152, nnz = 14,581,760), adaptive s-step CG with the Chebyshev basis
+on the closed-form eigenvalue bounds, s_max = 16, relative target 1e-12,
+x_1 = 0. Each step runs every row of the hot path: residual setup, matrix
+powers, Gram, condition estimates and choice of s_k, coordinate CG steps,
+recovery, and the final true residual.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line on rank 0. For N > 1 (torchrun), every rank solves its
+own replica: a single solve does not shard across GPUs here, so the job is
+replicas only, with weak scaling.
+"""
+from __future__ import annotations
+
+import os
+
+# the oracle (CPU baseline) runs single-threaded; set before numpy is imported
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+    os.environ.setdefault(_v, "1")
+
+import argparse
+import hashlib
+import json
+import math
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "CG iters/s and HBM GB/s vs classical CG at 1e-10; served p50/p99 solve latency"
+WORKLOAD = ("3D Poisson 7-point 128^3 (n=2097152, nnz=14581760), equilibrated, b~U[-1,1] normalised (seed 1002), "
+            "x1=0; adaptive s-step CG, Chebyshev basis on closed-form bounds, s_max=16, s0=f=16, c=1, eps*=1e-12; "
+            "one full solve per step")
+SMS = 152
+SM_MAX_MHZ = 2070.0
+FP64_FMA_PER_CLK_SM = 2.0   # nominal: 1.25 TFLOP/s FP64 = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.gpu)], stdout=open(self.path, "w"),
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------------------
+# roofline traffic from a committed ncu summary (bytes per launch), if current
+# ---------------------------------------------------------------------------
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    with open(os.path.join(ROOT, "paper_1701_03989_gb300", "csrc", "kernels_gram.cu"), "rb") as f:
+        h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic():
+    """DRAM bytes per launch of the Gram kernel from profiles/, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "gram_partial_poisson3d_128.txt")
+    if not os.path.exists(path):
+        return None, None
+    vals = {}
+    for line in open(path):
+        if ":" in line and line.split(":", 1)[0].strip() in ("source_hash", "dram_bytes_per_launch_full"):
+            k, v = line.split(":", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("source_hash") != kernel_source_hash():
+        return None, "kernel changed since the ncu capture"
+    try:
+        return float(vals["dram_bytes_per_launch_full"]), None
+    except (KeyError, ValueError):
+        return None, "no traffic figure"
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(cfg, seconds: float):
+    """Times whole oracle blocks of the adaptive solve (sbar = 16, Chebyshev).
+
+    p and r come from 24 classical oracle iterations (untimed), so the timed
+    blocks are steady-state blocks. Each block runs the oracle's matrix powers,
+    Gram, block controller and recovery. Returns (iterations, seconds, blocks).
+    """
+    from oracle import ascg_oracle as O
+    A = O.Operator.from_csr(cfg["A"])
+    b = cfg["b"]
+    warm = O.classical_cg(A, b, np.zeros(A.n), eps_target=0.0, max_iters=24)
+    x, r, p = warm.x, warm.r, warm.p
+    bp = O.chebyshev_params(cfg["lam"][0], cfg["lam"][1], 16)
+    eps_star = 1e-12 * O.norm2(b)
+    iters, blocks = 0, 0
+    t0 = time.perf_counter()
+    while True:
+        Y = O.matrix_powers(A, p, r, 16, bp)
+        G = O.gram(Y)
+        blk, inner, idx = O.adaptive_block(G, 16, bp, eps_star, 1.0, A.n, True, 10 ** 6)
+        x, r, p = O.recover(Y[:, idx], x, inner.xc, inner.rc, inner.pc)
+        iters += inner.steps
+        blocks += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            return iters, el, blocks
+
+
+def reference_arm(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    import workloads as W
+    cfg = W.poisson3d_128()
+    for _ in range(args.warmup):
+        oracle_sample(cfg, 1.0)
+    its, secs = 0, 0.0
+    for _ in range(args.steps):
+        i, s, _b = oracle_sample(cfg, 10.0)
+        its += i
+        secs += s
+    v = its / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "parallelism": "replicas only"},
+        "cpu_baseline": {"value": v, "unit": "iters/s", "cores": 1, "kind": "oracle",
+                         "sample": "per step: >=10 s of whole steady-state oracle blocks (sbar=16, Chebyshev) "
+                                   "after 24 untimed classical iterations"},
+        "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def our_arm(args):
+    rank, world, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1701_03989_gb300 import build as B
+    if rank == 0 or world == 1:
+        B.build_all()
+    if world > 1:
+        dist.barrier()
+        B.build_all()
+    import paper_1701_03989_gb300 as P
+    import workloads as W
+
+    cfg = W.poisson3d_128()
+    A, b = cfg["A"], cfg["b"]
+    n = A.n
+    op = P.ascg_op_create_csr(n, A.nnz, A.rowptr, A.colind, A.val, 0)
+    stream = torch.cuda.current_stream()
+    bd = torch.from_numpy(b).cuda()
+    xd = torch.zeros(n, dtype=torch.float64, device="cuda")
+    max_it = 20000
+    o = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
+                       max_iters=max_it, timing=True)
+
+    def solve_once():
+        xd.zero_()
+        return P.ascg_solve(op, bd, xd, o, stream=stream)
+
+    for _ in range(args.warmup):
+        solve_once()
+    torch.cuda.synchronize()
+
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] if world == 1 else local
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    time.sleep(0.3)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    results = [solve_once() for _ in range(args.steps)]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    iters = sum(r.iters for r in results)
+    if world > 1:
+        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+        tsum = t.clone()
+        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+        ms_job, iters_job = float(tmax[0]), float(tsum[1])
+    else:
+        ms_job, iters_job = ms, float(iters)
+    value = iters_job / (ms_job * 1e-3)
+    ok = all(r.status == P.ASCG_OK for r in results)
+
+    # per-kernel device times recorded by the library with CUDA events on this stream
+    t_gram = sum(r.t_gram_ms for r in results)
+    n_gram = sum(r.gram_launches for r in results)
+    f_gram = sum(r.gram_flops for r in results)
+    t_mpk = sum(r.t_mpk_ms for r in results)
+    t_ctrl = sum(r.t_ctrl_ms for r in results)
+    t_rec = sum(r.t_recover_ms for r in results)
+    bytes_alg = sum(r.mpk_bytes + r.gram_bytes + r.recover_bytes for r in results)
+    flops_alg = sum(r.mpk_flops + r.gram_flops + r.recover_flops for r in results)
+    peak_tf = FP64_FMA_PER_CLK_SM * 2 * SMS * SM_MAX_MHZ * 1e6 / 1e12
+    achieved_tf = f_gram / (t_gram * 1e-3) / 1e12 if t_gram > 0 else None
+    traffic_full, traffic_note = committed_traffic()
+    per_launch_flops = f_gram / n_gram if n_gram else None
+
+    # end to end: host buffers through ascg_solve_host, copies inside the timed region
+    bh = torch.from_numpy(b).pin_memory()
+    xh = torch.zeros(n, dtype=torch.float64).pin_memory()
+    o_e2e = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
+                           max_iters=max_it)
+    P.ascg_solve_host(op, bh, xh, o_e2e, stream=stream)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_iters = 0
+    for _ in range(args.steps):
+        xh.zero_()
+        r = P.ascg_solve_host(op, bh, xh, o_e2e, stream=stream)
+        e2e_iters += r.iters
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s, float(e2e_iters)], dtype=torch.float64, device="cuda")
+        tm = t.clone()
+        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
+        ts = t.clone()
+        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
+        e2e_s, e2e_iters = float(tm[0]), float(ts[1])
+    e2e_value = e2e_iters / e2e_s
+
+    # classical CG on the same GPU, same problem, same target
+    classical = None
+    if not args.no_classical:
+        oc = P.make_options(method="classical", eps_target=1e-12, max_iters=max_it)
+        xd.zero_()
+        P.ascg_solve(op, bd, xd, oc, stream=stream)
+        torch.cuda.synchronize()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        cres = []
+        for _ in range(args.steps):
+            xd.zero_()
+            cres.append(P.ascg_solve(op, bd, xd, oc, stream=stream))
+        c1.record(stream)
+        torch.cuda.synchronize()
+        cms = c0.elapsed_time(c1) / args.steps
+        cit = sum(r.iters for r in cres) / args.steps
+        ams = ms / args.steps
+        classical = {"iters_per_s": cit / (cms * 1e-3), "iters_per_solve": cit, "ms_per_solve": cms,
+                     "adaptive_ms_per_solve": ams, "adaptive_iters_per_solve": iters / args.steps,
+                     "time_to_solution_speedup": cms / ams,
+                     "syncs_classical": sum(r.grid_reductions for r in cres) / args.steps,
+                     "syncs_adaptive": sum(r.grid_reductions for r in results) / args.steps,
+                     "true_res_classical": cres[-1].rel_res_true}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        ci, cs, cb = oracle_sample(cfg, 12.0)
+        cpu = {"value": ci / cs, "unit": "iters/s", "cores": 1, "kind": "oracle",
+               "sample": f"{cb} whole steady-state oracle blocks (sbar=16, Chebyshev, {ci} iterations) after 24 "
+                         f"untimed classical iterations, {cs:.1f} s"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "parallelism": "replicas only" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2: A 183 MB, basis 554 MB, vectors 16.8 MB each"},
+            "status_ok": ok,
+            "iters_per_solve": iters / args.steps,
+            "blocks_per_solve": sum(r.blocks for r in results) / args.steps,
+            "true_rel_res": results[-1].rel_res_true,
+            "hbm_gbs_algorithmic": bytes_alg / (sum(r.t_total_ms for r in results) * 1e-3) / 1e9,
+            "fp64_tflops_algorithmic": flops_alg / (sum(r.t_total_ms for r in results) * 1e-3) / 1e12,
+            "phase_ms_per_solve": {"matrix_powers": t_mpk / args.steps, "gram": t_gram / args.steps,
+                                   "controller": t_ctrl / args.steps, "recovery": t_rec / args.steps},
+            "roofline": {"bound": "alu", "kernel": "gram_partial_kernel<33>", "achieved": achieved_tf,
+                         "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+                         "traffic": traffic_full, "traffic_note": traffic_note,
+                         "flops_per_launch": per_launch_flops,
+                         "peak_source": "FP64 DFMA: 2 per clock per SM (nominal 1.25 TFLOP/s) x 152 SMs x 2070 MHz "
+                                        "max clock; FP64 is the binding unit (not HBM)"},
+            "vs_classical": classical,
+            "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 16 * n,
+                    "d2h_bytes_per_step": 8 * n},
+            "gpu_launches": sum(r.launches for r in results),
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    P.ascg_op_destroy(op)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    return our_arm(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

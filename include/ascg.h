@@ -1,0 +1,240 @@
+/*
+ * ascg.h - C ABI of libascg, an FP64 adaptive s-step conjugate gradient solver
+ * for one NVIDIA GB300 (sm_103a).
+ *
+ * Method: E. Carson, "The Adaptive s-step Conjugate Gradient Method",
+ * arXiv:1701.03989. Names below follow the paper's notation:
+ *   Alg. 1 classical CG; Alg. 2 s-step CG; Alg. 4 adaptive s-step CG;
+ *   eq. (polybasiscg) basis recurrence; eq. (cg-krylovbasis) bases P, R;
+ *   eq. (AVVB) A*Yunder = Y*B; eq. (coords) recovery; eq. (condy) choice of
+ *   s~_k; eq. (check) in-loop break test.
+ *
+ * Conventions for every call:
+ *  - Every call returns an ascg_status and never aborts. On an error,
+ *    ascg_last_error() returns a message (per thread, valid until the next
+ *    call on that thread).
+ *  - "device" pointers are CUDA device memory of the current device. "host"
+ *    pointers are ordinary (pageable or pinned) host memory.
+ *  - Calls are ordered on the given CUDA stream (NULL = the legacy default
+ *    stream). Calls that report results on the host (ascg_solve*,
+ *    ascg_block_step, ascg_newton_shifts) synchronise that stream before
+ *    they return. The others return as soon as their work is enqueued.
+ *  - Sizes are int64_t. Matrices have n >= 1 rows and nnz < 2^31 nonzeros.
+ *  - All arithmetic is IEEE double. eps = 2^-53.
+ *  - An ascg_op is not safe for concurrent use from several threads or
+ *    streams: it owns one workspace.
+ */
+#ifndef ASCG_H
+#define ASCG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque operator handle: owns device copies of a CSR matrix and a workspace. */
+typedef struct ascg_op_s* ascg_op;
+
+#define ASCG_MAX_S 16                     /* largest s (s_max) supported   */
+#define ASCG_MAX_W (2 * ASCG_MAX_S + 1)   /* basis columns at s = s_max    */
+
+typedef enum {
+  ASCG_OK = 0,
+  ASCG_ERR_INVALID = 1,      /* bad argument or malformed CSR                    */
+  ASCG_ERR_OOM = 2,          /* device allocation failed                         */
+  ASCG_ERR_CUDA = 3,         /* a CUDA runtime call failed                       */
+  ASCG_ERR_BREAKDOWN = 4,    /* a block could not take a single inner step       */
+  ASCG_NOT_CONVERGED = 5,    /* max_iters reached before the target              */
+  ASCG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up               */
+  ASCG_ERR_NOT_SPD = 7       /* a diagonal entry is missing or not positive      */
+} ascg_status;
+
+typedef enum {
+  ASCG_CLASSICAL = 0,        /* Alg. 1                                            */
+  ASCG_FIXED_S = 1,          /* Alg. 2 with s = s_max                             */
+  ASCG_ADAPTIVE = 2          /* Alg. 4                                            */
+} ascg_method;
+
+typedef enum {
+  ASCG_MONOMIAL = 0,         /* theta = sigma = 0, gamma = 1 (Sec. 2)             */
+  ASCG_NEWTON = 1,           /* Leja-ordered Ritz values as shifts                */
+  ASCG_CHEBYSHEV = 2         /* T_j((z - c)/h) on [lambda_min, lambda_max]        */
+} ascg_basis;
+
+/* Why a block's inner loop ended (Alg. 4). */
+typedef enum {
+  ASCG_STOP_DONE = 0,        /* ran all s~_k steps                                 */
+  ASCG_STOP_CONVERGED = 1,   /* sqrt(r'^T G r') <= eps* after step s_k             */
+  ASCG_STOP_BREAK = 2,       /* eq. (check) failed after step s_k                  */
+  ASCG_STOP_BREAKDOWN = 3,   /* a denominator was not positive and finite          */
+  ASCG_STOP_MAXITER = 4      /* the iteration cap ended the block                  */
+} ascg_stop;
+
+/* One record per outer loop (block) k. */
+typedef struct {
+  int sbar;                  /* basis size built, sbar_k                          */
+  int stilde;                /* size accepted by eq. (condy), s~_k                */
+  int s_k;                   /* inner steps taken                                 */
+  int stop;                  /* ascg_stop                                         */
+  int m;                     /* iterations done before this block                 */
+  int pad_;
+  double rnorm;              /* ||r_{m+1}|| = sqrt(G[r0, r0])                     */
+  double threshold;          /* eps* / (c eps ||r_{m+1}||), eq. (condy)           */
+  double gamma;              /* sqrt(kappa(G_{k,s~})) (+inf when uncertified)     */
+  double sqrt_kappa[ASCG_MAX_S]; /* sqrt(kappa(G_{k,i})), i = 1..sbar; +inf when
+                                    lambda_min <= (2i+1) sqrt(n) eps lambda_max;
+                                    0 where not computed                          */
+} ascg_block_info;
+
+typedef struct {
+  int method;                /* ascg_method                                       */
+  int basis;                 /* ascg_basis                                        */
+  int s_max;                 /* Alg. 4: s_max; Alg. 2: s. 1 <= s_max <= 16        */
+  int s0;                    /* sbar_0 (Alg. 4 "initial s value")                 */
+  int f;                     /* basis growth cap: sbar_k = min(s_{k-1}+f, s_max)  */
+  int newton_warmup;         /* classical steps whose Ritz values give the shifts */
+  int max_iters;             /* cap on total iterations                           */
+  int check_in_loop;         /* 1: eq. (check) break test on, 0: off (Sec. 3.2)   */
+  int flags;                 /* ASCG_FLAG_* bits                                  */
+  int pad_;
+  double eps_target;         /* relative target: eps* = eps_target * ||b||        */
+  double c;                  /* c_{k,j}, a constant (Alg. 4 "function c_{k,j}")   */
+  double lambda_min, lambda_max; /* Chebyshev interval (required for CHEBYSHEV)   */
+  /* optional host output buffers (may be NULL) */
+  double* res_hist; int res_hist_cap;   /* ||r_i||/||b||, i = 0 .. iters          */
+  int pad2_;
+  ascg_block_info* block_hist; int block_hist_cap;  /* per block                   */
+  int pad3_;
+  double* alpha_hist; double* beta_hist; int coef_hist_cap; /* alpha_i, beta_i     */
+  int pad4_;
+} ascg_options;
+
+#define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
+
+typedef struct {
+  int status;                /* ascg_status of the solve                          */
+  int iters;                 /* total CG iterations (warm-up included)            */
+  int blocks;                /* outer loops = global reductions of G              */
+  int grid_reductions;       /* device-wide reductions issued                     */
+  int wasted_vecs;           /* sum over blocks of 2 (sbar_k - s_k) basis vectors */
+  int launches;              /* kernels launched by this call                     */
+  double bnorm;              /* ||b||                                             */
+  double rel_res_updated;    /* last updated residual norm / ||b||                */
+  double rel_res_true;       /* ||b - A x|| / ||b|| of the returned x             */
+  /* device times (ms) when ASCG_FLAG_TIMING is set, else 0 */
+  double t_total_ms, t_mpk_ms, t_gram_ms, t_ctrl_ms, t_recover_ms, t_cg_ms;
+  int gram_launches;         /* Gram kernel launches timed in t_gram_ms            */
+  int pad_;
+  double gram_flops;         /* algorithmic FP64 flops of those launches          */
+  double gram_bytes;         /* algorithmic bytes read by those launches           */
+  double mpk_flops, mpk_bytes, recover_flops, recover_bytes;
+} ascg_result;
+
+/* Fills *o with the defaults: ADAPTIVE, MONOMIAL, s_max = 8, s0 = f = s_max,
+ * eps_target = 1e-10, c = 1, check_in_loop = 1, max_iters = 100000,
+ * newton_warmup = 0 (meaning 2 s_max), no history buffers. */
+ascg_status ascg_options_default(ascg_options* o);
+
+/* --- operator ------------------------------------------------------------ */
+
+/* Creates an operator from a square CSR matrix (the matrix A of Alg. 1-4).
+ * rowptr: int64[n+1], rowptr[0] = 0, non-decreasing, rowptr[n] = nnz;
+ * colind: int32[nnz] in [0, n); val: double[nnz]. Every row must hold a
+ * positive diagonal entry (else ASCG_ERR_NOT_SPD). A must be symmetric; that
+ * is not checked. on_device = 0: the three arrays are host memory;
+ * 1: device memory. The library copies them; the caller keeps ownership.
+ * On error *out is NULL. */
+ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr,
+                               const int32_t* colind, const double* val,
+                               int on_device, ascg_op* out);
+
+/* Frees the operator and its workspace. NULL is accepted. */
+ascg_status ascg_op_destroy(ascg_op op);
+
+/* n and nnz of the operator (host out-pointers may be NULL). */
+ascg_status ascg_op_size(ascg_op op, int64_t* n, int64_t* nnz);
+
+/* --- solve (Alg. 1, 2, 4) --------------------------------------------------- */
+
+/* Solves A x = b. b: device double[n]; x: device double[n], holds x_1 on entry
+ * and the solution on return. opts: host; NULL means the defaults. result:
+ * host, always written (result->status == the return value). Returns after
+ * the result is on the host. Returns ASCG_NOT_CONVERGED (with x = the last
+ * iterate) if max_iters is reached. */
+ascg_status ascg_solve(ascg_op op, const double* b, double* x, const ascg_options* opts,
+                       ascg_result* result, void* cuda_stream);
+
+/* As ascg_solve, with b and x in host memory. The library copies b and x_1 to
+ * the device and the solution back, on the same stream. */
+ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_options* opts,
+                            ascg_result* result, void* cuda_stream);
+
+/* --- steps of one block, exposed for testing (Alg. 4) --------------------------
+ * Basis layout used by every step: Y is column-major, leading dimension
+ * ldY >= n (device). The columns interleave the two bases of
+ * eq. (cg-krylovbasis):
+ *   column 2j   = rho_j(A) p,  j = 0..s     (P_{k,s})
+ *   column 2j+1 = rho_j(A) r,  j = 0..s-1   (R_{k,s})
+ * so w = 2s+1 columns. The i-step basis Y_{k,i} of Sec. 3.2 is then the
+ * leading 2i+1 columns, and every Gram submatrix G_{k,i} is a leading
+ * principal submatrix. */
+
+/* y = A x (device x, y of length n; x and y must not overlap). */
+ascg_status ascg_spmv(ascg_op op, const double* x, double* y, void* cuda_stream);
+
+/* Matrix powers, eq. (polybasiscg): on entry columns 0 (p) and 1 (r) of Y hold
+ * p and r. Fills columns 2..2s by
+ *   rho_{j+1} = ((A - theta_j) rho_j - sigma_{j-1} rho_{j-1}) / gamma_j.
+ * theta, sigma, gamma: host double[s] (eq. (polybasiscg) coefficients;
+ * sigma[j] multiplies rho_j when rho_{j+2} is formed). 1 <= s <= 16. */
+ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const double* sigma,
+                               const double* gamma, double* Y, int64_t ldY, void* cuda_stream);
+
+/* Gram matrix G = Y^T Y of the first w columns of Y (Sec. 2.1): device Y as
+ * above with n rows, device G double[w*w], row-major, symmetric (both halves
+ * written). 1 <= w <= 33. Sums run in a fixed order: the result is bitwise
+ * reproducible for a given n, w and device. */
+ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
+
+/* One block controller step on a given Gram matrix (Alg. 4 from "Determine
+ * s~_k" to the end of the inner loop). G: device double[(2 sbar+1)^2],
+ * interleaved order as above. method: ASCG_ADAPTIVE (eq. (condy) and, if
+ * check_in_loop, eq. (check)) or ASCG_FIXED_S (s~ = sbar, no test).
+ * nrows: length n of the basis vectors (sets the certification floor
+ * (2i+1) sqrt(n) eps of kappa(G_{k,i})). eps_star: absolute target.
+ * max_steps: cap on inner steps. bnorm: scales the residual history.
+ * Outputs: coords: device double[3 * (2 sbar+1)] = x', r', p' (interleaved
+ * order, zero beyond 2 s~+1); info: host record of the block; hist: host
+ * double[3 * sbar] = alpha_j, beta_j, sqrt(max(r'^T G r', 0))/bnorm for
+ * j = 1..s_k (may be NULL). Synchronises the stream. */
+ascg_status ascg_block_step(int sbar, const double* G, int method, const double* theta,
+                            const double* sigma, const double* gamma, int64_t nrows,
+                            double eps_star, double c, int check_in_loop, int max_steps,
+                            double bnorm, double* coords, ascg_block_info* info, double* hist,
+                            void* cuda_stream);
+
+/* Recovery, eq. (coords): x += Y x', r = Y r', p = Y p' using the first w
+ * columns of Y. coords: device double[3w] (x', r', p'). x, r, p: device
+ * double[n]. r and p may alias columns 1 and 0 of Y (each row is read before
+ * it is written). */
+ascg_status ascg_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
+                         double* x, double* r, double* p, void* cuda_stream);
+
+/* Newton basis shifts: Ritz values of the Lanczos tridiagonal of k classical
+ * CG steps (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} =
+ * sqrt(beta_j)/alpha_j), put in Leja order (first the largest magnitude, then
+ * each next maximises the product of distances; ties to the larger value).
+ * alphas: host double[k], betas: host double[k-1]; shifts: host double[s]
+ * receives the first s values (s <= k <= 32). Synchronises the stream. */
+ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k, int s,
+                               double* shifts, void* cuda_stream);
+
+/* Message of the last error on this thread ("" if none). */
+const char* ascg_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ASCG_H */

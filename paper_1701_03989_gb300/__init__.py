@@ -1,0 +1,270 @@
+"""Python binding of libascg (include/ascg.h): argument marshalling only.
+
+Every function has the name of the C call it wraps and passes plain pointers
+and sizes. Arrays may be given as integers (raw pointers), numpy arrays (host
+memory), or objects with a `data_ptr()` method such as torch tensors (device
+or host memory, as the C call expects). PyTorch is not imported here; callers
+use it only to own device memory and streams.
+
+All numerical work runs in the CUDA kernels of libascg.so. If the library has
+not been built, importing this package raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libascg.so")
+
+ASCG_MAX_S = 16
+ASCG_MAX_W = 2 * ASCG_MAX_S + 1
+
+# ascg_status
+ASCG_OK, ASCG_ERR_INVALID, ASCG_ERR_OOM, ASCG_ERR_CUDA = 0, 1, 2, 3
+ASCG_ERR_BREAKDOWN, ASCG_NOT_CONVERGED, ASCG_ERR_TIMEOUT, ASCG_ERR_NOT_SPD = 4, 5, 6, 7
+STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_BREAKDOWN",
+                5: "NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_NOT_SPD"}
+# ascg_method / ascg_basis / ascg_stop
+ASCG_CLASSICAL, ASCG_FIXED_S, ASCG_ADAPTIVE = 0, 1, 2
+ASCG_MONOMIAL, ASCG_NEWTON, ASCG_CHEBYSHEV = 0, 1, 2
+ASCG_STOP_DONE, ASCG_STOP_CONVERGED, ASCG_STOP_BREAK, ASCG_STOP_BREAKDOWN, ASCG_STOP_MAXITER = 0, 1, 2, 3, 4
+ASCG_FLAG_TIMING = 1
+
+
+class ascg_block_info(C.Structure):
+    _fields_ = [("sbar", C.c_int), ("stilde", C.c_int), ("s_k", C.c_int), ("stop", C.c_int),
+                ("m", C.c_int), ("pad_", C.c_int), ("rnorm", C.c_double), ("threshold", C.c_double),
+                ("gamma", C.c_double), ("sqrt_kappa", C.c_double * ASCG_MAX_S)]
+
+
+class ascg_options(C.Structure):
+    _fields_ = [("method", C.c_int), ("basis", C.c_int), ("s_max", C.c_int), ("s0", C.c_int),
+                ("f", C.c_int), ("newton_warmup", C.c_int), ("max_iters", C.c_int),
+                ("check_in_loop", C.c_int), ("flags", C.c_int), ("pad_", C.c_int),
+                ("eps_target", C.c_double), ("c", C.c_double), ("lambda_min", C.c_double),
+                ("lambda_max", C.c_double),
+                ("res_hist", C.POINTER(C.c_double)), ("res_hist_cap", C.c_int), ("pad2_", C.c_int),
+                ("block_hist", C.POINTER(ascg_block_info)), ("block_hist_cap", C.c_int), ("pad3_", C.c_int),
+                ("alpha_hist", C.POINTER(C.c_double)), ("beta_hist", C.POINTER(C.c_double)),
+                ("coef_hist_cap", C.c_int), ("pad4_", C.c_int)]
+
+
+class ascg_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("blocks", C.c_int), ("grid_reductions", C.c_int),
+                ("wasted_vecs", C.c_int), ("launches", C.c_int), ("bnorm", C.c_double),
+                ("rel_res_updated", C.c_double), ("rel_res_true", C.c_double),
+                ("t_total_ms", C.c_double), ("t_mpk_ms", C.c_double), ("t_gram_ms", C.c_double),
+                ("t_ctrl_ms", C.c_double), ("t_recover_ms", C.c_double), ("t_cg_ms", C.c_double),
+                ("gram_launches", C.c_int), ("pad_", C.c_int), ("gram_flops", C.c_double),
+                ("gram_bytes", C.c_double), ("mpk_flops", C.c_double), ("mpk_bytes", C.c_double),
+                ("recover_flops", C.c_double), ("recover_bytes", C.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"libascg.so not found at {LIB_PATH}; build it with "
+            "`python -m paper_1701_03989_gb300.build` (there is no CPU fallback)")
+    lib = C.CDLL(LIB_PATH)
+    P = C.c_void_p
+    I64 = C.c_int64
+    sig = {
+        "ascg_options_default": (C.c_int, [C.POINTER(ascg_options)]),
+        "ascg_op_create_csr": (C.c_int, [I64, I64, P, P, P, C.c_int, C.POINTER(P)]),
+        "ascg_op_destroy": (C.c_int, [P]),
+        "ascg_op_size": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
+        "ascg_solve": (C.c_int, [P, P, P, C.POINTER(ascg_options), C.POINTER(ascg_result), P]),
+        "ascg_solve_host": (C.c_int, [P, P, P, C.POINTER(ascg_options), C.POINTER(ascg_result), P]),
+        "ascg_spmv": (C.c_int, [P, P, P, P]),
+        "ascg_matrix_powers": (C.c_int, [P, C.c_int, P, P, P, P, I64, P]),
+        "ascg_gram": (C.c_int, [I64, C.c_int, P, I64, P, P]),
+        "ascg_block_step": (C.c_int, [C.c_int, P, C.c_int, P, P, P, I64, C.c_double, C.c_double, C.c_int,
+                                      C.c_int, C.c_double, P, C.POINTER(ascg_block_info), P, P]),
+        "ascg_recover": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
+        "ascg_newton_shifts": (C.c_int, [P, P, C.c_int, C.c_int, P, P]),
+        "ascg_last_error": (C.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+_lib = _load()
+
+
+class AscgError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {STATUS_NAMES.get(status, status)}: {last_error()}")
+
+
+def _ptr(a):
+    """Raw address of an array-like: int, numpy array, or object with data_ptr()."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+def _stream(s):
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream  # torch.cuda.Stream
+
+
+def _check(status, where, ok=(ASCG_OK,)):
+    if status not in ok:
+        raise AscgError(status, where)
+    return status
+
+
+def last_error() -> str:
+    return _lib.ascg_last_error().decode()
+
+
+def ascg_options_default() -> ascg_options:
+    o = ascg_options()
+    _check(_lib.ascg_options_default(C.byref(o)), "ascg_options_default")
+    return o
+
+
+def ascg_op_create_csr(n, nnz, rowptr, colind, val, on_device=0):
+    """Returns an opaque operator handle (int). rowptr int64, colind int32, val float64."""
+    h = C.c_void_p()
+    _check(_lib.ascg_op_create_csr(int(n), int(nnz), _ptr(rowptr), _ptr(colind), _ptr(val), int(on_device),
+                                   C.byref(h)), "ascg_op_create_csr")
+    return h.value
+
+
+def ascg_op_destroy(op):
+    _check(_lib.ascg_op_destroy(op), "ascg_op_destroy")
+
+
+def ascg_op_size(op):
+    n, nnz = C.c_int64(), C.c_int64()
+    _check(_lib.ascg_op_size(op, C.byref(n), C.byref(nnz)), "ascg_op_size")
+    return n.value, nnz.value
+
+
+def ascg_solve(op, b, x, opts=None, stream=None, raise_on=(ASCG_OK, ASCG_NOT_CONVERGED)):
+    """b, x: device arrays. Returns the ascg_result struct."""
+    res = ascg_result()
+    st = _lib.ascg_solve(op, _ptr(b), _ptr(x), C.byref(opts) if opts is not None else None, C.byref(res),
+                         _stream(stream))
+    _check(st, "ascg_solve", raise_on)
+    return res
+
+
+def ascg_solve_host(op, b, x, opts=None, stream=None, raise_on=(ASCG_OK, ASCG_NOT_CONVERGED)):
+    """b, x: host arrays (x holds x_1 and receives the solution)."""
+    res = ascg_result()
+    st = _lib.ascg_solve_host(op, _ptr(b), _ptr(x), C.byref(opts) if opts is not None else None, C.byref(res),
+                              _stream(stream))
+    _check(st, "ascg_solve_host", raise_on)
+    return res
+
+
+def ascg_spmv(op, x, y, stream=None):
+    _check(_lib.ascg_spmv(op, _ptr(x), _ptr(y), _stream(stream)), "ascg_spmv")
+
+
+def ascg_matrix_powers(op, s, theta, sigma, gamma, Y, ldY, stream=None):
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    gm = np.ascontiguousarray(gamma, dtype=np.float64)
+    _check(_lib.ascg_matrix_powers(op, int(s), _ptr(th), _ptr(sg), _ptr(gm), _ptr(Y), int(ldY), _stream(stream)),
+           "ascg_matrix_powers")
+
+
+def ascg_gram(n, w, Y, ldY, G, stream=None):
+    _check(_lib.ascg_gram(int(n), int(w), _ptr(Y), int(ldY), _ptr(G), _stream(stream)), "ascg_gram")
+
+
+def ascg_block_step(sbar, G, method, theta, sigma, gamma, nrows, eps_star, c, check_in_loop, max_steps, bnorm,
+                    coords, stream=None):
+    """Returns (ascg_block_info, hist ndarray [s_k, 3] of alpha, beta, relres)."""
+    th = np.ascontiguousarray(theta, dtype=np.float64)
+    sg = np.ascontiguousarray(sigma, dtype=np.float64)
+    gm = np.ascontiguousarray(gamma, dtype=np.float64)
+    info = ascg_block_info()
+    hist = np.zeros(3 * ASCG_MAX_S)
+    _check(_lib.ascg_block_step(int(sbar), _ptr(G), int(method), _ptr(th), _ptr(sg), _ptr(gm), int(nrows),
+                                float(eps_star), float(c), int(check_in_loop), int(max_steps), float(bnorm),
+                                _ptr(coords), C.byref(info), _ptr(hist), _stream(stream)), "ascg_block_step")
+    return info, hist[: 3 * max(info.s_k, 0)].reshape(-1, 3)
+
+
+def ascg_recover(n, w, Y, ldY, coords, x, r, p, stream=None):
+    _check(_lib.ascg_recover(int(n), int(w), _ptr(Y), int(ldY), _ptr(coords), _ptr(x), _ptr(r), _ptr(p),
+                             _stream(stream)), "ascg_recover")
+
+
+def ascg_newton_shifts(alphas, betas, k, s, stream=None):
+    al = np.ascontiguousarray(alphas, dtype=np.float64)
+    be = np.ascontiguousarray(betas if len(betas) else [0.0], dtype=np.float64)
+    out = np.zeros(s)
+    _check(_lib.ascg_newton_shifts(_ptr(al), _ptr(be), int(k), int(s), _ptr(out), _stream(stream)),
+           "ascg_newton_shifts")
+    return out
+
+
+# --- convenience: options from keywords -------------------------------------
+
+_METHODS = {"classical": ASCG_CLASSICAL, "fixed": ASCG_FIXED_S, "adaptive": ASCG_ADAPTIVE}
+_BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CHEBYSHEV}
+
+
+def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
+                 lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
+                 res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None) -> ascg_options:
+    """ascg_options filled from keywords. History arrays are numpy (float64) or a
+    ctypes array of ascg_block_info; the caller keeps them alive for the call."""
+    o = ascg_options_default()
+    o.method = _METHODS[method] if isinstance(method, str) else int(method)
+    o.basis = _BASES[basis] if isinstance(basis, str) else int(basis)
+    o.s_max = int(s_max)
+    o.s0 = int(s_max if s0 is None else s0)
+    o.f = int(s_max if f is None else f)
+    o.eps_target = float(eps_target)
+    o.c = float(c)
+    if lam is not None:
+        o.lambda_min, o.lambda_max = float(lam[0]), float(lam[1])
+    o.newton_warmup = int(newton_warmup)
+    o.max_iters = int(max_iters)
+    o.check_in_loop = 1 if check_in_loop else 0
+    o.flags = ASCG_FLAG_TIMING if timing else 0
+    if res_hist is not None:
+        o.res_hist = res_hist.ctypes.data_as(C.POINTER(C.c_double))
+        o.res_hist_cap = len(res_hist)
+    if block_hist is not None:
+        o.block_hist = C.cast(block_hist, C.POINTER(ascg_block_info))
+        o.block_hist_cap = len(block_hist)
+    if alpha_hist is not None and beta_hist is not None:
+        o.alpha_hist = alpha_hist.ctypes.data_as(C.POINTER(C.c_double))
+        o.beta_hist = beta_hist.ctypes.data_as(C.POINTER(C.c_double))
+        o.coef_hist_cap = min(len(alpha_hist), len(beta_hist))
+    return o
+
+
+def block_infos(count: int):
+    """A ctypes array of ascg_block_info for options.block_hist."""
+    return (ascg_block_info * count)()
+
+
+EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
+            "ascg_solve_host", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_block_step", "ascg_recover",
+            "ascg_newton_shifts", "ascg_last_error"]

@@ -1,0 +1,763 @@
+// Host side of the libascg C ABI (include/ascg.h): operator, workspace and the
+// solve drivers for Alg. 1 (classical CG), Alg. 2 (fixed s) and Alg. 4
+// (adaptive s).
+//
+// Per block the device runs, in stream order: s matrix powers steps, the Gram
+// partials and their fixed-order sum (the block's single grid-wide
+// reduction, Sec. 2.1), the condition estimates, the controller, and the
+// recovery. The host reads back one small status record per block, since the
+// next block's basis size sbar_k = min(s_{k-1} + f, s_max) depends on it.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "ascg_common.cuh"
+
+using namespace ascg;
+
+namespace {
+
+thread_local std::string g_err;
+
+ascg_status fail(ascg_status st, const std::string& msg) {
+  g_err = msg;
+  return st;
+}
+
+#define ASCG_CUDA(call)                                                                        \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(e_ == cudaErrorMemoryAllocation ? ASCG_ERR_OOM : ASCG_ERR_CUDA,              \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                         \
+  } while (0)
+
+#define ASCG_TRY(expr)              \
+  do {                              \
+    ascg_status s_ = (expr);        \
+    if (s_ != ASCG_OK) return s_;   \
+  } while (0)
+
+template <class T>
+ascg_status dev_alloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(ASCG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return ASCG_OK;
+}
+
+template <class T>
+void dev_free(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+// Device workspace owned by an operator; grows on demand.
+struct Workspace {
+  int64_t n = 0;
+  int wcols = 0;
+  int64_t ldY = 0;
+  double* Y = nullptr;
+  double* b = nullptr;      // for host-buffer solves
+  double* x = nullptr;      // for host-buffer solves
+  double* q = nullptr;      // classical CG: A p; also a scratch vector
+  double* partials = nullptr;
+  int64_t partials_cap = 0;
+  unsigned* counter = nullptr;
+  double* G = nullptr;      // kMaxW^2
+  double* coords = nullptr; // 3 kMaxW
+  double* params = nullptr; // theta, sigma, gamma: 3 kMaxS
+  double* scal = nullptr;   // 4 scalars
+  double* shifts = nullptr; // 32
+  BlockState* bst = nullptr;
+  CGState* cgs = nullptr;
+  double* res_hist = nullptr;
+  int res_cap = 0;
+  double* ab_hist = nullptr;  // alpha[ab_cap], beta[ab_cap]
+  int ab_cap = 0;
+  // pinned host mirrors
+  BlockState* h_bst = nullptr;
+  CGState* h_cgs = nullptr;
+  double* h_scal = nullptr;
+  cudaEvent_t ev[8] = {};
+  bool events = false;
+
+  void release() {
+    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(counter);
+    dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
+    dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
+    if (h_bst) cudaFreeHost(h_bst);
+    if (h_cgs) cudaFreeHost(h_cgs);
+    if (h_scal) cudaFreeHost(h_scal);
+    h_bst = nullptr; h_cgs = nullptr; h_scal = nullptr;
+    if (events)
+      for (auto& e : ev) cudaEventDestroy(e);
+    events = false;
+    n = 0; wcols = 0; ldY = 0; partials_cap = 0; res_cap = 0; ab_cap = 0;
+  }
+};
+
+}  // namespace
+
+struct ascg_op_s {
+  int64_t n = 0, nnz = 0;
+  int device = 0;
+  int32_t* rowptr = nullptr;
+  int32_t* colind = nullptr;
+  double* val = nullptr;
+  Workspace ws;
+  DevCSR csr() const { return DevCSR{n, nnz, rowptr, colind, val}; }
+};
+
+namespace {
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+// Ensures the workspace can hold n rows, wcols basis columns and histories of
+// res_cap entries.
+ascg_status ensure(ascg_op op, int wcols, int res_cap) {
+  Workspace& w = op->ws;
+  const int64_t n = op->n;
+  if (!w.counter) {
+    ASCG_TRY(dev_alloc(&w.counter, 1));
+    ASCG_CUDA(cudaMemset(w.counter, 0, sizeof(unsigned)));
+    ASCG_TRY(dev_alloc(&w.G, kMaxW * kMaxW));
+    ASCG_TRY(dev_alloc(&w.coords, 3 * kMaxW));
+    ASCG_TRY(dev_alloc(&w.params, 3 * kMaxS));
+    ASCG_TRY(dev_alloc(&w.scal, 4));
+    ASCG_TRY(dev_alloc(&w.shifts, 32));
+    ASCG_TRY(dev_alloc(&w.bst, 1));
+    ASCG_TRY(dev_alloc(&w.cgs, 1));
+    ASCG_CUDA(cudaMallocHost((void**)&w.h_bst, sizeof(BlockState)));
+    ASCG_CUDA(cudaMallocHost((void**)&w.h_cgs, sizeof(CGState)));
+    ASCG_CUDA(cudaMallocHost((void**)&w.h_scal, 4 * sizeof(double)));
+    for (auto& e : w.ev) ASCG_CUDA(cudaEventCreate(&e));
+    w.events = true;
+  }
+  if (w.n != n || w.wcols < wcols) {
+    dev_free(w.Y); dev_free(w.q);
+    const int64_t ld = round_up(n, 32);  // 256-byte aligned columns
+    const int cols = wcols > 2 ? wcols : 2;
+    ASCG_TRY(dev_alloc(&w.Y, (size_t)(cols * ld)));
+    ASCG_TRY(dev_alloc(&w.q, (size_t)n));
+    w.ldY = ld;
+    w.wcols = cols;
+    w.n = n;
+  }
+  const int64_t spmv_blocks = (n + kSpmvRows - 1) / kSpmvRows;
+  const int64_t pcap = std::max<int64_t>(std::max<int64_t>(spmv_blocks, kRedBlocks),
+                                         (int64_t)gram_grid() * kMaxPairs);
+  if (w.partials_cap < pcap) {
+    dev_free(w.partials);
+    ASCG_TRY(dev_alloc(&w.partials, (size_t)pcap));
+    w.partials_cap = pcap;
+  }
+  if (w.res_cap < res_cap) {
+    dev_free(w.res_hist); dev_free(w.ab_hist);
+    ASCG_TRY(dev_alloc(&w.res_hist, (size_t)res_cap));
+    ASCG_TRY(dev_alloc(&w.ab_hist, (size_t)2 * res_cap));
+    w.res_cap = res_cap;
+    w.ab_cap = res_cap;
+  }
+  return ASCG_OK;
+}
+
+ascg_status check_opts(const ascg_options& o) {
+  if (o.method != ASCG_CLASSICAL && o.method != ASCG_FIXED_S && o.method != ASCG_ADAPTIVE)
+    return fail(ASCG_ERR_INVALID, "unknown method");
+  if (o.method != ASCG_CLASSICAL) {
+    if (o.s_max < 1 || o.s_max > ASCG_MAX_S) return fail(ASCG_ERR_INVALID, "s_max must be in 1..16");
+    if (o.s0 < 1 || o.s0 > o.s_max) return fail(ASCG_ERR_INVALID, "s0 must be in 1..s_max");
+    if (o.f < 1) return fail(ASCG_ERR_INVALID, "f must be >= 1");
+    if (o.basis != ASCG_MONOMIAL && o.basis != ASCG_NEWTON && o.basis != ASCG_CHEBYSHEV)
+      return fail(ASCG_ERR_INVALID, "unknown basis");
+    if (o.basis == ASCG_CHEBYSHEV && !(o.lambda_max > o.lambda_min))
+      return fail(ASCG_ERR_INVALID, "Chebyshev basis needs lambda_max > lambda_min");
+    if (o.basis == ASCG_NEWTON) {
+      const int nw = o.newton_warmup > 0 ? o.newton_warmup : 2 * o.s_max;
+      if (nw < o.s_max || nw > 32) return fail(ASCG_ERR_INVALID, "newton_warmup must be in s_max..32");
+    }
+  }
+  if (!(o.eps_target >= 0.0)) return fail(ASCG_ERR_INVALID, "eps_target must be >= 0");
+  if (!(o.c > 0.0)) return fail(ASCG_ERR_INVALID, "c must be > 0");
+  if (o.max_iters < 0) return fail(ASCG_ERR_INVALID, "max_iters must be >= 0");
+  return ASCG_OK;
+}
+
+// theta, sigma, gamma of eq. (polybasiscg) for monomial and Chebyshev bases.
+void basis_params(const ascg_options& o, double* th, double* sg, double* gm) {
+  for (int j = 0; j < kMaxS; ++j) {
+    th[j] = 0.0;
+    sg[j] = 0.0;
+    gm[j] = 1.0;
+  }
+  if (o.basis == ASCG_CHEBYSHEV) {
+    // rho_j(z) = T_j((z - c)/h): theta_j = c, gamma_0 = h, gamma_j = h/2, sigma_j = h/2
+    const double c = (o.lambda_max + o.lambda_min) / 2, h = (o.lambda_max - o.lambda_min) / 2;
+    for (int j = 0; j < kMaxS; ++j) {
+      th[j] = c;
+      sg[j] = h / 2;
+      gm[j] = j == 0 ? h : h / 2;
+    }
+  }
+}
+
+// Runs classical CG iterations (Alg. 1) on the device until the CG state says
+// done. x, r, p, q are device vectors. Returns the iterations done by this call.
+ascg_status run_classical(ascg_op op, double* x, double* r, double* p, double eps_star, double bnorm,
+                          int max_iters, int iter0, cudaStream_t s, ascg_result* res, bool timing) {
+  Workspace& w = op->ws;
+  const int64_t n = op->n;
+  const DevCSR A = op->csr();
+  ASCG_CUDA(launch_dot(r, r, n, &w.cgs->rr, w.partials, w.counter, s));
+  ASCG_CUDA(launch_cg_init(w.cgs, eps_star, bnorm, max_iters, iter0, w.res_hist, w.res_cap, s));
+  res->launches += 2;
+  res->grid_reductions += 1;
+  if (timing) ASCG_CUDA(cudaEventRecord(w.ev[6], s));
+  int batch = 8;
+  for (;;) {
+    for (int i = 0; i < batch; ++i) {
+      ASCG_CUDA(launch_cg_spmv_dot(A, p, w.q, w.cgs, w.partials, w.counter, s));
+      ASCG_CUDA(launch_cg_update(n, x, r, p, w.q, w.cgs, w.partials, w.counter, w.res_hist, w.res_cap,
+                                 w.ab_hist, w.ab_hist + w.ab_cap, w.ab_cap, s));
+      ASCG_CUDA(launch_cg_pupdate(n, r, p, w.cgs, s));
+    }
+    res->launches += 3 * batch;
+    ASCG_CUDA(cudaMemcpyAsync(w.h_cgs, w.cgs, sizeof(CGState), cudaMemcpyDeviceToHost, s));
+    ASCG_CUDA(cudaStreamSynchronize(s));
+    if (w.h_cgs->done) break;
+    if (batch < 64) batch *= 2;
+  }
+  if (timing) {
+    ASCG_CUDA(cudaEventRecord(w.ev[7], s));
+    ASCG_CUDA(cudaEventSynchronize(w.ev[7]));
+    float ms = 0.f;
+    ASCG_CUDA(cudaEventElapsedTime(&ms, w.ev[6], w.ev[7]));
+    res->t_cg_ms += ms;
+  }
+  res->grid_reductions += 2 * (w.h_cgs->iter - iter0);
+  return ASCG_OK;
+}
+
+ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_options& o, ascg_result* res,
+                         cudaStream_t s) {
+  Workspace& w = op->ws;
+  const int64_t n = op->n;
+  const DevCSR A = op->csr();
+  const bool sstep = o.method != ASCG_CLASSICAL;
+  const int wmax = sstep ? 2 * o.s_max + 1 : 2;
+  ASCG_TRY(ensure(op, wmax, o.max_iters + 2));
+  const bool timing = (o.flags & ASCG_FLAG_TIMING) != 0;
+  if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
+
+  // ||b||, r_1 = b - A x_1, p_1 = r_1 (Alg. 1/4 first line). p = column 0 and
+  // r = column 1 of the basis buffer.
+  double* p = w.Y;
+  double* r = w.Y + w.ldY;
+  ASCG_CUDA(launch_dot(b, b, n, &w.scal[0], w.partials, w.counter, s));
+  ASCG_CUDA(launch_residual(A, b, x, r, p, s));
+  res->launches += 2;
+  res->grid_reductions += 1;
+  ASCG_CUDA(cudaMemcpyAsync(w.h_scal, w.scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  ASCG_CUDA(cudaStreamSynchronize(s));
+  const double bnorm = std::sqrt(w.h_scal[0]);
+  res->bnorm = bnorm;
+  if (!(bnorm > 0.0) || !std::isfinite(bnorm)) {
+    if (bnorm == 0.0) {  // b = 0: x = 0 is the solution
+      ASCG_CUDA(cudaMemsetAsync(x, 0, n * sizeof(double), s));
+      ASCG_CUDA(cudaStreamSynchronize(s));
+      res->status = ASCG_OK;
+      return ASCG_OK;
+    }
+    return fail(ASCG_ERR_INVALID, "b is not finite");
+  }
+  const double eps_star = o.eps_target * bnorm;
+  int m = 0;
+  ascg_status final_status = ASCG_OK;
+
+  if (!sstep) {
+    ASCG_TRY(run_classical(op, x, r, p, eps_star, bnorm, o.max_iters, 0, s, res, timing));
+    m = w.h_cgs->iter;
+    final_status = w.h_cgs->converged ? ASCG_OK : ASCG_NOT_CONVERGED;
+    res->rel_res_updated = std::sqrt(std::max(w.h_cgs->rr, 0.0)) / bnorm;
+  } else {
+    double th[kMaxS], sg[kMaxS], gm[kMaxS];
+    basis_params(o, th, sg, gm);
+    bool done = false;
+    // the residual history entry for i = 1 (m = 0)
+    ASCG_CUDA(launch_dot(r, r, n, &w.scal[1], w.partials, w.counter, s));
+    ASCG_CUDA(cudaMemcpyAsync(w.h_scal + 1, w.scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    ASCG_CUDA(cudaStreamSynchronize(s));
+    res->launches += 1;
+    res->grid_reductions += 1;
+    double r0 = std::sqrt(std::max(w.h_scal[1], 0.0));
+    {
+      const double rel = r0 / bnorm;
+      ASCG_CUDA(cudaMemcpyAsync(w.res_hist, &rel, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
+    res->rel_res_updated = r0 / bnorm;
+    if (r0 <= eps_star) done = true;
+    if (!done && o.basis == ASCG_NEWTON) {
+      // 2 s_max classical steps; the Ritz values of their Lanczos tridiagonal,
+      // in Leja order, are the shifts theta_j of the Newton basis.
+      const int nw = o.newton_warmup > 0 ? o.newton_warmup : 2 * o.s_max;
+      const int cap = std::min(nw, o.max_iters);
+      ASCG_TRY(run_classical(op, x, r, p, eps_star, bnorm, cap, 0, s, res, timing));
+      m = w.h_cgs->iter;
+      res->rel_res_updated = std::sqrt(std::max(w.h_cgs->rr, 0.0)) / bnorm;
+      if (w.h_cgs->converged) done = true;
+      if (!done && m >= o.max_iters) {
+        done = true;
+        final_status = ASCG_NOT_CONVERGED;
+      }
+      if (!done) {
+        if (m < o.s_max) return fail(ASCG_ERR_BREAKDOWN, "Newton warm-up ended early");
+        ASCG_CUDA(launch_newton_shifts(w.ab_hist, w.ab_hist + w.ab_cap, m, w.shifts, s));
+        res->launches += 1;
+        double sh[32];
+        ASCG_CUDA(cudaMemcpyAsync(sh, w.shifts, m * sizeof(double), cudaMemcpyDeviceToHost, s));
+        ASCG_CUDA(cudaStreamSynchronize(s));
+        for (int j = 0; j < kMaxS; ++j) th[j] = j < o.s_max ? sh[j] : 0.0;
+      }
+    }
+    double hp[3 * kMaxS];
+    std::memcpy(hp, th, sizeof(th));
+    std::memcpy(hp + kMaxS, sg, sizeof(sg));
+    std::memcpy(hp + 2 * kMaxS, gm, sizeof(gm));
+    ASCG_CUDA(cudaMemcpyAsync(w.params, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
+    const double sqrt_n = std::sqrt((double)n);
+    int k = 0, s_prev = 0;
+    int nb_info = 0;
+    while (!done) {
+      const int sbar = o.method == ASCG_FIXED_S ? o.s_max : (k == 0 ? o.s0 : std::min(s_prev + o.f, o.s_max));
+      const int wb = 2 * sbar + 1;
+      BlockState& hb = *w.h_bst;
+      std::memset(&hb, 0, sizeof(hb));
+      hb.sbar = sbar;
+      hb.method = o.method;
+      hb.check_in_loop = o.check_in_loop;
+      hb.max_steps = o.max_iters - m;
+      hb.m = m;
+      hb.k = k;
+      hb.eps_star = eps_star;
+      hb.c = o.c;
+      hb.bnorm = bnorm;
+      hb.sqrt_n = sqrt_n;
+      ASCG_CUDA(cudaMemcpyAsync(w.bst, &hb, sizeof(BlockState), cudaMemcpyHostToDevice, s));
+      // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
+      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
+      for (int j = 0; j < sbar; ++j) {
+        ASCG_CUDA(launch_mpk_step(A, w.Y, w.ldY, j, 1, j < sbar - 1, th[j], j >= 1 ? sg[j - 1] : 0.0, gm[j], s));
+      }
+      res->launches += sbar;
+      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
+      // Gram: the block's one grid-wide reduction
+      ASCG_CUDA(launch_gram_partial(n, wb, w.Y, w.ldY, w.partials, s));
+      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
+      ASCG_CUDA(launch_gram_finalize(wb, w.partials, gram_parts(n), w.G, s));
+      res->launches += 2;
+      res->grid_reductions += 1;
+      if (o.method == ASCG_ADAPTIVE) {
+        ASCG_CUDA(launch_kappa(w.G, w.bst, sbar, s));
+        res->launches += 1;
+      }
+      ASCG_CUDA(launch_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, w.coords, nullptr,
+                            w.res_hist, w.res_cap, w.ab_hist, w.ab_cap, s));
+      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[4], s));
+      ASCG_CUDA(launch_recover(n, wb, w.Y, w.ldY, w.coords, x, r, p, s));
+      res->launches += 2;
+      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[5], s));
+      ASCG_CUDA(cudaMemcpyAsync(w.h_bst, w.bst, sizeof(BlockState), cudaMemcpyDeviceToHost, s));
+      ASCG_CUDA(cudaStreamSynchronize(s));
+      if (timing) {
+        float a = 0.f, b2 = 0.f, c2 = 0.f, d2 = 0.f;
+        ASCG_CUDA(cudaEventElapsedTime(&a, w.ev[1], w.ev[2]));
+        ASCG_CUDA(cudaEventElapsedTime(&b2, w.ev[2], w.ev[3]));
+        ASCG_CUDA(cudaEventElapsedTime(&c2, w.ev[3], w.ev[4]));
+        ASCG_CUDA(cudaEventElapsedTime(&d2, w.ev[4], w.ev[5]));
+        res->t_mpk_ms += a;
+        res->t_gram_ms += b2;
+        res->t_ctrl_ms += c2;
+        res->t_recover_ms += d2;
+        res->gram_launches += 1;
+        res->gram_flops += 2.0 * (double)wb * (wb + 1) / 2.0 * (double)n;
+        res->gram_bytes += 8.0 * (double)wb * (double)n;
+        // per step: nnz FMAs per chain, plus the recurrence terms
+        const double nchains = 2.0 * sbar - 1.0;
+        res->mpk_flops += nchains * 2.0 * (double)op->nnz;
+        res->mpk_bytes += (double)sbar * (12.0 * op->nnz + 4.0 * (n + 1)) + nchains * 16.0 * n + 8.0 * n;
+        res->recover_flops += 3.0 * 2.0 * wb * (double)n;
+        res->recover_bytes += 8.0 * (wb + 1) * (double)n + 24.0 * n;
+      }
+      const BlockState& out = *w.h_bst;
+      if (o.block_hist && nb_info < o.block_hist_cap) {
+        ascg_block_info& bi = o.block_hist[nb_info];
+        std::memset(&bi, 0, sizeof(bi));
+        bi.sbar = sbar;
+        bi.stilde = out.stilde;
+        bi.s_k = out.s_k;
+        bi.stop = out.stop;
+        bi.m = m;
+        bi.rnorm = out.rnorm;
+        bi.threshold = out.threshold;
+        bi.gamma = out.gamma;
+        for (int i = 0; i < sbar; ++i) bi.sqrt_kappa[i] = o.method == ASCG_ADAPTIVE ? out.sqrt_kappa[i] : 0.0;
+      }
+      ++nb_info;
+      res->wasted_vecs += 2 * (sbar - out.s_k);
+      if (out.s_k == 0) {
+        final_status = ASCG_ERR_BREAKDOWN;
+        g_err = "breakdown: a block could not take an inner step";
+        break;
+      }
+      res->rel_res_updated = out.rel_res;
+      m += out.s_k;
+      s_prev = out.s_k;
+      ++k;
+      if (out.converged) break;
+      if (m >= o.max_iters) {
+        final_status = ASCG_NOT_CONVERGED;
+        break;
+      }
+    }
+    res->blocks = k;
+  }
+  res->iters = m;
+  // true residual ||b - A x|| / ||b||
+  ASCG_CUDA(launch_residual(A, b, x, w.q, nullptr, s));
+  ASCG_CUDA(launch_dot(w.q, w.q, n, &w.scal[2], w.partials, w.counter, s));
+  res->launches += 2;
+  if (timing) ASCG_CUDA(cudaEventRecord(w.ev[7], s));
+  ASCG_CUDA(cudaMemcpyAsync(w.h_scal + 2, w.scal + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  ASCG_CUDA(cudaStreamSynchronize(s));
+  res->rel_res_true = std::sqrt(w.h_scal[2]) / bnorm;
+  if (timing) {
+    float ms = 0.f;
+    ASCG_CUDA(cudaEventElapsedTime(&ms, w.ev[0], w.ev[7]));
+    res->t_total_ms = ms;
+  }
+  // histories to the caller
+  const int nh = m + 1;
+  if (o.res_hist && o.res_hist_cap > 0)
+    ASCG_CUDA(cudaMemcpy(o.res_hist, w.res_hist, sizeof(double) * std::min(nh, o.res_hist_cap),
+                         cudaMemcpyDeviceToHost));
+  if (o.alpha_hist && o.coef_hist_cap > 0 && m > 0)
+    ASCG_CUDA(cudaMemcpy(o.alpha_hist, w.ab_hist, sizeof(double) * std::min(m, o.coef_hist_cap),
+                         cudaMemcpyDeviceToHost));
+  if (o.beta_hist && o.coef_hist_cap > 0 && m > 0)
+    ASCG_CUDA(cudaMemcpy(o.beta_hist, w.ab_hist + w.ab_cap, sizeof(double) * std::min(m, o.coef_hist_cap),
+                         cudaMemcpyDeviceToHost));
+  res->status = final_status;
+  return final_status;
+}
+
+void zero_result(ascg_result* r) {
+  if (r) std::memset(r, 0, sizeof(*r));
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+ascg_status ascg_options_default(ascg_options* o) {
+  if (!o) return fail(ASCG_ERR_INVALID, "options pointer is NULL");
+  std::memset(o, 0, sizeof(*o));
+  o->method = ASCG_ADAPTIVE;
+  o->basis = ASCG_MONOMIAL;
+  o->s_max = 8;
+  o->s0 = 8;
+  o->f = 8;
+  o->newton_warmup = 0;
+  o->max_iters = 100000;
+  o->check_in_loop = 1;
+  o->eps_target = 1e-10;
+  o->c = 1.0;
+  return ASCG_OK;
+}
+
+ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, const int32_t* colind,
+                               const double* val, int on_device, ascg_op* out) {
+  g_err.clear();
+  if (!out) return fail(ASCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (n < 1) return fail(ASCG_ERR_INVALID, "n must be >= 1");
+  if (nnz < 0 || nnz >= (int64_t)1 << 31) return fail(ASCG_ERR_INVALID, "nnz must be in [0, 2^31)");
+  if (n >= (int64_t)1 << 31) return fail(ASCG_ERR_INVALID, "n must be < 2^31");
+  if (!rowptr || (nnz > 0 && (!colind || !val))) return fail(ASCG_ERR_INVALID, "NULL CSR array");
+  std::vector<int64_t> rp;
+  std::vector<int32_t> ci;
+  std::vector<double> va;
+  const int64_t* hrp = rowptr;
+  const int32_t* hci = colind;
+  const double* hva = val;
+  if (on_device) {
+    rp.resize(n + 1);
+    ci.resize(nnz);
+    va.resize(nnz);
+    ASCG_CUDA(cudaMemcpy(rp.data(), rowptr, sizeof(int64_t) * (n + 1), cudaMemcpyDeviceToHost));
+    if (nnz) {
+      ASCG_CUDA(cudaMemcpy(ci.data(), colind, sizeof(int32_t) * nnz, cudaMemcpyDeviceToHost));
+      ASCG_CUDA(cudaMemcpy(va.data(), val, sizeof(double) * nnz, cudaMemcpyDeviceToHost));
+    }
+    hrp = rp.data();
+    hci = ci.data();
+    hva = va.data();
+  }
+  if (hrp[0] != 0 || hrp[n] != nnz) return fail(ASCG_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] = nnz");
+  std::vector<int32_t> rp32(n + 1);
+  for (int64_t i = 0; i < n; ++i)  // all of rowptr first, so rows below index only [0, nnz)
+    if (hrp[i + 1] < hrp[i] || hrp[i + 1] > nnz) return fail(ASCG_ERR_INVALID, "rowptr is not non-decreasing");
+  for (int64_t i = 0; i < n; ++i) {
+    bool diag = false;
+    for (int64_t k = hrp[i]; k < hrp[i + 1]; ++k) {
+      const int32_t c = hci[k];
+      if (c < 0 || c >= n) return fail(ASCG_ERR_INVALID, "column index out of range");
+      if (!std::isfinite(hva[k])) return fail(ASCG_ERR_INVALID, "non-finite matrix entry");
+      if (c == i) {
+        if (!(hva[k] > 0.0)) return fail(ASCG_ERR_NOT_SPD, "diagonal entry is not positive");
+        diag = true;
+      }
+    }
+    if (!diag) return fail(ASCG_ERR_NOT_SPD, "a row has no diagonal entry");
+    rp32[i] = (int32_t)hrp[i];
+  }
+  rp32[n] = (int32_t)hrp[n];
+  ascg_op op = new ascg_op_s();
+  op->n = n;
+  op->nnz = nnz;
+  cudaGetDevice(&op->device);
+  ascg_status st = dev_alloc(&op->rowptr, n + 1);
+  if (st == ASCG_OK) st = dev_alloc(&op->colind, (size_t)nnz);
+  if (st == ASCG_OK) st = dev_alloc(&op->val, (size_t)nnz);
+  if (st == ASCG_OK) {
+    cudaError_t e = cudaMemcpy(op->rowptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz) e = cudaMemcpy(op->colind, hci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && nnz) e = cudaMemcpy(op->val, hva, sizeof(double) * nnz, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) st = fail(ASCG_ERR_CUDA, std::string("copy CSR: ") + cudaGetErrorString(e));
+  }
+  if (st != ASCG_OK) {
+    dev_free(op->rowptr);
+    dev_free(op->colind);
+    dev_free(op->val);
+    delete op;
+    return st;
+  }
+  *out = op;
+  return ASCG_OK;
+}
+
+ascg_status ascg_op_destroy(ascg_op op) {
+  if (!op) return ASCG_OK;
+  op->ws.release();
+  dev_free(op->rowptr);
+  dev_free(op->colind);
+  dev_free(op->val);
+  delete op;
+  return ASCG_OK;
+}
+
+ascg_status ascg_op_size(ascg_op op, int64_t* n, int64_t* nnz) {
+  if (!op) return fail(ASCG_ERR_INVALID, "op is NULL");
+  if (n) *n = op->n;
+  if (nnz) *nnz = op->nnz;
+  return ASCG_OK;
+}
+
+ascg_status ascg_solve(ascg_op op, const double* b, double* x, const ascg_options* opts, ascg_result* result,
+                       void* cuda_stream) {
+  g_err.clear();
+  ascg_result local;
+  ascg_result* res = result ? result : &local;
+  zero_result(res);
+  ascg_options o;
+  if (opts)
+    o = *opts;
+  else
+    ascg_options_default(&o);
+  auto finish = [&](ascg_status st) {
+    res->status = st;
+    return st;
+  };
+  if (!op || !b || !x) return finish(fail(ASCG_ERR_INVALID, "NULL op, b or x"));
+  ascg_status st = check_opts(o);
+  if (st != ASCG_OK) return finish(st);
+  st = solve_device(op, b, x, o, res, (cudaStream_t)cuda_stream);
+  return finish(st);
+}
+
+ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_options* opts,
+                            ascg_result* result, void* cuda_stream) {
+  g_err.clear();
+  ascg_result local;
+  ascg_result* res = result ? result : &local;
+  zero_result(res);
+  auto finish = [&](ascg_status st) {
+    res->status = st;
+    return st;
+  };
+  if (!op || !b || !x) return finish(fail(ASCG_ERR_INVALID, "NULL op, b or x"));
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  Workspace& w = op->ws;
+  if (!w.b || w.n != op->n) {
+    dev_free(w.b);
+    dev_free(w.x);
+    ascg_status a = dev_alloc(&w.b, (size_t)op->n);
+    if (a == ASCG_OK) a = dev_alloc(&w.x, (size_t)op->n);
+    if (a != ASCG_OK) return finish(a);
+  }
+  cudaError_t e = cudaMemcpyAsync(w.b, b, sizeof(double) * op->n, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(w.x, x, sizeof(double) * op->n, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return finish(fail(ASCG_ERR_CUDA, std::string("H2D: ") + cudaGetErrorString(e)));
+  // solve_device may reallocate the basis buffers but keeps b and x
+  double* db = w.b;
+  double* dx = w.x;
+  ascg_status st = ascg_solve(op, db, dx, opts, res, cuda_stream);
+  e = cudaMemcpyAsync(x, dx, sizeof(double) * op->n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return finish(fail(ASCG_ERR_CUDA, std::string("D2H: ") + cudaGetErrorString(e)));
+  return finish(st);
+}
+
+ascg_status ascg_spmv(ascg_op op, const double* x, double* y, void* cuda_stream) {
+  g_err.clear();
+  if (!op || !x || !y) return fail(ASCG_ERR_INVALID, "NULL argument");
+  ASCG_CUDA(launch_spmv(op->csr(), x, y, (cudaStream_t)cuda_stream));
+  return ASCG_OK;
+}
+
+ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const double* sigma, const double* gamma,
+                               double* Y, int64_t ldY, void* cuda_stream) {
+  g_err.clear();
+  if (!op || !theta || !sigma || !gamma || !Y) return fail(ASCG_ERR_INVALID, "NULL argument");
+  if (s < 1 || s > ASCG_MAX_S) return fail(ASCG_ERR_INVALID, "s must be in 1..16");
+  if (ldY < op->n) return fail(ASCG_ERR_INVALID, "ldY < n");
+  for (int j = 0; j < s; ++j)
+    if (!(gamma[j] != 0.0) || !std::isfinite(gamma[j])) return fail(ASCG_ERR_INVALID, "gamma must be nonzero");
+  for (int j = 0; j < s; ++j)
+    ASCG_CUDA(launch_mpk_step(op->csr(), Y, ldY, j, 1, j < s - 1, theta[j], j >= 1 ? sigma[j - 1] : 0.0, gamma[j],
+                              (cudaStream_t)cuda_stream));
+  return ASCG_OK;
+}
+
+ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream) {
+  g_err.clear();
+  if (!Y || !G || n < 1 || w < 1 || w > ASCG_MAX_W || ldY < n) return fail(ASCG_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double* partials = nullptr;
+  const int parts = gram_parts(n);
+  ASCG_TRY(dev_alloc(&partials, (size_t)parts * kMaxPairs));
+  cudaError_t e = launch_gram_partial(n, w, Y, ldY, partials, s);
+  if (e == cudaSuccess) e = launch_gram_finalize(w, partials, parts, G, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(partials);
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("gram: ") + cudaGetErrorString(e));
+  return ASCG_OK;
+}
+
+ascg_status ascg_block_step(int sbar, const double* G, int method, const double* theta, const double* sigma,
+                            const double* gamma, int64_t nrows, double eps_star, double c, int check_in_loop,
+                            int max_steps, double bnorm, double* coords, ascg_block_info* info, double* hist,
+                            void* cuda_stream) {
+  g_err.clear();
+  if (sbar < 1 || sbar > ASCG_MAX_S || !G || !theta || !sigma || !gamma || !coords || !info)
+    return fail(ASCG_ERR_INVALID, "bad argument");
+  if (method != ASCG_ADAPTIVE && method != ASCG_FIXED_S) return fail(ASCG_ERR_INVALID, "method");
+  if (!(bnorm > 0.0) || !(c > 0.0) || nrows < 1 || max_steps < 0) return fail(ASCG_ERR_INVALID, "bad scalar");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  BlockState* bst = nullptr;
+  double* dpar = nullptr;
+  double* dhist = nullptr;
+  ASCG_TRY(dev_alloc(&bst, 1));
+  ascg_status st = dev_alloc(&dpar, 3 * kMaxS);
+  if (st == ASCG_OK) st = dev_alloc(&dhist, 3 * kMaxS);
+  if (st != ASCG_OK) {
+    cudaFree(bst);
+    cudaFree(dpar);
+    return st;
+  }
+  BlockState hb;
+  std::memset(&hb, 0, sizeof(hb));
+  hb.sbar = sbar;
+  hb.method = method;
+  hb.check_in_loop = check_in_loop;
+  hb.max_steps = max_steps;
+  hb.eps_star = eps_star;
+  hb.c = c;
+  hb.bnorm = bnorm;
+  hb.sqrt_n = std::sqrt((double)nrows);
+  double hp[3 * kMaxS];
+  for (int j = 0; j < kMaxS; ++j) {
+    hp[j] = j < sbar ? theta[j] : 0.0;
+    hp[kMaxS + j] = j < sbar ? sigma[j] : 0.0;
+    hp[2 * kMaxS + j] = j < sbar ? gamma[j] : 1.0;
+  }
+  double hh[3 * kMaxS];
+  cudaError_t e = cudaMemcpyAsync(bst, &hb, sizeof(hb), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(dpar, hp, sizeof(hp), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && method == ASCG_ADAPTIVE) e = launch_kappa(G, bst, sbar, s);
+  if (e == cudaSuccess)
+    e = launch_ctrl(G, dpar, dpar + kMaxS, dpar + 2 * kMaxS, bst, coords, dhist, nullptr, 0, nullptr, 0, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bst, sizeof(hb), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(hh, dhist, sizeof(hh), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(bst);
+  cudaFree(dpar);
+  cudaFree(dhist);
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("block step: ") + cudaGetErrorString(e));
+  std::memset(info, 0, sizeof(*info));
+  info->sbar = sbar;
+  info->stilde = hb.stilde;
+  info->s_k = hb.s_k;
+  info->stop = hb.stop;
+  info->rnorm = hb.rnorm;
+  info->threshold = hb.threshold;
+  info->gamma = hb.gamma;
+  for (int i = 0; i < sbar; ++i) info->sqrt_kappa[i] = method == ASCG_ADAPTIVE ? hb.sqrt_kappa[i] : 0.0;
+  if (hist) std::memcpy(hist, hh, sizeof(double) * 3 * std::max(hb.s_k, 0));
+  return ASCG_OK;
+}
+
+ascg_status ascg_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
+                         double* p, void* cuda_stream) {
+  g_err.clear();
+  if (!Y || !coords || !x || !r || !p || n < 1 || w < 1 || w > ASCG_MAX_W || (w % 2) == 0 || ldY < n)
+    return fail(ASCG_ERR_INVALID, "bad argument");
+  ASCG_CUDA(launch_recover(n, w, Y, ldY, coords, x, r, p, (cudaStream_t)cuda_stream));
+  return ASCG_OK;
+}
+
+ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k, int s, double* shifts,
+                               void* cuda_stream) {
+  g_err.clear();
+  if (!alphas || (k > 1 && !betas) || !shifts || k < 1 || k > 32 || s < 1 || s > k)
+    return fail(ASCG_ERR_INVALID, "bad argument");
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* d = nullptr;
+  ASCG_TRY(dev_alloc(&d, 96));
+  double h[96] = {0};
+  for (int j = 0; j < k; ++j) h[j] = alphas[j];
+  for (int j = 0; j + 1 < k; ++j) h[32 + j] = betas[j];
+  cudaError_t e = cudaMemcpyAsync(d, h, sizeof(h), cudaMemcpyHostToDevice, st);
+  if (e == cudaSuccess) e = launch_newton_shifts(d, d + 32, k, d + 64, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h, d + 64, sizeof(double) * 32, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("newton shifts: ") + cudaGetErrorString(e));
+  for (int j = 0; j < s; ++j) shifts[j] = h[j];
+  return ASCG_OK;
+}
+
+const char* ascg_last_error(void) { return g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,153 @@
+// Shared device helpers and kernel declarations of libascg.
+//
+// Arithmetic is IEEE double throughout. On GB300 the FP64 pipe retires one
+// warp-wide DFMA per ~20 SM cycles (about 1.0 TFLOP/s per GPU), and an
+// instruction costs the same with 1 or 32 active lanes. Kernels therefore
+// keep every lane busy and count FP64 instructions, not bytes.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "../../include/ascg.h"
+
+namespace ascg {
+
+constexpr int kMaxS = ASCG_MAX_S;
+constexpr int kMaxW = ASCG_MAX_W;                 // 33
+constexpr int kMaxPairs = kMaxW * (kMaxW + 1) / 2;  // 561
+constexpr double kEps = 1.1102230246251565e-16;   // 2^-53
+
+// CSR matrix on the device. rowptr is int32 (nnz < 2^31).
+struct DevCSR {
+  int64_t n;
+  int64_t nnz;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+};
+
+// Rows handled by one CTA of the SpMV-based kernels, and the largest nonzero
+// count of such a row block that is staged through shared memory.
+constexpr int kSpmvRows = 256;
+constexpr int kSpmvTileNnz = 2560;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Number of blocks for a grid-stride kernel over n items.
+inline int grid_for(int64_t n, int threads, int cap) {
+  int64_t g = (n + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+// ---------------------------------------------------------------------------
+// Launchers (defined in the kernel .cu files). Each returns the CUDA error of
+// the launch.
+// ---------------------------------------------------------------------------
+
+// y = A x
+cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s);
+// r = b - A x; also writes p = r when p != nullptr
+cudaError_t launch_residual(const DevCSR& A, const double* b, const double* x, double* r,
+                            double* p, cudaStream_t s);
+// out[0] = sum_i u_i v_i over n, deterministic two-stage reduction.
+// partials: device double[kRedBlocks], counter: device unsigned (zero on entry, left zero).
+constexpr int kRedBlocks = 304;
+cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out, double* partials,
+                       unsigned* counter, cudaStream_t s);
+
+// Matrix powers step (eq. polybasiscg): forms column 2(j+1) from 2j, 2(j-1) if do_p,
+// and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
+cudaError_t launch_mpk_step(const DevCSR& A, double* Y, int64_t ldY, int j, int do_p, int do_r,
+                            double theta, double sigma_prev, double gamma, cudaStream_t s);
+
+// Gram partials: per CTA, the upper triangle (row-major pair order) of Y^T Y.
+int gram_grid();                // CTAs per launch at most (the SM count)
+int gram_parts(int64_t n);      // CTAs (= partials) used for n rows
+cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, double* partials,
+                                cudaStream_t s);
+// Sum the partials in a fixed order; G row-major w x w, both halves.
+cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
+
+// Recovery (eq. coords).
+cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
+                           double* x, double* r, double* p, cudaStream_t s);
+
+// Block controller state shared by the controller kernels and the host driver.
+struct BlockState {
+  // inputs set by the host before the block
+  int sbar;
+  int method;          // ASCG_ADAPTIVE or ASCG_FIXED_S
+  int check_in_loop;
+  int max_steps;
+  int m;               // iterations before this block
+  int k;               // block index
+  double eps_star;
+  double c;
+  double bnorm;
+  double sqrt_n;       // sqrt(length of the basis vectors)
+  // outputs
+  int stilde;
+  int s_k;
+  int stop;
+  int converged;
+  int status;          // ascg_status of the device side
+  double rnorm;
+  double threshold;
+  double gamma;
+  double rel_res;      // sqrt(max(r'Gr',0)) / bnorm after the last step
+  double sqrt_kappa[kMaxS];
+};
+
+// kappa(G_{k,i}) for i = 1..sbar, one CTA per i. Writes st->sqrt_kappa.
+cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s);
+// Selection of s~ (adaptive), B, inner loop; writes coords[3w], histories.
+// theta/sigma/gamma: device double[kMaxS]. hist: device double[3 * kMaxS] per block
+// (alpha, beta, rel res) or nullptr; res_hist: device array indexed by iteration,
+// capacity res_cap (entries m+1 .. m+s_k written), or nullptr.
+cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma,
+                        const double* gamma, BlockState* st, double* coords, double* hist,
+                        double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s);
+
+// Newton shifts: Ritz values of the CG tridiagonal, Leja order. alphas, betas:
+// device; shifts: device double[k].
+cudaError_t launch_newton_shifts(const double* alphas, const double* betas, int k, double* shifts,
+                                 cudaStream_t s);
+
+// Classical CG (Alg. 1). State lives on the device.
+struct CGState {
+  double rr;        // r^T r
+  double pAp;
+  double alpha;
+  double beta;
+  double eps_star;
+  double bnorm;
+  int iter;         // iterations completed
+  int max_iters;
+  int done;         // 1 once converged or capped
+  int converged;
+  int active;       // 1 if the current iteration runs (set by the SpMV kernel)
+  int pad_;
+};
+// q = A p, state.pAp; the last CTA sets alpha.
+cudaError_t launch_cg_spmv_dot(const DevCSR& A, const double* p, double* q, CGState* st,
+                               double* partials, unsigned* counter, cudaStream_t s);
+// x += alpha p, r -= alpha q, rr_new; the last CTA sets beta, records histories,
+// tests convergence.
+cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q,
+                             CGState* st, double* partials, unsigned* counter, double* res_hist,
+                             int res_cap, double* alpha_hist, double* beta_hist, int ab_cap,
+                             cudaStream_t s);
+// p = r + beta p
+cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGState* st, cudaStream_t s);
+// CG state init from rr = r^T r computed into st->rr.
+cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
+                           double* res_hist, int res_cap, cudaStream_t s);
+
+}  // namespace ascg

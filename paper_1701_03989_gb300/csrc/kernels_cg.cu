@@ -1,0 +1,289 @@
+// CSR SpMV, residual, dot products and classical CG (Alg. 1).
+//
+// SpMV layout: one CTA per block of kSpmvRows consecutive rows, one thread per
+// row. The block's nonzeros are staged through shared memory with coalesced
+// loads when they fit (kSpmvTileNnz). Each thread then sums its row with
+// sequential FMAs in stored column order, which is the fewest FP64
+// instructions per nonzero. Rows whose block does not fit read from global
+// memory directly.
+//
+// Reductions are deterministic. Each CTA writes a partial sum; the last CTA
+// to finish (by an atomic ticket) adds the partials in index order. There are
+// no spin-waits.
+#include "ascg_common.cuh"
+
+namespace ascg {
+
+namespace {
+
+struct RowTile {
+  int base;     // rowptr of the first row
+  bool staged;  // nonzeros are in shared memory
+};
+
+// Loads rowptr[r0..r1] and, if they fit, the nonzeros of rows [r0, r1).
+__device__ __forceinline__ RowTile stage_rows(const DevCSR& A, int64_t r0, int64_t r1, int* srow,
+                                              double* sval, int* scol) {
+  const int nr = (int)(r1 - r0);
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = A.rowptr[r0 + i];
+  __syncthreads();
+  RowTile t;
+  t.base = srow[0];
+  const int cnt = srow[nr] - t.base;
+  t.staged = cnt <= kSpmvTileNnz;
+  if (t.staged) {
+    const double* gv = A.val + t.base;
+    const int* gc = A.colind + t.base;
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      sval[k] = __ldg(gv + k);
+      scol[k] = __ldg(gc + k);
+    }
+  }
+  __syncthreads();
+  return t;
+}
+
+__device__ __forceinline__ double row_times(const DevCSR& A, const RowTile& t, const int* srow,
+                                            const double* sval, const int* scol, int lr,
+                                            const double* __restrict__ x) {
+  double s = 0.0;
+  const int k0 = srow[lr], k1 = srow[lr + 1];
+  if (t.staged) {
+    for (int k = k0 - t.base; k < k1 - t.base; ++k) s = fma(sval[k], __ldg(x + scol[k]), s);
+  } else {
+    for (int k = k0; k < k1; ++k) s = fma(__ldg(A.val + k), __ldg(x + __ldg(A.colind + k)), s);
+  }
+  return s;
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  // fixed-order CTA reduction: warp trees, then warp 0 adds the warp sums in order
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (warp == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    t = lane < nw ? red[lane] : 0.0;
+    t = warp_sum(t);
+  }
+  __syncthreads();
+  return t;  // valid in thread 0
+}
+
+// Deterministic completion: writes partials[blockIdx.x] and returns true in the
+// CTA that finishes last, which may then read every partial.
+__device__ __forceinline__ bool last_block(double part, double* partials, unsigned* counter, int* flag) {
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = part;
+    __threadfence();
+    const unsigned prev = atomicAdd(counter, 1u);
+    *flag = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  const bool last = *flag;
+  if (last) __threadfence();
+  return last;
+}
+
+__device__ __forceinline__ double sum_partials(const double* partials, int np, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += __ldcg(partials + i);
+  return block_sum(s, red);
+}
+
+// ---------------------------------------------------------------------------
+
+__global__ void __launch_bounds__(kSpmvRows) spmv_kernel(DevCSR A, const double* __restrict__ x,
+                                                         double* __restrict__ y) {
+  __shared__ int srow[kSpmvRows + 1];
+  __shared__ double sval[kSpmvTileNnz];
+  __shared__ int scol[kSpmvTileNnz];
+  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
+  const int64_t r1 = min(r0 + kSpmvRows, A.n);
+  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
+  const int lr = threadIdx.x;
+  if (r0 + lr < r1) y[r0 + lr] = row_times(A, t, srow, sval, scol, lr, x);
+}
+
+__global__ void __launch_bounds__(kSpmvRows) residual_kernel(DevCSR A, const double* __restrict__ b,
+                                                             const double* __restrict__ x,
+                                                             double* __restrict__ r, double* __restrict__ p) {
+  __shared__ int srow[kSpmvRows + 1];
+  __shared__ double sval[kSpmvTileNnz];
+  __shared__ int scol[kSpmvTileNnz];
+  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
+  const int64_t r1 = min(r0 + kSpmvRows, A.n);
+  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
+  const int lr = threadIdx.x;
+  if (r0 + lr < r1) {
+    const double v = b[r0 + lr] - row_times(A, t, srow, sval, scol, lr, x);
+    r[r0 + lr] = v;
+    if (p) p[r0 + lr] = v;
+  }
+}
+
+__global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ u, const double* __restrict__ v,
+                                                  int64_t n, double* out, double* partials, unsigned* counter) {
+  __shared__ double red[32];
+  __shared__ int flag;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s = fma(u[i], v[i], s);
+  s = block_sum(s, red);
+  if (last_block(s, partials, counter, &flag)) {
+    const double tot = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      *out = tot;
+      *counter = 0u;
+    }
+  }
+}
+
+// --- classical CG -----------------------------------------------------------
+
+__global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevCSR A, const double* __restrict__ p,
+                                                                double* __restrict__ q, CGState* st,
+                                                                double* partials, unsigned* counter) {
+  __shared__ int srow[kSpmvRows + 1];
+  __shared__ double sval[kSpmvTileNnz];
+  __shared__ int scol[kSpmvTileNnz];
+  __shared__ double red[32];
+  __shared__ int flag;
+  const int done = st->done;  // uniform: written by an earlier kernel
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->active = !done;  // read by the next two kernels
+  if (done) return;
+  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
+  const int64_t r1 = min(r0 + kSpmvRows, A.n);
+  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
+  const int lr = threadIdx.x;
+  double part = 0.0;
+  if (r0 + lr < r1) {
+    const double v = row_times(A, t, srow, sval, scol, lr, p);
+    q[r0 + lr] = v;
+    part = p[r0 + lr] * v;
+  }
+  part = block_sum(part, red);
+  if (last_block(part, partials, counter, &flag)) {
+    const double pq = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      st->pAp = pq;
+      st->alpha = st->rr / pq;  // Alg. 1: alpha_i = r^T r / p^T A p
+      *counter = 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
+                                                        const double* __restrict__ p, const double* __restrict__ q,
+                                                        CGState* st, double* partials, unsigned* counter,
+                                                        double* res_hist, int res_cap, double* alpha_hist,
+                                                        double* beta_hist, int ab_cap) {
+  __shared__ double red[32];
+  __shared__ int flag;
+  if (!st->active) return;
+  const double alpha = st->alpha;
+  double s = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    x[i] = fma(alpha, p[i], x[i]);          // x += q, q = alpha p
+    const double ri = fma(-alpha, q[i], r[i]);  // r -= A q = alpha (A p)
+    r[i] = ri;
+    s = fma(ri, ri, s);
+  }
+  s = block_sum(s, red);
+  if (last_block(s, partials, counter, &flag)) {
+    const double rr = sum_partials(partials, gridDim.x, red);
+    if (threadIdx.x == 0) {
+      const double beta = rr / st->rr;       // beta_i = r_{i+1}^T r_{i+1} / r_i^T r_i
+      const int it = st->iter;
+      if (it < ab_cap) {
+        if (alpha_hist) alpha_hist[it] = alpha;
+        if (beta_hist) beta_hist[it] = beta;
+      }
+      st->beta = beta;
+      st->rr = rr;
+      st->iter = it + 1;
+      const double rn = sqrt(rr);
+      if (res_hist && it + 1 < res_cap) res_hist[it + 1] = rn / st->bnorm;
+      const int conv = rn <= st->eps_star;
+      st->converged = conv;
+      // p is still updated for this iteration (cg_pupdate reads 'active')
+      st->done = conv || (it + 1 >= st->max_iters);
+      *counter = 0u;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
+                                                         double* __restrict__ p, const CGState* st) {
+  if (!st->active) return;  // this iteration was skipped (solve already done)
+  const double beta = st->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    p[i] = fma(beta, p[i], r[i]);            // p = r + beta p
+}
+
+__global__ void cg_init_kernel(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
+                               double* res_hist, int res_cap) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    st->eps_star = eps_star;
+    st->bnorm = bnorm;
+    st->iter = iter0;
+    st->max_iters = max_iters;
+    const double rn = sqrt(st->rr);
+    if (res_hist && iter0 < res_cap) res_hist[iter0] = rn / bnorm;
+    st->converged = rn <= eps_star;
+    st->done = st->converged || iter0 >= max_iters;
+    st->alpha = st->beta = st->pAp = 0.0;
+    st->active = 0;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s) {
+  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
+  spmv_kernel<<<g, kSpmvRows, 0, s>>>(A, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_residual(const DevCSR& A, const double* b, const double* x, double* r, double* p,
+                            cudaStream_t s) {
+  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
+  residual_kernel<<<g, kSpmvRows, 0, s>>>(A, b, x, r, p);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out, double* partials,
+                       unsigned* counter, cudaStream_t s) {
+  dot_kernel<<<grid_for(n, 256, kRedBlocks), 256, 0, s>>>(u, v, n, out, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_spmv_dot(const DevCSR& A, const double* p, double* q, CGState* st, double* partials,
+                               unsigned* counter, cudaStream_t s) {
+  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
+  cg_spmv_dot_kernel<<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, CGState* st,
+                             double* partials, unsigned* counter, double* res_hist, int res_cap,
+                             double* alpha_hist, double* beta_hist, int ab_cap, cudaStream_t s) {
+  cg_update_kernel<<<grid_for(n, 256, kRedBlocks), 256, 0, s>>>(n, x, r, p, q, st, partials, counter, res_hist,
+                                                                res_cap, alpha_hist, beta_hist, ab_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGState* st, cudaStream_t s) {
+  cg_pupdate_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(n, r, p, st);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
+                           double* res_hist, int res_cap, cudaStream_t s) {
+  cg_init_kernel<<<1, 32, 0, s>>>(st, eps_star, bnorm, max_iters, iter0, res_hist, res_cap);
+  return cudaGetLastError();
+}
+
+}  // namespace ascg

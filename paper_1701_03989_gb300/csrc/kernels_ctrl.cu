@@ -1,0 +1,415 @@
+// Block controller of adaptive s-step CG (Alg. 4): condition estimates of the
+// Gram submatrices (eq. condy), the choice of s~_k, the in-loop check
+// (eq. check), the coordinate CG steps (Sec. 2.1), and the Newton-basis
+// shifts.
+//
+// All of this is tiny dense work on matrices of order <= 33. On GB300 an FP64
+// warp instruction costs ~20 SM cycles whether 1 or 32 lanes are active, and
+// a dependent DFMA takes 64 cycles. So this code keeps the lanes busy on
+// independent work: one lane per row for the Householder steps, and 32
+// evaluation points per Sturm multisection round.
+#include <math_constants.h>
+
+#include "ascg_common.cuh"
+
+namespace ascg {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+// Number of eigenvalues of the symmetric tridiagonal (d, e2 = e^2) that are
+// smaller than x (Sturm count from the LDL^T pivots).
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int m, double x, double pivmin) {
+  int cnt = 0;
+  double q = d[0] - x;
+  if (fabs(q) < pivmin) q = -pivmin;
+  cnt += q < 0.0;
+  for (int r = 1; r < m; ++r) {
+    q = (d[r] - x) - e2[r - 1] / q;
+    if (fabs(q) < pivmin) q = -pivmin;
+    cnt += q < 0.0;
+  }
+  return cnt;
+}
+
+// Finds the smallest x with count(x) >= target by 33-way multisection on
+// [lo, hi] (count(lo) < target <= count(hi)). Every lane of the warp calls
+// this with the same arguments; at most 40 rounds.
+__device__ double multisect(const double* d, const double* e2, int m, double lo, double hi, int target,
+                            double pivmin) {
+  const int lane = threadIdx.x & 31;
+  for (int round = 0; round < 40; ++round) {
+    const double scale = fmax(fabs(lo), fabs(hi));
+    if (hi - lo <= 2.0 * kEps * scale || !(hi > lo)) break;
+    const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
+    const int c = sturm_count(d, e2, m, x, pivmin);
+    const unsigned mask = __ballot_sync(kFull, c >= target);
+    const double x_hi_all = __shfl_sync(kFull, x, 31);
+    if (mask == 0u) {
+      lo = x_hi_all;
+    } else {
+      const int t = __ffs(mask) - 1;
+      const double nh = __shfl_sync(kFull, x, t);
+      const double nl = __shfl_sync(kFull, x, t > 0 ? t - 1 : 0);
+      if (t > 0) lo = nl;
+      hi = nh;
+    }
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Gershgorin interval of the tridiagonal, widened by a few ulps.
+__device__ void gershgorin(const double* d, const double* e, int m, double* lo, double* hi, double* pivmin) {
+  double gl = CUDART_INF, gh = -CUDART_INF, e2max = 0.0;
+  for (int r = 0; r < m; ++r) {
+    const double off = (r > 0 ? fabs(e[r - 1]) : 0.0) + (r + 1 < m ? fabs(e[r]) : 0.0);
+    gl = fmin(gl, d[r] - off);
+    gh = fmax(gh, d[r] + off);
+    if (r + 1 < m) e2max = fmax(e2max, e[r] * e[r]);
+  }
+  const double widen = 4.0 * kEps * fmax(fabs(gl), fabs(gh)) * m + 1e-300;
+  *lo = gl - widen;
+  *hi = gh + widen;
+  *pivmin = 2.2250738585072014e-308 * fmax(1.0, e2max);
+}
+
+// kappa(G_{k,i}) for i = blockIdx.x + 1. G_{k,i} is the leading (2i+1) block of G
+// (interleaved column order). Warp 0 reduces it to tridiagonal form by
+// Householder reflections, one lane per row. Then warp 0 finds lambda_min and
+// warp 1 finds lambda_max by multisection.
+__global__ void __launch_bounds__(64) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
+  const int i = blockIdx.x + 1;
+  const int m = 2 * i + 1;
+  const int w = 2 * sbar + 1;
+  __shared__ double A[kMaxW][kMaxW + 1];
+  __shared__ double v[32], wv[32];
+  __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
+  __shared__ double lam[2];
+  __shared__ double gl, gh, pm;
+  for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (warp == 0) {
+    for (int k = 0; k + 2 < m; ++k) {
+      const int len = m - k - 1;  // rows k+1 .. m-1, at most 32
+      const int row = k + 1 + lane;
+      const bool on = lane < len;
+      const double xi = on ? A[row][k] : 0.0;
+      const double s2 = warp_sum(xi * xi);
+      const double x0 = __shfl_sync(kFull, xi, 0);
+      double alpha = 0.0;
+      if (s2 > 0.0) {
+        alpha = -copysign(sqrt(s2), x0);
+        const double vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
+        const double vn2 = warp_sum(vi * vi);
+        const double beta = 2.0 / vn2;
+        v[lane] = vi;
+        __syncwarp();
+        double p0 = 0.0, p1 = 0.0;
+        if (on) {
+          int c = 0;
+          for (; c + 1 < len; c += 2) {
+            p0 = fma(A[row][k + 1 + c], v[c], p0);
+            p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
+          }
+          if (c < len) p0 = fma(A[row][k + 1 + c], v[c], p0);
+        }
+        const double pi = beta * (p0 + p1);
+        const double K = 0.5 * beta * warp_sum(vi * pi);
+        const double wi = pi - K * vi;
+        wv[lane] = wi;
+        __syncwarp();
+        if (on)
+          for (int c = 0; c < len; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
+        __syncwarp();
+      }
+      if (lane == 0) e[k] = alpha;  // s2 == 0: the column is already zero
+    }
+    for (int r = lane; r < m; r += 32) d[r] = A[r][r];
+    if (lane == 0) e[m - 2] = A[m - 1][m - 2];
+    __syncwarp();
+    for (int r = lane; r + 1 < m; r += 32) e2[r] = e[r] * e[r];
+    if (lane == 0) {
+      double lo, hi, piv;
+      gershgorin(d, e, m, &lo, &hi, &piv);
+      gl = lo;
+      gh = hi;
+      pm = piv;
+    }
+  }
+  __syncthreads();
+  // lambda_min: smallest x with count >= 1; lambda_max: smallest x with count >= m
+  lam[warp] = multisect(d, e2, m, gl, gh, warp == 0 ? 1 : m, pm);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double lmin = lam[0], lmax = lam[1];
+    double sk;
+    // reading: uncertified when lambda_min <= (2i+1) sqrt(n) eps lambda_max
+    if (!(lmax > 0.0) || !isfinite(lmax) || lmin <= (double)m * st->sqrt_n * kEps * lmax)
+      sk = CUDART_INF;
+    else
+      sk = sqrt(lmax / lmin);
+    st->sqrt_kappa[i - 1] = sk;
+  }
+}
+
+// (B v)[t] for the interleaved coordinates of an s-step basis of size ss
+// (eq. AVVB): chain ch = t & 1 (0: P, 1: R), position j = t >> 1, last
+// position L = ss (P) or ss - 1 (R), whose column of B is zero.
+__device__ __forceinline__ double bapply(const double* v, int t, int ss, const double* th, const double* sg,
+                                         const double* gm) {
+  const int ch = t & 1, j = t >> 1;
+  const int L = ch ? ss - 1 : ss;
+  double acc = 0.0;
+  if (j >= 1) acc = gm[j - 1] * v[t - 2];
+  if (j < L) acc = fma(th[j], v[t], acc);
+  if (j + 1 < L) acc = fma(sg[j], v[t + 2], acc);
+  return acc;
+}
+
+// Sum over the 64 threads of the CTA, identical in every thread, fixed order.
+__device__ __forceinline__ double sum64(double x, double* red) {
+  x = warp_sum(x);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[warp] = x;
+  __syncthreads();
+  return red[0] + red[1];
+}
+
+__global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
+                                                  const double* __restrict__ sg_g, const double* __restrict__ gm_g,
+                                                  BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
+                                                  double* __restrict__ res_hist, int res_cap,
+                                                  double* __restrict__ ab_hist, int ab_cap) {
+  __shared__ double Gs[kMaxW][kMaxW + 1];
+  __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2];
+  __shared__ double th[kMaxS], sg[kMaxS], gm[kMaxS];
+  __shared__ double red[2];
+  __shared__ int s_tilde;
+  __shared__ double s_gamma;
+  const int t = threadIdx.x;
+  const int sbar = st->sbar;
+  const int w = 2 * sbar + 1;
+  const int adaptive = st->method == ASCG_ADAPTIVE;
+  const double eps_star = st->eps_star, cc = st->c, bnorm = st->bnorm;
+  for (int idx = t; idx < w * w; idx += blockDim.x) Gs[idx / w][idx % w] = G[idx];
+  if (t < kMaxS) {
+    th[t] = th_g[t];
+    sg[t] = sg_g[t];
+    gm[t] = gm_g[t];
+  }
+  __syncthreads();
+  if (t == 0) {
+    // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
+    const double rnorm = sqrt(fmax(Gs[1][1], 0.0));
+    const double T = rnorm > 0.0 ? eps_star / (cc * kEps * rnorm) : CUDART_INF;
+    int stilde;
+    double gamma;
+    if (adaptive) {
+      // eq. (condy): largest prefix i with sqrt(kappa(G_{k,i})) <= T; none -> 1
+      stilde = 0;
+      for (int i = 1; i <= sbar; ++i) {
+        if (st->sqrt_kappa[i - 1] <= T)
+          stilde = i;
+        else
+          break;
+      }
+      if (stilde < 1) stilde = 1;
+      gamma = st->sqrt_kappa[stilde - 1];
+    } else {
+      stilde = sbar;
+      gamma = 0.0;
+    }
+    st->rnorm = rnorm;
+    st->threshold = T;
+    st->stilde = stilde;
+    st->gamma = gamma;
+    s_tilde = stilde;
+    s_gamma = gamma;
+  }
+  __syncthreads();
+  const int ss = s_tilde;
+  const int ws = 2 * ss + 1;
+  const double gamma = s_gamma;
+  const bool row = t < ws;
+  if (t < kMaxW + 2) {
+    pc[t] = (t == 0) ? 1.0 : 0.0;  // p' = e_1 (column p_0)
+    rc[t] = (t == 1) ? 1.0 : 0.0;  // r' = e_{s+2} (column r_0)
+    xc[t] = 0.0;
+    u[t] = 0.0;
+    rn[t] = 0.0;
+  }
+  __syncthreads();
+  double rGr = Gs[1][1];
+  int steps = 0, stop = ASCG_STOP_DONE;
+  const int nsteps = min(ss, st->max_steps);
+  const int m0 = st->m;
+  double relres = sqrt(fmax(rGr, 0.0)) / bnorm;
+  for (int j = 1; j <= nsteps; ++j) {
+    // alpha = (r'^T G r') / (p'^T G B p')
+    if (row) u[t] = bapply(pc, t, ss, th, sg, gm);
+    __syncthreads();
+    double gi = 0.0;
+    if (row)
+      for (int c = 0; c < ws; ++c) gi = fma(Gs[t][c], u[c], gi);
+    const double pGBp = sum64(row ? pc[t] * gi : 0.0, red);
+    if (!(pGBp > 0.0) || !isfinite(pGBp) || !(rGr > 0.0) || !isfinite(rGr)) {
+      stop = ASCG_STOP_BREAKDOWN;
+      break;
+    }
+    const double alpha = rGr / pGBp;
+    // q' = alpha p'; x' += q'; r' -= B q'
+    __syncthreads();
+    if (row) {
+      const double q = alpha * pc[t];
+      u[t] = q;
+      xc[t] += q;
+    }
+    __syncthreads();
+    if (row) rn[t] = rc[t] - bapply(u, t, ss, th, sg, gm);
+    __syncthreads();
+    double g2 = 0.0;
+    if (row)
+      for (int c = 0; c < ws; ++c) g2 = fma(Gs[t][c], rn[c], g2);
+    const double rGr_new = sum64(row ? rn[t] * g2 : 0.0, red);
+    const double beta = rGr_new / rGr;
+    if (row) {
+      pc[t] = fma(beta, pc[t], rn[t]);  // p' = r'_new + beta p'
+      rc[t] = rn[t];
+    }
+    rGr = rGr_new;
+    steps = j;
+    const double rnn = sqrt(fmax(rGr_new, 0.0));
+    relres = rnn / bnorm;
+    if (t == 0) {
+      const int it = m0 + j;  // 1-based iteration index
+      if (res_hist && it < res_cap) res_hist[it] = relres;
+      if (ab_hist && it - 1 < ab_cap) {
+        ab_hist[it - 1] = alpha;
+        ab_hist[ab_cap + it - 1] = beta;
+      }
+      if (hist) {
+        hist[3 * (j - 1)] = alpha;
+        hist[3 * (j - 1) + 1] = beta;
+        hist[3 * (j - 1) + 2] = relres;
+      }
+    }
+    if (rnn <= eps_star) {
+      stop = ASCG_STOP_CONVERGED;
+      break;
+    }
+    if (adaptive && st->check_in_loop) {
+      // eq. (check): break when gamma >= eps* / (c eps (r'^T G r')^(1/2))
+      const double Tj = rnn > 0.0 ? eps_star / (cc * kEps * rnn) : CUDART_INF;
+      if (gamma >= Tj) {
+        stop = ASCG_STOP_BREAK;
+        break;
+      }
+    }
+    __syncthreads();
+  }
+  if (stop == ASCG_STOP_DONE && steps < ss) stop = ASCG_STOP_MAXITER;
+  __syncthreads();
+  for (int c = t; c < w; c += blockDim.x) {
+    const bool in = c < ws;
+    coords[c] = in ? xc[c] : 0.0;
+    coords[w + c] = in ? rc[c] : 0.0;
+    coords[2 * w + c] = in ? pc[c] : 0.0;
+  }
+  if (t == 0) {
+    st->s_k = steps;
+    st->stop = stop;
+    st->converged = stop == ASCG_STOP_CONVERGED;
+    st->rel_res = relres;
+  }
+}
+
+// Ritz values of the CG tridiagonal (k <= 32), one lane per eigenvalue index by
+// bisection, then Leja order computed by the whole warp.
+__global__ void __launch_bounds__(32) newton_shifts_kernel(const double* __restrict__ al,
+                                                           const double* __restrict__ be, int k,
+                                                           double* __restrict__ shifts) {
+  __shared__ double d[32], e[32], e2[32], ritz[32];
+  __shared__ double gl, gh, pm;
+  const int lane = threadIdx.x;
+  if (lane < k) {
+    d[lane] = 1.0 / al[lane] + (lane > 0 ? be[lane - 1] / al[lane - 1] : 0.0);
+    if (lane + 1 < k) {
+      e[lane] = sqrt(be[lane]) / al[lane];
+      e2[lane] = e[lane] * e[lane];
+    }
+  }
+  __syncwarp();
+  if (lane == 0) {
+    double lo, hi, piv;
+    gershgorin(d, e, k, &lo, &hi, &piv);
+    gl = lo;
+    gh = hi;
+    pm = piv;
+  }
+  __syncwarp();
+  if (lane < k) {
+    // the (lane+1)-th smallest eigenvalue: smallest x with count(x) >= lane + 1
+    double lo = gl, hi = gh;
+    for (int it = 0; it < 200; ++it) {
+      const double scale = fmax(fabs(lo), fabs(hi));
+      if (hi - lo <= 2.0 * kEps * scale || !(hi > lo)) break;
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(d, e2, k, mid, pm) >= lane + 1)
+        hi = mid;
+      else
+        lo = mid;
+    }
+    ritz[lane] = 0.5 * (lo + hi);
+  }
+  __syncwarp();
+  // Leja order: first the largest |value|; then the largest product of distances
+  // to the values chosen so far. Ties: larger value, then lower index.
+  const double val = lane < k ? ritz[lane] : 0.0;
+  double score = fabs(val);
+  bool avail = lane < k;
+  for (int step = 0; step < k; ++step) {
+    double bs = avail ? score : -1.0, bv = val;
+    int bi = avail ? lane : 64;
+    for (int o = 16; o > 0; o >>= 1) {
+      const double os = __shfl_xor_sync(kFull, bs, o);
+      const double ov = __shfl_xor_sync(kFull, bv, o);
+      const int oi = __shfl_xor_sync(kFull, bi, o);
+      const bool better = (os > bs) || (os == bs && (ov > bv || (ov == bv && oi < bi)));
+      if (better) {
+        bs = os;
+        bv = ov;
+        bi = oi;
+      }
+    }
+    if (lane == 0) shifts[step] = bv;
+    if (lane == bi) avail = false;
+    const double dist = fabs(val - bv);
+    score = (step == 0) ? dist : score * dist;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s) {
+  kappa_kernel<<<sbar, 64, 0, s>>>(G, st, sbar);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
+                        BlockState* st, double* coords, double* hist, double* res_hist, int res_cap,
+                        double* ab_hist, int ab_cap, cudaStream_t s) {
+  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_newton_shifts(const double* alphas, const double* betas, int k, double* shifts,
+                                 cudaStream_t s) {
+  newton_shifts_kernel<<<1, 32, 0, s>>>(alphas, betas, k, shifts);
+  return cudaGetLastError();
+}
+
+}  // namespace ascg

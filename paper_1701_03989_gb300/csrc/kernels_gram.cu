@@ -1,0 +1,189 @@
+// Gram matrix G = Y^T Y of the s-step basis (Sec. 2.1; Alg. 4 "Compute G").
+//
+// This is the largest FP64 cost of a block: w(w+1)/2 fused multiply-adds per
+// row (561 at w = 33), against about 2 * (2s-1) * nnz/n for the matrix powers
+// kernel. GB300 runs FP64 at one warp instruction per ~20 SM cycles, and DMMA
+// (mma.sync m8n8k4 f64) shares that pipe at the same rate. So the Gram stays
+// on CUDA cores, and the design goal is to keep every FP64 lane busy on a
+// distinct product.
+//
+// Mapping: a CTA owns a contiguous range of 32-row chunks. Each chunk of Y
+// (w columns x 32 rows) goes to shared memory. Lane l of every warp works on
+// row l of the chunk. Warp g owns the upper-triangle pairs p = g, g + 16,
+// g + 32, ..., and accumulates y_a * y_b for its pairs in registers. After the
+// range, each warp reduces its accumulators across lanes (fixed shuffle tree)
+// and writes one partial per pair. A second kernel adds the partials of all
+// CTAs in index order. Results are bitwise reproducible for a given n, w and
+// grid.
+#include "ascg_common.cuh"
+
+namespace ascg {
+
+namespace {
+
+constexpr int kGramWarps = 16;
+constexpr int kGramThreads = kGramWarps * 32;
+constexpr int kChunk = 32;  // rows per chunk = lanes
+
+int g_gram_grid = 0;
+
+template <int W>
+__global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n, const double* __restrict__ Y,
+                                                                        int64_t ldY, double* __restrict__ partials) {
+  constexpr int NP = W * (W + 1) / 2;
+  constexpr int PPW = (NP + kGramWarps - 1) / kGramWarps;
+  constexpr int ELEMS = W * kChunk;
+  constexpr int LPT = (ELEMS + kGramThreads - 1) / kGramThreads;  // loads per thread per chunk
+  __shared__ double tile[2][W][kChunk];
+  __shared__ unsigned short pab[kGramWarps][PPW];  // a | b << 8 for each of the warp's pairs
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // pair p in row-major upper-triangle order: (0,0), (0,1), ..., (0,W-1), (1,1), ...
+  for (int k = lane; k < PPW; k += 32) {
+    const int p = warp + kGramWarps * k;
+    int a = 0, b = 0;
+    if (p < NP) {
+      int rem = p;
+      while (rem >= W - a) {
+        rem -= W - a;
+        ++a;
+      }
+      b = a + rem;
+    }
+    pab[warp][k] = (unsigned short)(a | (b << 8));
+  }
+
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  const int64_t c0 = nchunks * blockIdx.x / gridDim.x;
+  const int64_t c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
+
+  double acc[PPW];
+#pragma unroll
+  for (int k = 0; k < PPW; ++k) acc[k] = 0.0;
+
+  double pre[LPT];
+  auto load = [&](int64_t c) {
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+      const int e = threadIdx.x + i * kGramThreads;
+      double v = 0.0;
+      if (e < ELEMS) {
+        const int col = e / kChunk, r = e % kChunk;
+        const int64_t row = c * kChunk + r;
+        if (row < n) v = __ldcs(Y + (int64_t)col * ldY + row);
+      }
+      pre[i] = v;
+    }
+  };
+  auto store = [&](int buf) {
+#pragma unroll
+    for (int i = 0; i < LPT; ++i) {
+      const int e = threadIdx.x + i * kGramThreads;
+      if (e < ELEMS) (&tile[buf][0][0])[e] = pre[i];
+    }
+  };
+
+  if (c0 < c1) {
+    load(c0);
+    store(0);
+  }
+  __syncthreads();
+  for (int64_t c = c0; c < c1; ++c) {
+    const int buf = (int)((c - c0) & 1);
+    const bool more = c + 1 < c1;
+    if (more) load(c + 1);
+    const double* t = &tile[buf][0][0];
+#pragma unroll
+    for (int k = 0; k < PPW; ++k) {
+      if (warp + kGramWarps * k < NP) {
+        const unsigned ab = pab[warp][k];
+        const double ya = t[(ab & 0xff) * kChunk + lane];
+        const double yb = t[(ab >> 8) * kChunk + lane];
+        acc[k] = fma(ya, yb, acc[k]);
+      }
+    }
+    if (more) store(buf ^ 1);
+    __syncthreads();
+  }
+  double* out = partials + (int64_t)blockIdx.x * NP;
+#pragma unroll
+  for (int k = 0; k < PPW; ++k) {
+    const int p = warp + kGramWarps * k;
+    const double v = warp_sum(acc[k]);
+    if (lane == 0 && p < NP) out[p] = v;
+  }
+}
+
+// One thread per pair; adds the partials of all CTAs in index order with four
+// interleaved accumulators (fixed order) to shorten the dependency chain.
+__global__ void gram_finalize_kernel(int w, const double* __restrict__ partials, int nparts,
+                                     double* __restrict__ G) {
+  const int np = w * (w + 1) / 2;
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 3 < nparts; c += 4) {
+    s0 += partials[(int64_t)c * np + p];
+    s1 += partials[(int64_t)(c + 1) * np + p];
+    s2 += partials[(int64_t)(c + 2) * np + p];
+    s3 += partials[(int64_t)(c + 3) * np + p];
+  }
+  for (; c < nparts; ++c) s0 += partials[(int64_t)c * np + p];
+  const double s = (s0 + s1) + (s2 + s3);
+  int a = 0, rem = p;
+  while (rem >= w - a) {
+    rem -= w - a;
+    ++a;
+  }
+  const int b = a + rem;
+  G[a * w + b] = s;
+  G[b * w + a] = s;
+}
+
+template <int W>
+cudaError_t gram_w(int64_t n, const double* Y, int64_t ldY, double* partials, int grid, cudaStream_t s) {
+  gram_partial_kernel<W><<<grid, kGramThreads, 0, s>>>(n, Y, ldY, partials);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int gram_grid() {
+  if (g_gram_grid == 0) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    g_gram_grid = sms > 0 ? sms : 1;
+  }
+  return g_gram_grid;
+}
+
+int gram_parts(int64_t n) {
+  const int64_t chunks = (n + kChunk - 1) / kChunk;
+  return (int)(chunks < gram_grid() ? chunks : gram_grid());
+}
+
+cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, double* partials, cudaStream_t s) {
+  const int grid = gram_parts(n);
+  switch (w) {
+#define ASCG_GW(W) \
+  case W:          \
+    return gram_w<W>(n, Y, ldY, partials, grid, s);
+    ASCG_GW(1) ASCG_GW(2) ASCG_GW(3) ASCG_GW(4) ASCG_GW(5) ASCG_GW(6) ASCG_GW(7) ASCG_GW(8) ASCG_GW(9)
+    ASCG_GW(10) ASCG_GW(11) ASCG_GW(12) ASCG_GW(13) ASCG_GW(14) ASCG_GW(15) ASCG_GW(16) ASCG_GW(17)
+    ASCG_GW(18) ASCG_GW(19) ASCG_GW(20) ASCG_GW(21) ASCG_GW(22) ASCG_GW(23) ASCG_GW(24) ASCG_GW(25)
+    ASCG_GW(26) ASCG_GW(27) ASCG_GW(28) ASCG_GW(29) ASCG_GW(30) ASCG_GW(31) ASCG_GW(32) ASCG_GW(33)
+#undef ASCG_GW
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s) {
+  const int np = w * (w + 1) / 2;
+  gram_finalize_kernel<<<(np + 63) / 64, 64, 0, s>>>(w, partials, nparts, G);
+  return cudaGetLastError();
+}
+
+}  // namespace ascg

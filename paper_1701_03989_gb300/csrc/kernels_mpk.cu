@@ -1,0 +1,150 @@
+// Matrix powers (eq. polybasiscg / cg-krylovbasis) and recovery (eq. coords).
+//
+// Basis layout: Y is column-major with leading dimension ldY and interleaves
+// the two Krylov bases: column 2j = rho_j(A) p, column 2j+1 = rho_j(A) r.
+// Then every i-step sub-basis Y_{k,i} is the first 2i+1 columns.
+//
+// One matrix powers step j forms column 2(j+1) of P and column 2(j+1)+1 of R
+// in the same pass over A. The CSR row block is staged once in shared memory
+// and applied to both vectors, so A is read s times per block, not 2s-1.
+// The GPU has no room to keep A on chip across steps for the large
+// workloads. This step is FP64-bound on GB300, so re-reading A costs no time.
+#include "ascg_common.cuh"
+
+namespace ascg {
+
+namespace {
+
+__global__ void __launch_bounds__(kSpmvRows) mpk_step_kernel(DevCSR A, double* __restrict__ Y, int64_t ldY,
+                                                             int j, int do_p, int do_r, double theta,
+                                                             double sigma_prev, double gamma_inv, int use_theta,
+                                                             int use_sigma, int use_gamma) {
+  __shared__ int srow[kSpmvRows + 1];
+  __shared__ double sval[kSpmvTileNnz];
+  __shared__ int scol[kSpmvTileNnz];
+  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
+  const int64_t r1 = min(r0 + kSpmvRows, A.n);
+  const int nr = (int)(r1 - r0);
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = A.rowptr[r0 + i];
+  __syncthreads();
+  const int base = srow[0];
+  const int cnt = srow[nr] - base;
+  const bool staged = cnt <= kSpmvTileNnz;
+  if (staged) {
+    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+      sval[k] = __ldg(A.val + base + k);
+      scol[k] = __ldg(A.colind + base + k);
+    }
+  }
+  __syncthreads();
+  const int lr = threadIdx.x;
+  if (lr >= nr) return;
+  const int64_t row = r0 + lr;
+  const double* pj = Y + (int64_t)(2 * j) * ldY;
+  const double* rj = Y + (int64_t)(2 * j + 1) * ldY;
+  double tp = 0.0, tr = 0.0;
+  const int k0 = srow[lr], k1 = srow[lr + 1];
+  if (do_r) {
+    if (staged) {
+      for (int k = k0 - base; k < k1 - base; ++k) {
+        const double a = sval[k];
+        const int c = scol[k];
+        tp = fma(a, __ldg(pj + c), tp);
+        tr = fma(a, __ldg(rj + c), tr);
+      }
+    } else {
+      for (int k = k0; k < k1; ++k) {
+        const double a = __ldg(A.val + k);
+        const int c = __ldg(A.colind + k);
+        tp = fma(a, __ldg(pj + c), tp);
+        tr = fma(a, __ldg(rj + c), tr);
+      }
+    }
+  } else {
+    if (staged) {
+      for (int k = k0 - base; k < k1 - base; ++k) tp = fma(sval[k], __ldg(pj + scol[k]), tp);
+    } else {
+      for (int k = k0; k < k1; ++k) tp = fma(__ldg(A.val + k), __ldg(pj + __ldg(A.colind + k)), tp);
+    }
+  }
+  // rho_{j+1} = ((A - theta_j) rho_j - sigma_{j-1} rho_{j-1}) / gamma_j
+  if (do_p) {
+    if (use_theta) tp = fma(-theta, pj[row], tp);
+    if (use_sigma && j >= 1) tp = fma(-sigma_prev, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
+    if (use_gamma) tp *= gamma_inv;
+    Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+  }
+  if (do_r) {
+    if (use_theta) tr = fma(-theta, rj[row], tr);
+    if (use_sigma && j >= 1) tr = fma(-sigma_prev, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
+    if (use_gamma) tr *= gamma_inv;
+    Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
+  }
+}
+
+// x += Y x', r = Y r', p = Y p' over the first w columns (eq. coords).
+// Each thread reads its whole row of Y before writing, so r and p may alias
+// columns 1 and 0 of Y.
+template <int W>
+__global__ void __launch_bounds__(256) recover_kernel(int64_t n, const double* Y, int64_t ldY,
+                                                      const double* __restrict__ coords, double* x, double* r,
+                                                      double* p) {
+  __shared__ double cx[W], cr[W], cp[W];
+  if (threadIdx.x < W) {
+    cx[threadIdx.x] = coords[threadIdx.x];
+    cr[threadIdx.x] = coords[W + threadIdx.x];
+    cp[threadIdx.x] = coords[2 * W + threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double y[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) y[c] = Y[(int64_t)c * ldY + i];
+    double sx = 0.0, sr = 0.0, sp = 0.0;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      sx = fma(y[c], cx[c], sx);
+      sr = fma(y[c], cr[c], sr);
+      sp = fma(y[c], cp[c], sp);
+    }
+    x[i] = x[i] + sx;
+    r[i] = sr;
+    p[i] = sp;
+  }
+}
+
+template <int W>
+cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
+                      double* p, cudaStream_t s) {
+  recover_kernel<W><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, Y, ldY, coords, x, r, p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_mpk_step(const DevCSR& A, double* Y, int64_t ldY, int j, int do_p, int do_r, double theta,
+                            double sigma_prev, double gamma, cudaStream_t s) {
+  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
+  const int use_theta = theta != 0.0;
+  const int use_sigma = sigma_prev != 0.0;
+  const int use_gamma = gamma != 1.0;
+  mpk_step_kernel<<<g, kSpmvRows, 0, s>>>(A, Y, ldY, j, do_p, do_r, theta, sigma_prev, 1.0 / gamma, use_theta,
+                                          use_sigma, use_gamma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
+                           double* r, double* p, cudaStream_t s) {
+  switch (w) {
+#define ASCG_RW(W) \
+  case W:          \
+    return recover_w<W>(n, Y, ldY, coords, x, r, p, s);
+    ASCG_RW(1) ASCG_RW(3) ASCG_RW(5) ASCG_RW(7) ASCG_RW(9) ASCG_RW(11) ASCG_RW(13) ASCG_RW(15) ASCG_RW(17)
+    ASCG_RW(19) ASCG_RW(21) ASCG_RW(23) ASCG_RW(25) ASCG_RW(27) ASCG_RW(29) ASCG_RW(31) ASCG_RW(33)
+#undef ASCG_RW
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace ascg

@@ -1,0 +1,99 @@
+"""Helpers for comparing the CUDA path with the oracle (test infrastructure).
+
+Tolerances are derived from the arithmetic (see each function):
+  * residual histories: 1e-10 absolute on ||r_i||/||b|| over the first 20
+    iterations;
+  * s_k sequences: identical, except where the oracle's decision lies within
+    the uncertainty of its criterion. For the kappa test, that uncertainty is
+    max(1e-6, K w sqrt(n) eps kappa): the two sides form G in different
+    summation orders, which moves lambda_min by about sqrt(n) eps lambda_max.
+    After the first exempt block only the earlier iterations are compared;
+  * final true residual: within a factor 2 of the oracle's.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+EPS = 2.0 ** -53
+K_UNCERTAINTY = 64.0
+
+
+def kappa_uncertainty(sk: float, w: int, n: int) -> float:
+    """Relative uncertainty of sqrt(kappa(G_sub)) from rounding in G and its eigenvalues."""
+    if not math.isfinite(sk):
+        return math.inf
+    return max(1e-6, K_UNCERTAINTY * w * math.sqrt(n) * EPS * sk * sk)
+
+
+def decision_is_near(sk_o: float, sk_g: float, T: float, w: int, n: int) -> bool:
+    """True if the two sides may legitimately disagree on 'sqrt(kappa) <= T'."""
+    pass_o, pass_g = sk_o <= T, sk_g <= T
+    if pass_o == pass_g:
+        return False
+    if math.isfinite(sk_o) and math.isfinite(sk_g):
+        return abs(sk_o - T) <= kappa_uncertainty(sk_o, w, n) * T or abs(sk_g - T) <= kappa_uncertainty(sk_g, w, n) * T
+    # one side certified the basis, the other did not: only near the floor
+    # lambda_min = w sqrt(n) eps lambda_max, i.e. kappa ~ 1 / (w sqrt(n) eps)
+    fin = sk_o if math.isfinite(sk_o) else sk_g
+    floor_sk = math.sqrt(1.0 / (w * math.sqrt(n) * EPS))
+    return fin >= floor_sk / 8.0
+
+
+def compare_block_sequences(gpu_blocks, oracle_blocks, n: int, oracle_hist=None, target=None):
+    """Walks both block sequences. Returns (index of the first exempt block or
+    None, list of mismatch messages that are not exempt).
+
+    oracle_hist / target (relative residual history and eps_target) let a
+    convergence decision count as near when the residual at either side's
+    stopping step is within 1e-6 (relative) of the target."""
+    bad = []
+    for k, (g, o) in enumerate(zip(gpu_blocks, oracle_blocks)):
+        if g["sbar"] != o["sbar"]:
+            bad.append(f"block {k}: sbar {g['sbar']} vs {o['sbar']}")
+            return k, bad
+        same = g["stilde"] == o["stilde"] and g["s_k"] == o["s_k"]
+        if same:
+            continue
+        T = o["threshold"]
+        near = False
+        sk_o = {i: s for i, s, _ in o.get("kappas", [])}
+        for i in range(1, g["sbar"] + 1):
+            if i in sk_o:
+                if decision_is_near(sk_o[i], g["sqrt_kappa"][i - 1], T, 2 * i + 1, n):
+                    near = True
+        # in-loop check: gamma >= T_j
+        for j, tj in o.get("checks", []):
+            if abs(o["gamma"] - tj) <= kappa_uncertainty(o["gamma"], 2 * o["stilde"] + 1, n) * tj:
+                near = True
+        if oracle_hist is not None and target is not None:
+            for s_ in (g["s_k"], o["s_k"]):
+                i = o["m"] + s_
+                if i < len(oracle_hist) and abs(oracle_hist[i] - target) <= 1e-6 * target:
+                    near = True
+        if near:
+            return k, bad
+        bad.append(f"block {k}: stilde/s_k gpu {g['stilde']}/{g['s_k']} oracle {o['stilde']}/{o['s_k']} "
+                   f"T={T:.6g} sk_gpu={list(g['sqrt_kappa'][:g['sbar']])} sk_or={o.get('kappas')}")
+        return k, bad
+    return None, bad
+
+
+def gpu_blocks_from_infos(infos, count):
+    out = []
+    for i in range(count):
+        b = infos[i]
+        out.append(dict(sbar=b.sbar, stilde=b.stilde, s_k=b.s_k, stop=b.stop, m=b.m, rnorm=b.rnorm,
+                        threshold=b.threshold, gamma=b.gamma, sqrt_kappa=[b.sqrt_kappa[j] for j in range(16)]))
+    return out
+
+
+def history_window(gpu_blocks, oracle_blocks, exempt_block, iters=20, offset=0):
+    """Number of leading history entries to compare: the first `iters`
+    iterations, cut at the start of the first exempt block."""
+    limit = iters
+    if exempt_block is not None:
+        m = oracle_blocks[exempt_block]["m"]
+        limit = min(limit, m)
+    return limit + 1  # entry 0 is the initial residual

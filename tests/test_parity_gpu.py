@@ -1,0 +1,506 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Each step of the hot path is compared element by element on the same seeded
+inputs, within bounds derived from the floating-point arithmetic. Whole solves
+are compared on residual histories (1e-10 absolute over the first 20
+iterations), s_k sequences (identical except where the decision lies within
+its rounding uncertainty, see parity.py) and the final true residual (within
+a factor 2).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import parity
+import workloads as W
+from oracle import ascg_oracle as O
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+
+
+def gamma_n(k):
+    return k * EPS / (1 - k * EPS)
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    from paper_1701_03989_gb300 import build as B
+    B.build_all()
+    import paper_1701_03989_gb300 as P
+    torch.cuda.init()
+    return P, torch
+
+
+def dev(torch, a, dtype=None):
+    a = np.ascontiguousarray(a)
+    return torch.from_numpy(a).to("cuda")
+
+
+def make_op(P, A):
+    return P.ascg_op_create_csr(A.n, A.nnz, np.ascontiguousarray(A.rowptr, np.int64),
+                                np.ascontiguousarray(A.colind, np.int32), np.ascontiguousarray(A.val, np.float64), 0)
+
+
+MATRICES = {
+    "poisson2d_32": lambda: W.poisson2d(32),
+    "poisson3d_23": lambda: W.poisson3d(23),                       # n = 12167: ragged tail
+    "diffusion_63": lambda: W.fv_diffusion2d(63, 2.0, np.random.default_rng(7)),
+    "banded_3001": lambda: W.banded_spd(3001, 48, np.random.default_rng(8)),  # rows too long to stage
+    "one": lambda: W.CSRMatrix(1, np.array([0, 1]), np.array([0], np.int32), np.array([2.5])),
+}
+
+
+# ---------------------------------------------------------------------------
+# a10 / a1: SpMV (A p) and residual
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(MATRICES))
+def test_spmv_parity(env, name):
+    P, torch = env
+    A = MATRICES[name]()
+    op = make_op(P, A)
+    x = np.random.default_rng(1).standard_normal(A.n)
+    y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    P.ascg_spmv(op, dev(torch, x), y)
+    torch.cuda.synchronize()
+    yo = O.spmv(O.Operator.from_csr(A), x)
+    absAx = O.spmv(O.Operator(A.n, A.rowptr, A.colind, np.abs(A.val)), np.abs(x))
+    nmax = int(np.max(np.diff(A.rowptr)))
+    assert np.all(np.abs(y.cpu().numpy() - yo) <= 2 * gamma_n(nmax) * absAx + 1e-300)
+    P.ascg_op_destroy(op)
+
+
+# ---------------------------------------------------------------------------
+# a4: matrix powers
+# ---------------------------------------------------------------------------
+
+def basis_for(kind, s, lam):
+    if kind == "monomial":
+        return O.monomial_params(s)
+    if kind == "chebyshev":
+        return O.chebyshev_params(lam[0], lam[1], s)
+    return O.newton_params(list(np.linspace(1.9, 0.05, s)), s)
+
+
+def abs_bound_columns(A, v, ncols, bp):
+    """|rho_j| recurrence run on |A|, |theta|, |sigma|, 1/|gamma|, |v|: bounds the
+    rounding error of the computed columns."""
+    Aa = O.Operator(A.n, A.rowptr, A.colind, np.abs(A.val))
+    cols = [np.abs(v)]
+    for j in range(1, ncols):
+        t = O.spmv(Aa, cols[j - 1]) + abs(bp.theta[j - 1]) * cols[j - 1]
+        if j >= 2:
+            t = t + abs(bp.sigma[j - 2]) * cols[j - 2]
+        cols.append(t / abs(bp.gamma[j - 1]))
+    return cols
+
+
+@pytest.mark.parametrize("kind", ["monomial", "chebyshev", "newton"])
+@pytest.mark.parametrize("s", [1, 4, 8, 16])
+@pytest.mark.parametrize("name", ["poisson2d_32", "poisson3d_23", "banded_3001"])
+def test_matrix_powers_parity(env, kind, s, name):
+    P, torch = env
+    A = MATRICES[name]()
+    lam = (0.0, 2.0) if name == "banded_3001" else (W.poisson_eig_bounds(2, 32) if name == "poisson2d_32"
+                                                    else W.poisson_eig_bounds(3, 23))
+    bp = basis_for(kind, s, lam)
+    op = make_op(P, A)
+    rng = np.random.default_rng(s)
+    p = rng.standard_normal(A.n)
+    r = rng.standard_normal(A.n)
+    ld = A.n + 7   # odd leading dimension: no alignment assumption
+    w = 2 * s + 1
+    Y = torch.zeros(w * ld, dtype=torch.float64, device="cuda")
+    Y[0:A.n] = dev(torch, p)
+    Y[ld:ld + A.n] = dev(torch, r)
+    th = np.array(bp.theta[:s], float)
+    sg = np.array(bp.sigma[:s], float)
+    gm = np.array(bp.gamma[:s], float)
+    P.ascg_matrix_powers(op, s, th, sg, gm, Y, ld)
+    torch.cuda.synchronize()
+    Yg = Y.cpu().numpy().reshape(w, ld)[:, :A.n]
+    Ao = O.Operator.from_csr(A)
+    Yo = O.matrix_powers(Ao, p, r, s, bp)
+    bp_abs = abs_bound_columns(A, p, s + 1, bp), abs_bound_columns(A, r, s, bp)
+    NA = int(np.max(np.diff(A.rowptr)))
+    for j in range(s + 1):
+        tol = 4 * (j + 1) * (NA + 3) * EPS * bp_abs[0][j] + 1e-300
+        assert np.all(np.abs(Yg[2 * j] - Yo[:, j]) <= tol), (kind, s, "P", j)
+    for j in range(s):
+        tol = 4 * (j + 1) * (NA + 3) * EPS * bp_abs[1][j] + 1e-300
+        assert np.all(np.abs(Yg[2 * j + 1] - Yo[:, s + 1 + j]) <= tol), (kind, s, "R", j)
+    P.ascg_op_destroy(op)
+
+
+# ---------------------------------------------------------------------------
+# a5: Gram matrix
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,w", [(1, 1), (31, 3), (1000, 9), (5000, 17), (70001, 33), (70001, 25), (200003, 2)])
+def test_gram_parity(env, n, w):
+    P, torch = env
+    rng = np.random.default_rng(n + w)
+    Y = rng.standard_normal((w, n)) * np.logspace(0, 4, w)[:, None]
+    ld = n + (32 - n % 32) % 32
+    Yd = torch.zeros(w * ld, dtype=torch.float64, device="cuda")
+    for c in range(w):
+        Yd[c * ld:c * ld + n] = dev(torch, Y[c])
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, ld, G)
+    Gg = G.cpu().numpy().reshape(w, w)
+    Go = O.gram(Y.T)
+    bound = 2 * gamma_n(n) * (np.abs(Y) @ np.abs(Y).T)
+    assert np.all(np.abs(Gg - Go) <= bound)
+    assert np.array_equal(Gg, Gg.T)
+    G2 = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, ld, G2)
+    assert torch.equal(G, G2)   # fixed reduction order: bitwise reproducible
+
+
+# ---------------------------------------------------------------------------
+# a6-a8: block controller on a given Gram matrix
+# ---------------------------------------------------------------------------
+
+def interleave_perm(sbar):
+    """perm[c] = [P, R]-order index of interleaved column c."""
+    perm = []
+    for j in range(sbar + 1):
+        perm.append(j)
+        if j < sbar:
+            perm.append(sbar + 1 + j)
+    return np.array(perm)
+
+
+def block_inputs(name, kind, sbar, warm):
+    A = MATRICES[name]()
+    Ao = O.Operator.from_csr(A)
+    lam = W.poisson_eig_bounds(2, 32) if name == "poisson2d_32" else W.poisson_eig_bounds(3, 23)
+    bp = basis_for(kind, sbar, lam)
+    b = W.rhs_uniform(A.n, np.random.default_rng(3))
+    cl = O.classical_cg(Ao, b, np.zeros(A.n), eps_target=0.0, max_iters=warm)
+    Y = O.matrix_powers(Ao, cl.p, cl.r, sbar, bp)
+    return A, bp, b, O.gram(Y)
+
+
+@pytest.mark.parametrize("name,kind,sbar,warm,eps", [
+    ("poisson2d_32", "monomial", 8, 20, 1e-10),
+    ("poisson2d_32", "monomial", 8, 0, 1e-10),       # first block: p = r, rank deficient
+    ("poisson2d_32", "monomial", 8, 40, 1e-6),
+    ("poisson3d_23", "chebyshev", 16, 30, 1e-12),
+    ("poisson3d_23", "chebyshev", 5, 3, 1e-12),
+    ("poisson3d_23", "newton", 12, 30, 1e-10),
+])
+def test_block_step_parity(env, name, kind, sbar, warm, eps):
+    P, torch = env
+    A, bp, b, G = block_inputs(name, kind, sbar, warm)
+    w = 2 * sbar + 1
+    perm = interleave_perm(sbar)
+    Gi = G[np.ix_(perm, perm)]
+    coords = torch.zeros(3 * w, dtype=torch.float64, device="cuda")
+    info, hist = P.ascg_block_step(sbar, dev(torch, Gi.ravel()), P.ASCG_ADAPTIVE, bp.theta[:sbar], bp.sigma[:sbar],
+                                   bp.gamma[:sbar], A.n, eps, 1.0, 1, 1000, 1.0, coords)
+    blk, inner, idx = O.adaptive_block(G, sbar, bp, eps, 1.0, A.n, True, 1000)
+    sk_g = [info.sqrt_kappa[i] for i in range(sbar)]
+    gblk = dict(sbar=sbar, stilde=info.stilde, s_k=info.s_k, sqrt_kappa=sk_g, threshold=info.threshold)
+    exempt, bad = parity.compare_block_sequences([gblk], [blk], A.n)
+    assert not bad, bad
+    if exempt is not None:
+        pytest.skip("decision within rounding uncertainty of its threshold")
+    assert abs(info.threshold - blk["threshold"]) <= 1e-12 * blk["threshold"]
+    for i, s_o, unc in blk["kappas"]:
+        s_g = sk_g[i - 1]
+        if math.isfinite(s_o) and math.isfinite(s_g):
+            assert abs(s_g - s_o) <= parity.kappa_uncertainty(s_o, 2 * i + 1, A.n) * s_o
+    st = info.stilde
+    ws = 2 * st + 1
+    c = coords.cpu().numpy().reshape(3, w)
+    # oracle coordinates are in [P, R] order of the s~ basis
+    perm_s = interleave_perm(st)
+    for row, ref in ((0, inner.xc), (1, inner.rc), (2, inner.pc)):
+        got = c[row, :ws]
+        want = np.asarray(ref)[perm_s]
+        assert np.all(c[row, ws:] == 0)
+        assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max()), row
+    np.testing.assert_allclose(hist[:, 0], inner.alphas, rtol=1e-9)
+    np.testing.assert_allclose(hist[:, 1], inner.betas, rtol=1e-8, atol=1e-14)
+    np.testing.assert_allclose(hist[:, 2], [math.sqrt(max(v, 0)) for v in inner.rGr], rtol=1e-8, atol=1e-14)
+
+
+def test_block_step_fixed_s(env):
+    P, torch = env
+    A, bp, b, G = block_inputs("poisson2d_32", "monomial", 4, 10)
+    w = 9
+    perm = interleave_perm(4)
+    coords = torch.zeros(3 * w, dtype=torch.float64, device="cuda")
+    info, hist = P.ascg_block_step(4, dev(torch, G[np.ix_(perm, perm)].ravel()), P.ASCG_FIXED_S, bp.theta[:4],
+                                   bp.sigma[:4], bp.gamma[:4], A.n, 0.0, 1.0, 0, 1000, 1.0, coords)
+    B = O.basis_change_matrix(4, bp)
+    inner = O.coordinate_steps(G, B, 4, 4)
+    assert info.stilde == 4 and info.s_k == 4
+    c = coords.cpu().numpy().reshape(3, w)
+    for row, ref in ((0, inner.xc), (1, inner.rc), (2, inner.pc)):
+        assert np.allclose(c[row], np.asarray(ref)[perm], rtol=1e-10, atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# a9: recovery
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,w", [(1, 1), (1000, 9), (70001, 33), (12345, 17)])
+def test_recover_parity(env, n, w):
+    P, torch = env
+    rng = np.random.default_rng(n * w)
+    Y = rng.standard_normal((w, n))
+    x = rng.standard_normal(n)
+    cf = rng.standard_normal(3 * w)
+    ld = n
+    Yd = dev(torch, Y.ravel())
+    xd = dev(torch, x)
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    p = torch.empty(n, dtype=torch.float64, device="cuda")
+    P.ascg_recover(n, w, Yd, ld, dev(torch, cf), xd, r, p)
+    torch.cuda.synchronize()
+    xo, ro, po = O.recover(Y.T, x, cf[:w], cf[w:2 * w], cf[2 * w:])
+    g = gamma_n(w + 1)
+    assert np.all(np.abs(xd.cpu().numpy() - xo) <= 2 * g * (np.abs(Y.T) @ np.abs(cf[:w]) + np.abs(x)))
+    assert np.all(np.abs(r.cpu().numpy() - ro) <= 2 * g * (np.abs(Y.T) @ np.abs(cf[w:2 * w])))
+    assert np.all(np.abs(p.cpu().numpy() - po) <= 2 * g * (np.abs(Y.T) @ np.abs(cf[2 * w:])))
+
+
+def test_recover_in_place_on_basis(env):
+    """r and p may be columns 1 and 0 of Y itself."""
+    P, torch = env
+    n, w = 5003, 7
+    rng = np.random.default_rng(5)
+    Y = rng.standard_normal((w, n))
+    cf = rng.standard_normal(3 * w)
+    Yd = dev(torch, Y.ravel())
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P.ascg_recover(n, w, Yd, n, dev(torch, cf), x, Yd[n:].data_ptr(), Yd.data_ptr())
+    _, ro, po = O.recover(Y.T, np.zeros(n), cf[:w], cf[w:2 * w], cf[2 * w:])
+    got = Yd.cpu().numpy().reshape(w, n)
+    assert np.allclose(got[1], ro, rtol=1e-13, atol=1e-13) and np.allclose(got[0], po, rtol=1e-13, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# a2: Newton shifts (Ritz values + Leja order)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("k,s", [(24, 12), (8, 4), (32, 16), (2, 1)])
+def test_newton_shifts_parity(env, k, s):
+    P, torch = env
+    A = MATRICES["diffusion_63"]()
+    Ao = O.Operator.from_csr(A)
+    b = W.rhs_uniform(A.n, np.random.default_rng(k))
+    cl = O.classical_cg(Ao, b, np.zeros(A.n), eps_target=0.0, max_iters=k)
+    got = P.ascg_newton_shifts(cl.alphas, cl.betas, k, s)
+    want = O.leja_order(O.ritz_values(cl.alphas, cl.betas))[:s]
+    scale = max(abs(v) for v in want)
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * scale), (got, want)
+
+
+# ---------------------------------------------------------------------------
+# whole solves (Alg. 1, 2, 4)
+# ---------------------------------------------------------------------------
+
+SOLVES = [
+    ("poisson2d_32", dict(method="classical"), 1e-10),
+    ("poisson2d_32", dict(method="fixed", basis="monomial", s_max=4), 1e-10),
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8), 1e-10),
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=10), 1e-13),
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8, s0=2, f=1), 1e-10),
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8, check_in_loop=False), 1e-10),
+    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16), 1e-12),
+    ("poisson3d_23", dict(method="classical"), 1e-12),
+    ("diffusion_63", dict(method="adaptive", basis="newton", s_max=12, newton_warmup=24), 1e-10),
+    ("banded_3001", dict(method="adaptive", basis="monomial", s_max=10), 1e-8),
+    ("banded_3001", dict(method="adaptive", basis="chebyshev", s_max=10), 1e-12),
+]
+
+
+def lam_for(name, A):
+    if name.startswith("poisson2d"):
+        return W.poisson_eig_bounds(2, 32)
+    if name.startswith("poisson3d"):
+        return W.poisson_eig_bounds(3, 23)
+    ev = np.linalg.eigvalsh(A.to_dense()) if A.n <= 4000 else None
+    return (float(ev[0]), float(ev[-1])) if ev is not None else None
+
+
+def run_gpu(P, torch, A, b, x1, kw, eps, timing=False, max_iters=20000):
+    op = make_op(P, A)
+    res_hist = np.zeros(max_iters + 2)
+    infos = P.block_infos(max_iters + 2)
+    o = P.make_options(eps_target=eps, max_iters=max_iters, res_hist=res_hist, block_hist=infos, timing=timing,
+                       **kw)
+    bd = dev(torch, b)
+    xd = dev(torch, x1)
+    res = P.ascg_solve(op, bd, xd, o)
+    x = xd.cpu().numpy()
+    P.ascg_op_destroy(op)
+    blocks = parity.gpu_blocks_from_infos(infos, res.blocks)
+    return res, res_hist[:res.iters + 1], blocks, x
+
+
+def run_oracle(A, b, x1, kw, eps, lam, max_iters=20000):
+    Ao = O.Operator.from_csr(A)
+    method = kw.get("method", "adaptive")
+    if method == "classical":
+        return O.classical_cg(Ao, b, x1, eps_target=eps, max_iters=max_iters)
+    s = kw.get("s_max", 8)
+    if method == "fixed":
+        return O.fixed_sstep_cg(Ao, b, x1, s, O.monomial_params(s), eps_target=eps, max_iters=max_iters)
+    return O.adaptive_sstep_cg(Ao, b, x1, s_max=s, s0=kw.get("s0"), f=kw.get("f"), eps_target=eps,
+                               basis=kw.get("basis", "monomial"), lam=lam, newton_warmup=kw.get("newton_warmup"),
+                               check_in_loop=kw.get("check_in_loop", True), max_iters=max_iters)
+
+
+@pytest.mark.parametrize("name,kw,eps", SOLVES)
+def test_solve_parity(env, name, kw, eps):
+    P, torch = env
+    A = MATRICES[name]()
+    b = W.rhs_uniform(A.n, np.random.default_rng(1001))
+    x1 = np.zeros(A.n)
+    lam = lam_for(name, A) if kw.get("basis") == "chebyshev" else None
+    kwg = dict(kw)
+    if lam is not None:
+        kwg["lam"] = lam
+    res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kwg, eps)
+    orc = run_oracle(A, b, x1, kw, eps, lam)
+    assert res.status == P.ASCG_OK and orc.converged, (res.status, orc.status)
+    if kw["method"] == "adaptive":
+        exempt, bad = parity.compare_block_sequences(blocks, orc.blocks, A.n, orc.res_hist, eps)
+        assert not bad, bad
+    else:
+        exempt = None
+        if kw["method"] == "fixed":
+            assert [b_["s_k"] for b_ in blocks] == [b_["s_k"] for b_ in orc.blocks]
+    nwin = parity.history_window(blocks, getattr(orc, "blocks", []), exempt, iters=20)
+    if kw.get("basis") == "newton":
+        nwin = max(nwin, min(25, len(hist)))   # the classical warm-up is compared too
+    hg, ho = np.asarray(hist[:nwin]), np.asarray(orc.res_hist[:nwin])
+    assert len(hg) == len(ho)
+    assert np.all(np.abs(hg - ho) <= 1e-10), np.abs(hg - ho).max()
+    if exempt is None and kw["method"] == "adaptive":
+        assert len(blocks) == len(orc.blocks) and res.iters == orc.iters
+    assert 0.5 * orc.true_res <= res.rel_res_true <= 2.0 * orc.true_res, (res.rel_res_true, orc.true_res)
+    Ao = O.Operator.from_csr(A)
+    assert abs(O.norm2(O.residual(Ao, b, x)) / np.linalg.norm(b) - res.rel_res_true) <= 1e-3 * res.rel_res_true
+
+
+def test_solve_is_deterministic(env):
+    P, torch = env
+    A = MATRICES["poisson3d_23"]()
+    b = W.rhs_uniform(A.n, np.random.default_rng(2))
+    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=W.poisson_eig_bounds(3, 23))
+    r1, h1, b1, x1 = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-12)
+    r2, h2, b2, x2 = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-12)
+    assert np.array_equal(h1, h2) and np.array_equal(x1, x2) and b1 == b2
+
+
+def test_solve_host_matches_device(env):
+    P, torch = env
+    A = MATRICES["poisson2d_32"]()
+    b = W.rhs_uniform(A.n, np.random.default_rng(3))
+    op = make_op(P, A)
+    o = P.make_options(method="adaptive", s_max=8, eps_target=1e-10)
+    xh = np.zeros(A.n)
+    rh = P.ascg_solve_host(op, np.ascontiguousarray(b), xh, o)
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    rd = P.ascg_solve(op, dev(torch, b), xd, o)
+    assert rh.iters == rd.iters and np.array_equal(xh, xd.cpu().numpy())
+    P.ascg_op_destroy(op)
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+
+def test_one_by_one_system(env):
+    P, torch = env
+    A = MATRICES["one"]()
+    for kw in (dict(method="classical"), dict(method="adaptive", s_max=4), dict(method="fixed", s_max=3)):
+        res, hist, blocks, x = run_gpu(P, torch, A, np.array([5.0]), np.zeros(1), kw, 1e-12)
+        assert res.status == P.ASCG_OK and abs(x[0] - 2.0) <= 1e-15
+
+
+def test_zero_rhs_gives_zero(env):
+    P, torch = env
+    A = MATRICES["poisson2d_32"]()
+    res, hist, blocks, x = run_gpu(P, torch, A, np.zeros(A.n), np.ones(A.n), dict(method="adaptive"), 1e-10)
+    assert res.status == P.ASCG_OK and np.all(x == 0)
+
+
+def test_warm_start_and_cap(env):
+    P, torch = env
+    A = MATRICES["poisson2d_32"]()
+    b = W.rhs_uniform(A.n, np.random.default_rng(4))
+    x1 = np.random.default_rng(5).standard_normal(A.n) * 1e-3
+    kw = dict(method="adaptive", basis="monomial", s_max=8)
+    res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kw, 1e-10)
+    orc = run_oracle(A, b, x1, kw, 1e-10, None)
+    assert res.status == P.ASCG_OK
+    assert np.all(np.abs(hist[:21] - np.asarray(orc.res_hist[:21])) <= 1e-10)
+    res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kw, 1e-10, max_iters=30)
+    assert res.status == P.ASCG_NOT_CONVERGED and res.iters == 30
+
+
+def test_small_n_large_s(env):
+    """n < 2s+1: every basis is rank deficient; the method must still converge."""
+    P, torch = env
+    A = W.poisson2d(4)   # n = 16
+    b = W.rhs_uniform(A.n, np.random.default_rng(6))
+    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=W.poisson_eig_bounds(2, 4))
+    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-12)
+    assert res.status == P.ASCG_OK and res.rel_res_true <= 2e-12
+
+
+# ---------------------------------------------------------------------------
+# full sizes: sampled outputs and the first iterations against the oracle
+# ---------------------------------------------------------------------------
+
+def test_full_size_poisson3d_128(env):
+    """3D Poisson 128^3, adaptive Chebyshev s_max = 16, target 1e-12 (the measured workload)."""
+    P, torch = env
+    cfg = W.poisson3d_128()
+    A, b = cfg["A"], cfg["b"]
+    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=cfg["lam"])
+    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-12)
+    assert res.status == P.ASCG_OK and res.rel_res_true <= 2e-12
+    Ao = O.Operator.from_csr(A)
+    orc = O.adaptive_sstep_cg(Ao, b, np.zeros(A.n), s_max=16, eps_target=1e-12, basis="chebyshev",
+                              lam=cfg["lam"], max_iters=20)
+    exempt, bad = parity.compare_block_sequences(blocks, orc.blocks[:-1], A.n)
+    assert not bad, bad
+    nwin = parity.history_window(blocks, orc.blocks, exempt, iters=20)
+    assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= 1e-10)
+    # sampled rows of A x against the oracle, row by row
+    rng = np.random.default_rng(9)
+    xs = torch.from_numpy(x).cuda()
+    y = torch.empty(A.n, dtype=torch.float64, device="cuda")
+    op = make_op(P, A)
+    P.ascg_spmv(op, xs, y)
+    yg = y.cpu().numpy()
+    for i in rng.integers(0, A.n, 200):
+        k0, k1 = A.rowptr[i], A.rowptr[i + 1]
+        want = sum(A.val[k] * x[A.colind[k]] for k in range(k0, k1))
+        assert abs(yg[i] - want) <= 1e-14 * sum(abs(A.val[k] * x[A.colind[k]]) for k in range(k0, k1)) + 1e-300
+    P.ascg_op_destroy(op)
+
+
+def test_full_size_diffusion_2048_warmup_and_shifts(env):
+    """2D diffusion 2048^2, Newton basis: the 24 warm-up iterations and the shifts."""
+    P, torch = env
+    cfg = W.diffusion2d_2048()
+    A, b = cfg["A"], cfg["b"]
+    kw = dict(method="adaptive", basis="newton", s_max=12, newton_warmup=24)
+    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-10, max_iters=60)
+    Ao = O.Operator.from_csr(A)
+    cl = O.classical_cg(Ao, b, np.zeros(A.n), eps_target=1e-10, max_iters=24)
+    assert np.all(np.abs(hist[:25] - np.asarray(cl.res_hist[:25])) <= 1e-10)
+    want = O.leja_order(O.ritz_values(cl.alphas, cl.betas))[:12]
+    got = P.ascg_newton_shifts(cl.alphas, cl.betas, 24, 12)
+    assert np.allclose(got, want, rtol=0, atol=1e-12 * max(abs(v) for v in want))
