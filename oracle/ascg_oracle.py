@@ -357,6 +357,47 @@ def recover(Y, x, xc, rc, pc):
     return x + Y @ xc, Y @ rc, Y @ pc
 
 
+def adaptive_block(G, sbar: int, bp: BasisParams, eps_star: float, c: float, nrows: int,
+                   check_in_loop: bool = True, max_steps: int | None = None, trace: bool = False):
+    """One block of Alg. 4 after G is formed: "Determine s~_k" to the end of the inner loop.
+
+    ||r_{m+1}|| = sqrt(G[i_s, i_s]) (column i_s is r since rho_0 = 1);
+    threshold = eps* / (c eps ||r_{m+1}||); s~ by eq. (condy); gamma =
+    sqrt(kappa(G_{k,s~})); G and B restricted to Y_{k,s~}; inner steps with the
+    eq. (check) break test. Returns (block record, InnerResult, column indices
+    of Y_{k,s~} inside Y_{k,sbar}).
+    """
+    i_s = sbar + 1
+    rnorm = math.sqrt(max(float(G[i_s, i_s]), 0.0))
+    threshold = eps_star / (c * EPS * rnorm) if rnorm > 0 else math.inf
+    stilde, kappas = choose_s(G, sbar, threshold, nrows)
+    idx = submatrix_index(sbar, stilde)
+    kap, gclamped = kappa_gram(G[np.ix_(idx, idx)], nrows)
+    gamma_est = math.sqrt(kap)
+    Gt = G[np.ix_(idx, idx)]
+    Bt = basis_change_matrix(stilde, bp)
+    nsteps = stilde if max_steps is None else min(stilde, max_steps)
+    checks = []
+
+    def stop_test(j, rGr_new):
+        rn = math.sqrt(max(float(rGr_new), 0.0))
+        if rn <= eps_star:
+            return "converged"
+        if check_in_loop:
+            tj = eps_star / (c * EPS * rn) if rn > 0 else math.inf
+            checks.append((j, tj))
+            if gamma_est >= tj:
+                return "break"
+        return None
+
+    inner = coordinate_steps(Gt, Bt, stilde, nsteps, stop_test, trace=trace)
+    blk = dict(sbar=sbar, stilde=stilde, s_k=inner.steps, threshold=threshold, rnorm=rnorm, kappas=kappas,
+               gamma=gamma_est, gamma_clamped=gclamped, checks=checks, stop=inner.stop)
+    if trace:
+        blk.update(G=Gt, B=Bt, inner=inner.trace)
+    return blk, inner, idx
+
+
 # ---------------------------------------------------------------------------
 # Drivers
 # ---------------------------------------------------------------------------
@@ -552,38 +593,14 @@ def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, 
         sbar = s0 if k == 0 else min(s_prev + f, s_max)
         Y = matrix_powers(A, p, r, sbar, bp)
         G = gram(Y)
-        i_s = sbar + 1
-        rnorm = math.sqrt(max(float(G[i_s, i_s]), 0.0))
-        threshold = eps_star / (c * EPS * rnorm) if rnorm > 0 else math.inf
-        stilde, kappas = choose_s(G, sbar, threshold, A.n)
-        idx = submatrix_index(sbar, stilde)
-        kap, gclamped = kappa_gram(G[np.ix_(idx, idx)], A.n)
-        gamma_est = math.sqrt(kap)
-        Yt = Y[:, idx]
-        Gt = G[np.ix_(idx, idx)]
-        Bt = basis_change_matrix(stilde, bp)
-        nsteps = min(stilde, max_iters - m)
-        checks = []
-
-        def stop_test(j, rGr_new):
-            rn = math.sqrt(max(float(rGr_new), 0.0))
-            if rn <= eps_star:
-                return "converged"
-            if check_in_loop:
-                tj = eps_star / (c * EPS * rn) if rn > 0 else math.inf
-                checks.append((j, tj))
-                if gamma_est >= tj:
-                    return "break"
-            return None
-
-        inner = coordinate_steps(Gt, Bt, stilde, nsteps, stop_test, trace=trace)
+        blk, inner, idx = adaptive_block(G, sbar, bp, eps_star, c, A.n, check_in_loop, max_iters - m,
+                                         trace=trace)
         if inner.steps == 0:
             return SolveResult(x, r, p, hist, alphas, betas, m, False, "breakdown", blocks)
-        blk = dict(k=k, sbar=sbar, stilde=stilde, s_k=inner.steps, threshold=threshold, rnorm=rnorm,
-                   kappas=kappas, gamma=gamma_est, gamma_clamped=gclamped, checks=checks,
-                   stop=inner.stop, m=m)
+        Yt = Y[:, idx]
+        blk.update(k=k, m=m)
         if trace:
-            blk.update(Y=Yt, G=Gt, B=Bt, x_start=x.copy(), r_start=r.copy(), inner=inner.trace)
+            blk.update(Y=Yt, x_start=x.copy(), r_start=r.copy())
         x, r, p = recover(Yt, x, inner.xc, inner.rc, inner.pc)
         alphas += inner.alphas
         betas += inner.betas
