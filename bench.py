@@ -218,12 +218,12 @@ def our_arm(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    from paper_1701_03989_gb300 import build as B
+    import __graft_entry__
     if rank == 0 or world == 1:
-        B.build_all()
+        __graft_entry__.build()
     if world > 1:
         dist.barrier()
-        B.build_all()
+        __graft_entry__.build()
     import paper_1701_03989_gb300 as P
     import workloads as W
 

@@ -10,6 +10,7 @@ from __future__ import annotations
 
 import glob
 import os
+import platform
 import subprocess
 import sys
 from concurrent.futures import ThreadPoolExecutor
@@ -52,9 +53,25 @@ def _compile(src: str, extra: list[str], verbose: bool) -> str:
     return obj
 
 
+def _same_machine() -> bool:
+    """Objects are reused only on the machine type that built them (x86_64 vs aarch64)."""
+    stamp = os.path.join(BUILD, "MACHINE")
+    me = platform.machine()
+    ok = os.path.exists(stamp) and open(stamp).read().strip() == me
+    if not ok:
+        for f in glob.glob(os.path.join(BUILD, "*.o")):
+            os.remove(f)
+        if os.path.exists(LIB):
+            os.remove(LIB)
+        with open(stamp, "w") as fh:
+            fh.write(me + "\n")
+    return ok
+
+
 def build_all(verbose: bool = False, extra: list[str] | None = None) -> str:
     """Compiles every csrc/*.cu and links libascg.so. Returns the library path."""
     os.makedirs(BUILD, exist_ok=True)
+    _same_machine()
     srcs = sorted(glob.glob(os.path.join(CSRC, "*.cu")))
     extra = list(extra or [])
     with ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:

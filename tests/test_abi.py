@@ -18,8 +18,8 @@ HEADER = os.path.join(ROOT, "include", "ascg.h")
 
 @pytest.fixture(scope="module")
 def P():
-    from paper_1701_03989_gb300 import build as B
-    B.build_all()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1701_03989_gb300 as P
     return P
 

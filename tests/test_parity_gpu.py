@@ -27,8 +27,8 @@ def gamma_n(k):
 @pytest.fixture(scope="module")
 def env():
     import torch
-    from paper_1701_03989_gb300 import build as B
-    B.build_all()
+    import __graft_entry__
+    __graft_entry__.build()
     import paper_1701_03989_gb300 as P
     torch.cuda.init()
     return P, torch
