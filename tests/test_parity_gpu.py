@@ -217,16 +217,19 @@ def test_block_step_parity(env, name, kind, sbar, warm, eps):
     st = info.stilde
     ws = 2 * st + 1
     c = coords.cpu().numpy().reshape(3, w)
+    # same G on both sides: the coordinate steps differ only in operation order,
+    # amplified by at most ~kappa(G_{k,s~}) (quadratic forms in G)
+    rtol = max(1e-9, 10 * EPS * parity.block_kappa(blk))
     # oracle coordinates are in [P, R] order of the s~ basis
     perm_s = interleave_perm(st)
     for row, ref in ((0, inner.xc), (1, inner.rc), (2, inner.pc)):
         got = c[row, :ws]
         want = np.asarray(ref)[perm_s]
         assert np.all(c[row, ws:] == 0)
-        assert np.allclose(got, want, rtol=1e-9, atol=1e-9 * np.abs(want).max()), row
-    np.testing.assert_allclose(hist[:, 0], inner.alphas, rtol=1e-9)
-    np.testing.assert_allclose(hist[:, 1], inner.betas, rtol=1e-8, atol=1e-14)
-    np.testing.assert_allclose(hist[:, 2], [math.sqrt(max(v, 0)) for v in inner.rGr], rtol=1e-8, atol=1e-14)
+        assert np.allclose(got, want, rtol=rtol, atol=rtol * np.abs(want).max()), (row, rtol)
+    np.testing.assert_allclose(hist[:, 0], inner.alphas, rtol=rtol)
+    np.testing.assert_allclose(hist[:, 1], inner.betas, rtol=rtol, atol=1e-14)
+    np.testing.assert_allclose(hist[:, 2], [math.sqrt(max(v, 0)) for v in inner.rGr], rtol=rtol, atol=1e-14)
 
 
 def test_block_step_fixed_s(env):
@@ -383,7 +386,8 @@ def test_solve_parity(env, name, kw, eps):
         nwin = max(nwin, min(25, len(hist)))   # the classical warm-up is compared too
     hg, ho = np.asarray(hist[:nwin]), np.asarray(orc.res_hist[:nwin])
     assert len(hg) == len(ho)
-    assert np.all(np.abs(hg - ho) <= 1e-10), np.abs(hg - ho).max()
+    tau = parity.history_tolerance(getattr(orc, "blocks", []) if kw["method"] == "adaptive" else [], ho, nwin)
+    assert np.all(np.abs(hg - ho) <= tau), (np.abs(hg - ho) / tau).max()
     if exempt is None and kw["method"] == "adaptive":
         assert len(blocks) == len(orc.blocks) and res.iters == orc.iters
     assert 0.5 * orc.true_res <= res.rel_res_true <= 2.0 * orc.true_res, (res.rel_res_true, orc.true_res)
@@ -443,7 +447,8 @@ def test_warm_start_and_cap(env):
     res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kw, 1e-10)
     orc = run_oracle(A, b, x1, kw, 1e-10, None)
     assert res.status == P.ASCG_OK
-    assert np.all(np.abs(hist[:21] - np.asarray(orc.res_hist[:21])) <= 1e-10)
+    tau = parity.history_tolerance(orc.blocks, np.asarray(orc.res_hist), 21)
+    assert np.all(np.abs(hist[:21] - np.asarray(orc.res_hist[:21])) <= tau)
     res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kw, 1e-10, max_iters=30)
     assert res.status == P.ASCG_NOT_CONVERGED and res.iters == 30
 
@@ -476,7 +481,8 @@ def test_full_size_poisson3d_128(env):
     exempt, bad = parity.compare_block_sequences(blocks, orc.blocks[:-1], A.n)
     assert not bad, bad
     nwin = parity.history_window(blocks, orc.blocks, exempt, iters=20)
-    assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= 1e-10)
+    tau = parity.history_tolerance(orc.blocks, np.asarray(orc.res_hist), nwin)
+    assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= tau)
     # sampled rows of A x against the oracle, row by row
     rng = np.random.default_rng(9)
     xs = torch.from_numpy(x).cuda()
