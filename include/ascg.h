@@ -230,6 +230,30 @@ ascg_status ascg_recover(int64_t n, int w, const double* Y, int64_t ldY, const d
 ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k, int s,
                                double* shifts, void* cuda_stream);
 
+/* Gram matrix G = Y^T Y exactly as ascg_gram computes it (same kernels, same
+ * summation order, so the same bits), but without allocating device memory.
+ * The paper has no counterpart: this exists for callers that must not call
+ * cudaMalloc or cudaFree, such as code running under a fixed device-memory
+ * budget owned by a host framework, or latency-sensitive loops where the
+ * device-wide synchronisation of cudaFree would stall other streams.
+ *  - Y, ldY, n, w, G: as for ascg_gram (device Y; device G of w*w doubles,
+ *    row-major, both halves written). 1 <= w <= 33; larger w returns
+ *    ASCG_ERR_INVALID.
+ *  - The per-CTA partial sums live in one static device array of 160 x 561
+ *    doubles (701 KB). Every GPU that loads the library holds it until the
+ *    process exits. A GPU that would use more than 160 CTAs (more than 160 SMs)
+ *    gets ASCG_ERR_INVALID.
+ *  - Calls nothing that allocates: no cudaMalloc, cudaFree or allocating
+ *    library routine. The first call on each device looks up the array's
+ *    device address (cudaGetSymbolAddress) with that device current. Make
+ *    that first call before any stream capture.
+ *  - Every call uses the same array. Calls whose work overlaps on the GPU
+ *    (for example on two streams at once) race and give wrong results:
+ *    order them on one stream.
+ *  - Returns once the work is enqueued on the stream (it does not
+ *    synchronise). */
+ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
+
 /* Message of the last error on this thread ("" if none). */
 const char* ascg_last_error(void);
 

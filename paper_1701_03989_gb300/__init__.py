@@ -81,6 +81,7 @@ def _load():
         "ascg_spmv": (C.c_int, [P, P, P, P]),
         "ascg_matrix_powers": (C.c_int, [P, C.c_int, P, P, P, P, I64, P]),
         "ascg_gram": (C.c_int, [I64, C.c_int, P, I64, P, P]),
+        "ascg_gram_noalloc": (C.c_int, [I64, C.c_int, P, I64, P, P]),
         "ascg_block_step": (C.c_int, [C.c_int, P, C.c_int, P, P, P, I64, C.c_double, C.c_double, C.c_int,
                                       C.c_int, C.c_double, P, C.POINTER(ascg_block_info), P, P]),
         "ascg_recover": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
@@ -194,6 +195,13 @@ def ascg_gram(n, w, Y, ldY, G, stream=None):
     _check(_lib.ascg_gram(int(n), int(w), _ptr(Y), int(ldY), _ptr(G), _stream(stream)), "ascg_gram")
 
 
+def ascg_gram_noalloc(n, w, Y, ldY, G, stream=None):
+    """As ascg_gram, but with no device allocation (static scratch; see include/ascg.h).
+    Enqueues only: synchronise the stream before reading G."""
+    _check(_lib.ascg_gram_noalloc(int(n), int(w), _ptr(Y), int(ldY), _ptr(G), _stream(stream)),
+           "ascg_gram_noalloc")
+
+
 def ascg_block_step(sbar, G, method, theta, sigma, gamma, nrows, eps_star, c, check_in_loop, max_steps, bnorm,
                     coords, stream=None):
     """Returns (ascg_block_info, hist ndarray [s_k, 3] of alpha, beta, relres)."""
@@ -266,5 +274,6 @@ def block_infos(count: int):
 
 
 EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
-            "ascg_solve_host", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_block_step", "ascg_recover",
+            "ascg_solve_host", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc",
+            "ascg_block_step", "ascg_recover",
             "ascg_newton_shifts", "ascg_last_error"]

@@ -761,3 +761,7 @@ ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k,
 const char* ascg_last_error(void) { return g_err.c_str(); }
 
 }  // extern "C"
+
+namespace ascg {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace ascg

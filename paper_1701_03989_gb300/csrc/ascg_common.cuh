@@ -7,6 +7,7 @@
 #pragma once
 
 #include <cstdint>
+#include <string>
 #include <cuda_runtime.h>
 
 #include "../../include/ascg.h"
@@ -149,5 +150,8 @@ cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGSta
 // CG state init from rr = r^T r computed into st->rr.
 cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
                            double* res_hist, int res_cap, cudaStream_t s);
+
+// Sets the message that ascg_last_error() returns on this thread.
+void set_last_error(const std::string& msg);
 
 }  // namespace ascg
