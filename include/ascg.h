@@ -16,9 +16,10 @@
  *  - "device" pointers are CUDA device memory of the current device. "host"
  *    pointers are ordinary (pageable or pinned) host memory.
  *  - Calls are ordered on the given CUDA stream (NULL = the legacy default
- *    stream). Calls that report results on the host (ascg_solve*,
- *    ascg_block_step, ascg_newton_shifts) synchronise that stream before
- *    they return. The others return as soon as their work is enqueued.
+ *    stream). Calls that report results on the host or free temporaries
+ *    (ascg_solve*, ascg_block_step, ascg_newton_shifts, ascg_matrix_powers,
+ *    ascg_gram) synchronise that stream before they return. The others return
+ *    as soon as their work is enqueued.
  *  - Sizes are int64_t. Matrices have n >= 1 rows and nnz < 2^31 nonzeros.
  *  - All arithmetic is IEEE double. eps = 2^-53.
  *  - An ascg_op is not safe for concurrent use from several threads or
@@ -187,7 +188,11 @@ ascg_status ascg_spmv(ascg_op op, const double* x, double* y, void* cuda_stream)
  * p and r. Fills columns 2..2s by
  *   rho_{j+1} = ((A - theta_j) rho_j - sigma_{j-1} rho_{j-1}) / gamma_j.
  * theta, sigma, gamma: host double[s] (eq. (polybasiscg) coefficients;
- * sigma[j] multiplies rho_j when rho_{j+2} is formed). 1 <= s <= 16. */
+ * sigma[j] multiplies rho_j when rho_{j+2} is formed; gamma[j] != 0; at most
+ * two distinct gamma values other than 1). 1 <= s <= 16. The coefficients are
+ * folded into the operator first ((D - theta_j)/gamma_j and O/gamma_j for
+ * A = D + O), exactly as ascg_solve does, so this call runs the solver's own
+ * kernel. */
 ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const double* sigma,
                                const double* gamma, double* Y, int64_t ldY, void* cuda_stream);
 

@@ -82,6 +82,9 @@ struct Workspace {
   int res_cap = 0;
   double* ab_hist = nullptr;  // alpha[ab_cap], beta[ab_cap]
   int ab_cap = 0;
+  double* dtils = nullptr;      // folded diagonals Dt_j, kMaxS x n
+  double* oscaled[2] = {};      // O / gamma for up to two gamma != 1
+  bool steps_ready = false;
   // pinned host mirrors
   BlockState* h_bst = nullptr;
   CGState* h_cgs = nullptr;
@@ -93,6 +96,8 @@ struct Workspace {
     dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(counter);
     dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
     dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
+    dev_free(dtils); dev_free(oscaled[0]); dev_free(oscaled[1]);
+    steps_ready = false;
     if (h_bst) cudaFreeHost(h_bst);
     if (h_cgs) cudaFreeHost(h_cgs);
     if (h_scal) cudaFreeHost(h_scal);
@@ -112,8 +117,15 @@ struct ascg_op_s {
   int32_t* rowptr = nullptr;
   int32_t* colind = nullptr;
   double* val = nullptr;
+  // A = D + O for the matrix powers kernel
+  int64_t nnz_off = 0;
+  int32_t* o_rowptr = nullptr;
+  int32_t* o_colind = nullptr;
+  double* o_val = nullptr;
+  double* diag = nullptr;
   Workspace ws;
   DevCSR csr() const { return DevCSR{n, nnz, rowptr, colind, val}; }
+  DevSplit split() const { return DevSplit{n, nnz_off, o_rowptr, o_colind, o_val, diag}; }
 };
 
 namespace {
@@ -158,6 +170,11 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     dev_free(w.partials);
     ASCG_TRY(dev_alloc(&w.partials, (size_t)pcap));
     w.partials_cap = pcap;
+  }
+  if (wcols > 2 && !w.dtils) {
+    ASCG_TRY(dev_alloc(&w.dtils, (size_t)kMaxS * n));
+    ASCG_TRY(dev_alloc(&w.oscaled[0], (size_t)op->nnz_off));
+    ASCG_TRY(dev_alloc(&w.oscaled[1], (size_t)op->nnz_off));
   }
   if (w.res_cap < res_cap) {
     dev_free(w.res_hist); dev_free(w.ab_hist);
@@ -211,6 +228,47 @@ void basis_params(const ascg_options& o, double* th, double* sg, double* gm) {
 
 // Runs classical CG iterations (Alg. 1) on the device until the CG state says
 // done. x, r, p, q are device vectors. Returns the iterations done by this call.
+// Per-step operators of the matrix powers recurrence with theta, sigma and gamma
+// folded in (see StepOp). dtils: n x s doubles; oscaled: two arrays of nnz_off
+// doubles (used when gamma != 1; at most two distinct gamma values, which covers
+// the monomial, Chebyshev and Newton bases).
+ascg_status prepare_steps(ascg_op op, const double* th, const double* sg, const double* gm, int s, double* dtils,
+                          double* const oscaled[2], StepOp* out, cudaStream_t st, int* launches) {
+  double gam_of[2] = {0.0, 0.0};
+  int ng = 0;
+  for (int j = 0; j < s; ++j) {
+    if (!(gm[j] != 0.0) || !std::isfinite(gm[j]) || !std::isfinite(th[j]))
+      return fail(ASCG_ERR_INVALID, "basis coefficients must be finite with gamma != 0");
+    const double inv = 1.0 / gm[j];
+    const double* ov = op->o_val;
+    if (gm[j] != 1.0) {
+      int slot = -1;
+      for (int q = 0; q < ng; ++q)
+        if (gam_of[q] == gm[j]) slot = q;
+      if (slot < 0) {
+        if (ng == 2) return fail(ASCG_ERR_INVALID, "at most two distinct gamma != 1 are supported");
+        slot = ng++;
+        gam_of[slot] = gm[j];
+        ASCG_CUDA(launch_shift_scale(op->o_val, op->nnz_off, 0.0, inv, oscaled[slot], st));
+        ++*launches;
+      }
+      ov = oscaled[slot];
+    }
+    const double* dt = nullptr;
+    if (th[j] == 0.0 && gm[j] == 1.0) dt = op->diag;
+    for (int q = 0; q < j && !dt; ++q)
+      if (th[q] == th[j] && gm[q] == gm[j]) dt = out[q].dtil;
+    if (!dt) {
+      double* dst = dtils + (int64_t)j * op->n;
+      ASCG_CUDA(launch_shift_scale(op->diag, op->n, th[j], inv, dst, st));
+      ++*launches;
+      dt = dst;
+    }
+    out[j] = StepOp{ov, dt, j >= 1 ? sg[j - 1] * inv : 0.0};
+  }
+  return ASCG_OK;
+}
+
 ascg_status run_classical(ascg_op op, double* x, double* r, double* p, double eps_star, double bnorm,
                           int max_iters, int iter0, cudaStream_t s, ascg_result* res, bool timing) {
   Workspace& w = op->ws;
@@ -332,6 +390,13 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     std::memcpy(hp + kMaxS, sg, sizeof(sg));
     std::memcpy(hp + 2 * kMaxS, gm, sizeof(gm));
     ASCG_CUDA(cudaMemcpyAsync(w.params, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
+    StepOp steps[kMaxS];
+    if (!done) {
+      int nl = 0;
+      ASCG_TRY(prepare_steps(op, th, sg, gm, o.s_max, w.dtils, w.oscaled, steps, s, &nl));
+      res->launches += nl;
+    }
+    const DevSplit Asplit = op->split();
     const double sqrt_n = std::sqrt((double)n);
     int k = 0, s_prev = 0;
     int nb_info = 0;
@@ -354,7 +419,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
       for (int j = 0; j < sbar; ++j) {
-        ASCG_CUDA(launch_mpk_step(A, w.Y, w.ldY, j, 1, j < sbar - 1, th[j], j >= 1 ? sg[j - 1] : 0.0, gm[j], s));
+        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], w.Y, w.ldY, j, 1, j < sbar - 1, s));
       }
       res->launches += sbar;
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
@@ -533,23 +598,56 @@ ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, co
     rp32[i] = (int32_t)hrp[i];
   }
   rp32[n] = (int32_t)hrp[n];
+  // A = D + O: diagonal and off-diagonal parts for the matrix powers kernel
+  std::vector<int32_t> orp(n + 1);
+  std::vector<int32_t> oci;
+  std::vector<double> ova, dg(n, 0.0);
+  oci.reserve(nnz);
+  ova.reserve(nnz);
+  for (int64_t i = 0; i < n; ++i) {
+    orp[i] = (int32_t)oci.size();
+    for (int64_t k = hrp[i]; k < hrp[i + 1]; ++k) {
+      if (hci[k] == i) {
+        dg[i] += hva[k];
+      } else {
+        oci.push_back(hci[k]);
+        ova.push_back(hva[k]);
+      }
+    }
+  }
+  orp[n] = (int32_t)oci.size();
   ascg_op op = new ascg_op_s();
+  op->nnz_off = (int64_t)oci.size();
   op->n = n;
   op->nnz = nnz;
   cudaGetDevice(&op->device);
   ascg_status st = dev_alloc(&op->rowptr, n + 1);
   if (st == ASCG_OK) st = dev_alloc(&op->colind, (size_t)nnz);
   if (st == ASCG_OK) st = dev_alloc(&op->val, (size_t)nnz);
+  if (st == ASCG_OK) st = dev_alloc(&op->o_rowptr, n + 1);
+  if (st == ASCG_OK) st = dev_alloc(&op->o_colind, (size_t)op->nnz_off);
+  if (st == ASCG_OK) st = dev_alloc(&op->o_val, (size_t)op->nnz_off);
+  if (st == ASCG_OK) st = dev_alloc(&op->diag, (size_t)n);
   if (st == ASCG_OK) {
     cudaError_t e = cudaMemcpy(op->rowptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nnz) e = cudaMemcpy(op->colind, hci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
     if (e == cudaSuccess && nnz) e = cudaMemcpy(op->val, hva, sizeof(double) * nnz, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(op->o_rowptr, orp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && op->nnz_off)
+      e = cudaMemcpy(op->o_colind, oci.data(), sizeof(int32_t) * op->nnz_off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && op->nnz_off)
+      e = cudaMemcpy(op->o_val, ova.data(), sizeof(double) * op->nnz_off, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(op->diag, dg.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) st = fail(ASCG_ERR_CUDA, std::string("copy CSR: ") + cudaGetErrorString(e));
   }
   if (st != ASCG_OK) {
     dev_free(op->rowptr);
     dev_free(op->colind);
     dev_free(op->val);
+    dev_free(op->o_rowptr);
+    dev_free(op->o_colind);
+    dev_free(op->o_val);
+    dev_free(op->diag);
     delete op;
     return st;
   }
@@ -563,6 +661,10 @@ ascg_status ascg_op_destroy(ascg_op op) {
   dev_free(op->rowptr);
   dev_free(op->colind);
   dev_free(op->val);
+  dev_free(op->o_rowptr);
+  dev_free(op->o_colind);
+  dev_free(op->o_val);
+  dev_free(op->diag);
   delete op;
   return ASCG_OK;
 }
@@ -642,11 +744,24 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
   if (!op || !theta || !sigma || !gamma || !Y) return fail(ASCG_ERR_INVALID, "NULL argument");
   if (s < 1 || s > ASCG_MAX_S) return fail(ASCG_ERR_INVALID, "s must be in 1..16");
   if (ldY < op->n) return fail(ASCG_ERR_INVALID, "ldY < n");
-  for (int j = 0; j < s; ++j)
-    if (!(gamma[j] != 0.0) || !std::isfinite(gamma[j])) return fail(ASCG_ERR_INVALID, "gamma must be nonzero");
-  for (int j = 0; j < s; ++j)
-    ASCG_CUDA(launch_mpk_step(op->csr(), Y, ldY, j, 1, j < s - 1, theta[j], j >= 1 ? sigma[j - 1] : 0.0, gamma[j],
-                              (cudaStream_t)cuda_stream));
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  double* dtils = nullptr;
+  double* osc[2] = {nullptr, nullptr};
+  ascg_status rs = dev_alloc(&dtils, (size_t)s * op->n);
+  if (rs == ASCG_OK) rs = dev_alloc(&osc[0], (size_t)op->nnz_off);
+  if (rs == ASCG_OK) rs = dev_alloc(&osc[1], (size_t)op->nnz_off);
+  StepOp steps[kMaxS];
+  int nl = 0;
+  if (rs == ASCG_OK) rs = prepare_steps(op, theta, sigma, gamma, s, dtils, osc, steps, st, &nl);
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; rs == ASCG_OK && j < s && e == cudaSuccess; ++j)
+    e = launch_mpk_split_step(op->split(), steps[j], Y, ldY, j, 1, j < s - 1, st);
+  if (e == cudaSuccess && rs == ASCG_OK) e = cudaStreamSynchronize(st);
+  cudaFree(dtils);
+  cudaFree(osc[0]);
+  cudaFree(osc[1]);
+  if (rs != ASCG_OK) return rs;
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("matrix powers: ") + cudaGetErrorString(e));
   return ASCG_OK;
 }
 

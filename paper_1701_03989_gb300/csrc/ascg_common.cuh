@@ -63,10 +63,34 @@ constexpr int kRedBlocks = 304;
 cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out, double* partials,
                        unsigned* counter, cudaStream_t s);
 
-// Matrix powers step (eq. polybasiscg): forms column 2(j+1) from 2j, 2(j-1) if do_p,
-// and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
-cudaError_t launch_mpk_step(const DevCSR& A, double* Y, int64_t ldY, int j, int do_p, int do_r,
-                            double theta, double sigma_prev, double gamma, cudaStream_t s);
+// A split as D + O for the matrix powers kernel: O is the off-diagonal part in
+// CSR form (diagonal removed), D the diagonal.
+struct DevSplit {
+  int64_t n;
+  int64_t nnz_off;
+  const int32_t* rowptr;
+  const int32_t* colind;
+  const double* val;
+  const double* diag;
+};
+
+// Operator of one matrix powers step j (eq. polybasiscg) after folding the
+// basis coefficients into the matrix:
+//   rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1},
+//   Dt_j = (D - theta_j) / gamma_j,  Ot_j = O / gamma_j,  sig_j = sigma_{j-1} / gamma_j.
+// One multiply for the diagonal, one FMA per off-diagonal nonzero and one FMA for
+// the sigma term per row: nnz_row + 1 FP64 instructions instead of nnz_row + 3.
+struct StepOp {
+  const double* oval;   // values of Ot_j (O's pattern)
+  const double* dtil;   // Dt_j, n values
+  double sig;           // sig_j (0 for j = 0)
+};
+// Forms column 2(j+1) from 2j, 2(j-1) if do_p, and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
+cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
+                                  int do_r, cudaStream_t s);
+// dst[i] = (src[i] - theta) * scale, for i < n
+cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, double scale, double* dst,
+                               cudaStream_t s);
 
 // Gram partials: per CTA, the upper triangle (row-major pair order) of Y^T Y.
 int gram_grid();                // CTAs per launch at most (the SM count)

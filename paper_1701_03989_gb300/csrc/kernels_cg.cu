@@ -270,7 +270,9 @@ cudaError_t launch_cg_spmv_dot(const DevCSR& A, const double* p, double* q, CGSt
 cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, CGState* st,
                              double* partials, unsigned* counter, double* res_hist, int res_cap,
                              double* alpha_hist, double* beta_hist, int ab_cap, cudaStream_t s) {
-  cg_update_kernel<<<grid_for(n, 256, kRedBlocks), 256, 0, s>>>(n, x, r, p, q, st, partials, counter, res_hist,
+  // HBM-bound axpys: 8 CTAs per SM keep enough loads in flight (partials hold one
+  // slot per 256-row block, so any grid up to n/256 fits)
+  cg_update_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, x, r, p, q, st, partials, counter, res_hist,
                                                                 res_cap, alpha_hist, beta_hist, ab_cap);
   return cudaGetLastError();
 }

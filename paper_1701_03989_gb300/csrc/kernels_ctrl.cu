@@ -6,7 +6,7 @@
 // All of this is tiny dense work on matrices of order <= 33. On GB300 an FP64
 // warp instruction costs ~20 SM cycles whether 1 or 32 lanes are active, and
 // a dependent DFMA takes 64 cycles. So this code keeps the lanes busy on
-// independent work: one lane per row for the Householder steps, and 32
+// independent work: one lane per row for the Householder steps, and 64
 // evaluation points per Sturm multisection round.
 #include <math_constants.h>
 
@@ -74,19 +74,60 @@ __device__ void gershgorin(const double* d, const double* e, int m, double* lo, 
   *pivmin = 2.2250738585072014e-308 * fmax(1.0, e2max);
 }
 
+// Number of eigenvalues smaller than x of the symmetric tridiagonal (d, e2 =
+// e^2), from the signs of the leading principal minors of T - xI. The minors
+// follow p_k = (d_k - x) p_{k-1} - e2_{k-1} p_{k-2}, with no division. The
+// critical path is one FMA per step, against a division per step for the
+// pivot form. Rounding in this recurrence gives the exact signs of a matrix
+// whose d_k - x and e2 are perturbed by a few ulps (positive rescalings do
+// not change signs), the same backward error as the pivot form. The caller
+// scales T to norm <= 1, so |p_k| <= 3^k cannot overflow. Tiny minors are
+// rescaled by 2^256 (exact). A zero minor is replaced by a tiny value of the
+// sign opposite to its predecessor, as the pivot form does with -pivmin.
+__device__ __forceinline__ int sturm_det(const double* d, const double* e2, int m, double x) {
+  const double kUp = 1.157920892373162e77;    // 2^256
+  const double kTiny = 8.636168555094445e-78; // 2^-256
+  double pm2 = 1.0;
+  double pm1 = d[0] - x;
+  if (pm1 == 0.0) pm1 = -kTiny * kTiny;
+  int cnt = pm1 < 0.0;
+  for (int k = 1; k < m; ++k) {
+    const double t = e2[k - 1] * pm2;
+    double p = fma(d[k] - x, pm1, -t);
+    if (p == 0.0) p = -copysign(fabs(pm1) * kTiny, pm1);
+    cnt += (p < 0.0) != (pm1 < 0.0);
+    pm2 = pm1;
+    pm1 = p;
+    if (fabs(pm1) < kTiny) {
+      pm1 *= kUp;
+      pm2 *= kUp;
+    }
+  }
+  return cnt;
+}
+
 // kappa(G_{k,i}) for i = blockIdx.x + 1. G_{k,i} is the leading (2i+1) block of G
 // (interleaved column order). Warp 0 reduces it to tridiagonal form by
-// Householder reflections, one lane per row. Then warp 0 finds lambda_min and
-// warp 1 finds lambda_max by multisection.
-__global__ void __launch_bounds__(64) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
+// Householder reflections, one lane per row. The tridiagonal is scaled to unit
+// norm. Warps 0-1 then bracket lambda_min and warps 2-3 bracket lambda_max, each
+// pair evaluating 64 Sturm counts per round for a fixed 10 rounds.
+// lambda_min first decides certification (is it below the floor
+// (2i+1) sqrt(n) eps lambda_max?). Then a geometric grid finds its magnitude,
+// and a linear grid refines it to ~2^-50 relative. lambda_max is refined
+// linearly from [max d, Gershgorin bound].
+constexpr int kKappaRounds = 10;
+
+__global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
   const int i = blockIdx.x + 1;
   const int m = 2 * i + 1;
   const int w = 2 * sbar + 1;
   __shared__ double A[kMaxW][kMaxW + 1];
   __shared__ double v[32], wv[32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
-  __shared__ double lam[2];
-  __shared__ double gl, gh, pm;
+  __shared__ double lo_s[2], hi_s[2];
+  __shared__ unsigned mask_s[4];
+  __shared__ double floor_s, scale_s;
+  __shared__ int uncert_s;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -106,16 +147,18 @@ __global__ void __launch_bounds__(64) kappa_kernel(const double* __restrict__ G,
         const double beta = 2.0 / vn2;
         v[lane] = vi;
         __syncwarp();
-        double p0 = 0.0, p1 = 0.0;
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
         if (on) {
           int c = 0;
-          for (; c + 1 < len; c += 2) {
+          for (; c + 3 < len; c += 4) {
             p0 = fma(A[row][k + 1 + c], v[c], p0);
             p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
+            p2 = fma(A[row][k + 3 + c], v[c + 2], p2);
+            p3 = fma(A[row][k + 4 + c], v[c + 3], p3);
           }
-          if (c < len) p0 = fma(A[row][k + 1 + c], v[c], p0);
+          for (; c < len; ++c) p0 = fma(A[row][k + 1 + c], v[c], p0);
         }
-        const double pi = beta * (p0 + p1);
+        const double pi = beta * ((p0 + p1) + (p2 + p3));
         const double K = 0.5 * beta * warp_sum(vi * pi);
         const double wi = pi - K * vi;
         wv[lane] = wi;
@@ -129,24 +172,83 @@ __global__ void __launch_bounds__(64) kappa_kernel(const double* __restrict__ G,
     for (int r = lane; r < m; r += 32) d[r] = A[r][r];
     if (lane == 0) e[m - 2] = A[m - 1][m - 2];
     __syncwarp();
-    for (int r = lane; r + 1 < m; r += 32) e2[r] = e[r] * e[r];
     if (lane == 0) {
-      double lo, hi, piv;
-      gershgorin(d, e, m, &lo, &hi, &piv);
-      gl = lo;
-      gh = hi;
-      pm = piv;
+      double gl, gh, piv;
+      gershgorin(d, e, m, &gl, &gh, &piv);
+      const double S = fmax(fabs(gl), fabs(gh));
+      scale_s = S > 0.0 ? S : 1.0;
+    }
+    __syncwarp();
+    const double inv = 1.0 / scale_s;
+    for (int r = lane; r < m; r += 32) {
+      d[r] *= inv;
+      if (r + 1 < m) {
+        const double er = e[r] * inv;
+        e[r] = er;
+        e2[r] = er * er;
+      }
+    }
+    __syncwarp();
+    if (lane == 0) {
+      double gl, gh, piv, dmin = d[0], dmax = d[0];
+      gershgorin(d, e, m, &gl, &gh, &piv);
+      for (int r = 1; r < m; ++r) {
+        dmin = fmin(dmin, d[r]);
+        dmax = fmax(dmax, d[r]);
+      }
+      // certification floor, below the true one since lambda_max >= max d
+      floor_s = (double)m * st->sqrt_n * kEps * dmax;
+      lo_s[0] = 0.5 * floor_s;                    // geometric search range for lambda_min
+      hi_s[0] = dmin + 4.0 * kEps * fabs(dmin) + 1e-300;
+      lo_s[1] = dmax - 4.0 * kEps * fabs(dmax);   // lambda_max in [max d, Gershgorin]
+      hi_s[1] = gh;
+      // min d bounds lambda_min from above: below half the floor, uncertified outright
+      uncert_s = !(dmin > 0.0) || !(dmax > 0.0) || !(hi_s[0] > lo_s[0]);
     }
   }
   __syncthreads();
-  // lambda_min: smallest x with count >= 1; lambda_max: smallest x with count >= m
-  lam[warp] = multisect(d, e2, m, gl, gh, warp == 0 ? 1 : m, pm);
-  __syncthreads();
+  const int pair = warp >> 1;           // 0: lambda_min, 1: lambda_max
+  const int t = ((warp & 1) << 5) | lane;  // point index 0..63
+  const int target = pair == 0 ? 1 : m;
+  for (int round = 0; round < kKappaRounds; ++round) {
+    const double lo = lo_s[pair], hi = hi_s[pair];
+    double x;
+    if (pair == 0 && round == 0) {
+      // geometric grid between half the floor and min d: finds the magnitude
+      x = lo * pow(hi / lo, (double)(t + 1) / 65.0);
+    } else {
+      x = lo + (hi - lo) * ((double)(t + 1) / 65.0);
+    }
+    const int c = (pair == 0 && round == 0 && uncert_s) ? target : sturm_det(d, e2, m, x);
+    const unsigned bal = __ballot_sync(kFull, c >= target);
+    if (lane == 0) mask_s[warp] = bal;
+    __syncthreads();
+    if ((warp & 1) == 0 && lane == 0) {
+      const unsigned long long mk = (unsigned long long)mask_s[warp] | ((unsigned long long)mask_s[warp + 1] << 32);
+      // first point with count >= target; x re-derived with the lanes' expression
+      double nlo = lo, nhi = hi;
+      if (mk == 0ull) {
+        nlo = (pair == 0 && round == 0) ? lo * pow(hi / lo, 64.0 / 65.0) : lo + (hi - lo) * (64.0 / 65.0);
+      } else {
+        const int f = __ffsll((long long)mk) - 1;
+        nhi = (pair == 0 && round == 0) ? lo * pow(hi / lo, (double)(f + 1) / 65.0)
+                                       : lo + (hi - lo) * ((double)(f + 1) / 65.0);
+        if (f > 0)
+          nlo = (pair == 0 && round == 0) ? lo * pow(hi / lo, (double)f / 65.0) : lo + (hi - lo) * ((double)f / 65.0);
+      }
+      // lambda_min below the first geometric point, itself below the floor
+      if (pair == 0 && round == 0 && (mk & 1ull)) uncert_s = 1;
+      lo_s[pair] = nlo;
+      hi_s[pair] = nhi;
+    }
+    __syncthreads();
+  }
   if (threadIdx.x == 0) {
-    const double lmin = lam[0], lmax = lam[1];
+    const double lmin = 0.5 * (lo_s[0] + hi_s[0]);
+    const double lmax = 0.5 * (lo_s[1] + hi_s[1]);
     double sk;
     // reading: uncertified when lambda_min <= (2i+1) sqrt(n) eps lambda_max
-    if (!(lmax > 0.0) || !isfinite(lmax) || lmin <= (double)m * st->sqrt_n * kEps * lmax)
+    if (uncert_s || !(lmax > 0.0) || lmin <= (double)m * st->sqrt_n * kEps * lmax)
       sk = CUDART_INF;
     else
       sk = sqrt(lmax / lmin);
@@ -166,6 +268,21 @@ __device__ __forceinline__ double bapply(const double* v, int t, int ss, const d
   if (j < L) acc = fma(th[j], v[t], acc);
   if (j + 1 < L) acc = fma(sg[j], v[t + 2], acc);
   return acc;
+}
+
+// sum_c a[c] v[c] for c < w with four interleaved accumulators (fixed order),
+// which cuts the dependent-FMA chain to a quarter.
+__device__ __forceinline__ double rowdot(const double* a, const double* v, int w) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 3 < w; c += 4) {
+    s0 = fma(a[c], v[c], s0);
+    s1 = fma(a[c + 1], v[c + 1], s1);
+    s2 = fma(a[c + 2], v[c + 2], s2);
+    s3 = fma(a[c + 3], v[c + 3], s3);
+  }
+  for (; c < w; ++c) s0 = fma(a[c], v[c], s0);
+  return (s0 + s1) + (s2 + s3);
 }
 
 // Sum over the 64 threads of the CTA, identical in every thread, fixed order.
@@ -251,9 +368,7 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
     // alpha = (r'^T G r') / (p'^T G B p')
     if (row) u[t] = bapply(pc, t, ss, th, sg, gm);
     __syncthreads();
-    double gi = 0.0;
-    if (row)
-      for (int c = 0; c < ws; ++c) gi = fma(Gs[t][c], u[c], gi);
+    const double gi = row ? rowdot(Gs[t], u, ws) : 0.0;
     const double pGBp = sum64(row ? pc[t] * gi : 0.0, red);
     if (!(pGBp > 0.0) || !isfinite(pGBp) || !(rGr > 0.0) || !isfinite(rGr)) {
       stop = ASCG_STOP_BREAKDOWN;
@@ -270,9 +385,7 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
     __syncthreads();
     if (row) rn[t] = rc[t] - bapply(u, t, ss, th, sg, gm);
     __syncthreads();
-    double g2 = 0.0;
-    if (row)
-      for (int c = 0; c < ws; ++c) g2 = fma(Gs[t][c], rn[c], g2);
+    const double g2 = row ? rowdot(Gs[t], rn, ws) : 0.0;
     const double rGr_new = sum64(row ? rn[t] * g2 : 0.0, red);
     const double beta = rGr_new / rGr;
     if (row) {
@@ -395,7 +508,7 @@ __global__ void __launch_bounds__(32) newton_shifts_kernel(const double* __restr
 }  // namespace
 
 cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s) {
-  kappa_kernel<<<sbar, 64, 0, s>>>(G, st, sbar);
+  kappa_kernel<<<sbar, 128, 0, s>>>(G, st, sbar);
   return cudaGetLastError();
 }
 

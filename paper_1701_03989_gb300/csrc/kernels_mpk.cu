@@ -9,31 +9,36 @@
 // and applied to both vectors, so A is read s times per block, not 2s-1.
 // The GPU has no room to keep A on chip across steps for the large
 // workloads. This step is FP64-bound on GB300, so re-reading A costs no time.
+//
+// The basis coefficients are folded into the operator beforehand. A is kept
+// as D + O, and step j uses Dt_j = (D - theta_j)/gamma_j and O/gamma_j, so a
+// row costs nnz_row + 1 FP64 instructions rather than nnz_row + 3. That spends
+// HBM capacity, of which a GB300 has plenty, to save FP64 work, which it lacks.
 #include "ascg_common.cuh"
 
 namespace ascg {
 
 namespace {
 
-__global__ void __launch_bounds__(kSpmvRows) mpk_step_kernel(DevCSR A, double* __restrict__ Y, int64_t ldY,
-                                                             int j, int do_p, int do_r, double theta,
-                                                             double sigma_prev, double gamma_inv, int use_theta,
-                                                             int use_sigma, int use_gamma) {
+__global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSplit O, const double* __restrict__ oval,
+                                                                   const double* __restrict__ dtil, double sig,
+                                                                   double* __restrict__ Y, int64_t ldY, int j,
+                                                                   int do_p, int do_r) {
   __shared__ int srow[kSpmvRows + 1];
   __shared__ double sval[kSpmvTileNnz];
   __shared__ int scol[kSpmvTileNnz];
   const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
-  const int64_t r1 = min(r0 + kSpmvRows, A.n);
+  const int64_t r1 = min(r0 + kSpmvRows, O.n);
   const int nr = (int)(r1 - r0);
-  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = A.rowptr[r0 + i];
+  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = O.rowptr[r0 + i];
   __syncthreads();
   const int base = srow[0];
   const int cnt = srow[nr] - base;
   const bool staged = cnt <= kSpmvTileNnz;
   if (staged) {
     for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-      sval[k] = __ldg(A.val + base + k);
-      scol[k] = __ldg(A.colind + base + k);
+      sval[k] = __ldg(oval + base + k);
+      scol[k] = __ldg(O.colind + base + k);
     }
   }
   __syncthreads();
@@ -42,7 +47,9 @@ __global__ void __launch_bounds__(kSpmvRows) mpk_step_kernel(DevCSR A, double* _
   const int64_t row = r0 + lr;
   const double* pj = Y + (int64_t)(2 * j) * ldY;
   const double* rj = Y + (int64_t)(2 * j + 1) * ldY;
-  double tp = 0.0, tr = 0.0;
+  const double dt = dtil[row];
+  double tp = dt * pj[row];
+  double tr = do_r ? dt * rj[row] : 0.0;
   const int k0 = srow[lr], k1 = srow[lr + 1];
   if (do_r) {
     if (staged) {
@@ -54,8 +61,8 @@ __global__ void __launch_bounds__(kSpmvRows) mpk_step_kernel(DevCSR A, double* _
       }
     } else {
       for (int k = k0; k < k1; ++k) {
-        const double a = __ldg(A.val + k);
-        const int c = __ldg(A.colind + k);
+        const double a = __ldg(oval + k);
+        const int c = __ldg(O.colind + k);
         tp = fma(a, __ldg(pj + c), tp);
         tr = fma(a, __ldg(rj + c), tr);
       }
@@ -64,22 +71,22 @@ __global__ void __launch_bounds__(kSpmvRows) mpk_step_kernel(DevCSR A, double* _
     if (staged) {
       for (int k = k0 - base; k < k1 - base; ++k) tp = fma(sval[k], __ldg(pj + scol[k]), tp);
     } else {
-      for (int k = k0; k < k1; ++k) tp = fma(__ldg(A.val + k), __ldg(pj + __ldg(A.colind + k)), tp);
+      for (int k = k0; k < k1; ++k) tp = fma(__ldg(oval + k), __ldg(pj + __ldg(O.colind + k)), tp);
     }
   }
-  // rho_{j+1} = ((A - theta_j) rho_j - sigma_{j-1} rho_{j-1}) / gamma_j
-  if (do_p) {
-    if (use_theta) tp = fma(-theta, pj[row], tp);
-    if (use_sigma && j >= 1) tp = fma(-sigma_prev, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
-    if (use_gamma) tp *= gamma_inv;
-    Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+  // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
+  if (sig != 0.0 && j >= 1) {
+    tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
+    if (do_r) tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
   }
-  if (do_r) {
-    if (use_theta) tr = fma(-theta, rj[row], tr);
-    if (use_sigma && j >= 1) tr = fma(-sigma_prev, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
-    if (use_gamma) tr *= gamma_inv;
-    Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
-  }
+  if (do_p) Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+  if (do_r) Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
+}
+
+__global__ void shift_scale_kernel(const double* __restrict__ src, int64_t n, double theta, double scale,
+                                   double* __restrict__ dst) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = (src[i] - theta) * scale;
 }
 
 // x += Y x', r = Y r', p = Y p' over the first w columns (eq. coords).
@@ -122,14 +129,16 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
 
 }  // namespace
 
-cudaError_t launch_mpk_step(const DevCSR& A, double* Y, int64_t ldY, int j, int do_p, int do_r, double theta,
-                            double sigma_prev, double gamma, cudaStream_t s) {
-  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
-  const int use_theta = theta != 0.0;
-  const int use_sigma = sigma_prev != 0.0;
-  const int use_gamma = gamma != 1.0;
-  mpk_step_kernel<<<g, kSpmvRows, 0, s>>>(A, Y, ldY, j, do_p, do_r, theta, sigma_prev, 1.0 / gamma, use_theta,
-                                          use_sigma, use_gamma);
+cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
+                                  int do_r, cudaStream_t s) {
+  const int g = (int)((O.n + kSpmvRows - 1) / kSpmvRows);
+  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, double scale, double* dst,
+                               cudaStream_t s) {
+  shift_scale_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(src, n, theta, scale, dst);
   return cudaGetLastError();
 }
 
