@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--method", default="adaptive", choices=["adaptive", "classical"],
+                    help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -235,8 +237,11 @@ def our_arm(args):
     bd = torch.from_numpy(b).cuda()
     xd = torch.zeros(n, dtype=torch.float64, device="cuda")
     max_it = 20000
-    o = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
-                       max_iters=max_it, timing=True)
+    if args.method == "classical":
+        o = P.make_options(method="classical", eps_target=1e-12, max_iters=max_it, timing=True)
+    else:
+        o = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
+                           max_iters=max_it, timing=True)
 
     def solve_once():
         xd.zero_()
@@ -292,8 +297,8 @@ def our_arm(args):
     # end to end: host buffers through ascg_solve_host, copies inside the timed region
     bh = torch.from_numpy(b).pin_memory()
     xh = torch.zeros(n, dtype=torch.float64).pin_memory()
-    o_e2e = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
-                           max_iters=max_it)
+    o_e2e = P.ascg_options.from_buffer_copy(o)   # same solve, library timing off
+    o_e2e.flags = 0
     P.ascg_solve_host(op, bh, xh, o_e2e, stream=stream)
     if world > 1:
         dist.barrier()
@@ -352,7 +357,11 @@ def our_arm(args):
             "metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_job / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "parallelism": "replicas only" if world > 1 else "single GPU",
+            "config": {"workload": WORKLOAD if args.method == "adaptive" else WORKLOAD.replace(
+                           "adaptive s-step CG, Chebyshev basis on closed-form bounds, s_max=16, s0=f=16, c=1",
+                           "classical CG (Alg. 1)"),
+                       "method": args.method,
+                       "parallelism": "replicas only" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2: A 183 MB, basis 554 MB, vectors 16.8 MB each"},
             "status_ok": ok,
             "iters_per_solve": iters / args.steps,
