@@ -114,19 +114,82 @@ struct Workspace {
 struct ascg_op_s {
   int64_t n = 0, nnz = 0;
   int device = 0;
-  int32_t* rowptr = nullptr;
-  int32_t* colind = nullptr;
-  double* val = nullptr;
-  // A = D + O for the matrix powers kernel
-  int64_t nnz_off = 0;
-  int32_t* o_rowptr = nullptr;
-  int32_t* o_colind = nullptr;
+  // A in sliced ELL form (SpMV, residual, classical CG)
+  int64_t* a_ptr = nullptr;
+  int32_t* a_col = nullptr;
+  double* a_val = nullptr;
+  // A = D + O for the matrix powers kernel, O in sliced ELL form
+  int64_t o_len = 0;
+  int64_t* o_ptr = nullptr;
+  int32_t* o_col = nullptr;
   double* o_val = nullptr;
   double* diag = nullptr;
   Workspace ws;
-  DevCSR csr() const { return DevCSR{n, nnz, rowptr, colind, val}; }
-  DevSplit split() const { return DevSplit{n, nnz_off, o_rowptr, o_colind, o_val, diag}; }
+  DevSell sell() const { return DevSell{n, a_ptr, a_col, a_val}; }
+  DevSplit split() const { return DevSplit{DevSell{n, o_ptr, o_col, o_val}, o_len, diag}; }
+  void free_device() {
+    dev_free(a_ptr); dev_free(a_col); dev_free(a_val);
+    dev_free(o_ptr); dev_free(o_col); dev_free(o_val); dev_free(diag);
+  }
 };
+
+namespace {
+
+// Host construction of a sliced ELL matrix (see DevSell) from CSR. With
+// drop_diag, diagonal entries are summed into diag[] and left out.
+struct HostSell {
+  std::vector<int64_t> ptr;
+  std::vector<int32_t> col;
+  std::vector<double> val;
+};
+
+HostSell build_sell(int64_t n, const int64_t* rp, const int32_t* ci, const double* va, bool drop_diag,
+                    std::vector<double>* diag) {
+  const int64_t nsl = (n + kSlice - 1) / kSlice;
+  HostSell h;
+  h.ptr.assign(nsl + 1, 0);
+  for (int64_t s = 0; s < nsl; ++s) {
+    int64_t width = 0;
+    for (int64_t i = s * kSlice; i < std::min<int64_t>(n, (s + 1) * kSlice); ++i) {
+      int64_t len = 0;
+      for (int64_t k = rp[i]; k < rp[i + 1]; ++k) len += !(drop_diag && ci[k] == i);
+      width = std::max(width, len);
+    }
+    h.ptr[s + 1] = h.ptr[s] + width * kSlice;
+  }
+  h.col.assign(h.ptr[nsl], 0);
+  h.val.assign(h.ptr[nsl], 0.0);
+  for (int64_t s = 0; s < nsl; ++s) {
+    const int64_t width = (h.ptr[s + 1] - h.ptr[s]) / kSlice;
+    for (int l = 0; l < kSlice; ++l) {
+      const int64_t i = s * kSlice + l;
+      int64_t j = 0;
+      if (i < n) {
+        for (int64_t k = rp[i]; k < rp[i + 1]; ++k) {
+          if (drop_diag && ci[k] == i) {
+            (*diag)[i] += va[k];
+            continue;
+          }
+          h.col[h.ptr[s] + j * kSlice + l] = ci[k];
+          h.val[h.ptr[s] + j * kSlice + l] = va[k];
+          ++j;
+        }
+      }
+      for (; j < width; ++j)  // padding: value 0, a valid column (the row itself)
+        h.col[h.ptr[s] + j * kSlice + l] = (int32_t)std::min<int64_t>(i, n - 1);
+    }
+  }
+  return h;
+}
+
+template <class T>
+ascg_status upload(T** dst, const std::vector<T>& src) {
+  ASCG_TRY(dev_alloc(dst, src.size()));
+  if (!src.empty()) ASCG_CUDA(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return ASCG_OK;
+}
+
+}  // namespace
 
 namespace {
 
@@ -173,8 +236,8 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
   }
   if (wcols > 2 && !w.dtils) {
     ASCG_TRY(dev_alloc(&w.dtils, (size_t)kMaxS * n));
-    ASCG_TRY(dev_alloc(&w.oscaled[0], (size_t)op->nnz_off));
-    ASCG_TRY(dev_alloc(&w.oscaled[1], (size_t)op->nnz_off));
+    ASCG_TRY(dev_alloc(&w.oscaled[0], (size_t)op->o_len));
+    ASCG_TRY(dev_alloc(&w.oscaled[1], (size_t)op->o_len));
   }
   if (w.res_cap < res_cap) {
     dev_free(w.res_hist); dev_free(w.ab_hist);
@@ -229,7 +292,7 @@ void basis_params(const ascg_options& o, double* th, double* sg, double* gm) {
 // Runs classical CG iterations (Alg. 1) on the device until the CG state says
 // done. x, r, p, q are device vectors. Returns the iterations done by this call.
 // Per-step operators of the matrix powers recurrence with theta, sigma and gamma
-// folded in (see StepOp). dtils: n x s doubles; oscaled: two arrays of nnz_off
+// folded in (see StepOp). dtils: n x s doubles; oscaled: two arrays of o_len
 // doubles (used when gamma != 1; at most two distinct gamma values, which covers
 // the monomial, Chebyshev and Newton bases).
 ascg_status prepare_steps(ascg_op op, const double* th, const double* sg, const double* gm, int s, double* dtils,
@@ -249,7 +312,7 @@ ascg_status prepare_steps(ascg_op op, const double* th, const double* sg, const 
         if (ng == 2) return fail(ASCG_ERR_INVALID, "at most two distinct gamma != 1 are supported");
         slot = ng++;
         gam_of[slot] = gm[j];
-        ASCG_CUDA(launch_shift_scale(op->o_val, op->nnz_off, 0.0, inv, oscaled[slot], st));
+        ASCG_CUDA(launch_shift_scale(op->o_val, op->o_len, 0.0, inv, oscaled[slot], st));
         ++*launches;
       }
       ov = oscaled[slot];
@@ -273,7 +336,7 @@ ascg_status run_classical(ascg_op op, double* x, double* r, double* p, double ep
                           int max_iters, int iter0, cudaStream_t s, ascg_result* res, bool timing) {
   Workspace& w = op->ws;
   const int64_t n = op->n;
-  const DevCSR A = op->csr();
+  const DevSell A = op->sell();
   ASCG_CUDA(launch_dot(r, r, n, &w.cgs->rr, w.partials, w.counter, s));
   ASCG_CUDA(launch_cg_init(w.cgs, eps_star, bnorm, max_iters, iter0, w.res_hist, w.res_cap, s));
   res->launches += 2;
@@ -308,7 +371,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
                          cudaStream_t s) {
   Workspace& w = op->ws;
   const int64_t n = op->n;
-  const DevCSR A = op->csr();
+  const DevSell A = op->sell();
   const bool sstep = o.method != ASCG_CLASSICAL;
   const int wmax = sstep ? 2 * o.s_max + 1 : 2;
   ASCG_TRY(ensure(op, wmax, o.max_iters + 2));
@@ -580,7 +643,6 @@ ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, co
     hva = va.data();
   }
   if (hrp[0] != 0 || hrp[n] != nnz) return fail(ASCG_ERR_INVALID, "rowptr[0] must be 0 and rowptr[n] = nnz");
-  std::vector<int32_t> rp32(n + 1);
   for (int64_t i = 0; i < n; ++i)  // all of rowptr first, so rows below index only [0, nnz)
     if (hrp[i + 1] < hrp[i] || hrp[i + 1] > nnz) return fail(ASCG_ERR_INVALID, "rowptr is not non-decreasing");
   for (int64_t i = 0; i < n; ++i) {
@@ -595,59 +657,24 @@ ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, co
       }
     }
     if (!diag) return fail(ASCG_ERR_NOT_SPD, "a row has no diagonal entry");
-    rp32[i] = (int32_t)hrp[i];
   }
-  rp32[n] = (int32_t)hrp[n];
-  // A = D + O: diagonal and off-diagonal parts for the matrix powers kernel
-  std::vector<int32_t> orp(n + 1);
-  std::vector<int32_t> oci;
-  std::vector<double> ova, dg(n, 0.0);
-  oci.reserve(nnz);
-  ova.reserve(nnz);
-  for (int64_t i = 0; i < n; ++i) {
-    orp[i] = (int32_t)oci.size();
-    for (int64_t k = hrp[i]; k < hrp[i + 1]; ++k) {
-      if (hci[k] == i) {
-        dg[i] += hva[k];
-      } else {
-        oci.push_back(hci[k]);
-        ova.push_back(hva[k]);
-      }
-    }
-  }
-  orp[n] = (int32_t)oci.size();
+  std::vector<double> dg(n, 0.0);
+  const HostSell ha = build_sell(n, hrp, hci, hva, false, nullptr);
+  const HostSell ho = build_sell(n, hrp, hci, hva, true, &dg);
   ascg_op op = new ascg_op_s();
-  op->nnz_off = (int64_t)oci.size();
   op->n = n;
   op->nnz = nnz;
+  op->o_len = (int64_t)ho.val.size();
   cudaGetDevice(&op->device);
-  ascg_status st = dev_alloc(&op->rowptr, n + 1);
-  if (st == ASCG_OK) st = dev_alloc(&op->colind, (size_t)nnz);
-  if (st == ASCG_OK) st = dev_alloc(&op->val, (size_t)nnz);
-  if (st == ASCG_OK) st = dev_alloc(&op->o_rowptr, n + 1);
-  if (st == ASCG_OK) st = dev_alloc(&op->o_colind, (size_t)op->nnz_off);
-  if (st == ASCG_OK) st = dev_alloc(&op->o_val, (size_t)op->nnz_off);
-  if (st == ASCG_OK) st = dev_alloc(&op->diag, (size_t)n);
-  if (st == ASCG_OK) {
-    cudaError_t e = cudaMemcpy(op->rowptr, rp32.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(op->colind, hci, sizeof(int32_t) * nnz, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && nnz) e = cudaMemcpy(op->val, hva, sizeof(double) * nnz, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(op->o_rowptr, orp.data(), sizeof(int32_t) * (n + 1), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && op->nnz_off)
-      e = cudaMemcpy(op->o_colind, oci.data(), sizeof(int32_t) * op->nnz_off, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && op->nnz_off)
-      e = cudaMemcpy(op->o_val, ova.data(), sizeof(double) * op->nnz_off, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(op->diag, dg.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) st = fail(ASCG_ERR_CUDA, std::string("copy CSR: ") + cudaGetErrorString(e));
-  }
+  ascg_status st = upload(&op->a_ptr, ha.ptr);
+  if (st == ASCG_OK) st = upload(&op->a_col, ha.col);
+  if (st == ASCG_OK) st = upload(&op->a_val, ha.val);
+  if (st == ASCG_OK) st = upload(&op->o_ptr, ho.ptr);
+  if (st == ASCG_OK) st = upload(&op->o_col, ho.col);
+  if (st == ASCG_OK) st = upload(&op->o_val, ho.val);
+  if (st == ASCG_OK) st = upload(&op->diag, dg);
   if (st != ASCG_OK) {
-    dev_free(op->rowptr);
-    dev_free(op->colind);
-    dev_free(op->val);
-    dev_free(op->o_rowptr);
-    dev_free(op->o_colind);
-    dev_free(op->o_val);
-    dev_free(op->diag);
+    op->free_device();
     delete op;
     return st;
   }
@@ -658,13 +685,7 @@ ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, co
 ascg_status ascg_op_destroy(ascg_op op) {
   if (!op) return ASCG_OK;
   op->ws.release();
-  dev_free(op->rowptr);
-  dev_free(op->colind);
-  dev_free(op->val);
-  dev_free(op->o_rowptr);
-  dev_free(op->o_colind);
-  dev_free(op->o_val);
-  dev_free(op->diag);
+  op->free_device();
   delete op;
   return ASCG_OK;
 }
@@ -734,7 +755,7 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
 ascg_status ascg_spmv(ascg_op op, const double* x, double* y, void* cuda_stream) {
   g_err.clear();
   if (!op || !x || !y) return fail(ASCG_ERR_INVALID, "NULL argument");
-  ASCG_CUDA(launch_spmv(op->csr(), x, y, (cudaStream_t)cuda_stream));
+  ASCG_CUDA(launch_spmv(op->sell(), x, y, (cudaStream_t)cuda_stream));
   return ASCG_OK;
 }
 
@@ -748,8 +769,8 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
   double* dtils = nullptr;
   double* osc[2] = {nullptr, nullptr};
   ascg_status rs = dev_alloc(&dtils, (size_t)s * op->n);
-  if (rs == ASCG_OK) rs = dev_alloc(&osc[0], (size_t)op->nnz_off);
-  if (rs == ASCG_OK) rs = dev_alloc(&osc[1], (size_t)op->nnz_off);
+  if (rs == ASCG_OK) rs = dev_alloc(&osc[0], (size_t)op->o_len);
+  if (rs == ASCG_OK) rs = dev_alloc(&osc[1], (size_t)op->o_len);
   StepOp steps[kMaxS];
   int nl = 0;
   if (rs == ASCG_OK) rs = prepare_steps(op, theta, sigma, gamma, s, dtils, osc, steps, st, &nl);

@@ -19,19 +19,23 @@ constexpr int kMaxW = ASCG_MAX_W;                 // 33
 constexpr int kMaxPairs = kMaxW * (kMaxW + 1) / 2;  // 561
 constexpr double kEps = 1.1102230246251565e-16;   // 2^-53
 
-// CSR matrix on the device. rowptr is int32 (nnz < 2^31).
-struct DevCSR {
+// Sparse matrix on the device in sliced ELL form, slices of 32 rows (one warp
+// per slice). Entry j of row 32 s + l sits at val[ptr[s] + 32 j + l]; a
+// slice's width is its longest row, and shorter rows are padded with value 0
+// and their own column index. Every load of a warp is then one contiguous
+// 256-byte (values) or 128-byte (columns) segment. No shared-memory staging
+// is needed, and the padding costs no more than the divergence that a
+// thread-per-row CSR loop pays for the warp's longest row.
+constexpr int kSlice = 32;
+struct DevSell {
   int64_t n;
-  int64_t nnz;
-  const int32_t* rowptr;
-  const int32_t* colind;
+  const int64_t* ptr;   // ceil(n/32) + 1 element offsets
+  const int32_t* col;
   const double* val;
 };
 
-// Rows handled by one CTA of the SpMV-based kernels, and the largest nonzero
-// count of such a row block that is staged through shared memory.
+// Rows (threads) per CTA of the SpMV-based kernels.
 constexpr int kSpmvRows = 256;
-constexpr int kSpmvTileNnz = 2560;
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -53,9 +57,9 @@ inline int grid_for(int64_t n, int threads, int cap) {
 // ---------------------------------------------------------------------------
 
 // y = A x
-cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s);
+cudaError_t launch_spmv(const DevSell& A, const double* x, double* y, cudaStream_t s);
 // r = b - A x; also writes p = r when p != nullptr
-cudaError_t launch_residual(const DevCSR& A, const double* b, const double* x, double* r,
+cudaError_t launch_residual(const DevSell& A, const double* b, const double* x, double* r,
                             double* p, cudaStream_t s);
 // out[0] = sum_i u_i v_i over n, deterministic two-stage reduction.
 // partials: device double[kRedBlocks], counter: device unsigned (zero on entry, left zero).
@@ -64,13 +68,10 @@ cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out,
                        unsigned* counter, cudaStream_t s);
 
 // A split as D + O for the matrix powers kernel: O is the off-diagonal part in
-// CSR form (diagonal removed), D the diagonal.
+// sliced ELL form (diagonal removed), D the diagonal.
 struct DevSplit {
-  int64_t n;
-  int64_t nnz_off;
-  const int32_t* rowptr;
-  const int32_t* colind;
-  const double* val;
+  DevSell O;
+  int64_t o_len;        // elements of O's value array (padding included)
   const double* diag;
 };
 
@@ -81,7 +82,7 @@ struct DevSplit {
 // One multiply for the diagonal, one FMA per off-diagonal nonzero and one FMA for
 // the sigma term per row: nnz_row + 1 FP64 instructions instead of nnz_row + 3.
 struct StepOp {
-  const double* oval;   // values of Ot_j (O's pattern)
+  const double* oval;   // values of Ot_j (O's sliced ELL layout)
   const double* dtil;   // Dt_j, n values
   double sig;           // sig_j (0 for j = 0)
 };
@@ -161,7 +162,7 @@ struct CGState {
   int pad_;
 };
 // q = A p, state.pAp; the last CTA sets alpha.
-cudaError_t launch_cg_spmv_dot(const DevCSR& A, const double* p, double* q, CGState* st,
+cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st,
                                double* partials, unsigned* counter, cudaStream_t s);
 // x += alpha p, r -= alpha q, rr_new; the last CTA sets beta, records histories,
 // tests convergence.

@@ -1,11 +1,9 @@
-// CSR SpMV, residual, dot products and classical CG (Alg. 1).
+// SpMV, residual, dot products and classical CG (Alg. 1).
 //
-// SpMV layout: one CTA per block of kSpmvRows consecutive rows, one thread per
-// row. The block's nonzeros are staged through shared memory with coalesced
-// loads when they fit (kSpmvTileNnz). Each thread then sums its row with
-// sequential FMAs in stored column order, which is the fewest FP64
-// instructions per nonzero. Rows whose block does not fit read from global
-// memory directly.
+// SpMV layout: sliced ELL (see DevSell), one thread per row, one warp per
+// 32-row slice. Each thread sums its row with sequential FMAs in stored column
+// order, which is the fewest FP64 instructions per nonzero. Every load of a
+// warp is one contiguous segment.
 //
 // Reductions are deterministic. Each CTA writes a partial sum; the last CTA
 // to finish (by an atomic ticket) adds the partials in index order. There are
@@ -16,44 +14,17 @@ namespace ascg {
 
 namespace {
 
-struct RowTile {
-  int base;     // rowptr of the first row
-  bool staged;  // nonzeros are in shared memory
-};
-
-// Loads rowptr[r0..r1] and, if they fit, the nonzeros of rows [r0, r1).
-__device__ __forceinline__ RowTile stage_rows(const DevCSR& A, int64_t r0, int64_t r1, int* srow,
-                                              double* sval, int* scol) {
-  const int nr = (int)(r1 - r0);
-  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = A.rowptr[r0 + i];
-  __syncthreads();
-  RowTile t;
-  t.base = srow[0];
-  const int cnt = srow[nr] - t.base;
-  t.staged = cnt <= kSpmvTileNnz;
-  if (t.staged) {
-    const double* gv = A.val + t.base;
-    const int* gc = A.colind + t.base;
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-      sval[k] = __ldg(gv + k);
-      scol[k] = __ldg(gc + k);
-    }
-  }
-  __syncthreads();
+// sum_j a_ij x_j for row i (i < A.n) in stored order, starting from 0.
+__device__ __forceinline__ double sell_row(const DevSell& A, int64_t i, const double* __restrict__ x) {
+  const int64_t s = i >> 5;
+  const int l = (int)(i & 31);
+  const int64_t b = A.ptr[s];
+  const int width = (int)((A.ptr[s + 1] - b) >> 5);
+  const double* v = A.val + b + l;
+  const int32_t* c = A.col + b + l;
+  double t = 0.0;
+  for (int j = 0; j < width; ++j) t = fma(__ldg(v + kSlice * j), __ldg(x + __ldg(c + kSlice * j)), t);
   return t;
-}
-
-__device__ __forceinline__ double row_times(const DevCSR& A, const RowTile& t, const int* srow,
-                                            const double* sval, const int* scol, int lr,
-                                            const double* __restrict__ x) {
-  double s = 0.0;
-  const int k0 = srow[lr], k1 = srow[lr + 1];
-  if (t.staged) {
-    for (int k = k0 - t.base; k < k1 - t.base; ++k) s = fma(sval[k], __ldg(x + scol[k]), s);
-  } else {
-    for (int k = k0; k < k1; ++k) s = fma(__ldg(A.val + k), __ldg(x + __ldg(A.colind + k)), s);
-  }
-  return s;
 }
 
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -95,32 +66,20 @@ __device__ __forceinline__ double sum_partials(const double* partials, int np, d
 
 // ---------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kSpmvRows) spmv_kernel(DevCSR A, const double* __restrict__ x,
+__global__ void __launch_bounds__(kSpmvRows) spmv_kernel(DevSell A, const double* __restrict__ x,
                                                          double* __restrict__ y) {
-  __shared__ int srow[kSpmvRows + 1];
-  __shared__ double sval[kSpmvTileNnz];
-  __shared__ int scol[kSpmvTileNnz];
-  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
-  const int64_t r1 = min(r0 + kSpmvRows, A.n);
-  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
-  const int lr = threadIdx.x;
-  if (r0 + lr < r1) y[r0 + lr] = row_times(A, t, srow, sval, scol, lr, x);
+  const int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
+  if (i < A.n) y[i] = sell_row(A, i, x);
 }
 
-__global__ void __launch_bounds__(kSpmvRows) residual_kernel(DevCSR A, const double* __restrict__ b,
+__global__ void __launch_bounds__(kSpmvRows) residual_kernel(DevSell A, const double* __restrict__ b,
                                                              const double* __restrict__ x,
                                                              double* __restrict__ r, double* __restrict__ p) {
-  __shared__ int srow[kSpmvRows + 1];
-  __shared__ double sval[kSpmvTileNnz];
-  __shared__ int scol[kSpmvTileNnz];
-  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
-  const int64_t r1 = min(r0 + kSpmvRows, A.n);
-  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
-  const int lr = threadIdx.x;
-  if (r0 + lr < r1) {
-    const double v = b[r0 + lr] - row_times(A, t, srow, sval, scol, lr, x);
-    r[r0 + lr] = v;
-    if (p) p[r0 + lr] = v;
+  const int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
+  if (i < A.n) {
+    const double v = b[i] - sell_row(A, i, x);
+    r[i] = v;
+    if (p) p[i] = v;
   }
 }
 
@@ -143,26 +102,20 @@ __global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ u, 
 
 // --- classical CG -----------------------------------------------------------
 
-__global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevCSR A, const double* __restrict__ p,
+__global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const double* __restrict__ p,
                                                                 double* __restrict__ q, CGState* st,
                                                                 double* partials, unsigned* counter) {
-  __shared__ int srow[kSpmvRows + 1];
-  __shared__ double sval[kSpmvTileNnz];
-  __shared__ int scol[kSpmvTileNnz];
   __shared__ double red[32];
   __shared__ int flag;
   const int done = st->done;  // uniform: written by an earlier kernel
   if (blockIdx.x == 0 && threadIdx.x == 0) st->active = !done;  // read by the next two kernels
   if (done) return;
-  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
-  const int64_t r1 = min(r0 + kSpmvRows, A.n);
-  const RowTile t = stage_rows(A, r0, r1, srow, sval, scol);
-  const int lr = threadIdx.x;
+  const int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   double part = 0.0;
-  if (r0 + lr < r1) {
-    const double v = row_times(A, t, srow, sval, scol, lr, p);
-    q[r0 + lr] = v;
-    part = p[r0 + lr] * v;
+  if (i < A.n) {
+    const double v = sell_row(A, i, p);
+    q[i] = v;
+    part = p[i] * v;
   }
   part = block_sum(part, red);
   if (last_block(part, partials, counter, &flag)) {
@@ -241,13 +194,13 @@ __global__ void cg_init_kernel(CGState* st, double eps_star, double bnorm, int m
 
 }  // namespace
 
-cudaError_t launch_spmv(const DevCSR& A, const double* x, double* y, cudaStream_t s) {
+cudaError_t launch_spmv(const DevSell& A, const double* x, double* y, cudaStream_t s) {
   const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
   spmv_kernel<<<g, kSpmvRows, 0, s>>>(A, x, y);
   return cudaGetLastError();
 }
 
-cudaError_t launch_residual(const DevCSR& A, const double* b, const double* x, double* r, double* p,
+cudaError_t launch_residual(const DevSell& A, const double* b, const double* x, double* r, double* p,
                             cudaStream_t s) {
   const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
   residual_kernel<<<g, kSpmvRows, 0, s>>>(A, b, x, r, p);
@@ -260,7 +213,7 @@ cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out,
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_spmv_dot(const DevCSR& A, const double* p, double* q, CGState* st, double* partials,
+cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st, double* partials,
                                unsigned* counter, cudaStream_t s) {
   const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
   cg_spmv_dot_kernel<<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);

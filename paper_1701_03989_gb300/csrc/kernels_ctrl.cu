@@ -90,15 +90,22 @@ __device__ __forceinline__ int sturm_det(const double* d, const double* e2, int 
   double pm2 = 1.0;
   double pm1 = d[0] - x;
   if (pm1 == 0.0) pm1 = -kTiny * kTiny;
-  int cnt = pm1 < 0.0;
+  int hprev = __double2hiint(pm1);
+  int cnt = (int)((unsigned)hprev >> 31);
   for (int k = 1; k < m; ++k) {
     const double t = e2[k - 1] * pm2;
     double p = fma(d[k] - x, pm1, -t);
-    if (p == 0.0) p = -copysign(fabs(pm1) * kTiny, pm1);
-    cnt += (p < 0.0) != (pm1 < 0.0);
+    int hp = __double2hiint(p);
+    // sign, zero and exponent tests on the bit pattern: integer pipe, not FP64
+    if (((hp & 0x7fffffff) | __double2loint(p)) == 0) {
+      p = -copysign(fabs(pm1) * kTiny, pm1);
+      hp = __double2hiint(p);
+    }
+    cnt += (int)((unsigned)(hp ^ hprev) >> 31);
     pm2 = pm1;
     pm1 = p;
-    if (fabs(pm1) < kTiny) {
+    hprev = hp;
+    if (((hp >> 20) & 0x7ff) < 767) {  // |p| < 2^-256
       pm1 *= kUp;
       pm2 *= kUp;
     }
@@ -110,19 +117,20 @@ __device__ __forceinline__ int sturm_det(const double* d, const double* e2, int 
 // (interleaved column order). Warp 0 reduces it to tridiagonal form by
 // Householder reflections, one lane per row. The tridiagonal is scaled to unit
 // norm. Warps 0-1 then bracket lambda_min and warps 2-3 bracket lambda_max, each
-// pair evaluating 64 Sturm counts per round for a fixed 10 rounds.
+// pair evaluating 64 Sturm counts per round for a fixed 9 rounds.
 // lambda_min first decides certification (is it below the floor
 // (2i+1) sqrt(n) eps lambda_max?). Then a geometric grid finds its magnitude,
-// and a linear grid refines it to ~2^-50 relative. lambda_max is refined
+// and a linear grid refines it to ~2^-48 relative. lambda_max is refined
 // linearly from [max d, Gershgorin bound].
-constexpr int kKappaRounds = 10;
+constexpr int kKappaRounds = 9;
 
 __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
   const int i = blockIdx.x + 1;
   const int m = 2 * i + 1;
   const int w = 2 * sbar + 1;
-  __shared__ double A[kMaxW][kMaxW + 1];
+  __shared__ double A[kMaxW][kMaxW];  // odd row stride: conflict-free column access
   __shared__ double v[32], wv[32];
+  __shared__ double part[4][32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
   __shared__ double lo_s[2], hi_s[2];
   __shared__ unsigned mask_s[4];
@@ -131,44 +139,49 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    for (int k = 0; k + 2 < m; ++k) {
-      const int len = m - k - 1;  // rows k+1 .. m-1, at most 32
-      const int row = k + 1 + lane;
-      const bool on = lane < len;
-      const double xi = on ? A[row][k] : 0.0;
-      const double s2 = warp_sum(xi * xi);
-      const double x0 = __shfl_sync(kFull, xi, 0);
-      double alpha = 0.0;
-      if (s2 > 0.0) {
-        alpha = -copysign(sqrt(s2), x0);
-        const double vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
-        const double vn2 = warp_sum(vi * vi);
-        const double beta = 2.0 / vn2;
-        v[lane] = vi;
-        __syncwarp();
-        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
-        if (on) {
-          int c = 0;
-          for (; c + 3 < len; c += 4) {
-            p0 = fma(A[row][k + 1 + c], v[c], p0);
-            p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
-            p2 = fma(A[row][k + 3 + c], v[c + 2], p2);
-            p3 = fma(A[row][k + 4 + c], v[c + 3], p3);
-          }
-          for (; c < len; ++c) p0 = fma(A[row][k + 1 + c], v[c], p0);
+  // Householder: every warp computes the scalars of step k redundantly (no
+  // extra latency, one warp per SM sub-partition); the matrix-vector product
+  // and the rank-2 update are split by columns across the four warps.
+  for (int k = 0; k + 2 < m; ++k) {
+    const int len = m - k - 1;  // rows k+1 .. m-1, at most 32
+    const int row = k + 1 + lane;
+    const bool on = lane < len;
+    const int c0 = (len * warp) >> 2, c1 = (len * (warp + 1)) >> 2;
+    const double xi = on ? A[row][k] : 0.0;
+    const double s2 = warp_sum(xi * xi);
+    const double x0 = __shfl_sync(kFull, xi, 0);
+    double alpha = 0.0;
+    if (s2 > 0.0) {
+      alpha = -copysign(sqrt(s2), x0);
+      const double vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
+      const double vn2 = warp_sum(vi * vi);
+      const double beta = 2.0 / vn2;
+      if (warp == 0) v[lane] = vi;
+      __syncthreads();
+      double p0 = 0.0, p1 = 0.0;
+      if (on) {
+        int c = c0;
+        for (; c + 1 < c1; c += 2) {
+          p0 = fma(A[row][k + 1 + c], v[c], p0);
+          p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
         }
-        const double pi = beta * ((p0 + p1) + (p2 + p3));
-        const double K = 0.5 * beta * warp_sum(vi * pi);
-        const double wi = pi - K * vi;
-        wv[lane] = wi;
-        __syncwarp();
-        if (on)
-          for (int c = 0; c < len; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
-        __syncwarp();
+        if (c < c1) p0 = fma(A[row][k + 1 + c], v[c], p0);
       }
-      if (lane == 0) e[k] = alpha;  // s2 == 0: the column is already zero
+      part[warp][lane] = p0 + p1;
+      __syncthreads();
+      const double pi = beta * ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]));
+      const double K = 0.5 * beta * warp_sum(vi * pi);
+      const double wi = pi - K * vi;
+      if (warp == 0) wv[lane] = wi;
+      __syncthreads();
+      if (on)
+        for (int c = c0; c < c1; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
+      __syncthreads();
     }
+    if (threadIdx.x == 0) e[k] = alpha;  // s2 == 0: the column is already zero
+  }
+  __syncthreads();
+  if (warp == 0) {
     for (int r = lane; r < m; r += 32) d[r] = A[r][r];
     if (lane == 0) e[m - 2] = A[m - 1][m - 2];
     __syncwarp();
@@ -270,43 +283,46 @@ __device__ __forceinline__ double bapply(const double* v, int t, int ss, const d
   return acc;
 }
 
-// sum_c a[c] v[c] for c < w with four interleaved accumulators (fixed order),
-// which cuts the dependent-FMA chain to a quarter.
-__device__ __forceinline__ double rowdot(const double* a, const double* v, int w) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 3 < w; c += 4) {
+// sum_c a[c] v[c] for c in [c0, c1) with two interleaved accumulators (fixed order).
+__device__ __forceinline__ double rowdot(const double* a, const double* v, int c0, int c1) {
+  double s0 = 0.0, s1 = 0.0;
+  int c = c0;
+  for (; c + 1 < c1; c += 2) {
     s0 = fma(a[c], v[c], s0);
     s1 = fma(a[c + 1], v[c + 1], s1);
-    s2 = fma(a[c + 2], v[c + 2], s2);
-    s3 = fma(a[c + 3], v[c + 3], s3);
   }
-  for (; c < w; ++c) s0 = fma(a[c], v[c], s0);
-  return (s0 + s1) + (s2 + s3);
+  if (c < c1) s0 = fma(a[c], v[c], s0);
+  return s0 + s1;
 }
 
-// Sum over the 64 threads of the CTA, identical in every thread, fixed order.
-__device__ __forceinline__ double sum64(double x, double* red) {
+// Sum over the 128 threads of the CTA, identical in every thread, fixed order.
+__device__ __forceinline__ double sum128(double x, double* red) {
   x = warp_sum(x);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   __syncthreads();
   if (lane == 0) red[warp] = x;
   __syncthreads();
-  return red[0] + red[1];
+  return (red[0] + red[1]) + (red[2] + red[3]);
 }
 
-__global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
-                                                  const double* __restrict__ sg_g, const double* __restrict__ gm_g,
-                                                  BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
-                                                  double* __restrict__ res_hist, int res_cap,
-                                                  double* __restrict__ ab_hist, int ab_cap) {
-  __shared__ double Gs[kMaxW][kMaxW + 1];
+// One CTA of 128 threads. Thread t works on coordinate row tr = t & 63 and on
+// half h = t >> 6 of that row's columns, so each w-long product G u is split
+// over four warps (one per SM sub-partition) and then combined in shared
+// memory in a fixed order.
+__global__ void __launch_bounds__(128) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
+                                                   const double* __restrict__ sg_g, const double* __restrict__ gm_g,
+                                                   BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
+                                                   double* __restrict__ res_hist, int res_cap,
+                                                   double* __restrict__ ab_hist, int ab_cap) {
+  __shared__ double Gs[kMaxW][kMaxW];  // odd row stride: conflict-free
   __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2];
+  __shared__ double half_sum[2][64];
   __shared__ double th[kMaxS], sg[kMaxS], gm[kMaxS];
-  __shared__ double red[2];
+  __shared__ double red[4];
   __shared__ int s_tilde;
   __shared__ double s_gamma;
   const int t = threadIdx.x;
+  const int tr = t & 63, hh = t >> 6;
   const int sbar = st->sbar;
   const int w = 2 * sbar + 1;
   const int adaptive = st->method == ASCG_ADAPTIVE;
@@ -350,7 +366,10 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
   const int ss = s_tilde;
   const int ws = 2 * ss + 1;
   const double gamma = s_gamma;
-  const bool row = t < ws;
+  const bool row = tr < ws;      // this thread's row exists
+  const bool own = row && hh == 0;  // and this thread owns the row's vector entries
+  const int cmid = (ws + 1) >> 1;
+  const int c0 = hh ? cmid : 0, c1 = hh ? ws : cmid;
   if (t < kMaxW + 2) {
     pc[t] = (t == 0) ? 1.0 : 0.0;  // p' = e_1 (column p_0)
     rc[t] = (t == 1) ? 1.0 : 0.0;  // r' = e_{s+2} (column r_0)
@@ -366,31 +385,34 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
   double relres = sqrt(fmax(rGr, 0.0)) / bnorm;
   for (int j = 1; j <= nsteps; ++j) {
     // alpha = (r'^T G r') / (p'^T G B p')
-    if (row) u[t] = bapply(pc, t, ss, th, sg, gm);
+    if (own) u[tr] = bapply(pc, tr, ss, th, sg, gm);
     __syncthreads();
-    const double gi = row ? rowdot(Gs[t], u, ws) : 0.0;
-    const double pGBp = sum64(row ? pc[t] * gi : 0.0, red);
+    if (row) half_sum[hh][tr] = rowdot(Gs[tr], u, c0, c1);
+    __syncthreads();
+    const double gi = own ? half_sum[0][tr] + half_sum[1][tr] : 0.0;
+    const double pGBp = sum128(own ? pc[tr] * gi : 0.0, red);
     if (!(pGBp > 0.0) || !isfinite(pGBp) || !(rGr > 0.0) || !isfinite(rGr)) {
       stop = ASCG_STOP_BREAKDOWN;
       break;
     }
     const double alpha = rGr / pGBp;
     // q' = alpha p'; x' += q'; r' -= B q'
-    __syncthreads();
-    if (row) {
-      const double q = alpha * pc[t];
-      u[t] = q;
-      xc[t] += q;
+    if (own) {
+      const double q = alpha * pc[tr];
+      u[tr] = q;
+      xc[tr] += q;
     }
     __syncthreads();
-    if (row) rn[t] = rc[t] - bapply(u, t, ss, th, sg, gm);
+    if (own) rn[tr] = rc[tr] - bapply(u, tr, ss, th, sg, gm);
     __syncthreads();
-    const double g2 = row ? rowdot(Gs[t], rn, ws) : 0.0;
-    const double rGr_new = sum64(row ? rn[t] * g2 : 0.0, red);
+    if (row) half_sum[hh][tr] = rowdot(Gs[tr], rn, c0, c1);
+    __syncthreads();
+    const double g2 = own ? half_sum[0][tr] + half_sum[1][tr] : 0.0;
+    const double rGr_new = sum128(own ? rn[tr] * g2 : 0.0, red);
     const double beta = rGr_new / rGr;
-    if (row) {
-      pc[t] = fma(beta, pc[t], rn[t]);  // p' = r'_new + beta p'
-      rc[t] = rn[t];
+    if (own) {
+      pc[tr] = fma(beta, pc[tr], rn[tr]);  // p' = r'_new + beta p'
+      rc[tr] = rn[tr];
     }
     rGr = rGr_new;
     steps = j;
@@ -515,7 +537,7 @@ cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t
 cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
                         BlockState* st, double* coords, double* hist, double* res_hist, int res_cap,
                         double* ab_hist, int ab_cap, cudaStream_t s) {
-  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
+  ctrl_kernel<<<1, 128, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
   return cudaGetLastError();
 }
 

@@ -5,8 +5,9 @@
 // Then every i-step sub-basis Y_{k,i} is the first 2i+1 columns.
 //
 // One matrix powers step j forms column 2(j+1) of P and column 2(j+1)+1 of R
-// in the same pass over A. The CSR row block is staged once in shared memory
-// and applied to both vectors, so A is read s times per block, not 2s-1.
+// in the same pass over A. Each value and column index of O (sliced ELL, one
+// warp per 32-row slice, coalesced) is loaded once and applied to both vectors,
+// so A is read s times per block, not 2s-1.
 // The GPU has no room to keep A on chip across steps for the large
 // workloads. This step is FP64-bound on GB300, so re-reading A costs no time.
 //
@@ -20,67 +21,41 @@ namespace ascg {
 
 namespace {
 
-__global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSplit O, const double* __restrict__ oval,
+__global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
                                                                    const double* __restrict__ dtil, double sig,
                                                                    double* __restrict__ Y, int64_t ldY, int j,
                                                                    int do_p, int do_r) {
-  __shared__ int srow[kSpmvRows + 1];
-  __shared__ double sval[kSpmvTileNnz];
-  __shared__ int scol[kSpmvTileNnz];
-  const int64_t r0 = (int64_t)blockIdx.x * kSpmvRows;
-  const int64_t r1 = min(r0 + kSpmvRows, O.n);
-  const int nr = (int)(r1 - r0);
-  for (int i = threadIdx.x; i <= nr; i += blockDim.x) srow[i] = O.rowptr[r0 + i];
-  __syncthreads();
-  const int base = srow[0];
-  const int cnt = srow[nr] - base;
-  const bool staged = cnt <= kSpmvTileNnz;
-  if (staged) {
-    for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
-      sval[k] = __ldg(oval + base + k);
-      scol[k] = __ldg(O.colind + base + k);
-    }
-  }
-  __syncthreads();
-  const int lr = threadIdx.x;
-  if (lr >= nr) return;
-  const int64_t row = r0 + lr;
+  const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
+  if (row >= O.n) return;
   const double* pj = Y + (int64_t)(2 * j) * ldY;
   const double* rj = Y + (int64_t)(2 * j + 1) * ldY;
+  const int64_t sl = row >> 5;
+  const int l = (int)(row & 31);
+  const int64_t b = O.ptr[sl];
+  const int width = (int)((O.ptr[sl + 1] - b) >> 5);
+  const double* v = oval + b + l;
+  const int32_t* c = O.col + b + l;
   const double dt = dtil[row];
   double tp = dt * pj[row];
-  double tr = do_r ? dt * rj[row] : 0.0;
-  const int k0 = srow[lr], k1 = srow[lr + 1];
   if (do_r) {
-    if (staged) {
-      for (int k = k0 - base; k < k1 - base; ++k) {
-        const double a = sval[k];
-        const int c = scol[k];
-        tp = fma(a, __ldg(pj + c), tp);
-        tr = fma(a, __ldg(rj + c), tr);
-      }
-    } else {
-      for (int k = k0; k < k1; ++k) {
-        const double a = __ldg(oval + k);
-        const int c = __ldg(O.colind + k);
-        tp = fma(a, __ldg(pj + c), tp);
-        tr = fma(a, __ldg(rj + c), tr);
-      }
+    double tr = dt * rj[row];
+    for (int k = 0; k < width; ++k) {
+      const double a = __ldg(v + kSlice * k);
+      const int cc = __ldg(c + kSlice * k);
+      tp = fma(a, __ldg(pj + cc), tp);
+      tr = fma(a, __ldg(rj + cc), tr);
     }
+    // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
+    if (sig != 0.0 && j >= 1) {
+      tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
+      tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
+    }
+    Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
   } else {
-    if (staged) {
-      for (int k = k0 - base; k < k1 - base; ++k) tp = fma(sval[k], __ldg(pj + scol[k]), tp);
-    } else {
-      for (int k = k0; k < k1; ++k) tp = fma(__ldg(oval + k), __ldg(pj + __ldg(O.colind + k)), tp);
-    }
-  }
-  // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
-  if (sig != 0.0 && j >= 1) {
-    tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
-    if (do_r) tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
+    for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
+    if (sig != 0.0 && j >= 1) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
   }
   if (do_p) Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
-  if (do_r) Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
 }
 
 __global__ void shift_scale_kernel(const double* __restrict__ src, int64_t n, double theta, double scale,
@@ -131,8 +106,8 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
 
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
                                   int do_r, cudaStream_t s) {
-  const int g = (int)((O.n + kSpmvRows - 1) / kSpmvRows);
-  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r);
+  const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
+  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r);
   return cudaGetLastError();
 }
 
