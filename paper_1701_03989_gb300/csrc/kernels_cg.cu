@@ -102,6 +102,9 @@ __global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ u, 
 
 // --- classical CG -----------------------------------------------------------
 
+// Grid-stride over rows with a bounded grid: every CTA ends in one block
+// reduction and one atomic ticket, so few CTAs keep that overhead small. Each
+// warp-wide FP64 add costs a full FP64 issue slot, however few lanes need it.
 __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const double* __restrict__ p,
                                                                 double* __restrict__ q, CGState* st,
                                                                 double* partials, unsigned* counter) {
@@ -110,12 +113,11 @@ __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const
   const int done = st->done;  // uniform: written by an earlier kernel
   if (blockIdx.x == 0 && threadIdx.x == 0) st->active = !done;  // read by the next two kernels
   if (done) return;
-  const int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   double part = 0.0;
-  if (i < A.n) {
+  for (int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * kSpmvRows) {
     const double v = sell_row(A, i, p);
     q[i] = v;
-    part = p[i] * v;
+    part = fma(p[i], v, part);
   }
   part = block_sum(part, red);
   if (last_block(part, partials, counter, &flag)) {
@@ -215,7 +217,7 @@ cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out,
 
 cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st, double* partials,
                                unsigned* counter, cudaStream_t s) {
-  const int g = (int)((A.n + kSpmvRows - 1) / kSpmvRows);
+  const int g = grid_for(A.n, kSpmvRows, 152 * 8);
   cg_spmv_dot_kernel<<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
   return cudaGetLastError();
 }

@@ -118,10 +118,10 @@ __device__ __forceinline__ int sturm_det(const double* d, const double* e2, int 
 // Householder reflections, one lane per row. The tridiagonal is scaled to unit
 // norm. Warps 0-1 then bracket lambda_min and warps 2-3 bracket lambda_max, each
 // pair evaluating 64 Sturm counts per round for a fixed 9 rounds.
-// lambda_min first decides certification (is it below the floor
-// (2i+1) sqrt(n) eps lambda_max?). Then a geometric grid finds its magnitude,
-// and a linear grid refines it to ~2^-48 relative. lambda_max is refined
-// linearly from [max d, Gershgorin bound].
+// For lambda_min, a first round on the powers of two 2^-64..2^-1 times min d
+// finds its magnitude and decides certification (is it below the floor
+// (2i+1) sqrt(n) eps lambda_max?). Linear rounds then refine it to ~2^-47
+// relative. lambda_max is refined linearly from [max d, Gershgorin bound].
 constexpr int kKappaRounds = 9;
 
 __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
@@ -211,28 +211,26 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
       }
       // certification floor, below the true one since lambda_max >= max d
       floor_s = (double)m * st->sqrt_n * kEps * dmax;
-      lo_s[0] = 0.5 * floor_s;                    // geometric search range for lambda_min
+      lo_s[0] = 0.0;                              // lambda_min in [0, min d] unless uncertified
       hi_s[0] = dmin + 4.0 * kEps * fabs(dmin) + 1e-300;
       lo_s[1] = dmax - 4.0 * kEps * fabs(dmax);   // lambda_max in [max d, Gershgorin]
       hi_s[1] = gh;
-      // min d bounds lambda_min from above: below half the floor, uncertified outright
-      uncert_s = !(dmin > 0.0) || !(dmax > 0.0) || !(hi_s[0] > lo_s[0]);
+      // min d bounds lambda_min from above: at or below the floor, uncertified outright
+      uncert_s = !(dmin > 0.0) || !(dmax > 0.0) || !(hi_s[0] > floor_s);
     }
   }
   __syncthreads();
   const int pair = warp >> 1;           // 0: lambda_min, 1: lambda_max
   const int t = ((warp & 1) << 5) | lane;  // point index 0..63
   const int target = pair == 0 ? 1 : m;
+  const double kStep = 1.0 / 65.0;
   for (int round = 0; round < kKappaRounds; ++round) {
     const double lo = lo_s[pair], hi = hi_s[pair];
-    double x;
-    if (pair == 0 && round == 0) {
-      // geometric grid between half the floor and min d: finds the magnitude
-      x = lo * pow(hi / lo, (double)(t + 1) / 65.0);
-    } else {
-      x = lo + (hi - lo) * ((double)(t + 1) / 65.0);
-    }
-    const int c = (pair == 0 && round == 0 && uncert_s) ? target : sturm_det(d, e2, m, x);
+    // round 0 of lambda_min: points hi * 2^-(64-t), t = 0..63 (exact powers of
+    // two below min d) find its magnitude; later rounds are linear
+    const bool geo = pair == 0 && round == 0;
+    const double x = geo ? ldexp(hi, t - 64) : lo + (hi - lo) * ((double)(t + 1) * kStep);
+    const int c = (geo && uncert_s) ? target : sturm_det(d, e2, m, x);
     const unsigned bal = __ballot_sync(kFull, c >= target);
     if (lane == 0) mask_s[warp] = bal;
     __syncthreads();
@@ -241,16 +239,15 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
       // first point with count >= target; x re-derived with the lanes' expression
       double nlo = lo, nhi = hi;
       if (mk == 0ull) {
-        nlo = (pair == 0 && round == 0) ? lo * pow(hi / lo, 64.0 / 65.0) : lo + (hi - lo) * (64.0 / 65.0);
+        nlo = geo ? ldexp(hi, -1) : lo + (hi - lo) * (64.0 * kStep);
       } else {
         const int f = __ffsll((long long)mk) - 1;
-        nhi = (pair == 0 && round == 0) ? lo * pow(hi / lo, (double)(f + 1) / 65.0)
-                                       : lo + (hi - lo) * ((double)(f + 1) / 65.0);
-        if (f > 0)
-          nlo = (pair == 0 && round == 0) ? lo * pow(hi / lo, (double)f / 65.0) : lo + (hi - lo) * ((double)f / 65.0);
+        nhi = geo ? ldexp(hi, f - 64) : lo + (hi - lo) * ((double)(f + 1) * kStep);
+        if (f > 0) nlo = geo ? ldexp(hi, f - 65) : lo + (hi - lo) * ((double)f * kStep);
+        else if (geo) nlo = 0.0;
       }
-      // lambda_min below the first geometric point, itself below the floor
-      if (pair == 0 && round == 0 && (mk & 1ull)) uncert_s = 1;
+      // lambda_min below a point that is itself below the floor: uncertified
+      if (geo && nhi <= floor_s) uncert_s = 1;
       lo_s[pair] = nlo;
       hi_s[pair] = nhi;
     }

@@ -23,8 +23,8 @@ namespace {
 
 __global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
                                                                    const double* __restrict__ dtil, double sig,
-                                                                   double* __restrict__ Y, int64_t ldY, int j,
-                                                                   int do_p, int do_r) {
+                                                                   int use_sig, double* __restrict__ Y, int64_t ldY,
+                                                                   int j, int do_p, int do_r) {
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   if (row >= O.n) return;
   const double* pj = Y + (int64_t)(2 * j) * ldY;
@@ -46,14 +46,14 @@ __global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSell O, co
       tr = fma(a, __ldg(rj + cc), tr);
     }
     // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
-    if (sig != 0.0 && j >= 1) {
+    if (use_sig) {  // integer test: a double compare would take an FP64 issue slot per row
       tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
       tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
     }
     Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
   } else {
     for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
-    if (sig != 0.0 && j >= 1) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
+    if (use_sig) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
   }
   if (do_p) Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
 }
@@ -107,7 +107,8 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
                                   int do_r, cudaStream_t s) {
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
-  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r);
+  const int use_sig = (op.sig != 0.0 && j >= 1) ? 1 : 0;
+  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p, do_r);
   return cudaGetLastError();
 }
 
