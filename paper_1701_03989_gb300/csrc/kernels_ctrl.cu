@@ -114,15 +114,16 @@ __device__ __forceinline__ int sturm_det(const double* d, const double* e2, int 
 }
 
 // kappa(G_{k,i}) for i = blockIdx.x + 1. G_{k,i} is the leading (2i+1) block of G
-// (interleaved column order). Warp 0 reduces it to tridiagonal form by
-// Householder reflections, one lane per row. The tridiagonal is scaled to unit
-// norm. Warps 0-1 then bracket lambda_min and warps 2-3 bracket lambda_max, each
-// pair evaluating 64 Sturm counts per round for a fixed 9 rounds.
-// For lambda_min, a first round on the powers of two 2^-64..2^-1 times min d
-// finds its magnitude and decides certification (is it below the floor
-// (2i+1) sqrt(n) eps lambda_max?). Linear rounds then refine it to ~2^-47
-// relative. lambda_max is refined linearly from [max d, Gershgorin bound].
-constexpr int kKappaRounds = 9;
+// (interleaved column order). The FP64 pipe is shared by the whole SM, so the
+// kernel avoids redundant FP64 work: warp 0 alone forms each Householder
+// reflection's scalars (norm, square root, one division) and publishes them
+// in shared memory. Only the O(len^2) product and rank-2 update are split by
+// columns over the four warps. The tridiagonal is then scaled to unit norm.
+// Warp 0 brackets lambda_min and warp 1 lambda_max with 32 Sturm counts per
+// round for a fixed 11 rounds. For lambda_min, the first round is on the powers
+// of two 2^-32..2^-1 times min d, which finds its magnitude and decides
+// certification (is it below the floor (2i+1) sqrt(n) eps lambda_max?).
+constexpr int kKappaRounds = 11;
 
 __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
   const int i = blockIdx.x + 1;
@@ -133,54 +134,63 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
   __shared__ double part[4][32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
   __shared__ double lo_s[2], hi_s[2];
-  __shared__ unsigned mask_s[4];
-  __shared__ double floor_s, scale_s;
-  __shared__ int uncert_s;
+  __shared__ double beta_s, floor_s, scale_s;
+  __shared__ int go_s, uncert_s;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  // Householder: every warp computes the scalars of step k redundantly (no
-  // extra latency, one warp per SM sub-partition); the matrix-vector product
-  // and the rank-2 update are split by columns across the four warps.
   for (int k = 0; k + 2 < m; ++k) {
     const int len = m - k - 1;  // rows k+1 .. m-1, at most 32
     const int row = k + 1 + lane;
     const bool on = lane < len;
     const int c0 = (len * warp) >> 2, c1 = (len * (warp + 1)) >> 2;
-    const double xi = on ? A[row][k] : 0.0;
-    const double s2 = warp_sum(xi * xi);
-    const double x0 = __shfl_sync(kFull, xi, 0);
-    double alpha = 0.0;
-    if (s2 > 0.0) {
-      alpha = -copysign(sqrt(s2), x0);
-      const double vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
-      const double vn2 = warp_sum(vi * vi);
-      const double beta = 2.0 / vn2;
-      if (warp == 0) v[lane] = vi;
-      __syncthreads();
-      double p0 = 0.0, p1 = 0.0;
-      if (on) {
-        int c = c0;
-        for (; c + 1 < c1; c += 2) {
-          p0 = fma(A[row][k + 1 + c], v[c], p0);
-          p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
-        }
-        if (c < c1) p0 = fma(A[row][k + 1 + c], v[c], p0);
+    double vi = 0.0;
+    if (warp == 0) {
+      const double xi = on ? A[row][k] : 0.0;
+      const double s2 = warp_sum(xi * xi);
+      const double x0 = __shfl_sync(kFull, xi, 0);
+      const int go = s2 > 0.0;
+      double alpha = 0.0;
+      if (go) {
+        const double r = sqrt(s2);
+        alpha = -copysign(r, x0);
+        vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
+        // v^T v = 2 (s2 + |x0| r), so beta = 2 / v^T v without another reduction
+        if (lane == 0) beta_s = 1.0 / (s2 + fabs(x0) * r);
       }
-      part[warp][lane] = p0 + p1;
-      __syncthreads();
+      v[lane] = vi;
+      if (lane == 0) {
+        go_s = go;
+        e[k] = alpha;  // s2 == 0: the column is already zero
+      }
+    }
+    __syncthreads();
+    if (!go_s) continue;  // uniform
+    if (warp != 0) vi = on ? v[lane] : 0.0;
+    double p0 = 0.0, p1 = 0.0;
+    if (on) {
+      int c = c0;
+      for (; c + 1 < c1; c += 2) {
+        p0 = fma(A[row][k + 1 + c], v[c], p0);
+        p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
+      }
+      if (c < c1) p0 = fma(A[row][k + 1 + c], v[c], p0);
+    }
+    part[warp][lane] = p0 + p1;
+    __syncthreads();
+    if (warp == 0) {
+      const double beta = beta_s;
       const double pi = beta * ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]));
       const double K = 0.5 * beta * warp_sum(vi * pi);
-      const double wi = pi - K * vi;
-      if (warp == 0) wv[lane] = wi;
-      __syncthreads();
-      if (on)
-        for (int c = c0; c < c1; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
-      __syncthreads();
+      wv[lane] = pi - K * vi;
     }
-    if (threadIdx.x == 0) e[k] = alpha;  // s2 == 0: the column is already zero
+    __syncthreads();
+    if (on) {
+      const double wi = wv[lane];
+      for (int c = c0; c < c1; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
+    }
+    __syncthreads();
   }
-  __syncthreads();
   if (warp == 0) {
     for (int r = lane; r < m; r += 32) d[r] = A[r][r];
     if (lane == 0) e[m - 2] = A[m - 1][m - 2];
@@ -189,10 +199,10 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
       double gl, gh, piv;
       gershgorin(d, e, m, &gl, &gh, &piv);
       const double S = fmax(fabs(gl), fabs(gh));
-      scale_s = S > 0.0 ? S : 1.0;
+      scale_s = S > 0.0 ? 1.0 / S : 1.0;
     }
     __syncwarp();
-    const double inv = 1.0 / scale_s;
+    const double inv = scale_s;
     for (int r = lane; r < m; r += 32) {
       d[r] *= inv;
       if (r + 1 < m) {
@@ -220,39 +230,41 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
     }
   }
   __syncthreads();
-  const int pair = warp >> 1;           // 0: lambda_min, 1: lambda_max
-  const int t = ((warp & 1) << 5) | lane;  // point index 0..63
-  const int target = pair == 0 ? 1 : m;
-  const double kStep = 1.0 / 65.0;
-  for (int round = 0; round < kKappaRounds; ++round) {
-    const double lo = lo_s[pair], hi = hi_s[pair];
-    // round 0 of lambda_min: points hi * 2^-(64-t), t = 0..63 (exact powers of
-    // two below min d) find its magnitude; later rounds are linear
-    const bool geo = pair == 0 && round == 0;
-    const double x = geo ? ldexp(hi, t - 64) : lo + (hi - lo) * ((double)(t + 1) * kStep);
-    const int c = (geo && uncert_s) ? target : sturm_det(d, e2, m, x);
-    const unsigned bal = __ballot_sync(kFull, c >= target);
-    if (lane == 0) mask_s[warp] = bal;
-    __syncthreads();
-    if ((warp & 1) == 0 && lane == 0) {
-      const unsigned long long mk = (unsigned long long)mask_s[warp] | ((unsigned long long)mask_s[warp + 1] << 32);
-      // first point with count >= target; x re-derived with the lanes' expression
+  if (warp < 2) {
+    const int pair = warp;  // 0: lambda_min, 1: lambda_max
+    const int target = pair == 0 ? 1 : m;
+    const double kStep = 1.0 / 33.0;
+    double lo = lo_s[pair], hi = hi_s[pair];
+    const int skip = pair == 0 && uncert_s;
+    for (int round = 0; round < kKappaRounds && !skip; ++round) {
+      // round 0 of lambda_min: points hi * 2^-(32-t), t = 0..31, find its magnitude;
+      // later rounds are linear
+      const bool geo = pair == 0 && round == 0;
+      const double x = geo ? ldexp(hi, lane - 32) : lo + (hi - lo) * ((double)(lane + 1) * kStep);
+      const unsigned mk = __ballot_sync(kFull, sturm_det(d, e2, m, x) >= target);
       double nlo = lo, nhi = hi;
-      if (mk == 0ull) {
-        nlo = geo ? ldexp(hi, -1) : lo + (hi - lo) * (64.0 * kStep);
+      if (mk == 0u) {
+        nlo = __shfl_sync(kFull, x, 31);
       } else {
-        const int f = __ffsll((long long)mk) - 1;
-        nhi = geo ? ldexp(hi, f - 64) : lo + (hi - lo) * ((double)(f + 1) * kStep);
-        if (f > 0) nlo = geo ? ldexp(hi, f - 65) : lo + (hi - lo) * ((double)f * kStep);
-        else if (geo) nlo = 0.0;
+        const int f = __ffs(mk) - 1;
+        nhi = __shfl_sync(kFull, x, f);
+        const double below = __shfl_sync(kFull, x, f > 0 ? f - 1 : 0);
+        nlo = f > 0 ? below : (geo ? 0.0 : lo);
       }
       // lambda_min below a point that is itself below the floor: uncertified
-      if (geo && nhi <= floor_s) uncert_s = 1;
-      lo_s[pair] = nlo;
-      hi_s[pair] = nhi;
+      if (geo && nhi <= floor_s) {
+        if (lane == 0) uncert_s = 1;
+        break;
+      }
+      lo = nlo;
+      hi = nhi;
     }
-    __syncthreads();
+    if (lane == 0) {
+      lo_s[pair] = lo;
+      hi_s[pair] = hi;
+    }
   }
+  __syncthreads();
   if (threadIdx.x == 0) {
     const double lmin = 0.5 * (lo_s[0] + hi_s[0]);
     const double lmax = 0.5 * (lo_s[1] + hi_s[1]);
@@ -280,46 +292,57 @@ __device__ __forceinline__ double bapply(const double* v, int t, int ss, const d
   return acc;
 }
 
-// sum_c a[c] v[c] for c in [c0, c1) with two interleaved accumulators (fixed order).
-__device__ __forceinline__ double rowdot(const double* a, const double* v, int c0, int c1) {
-  double s0 = 0.0, s1 = 0.0;
-  int c = c0;
-  for (; c + 1 < c1; c += 2) {
+// sum_c a[c] v[c] for c < w with four interleaved accumulators (fixed order).
+__device__ __forceinline__ double rowdot(const double* a, const double* v, int w) {
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  int c = 0;
+  for (; c + 3 < w; c += 4) {
     s0 = fma(a[c], v[c], s0);
     s1 = fma(a[c + 1], v[c + 1], s1);
+    s2 = fma(a[c + 2], v[c + 2], s2);
+    s3 = fma(a[c + 3], v[c + 3], s3);
   }
-  if (c < c1) s0 = fma(a[c], v[c], s0);
-  return s0 + s1;
+  for (; c < w; ++c) s0 = fma(a[c], v[c], s0);
+  return (s0 + s1) + (s2 + s3);
 }
 
-// Sum over the 128 threads of the CTA, identical in every thread, fixed order.
-__device__ __forceinline__ double sum128(double x, double* red) {
-  x = warp_sum(x);
+// g = Gs v over the first ws rows and columns. Warp 0 lane r does row r
+// (r < 32); for ws = 33, warp 1 spreads row 32 over its lanes and reduces it.
+__device__ __forceinline__ void gmatvec(const double (*Gs)[kMaxW], const double* v, int ws, double* g) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[warp] = x;
-  __syncthreads();
-  return (red[0] + red[1]) + (red[2] + red[3]);
+  if (warp == 0) {
+    if (lane < ws) g[lane] = rowdot(Gs[lane], v, ws);
+  } else if (ws > 32) {
+    double t = lane < ws ? Gs[32][lane] * v[lane] : 0.0;
+    if (lane + 32 < ws) t = fma(Gs[32][lane + 32], v[lane + 32], t);
+    t = warp_sum(t);
+    if (lane == 0) g[32] = t;
+  }
 }
 
-// One CTA of 128 threads. Thread t works on coordinate row tr = t & 63 and on
-// half h = t >> 6 of that row's columns, so each w-long product G u is split
-// over four warps (one per SM sub-partition) and then combined in shared
-// memory in a fixed order.
-__global__ void __launch_bounds__(128) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
-                                                   const double* __restrict__ sg_g, const double* __restrict__ gm_g,
-                                                   BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
-                                                   double* __restrict__ res_hist, int res_cap,
-                                                   double* __restrict__ ab_hist, int ab_cap) {
+// sum_r a[r] b[r] over the first ws rows, by warp 0 (valid in all its lanes).
+__device__ __forceinline__ double dot_rows(const double* a, const double* b, int ws) {
+  const int lane = threadIdx.x & 31;
+  double t = warp_sum(lane < ws ? a[lane] * b[lane] : 0.0);
+  if (ws > 32) t += a[32] * b[32];
+  return t;
+}
+
+// One CTA of 64 threads. Rows (coordinates) 0..31 belong to warp 0, row 32 to
+// warp 1. The FP64 pipe is shared by the whole SM, so each scalar of the
+// recurrence (alpha, beta, norms, thresholds) is formed once, by thread 0,
+// and published in shared memory.
+__global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
+                                                  const double* __restrict__ sg_g, const double* __restrict__ gm_g,
+                                                  BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
+                                                  double* __restrict__ res_hist, int res_cap,
+                                                  double* __restrict__ ab_hist, int ab_cap) {
   __shared__ double Gs[kMaxW][kMaxW];  // odd row stride: conflict-free
-  __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2];
-  __shared__ double half_sum[2][64];
+  __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2], g[kMaxW + 2];
   __shared__ double th[kMaxS], sg[kMaxS], gm[kMaxS];
-  __shared__ double red[4];
-  __shared__ int s_tilde;
-  __shared__ double s_gamma;
+  __shared__ int s_tilde, s_flag;
+  __shared__ double s_gamma, s_alpha, s_beta;
   const int t = threadIdx.x;
-  const int tr = t & 63, hh = t >> 6;
   const int sbar = st->sbar;
   const int w = 2 * sbar + 1;
   const int adaptive = st->method == ASCG_ADAPTIVE;
@@ -359,22 +382,21 @@ __global__ void __launch_bounds__(128) ctrl_kernel(const double* __restrict__ G,
     s_tilde = stilde;
     s_gamma = gamma;
   }
-  __syncthreads();
-  const int ss = s_tilde;
-  const int ws = 2 * ss + 1;
-  const double gamma = s_gamma;
-  const bool row = tr < ws;      // this thread's row exists
-  const bool own = row && hh == 0;  // and this thread owns the row's vector entries
-  const int cmid = (ws + 1) >> 1;
-  const int c0 = hh ? cmid : 0, c1 = hh ? ws : cmid;
   if (t < kMaxW + 2) {
     pc[t] = (t == 0) ? 1.0 : 0.0;  // p' = e_1 (column p_0)
     rc[t] = (t == 1) ? 1.0 : 0.0;  // r' = e_{s+2} (column r_0)
     xc[t] = 0.0;
     u[t] = 0.0;
     rn[t] = 0.0;
+    g[t] = 0.0;
   }
   __syncthreads();
+  const int ss = s_tilde;
+  const int ws = 2 * ss + 1;
+  const double gamma = s_gamma;
+  // thread owning coordinate row r: t = r for r < 32, t = 32 (warp 1, lane 0) for r = 32
+  const int myrow = t < 32 ? t : (t == 32 ? 32 : -1);
+  const bool own = myrow >= 0 && myrow < ws;
   double rGr = Gs[1][1];
   int steps = 0, stop = ASCG_STOP_DONE;
   const int nsteps = min(ss, st->max_steps);
@@ -382,65 +404,79 @@ __global__ void __launch_bounds__(128) ctrl_kernel(const double* __restrict__ G,
   double relres = sqrt(fmax(rGr, 0.0)) / bnorm;
   for (int j = 1; j <= nsteps; ++j) {
     // alpha = (r'^T G r') / (p'^T G B p')
-    if (own) u[tr] = bapply(pc, tr, ss, th, sg, gm);
+    if (own) u[myrow] = bapply(pc, myrow, ss, th, sg, gm);
     __syncthreads();
-    if (row) half_sum[hh][tr] = rowdot(Gs[tr], u, c0, c1);
+    gmatvec(Gs, u, ws, g);
     __syncthreads();
-    const double gi = own ? half_sum[0][tr] + half_sum[1][tr] : 0.0;
-    const double pGBp = sum128(own ? pc[tr] * gi : 0.0, red);
-    if (!(pGBp > 0.0) || !isfinite(pGBp) || !(rGr > 0.0) || !isfinite(rGr)) {
+    if (t < 32) {
+      const double pGBp = dot_rows(pc, g, ws);
+      if (t == 0) {
+        const int ok = (pGBp > 0.0) && isfinite(pGBp) && (rGr > 0.0) && isfinite(rGr);
+        s_flag = ok;
+        s_alpha = ok ? rGr / pGBp : 0.0;
+      }
+    }
+    __syncthreads();
+    if (!s_flag) {
       stop = ASCG_STOP_BREAKDOWN;
       break;
     }
-    const double alpha = rGr / pGBp;
+    const double alpha = s_alpha;
     // q' = alpha p'; x' += q'; r' -= B q'
     if (own) {
-      const double q = alpha * pc[tr];
-      u[tr] = q;
-      xc[tr] += q;
+      const double q = alpha * pc[myrow];
+      u[myrow] = q;
+      xc[myrow] += q;
     }
     __syncthreads();
-    if (own) rn[tr] = rc[tr] - bapply(u, tr, ss, th, sg, gm);
+    if (own) rn[myrow] = rc[myrow] - bapply(u, myrow, ss, th, sg, gm);
     __syncthreads();
-    if (row) half_sum[hh][tr] = rowdot(Gs[tr], rn, c0, c1);
+    gmatvec(Gs, rn, ws, g);
     __syncthreads();
-    const double g2 = own ? half_sum[0][tr] + half_sum[1][tr] : 0.0;
-    const double rGr_new = sum128(own ? rn[tr] * g2 : 0.0, red);
-    const double beta = rGr_new / rGr;
+    if (t < 32) {
+      const double rGr_new = dot_rows(rn, g, ws);
+      if (t == 0) {
+        const double beta = rGr_new / rGr;
+        const double rnn = sqrt(fmax(rGr_new, 0.0));
+        relres = rnn / bnorm;
+        const int it = m0 + j;  // 1-based iteration index
+        if (res_hist && it < res_cap) res_hist[it] = relres;
+        if (ab_hist && it - 1 < ab_cap) {
+          ab_hist[it - 1] = alpha;
+          ab_hist[ab_cap + it - 1] = beta;
+        }
+        if (hist) {
+          hist[3 * (j - 1)] = alpha;
+          hist[3 * (j - 1) + 1] = beta;
+          hist[3 * (j - 1) + 2] = relres;
+        }
+        int fl = ASCG_STOP_DONE;
+        if (rnn <= eps_star) {
+          fl = ASCG_STOP_CONVERGED;
+        } else if (adaptive && st->check_in_loop) {
+          // eq. (check): break when gamma >= eps* / (c eps (r'^T G r')^(1/2))
+          const double Tj = rnn > 0.0 ? eps_star / (cc * kEps * rnn) : CUDART_INF;
+          if (gamma >= Tj) fl = ASCG_STOP_BREAK;
+        }
+        s_beta = beta;
+        s_flag = fl;
+        s_alpha = rGr_new;
+      }
+    }
+    __syncthreads();
+    const double beta = s_beta;
     if (own) {
-      pc[tr] = fma(beta, pc[tr], rn[tr]);  // p' = r'_new + beta p'
-      rc[tr] = rn[tr];
+      pc[myrow] = fma(beta, pc[myrow], rn[myrow]);  // p' = r'_new + beta p'
+      rc[myrow] = rn[myrow];
     }
-    rGr = rGr_new;
+    rGr = s_alpha;
     steps = j;
-    const double rnn = sqrt(fmax(rGr_new, 0.0));
-    relres = rnn / bnorm;
-    if (t == 0) {
-      const int it = m0 + j;  // 1-based iteration index
-      if (res_hist && it < res_cap) res_hist[it] = relres;
-      if (ab_hist && it - 1 < ab_cap) {
-        ab_hist[it - 1] = alpha;
-        ab_hist[ab_cap + it - 1] = beta;
-      }
-      if (hist) {
-        hist[3 * (j - 1)] = alpha;
-        hist[3 * (j - 1) + 1] = beta;
-        hist[3 * (j - 1) + 2] = relres;
-      }
-    }
-    if (rnn <= eps_star) {
-      stop = ASCG_STOP_CONVERGED;
+    const int fl = s_flag;
+    __syncthreads();
+    if (fl != ASCG_STOP_DONE) {
+      stop = fl;
       break;
     }
-    if (adaptive && st->check_in_loop) {
-      // eq. (check): break when gamma >= eps* / (c eps (r'^T G r')^(1/2))
-      const double Tj = rnn > 0.0 ? eps_star / (cc * kEps * rnn) : CUDART_INF;
-      if (gamma >= Tj) {
-        stop = ASCG_STOP_BREAK;
-        break;
-      }
-    }
-    __syncthreads();
   }
   if (stop == ASCG_STOP_DONE && steps < ss) stop = ASCG_STOP_MAXITER;
   __syncthreads();
@@ -454,7 +490,7 @@ __global__ void __launch_bounds__(128) ctrl_kernel(const double* __restrict__ G,
     st->s_k = steps;
     st->stop = stop;
     st->converged = stop == ASCG_STOP_CONVERGED;
-    st->rel_res = relres;
+    st->rel_res = steps > 0 ? relres : sqrt(fmax(Gs[1][1], 0.0)) / bnorm;
   }
 }
 
@@ -534,7 +570,7 @@ cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t
 cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
                         BlockState* st, double* coords, double* hist, double* res_hist, int res_cap,
                         double* ab_hist, int ab_cap, cudaStream_t s) {
-  ctrl_kernel<<<1, 128, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
+  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
   return cudaGetLastError();
 }
 
