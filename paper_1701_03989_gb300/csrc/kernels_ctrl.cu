@@ -33,32 +33,6 @@ __device__ __forceinline__ int sturm_count(const double* d, const double* e2, in
   return cnt;
 }
 
-// Finds the smallest x with count(x) >= target by 33-way multisection on
-// [lo, hi] (count(lo) < target <= count(hi)). Every lane of the warp calls
-// this with the same arguments; at most 40 rounds.
-__device__ double multisect(const double* d, const double* e2, int m, double lo, double hi, int target,
-                            double pivmin) {
-  const int lane = threadIdx.x & 31;
-  for (int round = 0; round < 40; ++round) {
-    const double scale = fmax(fabs(lo), fabs(hi));
-    if (hi - lo <= 2.0 * kEps * scale || !(hi > lo)) break;
-    const double x = lo + (hi - lo) * ((double)(lane + 1) / 33.0);
-    const int c = sturm_count(d, e2, m, x, pivmin);
-    const unsigned mask = __ballot_sync(kFull, c >= target);
-    const double x_hi_all = __shfl_sync(kFull, x, 31);
-    if (mask == 0u) {
-      lo = x_hi_all;
-    } else {
-      const int t = __ffs(mask) - 1;
-      const double nh = __shfl_sync(kFull, x, t);
-      const double nl = __shfl_sync(kFull, x, t > 0 ? t - 1 : 0);
-      if (t > 0) lo = nl;
-      hi = nh;
-    }
-  }
-  return 0.5 * (lo + hi);
-}
-
 // Gershgorin interval of the tridiagonal, widened by a few ulps.
 __device__ void gershgorin(const double* d, const double* e, int m, double* lo, double* hi, double* pivmin) {
   double gl = CUDART_INF, gh = -CUDART_INF, e2max = 0.0;
@@ -75,42 +49,116 @@ __device__ void gershgorin(const double* d, const double* e, int m, double* lo, 
 }
 
 // Number of eigenvalues smaller than x of the symmetric tridiagonal (d, e2 =
-// e^2), from the signs of the leading principal minors of T - xI. The minors
-// follow p_k = (d_k - x) p_{k-1} - e2_{k-1} p_{k-2}, with no division. The
-// critical path is one FMA per step, against a division per step for the
-// pivot form. Rounding in this recurrence gives the exact signs of a matrix
-// whose d_k - x and e2 are perturbed by a few ulps (positive rescalings do
-// not change signs), the same backward error as the pivot form. The caller
-// scales T to norm <= 1, so |p_k| <= 3^k cannot overflow. Tiny minors are
-// rescaled by 2^256 (exact). A zero minor is replaced by a tiny value of the
-// sign opposite to its predecessor, as the pivot form does with -pivmin.
-__device__ __forceinline__ int sturm_det(const double* d, const double* e2, int m, double x) {
-  const double kUp = 1.157920892373162e77;    // 2^256
-  const double kTiny = 8.636168555094445e-78; // 2^-256
+// e^2) of order M, scaled to norm <= 1, from the signs of the leading
+// principal minors of T - xI. The minors follow p_k = (d_k - x) p_{k-1} -
+// e2_{k-1} p_{k-2}, with no division: rounding gives the exact signs of a
+// matrix whose d_k - x and e2 are perturbed by a few ulps (positive
+// rescalings do not change signs), the backward error of the pivot form.
+// The loop is unrolled with d and e2 in registers. Each step costs three FP64
+// instructions (d_k - x, the product with e2 and the FMA); on GB300 an SM
+// sub-partition issues about one FP64 warp instruction per 64 cycles, and
+// that rate, not latency, sets the time of a multisection round. The leading
+// minors grow at most like (1 + sqrt 2)^k <= 2^43 for M <= 33, so they cannot
+// overflow. One integer test of the exponent per step catches, on a rarely
+// taken branch, both a minor below 2^-256 (rescaled exactly by 2^256, with
+// its predecessor) and a zero minor (replaced by a tiny value of the sign
+// opposite to its predecessor).
+template <int M>
+__device__ __forceinline__ int sturm_unrolled(const double (&d)[M], const double (&e2)[M], double x) {
+  const double kUp = 1.157920892373162e77;     // 2^256
+  const double kTiny = 8.636168555094445e-78;  // 2^-256
   double pm2 = 1.0;
   double pm1 = d[0] - x;
   if (pm1 == 0.0) pm1 = -kTiny * kTiny;
   int hprev = __double2hiint(pm1);
   int cnt = (int)((unsigned)hprev >> 31);
-  for (int k = 1; k < m; ++k) {
+#pragma unroll
+  for (int k = 1; k < M; ++k) {
     const double t = e2[k - 1] * pm2;
     double p = fma(d[k] - x, pm1, -t);
     int hp = __double2hiint(p);
-    // sign, zero and exponent tests on the bit pattern: integer pipe, not FP64
-    if (((hp & 0x7fffffff) | __double2loint(p)) == 0) {
-      p = -copysign(fabs(pm1) * kTiny, pm1);
+    if (((hp >> 20) & 0x7ff) < 767) {  // |p| < 2^-256 or p == 0 (rare)
+      if (((hp & 0x7fffffff) | __double2loint(p)) == 0) {
+        p = -copysign(fabs(pm1) * kTiny, pm1);
+      } else {  // exact rescaling of p_k and p_{k-1}
+        p *= kUp;
+        pm1 *= kUp;
+      }
       hp = __double2hiint(p);
     }
     cnt += (int)((unsigned)(hp ^ hprev) >> 31);
     pm2 = pm1;
     pm1 = p;
     hprev = hp;
-    if (((hp >> 20) & 0x7ff) < 767) {  // |p| < 2^-256
-      pm1 *= kUp;
-      pm2 *= kUp;
-    }
   }
   return cnt;
+}
+
+// 33-way multisection (one warp) for the smallest x with count(x) >= target on
+// [lo, hi]. geo0: the first round uses the points hi * 2^-(32-t), t = 0..31.
+// Returns through lo/hi; stop_below: if the first geometric bracket lies at or
+// below this value, sets *below and stops.
+template <int M>
+__device__ void multisect_warp(const double* ds, const double* e2s, int target, int rounds, bool geo0,
+                               double stop_below, double* lo_io, double* hi_io, int* below) {
+  const int lane = threadIdx.x & 31;
+  double d[M], e2[M];
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    d[k] = ds[k];
+    e2[k] = k + 1 < M ? e2s[k] : 0.0;
+  }
+  const double kStep = 1.0 / 33.0;
+  double lo = *lo_io, hi = *hi_io;
+  for (int round = 0; round < rounds; ++round) {
+    const bool geo = geo0 && round == 0;
+    const double x = geo ? ldexp(hi, lane - 32) : lo + (hi - lo) * ((double)(lane + 1) * kStep);
+    const unsigned mk = __ballot_sync(kFull, sturm_unrolled<M>(d, e2, x) >= target);
+    double nlo = lo, nhi = hi;
+    if (mk == 0u) {
+      nlo = __shfl_sync(kFull, x, 31);
+    } else {
+      const int f = __ffs(mk) - 1;
+      nhi = __shfl_sync(kFull, x, f);
+      const double below_pt = __shfl_sync(kFull, x, f > 0 ? f - 1 : 0);
+      nlo = f > 0 ? below_pt : (geo ? 0.0 : lo);
+    }
+    if (geo && nhi <= stop_below) {
+      *below = 1;
+      break;
+    }
+    lo = nlo;
+    hi = nhi;
+  }
+  *lo_io = lo;
+  *hi_io = hi;
+}
+
+__device__ void multisect_dispatch(int m, const double* ds, const double* e2s, int target, int rounds, bool geo0,
+                                   double stop_below, double* lo, double* hi, int* below) {
+  switch (m) {
+#define ASCG_MS(M) \
+  case M:          \
+    multisect_warp<M>(ds, e2s, target, rounds, geo0, stop_below, lo, hi, below); \
+    break;
+    ASCG_MS(3) ASCG_MS(5) ASCG_MS(7) ASCG_MS(9) ASCG_MS(11) ASCG_MS(13) ASCG_MS(15) ASCG_MS(17)
+    ASCG_MS(19) ASCG_MS(21) ASCG_MS(23) ASCG_MS(25) ASCG_MS(27) ASCG_MS(29) ASCG_MS(31) ASCG_MS(33)
+#undef ASCG_MS
+    default:
+      break;
+  }
+}
+
+// Warp-wide min and max (identical in all lanes).
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(kFull, v, o));
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(kFull, v, o));
+  return v;
 }
 
 // kappa(G_{k,i}) for i = blockIdx.x + 1. G_{k,i} is the leading (2i+1) block of G
@@ -134,7 +182,7 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
   __shared__ double part[4][32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
   __shared__ double lo_s[2], hi_s[2];
-  __shared__ double beta_s, floor_s, scale_s;
+  __shared__ double beta_s, floor_s;
   __shared__ int go_s, uncert_s;
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
@@ -192,17 +240,25 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
     __syncthreads();
   }
   if (warp == 0) {
+    // tridiagonal (d, e), Gershgorin bounds and scaling by warp reductions; lane r
+    // holds row r (and row r + 32 for m = 33)
     for (int r = lane; r < m; r += 32) d[r] = A[r][r];
     if (lane == 0) e[m - 2] = A[m - 1][m - 2];
     __syncwarp();
-    if (lane == 0) {
-      double gl, gh, piv;
-      gershgorin(d, e, m, &gl, &gh, &piv);
-      const double S = fmax(fabs(gl), fabs(gh));
-      scale_s = S > 0.0 ? 1.0 / S : 1.0;
+    double gl = CUDART_INF, gh = -CUDART_INF, dmin = CUDART_INF, dmax = -CUDART_INF;
+    for (int r = lane; r < m; r += 32) {
+      const double off = (r > 0 ? fabs(e[r - 1]) : 0.0) + (r + 1 < m ? fabs(e[r]) : 0.0);
+      gl = fmin(gl, d[r] - off);
+      gh = fmax(gh, d[r] + off);
+      dmin = fmin(dmin, d[r]);
+      dmax = fmax(dmax, d[r]);
     }
-    __syncwarp();
-    const double inv = scale_s;
+    gl = warp_min(gl);
+    gh = warp_max(gh);
+    dmin = warp_min(dmin);
+    dmax = warp_max(dmax);
+    const double S = fmax(fabs(gl), fabs(gh));
+    const double inv = S > 0.0 ? 1.0 / S : 1.0;
     for (int r = lane; r < m; r += 32) {
       d[r] *= inv;
       if (r + 1 < m) {
@@ -211,57 +267,33 @@ __global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G
         e2[r] = er * er;
       }
     }
-    __syncwarp();
     if (lane == 0) {
-      double gl, gh, piv, dmin = d[0], dmax = d[0];
-      gershgorin(d, e, m, &gl, &gh, &piv);
-      for (int r = 1; r < m; ++r) {
-        dmin = fmin(dmin, d[r]);
-        dmax = fmax(dmax, d[r]);
-      }
+      dmin *= inv;
+      dmax *= inv;
+      // Gershgorin upper bound of the scaled matrix, widened by a few ulps
+      const double ghs = gh * inv + 4.0 * kEps * (double)m + 1e-300;
       // certification floor, below the true one since lambda_max >= max d
       floor_s = (double)m * st->sqrt_n * kEps * dmax;
       lo_s[0] = 0.0;                              // lambda_min in [0, min d] unless uncertified
       hi_s[0] = dmin + 4.0 * kEps * fabs(dmin) + 1e-300;
       lo_s[1] = dmax - 4.0 * kEps * fabs(dmax);   // lambda_max in [max d, Gershgorin]
-      hi_s[1] = gh;
+      hi_s[1] = ghs;
       // min d bounds lambda_min from above: at or below the floor, uncertified outright
       uncert_s = !(dmin > 0.0) || !(dmax > 0.0) || !(hi_s[0] > floor_s);
     }
   }
   __syncthreads();
   if (warp < 2) {
-    const int pair = warp;  // 0: lambda_min, 1: lambda_max
-    const int target = pair == 0 ? 1 : m;
-    const double kStep = 1.0 / 33.0;
+    const int pair = warp;  // 0: lambda_min (geometric first round), 1: lambda_max
     double lo = lo_s[pair], hi = hi_s[pair];
-    const int skip = pair == 0 && uncert_s;
-    for (int round = 0; round < kKappaRounds && !skip; ++round) {
-      // round 0 of lambda_min: points hi * 2^-(32-t), t = 0..31, find its magnitude;
-      // later rounds are linear
-      const bool geo = pair == 0 && round == 0;
-      const double x = geo ? ldexp(hi, lane - 32) : lo + (hi - lo) * ((double)(lane + 1) * kStep);
-      const unsigned mk = __ballot_sync(kFull, sturm_det(d, e2, m, x) >= target);
-      double nlo = lo, nhi = hi;
-      if (mk == 0u) {
-        nlo = __shfl_sync(kFull, x, 31);
-      } else {
-        const int f = __ffs(mk) - 1;
-        nhi = __shfl_sync(kFull, x, f);
-        const double below = __shfl_sync(kFull, x, f > 0 ? f - 1 : 0);
-        nlo = f > 0 ? below : (geo ? 0.0 : lo);
-      }
-      // lambda_min below a point that is itself below the floor: uncertified
-      if (geo && nhi <= floor_s) {
-        if (lane == 0) uncert_s = 1;
-        break;
-      }
-      lo = nlo;
-      hi = nhi;
-    }
+    int below = 0;
+    if (!(pair == 0 && uncert_s))
+      multisect_dispatch(m, d, e2, pair == 0 ? 1 : m, kKappaRounds, pair == 0, pair == 0 ? floor_s : -1.0, &lo, &hi,
+                         &below);
     if (lane == 0) {
       lo_s[pair] = lo;
       hi_s[pair] = hi;
+      if (below) uncert_s = 1;
     }
   }
   __syncthreads();
