@@ -112,6 +112,8 @@ typedef struct {
 } ascg_options;
 
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
+#define ASCG_FLAG_GRAM_FP64 2 /* Gram by FP64 FMAs on the CUDA cores for every w,
+                                 instead of the tensor-core kernel (w >= 9)      */
 
 typedef struct {
   int status;                /* ascg_status of the solve                          */
@@ -199,7 +201,15 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
 /* Gram matrix G = Y^T Y of the first w columns of Y (Sec. 2.1): device Y as
  * above with n rows, device G double[w*w], row-major, symmetric (both halves
  * written). 1 <= w <= 33. Sums run in a fixed order: the result is bitwise
- * reproducible for a given n, w and device. */
+ * reproducible for a given n, w and device.
+ * For w < 9 the products are FP64 FMAs (error <= gamma_n |Y|^T |Y| per
+ * entry). For w >= 9 they run on the bf16 tensor cores with an error-free
+ * split of Y: entries of column a are rounded to the grid 2^(E_a - 56), where
+ * 2^(E_a - 1) <= max|y_a| < 2^E_a, written in seven base-256 digits, and the
+ * digit products are summed exactly in integers. Per entry the error is at
+ * most 2^-51 (max|y_a| ||y_b||_1 + max|y_b| ||y_a||_1) + gamma_(m) |y_a|^T |y_b|
+ * (m = CTAs + 7); a column holding Inf or NaN gives NaN in its row and
+ * column. */
 ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
 
 /* One block controller step on a given Gram matrix (Alg. 4 from "Determine
@@ -245,9 +255,10 @@ ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k,
  *    row-major, both halves written). 1 <= w <= 33; larger w returns
  *    ASCG_ERR_INVALID.
  *  - The per-CTA partial sums live in one static device array of 160 x 561
- *    doubles (701 KB). Every GPU that loads the library holds it until the
- *    process exits. A GPU that would use more than 160 CTAs (more than 160 SMs)
- *    gets ASCG_ERR_INVALID.
+ *    doubles (701 KB), and the per-CTA column exponents of the tensor-core
+ *    kernel in one of 160 x 33 ints (21 KB). Every GPU that loads the library
+ *    holds them until the process exits. A GPU that would use more than 160
+ *    CTAs (more than 160 SMs) gets ASCG_ERR_INVALID.
  *  - Calls nothing that allocates: no cudaMalloc, cudaFree or allocating
  *    library routine. The first call on each device looks up the array's
  *    device address (cudaGetSymbolAddress) with that device current. Make

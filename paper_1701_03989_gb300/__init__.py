@@ -32,6 +32,7 @@ ASCG_CLASSICAL, ASCG_FIXED_S, ASCG_ADAPTIVE = 0, 1, 2
 ASCG_MONOMIAL, ASCG_NEWTON, ASCG_CHEBYSHEV = 0, 1, 2
 ASCG_STOP_DONE, ASCG_STOP_CONVERGED, ASCG_STOP_BREAK, ASCG_STOP_BREAKDOWN, ASCG_STOP_MAXITER = 0, 1, 2, 3, 4
 ASCG_FLAG_TIMING = 1
+ASCG_FLAG_GRAM_FP64 = 2
 
 
 class ascg_block_info(C.Structure):
@@ -238,7 +239,8 @@ _BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CH
 
 def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
-                 res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None) -> ascg_options:
+                 res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
+                 gram_fp64=False) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call."""
     o = ascg_options_default()
@@ -254,7 +256,7 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
     o.newton_warmup = int(newton_warmup)
     o.max_iters = int(max_iters)
     o.check_in_loop = 1 if check_in_loop else 0
-    o.flags = ASCG_FLAG_TIMING if timing else 0
+    o.flags = (ASCG_FLAG_TIMING if timing else 0) | (ASCG_FLAG_GRAM_FP64 if gram_fp64 else 0)
     if res_hist is not None:
         o.res_hist = res_hist.ctypes.data_as(C.POINTER(C.c_double))
         o.res_hist_cap = len(res_hist)

@@ -70,6 +70,7 @@ struct Workspace {
   double* q = nullptr;      // classical CG: A p; also a scratch vector
   double* partials = nullptr;
   int64_t partials_cap = 0;
+  int* expp = nullptr;      // column exponents of the tensor-core Gram, gram_grid() x kMaxW
   unsigned* counter = nullptr;
   double* G = nullptr;      // kMaxW^2
   double* coords = nullptr; // 3 kMaxW
@@ -93,7 +94,7 @@ struct Workspace {
   bool events = false;
 
   void release() {
-    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(counter);
+    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(counter);
     dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
     dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
     dev_free(dtils); dev_free(oscaled[0]); dev_free(oscaled[1]);
@@ -234,6 +235,7 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     ASCG_TRY(dev_alloc(&w.partials, (size_t)pcap));
     w.partials_cap = pcap;
   }
+  if (!w.expp) ASCG_TRY(dev_alloc(&w.expp, (size_t)gram_grid() * kMaxW));
   if (wcols > 2 && !w.dtils) {
     ASCG_TRY(dev_alloc(&w.dtils, (size_t)kMaxS * n));
     ASCG_TRY(dev_alloc(&w.oscaled[0], (size_t)op->o_len));
@@ -376,6 +378,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
   const int wmax = sstep ? 2 * o.s_max + 1 : 2;
   ASCG_TRY(ensure(op, wmax, o.max_iters + 2));
   const bool timing = (o.flags & ASCG_FLAG_TIMING) != 0;
+  const bool gram_fp64 = (o.flags & ASCG_FLAG_GRAM_FP64) != 0;
   if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
 
   // ||b||, r_1 = b - A x_1, p_1 = r_1 (Alg. 1/4 first line). p = column 0 and
@@ -487,10 +490,11 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       res->launches += sbar;
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
       // Gram: the block's one grid-wide reduction
-      ASCG_CUDA(launch_gram_partial(n, wb, w.Y, w.ldY, w.partials, s));
+      int nparts = 0;
+      ASCG_CUDA(launch_gram_any(n, wb, w.Y, w.ldY, gram_fp64, w.expp, w.partials, &nparts, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
-      ASCG_CUDA(launch_gram_finalize(wb, w.partials, gram_parts(n), w.G, s));
-      res->launches += 2;
+      ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
+      res->launches += (!gram_fp64 && gram_tc_applies(wb)) ? 3 : 2;
       res->grid_reductions += 1;
       if (o.method == ASCG_ADAPTIVE) {
         ASCG_CUDA(launch_kappa(w.G, w.bst, sbar, s));
@@ -791,12 +795,19 @@ ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G,
   if (!Y || !G || n < 1 || w < 1 || w > ASCG_MAX_W || ldY < n) return fail(ASCG_ERR_INVALID, "bad argument");
   cudaStream_t s = (cudaStream_t)cuda_stream;
   double* partials = nullptr;
-  const int parts = gram_parts(n);
-  ASCG_TRY(dev_alloc(&partials, (size_t)parts * kMaxPairs));
-  cudaError_t e = launch_gram_partial(n, w, Y, ldY, partials, s);
+  int* expp = nullptr;
+  int parts = 0;
+  ASCG_TRY(dev_alloc(&partials, (size_t)gram_grid() * kMaxPairs));
+  ascg_status rs = dev_alloc(&expp, (size_t)gram_grid() * kMaxW);
+  if (rs != ASCG_OK) {
+    cudaFree(partials);
+    return rs;
+  }
+  cudaError_t e = launch_gram_any(n, w, Y, ldY, false, expp, partials, &parts, s);
   if (e == cudaSuccess) e = launch_gram_finalize(w, partials, parts, G, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(partials);
+  cudaFree(expp);
   if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("gram: ") + cudaGetErrorString(e));
   return ASCG_OK;
 }

@@ -101,6 +101,21 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
 // Sum the partials in a fixed order; G row-major w x w, both halves.
 cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
 
+// Tensor-core Gram (split-bf16 operands, exact integer sums) for
+// kGramTcMinW <= w <= kMaxW. Below that width the FP64 kernel is faster.
+constexpr int kGramTcMinW = 9;
+int gram_tc_parts(int64_t n);   // CTAs (= partials) of the tensor-core Gram
+bool gram_tc_applies(int w);
+// The tensor-core Gram needs 16-byte aligned columns: Y 16-byte aligned, ldY even.
+bool gram_tc_aligned(const double* Y, int64_t ldY);
+// exp_parts: device int[gram_grid() * kMaxW]; partials as for launch_gram_partial.
+cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, double* partials,
+                           cudaStream_t s);
+// Partials of G with the kernel for this width (FP64 when force_fp64); returns
+// the number of partials through *nparts.
+cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
+                            double* partials, int* nparts, cudaStream_t s);
+
 // Recovery (eq. coords).
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
                            double* x, double* r, double* p, cudaStream_t s);

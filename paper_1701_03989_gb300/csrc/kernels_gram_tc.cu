@@ -1,0 +1,766 @@
+// Gram matrix G = Y^T Y (eq. gram) on the tensor cores.
+//
+// On GB300 the FP64 pipe, not HBM, bounds a direct FP64 Gram: w(w+1)/2 FMAs
+// per row of Y at about 2 DFMA per clock per SM. This kernel moves the
+// products to the fp16 tensor cores with an error-free splitting of the
+// operands (Ozaki, Ogita, Oishi and Rump, "Error-free transformations of
+// matrix multiplication by using fast routines of matrix multiplication",
+// Numer. Algorithms 59, 2012), in the fixed-point form with one exponent per
+// column:
+//
+//  1. E_a is the exponent of the largest entry of column a (|y| < 2^E_a).
+//     Each entry becomes the integer Y = trunc(y 2^(55 - E_a)), |Y| < 2^55,
+//     written in seven balanced base-256 digits d_0 (most significant) ..
+//     d_6, every |d_i| <= 128. A digit is exact in fp16.
+//  2. The tensor cores form the digit products D[(i,a),(j,b)] =
+//     sum_k d_i,a,k d_j,b,k over chunks of 1024 rows of Y with FP32
+//     accumulation. Every product is an integer of magnitude <= 2^14 and a
+//     chunk sum stays <= 2^24, so the FP32 accumulator holds it exactly.
+//  3. Only pairs with i + j <= 7 are kept (the rest weigh below 2^-61
+//     relative to 2^(E_a + E_b) per row). G is symmetric, so each ordered
+//     pair ((i,a),(j,b)) is needed once, for the entry G_ab with a <= b. The
+//     128 digits with i <= 3, a <= 31 (set T0) multiply all 231 digits in
+//     tile 0 (M = 128, N = 240); a pair whose first digit is outside T0 is
+//     read there transposed, except pairs with a top digit (j <= 3) of
+//     column 32 as the partner, which tile 1 (M = 128, N = 16) supplies.
+//     That is 32.8K multiply-adds per row of Y instead of 53K for all pairs.
+//  4. Each needed product, scaled to its level L = i + j, is added to exact
+//     integer sums hi_ab (L <= 3, times 2^(8(3-L))) and lo_ab (L >= 4, times
+//     2^(8(7-L))): per chunk in int64 registers, then into the CTA's sums in
+//     shared memory, kept as three 32-bit words of 17-bit slices each so that
+//     plain 32-bit shared-memory reductions add them exactly. Integer sums do
+//     not depend on the order: the result is deterministic.
+//     G_ab = 2^(E_a + E_b - 14) (hi 2^-24 + lo 2^-56), formed in FP64 once per
+//     CTA; the finalize kernel of the FP64 path adds the per-CTA partials in a
+//     fixed order.
+//
+// Error: truncating y to the grid 2^(E - 55) gives |G^_ab - G_ab| <= about
+// 2^-51 (max|y_a| ||y_b||_1 + max|y_b| ||y_a||_1) + gamma_(parts+1) |y_a|^T |y_b|,
+// a normwise bound of the size of the FP64 rounding error of a dot product.
+//
+// Operand layout: 256 rows of fp16 digits per stage of 64 rows of Y, in
+// 8-row x 16-byte core matrices, K-major with no swizzle (LBO = 128 B along
+// K, SBO = 1024 B between 8-row groups). Row order: T0 i-major (rows 0..127),
+// (i <= 3, 32) (128..131), (i >= 4, 32) (132..134), zeros (135..143),
+// (i >= 4, a <= 31) i-major (144..239), zeros (240..255). Each TMEM load of
+// the drain is then one aligned 16-column block of a single digit level.
+//
+// Pipeline (PTX ISA, tcgen05 and cp.async.bulk.tensor), linked by mbarriers:
+//  - a loader thread issues one 2D tensor-map copy per stage (66 rows x 33
+//    columns of Y; rows past n and columns past w arrive as zeros);
+//  - 17 worker warps turn FP64 into digits (4 rows of a column per thread);
+//    8 of them also drain the TMEM accumulators of the previous chunk;
+//  - one thread issues tcgen05.mma kind::f16 (f16 x f16 -> f32) into one of
+//    two TMEM buffers (tile 0 at 256 p + 0..239, tile 1 at 256 p + 240..255),
+//    so a chunk is drained while the next one is multiplied.
+// All waits are bounded; a wait that runs out writes NaN partials.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_fp16.h>
+#include <math_constants.h>
+
+#include <mutex>
+
+#include "ascg_common.cuh"
+
+namespace ascg {
+namespace {
+
+constexpr int kTW = 33;              // columns (w padded to 33)
+constexpr int kDig = 7;              // digits per entry
+constexpr int kSub = 64;             // rows of Y per stage (MMA K)
+constexpr int kSubPerChunk = 16;
+constexpr int kTChunk = kSub * kSubPerChunk;  // 1024 rows per TMEM accumulation
+constexpr int kDStages = 3;          // digit operand stages
+constexpr int kFStages = 6;          // FP64 staging stages (tensor copies in flight)
+constexpr int kBoxRows = 66;         // rows per tensor copy: column stride 528 B (bank offset)
+constexpr uint32_t kColStride = kBoxRows * 8;
+constexpr uint32_t kFStageBytes = ((kTW * kColStride + 127) / 128) * 128;
+constexpr uint32_t kFBoxBytes = kTW * kColStride;   // bytes one tensor copy delivers
+constexpr uint32_t kLBO = 128;       // bytes between core matrices along K
+constexpr uint32_t kSBO = (kSub / 8) * 128;   // bytes between 8-row groups (1024)
+constexpr uint32_t kDStageBytes = 256 * kSub * 2;  // 32 KB: 256 digit rows x 64 fp16
+constexpr int kN0 = 240, kN1 = 16;   // MMA N of tiles 0 and 1
+constexpr int kTile1Col = 240;       // TMEM column of tile 1 within a buffer
+constexpr int kWorkWarps = 17;       // 544 threads: one 4-row item each (16 x 33 items)
+constexpr int kDrainWarps = 8;       // workers 0..7 also drain
+constexpr int kLoadWarp = 17, kMmaWarp = 18;
+constexpr int kTcThreads = 19 * 32;
+constexpr int kDrainLag = 2;         // drain chunk c after converting 3 stages of chunk c+1
+constexpr long long kWaitLimit = 1ll << 20;  // polls; with the suspend hint a wait ends within ~2 s
+
+// dynamic shared memory layout
+constexpr size_t kDOff = 0;
+constexpr size_t kFOff = kDOff + (size_t)kDStages * kDStageBytes;
+constexpr int kSlices = 3;           // 17-bit slices of an int64 sum, one 32-bit word each
+constexpr size_t kAccOff = kFOff + (size_t)kFStages * kFStageBytes;  // u32 [2 (hi, lo)][3][33][33]
+constexpr size_t kBarOff = kAccOff + 2 * kSlices * 4 * kTW * kTW;
+constexpr int kNumBars = 2 * kFStages + 2 * kDStages + 4;
+constexpr size_t kSlotOff = kBarOff + 8 * kNumBars;
+constexpr size_t kEmaxOff = kSlotOff + 16;
+constexpr size_t kErrOff = kEmaxOff + 4 * kTW;
+constexpr size_t kTcSmem = kErrOff + 16;
+static_assert(kFOff % 1024 == 0 && kFStageBytes % 128 == 0 && kAccOff % 16 == 0 && kBarOff % 8 == 0,
+              "alignment");
+static_assert(kTcSmem <= 227 * 1024, "shared memory per CTA");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start, LBO, SBO (all >> 4),
+// descriptor version 1 at bit 46, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((kLBO >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor of kind::f16: D f32 (bit 4), A and B f16 (format 0),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t instr_desc(int M, int N) {
+  return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// 2D tensor-map copy of the box at (row0, 0) into shared memory; completion
+// counted on the mbarrier's transaction count.
+__device__ __forceinline__ void tensor_g2s(void* dst, const CUtensorMap* map, int row0, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(row0), "r"(0), "r"(smem_u32(bar))
+      : "memory");
+}
+
+// One test of the phase; a thread whose phase is not complete is suspended
+// for up to kSuspendNs (woken early when the phase completes), so waiting
+// warps leave the issue slots to the working ones.
+constexpr uint32_t kSuspendNs = 2000;
+__device__ __forceinline__ int bar_try(uint32_t a, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      "selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(a), "r"(parity), "r"(kSuspendNs)
+      : "memory");
+  return (int)ok;
+}
+
+// Waits until the phase of the given parity has completed. Gives up after
+// kWaitLimit polls or once another role has given up; returns 0 then.
+__device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it) {
+    if (bar_try(a, parity)) return 1;
+    if ((it & 15) == 15 && *err) return 0;
+  }
+  *err = 1;
+  return 0;
+}
+
+// Bounded wait that ignores the error flag: lets copies and MMAs already
+// issued finish before the CTA exits after an error.
+__device__ __forceinline__ void bar_drain(uint64_t* bar, uint32_t parity) {
+  const uint32_t a = smem_u32(bar);
+  for (long long it = 0; it < kWaitLimit; ++it)
+    if (bar_try(a, parity)) return;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+      : "r"(taddr)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+}
+
+// Balanced digits, step 1. With E = emax - 1022 for the column's largest
+// biased exponent emax, Y = trunc(y 2^(55 - E)) (|Y| < 2^55), and
+// Z = Y + sum_{k<7} 128 * 256^k. Byte k of Z (k < 6) is c_k + 128, and
+// Z >> 48 (9 bits) is c_6 + 128, where Y = sum_k c_k 256^k with c_k in
+// [-128, 127] (k < 6) and c_6 in [-128, 128]. Integer operations only.
+__device__ __forceinline__ void split_z(double y, int emax, uint32_t& zlo, uint32_t& zhi) {
+  const int hi = __double2hiint(y);
+  const uint32_t lo = (uint32_t)__double2loint(y);
+  const int e = (hi >> 20) & 0x7ff;
+  const uint32_t mhi = ((uint32_t)hi & 0xFFFFFu) | (e != 0 ? 0x100000u : 0u);
+  // M = m * 8 (56 bits), Y = M >> s with s = emax + 1 - max(e, 1) >= 1
+  const uint32_t Mhi = __funnelshift_l(lo, mhi, 3);
+  const uint32_t Mlo = lo << 3;
+  int s = emax + 1 - (e > 1 ? e : 1);
+  s = s < 63 ? s : 63;
+  uint32_t ylo, yhi;
+  if (s < 32) {
+    ylo = __funnelshift_r(Mlo, Mhi, s);
+    yhi = Mhi >> s;
+  } else {
+    ylo = Mhi >> (s - 32);
+    yhi = 0u;
+  }
+  unsigned long long Y = ((unsigned long long)yhi << 32) | ylo;
+  if (hi < 0) Y = 0ull - Y;
+  const unsigned long long Z = Y + 0x0080808080808080ull;
+  zlo = (uint32_t)Z;
+  zhi = (uint32_t)(Z >> 32);
+}
+
+// Digit c_k of two entries as an fp16 pair (exact): fp16 0x6400 + t is 1024 + t,
+// minus 1152 gives t - 128.
+template <int K>
+__device__ __forceinline__ uint32_t digit_pair(uint32_t zlo0, uint32_t zhi0, uint32_t zlo1, uint32_t zhi1) {
+  uint32_t t;
+  if (K < 4) {
+    t = __byte_perm(zlo0, zlo1, 0x0400 | (K << 8) | K);  // byte K of each at positions 0, 2
+    t = (t & 0x00FF00FFu) | 0x64006400u;
+  } else if (K < 6) {
+    t = __byte_perm(zhi0, zhi1, 0x0400 | ((K - 4) << 8) | (K - 4));
+    t = (t & 0x00FF00FFu) | 0x64006400u;
+  } else {
+    t = (zhi0 >> 16) | (zhi1 & 0xFFFF0000u) | 0x64006400u;
+  }
+  const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&t), __floats2half2_rn(1152.0f, 1152.0f));
+  return *reinterpret_cast<const uint32_t*>(&h);
+}
+
+// Operand row of digit i of column a (see the layout above).
+__device__ __forceinline__ int digit_row(int i, int a) {
+  if (i <= 3) return a <= 31 ? 32 * i + a : 128 + i;
+  return a <= 31 ? 144 + 32 * (i - 4) + a : 132 + (i - 4);
+}
+
+// Converts one stage: rows [row0, row0 + 64) of Y from the FP64 staging box
+// (column a at a * 528 B; zeros past n) into the digit operand. Item (g, a):
+// rows 4 g .. 4 g + 3 of column a, i.e. half a core-matrix row (8 bytes) per
+// digit. Consecutive threads take consecutive columns, so the staging loads
+// (stride 528 B) and the digit stores (consecutive operand rows) do not
+// collide in the shared-memory banks.
+__device__ __forceinline__ void convert_stage(unsigned char* dst, const unsigned char* fst, int w, const int* s_emax,
+                                              int ptid) {
+  const int items = 16 * w;
+  for (int it = ptid; it < items; it += kWorkWarps * 32) {
+    const int g = it / w;
+    const int a = it - g * w;
+    const double2* src = reinterpret_cast<const double2*>(fst + a * kColStride + g * 32);
+    const int emax = s_emax[a];
+    const double2 t0 = src[0], t1 = src[1];
+    uint32_t zlo[4], zhi[4];
+    split_z(t0.x, emax, zlo[0], zhi[0]);
+    split_z(t0.y, emax, zlo[1], zhi[1]);
+    split_z(t1.x, emax, zlo[2], zhi[2]);
+    split_z(t1.y, emax, zlo[3], zhi[3]);
+    unsigned char* base = dst + (g >> 1) * kLBO + (g & 1) * 8;
+#pragma unroll
+    for (int i = 0; i < kDig; ++i) {  // digit i (most significant first) is c_(6-i)
+      uint32_t wd[2];
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const uint32_t a0 = zlo[2 * p], b0 = zhi[2 * p], a1 = zlo[2 * p + 1], b1 = zhi[2 * p + 1];
+        switch (6 - i) {
+          case 6: wd[p] = digit_pair<6>(a0, b0, a1, b1); break;
+          case 5: wd[p] = digit_pair<5>(a0, b0, a1, b1); break;
+          case 4: wd[p] = digit_pair<4>(a0, b0, a1, b1); break;
+          case 3: wd[p] = digit_pair<3>(a0, b0, a1, b1); break;
+          case 2: wd[p] = digit_pair<2>(a0, b0, a1, b1); break;
+          case 1: wd[p] = digit_pair<1>(a0, b0, a1, b1); break;
+          default: wd[p] = digit_pair<0>(a0, b0, a1, b1); break;
+        }
+      }
+      const int R = digit_row(i, a);
+      *reinterpret_cast<uint2*>(base + (R >> 3) * kSBO + (R & 7) * 16) = make_uint2(wd[0], wd[1]);
+    }
+  }
+}
+
+// Adds an int64 v (|v| < 2^50) to the CTA's sum at word index idx of the slice
+// arrays: v = s2 2^34 + s1 2^17 + s0 with s0, s1 in [0, 2^17) and |s2| < 2^16,
+// each added by a 32-bit shared-memory reduction. Up to 2^15 additions per
+// sum stay exact.
+__device__ __forceinline__ void slice_add(uint32_t* acc, int idx, long long v) {
+  constexpr int kPlane = kTW * kTW;
+  atomicAdd(acc + idx, (uint32_t)(v & 0x1FFFF));
+  atomicAdd(acc + kPlane + idx, (uint32_t)((v >> 17) & 0x1FFFF));
+  atomicAdd(reinterpret_cast<int*>(acc) + 2 * kPlane + idx, (int)(v >> 34));
+}
+
+// The exact int64 value of a sliced sum.
+__device__ __forceinline__ long long slice_value(const uint32_t* acc, int idx) {
+  constexpr int kPlane = kTW * kTW;
+  return ((long long)reinterpret_cast<const int*>(acc)[2 * kPlane + idx] << 34) +
+         ((long long)acc[kPlane + idx] << 17) + (long long)acc[idx];
+}
+
+// Scales a product to its level L = i + j and adds it to the hi/lo sums.
+__device__ __forceinline__ void level_add(long long& hi, long long& lo, int L, uint32_t fbits, int times) {
+  const long long d = (long long)__float2int_rn(__uint_as_float(fbits)) * times;
+  if (L <= 3)
+    hi += d << (8 * (3 - L));
+  else if (L <= 7)
+    lo += d << (8 * (7 - L));
+}
+
+// Drain of 4 columns of tile 0 at TMEM column col, whose operand rows are
+// digits (J, B0 + t), t = 0..3. The thread is T0 digit (i, a); for column b
+// its product stands for ((i,a),(J,b)), counted when a <= b, and, when (J,b)
+// is not in T0 (FAR), also for ((J,b),(i,a)), counted when b <= a. Either way
+// it belongs to the entry (min(a,b), max(a,b)), summed in slot t.
+template <int J, int B0, bool FAR>
+__device__ __forceinline__ void drain_cols(uint32_t taddr, uint32_t col, int i, int a, long long (&hi)[4],
+                                          long long (&lo)[4]) {
+  uint32_t r[4];
+  tmem_ld4(taddr + col, r);
+  const int L = i + J;
+  if (L > 7) return;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int b = B0 + t;
+    const int times = (a <= b ? 1 : 0) + (FAR && b <= a ? 1 : 0);
+    level_add(hi[t], lo[t], L, r[t], times);
+  }
+}
+
+// Entries b = B0 .. B0 + 3 of T0 digit (i, a): all seven digit levels j of b,
+// then one sliced addition per entry.
+template <int B0>
+__device__ __forceinline__ void drain_t0_pass(uint32_t taddr, uint32_t cb, int i, int a, int w, uint32_t* acc_hi,
+                                              uint32_t* acc_lo) {
+  long long hi[4], lo[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) hi[k] = lo[k] = 0;
+  drain_cols<0, B0, false>(taddr, cb + 0 + B0, i, a, hi, lo);
+  drain_cols<1, B0, false>(taddr, cb + 32 + B0, i, a, hi, lo);
+  drain_cols<2, B0, false>(taddr, cb + 64 + B0, i, a, hi, lo);
+  drain_cols<3, B0, false>(taddr, cb + 96 + B0, i, a, hi, lo);
+  drain_cols<4, B0, true>(taddr, cb + 144 + B0, i, a, hi, lo);
+  drain_cols<5, B0, true>(taddr, cb + 176 + B0, i, a, hi, lo);
+  drain_cols<6, B0, true>(taddr, cb + 208 + B0, i, a, hi, lo);
+  if (a < w) {
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int b = B0 + t;
+      if (b >= w) continue;
+      const int idx = (a < b ? a : b) * kTW + (a < b ? b : a);
+      if (hi[t] != 0) slice_add(acc_hi, idx, hi[t]);
+      if (lo[t] != 0) slice_add(acc_lo, idx, lo[t]);
+    }
+  }
+}
+
+// Entry b = 32 of T0 digit (i, a): operand rows 128..134 hold digits (j, 32),
+// j = 0..6, and b = 32 > a.
+__device__ __forceinline__ void drain_t0_b32(uint32_t taddr, uint32_t cb, int i, int a, int w, uint32_t* acc_hi,
+                                             uint32_t* acc_lo) {
+  uint32_t r[8];
+  tmem_ld8(taddr + cb + 128, r);
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) level_add(hi, lo, i + j, r[j], 1);
+  if (a < w && w == kTW) {
+    if (hi != 0) slice_add(acc_hi, a * kTW + 32, hi);
+    if (lo != 0) slice_add(acc_lo, a * kTW + 32, lo);
+  }
+}
+
+// Tile 1, operand row R = 128 + 32 quarter + lane: columns 0..3 hold
+// D[row, (j, 32)], j = 0..3. Row (i <= 3, 32): ((i,32),(j,32)) -> G_32,32.
+// Row (i >= 4, 32): also ((j,32),(i,32)), so twice. Row (i >= 4, a <= 31):
+// ((i,a),(j,32)) -> G_a,32. Slot 0 sums G_a,32, slot 1 sums G_32,32.
+__device__ __forceinline__ void drain_t1(uint32_t taddr, uint32_t cb, int R, long long (&hi2)[2],
+                                         long long (&lo2)[2]) {
+  uint32_t r[16];
+  tmem_ld16(taddr + cb + kTile1Col, r);
+  int i = 0, slot = -1, times = 1;
+  if (R < 132) {
+    i = R - 128;
+    slot = 1;
+  } else if (R < 135) {
+    i = 4 + (R - 132);
+    slot = 1;
+    times = 2;
+  } else if (R >= 144 && R < 240) {
+    i = 4 + (R - 144) / 32;
+    slot = 0;
+  }
+  if (slot < 0) return;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    if (slot == 0)
+      level_add(hi2[0], lo2[0], i + j, r[j], times);
+    else
+      level_add(hi2[1], lo2[1], i + j, r[j], times);
+  }
+}
+
+// Drains the accumulators of chunk c (TMEM buffer c & 1): sums per entry in
+// registers, then one sliced addition per entry into the CTA's sums
+// (acc_hi, acc_lo). Lanes of a warp have distinct a, so their entries differ.
+__device__ __forceinline__ bool drain_chunk(uint32_t c, int w, int half, int quarter, int lane, uint32_t taddr,
+                                            uint64_t* acc_full, uint64_t* acc_empty, volatile int* s_err,
+                                            uint32_t* acc_hi, uint32_t* acc_lo) {
+  const uint32_t p = c & 1;
+  if (!bar_wait(acc_full + p, (c >> 1) & 1, s_err)) return false;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t cb = 256u * p;
+  const int a = lane;
+  if (half == 0) {
+    drain_t0_pass<0>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<4>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<8>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<12>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+  } else {
+    drain_t0_pass<16>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<20>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<24>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_pass<28>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    drain_t0_b32(taddr, cb, quarter, a, w, acc_hi, acc_lo);
+    long long hi2[2] = {0, 0}, lo2[2] = {0, 0};
+    drain_t1(taddr, cb, 128 + quarter * 32 + lane, hi2, lo2);
+    if (w == kTW) {
+      const int R = 128 + quarter * 32 + lane;
+      if (R >= 144 && R < 240) {
+        const int a2 = (R - 144) % 32;
+        if (hi2[0] != 0) slice_add(acc_hi, a2 * kTW + 32, hi2[0]);
+        if (lo2[0] != 0) slice_add(acc_lo, a2 * kTW + 32, lo2[0]);
+      }
+      if (R < 135) {
+        if (hi2[1] != 0) slice_add(acc_hi, 32 * kTW + 32, hi2[1]);
+        if (lo2[1] != 0) slice_add(acc_lo, 32 * kTW + 32, lo2[1]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncwarp();
+  if (lane == 0) bar_arrive(acc_empty + p);
+  return true;
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
+                   double* __restrict__ partials) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* dstage = smem + kDOff;
+  unsigned char* fstage = smem + kFOff;
+  uint32_t* acc_hi = reinterpret_cast<uint32_t*>(smem + kAccOff);  // [3][33][33] slices
+  uint32_t* acc_lo = acc_hi + kSlices * kTW * kTW;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
+  uint64_t* f_full = bars;                  // tensor copy landed (tx count)
+  uint64_t* f_empty = bars + kFStages;      // workers done reading
+  uint64_t* d_full = bars + 2 * kFStages;   // workers done writing digits
+  uint64_t* d_empty = d_full + kDStages;    // MMAs done reading digits
+  uint64_t* acc_full = d_empty + kDStages;  // [2] a chunk's MMAs are complete
+  uint64_t* acc_empty = acc_full + 2;       // [2] its accumulators are drained
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kSlotOff);
+  int* s_emax = reinterpret_cast<int*>(smem + kEmaxOff);
+  volatile int* s_err = reinterpret_cast<volatile int*>(smem + kErrOff);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // digit rows never written stay zero; the sums start at zero
+  for (uint32_t o = tid * 16; o < kDStages * kDStageBytes; o += kTcThreads * 16)
+    *reinterpret_cast<uint4*>(dstage + o) = make_uint4(0, 0, 0, 0);
+  for (int k = tid; k < 2 * kSlices * kTW * kTW; k += kTcThreads) acc_hi[k] = 0u;
+  if (tid < kTW) s_emax[tid] = tid < w ? col_emax[tid] : 0;
+  if (tid == 0) {
+    *s_err = 0;
+    for (int k = 0; k < kFStages; ++k) {
+      bar_init(f_full + k, 1);
+      bar_init(f_empty + k, kWorkWarps);
+    }
+    for (int k = 0; k < kDStages; ++k) {
+      bar_init(d_full + k, kWorkWarps);
+      bar_init(d_empty + k, 1);
+    }
+    for (int k = 0; k < 2; ++k) {
+      bar_init(acc_full + k, 1);
+      bar_init(acc_empty + k, kDrainWarps);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  const int64_t chunks = (n + kTChunk - 1) / kTChunk;
+  uint32_t armed = 0;   // loader: stages whose copies were issued
+  uint32_t issued = 0;  // MMA issuer: stages whose MMAs were issued
+
+  if (warp < kWorkWarps) {
+    // ---- workers: FP64 -> digits; warps 0..7 also drain the previous chunk ----
+    const bool drains = warp < kDrainWarps;
+    const int half = warp >> 2, quarter = warp & 3;
+    const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16);
+    uint32_t t = 0, cu = 0, drained = 0;
+    for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x, ++cu) {
+      const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
+      const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
+      for (int sub = 0; sub < nsub; ++sub, ++t) {
+        const int fs = (int)(t % kFStages), ds = (int)(t % kDStages);
+        if (!bar_wait(f_full + fs, (t / kFStages) & 1, s_err)) goto done;
+        if (t >= kDStages && !bar_wait(d_empty + ds, (t / kDStages - 1) & 1, s_err)) goto done;
+        convert_stage(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, w, s_emax, tid);
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          bar_arrive(f_empty + fs);
+          bar_arrive(d_full + ds);
+        }
+        if (drains && sub == kDrainLag)
+          for (; drained < cu; ++drained)
+            if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, acc_hi, acc_lo))
+              goto done;
+      }
+    }
+    if (drains)
+      for (; drained < cu; ++drained)
+        if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, acc_hi, acc_lo))
+          goto done;
+  } else if (warp == kLoadWarp) {
+    // ---- loader: one tensor copy per stage ----
+    if (lane == 0) {
+      uint32_t t = 0;
+      for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+        const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
+        const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
+        for (int sub = 0; sub < nsub; ++sub, ++t) {
+          const int fs = (int)(t % kFStages);
+          if (t >= kFStages && !bar_wait(f_empty + fs, (t / kFStages - 1) & 1, s_err)) goto done;
+          bar_expect_tx(f_full + fs, kFBoxBytes);
+          tensor_g2s(fstage + fs * kFStageBytes, &ymap, (int)(ch * kTChunk + (int64_t)sub * kSub), f_full + fs);
+          armed = t + 1;
+        }
+      }
+    }
+  } else if (warp == kMmaWarp) {
+    // ---- MMA issue ----
+    if (lane == 0) {
+      uint32_t t = 0, cu = 0;
+      for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x, ++cu) {
+        const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
+        const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
+        const uint32_t p = cu & 1;
+        if (cu >= 2 && !bar_wait(acc_empty + p, ((cu >> 1) - 1) & 1, s_err)) goto done;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d0 = tbase + 256u * p;
+        for (int sub = 0; sub < nsub; ++sub, ++t) {
+          const int ds = (int)(t % kDStages);
+          if (!bar_wait(d_full + ds, (t / kDStages) & 1, s_err)) goto done;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t sb = smem_u32(dstage + ds * kDStageBytes);
+#pragma unroll
+          for (int ks = 0; ks < kSub / 16; ++ks) {
+            const uint32_t acc = (sub > 0 || ks > 0) ? 1u : 0u;
+            const uint64_t rows0 = smem_desc(sb + ks * 2 * kLBO);               // operand rows 0..
+            const uint64_t rows128 = smem_desc(sb + 16 * kSBO + ks * 2 * kLBO);  // operand rows 128..
+            mma_f16(d0, rows0, rows0, instr_desc(128, kN0), acc);
+            mma_f16(d0 + kTile1Col, rows128, rows128, instr_desc(128, kN1), acc);
+          }
+          mma_commit(d_empty + ds);
+          issued = t + 1;
+        }
+        mma_commit(acc_full + p);
+      }
+    }
+  }
+done:
+  if (*s_err) {
+    // error path: let the copies and MMAs already in flight land first
+    if (warp == kLoadWarp && lane == 0)
+      for (uint32_t k = armed > (uint32_t)kFStages ? armed - kFStages : 0; k < armed; ++k)
+        bar_drain(f_full + k % kFStages, (k / kFStages) & 1);
+    if (warp == kMmaWarp && lane == 0 && issued > 0)
+      bar_drain(d_empty + (issued - 1) % kDStages, ((issued - 1) / kDStages) & 1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  const int ok = !*s_err;
+  const int np = w * (w + 1) / 2;
+  for (int p = tid; p < np; p += kTcThreads) {
+    int a = 0, rem = p;
+    while (rem >= w - a) {
+      rem -= w - a;
+      ++a;
+    }
+    const int b = a + rem;
+    double v;
+    if (!ok || s_emax[a] == 0x7ff || s_emax[b] == 0x7ff) {
+      v = CUDART_NAN;
+    } else {
+      const long long hi = slice_value(acc_hi, a * kTW + b), lo = slice_value(acc_lo, a * kTW + b);
+      // G_ab = 2^(E_a + E_b - 14) (hi 2^-24 + lo 2^-56), E = emax - 1022
+      const double s = ldexp((double)hi, -24) + ldexp((double)lo, -56);
+      v = ldexp(s, s_emax[a] + s_emax[b] - 2058);
+    }
+    partials[(int64_t)blockIdx.x * np + p] = v;
+  }
+  if (warp == kMmaWarp) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
+  }
+}
+
+// Largest biased exponent of each column, reduced into col_emax (zeroed
+// before the launch) with one atomicMax per column and CTA. Rows are split
+// into even-sized ranges; 16-byte loads, four in flight per thread.
+constexpr int kExpBlocks = 1216;
+__global__ void __launch_bounds__(256) col_exponent_kernel(int64_t n, int w, const double* __restrict__ Y,
+                                                           int64_t ldY, int* __restrict__ col_emax) {
+  __shared__ unsigned red[8][kTW];
+  const int64_t per = (((n + gridDim.x - 1) / gridDim.x) + 1) & ~1ll;
+  const int64_t r0 = (int64_t)blockIdx.x * per;
+  const int64_t r1 = n < r0 + per ? n : r0 + per;
+  const int64_t full = r1 > r0 ? (r1 - r0) >> 1 : 0;  // whole double2 slots
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto ex = [](double v) { return ((unsigned)__double2hiint(v) >> 20) & 0x7ffu; };
+  for (int a = 0; a < w; ++a) {
+    const double2* col = reinterpret_cast<const double2*>(Y + (int64_t)a * ldY + r0);
+    unsigned m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+    int64_t q = threadIdx.x;
+    for (; q + 768 < full; q += 1024) {
+      const double2 v0 = __ldcs(col + q), v1 = __ldcs(col + q + 256), v2 = __ldcs(col + q + 512),
+                    v3 = __ldcs(col + q + 768);
+      m0 = max(m0, max(ex(v0.x), ex(v0.y)));
+      m1 = max(m1, max(ex(v1.x), ex(v1.y)));
+      m2 = max(m2, max(ex(v2.x), ex(v2.y)));
+      m3 = max(m3, max(ex(v3.x), ex(v3.y)));
+    }
+    for (; q < full; q += 256) {
+      const double2 v = __ldcs(col + q);
+      m0 = max(m0, max(ex(v.x), ex(v.y)));
+    }
+    if (threadIdx.x == 0 && r0 + 2 * full < r1) m0 = max(m0, ex(Y[(int64_t)a * ldY + r0 + 2 * full]));
+    const unsigned m = __reduce_max_sync(0xffffffffu, max(max(m0, m1), max(m2, m3)));
+    if (lane == 0) red[warp][a] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < w) {
+    unsigned m = 0;
+    for (int g = 0; g < 8; ++g) m = max(m, red[g][threadIdx.x]);
+    if (m > 0) atomicMax(col_emax + threadIdx.x, (int)m);
+  }
+}
+
+// cuTensorMapEncodeTiled, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::mutex g_encode_mu;
+
+cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int64_t ldY) {
+  {
+    std::lock_guard<std::mutex> lock(g_encode_mu);
+    if (!g_encode) {
+      void* fn = nullptr;
+      cudaDriverEntryPointQueryResult q;
+      cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+      if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+      g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+  }
+  const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)w};
+  const cuuint64_t strides[1] = {(cuuint64_t)ldY * sizeof(double)};
+  const cuuint32_t box[2] = {(cuuint32_t)kBoxRows, (cuuint32_t)kTW};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(Y), dims, strides, box,
+                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int g_tc_attr_dev = -1;
+
+}  // namespace
+
+int gram_tc_parts(int64_t n) {
+  const int64_t chunks = (n + kTChunk - 1) / kTChunk;
+  const int g = gram_grid();
+  return (int)(chunks < g ? chunks : g);
+}
+
+bool gram_tc_applies(int w) { return w >= kGramTcMinW && w <= kTW; }
+
+bool gram_tc_aligned(const double* Y, int64_t ldY) {
+  return (reinterpret_cast<uintptr_t>(Y) & 15) == 0 && (ldY & 1) == 0;
+}
+
+cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, double* partials,
+                           cudaStream_t s) {
+  if (w < 1 || w > kTW || n < 1 || n > 0x7fffffffll || !gram_tc_aligned(Y, ldY)) return cudaErrorInvalidValue;
+  const int parts = gram_tc_parts(n);
+  // a sliced sum takes <= 10 additions per chunk: at most 2^11 chunks per CTA
+  if ((n + kTChunk - 1) / kTChunk > (int64_t)parts * 2048) return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (g_tc_attr_dev != dev) {
+    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    g_tc_attr_dev = dev;
+  }
+  CUtensorMap map;
+  e = encode_map(&map, Y, n, w, ldY);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(exp_parts, 0, sizeof(int) * kTW, s);
+  if (e != cudaSuccess) return e;
+  const int64_t eb = (n + 255) / 256;
+  col_exponent_kernel<<<(int)(eb < kExpBlocks ? eb : kExpBlocks), 256, 0, s>>>(n, w, Y, ldY, exp_parts);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
+                            double* partials, int* nparts, cudaStream_t s) {
+  if (!force_fp64 && gram_tc_applies(w) && gram_tc_aligned(Y, ldY)) {
+    *nparts = gram_tc_parts(n);
+    return launch_gram_tc(n, w, Y, ldY, exp_parts, partials, s);
+  }
+  *nparts = gram_parts(n);
+  return launch_gram_partial(n, w, Y, ldY, partials, s);
+}
+
+}  // namespace ascg

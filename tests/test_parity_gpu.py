@@ -160,6 +160,78 @@ def test_gram_parity(env, n, w):
     assert torch.equal(G, G2)   # fixed reduction order: bitwise reproducible
 
 
+def tc_gram_bound(Y, parts=160):
+    """Error bound of the tensor-core Gram (w >= 9): entries of column a are
+    truncated to the grid 2^(E_a - 55), 2^(E_a - 1) <= max|y_a| < 2^E_a, the digit
+    products are summed exactly, and the per-CTA partials are added in FP64."""
+    absY = np.abs(Y)
+    mx, l1 = absY.max(axis=1), absY.sum(axis=1)
+    return 2.0 ** -51 * (mx[:, None] * l1[None, :] + l1[:, None] * mx[None, :]) + 2 * gamma_n(parts + 8) * (absY @ absY.T)
+
+
+def _gram_dev(torch, Y, ld):
+    w, n = Y.shape
+    Yd = torch.zeros(w * ld + 2, dtype=torch.float64, device="cuda")
+    for c in range(w):
+        Yd[c * ld:c * ld + n] = dev(torch, Y[c])
+    return Yd
+
+
+@pytest.mark.parametrize("n,w", [(300001, 33), (37, 17), (1025, 9), (65, 33)])
+def test_gram_tensor_wide_range(env, n, w):
+    """Columns whose entries span 60 orders of magnitude, exact zeros, denormals
+    and ragged n (not a multiple of 64 or 1024 rows): the tensor-core Gram stays
+    within its derived bound of the FP64 oracle (whose own error is added)."""
+    P, torch = env
+    rng = np.random.default_rng(n + 7 * w)
+    Y = rng.standard_normal((w, n)) * 10.0 ** rng.uniform(-30, 30, (1, n)) * np.logspace(0, 8, w)[:, None]
+    Y[0, ::3] = 0.0
+    Y[1, :] = rng.standard_normal(n) * 1e-310          # a column of denormals
+    Y[2, :] = 0.0                                      # a zero column
+    ld = n + (n % 2)
+    Yd = _gram_dev(torch, Y, ld)
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, ld, G)
+    Gg = G.cpu().numpy().reshape(w, w)
+    Go = O.gram(Y.T)
+    bound = tc_gram_bound(Y) + 2 * gamma_n(n) * (np.abs(Y) @ np.abs(Y).T)
+    assert np.all(np.isfinite(Gg))
+    assert np.all(np.abs(Gg - Go) <= bound)
+    assert np.array_equal(Gg[2], np.zeros(w)) and np.array_equal(Gg[:, 2], np.zeros(w))
+    assert np.array_equal(Gg, Gg.T)
+
+
+def test_gram_tensor_nan_column(env):
+    """A column holding NaN gives NaN in its row and column only."""
+    P, torch = env
+    rng = np.random.default_rng(5)
+    n, w = 4099, 33
+    Y = rng.standard_normal((w, n))
+    Y[7, 1234] = np.nan
+    Yd = _gram_dev(torch, Y, n + 1)
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, n + 1, G)
+    Gg = G.cpu().numpy().reshape(w, w)
+    assert np.all(np.isnan(Gg[7])) and np.all(np.isnan(Gg[:, 7]))
+    keep = [c for c in range(w) if c != 7]
+    Gk, Ok, Yk = Gg[np.ix_(keep, keep)], O.gram(Y[keep].T), Y[keep]
+    assert np.all(np.abs(Gk - Ok) <= tc_gram_bound(Yk) + 2 * gamma_n(n) * (np.abs(Yk) @ np.abs(Yk).T))
+
+
+def test_gram_unaligned_uses_fp64(env):
+    """An odd leading dimension rules out the tensor copies; the FP64 kernel then
+    runs, and its element-wise bound 2 gamma_n |Y|^T |Y| holds."""
+    P, torch = env
+    rng = np.random.default_rng(6)
+    n, w = 5001, 17
+    Y = rng.standard_normal((w, n)) * np.logspace(0, 4, w)[:, None]
+    Yd = _gram_dev(torch, Y, n)   # ld = n odd
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, n, G)
+    Gg = G.cpu().numpy().reshape(w, w)
+    assert np.all(np.abs(Gg - O.gram(Y.T)) <= 2 * gamma_n(n) * (np.abs(Y) @ np.abs(Y).T))
+
+
 # ---------------------------------------------------------------------------
 # a6-a8: block controller on a given Gram matrix
 # ---------------------------------------------------------------------------
@@ -321,6 +393,8 @@ SOLVES = [
     ("diffusion_63", dict(method="adaptive", basis="newton", s_max=12, newton_warmup=24), 1e-10),
     ("banded_3001", dict(method="adaptive", basis="monomial", s_max=10), 1e-8),
     ("banded_3001", dict(method="adaptive", basis="chebyshev", s_max=10), 1e-12),
+    # the same Chebyshev solve with the Gram matrix formed by FP64 FMAs instead of the tensor cores
+    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_fp64=True), 1e-12),
 ]
 
 
