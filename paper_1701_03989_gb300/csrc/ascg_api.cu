@@ -71,6 +71,8 @@ struct Workspace {
   double* partials = nullptr;
   int64_t partials_cap = 0;
   int* expp = nullptr;      // column exponents of the tensor-core Gram, gram_grid() x kMaxW
+  int* emax_part = nullptr; // per-warp column exponents from the matrix powers steps, kMaxW x emax_ld
+  int64_t emax_ld = 0;
   unsigned* counter = nullptr;
   double* G = nullptr;      // kMaxW^2
   double* coords = nullptr; // 3 kMaxW
@@ -94,7 +96,7 @@ struct Workspace {
   bool events = false;
 
   void release() {
-    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(counter);
+    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(emax_part); dev_free(counter);
     dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
     dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
     dev_free(dtils); dev_free(oscaled[0]); dev_free(oscaled[1]);
@@ -106,7 +108,7 @@ struct Workspace {
     if (events)
       for (auto& e : ev) cudaEventDestroy(e);
     events = false;
-    n = 0; wcols = 0; ldY = 0; partials_cap = 0; res_cap = 0; ab_cap = 0;
+    n = 0; wcols = 0; ldY = 0; partials_cap = 0; res_cap = 0; ab_cap = 0; emax_ld = 0;
   }
 };
 
@@ -236,6 +238,12 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     w.partials_cap = pcap;
   }
   if (!w.expp) ASCG_TRY(dev_alloc(&w.expp, (size_t)gram_grid() * kMaxW));
+  if (wcols > 2 && w.emax_ld < round_up((n + 31) / 32, 4)) {
+    dev_free(w.emax_part);
+    w.emax_ld = round_up((n + 31) / 32, 4);  // int4 rows; entries past the warp count stay zero
+    ASCG_TRY(dev_alloc(&w.emax_part, (size_t)kMaxW * w.emax_ld));
+    ASCG_CUDA(cudaMemset(w.emax_part, 0, sizeof(int) * kMaxW * w.emax_ld));
+  }
   if (wcols > 2 && !w.dtils) {
     ASCG_TRY(dev_alloc(&w.dtils, (size_t)kMaxS * n));
     ASCG_TRY(dev_alloc(&w.oscaled[0], (size_t)op->o_len));
@@ -484,17 +492,24 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       ASCG_CUDA(cudaMemcpyAsync(w.bst, &hb, sizeof(BlockState), cudaMemcpyHostToDevice, s));
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
+      // the steps also record each basis column's largest exponent for the tensor-core Gram
+      const bool tc_gram = !gram_fp64 && gram_tc_applies(wb) && gram_tc_aligned(w.Y, w.ldY);
       for (int j = 0; j < sbar; ++j) {
-        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], w.Y, w.ldY, j, 1, j < sbar - 1, s));
+        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], w.Y, w.ldY, j, 1, j < sbar - 1,
+                                        tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
+      }
+      if (tc_gram) {
+        ASCG_CUDA(launch_emax_reduce(w.emax_part, w.emax_ld, n, wb, w.expp, s));
+        res->launches += 1;
       }
       res->launches += sbar;
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
       // Gram: the block's one grid-wide reduction
       int nparts = 0;
-      ASCG_CUDA(launch_gram_any(n, wb, w.Y, w.ldY, gram_fp64, w.expp, w.partials, &nparts, s));
+      ASCG_CUDA(launch_gram_any(n, wb, w.Y, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
       ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
-      res->launches += (!gram_fp64 && gram_tc_applies(wb)) ? 3 : 2;
+      res->launches += 2;
       res->grid_reductions += 1;
       if (o.method == ASCG_ADAPTIVE) {
         ASCG_CUDA(launch_kappa(w.G, w.bst, sbar, s));
@@ -780,7 +795,7 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
   if (rs == ASCG_OK) rs = prepare_steps(op, theta, sigma, gamma, s, dtils, osc, steps, st, &nl);
   cudaError_t e = cudaSuccess;
   for (int j = 0; rs == ASCG_OK && j < s && e == cudaSuccess; ++j)
-    e = launch_mpk_split_step(op->split(), steps[j], Y, ldY, j, 1, j < s - 1, st);
+    e = launch_mpk_split_step(op->split(), steps[j], Y, ldY, j, 1, j < s - 1, nullptr, 0, st);
   if (e == cudaSuccess && rs == ASCG_OK) e = cudaStreamSynchronize(st);
   cudaFree(dtils);
   cudaFree(osc[0]);
@@ -803,7 +818,7 @@ ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G,
     cudaFree(partials);
     return rs;
   }
-  cudaError_t e = launch_gram_any(n, w, Y, ldY, false, expp, partials, &parts, s);
+  cudaError_t e = launch_gram_any(n, w, Y, ldY, false, expp, false, partials, &parts, s);
   if (e == cudaSuccess) e = launch_gram_finalize(w, partials, parts, G, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(partials);

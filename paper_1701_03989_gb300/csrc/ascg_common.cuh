@@ -87,8 +87,15 @@ struct StepOp {
   double sig;           // sig_j (0 for j = 0)
 };
 // Forms column 2(j+1) from 2j, 2(j-1) if do_p, and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
+// emax_part (device int[kMaxW * emax_ld] or nullptr, emax_ld >= ceil(n/32), a
+// multiple of 4, entries past ceil(n/32) zero):
+// per warp of 32 rows, the largest biased exponent of each column written (for
+// j = 0 also of columns 0 and 1), at [col * emax_ld + warp].
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
-                                  int do_r, cudaStream_t s);
+                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s);
+// col_emax[c] = max_k emax_part[c * emax_ld + k] for c < w, k < ceil(n/32).
+cudaError_t launch_emax_reduce(const int* emax_part, int64_t emax_ld, int64_t n, int w, int* col_emax,
+                               cudaStream_t s);
 // dst[i] = (src[i] - theta) * scale, for i < n
 cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, double scale, double* dst,
                                cudaStream_t s);
@@ -108,13 +115,15 @@ int gram_tc_parts(int64_t n);   // CTAs (= partials) of the tensor-core Gram
 bool gram_tc_applies(int w);
 // The tensor-core Gram needs 16-byte aligned columns: Y 16-byte aligned, ldY even.
 bool gram_tc_aligned(const double* Y, int64_t ldY);
-// exp_parts: device int[gram_grid() * kMaxW]; partials as for launch_gram_partial.
-cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, double* partials,
-                           cudaStream_t s);
+// col_emax: device int[kMaxW], the largest biased exponent of each column;
+// computed here unless emax_ready (then it already holds them, e.g. from the
+// matrix powers kernel). partials as for launch_gram_partial.
+cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, bool emax_ready,
+                           double* partials, cudaStream_t s);
 // Partials of G with the kernel for this width (FP64 when force_fp64); returns
 // the number of partials through *nparts.
-cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
-                            double* partials, int* nparts, cudaStream_t s);
+cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
+                            bool emax_ready, double* partials, int* nparts, cudaStream_t s);
 
 // Recovery (eq. coords).
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,

@@ -86,7 +86,7 @@ extern "C" ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int6
   // them, so nothing left in the array by an earlier call is ever read.
   cudaStream_t s = (cudaStream_t)cuda_stream;
   int used = 0;
-  e = launch_gram_any(n, w, Y, ldY, false, exp_scratch, scratch, &used, s);
+  e = launch_gram_any(n, w, Y, ldY, false, exp_scratch, false, scratch, &used, s);
   if (e == cudaSuccess) e = launch_gram_finalize(w, scratch, used, G, s);
   if (e != cudaSuccess)
     return fail(ASCG_ERR_CUDA, std::string("ascg_gram_noalloc: launch: ") + cudaGetErrorString(e));

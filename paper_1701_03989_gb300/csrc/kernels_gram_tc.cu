@@ -726,8 +726,8 @@ bool gram_tc_aligned(const double* Y, int64_t ldY) {
   return (reinterpret_cast<uintptr_t>(Y) & 15) == 0 && (ldY & 1) == 0;
 }
 
-cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, double* partials,
-                           cudaStream_t s) {
+cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, bool emax_ready,
+                           double* partials, cudaStream_t s) {
   if (w < 1 || w > kTW || n < 1 || n > 0x7fffffffll || !gram_tc_aligned(Y, ldY)) return cudaErrorInvalidValue;
   const int parts = gram_tc_parts(n);
   // a sliced sum takes <= 10 additions per chunk: at most 2^11 chunks per CTA
@@ -743,21 +743,23 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
   CUtensorMap map;
   e = encode_map(&map, Y, n, w, ldY);
   if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(exp_parts, 0, sizeof(int) * kTW, s);
-  if (e != cudaSuccess) return e;
-  const int64_t eb = (n + 255) / 256;
-  col_exponent_kernel<<<(int)(eb < kExpBlocks ? eb : kExpBlocks), 256, 0, s>>>(n, w, Y, ldY, exp_parts);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  if (!emax_ready) {
+    e = cudaMemsetAsync(exp_parts, 0, sizeof(int) * kTW, s);
+    if (e != cudaSuccess) return e;
+    const int64_t eb = (n + 255) / 256;
+    col_exponent_kernel<<<(int)(eb < kExpBlocks ? eb : kExpBlocks), 256, 0, s>>>(n, w, Y, ldY, exp_parts);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
   gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials);
   return cudaGetLastError();
 }
 
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
-                            double* partials, int* nparts, cudaStream_t s) {
+                            bool emax_ready, double* partials, int* nparts, cudaStream_t s) {
   if (!force_fp64 && gram_tc_applies(w) && gram_tc_aligned(Y, ldY)) {
     *nparts = gram_tc_parts(n);
-    return launch_gram_tc(n, w, Y, ldY, exp_parts, partials, s);
+    return launch_gram_tc(n, w, Y, ldY, exp_parts, emax_ready, partials, s);
   }
   *nparts = gram_parts(n);
   return launch_gram_partial(n, w, Y, ldY, partials, s);

@@ -21,41 +21,113 @@ namespace ascg {
 
 namespace {
 
-__global__ void __launch_bounds__(kSpmvRows) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
+__device__ __forceinline__ unsigned biased_exp(double v) { return ((unsigned)__double2hiint(v) >> 20) & 0x7ffu; }
+
+// emax_part (optional, int[kMaxW][emax_ld]): lane 0 of each warp stores the
+// warp's largest biased exponent of each column written (and, for j = 0, of
+// the input columns 0 and 1) at emax_part[col * emax_ld + warp]; plain stores,
+// no synchronisation. emax_reduce_kernel folds them per column for the
+// tensor-core Gram.
+// EMAX: record exponents (emax_part); both variants keep 32 registers, i.e.
+// 8 CTAs (64 warps) per SM, which the FP64 latency of this kernel needs.
+template <bool EMAX>
+__global__ void __launch_bounds__(kSpmvRows, 8) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
                                                                    const double* __restrict__ dtil, double sig,
                                                                    int use_sig, double* __restrict__ Y, int64_t ldY,
-                                                                   int j, int do_p, int do_r) {
+                                                                   int j, int do_p, int do_r, int* emax_part,
+                                                                   int64_t emax_ld) {
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
-  if (row >= O.n) return;
-  const double* pj = Y + (int64_t)(2 * j) * ldY;
-  const double* rj = Y + (int64_t)(2 * j + 1) * ldY;
-  const int64_t sl = row >> 5;
-  const int l = (int)(row & 31);
-  const int64_t b = O.ptr[sl];
-  const int width = (int)((O.ptr[sl + 1] - b) >> 5);
-  const double* v = oval + b + l;
-  const int32_t* c = O.col + b + l;
-  const double dt = dtil[row];
-  double tp = dt * pj[row];
-  if (do_r) {
-    double tr = dt * rj[row];
-    for (int k = 0; k < width; ++k) {
-      const double a = __ldg(v + kSlice * k);
-      const int cc = __ldg(c + kSlice * k);
-      tp = fma(a, __ldg(pj + cc), tp);
-      tr = fma(a, __ldg(rj + cc), tr);
+  unsigned e_op = 0, e_or = 0;
+  if (row < O.n) {
+    const double* pj = Y + (int64_t)(2 * j) * ldY;
+    const double* rj = Y + (int64_t)(2 * j + 1) * ldY;
+    const int64_t sl = row >> 5;
+    const int l = (int)(row & 31);
+    const int64_t b = O.ptr[sl];
+    const int width = (int)((O.ptr[sl + 1] - b) >> 5);
+    const double* v = oval + b + l;
+    const int32_t* c = O.col + b + l;
+    const double dt = dtil[row];
+    double tp = dt * pj[row];
+    if (do_r) {
+      double tr = dt * rj[row];
+      for (int k = 0; k < width; ++k) {
+        const double a = __ldg(v + kSlice * k);
+        const int cc = __ldg(c + kSlice * k);
+        tp = fma(a, __ldg(pj + cc), tp);
+        tr = fma(a, __ldg(rj + cc), tr);
+      }
+      // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
+      if (use_sig) {  // integer test: a double compare would take an FP64 issue slot per row
+        tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
+        tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
+      }
+      Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
+      if (EMAX) e_or = biased_exp(tr);
+    } else {
+      for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
+      if (use_sig) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
     }
-    // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
-    if (use_sig) {  // integer test: a double compare would take an FP64 issue slot per row
-      tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
-      tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
+    if (do_p) {
+      Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+      if (EMAX) e_op = biased_exp(tp);
     }
-    Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
-  } else {
-    for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
-    if (use_sig) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
   }
-  if (do_p) Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+  if (!EMAX) return;
+  // the warp's rows share one slice; lanes past n contribute 0
+  e_op = __reduce_max_sync(0xffffffffu, e_op);
+  e_or = __reduce_max_sync(0xffffffffu, e_or);
+  const int64_t wg = ((int64_t)blockIdx.x * kSpmvRows + threadIdx.x) >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    if (do_p) emax_part[(int64_t)(2 * j + 2) * emax_ld + wg] = (int)e_op;
+    if (do_r) emax_part[(int64_t)(2 * j + 3) * emax_ld + wg] = (int)e_or;
+  }
+  if (j == 0) {
+    // inputs p and r (columns 0, 1): reloaded here (cache hits) so that nothing
+    // extra stays live across the loop above
+    unsigned e_ip = 0, e_ir = 0;
+    if (row < O.n) {
+      e_ip = biased_exp(__ldcg(Y + row));
+      e_ir = biased_exp(__ldcg(Y + ldY + row));
+    }
+    e_ip = __reduce_max_sync(0xffffffffu, e_ip);
+    e_ir = __reduce_max_sync(0xffffffffu, e_ir);
+    if ((threadIdx.x & 31) == 0) {
+      emax_part[wg] = (int)e_ip;
+      emax_part[emax_ld + wg] = (int)e_ir;
+    }
+  }
+}
+
+// col_emax[c] = max over the warp entries of column c: one CTA of 1024 threads
+// per column, 16-byte loads, four in flight per thread. emax_ld is a multiple
+// of 4 and entries past the warp count are zero.
+__global__ void __launch_bounds__(1024) emax_reduce_kernel(const int* __restrict__ emax_part, int64_t emax_ld,
+                                                           int* __restrict__ col_emax) {
+  const int c = blockIdx.x;
+  const int4* src = reinterpret_cast<const int4*>(emax_part + (int64_t)c * emax_ld);
+  const int64_t n4 = emax_ld / 4;
+  int m0 = 0, m1 = 0, m2 = 0, m3 = 0;
+  int64_t k = threadIdx.x;
+  for (; k + 3072 < n4; k += 4096) {
+    const int4 a = __ldcs(src + k), b = __ldcs(src + k + 1024), d = __ldcs(src + k + 2048), e = __ldcs(src + k + 3072);
+    m0 = max(m0, max(max(a.x, a.y), max(a.z, a.w)));
+    m1 = max(m1, max(max(b.x, b.y), max(b.z, b.w)));
+    m2 = max(m2, max(max(d.x, d.y), max(d.z, d.w)));
+    m3 = max(m3, max(max(e.x, e.y), max(e.z, e.w)));
+  }
+  for (; k < n4; k += 1024) {
+    const int4 a = __ldcs(src + k);
+    m0 = max(m0, max(max(a.x, a.y), max(a.z, a.w)));
+  }
+  int m = __reduce_max_sync(0xffffffffu, max(max(m0, m1), max(m2, m3)));
+  __shared__ int red[32];
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    m = __reduce_max_sync(0xffffffffu, red[threadIdx.x]);
+    if (threadIdx.x == 0) col_emax[c] = m;
+  }
 }
 
 __global__ void shift_scale_kernel(const double* __restrict__ src, int64_t n, double theta, double scale,
@@ -105,10 +177,22 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
 }  // namespace
 
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
-                                  int do_r, cudaStream_t s) {
+                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s) {
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
   const int use_sig = (op.sig != 0.0 && j >= 1) ? 1 : 0;
-  mpk_split_step_kernel<<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p, do_r);
+  if (emax_part)
+    mpk_split_step_kernel<true><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p,
+                                                        do_r, emax_part, emax_ld);
+  else
+    mpk_split_step_kernel<false><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p,
+                                                         do_r, nullptr, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_emax_reduce(const int* emax_part, int64_t emax_ld, int64_t n, int w, int* col_emax,
+                               cudaStream_t s) {
+  (void)n;
+  emax_reduce_kernel<<<w, 1024, 0, s>>>(emax_part, emax_ld, col_emax);
   return cudaGetLastError();
 }
 
