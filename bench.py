@@ -46,6 +46,18 @@ SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_CLK_SM = 2.0   # nominal: 1.25 TFLOP/s FP64 = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 
 
+def _measured_bf16_tflops():
+    """Dense bf16 burst peak from MEASURED_PEAKS.json (driver-written), else the fallback."""
+    try:
+        with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["bf16_tflops"])
+    except (OSError, KeyError, ValueError):
+        return 1900.0
+
+
+BF16_PEAK_TF = _measured_bf16_tflops()
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -124,16 +136,16 @@ class ClockSampler:
 # roofline traffic from a committed ncu summary (bytes per launch), if current
 # ---------------------------------------------------------------------------
 
-def kernel_source_hash():
+def kernel_source_hash(name="kernels_mpk.cu"):
     h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1701_03989_gb300", "csrc", "kernels_gram.cu"), "rb") as f:
+    with open(os.path.join(ROOT, "paper_1701_03989_gb300", "csrc", name), "rb") as f:
         h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic():
-    """DRAM bytes per launch of the Gram kernel from profiles/, if taken on this source."""
-    path = os.path.join(ROOT, "profiles", "gram_partial_poisson3d_128.txt")
+    """DRAM bytes per launch of the matrix powers kernel from profiles/, if taken on this source."""
+    path = os.path.join(ROOT, "profiles", "mpk_split_poisson3d_128.txt")
     if not os.path.exists(path):
         return None, None
     vals = {}
@@ -290,9 +302,16 @@ def our_arm(args):
     bytes_alg = sum(r.mpk_bytes + r.gram_bytes + r.recover_bytes for r in results)
     flops_alg = sum(r.mpk_flops + r.gram_flops + r.recover_flops for r in results)
     peak_tf = FP64_FMA_PER_CLK_SM * 2 * SMS * SM_MAX_MHZ * 1e6 / 1e12
-    achieved_tf = f_gram / (t_gram * 1e-3) / 1e12 if t_gram > 0 else None
+    achieved_tf = f_gram / (t_gram * 1e-3) / 1e12 if t_gram > 0 else None   # FP64 flops of G = Y^T Y
     traffic_full, traffic_note = committed_traffic()
-    per_launch_flops = f_gram / n_gram if n_gram else None
+    f_mpk = sum(r.mpk_flops for r in results)
+    n_mpk = sum(r.mpk_launches for r in results)
+    achieved_mpk = f_mpk / (t_mpk * 1e-3) / 1e12 if t_mpk > 0 else None
+    per_launch_mpk = f_mpk / n_mpk if n_mpk else None
+    # the tensor-core Gram: its multiply-adds per launch (tiles of 128 x 240 and
+    # 128 x 16 per row of Y) against the measured dense bf16/fp16 peak
+    tc_flops = 2.0 * 128 * (240 + 16) * n * n_gram
+    achieved_tc = tc_flops / (t_gram * 1e-3) / 1e12 if t_gram > 0 else None
 
     # end to end: host buffers through ascg_solve_host, copies inside the timed region
     bh = torch.from_numpy(b).pin_memory()
@@ -371,12 +390,20 @@ def our_arm(args):
             "fp64_tflops_algorithmic": flops_alg / (sum(r.t_total_ms for r in results) * 1e-3) / 1e12,
             "phase_ms_per_solve": {"matrix_powers": t_mpk / args.steps, "gram": t_gram / args.steps,
                                    "controller": t_ctrl / args.steps, "recovery": t_rec / args.steps},
-            "roofline": {"bound": "alu", "kernel": "gram_partial_kernel<33>", "achieved": achieved_tf,
-                         "peak": peak_tf, "unit": "TFLOP/s", "frac": (achieved_tf / peak_tf) if achieved_tf else None,
+            "roofline": {"bound": "alu", "kernel": "mpk_split_step_kernel", "achieved": achieved_mpk,
+                         "peak": peak_tf, "unit": "TFLOP/s",
+                         "frac": (achieved_mpk / peak_tf) if achieved_mpk else None,
                          "traffic": traffic_full, "traffic_note": traffic_note,
-                         "flops_per_launch": per_launch_flops,
-                         "peak_source": "FP64 DFMA: 2 per clock per SM (nominal 1.25 TFLOP/s) x 152 SMs x 2070 MHz "
-                                        "max clock; FP64 is the binding unit (not HBM)"},
+                         "flops_per_launch": per_launch_mpk,
+                         "peak_source": "derived: FP64 DFMA 2 per clock per SM (nominal 1.25 TFLOP/s) x 152 SMs x "
+                                        "2070 MHz max clock; FP64 is the binding unit (not HBM); the MEASURED_PEAKS "
+                                        "file has no FP64 figure"},
+            "roofline_gram": {"bound": "tensor", "kernel": "gram_tc_kernel (+ column exponents)",
+                              "achieved": achieved_tc, "peak": BF16_PEAK_TF, "unit": "TFLOP/s",
+                              "frac": (achieved_tc / BF16_PEAK_TF) if achieved_tc and BF16_PEAK_TF else None,
+                              "flops_per_launch": 2.0 * 128 * (240 + 16) * n,
+                              "fp64_equiv_tflops": achieved_tf,
+                              "peak_source": "measured dense bf16 burst (fp16 runs at the same rate)"},
             "vs_classical": classical,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 8 * n},

@@ -128,7 +128,7 @@ typedef struct {
   /* device times (ms) when ASCG_FLAG_TIMING is set, else 0 */
   double t_total_ms, t_mpk_ms, t_gram_ms, t_ctrl_ms, t_recover_ms, t_cg_ms;
   int gram_launches;         /* Gram kernel launches timed in t_gram_ms            */
-  int pad_;
+  int mpk_launches;          /* matrix powers step launches timed in t_mpk_ms     */
   double gram_flops;         /* algorithmic FP64 flops of those launches          */
   double gram_bytes;         /* algorithmic bytes read by those launches           */
   double mpk_flops, mpk_bytes, recover_flops, recover_bytes;

@@ -59,7 +59,7 @@ class ascg_result(C.Structure):
                 ("rel_res_updated", C.c_double), ("rel_res_true", C.c_double),
                 ("t_total_ms", C.c_double), ("t_mpk_ms", C.c_double), ("t_gram_ms", C.c_double),
                 ("t_ctrl_ms", C.c_double), ("t_recover_ms", C.c_double), ("t_cg_ms", C.c_double),
-                ("gram_launches", C.c_int), ("pad_", C.c_int), ("gram_flops", C.c_double),
+                ("gram_launches", C.c_int), ("mpk_launches", C.c_int), ("gram_flops", C.c_double),
                 ("gram_bytes", C.c_double), ("mpk_flops", C.c_double), ("mpk_bytes", C.c_double),
                 ("recover_flops", C.c_double), ("recover_bytes", C.c_double)]
 

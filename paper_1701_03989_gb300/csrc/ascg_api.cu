@@ -534,9 +534,11 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         res->t_ctrl_ms += c2;
         res->t_recover_ms += d2;
         res->gram_launches += 1;
+        res->mpk_launches += sbar;
         res->gram_flops += 2.0 * (double)wb * (wb + 1) / 2.0 * (double)n;
         res->gram_bytes += 8.0 * (double)wb * (double)n;
-        // per step: nnz FMAs per chain, plus the recurrence terms
+        // per step and chain: the SpMV's 2 nnz flops (the folded shift, scale and
+        // sigma terms are not counted)
         const double nchains = 2.0 * sbar - 1.0;
         res->mpk_flops += nchains * 2.0 * (double)op->nnz;
         res->mpk_bytes += (double)sbar * (12.0 * op->nnz + 4.0 * (n + 1)) + nchains * 16.0 * n + 8.0 * n;
