@@ -68,6 +68,8 @@ def parse():
                     help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--gram-fp64", action="store_true",
+                    help="form the Gram matrix with FP64 FMAs (CUDA cores) instead of the tensor-core digit split")
     return ap.parse_args()
 
 
@@ -253,7 +255,7 @@ def our_arm(args):
         o = P.make_options(method="classical", eps_target=1e-12, max_iters=max_it, timing=True)
     else:
         o = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=cfg["lam"],
-                           max_iters=max_it, timing=True)
+                           max_iters=max_it, timing=True, gram_fp64=args.gram_fp64)
 
     def solve_once():
         xd.zero_()
@@ -381,6 +383,9 @@ def our_arm(args):
                            "classical CG (Alg. 1)"),
                        "method": args.method,
                        "parallelism": "replicas only" if world > 1 else "single GPU",
+                       "gram": ("FP64 FMAs on the CUDA cores" if args.gram_fp64 else
+                                "tensor cores: exact split of Y into fp16 digits, integer sums "
+                                "(FP64-level normwise error); FP64 kernel with --gram-fp64"),
                        "l2": "inputs larger than L2: A 183 MB, basis 554 MB, vectors 16.8 MB each"},
             "status_ok": ok,
             "iters_per_solve": iters / args.steps,

@@ -114,23 +114,32 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n
   }
 }
 
-// One thread per pair; adds the partials of all CTAs in index order with four
-// interleaved accumulators (fixed order) to shorten the dependency chain.
-__global__ void gram_finalize_kernel(int w, const double* __restrict__ partials, int nparts,
-                                     double* __restrict__ G) {
+// Four threads per pair (lanes 4q .. 4q+3 of a warp): thread t adds the
+// partials of CTAs c = t, t + 4, t + 8, ... with loads unrolled eight deep,
+// then the four sums combine as (s0 + s1) + (s2 + s3). Fixed order: the result
+// is bitwise reproducible.
+__global__ void __launch_bounds__(128) gram_finalize_kernel(int w, const double* __restrict__ partials, int nparts,
+                                                            double* __restrict__ G) {
   const int np = w * (w + 1) / 2;
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= np) return;
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 3 < nparts; c += 4) {
-    s0 += partials[(int64_t)c * np + p];
-    s1 += partials[(int64_t)(c + 1) * np + p];
-    s2 += partials[(int64_t)(c + 2) * np + p];
-    s3 += partials[(int64_t)(c + 3) * np + p];
+  const int gt = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = gt >> 2, t = gt & 3;
+  double acc = 0.0;
+  if (p < np) {
+    int c = t;
+    for (; c + 28 < nparts; c += 32) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = partials[(int64_t)(c + 4 * u) * np + p];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) acc += v[u];
+    }
+    for (; c < nparts; c += 4) acc += partials[(int64_t)c * np + p];
   }
-  for (; c < nparts; ++c) s0 += partials[(int64_t)c * np + p];
-  const double s = (s0 + s1) + (s2 + s3);
+  const double a1 = __shfl_down_sync(0xffffffffu, acc, 1);
+  const double a2 = __shfl_down_sync(0xffffffffu, acc, 2);
+  const double a3 = __shfl_down_sync(0xffffffffu, acc, 3);
+  if (t != 0 || p >= np) return;
+  const double s = (acc + a1) + (a2 + a3);
   int a = 0, rem = p;
   while (rem >= w - a) {
     rem -= w - a;
@@ -182,7 +191,7 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
 
 cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s) {
   const int np = w * (w + 1) / 2;
-  gram_finalize_kernel<<<(np + 63) / 64, 64, 0, s>>>(w, partials, nparts, G);
+  gram_finalize_kernel<<<(4 * np + 127) / 128, 128, 0, s>>>(w, partials, nparts, G);
   return cudaGetLastError();
 }
 
