@@ -183,6 +183,37 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  * leading 2i+1 columns, and every Gram submatrix G_{k,i} is a leading
  * principal submatrix. */
 
+/* Batched solves: `count` independent SPD systems A_q x_q = b_q of any sizes
+ * in one call (Alg. 4 per system, run in lockstep). The systems' rows are
+ * stacked (each padded to a multiple of 32) into one block-diagonal operator,
+ * so every phase of a block is one launch for all systems; a system that has
+ * converged drops out of the following blocks. Each system's arithmetic
+ * depends on that system alone: its result is bitwise the same alone and in
+ * any batch.
+ *  - ops: host array of count operators (any sizes) on the current device.
+ *  - b, x: host arrays of count device pointers (n_q doubles each); x[q] holds
+ *    x_1 on entry and the solution on exit. b[q] and x[q] must not overlap.
+ *  - eps_target: host double[count] of relative targets (eps*_q =
+ *    eps_target[q] ||b_q||), or NULL for opts->eps_target.
+ *  - opts: method ASCG_ADAPTIVE or ASCG_FIXED_S, basis ASCG_MONOMIAL (the other
+ *    bases need per-system parameters and are not batched); s_max, s0, f, c,
+ *    check_in_loop and max_iters apply to every system. Histories are per
+ *    system: res_hist is count x res_hist_cap, block_hist count x
+ *    block_hist_cap, alpha_hist and beta_hist count x coef_hist_cap (row q is
+ *    system q); the caps must be >= 1 when the arrays are given.
+ *  - results: host ascg_result[count] or NULL: per system status, iters,
+ *    blocks, wasted_vecs, bnorm, rel_res_updated, rel_res_true; launches holds
+ *    the number of lockstep blocks of the whole call. Device times are not
+ *    recorded.
+ * Temporary device memory: about (2 s_max + 5) 8 n_tot bytes plus a copy of the
+ * operators, n_tot = sum of the padded sizes (< 2^31). Returns ASCG_OK when
+ * every system converged, else ASCG_NOT_CONVERGED or ASCG_ERR_BREAKDOWN (the
+ * worst over the systems; results[q].status tells which). Synchronises the
+ * stream. */
+ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
+                             const double* eps_target, const ascg_options* opts, ascg_result* results,
+                             void* cuda_stream);
+
 /* y = A x (device x, y of length n; x and y must not overlap). */
 ascg_status ascg_spmv(ascg_op op, const double* x, double* y, void* cuda_stream);
 

@@ -79,6 +79,8 @@ def _load():
         "ascg_op_size": (C.c_int, [P, C.POINTER(I64), C.POINTER(I64)]),
         "ascg_solve": (C.c_int, [P, P, P, C.POINTER(ascg_options), C.POINTER(ascg_result), P]),
         "ascg_solve_host": (C.c_int, [P, P, P, C.POINTER(ascg_options), C.POINTER(ascg_result), P]),
+        "ascg_solve_batch": (C.c_int, [C.c_int, C.POINTER(P), C.POINTER(P), C.POINTER(P), P,
+                                       C.POINTER(ascg_options), C.POINTER(ascg_result), P]),
         "ascg_spmv": (C.c_int, [P, P, P, P]),
         "ascg_matrix_powers": (C.c_int, [P, C.c_int, P, P, P, P, I64, P]),
         "ascg_gram": (C.c_int, [I64, C.c_int, P, I64, P, P]),
@@ -169,6 +171,29 @@ def ascg_solve(op, b, x, opts=None, stream=None, raise_on=(ASCG_OK, ASCG_NOT_CON
                          _stream(stream))
     _check(st, "ascg_solve", raise_on)
     return res
+
+
+def ascg_solve_batch(ops, bs, xs, opts, eps_targets=None, stream=None,
+                     raise_on=(ASCG_OK, ASCG_NOT_CONVERGED, ASCG_ERR_BREAKDOWN)):
+    """ops: list of operators; bs, xs: lists of device arrays (x: start in, solution
+    out); eps_targets: per-system relative targets or None. Returns the list of
+    per-system ascg_result structs and the call's status."""
+    count = len(ops)
+    if not (len(bs) == len(xs) == count) or count < 1:
+        raise ValueError("ops, bs and xs must have the same positive length")
+    oa = (C.c_void_p * count)(*[C.c_void_p(o) if isinstance(o, int) else o for o in ops])
+    ba = (C.c_void_p * count)(*[_ptr(b) for b in bs])
+    xa = (C.c_void_p * count)(*[_ptr(x) for x in xs])
+    eps = None
+    if eps_targets is not None:
+        eps_arr = np.ascontiguousarray(np.asarray(eps_targets, dtype=np.float64))
+        if eps_arr.shape != (count,):
+            raise ValueError("eps_targets must have one entry per system")
+        eps = eps_arr.ctypes.data
+    res = (ascg_result * count)()
+    st = _lib.ascg_solve_batch(count, oa, ba, xa, eps, C.byref(opts), res, _stream(stream))
+    _check(st, "ascg_solve_batch", raise_on)
+    return list(res), st
 
 
 def ascg_solve_host(op, b, x, opts=None, stream=None, raise_on=(ASCG_OK, ASCG_NOT_CONVERGED)):
@@ -276,6 +301,6 @@ def block_infos(count: int):
 
 
 EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
-            "ascg_solve_host", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc",
+            "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc",
             "ascg_block_step", "ascg_recover",
             "ascg_newton_shifts", "ascg_last_error"]

@@ -108,6 +108,21 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
 // Sum the partials in a fixed order; G row-major w x w, both halves.
 cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
 
+// Batched solves: one Gram item = rows [row0, row0 + nrows) of system sys.
+struct GramItem {
+  int64_t row0;
+  int nrows;
+  int sys;
+};
+constexpr int kGramItemRows = 8192;
+// FP64 partials (W columns, W odd <= 33) of every item; items of systems with
+// sys_w 0 are skipped. partials: nitems x W(W+1)/2.
+cudaError_t launch_gram_items(int W, const double* Y, int64_t ldY, const GramItem* items, int nitems,
+                              const int* sys_w, double* partials, cudaStream_t s);
+// G of each active system q (w_q = sys_w[q] x w_q, stride w_q) at G + q * g_stride.
+cudaError_t launch_gram_items_finalize(int W, const double* partials, const int* sys_item0, const int* sys_nitems,
+                                       const int* sys_w, int count, double* G, int64_t g_stride, cudaStream_t s);
+
 // Tensor-core Gram (split-bf16 operands, exact integer sums) for
 // kGramTcMinW <= w <= kMaxW. Below that width the FP64 kernel is faster.
 constexpr int kGramTcMinW = 9;
@@ -124,6 +139,25 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
 // the number of partials through *nparts.
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s);
+
+// Batched solves (kernels_batch.cu): rows of all systems concatenated, each
+// system padded to whole 32-row slices; slice_sys maps a slice to its system.
+// Matrix powers step j in the monomial basis for every system q with
+// j < sys_steps[q].
+cudaError_t launch_mpk_batch_step(const DevSell& O, const double* diag, const int* slice_sys, const int* sys_steps,
+                                  double* Y, int64_t ldY, int j, cudaStream_t s);
+// r = b - (D + O) x over all rows; p = r too when p != nullptr.
+cudaError_t launch_batch_residual(const DevSell& O, const double* diag, const double* b, const double* x, double* r,
+                                  double* p, cudaStream_t s);
+// out[q] = sum of squares of u over system q's rows, fixed order.
+cudaError_t launch_seg_sumsq(const double* u, const int64_t* sys_row0, const int64_t* sys_n, int count, double* out,
+                             cudaStream_t s);
+// Recovery for every active system (w_q = sys_w[q] > 0), coordinates at coords + q * c_stride.
+cudaError_t launch_recover_batch(int W, int64_t n, const double* Y, int64_t ldY, const int* slice_sys,
+                                 const int* sys_w, const double* coords, int64_t c_stride, double* x, double* r,
+                                 double* p, cudaStream_t s);
+cudaError_t launch_add_offset_i32(int32_t* dst, const int32_t* src, int64_t n, int32_t off, cudaStream_t s);
+cudaError_t launch_add_offset_i64(int64_t* dst, const int64_t* src, int64_t n, int64_t off, cudaStream_t s);
 
 // Recovery (eq. coords).
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
@@ -142,6 +176,8 @@ struct BlockState {
   double c;
   double bnorm;
   double sqrt_n;       // sqrt(length of the basis vectors)
+  int active;          // batched solves: 0 skips this system's block (single solves: 1)
+  int pad_;
   // outputs
   int stilde;
   int s_k;
@@ -157,6 +193,11 @@ struct BlockState {
 
 // kappa(G_{k,i}) for i = 1..sbar, one CTA per i. Writes st->sqrt_kappa.
 cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s);
+// The same for `count` systems at once: system q uses G + q * g_stride (w_q x w_q,
+// w_q = 2 sbar_q + 1, sbar_q = st[q].sbar) and st + q; inactive systems and
+// i > sbar_q are skipped. max_sbar: the largest sbar_q.
+cudaError_t launch_kappa_batch(const double* G, int64_t g_stride, BlockState* st, int count, int max_sbar,
+                               cudaStream_t s);
 // Selection of s~ (adaptive), B, inner loop; writes coords[3w], histories.
 // theta/sigma/gamma: device double[kMaxS]. hist: device double[3 * kMaxS] per block
 // (alpha, beta, rel res) or nullptr; res_hist: device array indexed by iteration,
@@ -164,6 +205,12 @@ cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t
 cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma,
                         const double* gamma, BlockState* st, double* coords, double* hist,
                         double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s);
+// The same for `count` systems (shared theta/sigma/gamma): system q uses
+// G + q * g_stride, st + q, coords + q * c_stride, res_hist + q * res_cap and
+// ab_hist + q * 2 * ab_cap (histories may be nullptr); inactive systems skip.
+cudaError_t launch_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
+                              const double* gamma, BlockState* st, int count, double* coords, int64_t c_stride,
+                              double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s);
 
 // Newton shifts: Ritz values of the CG tridiagonal, Leja order. alphas, betas:
 // device; shifts: device double[k].

@@ -173,9 +173,18 @@ __device__ __forceinline__ double warp_max(double v) {
 // certification (is it below the floor (2i+1) sqrt(n) eps lambda_max?).
 constexpr int kKappaRounds = 11;
 
-__global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar) {
+// sbar > 0: one system; sbar == 0: batched, system blockIdx.y at G + y * g_stride
+// and st + y with its own sbar (inactive systems and i > sbar skip).
+__global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar,
+                                                    int64_t g_stride) {
   const int i = blockIdx.x + 1;
   const int m = 2 * i + 1;
+  G += (int64_t)blockIdx.y * g_stride;
+  st += blockIdx.y;
+  if (sbar == 0) {
+    if (!st->active || i > st->sbar) return;  // uniform over the CTA
+    sbar = st->sbar;
+  }
   const int w = 2 * sbar + 1;
   __shared__ double A[kMaxW][kMaxW];  // odd row stride: conflict-free column access
   __shared__ double v[32], wv[32];
@@ -368,8 +377,16 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
                                                   const double* __restrict__ sg_g, const double* __restrict__ gm_g,
                                                   BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
                                                   double* __restrict__ res_hist, int res_cap,
-                                                  double* __restrict__ ab_hist, int ab_cap) {
+                                                  double* __restrict__ ab_hist, int ab_cap, int64_t g_stride,
+                                                  int64_t c_stride) {
   __shared__ double Gs[kMaxW][kMaxW];  // odd row stride: conflict-free
+  // batched launches: system blockIdx.x (single solves: one CTA, strides unused)
+  G += (int64_t)blockIdx.x * g_stride;
+  st += blockIdx.x;
+  coords += (int64_t)blockIdx.x * c_stride;
+  if (res_hist) res_hist += (int64_t)blockIdx.x * res_cap;
+  if (ab_hist) ab_hist += (int64_t)blockIdx.x * 2 * ab_cap;
+  if (!st->active) return;  // uniform over the CTA
   __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2], g[kMaxW + 2];
   __shared__ double th[kMaxS], sg[kMaxS], gm[kMaxS];
   __shared__ int s_tilde, s_flag;
@@ -595,14 +612,30 @@ __global__ void __launch_bounds__(32) newton_shifts_kernel(const double* __restr
 }  // namespace
 
 cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s) {
-  kappa_kernel<<<sbar, 128, 0, s>>>(G, st, sbar);
+  kappa_kernel<<<sbar, 128, 0, s>>>(G, st, sbar, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_kappa_batch(const double* G, int64_t g_stride, BlockState* st, int count, int max_sbar,
+                               cudaStream_t s) {
+  if (count < 1 || max_sbar < 1) return cudaSuccess;
+  kappa_kernel<<<dim3(max_sbar, count), 128, 0, s>>>(G, st, 0, g_stride);
   return cudaGetLastError();
 }
 
 cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
                         BlockState* st, double* coords, double* hist, double* res_hist, int res_cap,
                         double* ab_hist, int ab_cap, cudaStream_t s) {
-  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
+  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap, 0, 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
+                              const double* gamma, BlockState* st, int count, double* coords, int64_t c_stride,
+                              double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  ctrl_kernel<<<count, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, nullptr, res_hist, res_cap, ab_hist, ab_cap,
+                                   g_stride, c_stride);
   return cudaGetLastError();
 }
 

@@ -27,9 +27,11 @@ constexpr int kChunk = 32;  // rows per chunk = lanes
 
 int g_gram_grid = 0;
 
+// Partial Gram of 32-row chunks [c0, c1) of rows [0, n) of Y into out[NP]
+// (row-major upper triangle). Called by every thread of a CTA of kGramThreads.
 template <int W>
-__global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n, const double* __restrict__ Y,
-                                                                        int64_t ldY, double* __restrict__ partials) {
+__device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict__ Y, int64_t ldY, int64_t c0,
+                                            int64_t c1, double* __restrict__ out) {
   constexpr int NP = W * (W + 1) / 2;
   constexpr int PPW = (NP + kGramWarps - 1) / kGramWarps;
   constexpr int ELEMS = W * kChunk;
@@ -53,9 +55,6 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n
     pab[warp][k] = (unsigned short)(a | (b << 8));
   }
 
-  const int64_t nchunks = (n + kChunk - 1) / kChunk;
-  const int64_t c0 = nchunks * blockIdx.x / gridDim.x;
-  const int64_t c1 = nchunks * (blockIdx.x + 1) / gridDim.x;
 
   double acc[PPW];
 #pragma unroll
@@ -105,13 +104,35 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n
     if (more) store(buf ^ 1);
     __syncthreads();
   }
-  double* out = partials + (int64_t)blockIdx.x * NP;
 #pragma unroll
   for (int k = 0; k < PPW; ++k) {
     const int p = warp + kGramWarps * k;
     const double v = warp_sum(acc[k]);
     if (lane == 0 && p < NP) out[p] = v;
   }
+}
+
+template <int W>
+__global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n, const double* __restrict__ Y,
+                                                                        int64_t ldY, double* __restrict__ partials) {
+  constexpr int NP = W * (W + 1) / 2;
+  const int64_t nchunks = (n + kChunk - 1) / kChunk;
+  gram_chunks<W>(n, Y, ldY, nchunks * blockIdx.x / gridDim.x, nchunks * (blockIdx.x + 1) / gridDim.x,
+                 partials + (int64_t)blockIdx.x * NP);
+}
+
+// Batched solves: CTA q takes item q (rows [row0, row0 + nrows) of one
+// system). Items depend only on the system's own size, so a system's Gram is
+// the same alone and in any batch. Items of inactive systems (sys_w 0) skip.
+template <int W>
+__global__ void __launch_bounds__(kGramThreads, 1) gram_items_kernel(const double* __restrict__ Y, int64_t ldY,
+                                                                      const GramItem* __restrict__ items,
+                                                                      const int* __restrict__ sys_w,
+                                                                      double* __restrict__ partials) {
+  constexpr int NP = W * (W + 1) / 2;
+  const GramItem it = items[blockIdx.x];
+  if (sys_w[it.sys] == 0) return;  // uniform over the CTA
+  gram_chunks<W>(it.nrows, Y + it.row0, ldY, 0, (it.nrows + kChunk - 1) / kChunk, partials + (int64_t)blockIdx.x * NP);
 }
 
 // Four threads per pair (lanes 4q .. 4q+3 of a warp): thread t adds the
@@ -148,6 +169,35 @@ __global__ void __launch_bounds__(128) gram_finalize_kernel(int w, const double*
   const int b = a + rem;
   G[a * w + b] = s;
   G[b * w + a] = s;
+}
+
+// Batched solves: G of system q (w_q x w_q, stride w_q, both halves) at
+// G + q * g_stride from its items' partials (computed with W >= w_q columns),
+// added in item order. One CTA per system.
+__global__ void __launch_bounds__(256) gram_items_finalize_kernel(int W, const double* __restrict__ partials,
+                                                                  const int* __restrict__ sys_item0,
+                                                                  const int* __restrict__ sys_nitems,
+                                                                  const int* __restrict__ sys_w, double* __restrict__ G,
+                                                                  int64_t g_stride) {
+  const int q = blockIdx.x;
+  const int w = sys_w[q];
+  if (w == 0) return;
+  const int NP = W * (W + 1) / 2;
+  const int i0 = sys_item0[q], ni = sys_nitems[q];
+  double* Gq = G + (int64_t)q * g_stride;
+  for (int e = threadIdx.x; e < w * (w + 1) / 2; e += blockDim.x) {
+    int a = 0, rem = e;
+    while (rem >= w - a) {
+      rem -= w - a;
+      ++a;
+    }
+    const int b = a + rem;
+    const int p = a * W - a * (a - 1) / 2 + (b - a);  // pair (a, b) in W-space
+    double s = 0.0;
+    for (int it = 0; it < ni; ++it) s += partials[(int64_t)(i0 + it) * NP + p];
+    Gq[a * w + b] = s;
+    Gq[b * w + a] = s;
+  }
 }
 
 template <int W>
@@ -187,6 +237,29 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
     default:
       return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_gram_items(int W, const double* Y, int64_t ldY, const GramItem* items, int nitems,
+                              const int* sys_w, double* partials, cudaStream_t s) {
+  if (nitems < 1) return cudaSuccess;
+  switch (W) {
+#define ASCG_GI(WW)                                                                            \
+  case WW:                                                                                     \
+    gram_items_kernel<WW><<<nitems, kGramThreads, 0, s>>>(Y, ldY, items, sys_w, partials); \
+    return cudaGetLastError();
+    ASCG_GI(3) ASCG_GI(5) ASCG_GI(7) ASCG_GI(9) ASCG_GI(11) ASCG_GI(13) ASCG_GI(15) ASCG_GI(17) ASCG_GI(19)
+    ASCG_GI(21) ASCG_GI(23) ASCG_GI(25) ASCG_GI(27) ASCG_GI(29) ASCG_GI(31) ASCG_GI(33)
+#undef ASCG_GI
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_gram_items_finalize(int W, const double* partials, const int* sys_item0, const int* sys_nitems,
+                                       const int* sys_w, int count, double* G, int64_t g_stride, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  gram_items_finalize_kernel<<<count, 256, 0, s>>>(W, partials, sys_item0, sys_nitems, sys_w, G, g_stride);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s) {

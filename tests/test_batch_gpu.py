@@ -1,0 +1,158 @@
+"""Batched solves (ascg_solve_batch): many independent SPD systems of uneven
+sizes in lockstep. Each system is checked against the FP64 oracle under the
+same parity rules as a single solve (residual history over the first 20
+iterations, s_k sequence up to near-threshold decisions, true residual within
+2x). Each system's result must be bitwise the same alone and in the batch.
+"""
+import numpy as np
+import pytest
+
+import parity
+import workloads as W
+from oracle import ascg_oracle as O
+
+pytestmark = pytest.mark.gpu
+EPS = 2.0 ** -53
+S_MAX = 10
+CAP = 4000
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1701_03989_gb300 as P
+    torch.cuda.init()
+    return P, torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def make_op(P, A):
+    return P.ascg_op_create_csr(A.n, A.nnz, np.ascontiguousarray(A.rowptr, np.int64),
+                                np.ascontiguousarray(A.colind, np.int32), np.ascontiguousarray(A.val, np.float64), 0)
+
+
+def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None):
+    count = len(systems)
+    ops = [make_op(P, s["A"]) for s in systems]
+    bs = [dev(torch, s["b"]) for s in systems]
+    xs = [dev(torch, s["x1"]) for s in systems]
+    res_hist = np.zeros((count, max_iters + 2))
+    infos = P.block_infos(count * (max_iters + 2))
+    o = P.make_options(method=method, basis="monomial", s_max=s_max, eps_target=1e-10, max_iters=max_iters,
+                       res_hist=res_hist.reshape(-1), block_hist=infos)
+    o.res_hist_cap = max_iters + 2
+    o.block_hist_cap = max_iters + 2
+    epsv = [s["eps"] for s in systems] if eps is None else eps
+    results, st = P.ascg_solve_batch(ops, bs, xs, o, eps_targets=epsv)
+    out = []
+    for q, s in enumerate(systems):
+        r = results[q]
+        blocks = parity.gpu_blocks_from_infos(infos[q * (max_iters + 2):], r.blocks)
+        out.append(dict(res=r, hist=res_hist[q, :r.iters + 1].copy(), blocks=blocks, x=xs[q].cpu().numpy()))
+    for op in ops:
+        P.ascg_op_destroy(op)
+    return out, st
+
+
+def small_batch(seed=11, count=9):
+    sys = W.batch_systems(count, seed=seed, nmin=60, nmax=2500)
+    # a ragged n (not a multiple of 32) in every family is likely; add a tiny one
+    A = W.banded_spd(7, 3, np.random.default_rng(3))
+    sys.append(dict(name="banded_7", family="banded", A=A, b=W.rhs_uniform(7, np.random.default_rng(4)),
+                    x1=np.zeros(7), eps=1e-12))
+    return sys
+
+
+def test_batch_parity_against_oracle(env):
+    P, torch = env
+    systems = small_batch()
+    out, st = run_batch(P, torch, systems)
+    assert st == P.ASCG_OK
+    for s, g in zip(systems, out):
+        orc = O.adaptive_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], s_max=S_MAX, eps_target=s["eps"],
+                                  basis="monomial", max_iters=CAP)
+        assert g["res"].status == P.ASCG_OK and orc.converged, s["name"]
+        exempt, bad = parity.compare_block_sequences(g["blocks"], orc.blocks, s["A"].n, orc.res_hist, s["eps"])
+        assert not bad, (s["name"], bad)
+        nwin = parity.history_window(g["blocks"], orc.blocks, exempt, iters=20)
+        # after n iterations CG has terminated in exact arithmetic: later entries are rounding noise
+        nwin = min(nwin, len(g["hist"]), len(orc.res_hist), s["A"].n)
+        hg, ho = g["hist"][:nwin], np.asarray(orc.res_hist[:nwin])
+        tau = parity.history_tolerance(orc.blocks, ho, nwin)
+        assert np.all(np.abs(hg - ho) <= tau), (s["name"], (np.abs(hg - ho) / tau).max())
+        assert 0.5 * orc.true_res <= g["res"].rel_res_true <= 2.0 * orc.true_res, (s["name"], g["res"].rel_res_true,
+                                                                                   orc.true_res)
+        if exempt is None:
+            assert g["res"].iters == orc.iters and g["res"].blocks == len(orc.blocks), (
+                s["name"], g["res"].iters, orc.iters, [b["s_k"] for b in g["blocks"]], [b["s_k"] for b in orc.blocks])
+
+
+def test_batch_result_same_alone_and_in_mix(env):
+    """Each system's arithmetic depends on that system alone: x, the residual
+    history and the block records are bitwise equal alone and in the batch."""
+    P, torch = env
+    systems = small_batch(seed=12, count=6)
+    mixed, _ = run_batch(P, torch, systems)
+    for q in (0, 3, len(systems) - 1):
+        alone, _ = run_batch(P, torch, [systems[q]])
+        a, m = alone[0], mixed[q]
+        assert np.array_equal(a["x"], m["x"]), systems[q]["name"]
+        assert np.array_equal(a["hist"], m["hist"]), systems[q]["name"]
+        assert a["blocks"] == m["blocks"], systems[q]["name"]
+
+
+def test_batch_edge_cases(env):
+    """A zero right-hand side (x = 0, no block), a system whose start is already
+    the solution, an iteration cap that stops one system, and fixed s."""
+    P, torch = env
+    A1 = W.poisson2d(9)
+    A2 = W.poisson2d(11)
+    b2 = W.rhs_uniform(A2.n, np.random.default_rng(1))
+    xs2 = np.linalg.solve(A2.to_dense(), b2)
+    A3 = W.banded_spd(500, 20, np.random.default_rng(2))
+    systems = [
+        dict(name="zero_rhs", A=A1, b=np.zeros(A1.n), x1=np.ones(A1.n), eps=1e-10),
+        dict(name="solved", A=A2, b=b2, x1=xs2, eps=1e-8),
+        dict(name="banded", A=A3, b=W.rhs_uniform(A3.n, np.random.default_rng(3)), x1=np.zeros(A3.n), eps=1e-12),
+    ]
+    out, st = run_batch(P, torch, systems)
+    assert st == P.ASCG_OK
+    assert out[0]["res"].iters == 0 and np.array_equal(out[0]["x"], np.zeros(A1.n))
+    assert out[1]["res"].iters == 0 and np.array_equal(out[1]["x"], xs2)
+    assert out[2]["res"].rel_res_true < 1e-11
+    capped, st = run_batch(P, torch, systems[2:], max_iters=7)
+    assert st == P.ASCG_NOT_CONVERGED and capped[0]["res"].status == P.ASCG_NOT_CONVERGED
+    assert capped[0]["res"].iters == 7
+    fixed, st = run_batch(P, torch, systems[2:], method="fixed", s_max=4)
+    orc = O.fixed_sstep_cg(O.Operator.from_csr(A3), systems[2]["b"], systems[2]["x1"], 4, O.monomial_params(4),
+                           eps_target=1e-12, max_iters=CAP)
+    sg, so = [b["s_k"] for b in fixed[0]["blocks"]], [b["s_k"] for b in orc.blocks]
+    k = next((i for i, (a, b) in enumerate(zip(sg, so)) if a != b), min(len(sg), len(so)))
+    assert sg[:k] == so[:k]
+    if sg != so:
+        # the first difference must be a convergence stop: the updated residual is
+        # pinned to the absolute history tolerance (1e-10), far above this target
+        i_g = min(sum(sg[:k + 1]), len(orc.res_hist) - 1)
+        assert orc.res_hist[i_g] <= 1e-12 + 1e-10 and fixed[0]["hist"][-1] <= 1e-12
+    assert 0.5 * orc.true_res <= fixed[0]["res"].rel_res_true <= 2.0 * orc.true_res
+
+
+def test_batch_rejects_unsupported(env):
+    P, torch = env
+    A = W.poisson2d(8)
+    op = make_op(P, A)
+    b = dev(torch, W.rhs_uniform(A.n, np.random.default_rng(0)))
+    x = dev(torch, np.zeros(A.n))
+    o = P.make_options(method="adaptive", basis="chebyshev", s_max=4, lam=(0.01, 2.0))
+    with pytest.raises(P.AscgError) as e:
+        P.ascg_solve_batch([op], [b], [x], o)
+    assert e.value.status == P.ASCG_ERR_INVALID
+    o = P.make_options(method="classical")
+    with pytest.raises(P.AscgError):
+        P.ascg_solve_batch([op], [b], [x], o)
+    P.ascg_op_destroy(op)

@@ -278,3 +278,28 @@ def scaled(family: str, size: int, seed: int):
         raise ValueError(family)
     b = rhs_uniform(A.n, rng)
     return dict(name=f"{family}_{size}", A=A, b=b, x1=np.zeros(A.n), lam=lam)
+
+
+def batch_systems(count: int = 256, seed: int | None = None, nmin: float = 1e3, nmax: float = 2e5):
+    """Batch of independent SPD systems (the uneven batched workload).
+
+    Sizes are log-uniform on [nmin, nmax]; the family is uniform over 2D
+    Poisson (m = round(sqrt n)), 3D Poisson (m = round(cbrt n)) and banded SPD
+    (half-bandwidth ~ U{8..64}); targets are 1e-8 or 1e-12 with probability
+    1/2 each; b ~ U[-1, 1] normalised, x1 = 0. Returns a list of dicts with A,
+    b, x1, eps and the family name."""
+    rng = np.random.default_rng(seed_for(4) if seed is None else seed)
+    out = []
+    for q in range(count):
+        n = int(round(float(np.exp(rng.uniform(np.log(nmin), np.log(nmax))))))
+        fam = ("poisson2d", "poisson3d", "banded")[int(rng.integers(0, 3))]
+        if fam == "poisson2d":
+            A = poisson2d(max(2, int(round(n ** 0.5))))
+        elif fam == "poisson3d":
+            A = poisson3d(max(2, int(round(n ** (1.0 / 3.0)))))
+        else:
+            A = banded_spd(n, int(rng.integers(8, 65)), rng)
+        eps = 1e-8 if rng.random() < 0.5 else 1e-12
+        b = rhs_uniform(A.n, rng)
+        out.append(dict(name=f"{fam}_{A.n}", family=fam, A=A, b=b, x1=np.zeros(A.n), eps=eps))
+    return out
