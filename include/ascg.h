@@ -184,15 +184,16 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  * principal submatrix. */
 
 /* Batched solves: `count` independent SPD systems A_q x_q = b_q of any sizes
- * in one call (Alg. 4 per system, run in lockstep). The systems' rows are
- * stacked (each padded to a multiple of 32) into one block-diagonal operator,
- * so every phase of a block is one launch for all systems; a system that has
- * converged drops out of the following blocks. Each system's arithmetic
- * depends on that system alone: its result is bitwise the same alone and in
- * any batch.
+ * in one call (Alg. 4 per system, run in lockstep). Each system keeps its own
+ * operator, basis, x and b; a device table of per-system descriptors and a
+ * list of row items (up to 256 rows of one system each) let every phase of a
+ * block be one launch for all systems. A system that has converged drops out
+ * of the following blocks. Each system's arithmetic depends on that system
+ * alone: its result is bitwise the same alone and in any batch.
  *  - ops: host array of count operators (any sizes) on the current device.
  *  - b, x: host arrays of count device pointers (n_q doubles each); x[q] holds
- *    x_1 on entry and the solution on exit. b[q] and x[q] must not overlap.
+ *    x_1 on entry and the solution on exit (updated in place; x[q] = 0 when
+ *    b[q] = 0). b[q] and x[q] must not overlap each other or another system's.
  *  - eps_target: host double[count] of relative targets (eps*_q =
  *    eps_target[q] ||b_q||), or NULL for opts->eps_target.
  *  - opts: method ASCG_ADAPTIVE or ASCG_FIXED_S, basis ASCG_MONOMIAL (the other
@@ -205,10 +206,11 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  *    blocks, wasted_vecs, bnorm, rel_res_updated, rel_res_true; launches holds
  *    the number of lockstep blocks of the whole call. Device times are not
  *    recorded.
- * Temporary device memory: about (2 s_max + 5) 8 n_tot bytes plus a copy of the
- * operators, n_tot = sum of the padded sizes (< 2^31). Returns ASCG_OK when
- * every system converged, else ASCG_NOT_CONVERGED or ASCG_ERR_BREAKDOWN (the
- * worst over the systems; results[q].status tells which). Synchronises the
+ * Temporary device memory: (2 s_max + 1) 8 round_up(n_q, 32) bytes of basis
+ * per system plus (2 s_max + 1)(s_max + 1) 8 bytes of Gram partials per 8192
+ * rows. Returns ASCG_OK when every system converged, else ASCG_NOT_CONVERGED
+ * or ASCG_ERR_BREAKDOWN (the worst over the systems; results[q].status tells
+ * which); ASCG_ERR_INVALID if some b or x_1 is not finite. Synchronises the
  * stream. */
 ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
                              const double* eps_target, const ascg_options* opts, ascg_result* results,
@@ -300,6 +302,80 @@ ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k,
  *  - Returns once the work is enqueued on the stream (it does not
  *    synchronise). */
 ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
+
+/* --- solve server (continuous batching) ------------------------------------
+ * A request loop over the batched engine: requests of different sizes and
+ * targets are submitted at any time; each ascg_server_step admits waiting
+ * requests while device memory and system slots allow, runs one block
+ * (Alg. 4) of every admitted system, and hands back the systems that
+ * finished. Bases and coefficients stay on the device between steps, and
+ * the blocks of all running systems share each step's launches. A system's
+ * arithmetic depends on that system alone: its x, iteration count and
+ * residuals are bitwise the same as from ascg_solve_batch with that system
+ * alone, whatever else runs beside it.
+ * Not safe for concurrent use from several threads. */
+typedef struct ascg_server_s* ascg_server;
+
+typedef struct {
+  int64_t tag;               /* the caller's tag from ascg_server_submit           */
+  ascg_result result;        /* as from ascg_solve_batch; result.launches = server
+                                steps from admission to completion               */
+  double queue_ms;           /* host time from submit to admission                */
+  double latency_ms;         /* host time from submit to completion               */
+  int64_t step_admitted;     /* server step at admission / at completion          */
+  int64_t step_done;
+} ascg_completion;
+
+typedef struct {
+  int64_t budget_bytes;      /* hbm_budget given at creation                       */
+  int64_t basis_bytes_total; /* part of the budget that holds bases                */
+  int64_t basis_bytes_used;  /* held by the running systems                        */
+  int systems_running;
+  int max_systems;
+  int64_t queued;            /* submitted, not yet admitted                        */
+  int64_t completions_pending; /* finished, not yet returned by ascg_server_step   */
+  int64_t steps;             /* steps that ran a block                             */
+  int64_t launches;          /* kernels launched so far                            */
+} ascg_server_stats;
+
+/* Creates a server. opts: as for ascg_solve_batch (ADAPTIVE or FIXED_S,
+ * MONOMIAL), history buffers NULL; eps_target is per request. hbm_budget:
+ * device bytes the server may hold for running systems. A system of n rows
+ * holds (2 s_max + 1) 8 round_up(n, 32) bytes of basis plus (2 s_max + 1)
+ * (s_max + 1) 8 bytes of Gram partials per 8192 rows; the whole budget is
+ * allocated here, as one arena for the bases and one buffer for the
+ * partials (plus about 16 bytes per 256 rows of row tables outside it).
+ * max_systems: most systems running at once (1 .. 2^20). All work is ordered
+ * on cuda_stream. The operators are the caller's and are not counted. */
+ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int max_systems,
+                               void* cuda_stream, ascg_server* out);
+
+/* Queues a request A x = b (FIFO). op: an operator on the current device; b,
+ * x: device double[n]; x holds x_1 and is updated in place while the system
+ * runs, so b, x and op must stay valid and untouched until its completion is
+ * returned. eps_target: relative target (eps* = eps_target ||b||). tag:
+ * returned in the completion. ASCG_ERR_INVALID if the system could never fit
+ * the budget. Host only: nothing is launched. */
+ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, double* x, double eps_target,
+                               int64_t tag);
+
+/* One step: admission (in submission order, stopping at the first request
+ * that does not fit yet), one block of every running system, completion of
+ * the systems that finished (true residual computed, memory freed). Writes
+ * up to cap completions to done (host) and their number to *ndone; the rest
+ * wait for the next call. *nactive: systems running after the step;
+ * *npending: requests not yet admitted plus completions not yet returned
+ * (the server is idle when both are 0). Synchronises the stream. */
+ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, int* ndone, int* nactive,
+                             int* npending);
+
+/* Counters of the server (host). */
+ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* stats);
+
+/* Synchronises the stream and frees the server. Requests not yet completed
+ * are dropped (their x holds whatever iterate was reached). NULL is
+ * accepted. */
+ascg_status ascg_server_destroy(ascg_server srv);
 
 /* Message of the last error on this thread ("" if none). */
 const char* ascg_last_error(void);

@@ -64,6 +64,17 @@ class ascg_result(C.Structure):
                 ("recover_flops", C.c_double), ("recover_bytes", C.c_double)]
 
 
+class ascg_completion(C.Structure):
+    _fields_ = [("tag", C.c_int64), ("result", ascg_result), ("queue_ms", C.c_double), ("latency_ms", C.c_double),
+                ("step_admitted", C.c_int64), ("step_done", C.c_int64)]
+
+
+class ascg_server_stats(C.Structure):
+    _fields_ = [("budget_bytes", C.c_int64), ("basis_bytes_total", C.c_int64), ("basis_bytes_used", C.c_int64),
+                ("systems_running", C.c_int), ("max_systems", C.c_int), ("queued", C.c_int64),
+                ("completions_pending", C.c_int64), ("steps", C.c_int64), ("launches", C.c_int64)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(
@@ -89,6 +100,12 @@ def _load():
                                       C.c_int, C.c_double, P, C.POINTER(ascg_block_info), P, P]),
         "ascg_recover": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
         "ascg_newton_shifts": (C.c_int, [P, P, C.c_int, C.c_int, P, P]),
+        "ascg_server_create": (C.c_int, [C.POINTER(ascg_options), I64, C.c_int, P, C.POINTER(P)]),
+        "ascg_server_submit": (C.c_int, [P, P, P, P, C.c_double, I64]),
+        "ascg_server_step": (C.c_int, [P, C.POINTER(ascg_completion), C.c_int, C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+        "ascg_server_info": (C.c_int, [P, C.POINTER(ascg_server_stats)]),
+        "ascg_server_destroy": (C.c_int, [P]),
         "ascg_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -194,6 +211,37 @@ def ascg_solve_batch(ops, bs, xs, opts, eps_targets=None, stream=None,
     st = _lib.ascg_solve_batch(count, oa, ba, xa, eps, C.byref(opts), res, _stream(stream))
     _check(st, "ascg_solve_batch", raise_on)
     return list(res), st
+
+
+def ascg_server_create(opts, hbm_budget, max_systems, stream=None):
+    """A solve server (continuous batching); returns its handle."""
+    h = C.c_void_p()
+    _check(_lib.ascg_server_create(C.byref(opts), int(hbm_budget), int(max_systems), _stream(stream), C.byref(h)),
+           "ascg_server_create")
+    return h.value
+
+
+def ascg_server_submit(srv, op, b, x, eps_target, tag):
+    """Queues A x = b (device arrays; x holds x_1 and receives the solution)."""
+    _check(_lib.ascg_server_submit(srv, op, _ptr(b), _ptr(x), float(eps_target), int(tag)), "ascg_server_submit")
+
+
+def ascg_server_step(srv, cap=64):
+    """One server step. Returns (completions, nactive, npending)."""
+    buf = (ascg_completion * max(int(cap), 1))()
+    nd, na, npd = C.c_int(), C.c_int(), C.c_int()
+    _check(_lib.ascg_server_step(srv, buf, int(cap), C.byref(nd), C.byref(na), C.byref(npd)), "ascg_server_step")
+    return [buf[i] for i in range(nd.value)], na.value, npd.value
+
+
+def ascg_server_info(srv):
+    st = ascg_server_stats()
+    _check(_lib.ascg_server_info(srv, C.byref(st)), "ascg_server_info")
+    return st
+
+
+def ascg_server_destroy(srv):
+    _check(_lib.ascg_server_destroy(srv), "ascg_server_destroy")
 
 
 def ascg_solve_host(op, b, x, opts=None, stream=None, raise_on=(ASCG_OK, ASCG_NOT_CONVERGED)):
@@ -303,4 +351,5 @@ def block_infos(count: int):
 EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
             "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc",
             "ascg_block_step", "ascg_recover",
-            "ascg_newton_shifts", "ascg_last_error"]
+            "ascg_newton_shifts", "ascg_server_create", "ascg_server_submit", "ascg_server_step",
+            "ascg_server_info", "ascg_server_destroy", "ascg_last_error"]

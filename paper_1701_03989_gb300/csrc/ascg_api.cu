@@ -609,306 +609,6 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
 }
 
 
-// ---------------------------------------------------------------------------
-// Batched solves (ascg_solve_batch): all systems advance block by block in
-// lockstep over one block-diagonal stacked operator.
-// ---------------------------------------------------------------------------
-
-// Device and pinned buffers of one batched call, freed on every exit path.
-struct BatchBufs {
-  int64_t* o_ptr = nullptr;
-  int32_t* o_col = nullptr;
-  double* o_val = nullptr;
-  double* diag = nullptr;
-  int* slice_sys = nullptr;
-  double* Y = nullptr;
-  double* xb = nullptr;
-  double* bb = nullptr;
-  double* scratch = nullptr;
-  BlockState* bst = nullptr;
-  double* G = nullptr;
-  double* coords = nullptr;
-  int* sys_steps = nullptr;
-  int* sys_w = nullptr;
-  GramItem* items = nullptr;
-  int* item0 = nullptr;
-  int* nitems = nullptr;
-  double* partials = nullptr;
-  int64_t* row0 = nullptr;
-  int64_t* nrows = nullptr;
-  double* sums = nullptr;
-  double* params = nullptr;
-  double* res_hist = nullptr;
-  double* ab_hist = nullptr;
-  BlockState* h_bst = nullptr;
-  int* h_int = nullptr;  // steps[count], w[count]
-  double* h_sums = nullptr;
-  ~BatchBufs() {
-    dev_free(o_ptr); dev_free(o_col); dev_free(o_val); dev_free(diag); dev_free(slice_sys); dev_free(Y);
-    dev_free(xb); dev_free(bb); dev_free(scratch); dev_free(bst); dev_free(G); dev_free(coords);
-    dev_free(sys_steps); dev_free(sys_w); dev_free(items); dev_free(item0); dev_free(nitems); dev_free(partials);
-    dev_free(row0); dev_free(nrows); dev_free(sums); dev_free(params); dev_free(res_hist); dev_free(ab_hist);
-    if (h_bst) cudaFreeHost(h_bst);
-    if (h_int) cudaFreeHost(h_int);
-    if (h_sums) cudaFreeHost(h_sums);
-  }
-};
-
-ascg_status solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
-                        const double* eps_target, const ascg_options& o, ascg_result* results, cudaStream_t s) {
-  int dev = 0;
-  ASCG_CUDA(cudaGetDevice(&dev));
-  for (int q = 0; q < count; ++q) {
-    if (!ops[q] || !b[q] || !x[q]) return fail(ASCG_ERR_INVALID, "ops, b and x must hold non-NULL entries");
-    if (ops[q]->device != dev) return fail(ASCG_ERR_INVALID, "every operator must live on the current device");
-    if (eps_target && !(eps_target[q] >= 0.0 && std::isfinite(eps_target[q])))
-      return fail(ASCG_ERR_INVALID, "eps_target entries must be finite and >= 0");
-  }
-  // layout: system q owns slices [slice0, slice0 + slices) and rows [32 slice0, ...)
-  std::vector<int64_t> slice0(count), nsl(count), elem0(count), row0(count), nq(count);
-  int64_t tot_sl = 0, tot_el = 0;
-  for (int q = 0; q < count; ++q) {
-    nq[q] = ops[q]->n;
-    nsl[q] = (nq[q] + kSlice - 1) / kSlice;
-    slice0[q] = tot_sl;
-    row0[q] = kSlice * tot_sl;
-    elem0[q] = tot_el;
-    tot_sl += nsl[q];
-    tot_el += ops[q]->o_len;
-  }
-  const int64_t n_tot = kSlice * tot_sl;
-  if (n_tot > 0x7fffffffll) return fail(ASCG_ERR_INVALID, "the batch exceeds 2^31 rows");
-  std::vector<GramItem> items;
-  std::vector<int> item0(count), nitems(count);
-  for (int q = 0; q < count; ++q) {
-    item0[q] = (int)items.size();
-    for (int64_t r = 0; r < nq[q]; r += kGramItemRows)
-      items.push_back(GramItem{row0[q] + r, (int)std::min<int64_t>(kGramItemRows, nq[q] - r), q});
-    nitems[q] = (int)items.size() - item0[q];
-  }
-  std::vector<int> slice_sys(tot_sl);
-  for (int q = 0; q < count; ++q)
-    for (int64_t k = 0; k < nsl[q]; ++k) slice_sys[slice0[q] + k] = q;
-
-  const int W = 2 * o.s_max + 1;
-  const int NPW = W * (W + 1) / 2;
-  const int64_t ld = n_tot;
-  const int64_t g_stride = (int64_t)kMaxW * kMaxW, c_stride = 3 * kMaxW;
-  const int rcap = o.res_hist ? std::max(o.res_hist_cap, 1) : 0;
-  const int abcap = (o.alpha_hist && o.beta_hist) ? std::max(o.coef_hist_cap, 1) : 0;
-  BatchBufs B;
-  ASCG_TRY(dev_alloc(&B.o_ptr, (size_t)tot_sl + 1));
-  ASCG_TRY(dev_alloc(&B.o_col, (size_t)std::max<int64_t>(tot_el, 1)));
-  ASCG_TRY(dev_alloc(&B.o_val, (size_t)std::max<int64_t>(tot_el, 1)));
-  ASCG_TRY(dev_alloc(&B.diag, (size_t)n_tot));
-  ASCG_TRY(dev_alloc(&B.slice_sys, (size_t)tot_sl));
-  ASCG_TRY(dev_alloc(&B.Y, (size_t)W * ld));
-  ASCG_TRY(dev_alloc(&B.xb, (size_t)n_tot));
-  ASCG_TRY(dev_alloc(&B.bb, (size_t)n_tot));
-  ASCG_TRY(dev_alloc(&B.scratch, (size_t)n_tot));
-  ASCG_TRY(dev_alloc(&B.bst, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.G, (size_t)count * g_stride));
-  ASCG_TRY(dev_alloc(&B.coords, (size_t)count * c_stride));
-  ASCG_TRY(dev_alloc(&B.sys_steps, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.sys_w, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.items, items.size()));
-  ASCG_TRY(dev_alloc(&B.item0, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.nitems, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.partials, items.size() * NPW));
-  ASCG_TRY(dev_alloc(&B.row0, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.nrows, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.sums, (size_t)count));
-  ASCG_TRY(dev_alloc(&B.params, (size_t)3 * kMaxS));
-  if (rcap) ASCG_TRY(dev_alloc(&B.res_hist, (size_t)count * rcap));
-  if (abcap) ASCG_TRY(dev_alloc(&B.ab_hist, (size_t)count * 2 * abcap));
-  ASCG_CUDA(cudaMallocHost((void**)&B.h_bst, sizeof(BlockState) * count));
-  ASCG_CUDA(cudaMallocHost((void**)&B.h_int, sizeof(int) * 2 * count));
-  ASCG_CUDA(cudaMallocHost((void**)&B.h_sums, sizeof(double) * count));
-
-  // stacked operator, right-hand sides and starting vectors
-  ASCG_CUDA(cudaMemsetAsync(B.diag, 0, sizeof(double) * n_tot, s));
-  ASCG_CUDA(cudaMemsetAsync(B.xb, 0, sizeof(double) * n_tot, s));
-  ASCG_CUDA(cudaMemsetAsync(B.bb, 0, sizeof(double) * n_tot, s));
-  ASCG_CUDA(cudaMemsetAsync(B.Y, 0, sizeof(double) * W * ld, s));
-  ASCG_CUDA(cudaMemsetAsync(B.coords, 0, sizeof(double) * count * c_stride, s));
-  for (int q = 0; q < count; ++q) {
-    const ascg_op op = ops[q];
-    if (op->o_len > 0) {
-      ASCG_CUDA(cudaMemcpyAsync(B.o_val + elem0[q], op->o_val, sizeof(double) * op->o_len, cudaMemcpyDeviceToDevice, s));
-      ASCG_CUDA(launch_add_offset_i32(B.o_col + elem0[q], op->o_col, op->o_len, (int32_t)row0[q], s));
-    }
-    ASCG_CUDA(launch_add_offset_i64(B.o_ptr + slice0[q], op->o_ptr, nsl[q], elem0[q], s));
-    ASCG_CUDA(cudaMemcpyAsync(B.diag + row0[q], op->diag, sizeof(double) * nq[q], cudaMemcpyDeviceToDevice, s));
-    ASCG_CUDA(cudaMemcpyAsync(B.xb + row0[q], x[q], sizeof(double) * nq[q], cudaMemcpyDeviceToDevice, s));
-    ASCG_CUDA(cudaMemcpyAsync(B.bb + row0[q], b[q], sizeof(double) * nq[q], cudaMemcpyDeviceToDevice, s));
-  }
-  ASCG_CUDA(cudaMemcpyAsync(B.o_ptr + tot_sl, &tot_el, sizeof(int64_t), cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.slice_sys, slice_sys.data(), sizeof(int) * tot_sl, cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.items, items.data(), sizeof(GramItem) * items.size(), cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.item0, item0.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.nitems, nitems.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.row0, row0.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.nrows, nq.data(), sizeof(int64_t) * count, cudaMemcpyHostToDevice, s));
-  {
-    double hp[3 * kMaxS];
-    basis_params(o, hp, hp + kMaxS, hp + 2 * kMaxS);  // monomial: theta = sigma = 0, gamma = 1
-    ASCG_CUDA(cudaMemcpyAsync(B.params, hp, sizeof(hp), cudaMemcpyHostToDevice, s));
-  }
-  const DevSell Ob{n_tot, B.o_ptr, B.o_col, B.o_val};
-  double* p = B.Y;
-  double* r = B.Y + ld;
-  // ||b_q||, r_1 = b - A x_1, p_1 = r_1, ||r_1||
-  std::vector<double> bnorm(count), rnorm0(count);
-  ASCG_CUDA(launch_seg_sumsq(B.bb, B.row0, B.nrows, count, B.sums, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.h_sums, B.sums, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-  ASCG_CUDA(cudaStreamSynchronize(s));
-  for (int q = 0; q < count; ++q) bnorm[q] = std::sqrt(B.h_sums[q]);
-  ASCG_CUDA(launch_batch_residual(Ob, B.diag, B.bb, B.xb, r, p, s));
-  ASCG_CUDA(launch_seg_sumsq(r, B.row0, B.nrows, count, B.sums, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.h_sums, B.sums, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-  ASCG_CUDA(cudaStreamSynchronize(s));
-  for (int q = 0; q < count; ++q) rnorm0[q] = std::sqrt(std::max(B.h_sums[q], 0.0));
-
-  std::vector<int> m(count, 0), kb(count, 0), s_prev(count, 0), nb_info(count, 0), wasted(count, 0);
-  std::vector<char> active(count, 0);
-  std::vector<ascg_status> status(count, ASCG_OK);
-  std::vector<double> eps_star(count), rel_upd(count);
-  for (int q = 0; q < count; ++q) {
-    if (!std::isfinite(bnorm[q])) return fail(ASCG_ERR_INVALID, "b is not finite");
-    eps_star[q] = (eps_target ? eps_target[q] : o.eps_target) * bnorm[q];
-    rel_upd[q] = bnorm[q] > 0.0 ? rnorm0[q] / bnorm[q] : 0.0;
-    active[q] = bnorm[q] > 0.0 && rnorm0[q] > eps_star[q] && o.max_iters > 0;
-    if (bnorm[q] > 0.0 && rnorm0[q] > eps_star[q] && o.max_iters == 0) status[q] = ASCG_NOT_CONVERGED;
-    if (rcap) {
-      const double rel = rel_upd[q];
-      ASCG_CUDA(cudaMemcpyAsync(B.res_hist + (int64_t)q * rcap, &rel, sizeof(double), cudaMemcpyHostToDevice, s));
-    }
-  }
-  int* h_steps = B.h_int;
-  int* h_w = B.h_int + count;
-  int super_blocks = 0;
-  for (;;) {
-    int max_sbar = 0;
-    for (int q = 0; q < count; ++q) {
-      BlockState& hb = B.h_bst[q];
-      std::memset(&hb, 0, sizeof(hb));
-      if (!active[q]) {
-        h_steps[q] = 0;
-        h_w[q] = 0;
-        continue;
-      }
-      const int sbar = o.method == ASCG_FIXED_S ? o.s_max : (kb[q] == 0 ? o.s0 : std::min(s_prev[q] + o.f, o.s_max));
-      hb.sbar = sbar;
-      hb.method = o.method;
-      hb.check_in_loop = o.check_in_loop;
-      hb.max_steps = o.max_iters - m[q];
-      hb.m = m[q];
-      hb.k = kb[q];
-      hb.eps_star = eps_star[q];
-      hb.c = o.c;
-      hb.bnorm = bnorm[q];
-      hb.sqrt_n = std::sqrt((double)nq[q]);
-      hb.active = 1;
-      h_steps[q] = sbar;
-      h_w[q] = 2 * sbar + 1;
-      max_sbar = std::max(max_sbar, sbar);
-    }
-    if (max_sbar == 0) break;
-    ASCG_CUDA(cudaMemcpyAsync(B.bst, B.h_bst, sizeof(BlockState) * count, cudaMemcpyHostToDevice, s));
-    ASCG_CUDA(cudaMemcpyAsync(B.sys_steps, h_steps, sizeof(int) * count, cudaMemcpyHostToDevice, s));
-    ASCG_CUDA(cudaMemcpyAsync(B.sys_w, h_w, sizeof(int) * count, cudaMemcpyHostToDevice, s));
-    for (int j = 0; j < max_sbar; ++j) ASCG_CUDA(launch_mpk_batch_step(Ob, B.diag, B.slice_sys, B.sys_steps, B.Y, ld, j, s));
-    const int Wb = 2 * max_sbar + 1;
-    ASCG_CUDA(launch_gram_items(Wb, B.Y, ld, B.items, (int)items.size(), B.sys_w, B.partials, s));
-    ASCG_CUDA(launch_gram_items_finalize(Wb, B.partials, B.item0, B.nitems, B.sys_w, count, B.G, g_stride, s));
-    if (o.method == ASCG_ADAPTIVE) ASCG_CUDA(launch_kappa_batch(B.G, g_stride, B.bst, count, max_sbar, s));
-    ASCG_CUDA(launch_ctrl_batch(B.G, g_stride, B.params, B.params + kMaxS, B.params + 2 * kMaxS, B.bst, count,
-                                B.coords, c_stride, B.res_hist, rcap, B.ab_hist, abcap, s));
-    ASCG_CUDA(launch_recover_batch(Wb, n_tot, B.Y, ld, B.slice_sys, B.sys_w, B.coords, c_stride, B.xb, r, p, s));
-    ASCG_CUDA(cudaMemcpyAsync(B.h_bst, B.bst, sizeof(BlockState) * count, cudaMemcpyDeviceToHost, s));
-    ASCG_CUDA(cudaStreamSynchronize(s));
-    ++super_blocks;
-    for (int q = 0; q < count; ++q) {
-      if (!active[q]) continue;
-      const BlockState& out = B.h_bst[q];
-      const int sbar = h_steps[q];
-      if (o.block_hist && nb_info[q] < o.block_hist_cap) {
-        ascg_block_info& bi = o.block_hist[(int64_t)q * o.block_hist_cap + nb_info[q]];
-        std::memset(&bi, 0, sizeof(bi));
-        bi.sbar = sbar;
-        bi.stilde = out.stilde;
-        bi.s_k = out.s_k;
-        bi.stop = out.stop;
-        bi.m = m[q];
-        bi.rnorm = out.rnorm;
-        bi.threshold = out.threshold;
-        bi.gamma = out.gamma;
-        for (int i = 0; i < sbar; ++i) bi.sqrt_kappa[i] = o.method == ASCG_ADAPTIVE ? out.sqrt_kappa[i] : 0.0;
-      }
-      ++nb_info[q];
-      wasted[q] += 2 * (sbar - out.s_k);
-      if (out.s_k == 0) {
-        status[q] = ASCG_ERR_BREAKDOWN;
-        active[q] = 0;
-        continue;
-      }
-      rel_upd[q] = out.rel_res;
-      m[q] += out.s_k;
-      s_prev[q] = out.s_k;
-      ++kb[q];
-      if (out.converged) {
-        active[q] = 0;
-      } else if (m[q] >= o.max_iters) {
-        status[q] = ASCG_NOT_CONVERGED;
-        active[q] = 0;
-      }
-    }
-  }
-  // true residuals; x back to the caller (b = 0: x = 0)
-  ASCG_CUDA(launch_batch_residual(Ob, B.diag, B.bb, B.xb, B.scratch, nullptr, s));
-  ASCG_CUDA(launch_seg_sumsq(B.scratch, B.row0, B.nrows, count, B.sums, s));
-  ASCG_CUDA(cudaMemcpyAsync(B.h_sums, B.sums, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
-  for (int q = 0; q < count; ++q) {
-    if (bnorm[q] == 0.0)
-      ASCG_CUDA(cudaMemsetAsync(x[q], 0, sizeof(double) * nq[q], s));
-    else
-      ASCG_CUDA(cudaMemcpyAsync(x[q], B.xb + row0[q], sizeof(double) * nq[q], cudaMemcpyDeviceToDevice, s));
-  }
-  ASCG_CUDA(cudaStreamSynchronize(s));
-  for (int q = 0; q < count; ++q) {
-    if (o.res_hist && rcap)
-      ASCG_CUDA(cudaMemcpy(o.res_hist + (int64_t)q * o.res_hist_cap, B.res_hist + (int64_t)q * rcap,
-                           sizeof(double) * std::min(m[q] + 1, o.res_hist_cap), cudaMemcpyDeviceToHost));
-    if (abcap && m[q] > 0) {
-      const int na = std::min(m[q], o.coef_hist_cap);
-      ASCG_CUDA(cudaMemcpy(o.alpha_hist + (int64_t)q * o.coef_hist_cap, B.ab_hist + (int64_t)q * 2 * abcap,
-                           sizeof(double) * na, cudaMemcpyDeviceToHost));
-      ASCG_CUDA(cudaMemcpy(o.beta_hist + (int64_t)q * o.coef_hist_cap, B.ab_hist + (int64_t)q * 2 * abcap + abcap,
-                           sizeof(double) * na, cudaMemcpyDeviceToHost));
-    }
-  }
-  ascg_status worst = ASCG_OK;
-  for (int q = 0; q < count; ++q) {
-    if (results) {
-      ascg_result& rq = results[q];
-      std::memset(&rq, 0, sizeof(rq));
-      rq.status = status[q];
-      rq.iters = m[q];
-      rq.blocks = kb[q];
-      rq.grid_reductions = kb[q];
-      rq.wasted_vecs = wasted[q];
-      rq.launches = super_blocks;  // lockstep blocks of the whole batch
-      rq.bnorm = bnorm[q];
-      rq.rel_res_updated = rel_upd[q];
-      rq.rel_res_true = bnorm[q] > 0.0 ? std::sqrt(std::max(B.h_sums[q], 0.0)) / bnorm[q] : 0.0;
-    }
-    if (status[q] == ASCG_ERR_BREAKDOWN) worst = ASCG_ERR_BREAKDOWN;
-    else if (status[q] == ASCG_NOT_CONVERGED && worst == ASCG_OK) worst = ASCG_NOT_CONVERGED;
-  }
-  if (worst == ASCG_ERR_BREAKDOWN) g_err = "breakdown in at least one system (see results[q].status)";
-  return worst;
-}
-
 void zero_result(ascg_result* r) {
   if (r) std::memset(r, 0, sizeof(*r));
 }
@@ -1088,7 +788,7 @@ ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const*
   if ((o.res_hist && o.res_hist_cap < 1) || (o.block_hist && o.block_hist_cap < 1))
     return fail(ASCG_ERR_INVALID, "history capacities must be >= 1");
   try {
-    return solve_batch(count, ops, b, x, eps_target, o, results, (cudaStream_t)cuda_stream);
+    return lockstep_solve_batch(count, ops, b, x, eps_target, o, results, (cudaStream_t)cuda_stream);
   } catch (const std::bad_alloc&) {
     return fail(ASCG_ERR_OOM, "host allocation failed");
   }
@@ -1250,4 +950,18 @@ const char* ascg_last_error(void) { return g_err.c_str(); }
 
 namespace ascg {
 void set_last_error(const std::string& msg) { g_err = msg; }
+
+ascg_status check_options(const ascg_options& o) { return check_opts(o); }
+
+ascg_status op_split_desc(ascg_op op, SysDesc* d, int* device) {
+  if (!op) return fail(ASCG_ERR_INVALID, "op is NULL");
+  std::memset(d, 0, sizeof(*d));
+  d->n = op->n;
+  d->o_ptr = op->o_ptr;
+  d->o_col = op->o_col;
+  d->o_val = op->o_val;
+  d->diag = op->diag;
+  *device = op->device;
+  return ASCG_OK;
+}
 }  // namespace ascg

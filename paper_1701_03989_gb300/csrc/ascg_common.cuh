@@ -115,10 +115,12 @@ struct GramItem {
   int sys;
 };
 constexpr int kGramItemRows = 8192;
-// FP64 partials (W columns, W odd <= 33) of every item; items of systems with
-// sys_w 0 are skipped. partials: nitems x W(W+1)/2.
-cudaError_t launch_gram_items(int W, const double* Y, int64_t ldY, const GramItem* items, int nitems,
-                              const int* sys_w, double* partials, cudaStream_t s);
+// FP64 partials (W columns, W odd <= 33) of every item, rows read from the
+// item's system (descs[sys].Y); items of systems with sys_w 0 are skipped.
+// partials: nitems x W(W+1)/2.
+struct SysDesc;
+cudaError_t launch_gram_items(int W, const SysDesc* descs, const GramItem* items, int nitems, const int* sys_w,
+                              double* partials, cudaStream_t s);
 // G of each active system q (w_q = sys_w[q] x w_q, stride w_q) at G + q * g_stride.
 cudaError_t launch_gram_items_finalize(int W, const double* partials, const int* sys_item0, const int* sys_nitems,
                                        const int* sys_w, int count, double* G, int64_t g_stride, cudaStream_t s);
@@ -140,24 +142,39 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s);
 
-// Batched solves (kernels_batch.cu): rows of all systems concatenated, each
-// system padded to whole 32-row slices; slice_sys maps a slice to its system.
-// Matrix powers step j in the monomial basis for every system q with
-// j < sys_steps[q].
-cudaError_t launch_mpk_batch_step(const DevSell& O, const double* diag, const int* slice_sys, const int* sys_steps,
-                                  double* Y, int64_t ldY, int j, cudaStream_t s);
-// r = b - (D + O) x over all rows; p = r too when p != nullptr.
-cudaError_t launch_batch_residual(const DevSell& O, const double* diag, const double* b, const double* x, double* r,
-                                  double* p, cudaStream_t s);
-// out[q] = sum of squares of u over system q's rows, fixed order.
-cudaError_t launch_seg_sumsq(const double* u, const int64_t* sys_row0, const int64_t* sys_n, int count, double* out,
+// Many systems in lockstep (kernels_batch.cu): a device table of per-system
+// descriptors and row items of one system each (up to kRowItem rows starting
+// on a 32-row slice).
+struct SysDesc {
+  int64_t n;
+  const int64_t* o_ptr;   // O (off-diagonal part of A) in sliced ELL form
+  const int32_t* o_col;
+  const double* o_val;
+  const double* diag;     // D
+  double* Y;              // basis, column 0 = p, column 1 = r
+  int64_t ldY;
+  double* x;
+  const double* b;
+};
+constexpr int kRowItem = 256;
+struct RowItem {
+  int sys;
+  int row0;
+  int nrows;
+  int pad_;
+};
+// Matrix powers step j (monomial basis) of every system q with j < sys_steps[q].
+cudaError_t launch_mpk_items(const SysDesc* descs, const RowItem* items, int nitems, const int* sys_steps, int j,
                              cudaStream_t s);
-// Recovery for every active system (w_q = sys_w[q] > 0), coordinates at coords + q * c_stride.
-cudaError_t launch_recover_batch(int W, int64_t n, const double* Y, int64_t ldY, const int* slice_sys,
-                                 const int* sys_w, const double* coords, int64_t c_stride, double* x, double* r,
-                                 double* p, cudaStream_t s);
-cudaError_t launch_add_offset_i32(int32_t* dst, const int32_t* src, int64_t n, int32_t off, cudaStream_t s);
-cudaError_t launch_add_offset_i64(int64_t* dst, const int64_t* src, int64_t n, int64_t off, cudaStream_t s);
+// b - A x of the systems with sel[q] != 0: into Y columns 1 and 0, or into column 2.
+cudaError_t launch_residual_items(const SysDesc* descs, const RowItem* items, int nitems, const int* sel,
+                                  int into_col2, cudaStream_t s);
+// out[q] = sum of squares (fixed order) of b (which 0) or Y column `which` of the systems in list.
+cudaError_t launch_seg_sumsq(const SysDesc* descs, const int* list, int nlist, int which, double* out,
+                             cudaStream_t s);
+// Recovery of every system with w_q = sys_w[q] > 0 (W >= max w_q), coordinates at coords + q * c_stride.
+cudaError_t launch_recover_items(int W, const SysDesc* descs, const RowItem* items, int nitems, const int* sys_w,
+                                 const double* coords, int64_t c_stride, cudaStream_t s);
 
 // Recovery (eq. coords).
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
@@ -249,5 +266,9 @@ cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_i
 
 // Sets the message that ascg_last_error() returns on this thread.
 void set_last_error(const std::string& msg);
+// Batched solves on the lockstep engine (lockstep.cu).
+ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
+                                 const double* eps_target, const ascg_options& o, ascg_result* results,
+                                 cudaStream_t s);
 
 }  // namespace ascg

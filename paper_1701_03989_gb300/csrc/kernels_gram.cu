@@ -125,14 +125,16 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n
 // system). Items depend only on the system's own size, so a system's Gram is
 // the same alone and in any batch. Items of inactive systems (sys_w 0) skip.
 template <int W>
-__global__ void __launch_bounds__(kGramThreads, 1) gram_items_kernel(const double* __restrict__ Y, int64_t ldY,
+__global__ void __launch_bounds__(kGramThreads, 1) gram_items_kernel(const SysDesc* __restrict__ descs,
                                                                       const GramItem* __restrict__ items,
                                                                       const int* __restrict__ sys_w,
                                                                       double* __restrict__ partials) {
   constexpr int NP = W * (W + 1) / 2;
   const GramItem it = items[blockIdx.x];
   if (sys_w[it.sys] == 0) return;  // uniform over the CTA
-  gram_chunks<W>(it.nrows, Y + it.row0, ldY, 0, (it.nrows + kChunk - 1) / kChunk, partials + (int64_t)blockIdx.x * NP);
+  const SysDesc& d = descs[it.sys];
+  gram_chunks<W>(it.nrows, d.Y + it.row0, d.ldY, 0, (it.nrows + kChunk - 1) / kChunk,
+                 partials + (int64_t)blockIdx.x * NP);
 }
 
 // Four threads per pair (lanes 4q .. 4q+3 of a warp): thread t adds the
@@ -239,13 +241,13 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
   }
 }
 
-cudaError_t launch_gram_items(int W, const double* Y, int64_t ldY, const GramItem* items, int nitems,
-                              const int* sys_w, double* partials, cudaStream_t s) {
+cudaError_t launch_gram_items(int W, const SysDesc* descs, const GramItem* items, int nitems, const int* sys_w,
+                              double* partials, cudaStream_t s) {
   if (nitems < 1) return cudaSuccess;
   switch (W) {
 #define ASCG_GI(WW)                                                                            \
   case WW:                                                                                     \
-    gram_items_kernel<WW><<<nitems, kGramThreads, 0, s>>>(Y, ldY, items, sys_w, partials); \
+    gram_items_kernel<WW><<<nitems, kGramThreads, 0, s>>>(descs, items, sys_w, partials);  \
     return cudaGetLastError();
     ASCG_GI(3) ASCG_GI(5) ASCG_GI(7) ASCG_GI(9) ASCG_GI(11) ASCG_GI(13) ASCG_GI(15) ASCG_GI(17) ASCG_GI(19)
     ASCG_GI(21) ASCG_GI(23) ASCG_GI(25) ASCG_GI(27) ASCG_GI(29) ASCG_GI(31) ASCG_GI(33)

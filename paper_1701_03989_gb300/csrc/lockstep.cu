@@ -1,0 +1,841 @@
+// Lockstep engine: many independent SPD systems, each running Alg. 4 (or
+// Alg. 2) on its own operator, advance one block at a time together. It is
+// the engine behind ascg_solve_batch and the solve server (ascg_server_*).
+//
+// Every system sits in a lane. A lane holds the system's descriptor (its
+// operator, its basis Y, x and b), its controller state and its Gram and
+// coordinate slots. One "super-block" runs one block of every active lane:
+//   sbar_max matrix powers steps  (mpk_items_kernel, one row item per CTA)
+//   Gram partials and their fixed-order sum  (gram_items_kernel, finalize)
+//   condition estimates, controller  (kappa_kernel, ctrl_kernel, per lane)
+//   recovery  (recover_items_kernel)
+// so a super-block is the same dozen launches for any number of systems.
+// The host reads back one BlockState per lane, since the next block's basis
+// size sbar_k = min(s_{k-1} + f, s_max) depends on it (Alg. 4).
+//
+// Each lane's arithmetic reads that lane's data only, in an order fixed by
+// its own size: a system's result is bitwise the same alone and in any mix,
+// whichever lane it lands in and whoever else is running.
+//
+// The bases live in one device arena (first-fit, merging free neighbours),
+// so admitting and retiring systems allocates nothing from CUDA.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <deque>
+#include <iterator>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "ascg_common.cuh"
+
+namespace ascg {
+
+// Defined in ascg_api.cu.
+ascg_status check_options(const ascg_options& o);
+ascg_status op_split_desc(ascg_op op, SysDesc* d, int* device);
+
+namespace {
+
+ascg_status lfail(ascg_status st, const std::string& msg) {
+  set_last_error(msg);
+  return st;
+}
+
+#define LS_CUDA(call)                                                                          \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return lfail(e_ == cudaErrorMemoryAllocation ? ASCG_ERR_OOM : ASCG_ERR_CUDA,             \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+#define LS_TRY(expr)                \
+  do {                              \
+    ascg_status s_ = (expr);        \
+    if (s_ != ASCG_OK) return s_;   \
+  } while (0)
+
+template <class T>
+ascg_status dalloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return lfail(ASCG_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return ASCG_OK;
+}
+
+template <class T>
+ascg_status halloc(T** p, size_t count) {
+  *p = nullptr;
+  if (count == 0) count = 1;
+  cudaError_t e = cudaMallocHost((void**)p, count * sizeof(T));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return lfail(ASCG_ERR_OOM, std::string("cudaMallocHost: ") + cudaGetErrorString(e));
+  }
+  return ASCG_OK;
+}
+
+template <class T>
+void dfree(T*& p) {
+  if (p) cudaFree(p);
+  p = nullptr;
+}
+
+template <class T>
+void hfree(T*& p) {
+  if (p) cudaFreeHost(p);
+  p = nullptr;
+}
+
+int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
+
+double now_ms() {
+  using namespace std::chrono;
+  return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+// First-fit allocator over one device allocation. Blocks are multiples of
+// kAlign bytes; a freed block merges with free neighbours.
+class Arena {
+ public:
+  static constexpr size_t kAlign = 256;
+  ~Arena() { dfree(base_); }
+  ascg_status init(size_t bytes) {
+    size_ = (size_t)round_up((int64_t)bytes, kAlign);
+    if (size_ > 0) {
+      LS_TRY(dalloc(&base_, size_));
+      free_[0] = size_;
+    }
+    return ASCG_OK;
+  }
+  static size_t rounded(size_t bytes) { return (size_t)round_up((int64_t)bytes, kAlign); }
+  bool take(size_t bytes, size_t* off) {
+    bytes = rounded(bytes);
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < bytes) continue;
+      *off = it->first;
+      const size_t rest = it->second - bytes, next = it->first + bytes;
+      free_.erase(it);
+      if (rest) free_[next] = rest;
+      live_[*off] = bytes;
+      used_ += bytes;
+      return true;
+    }
+    return false;
+  }
+  void give(size_t off) {
+    auto l = live_.find(off);
+    if (l == live_.end()) return;
+    size_t bytes = l->second;
+    live_.erase(l);
+    used_ -= bytes;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + bytes) {
+      bytes += nx->second;
+      nx = free_.erase(nx);
+    }
+    if (nx != free_.begin()) {
+      auto pv = std::prev(nx);
+      if (pv->first + pv->second == off) {
+        pv->second += bytes;
+        return;
+      }
+    }
+    free_[off] = bytes;
+  }
+  double* at(size_t off) const { return (double*)(base_ + off); }
+  size_t size() const { return size_; }
+  size_t used() const { return used_; }
+
+ private:
+  char* base_ = nullptr;
+  size_t size_ = 0, used_ = 0;
+  std::map<size_t, size_t> free_, live_;  // offset -> bytes
+};
+
+}  // namespace
+
+// One system: what the caller handed in, and its progress.
+struct LaneSys {
+  ascg_op op = nullptr;
+  SysDesc d{};
+  double eps_target = 0.0;
+  int64_t tag = 0;
+  size_t off = 0, bytes = 0;
+  int m = 0, kb = 0, s_prev = 0, nb_info = 0, wasted = 0, sbar = 0;
+  double bnorm = 0.0, eps_star = 0.0, rel_upd = 0.0, rnorm0 = 0.0, rel_true = 0.0;
+  bool active = false, done = false;
+  ascg_status status = ASCG_OK;
+  double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
+  int64_t step_admit = 0, step_done = 0;
+};
+
+class Lockstep {
+ public:
+  ~Lockstep() { release(); }
+
+  // lanes: most systems in flight; y_bytes: arena size for the bases; gitems,
+  // ritems: initial Gram and row item capacities (they grow on demand).
+  ascg_status init(const ascg_options& o, int lanes, size_t y_bytes, int64_t gitems, int64_t ritems,
+                   int rcap, int abcap, cudaStream_t s) {
+    o_ = o;
+    s_ = s;
+    lanes_ = lanes;
+    rcap_ = rcap;
+    abcap_ = abcap;
+    wcols_ = 2 * o.s_max + 1;
+    npw_ = wcols_ * (wcols_ + 1) / 2;
+    LS_TRY(arena_.init(y_bytes));
+    LS_TRY(dalloc(&d_desc_, lanes));
+    LS_TRY(dalloc(&d_bst_, lanes));
+    LS_TRY(dalloc(&d_G_, (size_t)lanes * kGStride));
+    LS_TRY(dalloc(&d_coords_, (size_t)lanes * kCStride));
+    LS_TRY(dalloc(&d_int_, (size_t)6 * lanes));
+    LS_TRY(dalloc(&d_sums_, (size_t)2 * lanes));
+    LS_TRY(dalloc(&d_params_, (size_t)3 * kMaxS));
+    if (rcap_) LS_TRY(dalloc(&d_res_hist_, (size_t)lanes * rcap_));
+    if (abcap_) LS_TRY(dalloc(&d_ab_hist_, (size_t)lanes * 2 * abcap_));
+    LS_TRY(halloc(&h_desc_, lanes));
+    LS_TRY(halloc(&h_bst_, lanes));
+    LS_TRY(halloc(&h_int_, (size_t)6 * lanes));
+    LS_TRY(halloc(&h_sums_, (size_t)2 * lanes));
+    LS_TRY(grow_items(ritems, gitems));
+    std::memset(h_desc_, 0, sizeof(SysDesc) * lanes);
+    std::memset(h_bst_, 0, sizeof(BlockState) * lanes);
+    std::memset(h_int_, 0, sizeof(int) * 6 * lanes);
+    LS_CUDA(cudaMemsetAsync(d_coords_, 0, sizeof(double) * lanes * kCStride, s_));
+    LS_CUDA(cudaMemsetAsync(d_bst_, 0, sizeof(BlockState) * lanes, s_));
+    double hp[3 * kMaxS];  // monomial basis: theta = sigma = 0, gamma = 1
+    for (int j = 0; j < kMaxS; ++j) {
+      hp[j] = 0.0;
+      hp[kMaxS + j] = 0.0;
+      hp[2 * kMaxS + j] = 1.0;
+    }
+    LS_CUDA(cudaMemcpyAsync(d_params_, hp, sizeof(hp), cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaStreamSynchronize(s_));
+    lane_.assign(lanes, LaneSys());
+    used_.assign(lanes, 0);
+    return ASCG_OK;
+  }
+
+  // Device bytes one system of n rows holds while it runs: its basis Y
+  // (2 s_max + 1 columns of round_up(n, 32) doubles) and its Gram partials.
+  size_t footprint(int64_t n) const {
+    const int64_t ld = round_up(n, kSlice);
+    const int64_t items = (n + kGramItemRows - 1) / kGramItemRows;
+    return Arena::rounded((size_t)wcols_ * ld * sizeof(double)) + (size_t)items * npw_ * sizeof(double);
+  }
+  static int64_t gram_items_of(int64_t n) { return (n + kGramItemRows - 1) / kGramItemRows; }
+  static int64_t row_items_of(int64_t n) { return (n + kRowItem - 1) / kRowItem; }
+
+  // Prepares a system for admission (validates it; fills its descriptor but Y).
+  ascg_status prepare(ascg_op op, const double* b, double* x, double eps_target, int64_t tag, LaneSys* out) const {
+    if (!op || !b || !x) return lfail(ASCG_ERR_INVALID, "op, b and x must be non-NULL");
+    if (!(eps_target >= 0.0 && std::isfinite(eps_target)))
+      return lfail(ASCG_ERR_INVALID, "eps_target must be finite and >= 0");
+    int dev = 0, cur = 0;
+    LS_TRY(op_split_desc(op, &out->d, &dev));
+    LS_CUDA(cudaGetDevice(&cur));
+    if (dev != cur) return lfail(ASCG_ERR_INVALID, "every operator must live on the current device");
+    out->op = op;
+    out->d.b = b;
+    out->d.x = x;
+    out->d.ldY = round_up(out->d.n, kSlice);
+    out->eps_target = eps_target;
+    out->tag = tag;
+    out->bytes = (size_t)wcols_ * out->d.ldY * sizeof(double);
+    return ASCG_OK;
+  }
+
+  bool has_free_lane() const { return nused_ < lanes_; }
+
+  // Admits the systems (each into the lowest free lane), computes ||b||,
+  // r_1 = b - A x_1 into Y columns 1 and 0 and ||r_1||. Systems that need no
+  // block (b = 0, r_1 already small enough, max_iters = 0) are marked done.
+  // Stops at the first system the arena cannot place; *admitted tells how many.
+  ascg_status admit(std::vector<LaneSys>& sys, size_t first, size_t* admitted, std::vector<int>* lanes_out) {
+    *admitted = 0;
+    std::vector<int> fresh;
+    for (size_t i = first; i < sys.size(); ++i) {
+      if (nused_ >= lanes_) break;
+      size_t off = 0;
+      if (!arena_.take(sys[i].bytes, &off)) break;
+      int q = 0;
+      while (used_[q]) ++q;
+      LaneSys& L = lane_[q];
+      L = sys[i];
+      L.off = off;
+      L.d.Y = arena_.at(off);
+      used_[q] = 1;
+      ++nused_;
+      hi_ = std::max(hi_, q + 1);
+      h_desc_[q] = L.d;
+      fresh.push_back(q);
+      ++*admitted;
+    }
+    if (lanes_out) *lanes_out = fresh;
+    if (fresh.empty()) return ASCG_OK;
+    LS_TRY(rebuild_tables());
+    int* h_sel = h_int_ + 2 * lanes_;
+    int* h_list = h_int_ + 3 * lanes_;
+    for (int q = 0; q < hi_; ++q) h_sel[q] = 0;
+    for (size_t i = 0; i < fresh.size(); ++i) {
+      h_sel[fresh[i]] = 1;
+      h_list[i] = fresh[i];
+    }
+    int* d_sel = d_int_ + 2 * lanes_;
+    int* d_list = d_int_ + 3 * lanes_;
+    LS_CUDA(cudaMemcpyAsync(d_sel, h_sel, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemcpyAsync(d_list, h_list, sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, s_));
+    LS_CUDA(launch_seg_sumsq(d_desc_, d_list, (int)fresh.size(), 0, d_sums_, s_));
+    LS_CUDA(launch_residual_items(d_desc_, d_ritems_, (int)ritems_.size(), d_sel, 0, s_));
+    LS_CUDA(launch_seg_sumsq(d_desc_, d_list, (int)fresh.size(), 1, d_sums_ + lanes_, s_));
+    LS_CUDA(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * 2 * lanes_, cudaMemcpyDeviceToHost, s_));
+    LS_CUDA(cudaStreamSynchronize(s_));
+    launches_ += 3;
+    for (int q : fresh) {
+      LaneSys& L = lane_[q];
+      L.bnorm = std::sqrt(h_sums_[q]);
+      L.rnorm0 = std::sqrt(std::max(h_sums_[lanes_ + q], 0.0));
+      if (!std::isfinite(L.bnorm) || !std::isfinite(L.rnorm0)) {
+        L.status = ASCG_ERR_INVALID;
+        L.done = true;
+        continue;
+      }
+      L.eps_star = L.eps_target * L.bnorm;
+      L.rel_upd = L.bnorm > 0.0 ? L.rnorm0 / L.bnorm : 0.0;
+      const bool need = L.bnorm > 0.0 && L.rnorm0 > L.eps_star;
+      L.active = need && o_.max_iters > 0;
+      if (need && o_.max_iters == 0) L.status = ASCG_NOT_CONVERGED;
+      L.done = !L.active;
+      if (rcap_) {
+        const double rel = L.rel_upd;
+        LS_CUDA(cudaMemcpyAsync(d_res_hist_ + (int64_t)q * rcap_, &rel, sizeof(double), cudaMemcpyHostToDevice, s_));
+      }
+    }
+    return ASCG_OK;
+  }
+
+  // One block of every active lane. Lanes whose system finished in it are
+  // marked done.
+  ascg_status super_block(ascg_block_info* block_hist, int block_hist_cap) {
+    int* h_steps = h_int_;
+    int* h_w = h_int_ + lanes_;
+    int max_sbar = 0;
+    for (int q = 0; q < hi_; ++q) {
+      BlockState& hb = h_bst_[q];
+      std::memset(&hb, 0, sizeof(hb));
+      LaneSys& L = lane_[q];
+      if (!used_[q] || !L.active) {
+        h_steps[q] = 0;
+        h_w[q] = 0;
+        continue;
+      }
+      const int sbar = o_.method == ASCG_FIXED_S ? o_.s_max : (L.kb == 0 ? o_.s0 : std::min(L.s_prev + o_.f, o_.s_max));
+      L.sbar = sbar;
+      hb.sbar = sbar;
+      hb.method = o_.method;
+      hb.check_in_loop = o_.check_in_loop;
+      hb.max_steps = o_.max_iters - L.m;
+      hb.m = L.m;
+      hb.k = L.kb;
+      hb.eps_star = L.eps_star;
+      hb.c = o_.c;
+      hb.bnorm = L.bnorm;
+      hb.sqrt_n = std::sqrt((double)L.d.n);
+      hb.active = 1;
+      h_steps[q] = sbar;
+      h_w[q] = 2 * sbar + 1;
+      max_sbar = std::max(max_sbar, sbar);
+    }
+    if (max_sbar == 0) return ASCG_OK;
+    int* d_steps = d_int_;
+    int* d_w = d_int_ + lanes_;
+    int* d_item0 = d_int_ + 4 * lanes_;
+    int* d_nitems = d_int_ + 5 * lanes_;
+    const int nr = (int)ritems_.size(), ng = (int)gitems_.size();
+    LS_CUDA(cudaMemcpyAsync(d_bst_, h_bst_, sizeof(BlockState) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemcpyAsync(d_steps, h_steps, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
+    const int Wb = 2 * max_sbar + 1;
+    LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_w, d_partials_, s_));
+    LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_w, hi_, d_G_, kGStride, s_));
+    if (o_.method == ASCG_ADAPTIVE) LS_CUDA(launch_kappa_batch(d_G_, kGStride, d_bst_, hi_, max_sbar, s_));
+    LS_CUDA(launch_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_, hi_,
+                              d_coords_, kCStride, d_res_hist_, rcap_, d_ab_hist_, abcap_, s_));
+    LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
+    LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
+    LS_CUDA(cudaStreamSynchronize(s_));
+    ++super_blocks_;
+    launches_ += max_sbar + 4 + (o_.method == ASCG_ADAPTIVE);
+    for (int q = 0; q < hi_; ++q) {
+      LaneSys& L = lane_[q];
+      if (!used_[q] || !L.active) continue;
+      const BlockState& out = h_bst_[q];
+      const int sbar = L.sbar;
+      if (block_hist && L.nb_info < block_hist_cap) {
+        ascg_block_info& bi = block_hist[(int64_t)q * block_hist_cap + L.nb_info];
+        std::memset(&bi, 0, sizeof(bi));
+        bi.sbar = sbar;
+        bi.stilde = out.stilde;
+        bi.s_k = out.s_k;
+        bi.stop = out.stop;
+        bi.m = L.m;
+        bi.rnorm = out.rnorm;
+        bi.threshold = out.threshold;
+        bi.gamma = out.gamma;
+        for (int i = 0; i < sbar; ++i) bi.sqrt_kappa[i] = o_.method == ASCG_ADAPTIVE ? out.sqrt_kappa[i] : 0.0;
+      }
+      ++L.nb_info;
+      L.wasted += 2 * (sbar - out.s_k);
+      if (out.s_k == 0) {
+        L.status = ASCG_ERR_BREAKDOWN;
+        L.active = false;
+        L.done = true;
+        continue;
+      }
+      L.rel_upd = out.rel_res;
+      L.m += out.s_k;
+      L.s_prev = out.s_k;
+      ++L.kb;
+      if (out.converged) {
+        L.active = false;
+      } else if (L.m >= o_.max_iters) {
+        L.status = ASCG_NOT_CONVERGED;
+        L.active = false;
+      }
+      L.done = !L.active;
+    }
+    return ASCG_OK;
+  }
+
+  // True residuals ||b - A x|| / ||b|| of the done lanes that are still held
+  // (into Y column 2), and x = 0 for b = 0. Fills rel_true.
+  ascg_status finish(const std::vector<int>& lanes) {
+    if (lanes.empty()) return ASCG_OK;
+    int* h_sel = h_int_ + 2 * lanes_;
+    int* h_list = h_int_ + 3 * lanes_;
+    for (int q = 0; q < hi_; ++q) h_sel[q] = 0;
+    for (size_t i = 0; i < lanes.size(); ++i) {
+      h_sel[lanes[i]] = 1;
+      h_list[i] = lanes[i];
+    }
+    int* d_sel = d_int_ + 2 * lanes_;
+    int* d_list = d_int_ + 3 * lanes_;
+    LS_CUDA(cudaMemcpyAsync(d_sel, h_sel, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemcpyAsync(d_list, h_list, sizeof(int) * lanes.size(), cudaMemcpyHostToDevice, s_));
+    LS_CUDA(launch_residual_items(d_desc_, d_ritems_, (int)ritems_.size(), d_sel, 1, s_));
+    LS_CUDA(launch_seg_sumsq(d_desc_, d_list, (int)lanes.size(), 2, d_sums_, s_));
+    LS_CUDA(cudaMemcpyAsync(h_sums_, d_sums_, sizeof(double) * lanes_, cudaMemcpyDeviceToHost, s_));
+    launches_ += 2;
+    for (int q : lanes)
+      if (lane_[q].bnorm == 0.0) LS_CUDA(cudaMemsetAsync(lane_[q].d.x, 0, sizeof(double) * lane_[q].d.n, s_));
+    LS_CUDA(cudaStreamSynchronize(s_));
+    for (int q : lanes) {
+      LaneSys& L = lane_[q];
+      L.rel_true = L.bnorm > 0.0 ? std::sqrt(std::max(h_sums_[q], 0.0)) / L.bnorm : 0.0;
+    }
+    return ASCG_OK;
+  }
+
+  // Frees the lanes (their arena blocks return to the pool).
+  void retire(const std::vector<int>& lanes) {
+    for (int q : lanes) {
+      if (!used_[q]) continue;
+      arena_.give(lane_[q].off);
+      used_[q] = 0;
+      --nused_;
+      std::memset(&h_desc_[q], 0, sizeof(SysDesc));
+      lane_[q] = LaneSys();
+    }
+    while (hi_ > 0 && !used_[hi_ - 1]) --hi_;
+    dirty_ = true;
+  }
+
+  // Copies lane q's histories to the caller's rows (batched solves).
+  ascg_status copy_histories(int q, const ascg_options& o, int64_t row) {
+    const LaneSys& L = lane_[q];
+    if (o.res_hist && rcap_)
+      LS_CUDA(cudaMemcpy(o.res_hist + row * o.res_hist_cap, d_res_hist_ + (int64_t)q * rcap_,
+                         sizeof(double) * std::min(L.m + 1, o.res_hist_cap), cudaMemcpyDeviceToHost));
+    if (abcap_ && L.m > 0) {
+      const int na = std::min(L.m, o.coef_hist_cap);
+      LS_CUDA(cudaMemcpy(o.alpha_hist + row * o.coef_hist_cap, d_ab_hist_ + (int64_t)q * 2 * abcap_,
+                         sizeof(double) * na, cudaMemcpyDeviceToHost));
+      LS_CUDA(cudaMemcpy(o.beta_hist + row * o.coef_hist_cap, d_ab_hist_ + (int64_t)q * 2 * abcap_ + abcap_,
+                         sizeof(double) * na, cudaMemcpyDeviceToHost));
+    }
+    return ASCG_OK;
+  }
+
+  void fill_result(int q, ascg_result* r) const {
+    const LaneSys& L = lane_[q];
+    std::memset(r, 0, sizeof(*r));
+    r->status = L.status;
+    r->iters = L.m;
+    r->blocks = L.kb;
+    r->grid_reductions = L.kb;
+    r->wasted_vecs = L.wasted;
+    r->launches = (int)std::min<int64_t>(super_blocks_, 0x7fffffff);
+    r->bnorm = L.bnorm;
+    r->rel_res_updated = L.rel_upd;
+    r->rel_res_true = L.rel_true;
+  }
+
+  LaneSys& lane(int q) { return lane_[q]; }
+  bool used(int q) const { return used_[q] != 0; }
+  int hi() const { return hi_; }
+  int nused() const { return nused_; }
+  int lanes() const { return lanes_; }
+  size_t arena_used() const { return arena_.used(); }
+  size_t arena_size() const { return arena_.size(); }
+  int64_t super_blocks() const { return super_blocks_; }
+  int64_t launches() const { return launches_; }
+  cudaStream_t stream() const { return s_; }
+
+ private:
+  static constexpr int64_t kGStride = (int64_t)kMaxW * kMaxW;
+  static constexpr int64_t kCStride = 3 * kMaxW;
+
+  ascg_status grow_items(int64_t ritems, int64_t gitems) {
+    if (ritems > rcap_items_) {
+      LS_CUDA(cudaStreamSynchronize(s_));
+      dfree(d_ritems_);
+      rcap_items_ = std::max<int64_t>(ritems, 2 * rcap_items_);
+      LS_TRY(dalloc(&d_ritems_, (size_t)rcap_items_));
+    }
+    if (gitems > gcap_items_) {
+      LS_CUDA(cudaStreamSynchronize(s_));
+      dfree(d_gitems_);
+      dfree(d_partials_);
+      gcap_items_ = std::max<int64_t>(gitems, 2 * gcap_items_);
+      LS_TRY(dalloc(&d_gitems_, (size_t)gcap_items_));
+      LS_TRY(dalloc(&d_partials_, (size_t)gcap_items_ * npw_));
+    }
+    return ASCG_OK;
+  }
+
+  // Row items, Gram items and descriptors of the held lanes, in lane order.
+  ascg_status rebuild_tables() {
+    ritems_.clear();
+    gitems_.clear();
+    int* h_item0 = h_int_ + 4 * lanes_;
+    int* h_nitems = h_int_ + 5 * lanes_;
+    for (int q = 0; q < hi_; ++q) {
+      h_item0[q] = (int)gitems_.size();
+      h_nitems[q] = 0;
+      if (!used_[q]) continue;
+      const int64_t n = lane_[q].d.n;
+      for (int64_t r = 0; r < n; r += kRowItem)
+        ritems_.push_back(RowItem{q, (int)r, (int)std::min<int64_t>(kRowItem, n - r), 0});
+      for (int64_t r = 0; r < n; r += kGramItemRows)
+        gitems_.push_back(GramItem{r, (int)std::min<int64_t>(kGramItemRows, n - r), q});
+      h_nitems[q] = (int)gitems_.size() - h_item0[q];
+    }
+    LS_TRY(grow_items((int64_t)ritems_.size(), (int64_t)gitems_.size()));
+    if (!ritems_.empty())
+      LS_CUDA(cudaMemcpyAsync(d_ritems_, ritems_.data(), sizeof(RowItem) * ritems_.size(), cudaMemcpyHostToDevice, s_));
+    if (!gitems_.empty())
+      LS_CUDA(cudaMemcpyAsync(d_gitems_, gitems_.data(), sizeof(GramItem) * gitems_.size(), cudaMemcpyHostToDevice, s_));
+    if (hi_ > 0) {
+      LS_CUDA(cudaMemcpyAsync(d_desc_, h_desc_, sizeof(SysDesc) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + 4 * lanes_, h_item0, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + 5 * lanes_, h_nitems, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    }
+    // The pinned tables above are rewritten only after the stream has been
+    // synchronised (every caller synchronises before it returns).
+    dirty_ = false;
+    return ASCG_OK;
+  }
+
+ public:
+  // Tables after retirements (admit rebuilds them itself).
+  ascg_status refresh() { return dirty_ ? rebuild_tables() : ASCG_OK; }
+
+ private:
+  void release() {
+    dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
+    dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
+    hfree(h_desc_); hfree(h_bst_); hfree(h_int_); hfree(h_sums_);
+  }
+
+  ascg_options o_{};
+  cudaStream_t s_ = nullptr;
+  int lanes_ = 0, nused_ = 0, hi_ = 0, rcap_ = 0, abcap_ = 0, wcols_ = 0, npw_ = 0;
+  bool dirty_ = true;
+  int64_t super_blocks_ = 0, launches_ = 0;
+  Arena arena_;
+  std::vector<LaneSys> lane_;
+  std::vector<char> used_;
+  std::vector<RowItem> ritems_;
+  std::vector<GramItem> gitems_;
+  int64_t rcap_items_ = 0, gcap_items_ = 0;
+  // device: descriptors, controller states, G and coordinate slots; ints:
+  // steps, w, sel, list, item0, nitems (lanes each); sums: 2 lanes
+  SysDesc* d_desc_ = nullptr;
+  BlockState* d_bst_ = nullptr;
+  double* d_G_ = nullptr;
+  double* d_coords_ = nullptr;
+  int* d_int_ = nullptr;
+  double* d_sums_ = nullptr;
+  double* d_params_ = nullptr;
+  double* d_res_hist_ = nullptr;
+  double* d_ab_hist_ = nullptr;
+  RowItem* d_ritems_ = nullptr;
+  GramItem* d_gitems_ = nullptr;
+  double* d_partials_ = nullptr;
+  // pinned host mirrors
+  SysDesc* h_desc_ = nullptr;
+  BlockState* h_bst_ = nullptr;
+  int* h_int_ = nullptr;
+  double* h_sums_ = nullptr;
+};
+
+// Batched solves: every system admitted at once, super-blocks until none is
+// active, then the true residuals.
+ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
+                                 const double* eps_target, const ascg_options& o, ascg_result* results,
+                                 cudaStream_t s) {
+  Lockstep eng;
+  std::vector<LaneSys> sys(count);
+  {
+    // footprints need wcols, known only after init: compute from the options here
+    const int64_t wcols = 2 * o.s_max + 1;
+    size_t y_bytes = 0;
+    int64_t gi = 0, ri = 0;
+    for (int q = 0; q < count; ++q) {
+      int64_t n = 0;
+      if (!ops[q]) return lfail(ASCG_ERR_INVALID, "ops must hold non-NULL entries");
+      SysDesc d{};
+      int dev = 0;
+      LS_TRY(op_split_desc(ops[q], &d, &dev));
+      n = d.n;
+      y_bytes += Arena::rounded((size_t)wcols * round_up(n, kSlice) * sizeof(double));
+      gi += Lockstep::gram_items_of(n);
+      ri += Lockstep::row_items_of(n);
+    }
+    const int rcap = o.res_hist ? std::max(o.res_hist_cap, 1) : 0;
+    const int abcap = (o.alpha_hist && o.beta_hist) ? std::max(o.coef_hist_cap, 1) : 0;
+    LS_TRY(eng.init(o, count, y_bytes, gi, ri, rcap, abcap, s));
+  }
+  for (int q = 0; q < count; ++q)
+    LS_TRY(eng.prepare(ops[q], b[q], x[q], eps_target ? eps_target[q] : o.eps_target, q, &sys[q]));
+  size_t admitted = 0;
+  LS_TRY(eng.admit(sys, 0, &admitted, nullptr));
+  if (admitted != (size_t)count) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
+  for (int q = 0; q < count; ++q)
+    if (eng.lane(q).status == ASCG_ERR_INVALID) return lfail(ASCG_ERR_INVALID, "b or x_1 is not finite");
+  for (;;) {
+    bool any = false;
+    for (int q = 0; q < count; ++q) any = any || eng.lane(q).active;
+    if (!any) break;
+    LS_TRY(eng.super_block(o.block_hist, o.block_hist_cap));
+  }
+  std::vector<int> all(count);
+  for (int q = 0; q < count; ++q) all[q] = q;
+  LS_TRY(eng.finish(all));
+  ascg_status worst = ASCG_OK;
+  for (int q = 0; q < count; ++q) {
+    LS_TRY(eng.copy_histories(q, o, q));
+    if (results) eng.fill_result(q, &results[q]);
+    const ascg_status st = eng.lane(q).status;
+    if (st == ASCG_ERR_BREAKDOWN) worst = ASCG_ERR_BREAKDOWN;
+    else if (st == ASCG_NOT_CONVERGED && worst == ASCG_OK) worst = ASCG_NOT_CONVERGED;
+  }
+  if (worst == ASCG_ERR_BREAKDOWN) set_last_error("breakdown in at least one system (see results[q].status)");
+  return worst;
+}
+
+}  // namespace ascg
+
+// ===========================================================================
+// Solve server (continuous batching)
+// ===========================================================================
+
+using namespace ascg;
+
+struct ascg_server_s {
+  Lockstep eng;
+  ascg_options o{};
+  size_t budget = 0;
+  std::deque<LaneSys> queue;
+  std::deque<ascg_completion> ready;
+  int64_t steps = 0;
+};
+
+extern "C" {
+
+ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int max_systems, void* cuda_stream,
+                               ascg_server* out) {
+  set_last_error("");
+  if (!out) return lfail(ASCG_ERR_INVALID, "out is NULL");
+  *out = nullptr;
+  if (!opts) return lfail(ASCG_ERR_INVALID, "opts is NULL");
+  const ascg_options o = *opts;
+  LS_TRY(check_options(o));
+  if (o.method != ASCG_ADAPTIVE && o.method != ASCG_FIXED_S)
+    return lfail(ASCG_ERR_INVALID, "the server runs ASCG_ADAPTIVE or ASCG_FIXED_S");
+  if (o.basis != ASCG_MONOMIAL) return lfail(ASCG_ERR_INVALID, "the server uses the monomial basis");
+  if (o.res_hist || o.block_hist || o.alpha_hist || o.beta_hist)
+    return lfail(ASCG_ERR_INVALID, "the server keeps no histories: the history buffers must be NULL");
+  if (max_systems < 1 || max_systems > (1 << 20)) return lfail(ASCG_ERR_INVALID, "max_systems must be in 1..2^20");
+  if (hbm_budget < 1) return lfail(ASCG_ERR_INVALID, "hbm_budget must be >= 1");
+  ascg_server srv = nullptr;
+  try {
+    srv = new ascg_server_s();
+  } catch (const std::bad_alloc&) {
+    return lfail(ASCG_ERR_OOM, "host allocation failed");
+  }
+  srv->o = o;
+  srv->budget = (size_t)hbm_budget;
+  // The Gram partials take (2 s_max + 1)(s_max + 1) doubles per 8192 rows
+  // against (2 s_max + 1) 8192 doubles of basis: reserve them out of the
+  // budget for the most rows the budget can hold, plus one item per system.
+  const int64_t wcols = 2 * o.s_max + 1, npw = wcols * (wcols + 1) / 2;
+  const int64_t rows_max = hbm_budget / (wcols * (int64_t)sizeof(double));
+  const int64_t gitems = rows_max / kGramItemRows + max_systems;
+  const int64_t part_bytes = gitems * npw * (int64_t)sizeof(double);
+  const int64_t y_bytes = std::max<int64_t>(hbm_budget - part_bytes, 0);
+  ascg_status st = srv->eng.init(o, max_systems, (size_t)y_bytes, gitems, 1024, 0, 0, (cudaStream_t)cuda_stream);
+  if (st != ASCG_OK) {
+    delete srv;
+    return st;
+  }
+  *out = srv;
+  return ASCG_OK;
+}
+
+ascg_status ascg_server_destroy(ascg_server srv) {
+  if (!srv) return ASCG_OK;
+  cudaStreamSynchronize(srv->eng.stream());
+  delete srv;
+  return ASCG_OK;
+}
+
+ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, double* x, double eps_target,
+                               int64_t tag) {
+  set_last_error("");
+  if (!srv) return lfail(ASCG_ERR_INVALID, "srv is NULL");
+  LaneSys L;
+  LS_TRY(srv->eng.prepare(op, b, x, eps_target, tag, &L));
+  if (srv->eng.footprint(L.d.n) > srv->budget || L.bytes > srv->eng.arena_size())
+    return lfail(ASCG_ERR_INVALID, "the system needs more device memory than the server's budget");
+  L.t_submit = now_ms();
+  try {
+    srv->queue.push_back(L);
+  } catch (const std::bad_alloc&) {
+    return lfail(ASCG_ERR_OOM, "host allocation failed");
+  }
+  return ASCG_OK;
+}
+
+ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, int* ndone, int* nactive,
+                             int* npending) {
+  set_last_error("");
+  if (!srv || (cap > 0 && !done) || cap < 0) return lfail(ASCG_ERR_INVALID, "bad argument");
+  Lockstep& eng = srv->eng;
+  auto complete = [&](int q) {
+    LaneSys& L = eng.lane(q);
+    ascg_completion c;
+    std::memset(&c, 0, sizeof(c));
+    c.tag = L.tag;
+    eng.fill_result(q, &c.result);
+    c.result.launches = (int)std::min<int64_t>(srv->steps - L.step_admit + 1, 0x7fffffff);
+    c.queue_ms = L.t_admit - L.t_submit;
+    c.latency_ms = L.t_done - L.t_submit;
+    c.step_admitted = L.step_admit;
+    c.step_done = L.step_done;
+    srv->ready.push_back(c);
+  };
+  try {
+    // 1. admission: FIFO, while a lane is free and the arena can place the head
+    if (!srv->queue.empty() && eng.has_free_lane()) {
+      std::vector<LaneSys> head;
+      for (const LaneSys& L : srv->queue) {
+        if ((int)head.size() >= eng.lanes() - eng.nused()) break;
+        head.push_back(L);
+      }
+      size_t admitted = 0;
+      std::vector<int> fresh;
+      LS_TRY(eng.admit(head, 0, &admitted, &fresh));
+      const double t = now_ms();
+      for (size_t i = 0; i < admitted; ++i) srv->queue.pop_front();
+      std::vector<int> finished;
+      for (int q : fresh) {
+        LaneSys& L = eng.lane(q);
+        L.t_admit = t;
+        L.step_admit = srv->steps;
+        if (L.done) finished.push_back(q);
+      }
+      if (!finished.empty()) {
+        LS_TRY(eng.finish(finished));
+        const double td = now_ms();
+        for (int q : finished) {
+          eng.lane(q).t_done = td;
+          eng.lane(q).step_done = srv->steps;
+          complete(q);
+        }
+        eng.retire(finished);
+        LS_TRY(eng.refresh());
+      }
+    }
+    // 2. one block of every active system
+    bool any = false;
+    for (int q = 0; q < eng.hi(); ++q) any = any || (eng.used(q) && eng.lane(q).active);
+    if (any) {
+      LS_TRY(eng.super_block(nullptr, 0));
+      std::vector<int> finished;
+      for (int q = 0; q < eng.hi(); ++q)
+        if (eng.used(q) && eng.lane(q).done) finished.push_back(q);
+      if (!finished.empty()) {
+        LS_TRY(eng.finish(finished));
+        const double td = now_ms();
+        for (int q : finished) {
+          eng.lane(q).t_done = td;
+          eng.lane(q).step_done = srv->steps;
+          complete(q);
+        }
+        eng.retire(finished);
+        LS_TRY(eng.refresh());
+      }
+      ++srv->steps;
+    }
+  } catch (const std::bad_alloc&) {
+    return lfail(ASCG_ERR_OOM, "host allocation failed");
+  }
+  int nd = 0;
+  while (nd < cap && !srv->ready.empty()) {
+    done[nd++] = srv->ready.front();
+    srv->ready.pop_front();
+  }
+  if (ndone) *ndone = nd;
+  if (nactive) *nactive = eng.nused();
+  if (npending) *npending = (int)std::min<size_t>(srv->queue.size() + srv->ready.size(), 0x7fffffff);
+  return ASCG_OK;
+}
+
+ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* st) {
+  if (!srv || !st) return lfail(ASCG_ERR_INVALID, "bad argument");
+  std::memset(st, 0, sizeof(*st));
+  st->budget_bytes = (int64_t)srv->budget;
+  st->basis_bytes_used = (int64_t)srv->eng.arena_used();
+  st->basis_bytes_total = (int64_t)srv->eng.arena_size();
+  st->systems_running = srv->eng.nused();
+  st->max_systems = srv->eng.lanes();
+  st->queued = (int64_t)srv->queue.size();
+  st->completions_pending = (int64_t)srv->ready.size();
+  st->steps = srv->steps;
+  st->launches = srv->eng.launches();
+  return ASCG_OK;
+}
+
+}  // extern "C"

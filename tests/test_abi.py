@@ -54,9 +54,10 @@ def test_struct_layouts_match_header(P):
     #include <stddef.h>
     #include "ascg.h"
     int main(void) {
-      printf("%zu %zu %zu %zu %zu %zu\n", sizeof(ascg_options), sizeof(ascg_result), sizeof(ascg_block_info),
-             offsetof(ascg_options, eps_target), offsetof(ascg_result, gram_flops),
-             offsetof(ascg_block_info, sqrt_kappa));
+      printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(ascg_options), sizeof(ascg_result),
+             sizeof(ascg_block_info), offsetof(ascg_options, eps_target), offsetof(ascg_result, gram_flops),
+             offsetof(ascg_block_info, sqrt_kappa), sizeof(ascg_completion), offsetof(ascg_completion, latency_ms),
+             sizeof(ascg_server_stats), offsetof(ascg_server_stats, steps));
       return 0;
     }
     """
@@ -68,7 +69,9 @@ def test_struct_layouts_match_header(P):
         vals = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [C.sizeof(P.ascg_options), C.sizeof(P.ascg_result), C.sizeof(P.ascg_block_info),
                     P.ascg_options.eps_target.offset, P.ascg_result.gram_flops.offset,
-                    P.ascg_block_info.sqrt_kappa.offset]
+                    P.ascg_block_info.sqrt_kappa.offset, C.sizeof(P.ascg_completion),
+                    P.ascg_completion.latency_ms.offset, C.sizeof(P.ascg_server_stats),
+                    P.ascg_server_stats.steps.offset]
 
 
 def test_options_default(P):
@@ -116,3 +119,27 @@ def test_null_arguments_are_errors(P):
     assert P._lib.ascg_gram(0, 3, None, 0, None, None) == P.ASCG_ERR_INVALID
     assert P._lib.ascg_recover(10, 4, 1, 10, 1, 1, 1, 1, None) == P.ASCG_ERR_INVALID  # even w
     assert P._lib.ascg_newton_shifts(None, None, 0, 0, None, None) == P.ASCG_ERR_INVALID
+
+
+def test_server_argument_checks(P):
+    """Server calls that fail before any device work."""
+    assert P._lib.ascg_server_destroy(None) == P.ASCG_OK
+    assert P._lib.ascg_server_step(None, None, 0, None, None, None) == P.ASCG_ERR_INVALID
+    assert P._lib.ascg_server_submit(None, None, None, None, 1e-8, 0) == P.ASCG_ERR_INVALID
+    assert P._lib.ascg_server_info(None, None) == P.ASCG_ERR_INVALID
+    o = P.ascg_options_default()
+    h = C.c_void_p()
+    assert P._lib.ascg_server_create(C.byref(o), 1 << 20, 4, None, None) == P.ASCG_ERR_INVALID
+    for field, value in [("basis", P.ASCG_CHEBYSHEV), ("method", P.ASCG_CLASSICAL)]:
+        bad = P.ascg_options_default()
+        setattr(bad, field, value)
+        bad.lambda_min, bad.lambda_max = 0.1, 2.0
+        assert P._lib.ascg_server_create(C.byref(bad), 1 << 20, 4, None, C.byref(h)) == P.ASCG_ERR_INVALID
+        assert h.value is None
+    hist = (C.c_double * 4)()
+    o.res_hist = C.cast(hist, C.POINTER(C.c_double))
+    o.res_hist_cap = 4
+    assert P._lib.ascg_server_create(C.byref(o), 1 << 20, 4, None, C.byref(h)) == P.ASCG_ERR_INVALID
+    o = P.ascg_options_default()
+    assert P._lib.ascg_server_create(C.byref(o), 1 << 20, 0, None, C.byref(h)) == P.ASCG_ERR_INVALID
+    assert P._lib.ascg_server_create(C.byref(o), 0, 4, None, C.byref(h)) == P.ASCG_ERR_INVALID

@@ -1,0 +1,227 @@
+"""Solve server (ascg_server_*): continuous batching over the lockstep engine.
+
+Requests of uneven sizes and targets arrive while others run; the server
+admits them in submission order as device memory and system slots free up.
+Each served result must be bitwise the same as the same system solved alone
+(ascg_solve_batch with one system), whatever ran beside it, and the admission
+must respect the memory budget and the slot count.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import ascg_oracle as O
+
+pytestmark = pytest.mark.gpu
+S_MAX = 10
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1701_03989_gb300 as P
+    torch.cuda.init()
+    return P, torch
+
+
+def dev(torch, a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to("cuda")
+
+
+def make_op(P, A):
+    return P.ascg_op_create_csr(A.n, A.nnz, np.ascontiguousarray(A.rowptr, np.int64),
+                                np.ascontiguousarray(A.colind, np.int32), np.ascontiguousarray(A.val, np.float64), 0)
+
+
+def opts(P, max_iters=4000):
+    return P.make_options(method="adaptive", basis="monomial", s_max=S_MAX, eps_target=1e-10, max_iters=max_iters)
+
+
+def footprint(n, s_max=S_MAX):
+    w = 2 * s_max + 1
+    ld = (n + 31) // 32 * 32
+    y = (w * ld * 8 + 255) // 256 * 256
+    return y + -(-n // 8192) * (w * (w + 1) // 2) * 8
+
+
+def solve_alone(P, torch, op, b, x1, eps, max_iters=4000):
+    x = dev(torch, x1)
+    res, _ = P.ascg_solve_batch([op], [dev(torch, b)], [x], opts(P, max_iters), eps_targets=[eps])
+    return res[0], x.cpu().numpy()
+
+
+def serve(P, torch, srv, systems, ops, waves, stats_log=None):
+    """Submits the systems in waves (lists of indices), running `gap` server
+    steps between waves; then steps until idle. Returns {index: (completion, x)}."""
+    xs = {q: dev(torch, systems[q]["x1"]) for wave, _ in waves for q in wave}
+    bs = {q: dev(torch, systems[q]["b"]) for wave, _ in waves for q in wave}
+    done = {}
+    order = []
+    for wave, gap in waves:
+        for q in wave:
+            P.ascg_server_submit(srv, ops[q], bs[q], xs[q], systems[q]["eps"], q)
+            order.append(q)
+        for _ in range(gap):
+            comps, _, _ = P.ascg_server_step(srv)
+            for c in comps:
+                done[c.tag] = c
+            if stats_log is not None:
+                stats_log.append(P.ascg_server_info(srv))
+    for _ in range(100000):
+        comps, nact, npend = P.ascg_server_step(srv, cap=3)
+        for c in comps:
+            done[c.tag] = c
+        if stats_log is not None:
+            stats_log.append(P.ascg_server_info(srv))
+        if nact == 0 and npend == 0:
+            break
+    assert sorted(done) == sorted(order)
+    return {q: (done[q], xs[q].cpu().numpy()) for q in order}, order
+
+
+def mixed_systems(seed=21, count=10):
+    sys = W.batch_systems(count, seed=seed, nmin=100, nmax=6000)
+    rng = np.random.default_rng(seed)
+    for s in sys:  # targets across the served range
+        s["eps"] = float(rng.choice([1e-6, 1e-8, 1e-10, 1e-12]))
+    return sys
+
+
+def test_served_results_equal_alone(env):
+    """Continuous batching: a first wave runs one step before the second
+    arrives; a budget of a third of the total footprint forces queueing. Every
+    served system equals its solve alone, bit for bit."""
+    P, torch = env
+    systems = mixed_systems()
+    ops = [make_op(P, s["A"]) for s in systems]
+    fp = [footprint(s["A"].n) for s in systems]
+    budget = max(max(fp), sum(fp) // 3) + 65536
+    srv = P.ascg_server_create(opts(P), budget, 8)
+    log = []
+    try:
+        served, order = serve(P, torch, srv, systems, ops, [(list(range(5)), 1), (list(range(5, 10)), 0)], log)
+    finally:
+        P.ascg_server_destroy(srv)
+    for st in log:
+        assert st.basis_bytes_used <= st.basis_bytes_total
+        assert st.systems_running <= 8
+    # admission is FIFO: admission steps never decrease in submission order
+    adm = [served[q][0].step_admitted for q in order]
+    assert adm == sorted(adm)
+    assert max(st.queued for st in log) > 0  # some requests had to wait
+    for q in range(len(systems)):
+        c, x = served[q]
+        r, xa = solve_alone(P, torch, ops[q], systems[q]["b"], systems[q]["x1"], systems[q]["eps"])
+        assert c.result.status == P.ASCG_OK == r.status, systems[q]["name"]
+        assert c.result.iters == r.iters and c.result.blocks == r.blocks, systems[q]["name"]
+        assert c.result.rel_res_true == r.rel_res_true and c.result.rel_res_updated == r.rel_res_updated
+        assert np.array_equal(x, xa), systems[q]["name"]
+        assert c.result.rel_res_updated <= systems[q]["eps"]
+        assert c.latency_ms >= c.queue_ms >= 0.0
+    for op in ops:
+        P.ascg_op_destroy(op)
+
+
+def test_served_result_against_oracle(env):
+    """Served systems against the FP64 oracle: each served result equals the
+    system solved alone bit for bit, and that solve, with its block records,
+    meets the parity rules (s_k sequence up to near-threshold decisions,
+    residual history, true residual within 2x). The target 1e-8 keeps the
+    true residuals well above the rounding floor eps ||A|| ||x||."""
+    import parity
+    from test_batch_gpu import run_batch
+    P, torch = env
+    systems = mixed_systems(seed=5, count=4)[:3]
+    for s in systems:
+        s["eps"] = 1e-8
+    ops = [make_op(P, s["A"]) for s in systems]
+    srv = P.ascg_server_create(opts(P), 1 << 28, 4)
+    try:
+        served, _ = serve(P, torch, srv, systems, ops, [([0, 1, 2], 0)])
+    finally:
+        P.ascg_server_destroy(srv)
+    for q, s in enumerate(systems):
+        g = run_batch(P, torch, [s], s_max=S_MAX)[0][0]
+        c, x = served[q]
+        assert np.array_equal(x, g["x"]) and c.result.iters == g["res"].iters
+        orc = O.adaptive_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], s_max=S_MAX, eps_target=s["eps"],
+                                  basis="monomial", max_iters=4000)
+        assert orc.converged and c.result.status == P.ASCG_OK
+        exempt, bad = parity.compare_block_sequences(g["blocks"], orc.blocks, s["A"].n, orc.res_hist, s["eps"])
+        assert not bad, (s["name"], bad)
+        nwin = min(parity.history_window(g["blocks"], orc.blocks, exempt, iters=20), len(g["hist"]),
+                   len(orc.res_hist), s["A"].n)
+        ho = np.asarray(orc.res_hist[:nwin])
+        tau = parity.history_tolerance(orc.blocks, ho, nwin)
+        assert np.all(np.abs(g["hist"][:nwin] - ho) <= tau), s["name"]
+        assert 0.5 * orc.true_res <= c.result.rel_res_true <= 2.0 * orc.true_res, (s["name"], c.result.rel_res_true,
+                                                                                 orc.true_res)
+        if exempt is None:
+            assert c.result.iters == orc.iters, (s["name"], c.result.iters, orc.iters)
+    for op in ops:
+        P.ascg_op_destroy(op)
+
+
+def test_server_slots_and_edge_requests(env):
+    """One slot: requests run one after another. A zero right-hand side and an
+    exact start complete at admission with no block; a request larger than
+    the budget is refused at submission."""
+    P, torch = env
+    A1 = W.poisson2d(9)
+    A2 = W.poisson2d(12)
+    b2 = W.rhs_uniform(A2.n, np.random.default_rng(1))
+    xs2 = np.linalg.solve(A2.to_dense(), b2)
+    A3 = W.banded_spd(700, 12, np.random.default_rng(2))
+    systems = [
+        dict(name="zero_rhs", A=A1, b=np.zeros(A1.n), x1=np.ones(A1.n), eps=1e-10),
+        dict(name="solved", A=A2, b=b2, x1=xs2, eps=1e-8),
+        dict(name="banded", A=A3, b=W.rhs_uniform(A3.n, np.random.default_rng(3)), x1=np.zeros(A3.n), eps=1e-12),
+        dict(name="banded2", A=A3, b=W.rhs_uniform(A3.n, np.random.default_rng(4)), x1=np.zeros(A3.n), eps=1e-8),
+    ]
+    ops = [make_op(P, s["A"]) for s in systems]
+    srv = P.ascg_server_create(opts(P), 1 << 26, 1)
+    log = []
+    try:
+        served, order = serve(P, torch, srv, systems, ops, [([0, 1, 2, 3], 0)], log)
+        big = W.poisson2d(64)
+        opb = make_op(P, big)
+        tiny = P.ascg_server_create(opts(P), footprint(big.n) - 1, 2)
+        with pytest.raises(P.AscgError) as e:
+            P.ascg_server_submit(tiny, opb, dev(torch, np.ones(big.n)), dev(torch, np.zeros(big.n)), 1e-8, 99)
+        assert e.value.status == P.ASCG_ERR_INVALID
+        P.ascg_server_destroy(tiny)
+        P.ascg_op_destroy(opb)
+    finally:
+        P.ascg_server_destroy(srv)
+    assert all(st.systems_running <= 1 for st in log)
+    c0, x0 = served[0]
+    assert c0.result.iters == 0 and c0.result.status == P.ASCG_OK and np.array_equal(x0, np.zeros(A1.n))
+    c1, x1 = served[1]
+    assert c1.result.iters == 0 and np.array_equal(x1, xs2)
+    # one slot: system 3 is admitted only after system 2 completed
+    assert served[3][0].step_admitted >= served[2][0].step_done
+    for q in (2, 3):
+        r, xa = solve_alone(P, torch, ops[q], systems[q]["b"], systems[q]["x1"], systems[q]["eps"])
+        assert np.array_equal(served[q][1], xa)
+    for op in ops:
+        P.ascg_op_destroy(op)
+
+
+def test_server_iteration_cap(env):
+    """max_iters stops a served system with ASCG_NOT_CONVERGED, like a batch."""
+    P, torch = env
+    A = W.banded_spd(900, 30, np.random.default_rng(7))
+    s = dict(name="capped", A=A, b=W.rhs_uniform(A.n, np.random.default_rng(8)), x1=np.zeros(A.n), eps=1e-12)
+    op = make_op(P, A)
+    srv = P.ascg_server_create(opts(P, max_iters=9), 1 << 26, 2)
+    try:
+        served, _ = serve(P, torch, srv, [s], [op], [([0], 0)])
+    finally:
+        P.ascg_server_destroy(srv)
+    c, x = served[0]
+    assert c.result.status == P.ASCG_NOT_CONVERGED and c.result.iters == 9
+    r, xa = solve_alone(P, torch, op, s["b"], s["x1"], s["eps"], max_iters=9)
+    assert np.array_equal(x, xa)
+    P.ascg_op_destroy(op)
