@@ -68,7 +68,10 @@ def parse():
                     help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", default="poisson3d_128", choices=["poisson3d_128", "batch"],
+    ap.add_argument("--requests", type=int, default=200, help="served workload: requests in the open-loop run")
+    ap.add_argument("--load", type=float, default=0.7, help="served workload: arrival rate / saturation throughput")
+    ap.add_argument("--budget-gb", type=float, default=150.0, help="served workload: device-memory budget (GB)")
+    ap.add_argument("--workload", default="poisson3d_128", choices=["poisson3d_128", "batch", "serve"],
                     help="batch: 256 uneven systems solved by ascg_solve_batch (one step = one batched call)")
     ap.add_argument("--gram-fp64", action="store_true",
                     help="form the Gram matrix with FP64 FMAs (CUDA cores) instead of the tensor-core digit split")
@@ -502,12 +505,183 @@ def batch_arm(args):
     return 0
 
 
+def _pct(v, q):
+    import numpy as np
+    return float(np.percentile(np.asarray(v, dtype=float), q)) if len(v) else None
+
+
+def serve_arm(args):
+    """Served workload: requests drawn from a pool of 12 SPD operators (2D/3D
+    Poisson and banded, sizes at log-uniform quantiles of [1e4, 4e6]), targets
+    uniform over {1e-6, 1e-8, 1e-10, 1e-12}, fresh seeded right-hand sides,
+    arriving as a Poisson process. The solve server (continuous batching,
+    adaptive monomial s_max = 10) serves them under a device-memory budget.
+    Steps: (1) saturation throughput: the same requests, all submitted at
+    once, served to the end (a smaller sample's mix is too far from the
+    stream's for a stable figure); (2) the open-loop run at `load` x
+    saturation, latency from each request's
+    arrival to the step that completed it; (3) the same arrivals through a
+    FIFO queue served one request at a time by classical CG (ascg_solve),
+    from measured service times per (operator, target); (4) an end-to-end
+    sample with right-hand sides copied from pinned host memory at submission
+    and solutions copied back at completion."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1701_03989_gb300 as P
+    import workloads as W
+    t_gen = time.perf_counter()
+    pool = W.serve_pool()
+    ops = [P.ascg_op_create_csr(p["A"].n, p["A"].nnz, p["A"].rowptr, p["A"].colind, p["A"].val, 0) for p in pool]
+    nop = [p["A"].n for p in pool]
+    nreq = max(int(args.requests), 8)
+    nwarm = max(4, nreq // 10)
+    ne2e = max(8, nreq // 4)
+    req = W.serve_requests(nreq)
+    t_gen = time.perf_counter() - t_gen
+
+    def rhs(i):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(int(req["rhs_seed"][i]) % (2 ** 63))
+        b = torch.rand(nop[req["op"][i]], dtype=torch.float64, device="cuda", generator=g).mul_(2.0).sub_(1.0)
+        return b.div_(torch.linalg.vector_norm(b))
+
+    bs = [rhs(i) for i in range(nreq)]
+    xs = [torch.zeros_like(b) for b in bs]
+    o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=60000)
+    stream = torch.cuda.current_stream()
+    budget = int(args.budget_gb * 1e9)
+    slots = 256
+    srv = P.ascg_server_create(o, budget, slots, stream)
+
+    def run(idx, arrivals, host_io=False):
+        """Serves requests idx arriving at `arrivals` (seconds from the start).
+        Returns per-request latency (s), completions, wall seconds, peak
+        systems running and the server steps taken."""
+        for i in idx:
+            xs[i].zero_()
+        hb = hx = None
+        if host_io:
+            hb = {i: bs[i].cpu().pin_memory() for i in idx}
+            hx = {i: torch.zeros(bs[i].numel(), dtype=torch.float64).pin_memory() for i in idx}
+            db = {i: torch.empty_like(bs[i]) for i in idx}
+        torch.cuda.synchronize()
+        order = np.argsort(arrivals, kind="stable")
+        arr = {int(idx[k]): float(arrivals[k]) for k in range(len(idx))}
+        lat, comp = {}, {}
+        pos, peak = 0, 0
+        steps0 = P.ascg_server_info(srv).steps
+        t0 = time.perf_counter()
+        while len(lat) < len(idx):
+            now = time.perf_counter() - t0
+            while pos < len(idx) and arrivals[order[pos]] <= now:
+                i = int(idx[order[pos]])
+                if host_io:
+                    db[i].copy_(hb[i], non_blocking=True)
+                    P.ascg_server_submit(srv, ops[req["op"][i]], db[i], xs[i], float(req["eps"][i]), i)
+                else:
+                    P.ascg_server_submit(srv, ops[req["op"][i]], bs[i], xs[i], float(req["eps"][i]), i)
+                pos += 1
+            comps, nact, npend = P.ascg_server_step(srv, cap=slots)
+            peak = max(peak, nact + len(comps))
+            if host_io and comps:
+                for c in comps:
+                    hx[c.tag].copy_(xs[c.tag], non_blocking=True)
+                stream.synchronize()
+            t = time.perf_counter() - t0
+            for c in comps:
+                lat[c.tag] = t - arr[c.tag]
+                comp[c.tag] = c
+            if nact == 0 and npend == 0 and pos < len(idx):
+                wait = arrivals[order[pos]] - (time.perf_counter() - t0)
+                if wait > 0:
+                    time.sleep(wait)
+        wall = time.perf_counter() - t0
+        return lat, comp, wall, peak, P.ascg_server_info(srv).steps - steps0
+
+    # (1) saturation: the stream's requests, all submitted at once
+    run(np.arange(nwarm), np.zeros(nwarm))  # warm-up
+    _, _, sat_wall, sat_peak, _ = run(np.arange(nreq), np.zeros(nreq))
+    mu = nreq / sat_wall
+    lam = args.load * mu
+    # (2) open loop at load x saturation
+    idx = np.arange(nreq)
+    arrivals = np.cumsum(req["gap"][:nreq]) / lam
+    sampler = ClockSampler(os.environ.get("CUDA_VISIBLE_DEVICES", "0").split(",")[0])
+    sampler.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat, comp, wall, peak, steps = run(idx, arrivals)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    gpu_ms = e0.elapsed_time(e1)
+    lat_ms = [1e3 * lat[i] for i in range(nreq)]
+    iters = sum(comp[i].result.iters for i in range(nreq))
+    ok = all(comp[i].result.status == P.ASCG_OK for i in range(nreq))
+    worst = max(comp[i].result.rel_res_true / req["eps"][i] for i in range(nreq))
+    # (3) FIFO sequential classical CG on the same arrivals, from measured service times
+    oc = P.make_options(method="classical", eps_target=1e-10, max_iters=200000)
+    service = {}
+    for key in sorted({(int(req["op"][i]), float(req["eps"][i])) for i in range(nreq)}):
+        i = next(i for i in range(nreq) if (int(req["op"][i]), float(req["eps"][i])) == key)
+        x = torch.zeros_like(bs[i])
+        oq = P.ascg_options.from_buffer_copy(oc)
+        oq.eps_target = key[1]
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        P.ascg_solve(ops[key[0]], bs[i], x, oq, stream=stream)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        service[key] = c0.elapsed_time(c1) * 1e-3
+    fin, fifo = 0.0, []
+    for k in np.argsort(arrivals, kind="stable"):
+        fin = max(arrivals[k], fin) + service[(int(req["op"][k]), float(req["eps"][k]))]
+        fifo.append(1e3 * (fin - arrivals[k]))
+    fifo_wall = fin - arrivals.min()
+    # (4) end to end: host right-hand sides in, solutions out
+    e_idx = np.arange(ne2e)
+    elat, _, ewall, _, _ = run(e_idx, arrivals[:ne2e], host_io=True)
+    elat_ms = [1e3 * elat[i] for i in range(ne2e)]
+    P.ascg_server_destroy(srv)
+    h2d = sum(8 * nop[req["op"][i]] for i in range(ne2e)) / ne2e
+    line = {
+        "metric": "served solve latency p50 (ms), Poisson arrivals at %.2fx saturation throughput" % args.load,
+        "value": _pct(lat_ms, 50), "unit": "ms", "n_gpus": 1, "steps": nreq, "warmup": nwarm,
+        "ms_per_step": gpu_ms / nreq, "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "solve server: %d requests from a pool of 12 SPD operators (2D/3D Poisson, banded hbw "
+                               "8..64; n at log-uniform quantiles of [1e4, 4e6]), eps* uniform over {1e-6, 1e-8, "
+                               "1e-10, 1e-12}, Poisson arrivals, seed 1005; adaptive monomial s_max=10; budget "
+                               "%.0f GB, %d slots" % (nreq, args.budget_gb, slots),
+                   "pool_n": nop, "pool_nnz": [int(p["A"].nnz) for p in pool]},
+        "p50_ms": _pct(lat_ms, 50), "p99_ms": _pct(lat_ms, 99), "max_ms": max(lat_ms),
+        "throughput_rps": nreq / wall, "arrival_rps": lam, "saturation_rps": mu,
+        "saturation_wall_s": sat_wall, "saturation_peak_running": sat_peak, "peak_running": peak,
+        "server_steps": steps, "iters_per_s": iters / wall, "status_ok": ok, "worst_true_res_over_target": worst,
+        "classical_fifo": {"p50_ms": _pct(fifo, 50), "p99_ms": _pct(fifo, 99), "max_ms": max(fifo),
+                           "throughput_rps": nreq / fifo_wall, "service_pairs": len(service),
+                           "note": "FIFO queue, one request at a time, ascg_solve classical CG; service time "
+                                   "measured once per (operator, target)"},
+        "e2e": {"value": _pct(elat_ms, 50), "unit": "ms", "p99_ms": _pct(elat_ms, 99), "requests": ne2e,
+                "throughput_rps": ne2e / ewall, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": h2d},
+        "setup_s": t_gen, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    for op in ops:
+        P.ascg_op_destroy(op)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.workload == "batch":
         return batch_arm(args)
+    if args.workload == "serve":
+        return serve_arm(args)
     return our_arm(args)
 
 

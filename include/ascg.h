@@ -305,24 +305,27 @@ ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int64_t ldY, do
 
 /* --- solve server (continuous batching) ------------------------------------
  * A request loop over the batched engine: requests of different sizes and
- * targets are submitted at any time; each ascg_server_step admits waiting
- * requests while device memory and system slots allow, runs one block
- * (Alg. 4) of every admitted system, and hands back the systems that
- * finished. Bases and coefficients stay on the device between steps, and
- * the blocks of all running systems share each step's launches. A system's
- * arithmetic depends on that system alone: its x, iteration count and
- * residuals are bitwise the same as from ascg_solve_batch with that system
- * alone, whatever else runs beside it.
+ * targets are submitted at any time, admitted while device memory and system
+ * slots allow, and run block by block (Alg. 4) until they finish. Bases and
+ * coefficients stay on the device between blocks. Running systems are split
+ * by size into three classes (n < 2^16, < 2^19, larger); each class runs its
+ * systems in lockstep on a stream of its own, and starts its next block as
+ * soon as its previous one has landed, so the classes' blocks interleave on
+ * the GPU and small systems do not wait for the blocks of large ones. A
+ * system's arithmetic depends on that system alone: its x, iteration count
+ * and residuals are bitwise the same as from ascg_solve_batch with that
+ * system alone, whatever else runs beside it.
  * Not safe for concurrent use from several threads. */
 typedef struct ascg_server_s* ascg_server;
 
 typedef struct {
   int64_t tag;               /* the caller's tag from ascg_server_submit           */
-  ascg_result result;        /* as from ascg_solve_batch; result.launches = server
-                                steps from admission to completion               */
+  ascg_result result;        /* as from ascg_solve_batch; result.launches = blocks
+                                landed (all size classes) from admission to
+                                completion                                       */
   double queue_ms;           /* host time from submit to admission                */
   double latency_ms;         /* host time from submit to completion               */
-  int64_t step_admitted;     /* server step at admission / at completion          */
+  int64_t step_admitted;     /* server block counter at admission / completion    */
   int64_t step_done;
 } ascg_completion;
 
@@ -334,7 +337,7 @@ typedef struct {
   int max_systems;
   int64_t queued;            /* submitted, not yet admitted                        */
   int64_t completions_pending; /* finished, not yet returned by ascg_server_step   */
-  int64_t steps;             /* steps that ran a block                             */
+  int64_t steps;             /* blocks landed, all size classes                    */
   int64_t launches;          /* kernels launched so far                            */
 } ascg_server_stats;
 
@@ -345,36 +348,45 @@ typedef struct {
  * (s_max + 1) 8 bytes of Gram partials per 8192 rows; the whole budget is
  * allocated here, as one arena for the bases and one buffer for the
  * partials (plus about 16 bytes per 256 rows of row tables outside it).
- * max_systems: most systems running at once (1 .. 2^20). All work is ordered
- * on cuda_stream. The operators are the caller's and are not counted. */
+ * max_systems: most systems running at once (1 .. 2^20). cuda_stream: the
+ * caller's stream, which orders submissions after the caller's work; the
+ * server runs its blocks on streams of its own. The operators are the
+ * caller's and are not counted. */
 ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int max_systems,
                                void* cuda_stream, ascg_server* out);
 
-/* Queues a request A x = b (FIFO). op: an operator on the current device; b,
- * x: device double[n]; x holds x_1 and is updated in place while the system
+/* Queues a request A x = b. op: an operator on the current device; b, x:
+ * device double[n]; x holds x_1 and is updated in place while the system
  * runs, so b, x and op must stay valid and untouched until its completion is
- * returned. eps_target: relative target (eps* = eps_target ||b||). tag:
- * returned in the completion. ASCG_ERR_INVALID if the system could never fit
- * the budget. Host only: nothing is launched. */
+ * returned. Work already queued on the server's stream (cuda_stream of
+ * ascg_server_create) when this is called, such as the writes of b and x_1,
+ * is done before the system starts. eps_target: relative target (eps* =
+ * eps_target ||b||). tag: returned in the completion. ASCG_ERR_INVALID if
+ * the system could never fit the budget. Launches nothing. */
 ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, double* x, double eps_target,
                                int64_t tag);
 
-/* One step: admission (in submission order, stopping at the first request
- * that does not fit yet), one block of every running system, completion of
- * the systems that finished (true residual computed, memory freed). Writes
- * up to cap completions to done (host) and their number to *ndone; the rest
- * wait for the next call. *nactive: systems running after the step;
- * *npending: requests not yet admitted plus completions not yet returned
- * (the server is idle when both are 0). Synchronises the stream. */
+/* Advances the server until at least one block has landed (or there is no
+ * work): completes the systems that finished (true residual computed, memory
+ * freed), admits waiting requests, and starts the next block of every size
+ * class that is idle and has running systems. Admission goes in submission
+ * order; a request whose size class is in the middle of a block waits for
+ * it while later requests of idle classes may go ahead, and the first
+ * request that finds no free slot or no memory stops the scan (nothing
+ * overtakes it). Writes up to cap completions to done (host) and their
+ * number to *ndone; the rest wait for the next call. *nactive: systems
+ * running; *npending: requests not yet admitted plus completions not yet
+ * returned (the server is idle when both are 0). The blocks it starts may
+ * still run on the GPU when it returns. */
 ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, int* ndone, int* nactive,
                              int* npending);
 
 /* Counters of the server (host). */
 ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* stats);
 
-/* Synchronises the stream and frees the server. Requests not yet completed
- * are dropped (their x holds whatever iterate was reached). NULL is
- * accepted. */
+/* Waits for the server's work on the GPU and frees the server. Requests not
+ * yet completed are dropped (their x holds whatever iterate was reached).
+ * NULL is accepted. */
 ascg_status ascg_server_destroy(ascg_server srv);
 
 /* Message of the last error on this thread ("" if none). */

@@ -17,8 +17,13 @@
 // its own size: a system's result is bitwise the same alone and in any mix,
 // whichever lane it lands in and whoever else is running.
 //
-// The bases live in one device arena (first-fit, merging free neighbours),
-// so admitting and retiring systems allocates nothing from CUDA.
+// The bases live in one device arena (first-fit, merging free neighbours)
+// owned by the caller of the engine, so admitting and retiring systems
+// allocates nothing from CUDA.
+//
+// Gram schedule per lane, fixed by the lane's own size: lanes of at least
+// kTcLaneRows rows (and w >= 9) take the tensor-core Gram kernel, one launch
+// per lane; all other lanes share one launch of the FP64 item kernel.
 #include <chrono>
 #include <cmath>
 #include <cstring>
@@ -176,16 +181,23 @@ struct LaneSys {
   ascg_status status = ASCG_OK;
   double t_submit = 0.0, t_admit = 0.0, t_done = 0.0;
   int64_t step_admit = 0, step_done = 0;
+  cudaEvent_t ready = nullptr;  // server: b and x_1 written on the caller's stream
 };
+
+// Rows from which a lane's Gram runs on the tensor cores (one launch per
+// lane); below it the lane joins the shared FP64 item launch, which keeps the
+// whole GPU busy with many small lanes at once.
+constexpr int64_t kTcLaneRows = (int64_t)1 << 18;
 
 class Lockstep {
  public:
   ~Lockstep() { release(); }
 
-  // lanes: most systems in flight; y_bytes: arena size for the bases; gitems,
-  // ritems: initial Gram and row item capacities (they grow on demand).
-  ascg_status init(const ascg_options& o, int lanes, size_t y_bytes, int64_t gitems, int64_t ritems,
-                   int rcap, int abcap, cudaStream_t s) {
+  // lanes: most systems held at once; gitems, ritems: initial Gram and row
+  // item capacities (they grow on demand); rcap, abcap: history capacities
+  // per lane (0: none). All work is ordered on stream s.
+  ascg_status init(const ascg_options& o, int lanes, int64_t gitems, int64_t ritems, int rcap, int abcap,
+                   cudaStream_t s) {
     o_ = o;
     s_ = s;
     lanes_ = lanes;
@@ -193,24 +205,25 @@ class Lockstep {
     abcap_ = abcap;
     wcols_ = 2 * o.s_max + 1;
     npw_ = wcols_ * (wcols_ + 1) / 2;
-    LS_TRY(arena_.init(y_bytes));
     LS_TRY(dalloc(&d_desc_, lanes));
     LS_TRY(dalloc(&d_bst_, lanes));
     LS_TRY(dalloc(&d_G_, (size_t)lanes * kGStride));
     LS_TRY(dalloc(&d_coords_, (size_t)lanes * kCStride));
-    LS_TRY(dalloc(&d_int_, (size_t)6 * lanes));
+    LS_TRY(dalloc(&d_int_, (size_t)kIntArrays * lanes));
     LS_TRY(dalloc(&d_sums_, (size_t)2 * lanes));
     LS_TRY(dalloc(&d_params_, (size_t)3 * kMaxS));
+    LS_TRY(dalloc(&d_tc_partials_, (size_t)gram_grid() * kMaxPairs));
+    LS_TRY(dalloc(&d_tc_exp_, (size_t)gram_grid() * kMaxW));
     if (rcap_) LS_TRY(dalloc(&d_res_hist_, (size_t)lanes * rcap_));
     if (abcap_) LS_TRY(dalloc(&d_ab_hist_, (size_t)lanes * 2 * abcap_));
     LS_TRY(halloc(&h_desc_, lanes));
     LS_TRY(halloc(&h_bst_, lanes));
-    LS_TRY(halloc(&h_int_, (size_t)6 * lanes));
+    LS_TRY(halloc(&h_int_, (size_t)kIntArrays * lanes));
     LS_TRY(halloc(&h_sums_, (size_t)2 * lanes));
     LS_TRY(grow_items(ritems, gitems));
     std::memset(h_desc_, 0, sizeof(SysDesc) * lanes);
     std::memset(h_bst_, 0, sizeof(BlockState) * lanes);
-    std::memset(h_int_, 0, sizeof(int) * 6 * lanes);
+    std::memset(h_int_, 0, sizeof(int) * kIntArrays * lanes);
     LS_CUDA(cudaMemsetAsync(d_coords_, 0, sizeof(double) * lanes * kCStride, s_));
     LS_CUDA(cudaMemsetAsync(d_bst_, 0, sizeof(BlockState) * lanes, s_));
     double hp[3 * kMaxS];  // monomial basis: theta = sigma = 0, gamma = 1
@@ -226,18 +239,21 @@ class Lockstep {
     return ASCG_OK;
   }
 
-  // Device bytes one system of n rows holds while it runs: its basis Y
-  // (2 s_max + 1 columns of round_up(n, 32) doubles) and its Gram partials.
-  size_t footprint(int64_t n) const {
-    const int64_t ld = round_up(n, kSlice);
-    const int64_t items = (n + kGramItemRows - 1) / kGramItemRows;
-    return Arena::rounded((size_t)wcols_ * ld * sizeof(double)) + (size_t)items * npw_ * sizeof(double);
-  }
   static int64_t gram_items_of(int64_t n) { return (n + kGramItemRows - 1) / kGramItemRows; }
   static int64_t row_items_of(int64_t n) { return (n + kRowItem - 1) / kRowItem; }
+  // Basis bytes of a system of n rows: 2 s_max + 1 columns of round_up(n, 32).
+  static size_t basis_bytes(int s_max, int64_t n) {
+    return (size_t)(2 * s_max + 1) * round_up(n, kSlice) * sizeof(double);
+  }
+  // Device bytes one system holds while it runs: its basis and its Gram partials.
+  static size_t footprint(int s_max, int64_t n) {
+    const int64_t w = 2 * s_max + 1;
+    return Arena::rounded(basis_bytes(s_max, n)) + (size_t)gram_items_of(n) * (w * (w + 1) / 2) * sizeof(double);
+  }
 
-  // Prepares a system for admission (validates it; fills its descriptor but Y).
-  ascg_status prepare(ascg_op op, const double* b, double* x, double eps_target, int64_t tag, LaneSys* out) const {
+  // Validates a system and fills its descriptor (all but Y).
+  static ascg_status prepare(int s_max, ascg_op op, const double* b, double* x, double eps_target, int64_t tag,
+                             LaneSys* out) {
     if (!op || !b || !x) return lfail(ASCG_ERR_INVALID, "op, b and x must be non-NULL");
     if (!(eps_target >= 0.0 && std::isfinite(eps_target)))
       return lfail(ASCG_ERR_INVALID, "eps_target must be finite and >= 0");
@@ -251,48 +267,40 @@ class Lockstep {
     out->d.ldY = round_up(out->d.n, kSlice);
     out->eps_target = eps_target;
     out->tag = tag;
-    out->bytes = (size_t)wcols_ * out->d.ldY * sizeof(double);
+    out->bytes = basis_bytes(s_max, out->d.n);
     return ASCG_OK;
   }
 
-  bool has_free_lane() const { return nused_ < lanes_; }
+  int free_lanes() const { return lanes_ - nused_; }
 
-  // Admits the systems (each into the lowest free lane), computes ||b||,
-  // r_1 = b - A x_1 into Y columns 1 and 0 and ||r_1||. Systems that need no
-  // block (b = 0, r_1 already small enough, max_iters = 0) are marked done.
-  // Stops at the first system the arena cannot place; *admitted tells how many.
-  ascg_status admit(std::vector<LaneSys>& sys, size_t first, size_t* admitted, std::vector<int>* lanes_out) {
-    *admitted = 0;
+  // Admits systems whose basis Y the caller has placed (each into the lowest
+  // free lane; the caller checks free_lanes()), computes ||b||, r_1 = b - A x_1
+  // into Y columns 1 and 0 and ||r_1||. Systems that need no block (b = 0, r_1
+  // already small enough, max_iters = 0) come out done. lanes_out: their lanes.
+  ascg_status admit(const std::vector<LaneSys>& sys, std::vector<int>* lanes_out) {
     std::vector<int> fresh;
-    for (size_t i = first; i < sys.size(); ++i) {
-      if (nused_ >= lanes_) break;
-      size_t off = 0;
-      if (!arena_.take(sys[i].bytes, &off)) break;
+    for (const LaneSys& S : sys) {
       int q = 0;
       while (used_[q]) ++q;
-      LaneSys& L = lane_[q];
-      L = sys[i];
-      L.off = off;
-      L.d.Y = arena_.at(off);
+      lane_[q] = S;
       used_[q] = 1;
       ++nused_;
       hi_ = std::max(hi_, q + 1);
-      h_desc_[q] = L.d;
+      h_desc_[q] = S.d;
       fresh.push_back(q);
-      ++*admitted;
     }
     if (lanes_out) *lanes_out = fresh;
     if (fresh.empty()) return ASCG_OK;
     LS_TRY(rebuild_tables());
-    int* h_sel = h_int_ + 2 * lanes_;
-    int* h_list = h_int_ + 3 * lanes_;
+    int* h_sel = h_int_ + kSel * lanes_;
+    int* h_list = h_int_ + kList * lanes_;
     for (int q = 0; q < hi_; ++q) h_sel[q] = 0;
     for (size_t i = 0; i < fresh.size(); ++i) {
       h_sel[fresh[i]] = 1;
       h_list[i] = fresh[i];
     }
-    int* d_sel = d_int_ + 2 * lanes_;
-    int* d_list = d_int_ + 3 * lanes_;
+    int* d_sel = d_int_ + kSel * lanes_;
+    int* d_list = d_int_ + kList * lanes_;
     LS_CUDA(cudaMemcpyAsync(d_sel, h_sel, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     LS_CUDA(cudaMemcpyAsync(d_list, h_list, sizeof(int) * fresh.size(), cudaMemcpyHostToDevice, s_));
     LS_CUDA(launch_seg_sumsq(d_desc_, d_list, (int)fresh.size(), 0, d_sums_, s_));
@@ -324,12 +332,22 @@ class Lockstep {
     return ASCG_OK;
   }
 
-  // One block of every active lane. Lanes whose system finished in it are
-  // marked done.
-  ascg_status super_block(ascg_block_info* block_hist, int block_hist_cap) {
-    int* h_steps = h_int_;
-    int* h_w = h_int_ + lanes_;
+  bool any_active() const {
+    for (int q = 0; q < hi_; ++q)
+      if (used_[q] && lane_[q].active) return true;
+    return false;
+  }
+
+  // Enqueues one block of every active lane and the read-back of their
+  // states; *launched = false when no lane is active. The host must call
+  // complete_block() once the stream has reached this point.
+  ascg_status launch_block(bool* launched) {
+    *launched = false;
+    int* h_steps = h_int_ + kSteps * lanes_;
+    int* h_w = h_int_ + kW * lanes_;
+    int* h_wi = h_int_ + kWItems * lanes_;
     int max_sbar = 0;
+    tc_lanes_.clear();
     for (int q = 0; q < hi_; ++q) {
       BlockState& hb = h_bst_[q];
       std::memset(&hb, 0, sizeof(hb));
@@ -337,6 +355,7 @@ class Lockstep {
       if (!used_[q] || !L.active) {
         h_steps[q] = 0;
         h_w[q] = 0;
+        h_wi[q] = 0;
         continue;
       }
       const int sbar = o_.method == ASCG_FIXED_S ? o_.s_max : (L.kb == 0 ? o_.s0 : std::min(L.s_prev + o_.f, o_.s_max));
@@ -352,31 +371,57 @@ class Lockstep {
       hb.bnorm = L.bnorm;
       hb.sqrt_n = std::sqrt((double)L.d.n);
       hb.active = 1;
+      const int w = 2 * sbar + 1;
       h_steps[q] = sbar;
-      h_w[q] = 2 * sbar + 1;
+      h_w[q] = w;
+      const bool tc = L.d.n >= kTcLaneRows && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
+      h_wi[q] = tc ? 0 : w;
+      if (tc) tc_lanes_.push_back(q);
       max_sbar = std::max(max_sbar, sbar);
     }
     if (max_sbar == 0) return ASCG_OK;
-    int* d_steps = d_int_;
-    int* d_w = d_int_ + lanes_;
-    int* d_item0 = d_int_ + 4 * lanes_;
-    int* d_nitems = d_int_ + 5 * lanes_;
+    int* d_steps = d_int_ + kSteps * lanes_;
+    int* d_w = d_int_ + kW * lanes_;
+    int* d_wi = d_int_ + kWItems * lanes_;
+    int* d_item0 = d_int_ + kItem0 * lanes_;
+    int* d_nitems = d_int_ + kNItems * lanes_;
     const int nr = (int)ritems_.size(), ng = (int)gitems_.size();
     LS_CUDA(cudaMemcpyAsync(d_bst_, h_bst_, sizeof(BlockState) * hi_, cudaMemcpyHostToDevice, s_));
     LS_CUDA(cudaMemcpyAsync(d_steps, h_steps, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemcpyAsync(d_wi, h_wi, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
     const int Wb = 2 * max_sbar + 1;
-    LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_w, d_partials_, s_));
-    LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_w, hi_, d_G_, kGStride, s_));
-    if (o_.method == ASCG_ADAPTIVE) LS_CUDA(launch_kappa_batch(d_G_, kGStride, d_bst_, hi_, max_sbar, s_));
+    int nl = max_sbar;
+    if ((int)tc_lanes_.size() < count_active()) {
+      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, s_));
+      LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, s_));
+      nl += 2;
+    }
+    for (int q : tc_lanes_) {  // one lane at a time: the lanes share the partials buffer in stream order
+      const LaneSys& L = lane_[q];
+      int parts = 0;
+      LS_CUDA(launch_gram_any(L.d.n, h_w[q], L.d.Y, L.d.ldY, false, d_tc_exp_, false, d_tc_partials_, &parts, s_));
+      LS_CUDA(launch_gram_finalize(h_w[q], d_tc_partials_, parts, d_G_ + (int64_t)q * kGStride, s_));
+      nl += 3;  // column exponents, tensor-core kernel, finalize
+    }
+    if (o_.method == ASCG_ADAPTIVE) {
+      LS_CUDA(launch_kappa_batch(d_G_, kGStride, d_bst_, hi_, max_sbar, s_));
+      ++nl;
+    }
     LS_CUDA(launch_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_, hi_,
                               d_coords_, kCStride, d_res_hist_, rcap_, d_ab_hist_, abcap_, s_));
     LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
     LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
-    LS_CUDA(cudaStreamSynchronize(s_));
+    launches_ += nl + 2;
+    *launched = true;
+    return ASCG_OK;
+  }
+
+  // Reads the block's outcome per lane (after the stream reached the end of
+  // launch_block's work). Lanes whose system finished are marked done.
+  void complete_block(ascg_block_info* block_hist, int block_hist_cap) {
     ++super_blocks_;
-    launches_ += max_sbar + 4 + (o_.method == ASCG_ADAPTIVE);
     for (int q = 0; q < hi_; ++q) {
       LaneSys& L = lane_[q];
       if (!used_[q] || !L.active) continue;
@@ -415,22 +460,39 @@ class Lockstep {
       }
       L.done = !L.active;
     }
+  }
+
+  // One block of every active lane, waiting for it.
+  ascg_status super_block(ascg_block_info* block_hist, int block_hist_cap) {
+    bool launched = false;
+    LS_TRY(launch_block(&launched));
+    if (!launched) return ASCG_OK;
+    LS_CUDA(cudaStreamSynchronize(s_));
+    complete_block(block_hist, block_hist_cap);
     return ASCG_OK;
   }
 
-  // True residuals ||b - A x|| / ||b|| of the done lanes that are still held
-  // (into Y column 2), and x = 0 for b = 0. Fills rel_true.
+  // Lanes held and done (finished, not yet retired).
+  std::vector<int> done_lanes() const {
+    std::vector<int> v;
+    for (int q = 0; q < hi_; ++q)
+      if (used_[q] && lane_[q].done) v.push_back(q);
+    return v;
+  }
+
+  // True residuals ||b - A x|| / ||b|| of done lanes that are still held
+  // (into Y column 2), and x = 0 for b = 0. Fills rel_true. Synchronises.
   ascg_status finish(const std::vector<int>& lanes) {
     if (lanes.empty()) return ASCG_OK;
-    int* h_sel = h_int_ + 2 * lanes_;
-    int* h_list = h_int_ + 3 * lanes_;
+    int* h_sel = h_int_ + kSel * lanes_;
+    int* h_list = h_int_ + kList * lanes_;
     for (int q = 0; q < hi_; ++q) h_sel[q] = 0;
     for (size_t i = 0; i < lanes.size(); ++i) {
       h_sel[lanes[i]] = 1;
       h_list[i] = lanes[i];
     }
-    int* d_sel = d_int_ + 2 * lanes_;
-    int* d_list = d_int_ + 3 * lanes_;
+    int* d_sel = d_int_ + kSel * lanes_;
+    int* d_list = d_int_ + kList * lanes_;
     LS_CUDA(cudaMemcpyAsync(d_sel, h_sel, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     LS_CUDA(cudaMemcpyAsync(d_list, h_list, sizeof(int) * lanes.size(), cudaMemcpyHostToDevice, s_));
     LS_CUDA(launch_residual_items(d_desc_, d_ritems_, (int)ritems_.size(), d_sel, 1, s_));
@@ -447,11 +509,11 @@ class Lockstep {
     return ASCG_OK;
   }
 
-  // Frees the lanes (their arena blocks return to the pool).
+  // Frees the lanes; the caller takes back their bases. Tables are rebuilt
+  // before the next block.
   void retire(const std::vector<int>& lanes) {
     for (int q : lanes) {
       if (!used_[q]) continue;
-      arena_.give(lane_[q].off);
       used_[q] = 0;
       --nused_;
       std::memset(&h_desc_[q], 0, sizeof(SysDesc));
@@ -461,7 +523,10 @@ class Lockstep {
     dirty_ = true;
   }
 
-  // Copies lane q's histories to the caller's rows (batched solves).
+  // Tables after retirements (admit rebuilds them itself).
+  ascg_status refresh() { return dirty_ ? rebuild_tables() : ASCG_OK; }
+
+  // Copies lane q's histories to the caller's row (batched solves).
   ascg_status copy_histories(int q, const ascg_options& o, int64_t row) {
     const LaneSys& L = lane_[q];
     if (o.res_hist && rcap_)
@@ -492,19 +557,21 @@ class Lockstep {
   }
 
   LaneSys& lane(int q) { return lane_[q]; }
-  bool used(int q) const { return used_[q] != 0; }
-  int hi() const { return hi_; }
   int nused() const { return nused_; }
-  int lanes() const { return lanes_; }
-  size_t arena_used() const { return arena_.used(); }
-  size_t arena_size() const { return arena_.size(); }
-  int64_t super_blocks() const { return super_blocks_; }
   int64_t launches() const { return launches_; }
   cudaStream_t stream() const { return s_; }
 
  private:
   static constexpr int64_t kGStride = (int64_t)kMaxW * kMaxW;
   static constexpr int64_t kCStride = 3 * kMaxW;
+  // int arrays of lanes entries each, in d_int_ and h_int_
+  enum { kSteps = 0, kW, kSel, kList, kItem0, kNItems, kWItems, kIntArrays };
+
+  int count_active() const {
+    int c = 0;
+    for (int q = 0; q < hi_; ++q) c += used_[q] && lane_[q].active;
+    return c;
+  }
 
   ascg_status grow_items(int64_t ritems, int64_t gitems) {
     if (ritems > rcap_items_) {
@@ -525,11 +592,14 @@ class Lockstep {
   }
 
   // Row items, Gram items and descriptors of the held lanes, in lane order.
+  // The pinned tables are rewritten only after the stream has passed the
+  // copies below (every caller synchronises, or waits for the block's end,
+  // before it changes the lanes again).
   ascg_status rebuild_tables() {
     ritems_.clear();
     gitems_.clear();
-    int* h_item0 = h_int_ + 4 * lanes_;
-    int* h_nitems = h_int_ + 5 * lanes_;
+    int* h_item0 = h_int_ + kItem0 * lanes_;
+    int* h_nitems = h_int_ + kNItems * lanes_;
     for (int q = 0; q < hi_; ++q) {
       h_item0[q] = (int)gitems_.size();
       h_nitems[q] = 0;
@@ -548,23 +618,17 @@ class Lockstep {
       LS_CUDA(cudaMemcpyAsync(d_gitems_, gitems_.data(), sizeof(GramItem) * gitems_.size(), cudaMemcpyHostToDevice, s_));
     if (hi_ > 0) {
       LS_CUDA(cudaMemcpyAsync(d_desc_, h_desc_, sizeof(SysDesc) * hi_, cudaMemcpyHostToDevice, s_));
-      LS_CUDA(cudaMemcpyAsync(d_int_ + 4 * lanes_, h_item0, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
-      LS_CUDA(cudaMemcpyAsync(d_int_ + 5 * lanes_, h_nitems, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + kItem0 * lanes_, h_item0, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + kNItems * lanes_, h_nitems, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     }
-    // The pinned tables above are rewritten only after the stream has been
-    // synchronised (every caller synchronises before it returns).
     dirty_ = false;
     return ASCG_OK;
   }
 
- public:
-  // Tables after retirements (admit rebuilds them itself).
-  ascg_status refresh() { return dirty_ ? rebuild_tables() : ASCG_OK; }
-
- private:
   void release() {
     dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
     dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
+    dfree(d_tc_partials_); dfree(d_tc_exp_);
     hfree(h_desc_); hfree(h_bst_); hfree(h_int_); hfree(h_sums_);
   }
 
@@ -573,14 +637,12 @@ class Lockstep {
   int lanes_ = 0, nused_ = 0, hi_ = 0, rcap_ = 0, abcap_ = 0, wcols_ = 0, npw_ = 0;
   bool dirty_ = true;
   int64_t super_blocks_ = 0, launches_ = 0;
-  Arena arena_;
   std::vector<LaneSys> lane_;
   std::vector<char> used_;
   std::vector<RowItem> ritems_;
   std::vector<GramItem> gitems_;
+  std::vector<int> tc_lanes_;
   int64_t rcap_items_ = 0, gcap_items_ = 0;
-  // device: descriptors, controller states, G and coordinate slots; ints:
-  // steps, w, sel, list, item0, nitems (lanes each); sums: 2 lanes
   SysDesc* d_desc_ = nullptr;
   BlockState* d_bst_ = nullptr;
   double* d_G_ = nullptr;
@@ -593,53 +655,42 @@ class Lockstep {
   RowItem* d_ritems_ = nullptr;
   GramItem* d_gitems_ = nullptr;
   double* d_partials_ = nullptr;
-  // pinned host mirrors
+  double* d_tc_partials_ = nullptr;
+  int* d_tc_exp_ = nullptr;
   SysDesc* h_desc_ = nullptr;
   BlockState* h_bst_ = nullptr;
   int* h_int_ = nullptr;
   double* h_sums_ = nullptr;
 };
 
-// Batched solves: every system admitted at once, super-blocks until none is
+// Batched solves: every system admitted at once, blocks until none is
 // active, then the true residuals.
 ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
                                  const double* eps_target, const ascg_options& o, ascg_result* results,
                                  cudaStream_t s) {
-  Lockstep eng;
   std::vector<LaneSys> sys(count);
-  {
-    // footprints need wcols, known only after init: compute from the options here
-    const int64_t wcols = 2 * o.s_max + 1;
-    size_t y_bytes = 0;
-    int64_t gi = 0, ri = 0;
-    for (int q = 0; q < count; ++q) {
-      int64_t n = 0;
-      if (!ops[q]) return lfail(ASCG_ERR_INVALID, "ops must hold non-NULL entries");
-      SysDesc d{};
-      int dev = 0;
-      LS_TRY(op_split_desc(ops[q], &d, &dev));
-      n = d.n;
-      y_bytes += Arena::rounded((size_t)wcols * round_up(n, kSlice) * sizeof(double));
-      gi += Lockstep::gram_items_of(n);
-      ri += Lockstep::row_items_of(n);
-    }
-    const int rcap = o.res_hist ? std::max(o.res_hist_cap, 1) : 0;
-    const int abcap = (o.alpha_hist && o.beta_hist) ? std::max(o.coef_hist_cap, 1) : 0;
-    LS_TRY(eng.init(o, count, y_bytes, gi, ri, rcap, abcap, s));
+  size_t y_bytes = 0;
+  int64_t gi = 0, ri = 0;
+  for (int q = 0; q < count; ++q) {
+    LS_TRY(Lockstep::prepare(o.s_max, ops[q], b[q], x[q], eps_target ? eps_target[q] : o.eps_target, q, &sys[q]));
+    y_bytes += Arena::rounded(sys[q].bytes);
+    gi += Lockstep::gram_items_of(sys[q].d.n);
+    ri += Lockstep::row_items_of(sys[q].d.n);
   }
-  for (int q = 0; q < count; ++q)
-    LS_TRY(eng.prepare(ops[q], b[q], x[q], eps_target ? eps_target[q] : o.eps_target, q, &sys[q]));
-  size_t admitted = 0;
-  LS_TRY(eng.admit(sys, 0, &admitted, nullptr));
-  if (admitted != (size_t)count) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
+  Arena arena;
+  LS_TRY(arena.init(y_bytes));
+  for (int q = 0; q < count; ++q) {
+    if (!arena.take(sys[q].bytes, &sys[q].off)) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
+    sys[q].d.Y = arena.at(sys[q].off);
+  }
+  const int rcap = o.res_hist ? std::max(o.res_hist_cap, 1) : 0;
+  const int abcap = (o.alpha_hist && o.beta_hist) ? std::max(o.coef_hist_cap, 1) : 0;
+  Lockstep eng;
+  LS_TRY(eng.init(o, count, gi, ri, rcap, abcap, s));
+  LS_TRY(eng.admit(sys, nullptr));
   for (int q = 0; q < count; ++q)
     if (eng.lane(q).status == ASCG_ERR_INVALID) return lfail(ASCG_ERR_INVALID, "b or x_1 is not finite");
-  for (;;) {
-    bool any = false;
-    for (int q = 0; q < count; ++q) any = any || eng.lane(q).active;
-    if (!any) break;
-    LS_TRY(eng.super_block(o.block_hist, o.block_hist_cap));
-  }
+  while (eng.any_active()) LS_TRY(eng.super_block(o.block_hist, o.block_hist_cap));
   std::vector<int> all(count);
   for (int q = 0; q < count; ++q) all[q] = q;
   LS_TRY(eng.finish(all));
@@ -663,13 +714,129 @@ ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* co
 
 using namespace ascg;
 
-struct ascg_server_s {
+namespace {
+
+// Size classes of the server, by rows: each runs its own lockstep engine on
+// its own stream and steps as soon as its previous block has landed, so
+// small systems are not held to the pace of the large ones' blocks.
+constexpr int kGroups = 3;
+constexpr int64_t kGroupEnd[kGroups] = {(int64_t)1 << 16, (int64_t)1 << 19, INT64_MAX};
+
+int group_of(int64_t n) {
+  int g = 0;
+  while (n >= kGroupEnd[g]) ++g;
+  return g;
+}
+
+struct Group {
   Lockstep eng;
+  cudaStream_t stream = nullptr;
+  cudaEvent_t done = nullptr;
+  bool in_flight = false;
+  int64_t seq = 0;  // launch order, to wait for the oldest block first
+};
+
+}  // namespace
+
+struct ascg_server_s {
   ascg_options o{};
   size_t budget = 0;
+  int max_systems = 0;
+  int running = 0;
+  cudaStream_t user = nullptr;
+  Arena arena;
+  Group group[kGroups];
   std::deque<LaneSys> queue;
   std::deque<ascg_completion> ready;
-  int64_t steps = 0;
+  int64_t steps = 0, seq = 0, launches = 0;
+
+  ~ascg_server_s() {
+    for (Group& g : group) {
+      if (g.stream) cudaStreamSynchronize(g.stream);
+    }
+    for (LaneSys& L : queue)
+      if (L.ready) cudaEventDestroy(L.ready);
+    for (Group& g : group) {
+      if (g.done) cudaEventDestroy(g.done);
+      if (g.stream) cudaStreamDestroy(g.stream);  // the engines free their buffers afterwards
+    }
+  }
+
+  void complete(Group& g, int q) {
+    LaneSys& L = g.eng.lane(q);
+    ascg_completion c;
+    std::memset(&c, 0, sizeof(c));
+    c.tag = L.tag;
+    g.eng.fill_result(q, &c.result);
+    c.result.launches = (int)std::min<int64_t>(steps - L.step_admit, 0x7fffffff);
+    c.queue_ms = L.t_admit - L.t_submit;
+    c.latency_ms = L.t_done - L.t_submit;
+    c.step_admitted = L.step_admit;
+    c.step_done = L.step_done;
+    ready.push_back(c);
+  }
+
+  // Finishes, reports and frees the done lanes of group g (its stream idle).
+  ascg_status retire_done(Group& g) {
+    std::vector<int> fin = g.eng.done_lanes();
+    if (fin.empty()) return ASCG_OK;
+    LS_TRY(g.eng.finish(fin));
+    const double t = now_ms();
+    for (int q : fin) {
+      LaneSys& L = g.eng.lane(q);
+      L.t_done = t;
+      L.step_done = steps;
+      complete(g, q);
+      arena.give(L.off);
+    }
+    running -= (int)fin.size();
+    g.eng.retire(fin);
+    return ASCG_OK;
+  }
+
+  // Admission in submission order: a request whose size class is in the
+  // middle of a block waits for it (later requests of idle classes may go
+  // ahead); the first request that finds no slot or no memory stops the scan.
+  ascg_status admit() {
+    std::vector<LaneSys> pick[kGroups];
+    int taken[kGroups] = {0, 0, 0};
+    for (auto it = queue.begin(); it != queue.end();) {
+      const int gi = group_of(it->d.n);
+      Group& g = group[gi];
+      if (g.in_flight || g.eng.free_lanes() - taken[gi] <= 0) {
+        ++it;
+        continue;
+      }
+      if (running >= max_systems) break;
+      size_t off = 0;
+      if (!arena.take(it->bytes, &off)) break;
+      LaneSys L = *it;
+      L.off = off;
+      L.d.Y = arena.at(off);
+      if (L.ready) {
+        LS_CUDA(cudaStreamWaitEvent(g.stream, L.ready, 0));
+        cudaEventDestroy(L.ready);
+        L.ready = nullptr;
+      }
+      pick[gi].push_back(L);
+      ++taken[gi];
+      ++running;
+      it = queue.erase(it);
+    }
+    for (int gi = 0; gi < kGroups; ++gi) {
+      if (pick[gi].empty()) continue;
+      Group& g = group[gi];
+      std::vector<int> lanes;
+      LS_TRY(g.eng.admit(pick[gi], &lanes));
+      const double t = now_ms();
+      for (int q : lanes) {
+        g.eng.lane(q).t_admit = t;
+        g.eng.lane(q).step_admit = steps;
+      }
+      LS_TRY(retire_done(g));  // systems that needed no block
+    }
+    return ASCG_OK;
+  }
 };
 
 extern "C" {
@@ -697,18 +864,29 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   }
   srv->o = o;
   srv->budget = (size_t)hbm_budget;
+  srv->max_systems = max_systems;
+  srv->user = (cudaStream_t)cuda_stream;
   // The Gram partials take (2 s_max + 1)(s_max + 1) doubles per 8192 rows
-  // against (2 s_max + 1) 8192 doubles of basis: reserve them out of the
+  // against (2 s_max + 1) 8192 doubles of basis: set them aside out of the
   // budget for the most rows the budget can hold, plus one item per system.
   const int64_t wcols = 2 * o.s_max + 1, npw = wcols * (wcols + 1) / 2;
   const int64_t rows_max = hbm_budget / (wcols * (int64_t)sizeof(double));
   const int64_t gitems = rows_max / kGramItemRows + max_systems;
   const int64_t part_bytes = gitems * npw * (int64_t)sizeof(double);
   const int64_t y_bytes = std::max<int64_t>(hbm_budget - part_bytes, 0);
-  ascg_status st = srv->eng.init(o, max_systems, (size_t)y_bytes, gitems, 1024, 0, 0, (cudaStream_t)cuda_stream);
-  if (st != ASCG_OK) {
+  auto fail_free = [&](ascg_status st) {
     delete srv;
     return st;
+  };
+  ascg_status st = srv->arena.init((size_t)y_bytes);
+  if (st != ASCG_OK) return fail_free(st);
+  for (int gi = 0; gi < kGroups; ++gi) {
+    Group& g = srv->group[gi];
+    cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail_free(lfail(ASCG_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e)));
+    st = g.eng.init(o, max_systems, gitems / kGroups + 1, 1024, 0, 0, g.stream);
+    if (st != ASCG_OK) return fail_free(st);
   }
   *out = srv;
   return ASCG_OK;
@@ -716,7 +894,6 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
 
 ascg_status ascg_server_destroy(ascg_server srv) {
   if (!srv) return ASCG_OK;
-  cudaStreamSynchronize(srv->eng.stream());
   delete srv;
   return ASCG_OK;
 }
@@ -726,13 +903,20 @@ ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, dou
   set_last_error("");
   if (!srv) return lfail(ASCG_ERR_INVALID, "srv is NULL");
   LaneSys L;
-  LS_TRY(srv->eng.prepare(op, b, x, eps_target, tag, &L));
-  if (srv->eng.footprint(L.d.n) > srv->budget || L.bytes > srv->eng.arena_size())
+  LS_TRY(Lockstep::prepare(srv->o.s_max, op, b, x, eps_target, tag, &L));
+  if (Lockstep::footprint(srv->o.s_max, L.d.n) > srv->budget || Arena::rounded(L.bytes) > srv->arena.size())
     return lfail(ASCG_ERR_INVALID, "the system needs more device memory than the server's budget");
+  LS_CUDA(cudaEventCreateWithFlags(&L.ready, cudaEventDisableTiming));
+  cudaError_t e = cudaEventRecord(L.ready, srv->user);
+  if (e != cudaSuccess) {
+    cudaEventDestroy(L.ready);
+    return lfail(ASCG_ERR_CUDA, std::string("cudaEventRecord: ") + cudaGetErrorString(e));
+  }
   L.t_submit = now_ms();
   try {
     srv->queue.push_back(L);
   } catch (const std::bad_alloc&) {
+    cudaEventDestroy(L.ready);
     return lfail(ASCG_ERR_OOM, "host allocation failed");
   }
   return ASCG_OK;
@@ -742,72 +926,46 @@ ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, in
                              int* npending) {
   set_last_error("");
   if (!srv || (cap > 0 && !done) || cap < 0) return lfail(ASCG_ERR_INVALID, "bad argument");
-  Lockstep& eng = srv->eng;
-  auto complete = [&](int q) {
-    LaneSys& L = eng.lane(q);
-    ascg_completion c;
-    std::memset(&c, 0, sizeof(c));
-    c.tag = L.tag;
-    eng.fill_result(q, &c.result);
-    c.result.launches = (int)std::min<int64_t>(srv->steps - L.step_admit + 1, 0x7fffffff);
-    c.queue_ms = L.t_admit - L.t_submit;
-    c.latency_ms = L.t_done - L.t_submit;
-    c.step_admitted = L.step_admit;
-    c.step_done = L.step_done;
-    srv->ready.push_back(c);
-  };
   try {
-    // 1. admission: FIFO, while a lane is free and the arena can place the head
-    if (!srv->queue.empty() && eng.has_free_lane()) {
-      std::vector<LaneSys> head;
-      for (const LaneSys& L : srv->queue) {
-        if ((int)head.size() >= eng.lanes() - eng.nused()) break;
-        head.push_back(L);
+    for (;;) {
+      bool progressed = false;
+      // 1. blocks that have landed
+      for (Group& g : srv->group) {
+        if (!g.in_flight) continue;
+        const cudaError_t q = cudaEventQuery(g.done);
+        if (q == cudaErrorNotReady) continue;
+        if (q != cudaSuccess) return lfail(ASCG_ERR_CUDA, std::string("block: ") + cudaGetErrorString(q));
+        g.in_flight = false;
+        g.eng.complete_block(nullptr, 0);
+        ++srv->steps;
+        progressed = true;
+        LS_TRY(srv->retire_done(g));
       }
-      size_t admitted = 0;
-      std::vector<int> fresh;
-      LS_TRY(eng.admit(head, 0, &admitted, &fresh));
-      const double t = now_ms();
-      for (size_t i = 0; i < admitted; ++i) srv->queue.pop_front();
-      std::vector<int> finished;
-      for (int q : fresh) {
-        LaneSys& L = eng.lane(q);
-        L.t_admit = t;
-        L.step_admit = srv->steps;
-        if (L.done) finished.push_back(q);
-      }
-      if (!finished.empty()) {
-        LS_TRY(eng.finish(finished));
-        const double td = now_ms();
-        for (int q : finished) {
-          eng.lane(q).t_done = td;
-          eng.lane(q).step_done = srv->steps;
-          complete(q);
+      // 2. admission
+      const size_t before = srv->ready.size();
+      if (!srv->queue.empty()) LS_TRY(srv->admit());
+      progressed = progressed || srv->ready.size() > before;
+      // 3. the next block of every idle group with work
+      bool in_flight = false;
+      for (Group& g : srv->group) {
+        if (!g.in_flight) {
+          LS_TRY(g.eng.refresh());
+          bool launched = false;
+          LS_TRY(g.eng.launch_block(&launched));
+          if (launched) {
+            LS_CUDA(cudaEventRecord(g.done, g.stream));
+            g.in_flight = true;
+            g.seq = ++srv->seq;
+          }
         }
-        eng.retire(finished);
-        LS_TRY(eng.refresh());
+        in_flight = in_flight || g.in_flight;
       }
-    }
-    // 2. one block of every active system
-    bool any = false;
-    for (int q = 0; q < eng.hi(); ++q) any = any || (eng.used(q) && eng.lane(q).active);
-    if (any) {
-      LS_TRY(eng.super_block(nullptr, 0));
-      std::vector<int> finished;
-      for (int q = 0; q < eng.hi(); ++q)
-        if (eng.used(q) && eng.lane(q).done) finished.push_back(q);
-      if (!finished.empty()) {
-        LS_TRY(eng.finish(finished));
-        const double td = now_ms();
-        for (int q : finished) {
-          eng.lane(q).t_done = td;
-          eng.lane(q).step_done = srv->steps;
-          complete(q);
-        }
-        eng.retire(finished);
-        LS_TRY(eng.refresh());
-      }
-      ++srv->steps;
+      if (progressed || !in_flight) break;
+      // 4. nothing landed yet: wait for the oldest block
+      Group* oldest = nullptr;
+      for (Group& g : srv->group)
+        if (g.in_flight && (!oldest || g.seq < oldest->seq)) oldest = &g;
+      LS_CUDA(cudaEventSynchronize(oldest->done));
     }
   } catch (const std::bad_alloc&) {
     return lfail(ASCG_ERR_OOM, "host allocation failed");
@@ -818,7 +976,7 @@ ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, in
     srv->ready.pop_front();
   }
   if (ndone) *ndone = nd;
-  if (nactive) *nactive = eng.nused();
+  if (nactive) *nactive = srv->running;
   if (npending) *npending = (int)std::min<size_t>(srv->queue.size() + srv->ready.size(), 0x7fffffff);
   return ASCG_OK;
 }
@@ -827,14 +985,16 @@ ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* st) {
   if (!srv || !st) return lfail(ASCG_ERR_INVALID, "bad argument");
   std::memset(st, 0, sizeof(*st));
   st->budget_bytes = (int64_t)srv->budget;
-  st->basis_bytes_used = (int64_t)srv->eng.arena_used();
-  st->basis_bytes_total = (int64_t)srv->eng.arena_size();
-  st->systems_running = srv->eng.nused();
-  st->max_systems = srv->eng.lanes();
+  st->basis_bytes_used = (int64_t)srv->arena.used();
+  st->basis_bytes_total = (int64_t)srv->arena.size();
+  st->systems_running = srv->running;
+  st->max_systems = srv->max_systems;
   st->queued = (int64_t)srv->queue.size();
   st->completions_pending = (int64_t)srv->ready.size();
   st->steps = srv->steps;
-  st->launches = srv->eng.launches();
+  int64_t l = 0;
+  for (const Group& g : srv->group) l += g.eng.launches();
+  st->launches = l;
   return ASCG_OK;
 }
 

@@ -303,3 +303,37 @@ def batch_systems(count: int = 256, seed: int | None = None, nmin: float = 1e3, 
         b = rhs_uniform(A.n, rng)
         out.append(dict(name=f"{fam}_{A.n}", family=fam, A=A, b=b, x1=np.zeros(A.n), eps=eps))
     return out
+
+
+def serve_pool(size: int = 12, seed: int | None = None, nmin: float = 1e4, nmax: float = 4e6):
+    """Operators for the served workload: `size` SPD matrices whose sizes sit
+    at the quantiles (i + 1/2)/size of the log-uniform law on [nmin, nmax],
+    families (2D Poisson, 3D Poisson, banded with half-bandwidth ~ U{8..64})
+    dealt out in a seeded random order, equal numbers of each. Returns a list
+    of dicts with A, family and name."""
+    rng = np.random.default_rng(seed_for(5) if seed is None else seed)
+    fams = np.array(["poisson2d", "poisson3d", "banded"] * ((size + 2) // 3))[:size]
+    fams = fams[rng.permutation(size)]
+    out = []
+    for i in range(size):
+        n = int(round(float(np.exp(np.log(nmin) + (i + 0.5) / size * (np.log(nmax) - np.log(nmin))))))
+        fam = str(fams[i])
+        if fam == "poisson2d":
+            A = poisson2d(max(2, int(round(n ** 0.5))))
+        elif fam == "poisson3d":
+            A = poisson3d(max(2, int(round(n ** (1.0 / 3.0)))))
+        else:
+            A = banded_spd(n, int(rng.integers(8, 65)), rng)
+        out.append(dict(name=f"{fam}_{A.n}", family=fam, A=A))
+    return out
+
+
+def serve_requests(count: int, pool_size: int = 12, seed: int | None = None):
+    """Request stream of the served workload: for each request the pool
+    operator (uniform), the relative target (uniform over 1e-6, 1e-8, 1e-10,
+    1e-12), a seed for its right-hand side, and its inter-arrival gap for a
+    Poisson process of rate 1 (exponential, mean 1; scale by 1/rate).
+    Returns a dict of numpy arrays: op, eps, rhs_seed, gap."""
+    rng = np.random.default_rng((seed_for(5) if seed is None else seed) + 1)
+    return dict(op=rng.integers(0, pool_size, count), eps=rng.choice([1e-6, 1e-8, 1e-10, 1e-12], count),
+                rhs_seed=rng.integers(0, 2 ** 62, count), gap=rng.exponential(1.0, count))
