@@ -54,7 +54,8 @@ typedef enum {
 typedef enum {
   ASCG_CLASSICAL = 0,        /* Alg. 1                                            */
   ASCG_FIXED_S = 1,          /* Alg. 2 with s = s_max                             */
-  ASCG_ADAPTIVE = 2          /* Alg. 4                                            */
+  ASCG_ADAPTIVE = 2,         /* Alg. 4                                            */
+  ASCG_VARIABLE_S = 3        /* Alg. 3: block k takes s_k = s_seq[min(k, len-1)]  */
 } ascg_method;
 
 typedef enum {
@@ -91,7 +92,8 @@ typedef struct {
 typedef struct {
   int method;                /* ascg_method                                       */
   int basis;                 /* ascg_basis                                        */
-  int s_max;                 /* Alg. 4: s_max; Alg. 2: s. 1 <= s_max <= 16        */
+  int s_max;                 /* Alg. 4: s_max; Alg. 2: s; Alg. 3: >= every s_k.
+                                1 <= s_max <= 16                                  */
   int s0;                    /* sbar_0 (Alg. 4 "initial s value")                 */
   int f;                     /* basis growth cap: sbar_k = min(s_{k-1}+f, s_max)  */
   int newton_warmup;         /* classical steps whose Ritz values give the shifts */
@@ -109,6 +111,11 @@ typedef struct {
   int pad3_;
   double* alpha_hist; double* beta_hist; int coef_hist_cap; /* alpha_i, beta_i     */
   int pad4_;
+  /* ASCG_VARIABLE_S: host int[s_seq_len], each in 1..s_max; the last value
+     repeats (for example a Fibonacci sequence min(s_max, s_{k-1} + s_{k-2})).
+     Unused (may be NULL) for the other methods. */
+  const int* s_seq; int s_seq_len;
+  int pad5_;
 } ascg_options;
 
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
@@ -196,9 +203,10 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  *    b[q] = 0). b[q] and x[q] must not overlap each other or another system's.
  *  - eps_target: host double[count] of relative targets (eps*_q =
  *    eps_target[q] ||b_q||), or NULL for opts->eps_target.
- *  - opts: method ASCG_ADAPTIVE or ASCG_FIXED_S, basis ASCG_MONOMIAL (the other
- *    bases need per-system parameters and are not batched); s_max, s0, f, c,
- *    check_in_loop and max_iters apply to every system. Histories are per
+ *  - opts: method ASCG_ADAPTIVE, ASCG_FIXED_S or ASCG_VARIABLE_S, basis
+ *    ASCG_MONOMIAL (the other bases need per-system parameters and are not
+ *    batched); s_max, s0, f, s_seq, c, check_in_loop and max_iters apply to
+ *    every system. Histories are per
  *    system: res_hist is count x res_hist_cap, block_hist count x
  *    block_hist_cap, alpha_hist and beta_hist count x coef_hist_cap (row q is
  *    system q); the caps must be >= 1 when the arrays are given.
@@ -207,8 +215,8 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  *    the number of lockstep blocks of the whole call. Device times are not
  *    recorded.
  * Temporary device memory: (2 s_max + 1) 8 round_up(n_q, 32) bytes of basis
- * per system plus (2 s_max + 1)(s_max + 1) 8 bytes of Gram partials per 8192
- * rows. Returns ASCG_OK when every system converged, else ASCG_NOT_CONVERGED
+ * per system plus (2 s_max + 1)(s_max + 1) 8 bytes of Gram partials per Gram
+ * item (items of 1024 to 8192 rows: about n_q/16 as a power of two). Returns ASCG_OK when every system converged, else ASCG_NOT_CONVERGED
  * or ASCG_ERR_BREAKDOWN (the worst over the systems; results[q].status tells
  * which); ASCG_ERR_INVALID if some b or x_1 is not finite. Synchronises the
  * stream. */
@@ -311,7 +319,8 @@ ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int64_t ldY, do
  * by size into three classes (n < 2^16, < 2^19, larger); each class runs its
  * systems in lockstep on a stream of its own, and starts its next block as
  * soon as its previous one has landed, so the classes' blocks interleave on
- * the GPU and small systems do not wait for the blocks of large ones. A
+ * the GPU and small systems do not wait for the blocks of large ones; the
+ * smaller the class, the higher its stream priority. A
  * system's arithmetic depends on that system alone: its x, iteration count
  * and residuals are bitwise the same as from ascg_solve_batch with that
  * system alone, whatever else runs beside it.
@@ -341,11 +350,13 @@ typedef struct {
   int64_t launches;          /* kernels launched so far                            */
 } ascg_server_stats;
 
-/* Creates a server. opts: as for ascg_solve_batch (ADAPTIVE or FIXED_S,
- * MONOMIAL), history buffers NULL; eps_target is per request. hbm_budget:
+/* Creates a server. opts: as for ascg_solve_batch (an s-step method, the
+ * MONOMIAL basis; s_seq is copied), history buffers NULL; eps_target is per
+ * request. hbm_budget:
  * device bytes the server may hold for running systems. A system of n rows
  * holds (2 s_max + 1) 8 round_up(n, 32) bytes of basis plus (2 s_max + 1)
- * (s_max + 1) 8 bytes of Gram partials per 8192 rows; the whole budget is
+ * (s_max + 1) 8 bytes of Gram partials per Gram item (1024 to 8192 rows,
+ * about n/16 as a power of two); the whole budget is
  * allocated here, as one arena for the bases and one buffer for the
  * partials (plus about 16 bytes per 256 rows of row tables outside it).
  * max_systems: most systems running at once (1 .. 2^20). cuda_stream: the

@@ -28,7 +28,7 @@ ASCG_ERR_BREAKDOWN, ASCG_NOT_CONVERGED, ASCG_ERR_TIMEOUT, ASCG_ERR_NOT_SPD = 4, 
 STATUS_NAMES = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_BREAKDOWN",
                 5: "NOT_CONVERGED", 6: "ERR_TIMEOUT", 7: "ERR_NOT_SPD"}
 # ascg_method / ascg_basis / ascg_stop
-ASCG_CLASSICAL, ASCG_FIXED_S, ASCG_ADAPTIVE = 0, 1, 2
+ASCG_CLASSICAL, ASCG_FIXED_S, ASCG_ADAPTIVE, ASCG_VARIABLE_S = 0, 1, 2, 3
 ASCG_MONOMIAL, ASCG_NEWTON, ASCG_CHEBYSHEV = 0, 1, 2
 ASCG_STOP_DONE, ASCG_STOP_CONVERGED, ASCG_STOP_BREAK, ASCG_STOP_BREAKDOWN, ASCG_STOP_MAXITER = 0, 1, 2, 3, 4
 ASCG_FLAG_TIMING = 1
@@ -50,7 +50,8 @@ class ascg_options(C.Structure):
                 ("res_hist", C.POINTER(C.c_double)), ("res_hist_cap", C.c_int), ("pad2_", C.c_int),
                 ("block_hist", C.POINTER(ascg_block_info)), ("block_hist_cap", C.c_int), ("pad3_", C.c_int),
                 ("alpha_hist", C.POINTER(C.c_double)), ("beta_hist", C.POINTER(C.c_double)),
-                ("coef_hist_cap", C.c_int), ("pad4_", C.c_int)]
+                ("coef_hist_cap", C.c_int), ("pad4_", C.c_int),
+                ("s_seq", C.POINTER(C.c_int)), ("s_seq_len", C.c_int), ("pad5_", C.c_int)]
 
 
 class ascg_result(C.Structure):
@@ -306,16 +307,19 @@ def ascg_newton_shifts(alphas, betas, k, s, stream=None):
 
 # --- convenience: options from keywords -------------------------------------
 
-_METHODS = {"classical": ASCG_CLASSICAL, "fixed": ASCG_FIXED_S, "adaptive": ASCG_ADAPTIVE}
+_METHODS = {"classical": ASCG_CLASSICAL, "fixed": ASCG_FIXED_S, "adaptive": ASCG_ADAPTIVE,
+            "variable": ASCG_VARIABLE_S}
 _BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CHEBYSHEV}
 
 
 def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
-                 gram_fp64=False) -> ascg_options:
+                 gram_fp64=False, s_seq=None) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
-    ctypes array of ascg_block_info; the caller keeps them alive for the call."""
+    ctypes array of ascg_block_info; the caller keeps them alive for the call.
+    s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
+    the options object keeps its own copy alive."""
     o = ascg_options_default()
     o.method = _METHODS[method] if isinstance(method, str) else int(method)
     o.basis = _BASES[basis] if isinstance(basis, str) else int(basis)
@@ -340,6 +344,11 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
         o.alpha_hist = alpha_hist.ctypes.data_as(C.POINTER(C.c_double))
         o.beta_hist = beta_hist.ctypes.data_as(C.POINTER(C.c_double))
         o.coef_hist_cap = min(len(alpha_hist), len(beta_hist))
+    if s_seq is not None:
+        arr = (C.c_int * len(s_seq))(*[int(v) for v in s_seq])
+        o._s_seq_keep = arr
+        o.s_seq = C.cast(arr, C.POINTER(C.c_int))
+        o.s_seq_len = len(s_seq)
     return o
 
 

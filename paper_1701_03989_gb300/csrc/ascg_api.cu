@@ -260,8 +260,14 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
 }
 
 ascg_status check_opts(const ascg_options& o) {
-  if (o.method != ASCG_CLASSICAL && o.method != ASCG_FIXED_S && o.method != ASCG_ADAPTIVE)
+  if (o.method != ASCG_CLASSICAL && o.method != ASCG_FIXED_S && o.method != ASCG_ADAPTIVE &&
+      o.method != ASCG_VARIABLE_S)
     return fail(ASCG_ERR_INVALID, "unknown method");
+  if (o.method == ASCG_VARIABLE_S) {
+    if (!o.s_seq || o.s_seq_len < 1) return fail(ASCG_ERR_INVALID, "ASCG_VARIABLE_S needs s_seq and s_seq_len >= 1");
+    for (int i = 0; i < o.s_seq_len; ++i)
+      if (o.s_seq[i] < 1 || o.s_seq[i] > o.s_max) return fail(ASCG_ERR_INVALID, "s_seq entries must be in 1..s_max");
+  }
   if (o.method != ASCG_CLASSICAL) {
     if (o.s_max < 1 || o.s_max > ASCG_MAX_S) return fail(ASCG_ERR_INVALID, "s_max must be in 1..16");
     if (o.s0 < 1 || o.s0 > o.s_max) return fail(ASCG_ERR_INVALID, "s0 must be in 1..s_max");
@@ -475,7 +481,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     int k = 0, s_prev = 0;
     int nb_info = 0;
     while (!done) {
-      const int sbar = o.method == ASCG_FIXED_S ? o.s_max : (k == 0 ? o.s0 : std::min(s_prev + o.f, o.s_max));
+      const int sbar = block_sbar(o, k, s_prev);
       const int wb = 2 * sbar + 1;
       BlockState& hb = *w.h_bst;
       std::memset(&hb, 0, sizeof(hb));
@@ -782,8 +788,7 @@ ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const*
   if (count < 1 || !ops || !b || !x || !opts) return fail(ASCG_ERR_INVALID, "bad argument");
   const ascg_options o = *opts;
   ASCG_TRY(check_opts(o));
-  if (o.method != ASCG_ADAPTIVE && o.method != ASCG_FIXED_S)
-    return fail(ASCG_ERR_INVALID, "batched solves run ASCG_ADAPTIVE or ASCG_FIXED_S");
+  if (o.method == ASCG_CLASSICAL) return fail(ASCG_ERR_INVALID, "batched solves run an s-step method");
   if (o.basis != ASCG_MONOMIAL) return fail(ASCG_ERR_INVALID, "batched solves use the monomial basis");
   if ((o.res_hist && o.res_hist_cap < 1) || (o.block_hist && o.block_hist_cap < 1))
     return fail(ASCG_ERR_INVALID, "history capacities must be >= 1");

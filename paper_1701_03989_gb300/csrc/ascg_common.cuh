@@ -114,13 +114,21 @@ struct GramItem {
   int nrows;
   int sys;
 };
-constexpr int kGramItemRows = 8192;
+// Rows per Gram item of a system of n rows: about n/16 as a power of two,
+// within [1024, 8192]. It depends on the system's own size only.
+inline int64_t gram_item_rows(int64_t n) {
+  int64_t r = 1024;
+  while (r < 8192 && r * 16 < n) r *= 2;
+  return r;
+}
+constexpr int kGramItemRowsMin = 1024;
 // FP64 partials (W columns, W odd <= 33) of every item, rows read from the
 // item's system (descs[sys].Y); items of systems with sys_w 0 are skipped.
-// partials: nitems x W(W+1)/2.
+// The pairs of each item are split over pair_groups CTAs (1 .. 65535), which
+// changes no result. partials: nitems x W(W+1)/2.
 struct SysDesc;
 cudaError_t launch_gram_items(int W, const SysDesc* descs, const GramItem* items, int nitems, const int* sys_w,
-                              double* partials, cudaStream_t s);
+                              double* partials, int pair_groups, cudaStream_t s);
 // G of each active system q (w_q = sys_w[q] x w_q, stride w_q) at G + q * g_stride.
 cudaError_t launch_gram_items_finalize(int W, const double* partials, const int* sys_item0, const int* sys_nitems,
                                        const int* sys_w, int count, double* G, int64_t g_stride, cudaStream_t s);
@@ -263,6 +271,14 @@ cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGSta
 // CG state init from rr = r^T r computed into st->rr.
 cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
                            double* res_hist, int res_cap, cudaStream_t s);
+
+// Basis size sbar_k of block k: s_max (Alg. 2), s_seq[min(k, len - 1)]
+// (Alg. 3), s0 then min(s_{k-1} + f, s_max) (Alg. 4).
+inline int block_sbar(const ascg_options& o, int k, int s_prev) {
+  if (o.method == ASCG_FIXED_S) return o.s_max;
+  if (o.method == ASCG_VARIABLE_S) return o.s_seq[k < o.s_seq_len ? k : o.s_seq_len - 1];
+  return k == 0 ? o.s0 : (s_prev + o.f < o.s_max ? s_prev + o.f : o.s_max);
+}
 
 // Sets the message that ascg_last_error() returns on this thread.
 void set_last_error(const std::string& msg);

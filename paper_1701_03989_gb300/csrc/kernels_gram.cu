@@ -29,9 +29,12 @@ int g_gram_grid = 0;
 
 // Partial Gram of 32-row chunks [c0, c1) of rows [0, n) of Y into out[NP]
 // (row-major upper triangle). Called by every thread of a CTA of kGramThreads.
+// With G pair groups, this CTA takes the pairs p = g, g + G, g + 2G, ... only
+// (group g of G) and writes just those; a pair's arithmetic is the same for
+// any G.
 template <int W>
 __device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict__ Y, int64_t ldY, int64_t c0,
-                                            int64_t c1, double* __restrict__ out) {
+                                            int64_t c1, double* __restrict__ out, int g = 0, int G = 1) {
   constexpr int NP = W * (W + 1) / 2;
   constexpr int PPW = (NP + kGramWarps - 1) / kGramWarps;
   constexpr int ELEMS = W * kChunk;
@@ -42,7 +45,7 @@ __device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // pair p in row-major upper-triangle order: (0,0), (0,1), ..., (0,W-1), (1,1), ...
   for (int k = lane; k < PPW; k += 32) {
-    const int p = warp + kGramWarps * k;
+    const int p = g + G * (warp + kGramWarps * k);
     int a = 0, b = 0;
     if (p < NP) {
       int rem = p;
@@ -94,7 +97,7 @@ __device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict_
     const double* t = &tile[buf][0][0];
 #pragma unroll
     for (int k = 0; k < PPW; ++k) {
-      if (warp + kGramWarps * k < NP) {
+      if (g + G * (warp + kGramWarps * k) < NP) {
         const unsigned ab = pab[warp][k];
         const double ya = t[(ab & 0xff) * kChunk + lane];
         const double yb = t[(ab >> 8) * kChunk + lane];
@@ -106,9 +109,10 @@ __device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict_
   }
 #pragma unroll
   for (int k = 0; k < PPW; ++k) {
-    const int p = warp + kGramWarps * k;
+    const int p = g + G * (warp + kGramWarps * k);
+    if (p >= NP) break;  // uniform over the warp
     const double v = warp_sum(acc[k]);
-    if (lane == 0 && p < NP) out[p] = v;
+    if (lane == 0) out[p] = v;
   }
 }
 
@@ -121,8 +125,9 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n
                  partials + (int64_t)blockIdx.x * NP);
 }
 
-// Batched solves: CTA q takes item q (rows [row0, row0 + nrows) of one
-// system). Items depend only on the system's own size, so a system's Gram is
+// Batched solves: CTA (q, g) takes pair group g of item q (rows [row0, row0 +
+// nrows) of one system). Items depend only on the system's own size, and a
+// pair's sum does not depend on the number of groups, so a system's Gram is
 // the same alone and in any batch. Items of inactive systems (sys_w 0) skip.
 template <int W>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_items_kernel(const SysDesc* __restrict__ descs,
@@ -134,7 +139,7 @@ __global__ void __launch_bounds__(kGramThreads, 1) gram_items_kernel(const SysDe
   if (sys_w[it.sys] == 0) return;  // uniform over the CTA
   const SysDesc& d = descs[it.sys];
   gram_chunks<W>(it.nrows, d.Y + it.row0, d.ldY, 0, (it.nrows + kChunk - 1) / kChunk,
-                 partials + (int64_t)blockIdx.x * NP);
+                 partials + (int64_t)blockIdx.x * NP, (int)blockIdx.y, (int)gridDim.y);
 }
 
 // Four threads per pair (lanes 4q .. 4q+3 of a warp): thread t adds the
@@ -242,12 +247,14 @@ cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, 
 }
 
 cudaError_t launch_gram_items(int W, const SysDesc* descs, const GramItem* items, int nitems, const int* sys_w,
-                              double* partials, cudaStream_t s) {
+                              double* partials, int pair_groups, cudaStream_t s) {
   if (nitems < 1) return cudaSuccess;
+  if (pair_groups < 1 || pair_groups > 65535) return cudaErrorInvalidValue;
+  const dim3 grid(nitems, pair_groups);
   switch (W) {
 #define ASCG_GI(WW)                                                                            \
   case WW:                                                                                     \
-    gram_items_kernel<WW><<<nitems, kGramThreads, 0, s>>>(descs, items, sys_w, partials);  \
+    gram_items_kernel<WW><<<grid, kGramThreads, 0, s>>>(descs, items, sys_w, partials);     \
     return cudaGetLastError();
     ASCG_GI(3) ASCG_GI(5) ASCG_GI(7) ASCG_GI(9) ASCG_GI(11) ASCG_GI(13) ASCG_GI(15) ASCG_GI(17) ASCG_GI(19)
     ASCG_GI(21) ASCG_GI(23) ASCG_GI(25) ASCG_GI(27) ASCG_GI(29) ASCG_GI(31) ASCG_GI(33)

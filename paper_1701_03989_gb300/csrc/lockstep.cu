@@ -199,6 +199,10 @@ class Lockstep {
   ascg_status init(const ascg_options& o, int lanes, int64_t gitems, int64_t ritems, int rcap, int abcap,
                    cudaStream_t s) {
     o_ = o;
+    if (o.method == ASCG_VARIABLE_S) {  // keep a copy: the caller's array may go
+      seq_.assign(o.s_seq, o.s_seq + o.s_seq_len);
+      o_.s_seq = seq_.data();
+    }
     s_ = s;
     lanes_ = lanes;
     rcap_ = rcap;
@@ -239,7 +243,7 @@ class Lockstep {
     return ASCG_OK;
   }
 
-  static int64_t gram_items_of(int64_t n) { return (n + kGramItemRows - 1) / kGramItemRows; }
+  static int64_t gram_items_of(int64_t n) { return (n + gram_item_rows(n) - 1) / gram_item_rows(n); }
   static int64_t row_items_of(int64_t n) { return (n + kRowItem - 1) / kRowItem; }
   // Basis bytes of a system of n rows: 2 s_max + 1 columns of round_up(n, 32).
   static size_t basis_bytes(int s_max, int64_t n) {
@@ -358,7 +362,7 @@ class Lockstep {
         h_wi[q] = 0;
         continue;
       }
-      const int sbar = o_.method == ASCG_FIXED_S ? o_.s_max : (L.kb == 0 ? o_.s0 : std::min(L.s_prev + o_.f, o_.s_max));
+      const int sbar = block_sbar(o_, L.kb, L.s_prev);
       L.sbar = sbar;
       hb.sbar = sbar;
       hb.method = o_.method;
@@ -394,7 +398,9 @@ class Lockstep {
     const int Wb = 2 * max_sbar + 1;
     int nl = max_sbar;
     if ((int)tc_lanes_.size() < count_active()) {
-      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, s_));
+      // pair groups: enough CTAs to cover the SMs twice
+      const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
+      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, s_));
       LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, s_));
       nl += 2;
     }
@@ -607,8 +613,8 @@ class Lockstep {
       const int64_t n = lane_[q].d.n;
       for (int64_t r = 0; r < n; r += kRowItem)
         ritems_.push_back(RowItem{q, (int)r, (int)std::min<int64_t>(kRowItem, n - r), 0});
-      for (int64_t r = 0; r < n; r += kGramItemRows)
-        gitems_.push_back(GramItem{r, (int)std::min<int64_t>(kGramItemRows, n - r), q});
+      const int64_t gr = gram_item_rows(n);
+      for (int64_t r = 0; r < n; r += gr) gitems_.push_back(GramItem{r, (int)std::min<int64_t>(gr, n - r), q});
       h_nitems[q] = (int)gitems_.size() - h_item0[q];
     }
     LS_TRY(grow_items((int64_t)ritems_.size(), (int64_t)gitems_.size()));
@@ -633,6 +639,7 @@ class Lockstep {
   }
 
   ascg_options o_{};
+  std::vector<int> seq_;
   cudaStream_t s_ = nullptr;
   int lanes_ = 0, nused_ = 0, hi_ = 0, rcap_ = 0, abcap_ = 0, wcols_ = 0, npw_ = 0;
   bool dirty_ = true;
@@ -849,8 +856,7 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   if (!opts) return lfail(ASCG_ERR_INVALID, "opts is NULL");
   const ascg_options o = *opts;
   LS_TRY(check_options(o));
-  if (o.method != ASCG_ADAPTIVE && o.method != ASCG_FIXED_S)
-    return lfail(ASCG_ERR_INVALID, "the server runs ASCG_ADAPTIVE or ASCG_FIXED_S");
+  if (o.method == ASCG_CLASSICAL) return lfail(ASCG_ERR_INVALID, "the server runs an s-step method");
   if (o.basis != ASCG_MONOMIAL) return lfail(ASCG_ERR_INVALID, "the server uses the monomial basis");
   if (o.res_hist || o.block_hist || o.alpha_hist || o.beta_hist)
     return lfail(ASCG_ERR_INVALID, "the server keeps no histories: the history buffers must be NULL");
@@ -866,12 +872,13 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   srv->budget = (size_t)hbm_budget;
   srv->max_systems = max_systems;
   srv->user = (cudaStream_t)cuda_stream;
-  // The Gram partials take (2 s_max + 1)(s_max + 1) doubles per 8192 rows
-  // against (2 s_max + 1) 8192 doubles of basis: set them aside out of the
-  // budget for the most rows the budget can hold, plus one item per system.
+  // The Gram partials take (2 s_max + 1)(s_max + 1) doubles per item of at
+  // least 1024 rows against (2 s_max + 1) 1024 doubles of basis: set them
+  // aside out of the budget for the most rows the budget can hold, plus one
+  // item per system.
   const int64_t wcols = 2 * o.s_max + 1, npw = wcols * (wcols + 1) / 2;
   const int64_t rows_max = hbm_budget / (wcols * (int64_t)sizeof(double));
-  const int64_t gitems = rows_max / kGramItemRows + max_systems;
+  const int64_t gitems = rows_max / kGramItemRowsMin + max_systems;
   const int64_t part_bytes = gitems * npw * (int64_t)sizeof(double);
   const int64_t y_bytes = std::max<int64_t>(hbm_budget - part_bytes, 0);
   auto fail_free = [&](ascg_status st) {
@@ -880,9 +887,14 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   };
   ascg_status st = srv->arena.init((size_t)y_bytes);
   if (st != ASCG_OK) return fail_free(st);
+  // Stream priorities: the smallest class highest, so that as the CTAs of a
+  // large class's kernels retire, the SMs go to waiting small-class CTAs first.
+  int prio_least = 0, prio_greatest = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest);
   for (int gi = 0; gi < kGroups; ++gi) {
     Group& g = srv->group[gi];
-    cudaError_t e = cudaStreamCreateWithFlags(&g.stream, cudaStreamNonBlocking);
+    const int prio = std::min(prio_least, prio_greatest + gi);  // greatest is the numerically lowest
+    cudaError_t e = cudaStreamCreateWithPriority(&g.stream, cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail_free(lfail(ASCG_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e)));
     st = g.eng.init(o, max_systems, gitems / kGroups + 1, 1024, 0, 0, g.stream);

@@ -103,10 +103,13 @@ def compare_block_sequences(gpu_blocks, oracle_blocks, n: int, oracle_hist=None,
         bad.append(f"block {k}: stilde/s_k gpu {g['stilde']}/{g['s_k']} oracle {o['stilde']}/{o['s_k']} "
                    f"T={T:.6g} sk_gpu={list(g['sqrt_kappa'][:g['sbar']])} sk_or={o.get('kappas')}")
         return k, bad
-    if len(gpu_blocks) != len(oracle_blocks) and min(len(gpu_blocks), len(oracle_blocks)) > 0:
+    shorter = gpu_blocks if len(gpu_blocks) < len(oracle_blocks) else oracle_blocks
+    if len(gpu_blocks) != len(oracle_blocks) and shorter and _stopped_converged(shorter[-1]):
         # Both ran their common blocks alike; after the last of them one side
-        # stopped and the other went on: a stop decision at iteration i.
-        k = min(len(gpu_blocks), len(oracle_blocks)) - 1
+        # stopped on convergence and the other went on: a stop decision at
+        # iteration i. (A side that ended for another reason, such as an
+        # iteration cap on a prefix comparison, decided nothing.)
+        k = len(shorter) - 1
         o = oracle_blocks[k]
         i = o["m"] + o["s_k"]
         near = False
@@ -118,6 +121,11 @@ def compare_block_sequences(gpu_blocks, oracle_blocks, n: int, oracle_hist=None,
         bad.append(f"after block {k}: {len(gpu_blocks)} gpu blocks vs {len(oracle_blocks)} oracle blocks")
         return k, bad
     return None, bad
+
+
+def _stopped_converged(block) -> bool:
+    st = block.get("stop")
+    return st == "converged" or st == 1  # oracle record / ascg_block_info (ASCG_STOP_CONVERGED)
 
 
 def final_residual_ok(gpu_true: float, oracle_true: float, target: float, exempt_block) -> bool:

@@ -36,7 +36,7 @@ def make_op(P, A):
                                 np.ascontiguousarray(A.colind, np.int32), np.ascontiguousarray(A.val, np.float64), 0)
 
 
-def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None):
+def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None, s_seq=None):
     count = len(systems)
     ops = [make_op(P, s["A"]) for s in systems]
     bs = [dev(torch, s["b"]) for s in systems]
@@ -44,7 +44,7 @@ def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", 
     res_hist = np.zeros((count, max_iters + 2))
     infos = P.block_infos(count * (max_iters + 2))
     o = P.make_options(method=method, basis="monomial", s_max=s_max, eps_target=1e-10, max_iters=max_iters,
-                       res_hist=res_hist.reshape(-1), block_hist=infos)
+                       res_hist=res_hist.reshape(-1), block_hist=infos, s_seq=s_seq)
     o.res_hist_cap = max_iters + 2
     o.block_hist_cap = max_iters + 2
     epsv = [s["eps"] for s in systems] if eps is None else eps
@@ -168,6 +168,37 @@ def test_batch_edge_cases(env):
     assert 0.5 * orc.true_res <= fixed[0]["res"].rel_res_true <= 2.0 * orc.true_res
 
 
+def test_batch_variable_s(env):
+    """Alg. 3 in a batch: every system takes the given block sizes (Fibonacci-type
+    growth capped at 5); s_k sequences equal the oracle's, histories and true
+    residuals within the parity rules."""
+    P, torch = env
+    systems = small_batch(seed=14, count=4)
+    seq = W.fibonacci_s_sequence(5, 7)
+    out, st = run_batch(P, torch, systems, s_max=5, method="variable", s_seq=seq)
+    assert st == P.ASCG_OK
+    for s, g in zip(systems, out):
+        orc = O.variable_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], seq, O.monomial_params(5),
+                                  eps_target=s["eps"], max_iters=CAP)
+        sg, so = [b["s_k"] for b in g["blocks"]], [b["s_k"] for b in orc.blocks]
+        assert [b["sbar"] for b in g["blocks"]][:len(so)] == [b["sbar"] for b in orc.blocks][:len(sg)]
+        exempt = None
+        if sg != so:
+            # only a stop decision may differ: the earlier of the two stops must lie
+            # where the oracle's residual is within the history tolerance of the target
+            k = next((i for i, (a, b) in enumerate(zip(sg, so)) if a != b), None)
+            if k is None:  # one sequence is a prefix of the other
+                k = min(len(sg), len(so)) - 1
+                i = sum(sg if len(sg) < len(so) else so)
+            else:
+                i = min(sum(sg[:k + 1]), sum(so[:k + 1]))
+            assert abs(orc.res_hist[i] - s["eps"]) <= 1e-10 + 1e-6 * s["eps"], (s["name"], sg, so)
+            exempt = k
+        nwin = min(21, len(g["hist"]), len(orc.res_hist), s["A"].n)
+        assert np.all(np.abs(g["hist"][:nwin] - np.asarray(orc.res_hist[:nwin])) <= 1e-10), s["name"]
+        assert parity.final_residual_ok(g["res"].rel_res_true, orc.true_res, s["eps"], exempt), s["name"]
+
+
 def test_batch_rejects_unsupported(env):
     P, torch = env
     A = W.poisson2d(8)
@@ -181,4 +212,8 @@ def test_batch_rejects_unsupported(env):
     o = P.make_options(method="classical")
     with pytest.raises(P.AscgError):
         P.ascg_solve_batch([op], [b], [x], o)
+    o = P.make_options(method="variable", s_max=4, s_seq=[2, 5])  # an entry above s_max
+    with pytest.raises(P.AscgError) as e:
+        P.ascg_solve_batch([op], [b], [x], o)
+    assert e.value.status == P.ASCG_ERR_INVALID
     P.ascg_op_destroy(op)

@@ -395,6 +395,12 @@ SOLVES = [
     ("banded_3001", dict(method="adaptive", basis="chebyshev", s_max=10), 1e-12),
     # the same Chebyshev solve with the Gram matrix formed by FP64 FMAs instead of the tensor cores
     ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_fp64=True), 1e-12),
+    # Alg. 3: block sizes from a given sequence (Fibonacci-type growth capped at s_max)
+    ("poisson2d_32", dict(method="variable", basis="monomial", s_max=5, s_seq=W.fibonacci_s_sequence(5, 8)), 1e-10),
+    ("poisson3d_23", dict(method="variable", basis="chebyshev", s_max=12, s_seq=W.fibonacci_s_sequence(12, 9)), 1e-12),
+    # s <= 3: without the adaptive test, a wider monomial basis on this matrix lets the residual gap of
+    # eq. (fb) reach the target, and both true residuals become rounding noise
+    ("banded_3001", dict(method="variable", basis="monomial", s_max=3, s_seq=[1, 3, 2]), 1e-8),
 ]
 
 
@@ -430,6 +436,9 @@ def run_oracle(A, b, x1, kw, eps, lam, max_iters=20000):
     s = kw.get("s_max", 8)
     if method == "fixed":
         return O.fixed_sstep_cg(Ao, b, x1, s, O.monomial_params(s), eps_target=eps, max_iters=max_iters)
+    if method == "variable":
+        bp = O.chebyshev_params(lam[0], lam[1], s) if kw.get("basis") == "chebyshev" else O.monomial_params(s)
+        return O.variable_sstep_cg(Ao, b, x1, kw["s_seq"], bp, eps_target=eps, max_iters=max_iters)
     return O.adaptive_sstep_cg(Ao, b, x1, s_max=s, s0=kw.get("s0"), f=kw.get("f"), eps_target=eps,
                                basis=kw.get("basis", "monomial"), lam=lam, newton_warmup=kw.get("newton_warmup"),
                                check_in_loop=kw.get("check_in_loop", True), max_iters=max_iters)
@@ -453,8 +462,9 @@ def test_solve_parity(env, name, kw, eps):
         assert not bad, bad
     else:
         exempt = None
-        if kw["method"] == "fixed":
+        if kw["method"] in ("fixed", "variable"):
             assert [b_["s_k"] for b_ in blocks] == [b_["s_k"] for b_ in orc.blocks]
+            assert [b_["sbar"] for b_ in blocks] == [b_["sbar"] for b_ in orc.blocks]
     nwin = parity.history_window(blocks, getattr(orc, "blocks", []), exempt, iters=20)
     if kw.get("basis") == "newton":
         nwin = max(nwin, min(25, len(hist)))   # the classical warm-up is compared too

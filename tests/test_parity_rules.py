@@ -14,6 +14,9 @@ import workloads as W
 from oracle import ascg_oracle as O
 
 
+STOP_CODE = {"done": 0, "converged": 1, "break": 2, "breakdown": 3, "maxiter": 4}
+
+
 def as_gpu(blocks):
     out = []
     for o in blocks:
@@ -21,7 +24,7 @@ def as_gpu(blocks):
         for i, v, _ in o["kappas"]:
             sk[i - 1] = v
         out.append(dict(sbar=o["sbar"], stilde=o["stilde"], s_k=o["s_k"], m=o["m"], rnorm=o["rnorm"],
-                        threshold=o["threshold"], gamma=o["gamma"], sqrt_kappa=sk))
+                        threshold=o["threshold"], gamma=o["gamma"], sqrt_kappa=sk, stop=STOP_CODE[o["stop"]]))
     return out
 
 
@@ -85,11 +88,20 @@ def test_stop_decision_one_block_apart(run):
     # far from it: a real mismatch
     exempt, bad = parity.compare_block_sequences(g + [extra], r.blocks, A.n, r.res_hist, h * 100)
     assert bad
-    # GPU stopped a block early (oracle went on): the same rule from the other side
-    exempt, bad = parity.compare_block_sequences(g[:-1], r.blocks, A.n, r.res_hist, 1e-8)
+    # GPU stopped on convergence a block early (oracle went on): the same rule from the other side
+    early = g[:-1]
+    early[-1] = dict(early[-1], stop=1)
     prev = r.blocks[-2]
-    near = abs(r.res_hist[prev["m"] + prev["s_k"]] - 1e-8) <= max(1e-10, 1e-6 * 1e-8)
-    assert (not bad) == near
+    h_prev = r.res_hist[prev["m"] + prev["s_k"]]
+    exempt, bad = parity.compare_block_sequences(early, r.blocks, A.n, r.res_hist, h_prev + 0.5e-10)
+    assert exempt == len(early) - 1 and not bad
+    exempt, bad = parity.compare_block_sequences(early, r.blocks, A.n, r.res_hist, h_prev / 100)
+    assert bad
+    # a side that ended for another reason (an iteration cap) decided nothing: prefix comparison
+    capped = g[:-1]
+    capped[-1] = dict(capped[-1], stop=4)
+    exempt, bad = parity.compare_block_sequences(capped, r.blocks, A.n, r.res_hist, 1e-8)
+    assert exempt is None and not bad
 
 
 def test_final_residual_rule_after_a_flipped_stop():

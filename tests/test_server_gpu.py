@@ -39,11 +39,18 @@ def opts(P, max_iters=4000):
     return P.make_options(method="adaptive", basis="monomial", s_max=S_MAX, eps_target=1e-10, max_iters=max_iters)
 
 
+def gram_item_rows(n):
+    r = 1024
+    while r < 8192 and r * 16 < n:
+        r *= 2
+    return r
+
+
 def footprint(n, s_max=S_MAX):
     w = 2 * s_max + 1
     ld = (n + 31) // 32 * 32
     y = (w * ld * 8 + 255) // 256 * 256
-    return y + -(-n // 8192) * (w * (w + 1) // 2) * 8
+    return y + -(-n // gram_item_rows(n)) * (w * (w + 1) // 2) * 8
 
 
 def solve_alone(P, torch, op, b, x1, eps, max_iters=4000):

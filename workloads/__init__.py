@@ -337,3 +337,13 @@ def serve_requests(count: int, pool_size: int = 12, seed: int | None = None):
     rng = np.random.default_rng((seed_for(5) if seed is None else seed) + 1)
     return dict(op=rng.integers(0, pool_size, count), eps=rng.choice([1e-6, 1e-8, 1e-10, 1e-12], count),
                 rhs_seed=rng.integers(0, 2 ** 62, count), gap=rng.exponential(1.0, count))
+
+
+def fibonacci_s_sequence(s_max: int, count: int, s0: int = 1, s1: int = 1):
+    """Block sizes s_k = min(s_max, s_{k-1} + s_{k-2}) (the Fibonacci-type growth
+    of Imberti and Erhel that the paper cites as related work), starting from
+    s0, s1: an input sequence for variable s-step CG (Alg. 3)."""
+    seq = [min(s_max, s0), min(s_max, s1)]
+    while len(seq) < count:
+        seq.append(min(s_max, seq[-1] + seq[-2]))
+    return seq[:count]
