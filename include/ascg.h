@@ -116,11 +116,21 @@ typedef struct {
      Unused (may be NULL) for the other methods. */
   const int* s_seq; int s_seq_len;
   int pad5_;
+  /* ASCG_FLAG_C_FORMULA (ASCG_ADAPTIVE, ascg_solve only): estimates of
+     kappa(A) (>= 1) and ||A||_2 (> 0) for c_{k,j} = 6 N_k j kappa(A) */
+  double kappa_A, norm_A;
 } ascg_options;
 
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
 #define ASCG_FLAG_GRAM_FP64 2 /* Gram by FP64 FMAs on the CUDA cores for every w,
                                  instead of the tensor-core kernel (w >= 9)      */
+#define ASCG_FLAG_C_FORMULA 4 /* c_{k,j} = 6 N_k j kappa(A), the factor of the gap
+                                 bound eq. (fb), instead of the constant c:
+                                 N_k = 7 + 2 N_A + 14 ||B_k|| / ||A||, N_A = most
+                                 nonzeros in a row of A, B_k of the block's basis
+                                 (size sbar_k), eq. (condy) with c_{k,s_max} and
+                                 eq. (check) after step j with c_{k,j}. Needs
+                                 kappa_A and norm_A; ASCG_ADAPTIVE only.         */
 
 typedef struct {
   int status;                /* ascg_status of the solve                          */

@@ -357,19 +357,38 @@ def recover(Y, x, xc, rc, pc):
     return x + Y @ xc, Y @ rc, Y @ pc
 
 
+def formula_c_step(A: Operator, B, kappa_A: float, norm_A: float) -> float:
+    """6 N_k kappa(A), the factor of c_{k,j} = 6 N_k j kappa(A) that the bound
+    eq. (fb) gives, with N_k = 7 + 2 N_A + 14 tau_k and tau_k = ||B|| / ||A||
+    (2-norms; notation set before eq. (fb)). kappa(A) and ||A|| are the
+    user's estimates. Reading: B is the block's B_{k,sbar}, since s_k is not
+    known when s~_k is chosen; B_{k,s_k} is a submatrix of it, so tau_k can
+    only be overestimated. For the monomial basis ||B|| = 1 either way."""
+    tau = float(np.linalg.norm(B, 2)) / norm_A
+    Nk = 7 + 2 * A.N_A + 14 * tau
+    return 6.0 * Nk * kappa_A
+
+
 def adaptive_block(G, sbar: int, bp: BasisParams, eps_star: float, c: float, nrows: int,
-                   check_in_loop: bool = True, max_steps: int | None = None, trace: bool = False):
+                   check_in_loop: bool = True, max_steps: int | None = None, trace: bool = False,
+                   c_step: float | None = None, s_max: int | None = None):
     """One block of Alg. 4 after G is formed: "Determine s~_k" to the end of the inner loop.
 
     ||r_{m+1}|| = sqrt(G[i_s, i_s]) (column i_s is r since rho_0 = 1);
-    threshold = eps* / (c eps ||r_{m+1}||); s~ by eq. (condy); gamma =
+    threshold = eps* / (c_{k,s_max} eps ||r_{m+1}||); s~ by eq. (condy); gamma =
     sqrt(kappa(G_{k,s~})); G and B restricted to Y_{k,s~}; inner steps with the
-    eq. (check) break test. Returns (block record, InnerResult, column indices
-    of Y_{k,s~} inside Y_{k,sbar}).
+    eq. (check) break test, which after step j uses c_{k,j}. With c_step None,
+    c_{k,j} = c for every j; else c_{k,j} = c_step * j. Returns (block record,
+    InnerResult, column indices of Y_{k,s~} inside Y_{k,sbar}).
     """
+    c_condy = c if c_step is None else c_step * s_max
+
+    def c_check(j):
+        return c if c_step is None else c_step * j
+
     i_s = sbar + 1
     rnorm = math.sqrt(max(float(G[i_s, i_s]), 0.0))
-    threshold = eps_star / (c * EPS * rnorm) if rnorm > 0 else math.inf
+    threshold = eps_star / (c_condy * EPS * rnorm) if rnorm > 0 else math.inf
     stilde, kappas = choose_s(G, sbar, threshold, nrows)
     idx = submatrix_index(sbar, stilde)
     kap, gclamped = kappa_gram(G[np.ix_(idx, idx)], nrows)
@@ -384,7 +403,7 @@ def adaptive_block(G, sbar: int, bp: BasisParams, eps_star: float, c: float, nro
         if rn <= eps_star:
             return "converged"
         if check_in_loop:
-            tj = eps_star / (c * EPS * rn) if rn > 0 else math.inf
+            tj = eps_star / (c_check(j) * EPS * rn) if rn > 0 else math.inf
             checks.append((j, tj))
             if gamma_est >= tj:
                 return "break"
@@ -392,7 +411,7 @@ def adaptive_block(G, sbar: int, bp: BasisParams, eps_star: float, c: float, nro
 
     inner = coordinate_steps(Gt, Bt, stilde, nsteps, stop_test, trace=trace)
     blk = dict(sbar=sbar, stilde=stilde, s_k=inner.steps, threshold=threshold, rnorm=rnorm, kappas=kappas,
-               gamma=gamma_est, gamma_clamped=gclamped, checks=checks, stop=inner.stop)
+               gamma=gamma_est, gamma_clamped=gclamped, checks=checks, stop=inner.stop, c_condy=c_condy)
     if trace:
         blk.update(G=Gt, B=Bt, inner=inner.trace)
     return blk, inner, idx
@@ -532,8 +551,11 @@ def fixed_sstep_cg(A: Operator, b, x1, s: int, bp: BasisParams, **kw):
 def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, f: int | None = None,
                       eps_target: float = 1e-10, c: float = 1.0, basis: str = "monomial",
                       lam=None, newton_warmup: int | None = None, check_in_loop: bool = True,
-                      max_iters: int = 10000, trace: bool = False):
+                      max_iters: int = 10000, trace: bool = False, c_formula=None):
     """Adaptive s-step CG, Alg. 4.
+
+    c_{k,j}: the constant c, or with c_formula = (kappa(A), ||A||) the bound's
+    own c_{k,j} = 6 N_k j kappa(A) (see formula_c_step).
 
     Per block k:
       sbar_k = s0 for k = 0, else min(s_{k-1} + f, s_max);
@@ -593,8 +615,11 @@ def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, 
         sbar = s0 if k == 0 else min(s_prev + f, s_max)
         Y = matrix_powers(A, p, r, sbar, bp)
         G = gram(Y)
+        c_step = None
+        if c_formula is not None:
+            c_step = formula_c_step(A, basis_change_matrix(sbar, bp), c_formula[0], c_formula[1])
         blk, inner, idx = adaptive_block(G, sbar, bp, eps_star, c, A.n, check_in_loop, max_iters - m,
-                                         trace=trace)
+                                         trace=trace, c_step=c_step, s_max=s_max)
         if inner.steps == 0:
             return SolveResult(x, r, p, hist, alphas, betas, m, False, "breakdown", blocks)
         Yt = Y[:, idx]

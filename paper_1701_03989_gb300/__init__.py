@@ -33,6 +33,7 @@ ASCG_MONOMIAL, ASCG_NEWTON, ASCG_CHEBYSHEV = 0, 1, 2
 ASCG_STOP_DONE, ASCG_STOP_CONVERGED, ASCG_STOP_BREAK, ASCG_STOP_BREAKDOWN, ASCG_STOP_MAXITER = 0, 1, 2, 3, 4
 ASCG_FLAG_TIMING = 1
 ASCG_FLAG_GRAM_FP64 = 2
+ASCG_FLAG_C_FORMULA = 4
 
 
 class ascg_block_info(C.Structure):
@@ -51,7 +52,8 @@ class ascg_options(C.Structure):
                 ("block_hist", C.POINTER(ascg_block_info)), ("block_hist_cap", C.c_int), ("pad3_", C.c_int),
                 ("alpha_hist", C.POINTER(C.c_double)), ("beta_hist", C.POINTER(C.c_double)),
                 ("coef_hist_cap", C.c_int), ("pad4_", C.c_int),
-                ("s_seq", C.POINTER(C.c_int)), ("s_seq_len", C.c_int), ("pad5_", C.c_int)]
+                ("s_seq", C.POINTER(C.c_int)), ("s_seq_len", C.c_int), ("pad5_", C.c_int),
+                ("kappa_A", C.c_double), ("norm_A", C.c_double)]
 
 
 class ascg_result(C.Structure):
@@ -315,11 +317,12 @@ _BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CH
 def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
-                 gram_fp64=False, s_seq=None) -> ascg_options:
+                 gram_fp64=False, s_seq=None, c_formula=None) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
-    the options object keeps its own copy alive."""
+    the options object keeps its own copy alive. c_formula = (kappa(A), ||A||):
+    c_{k,j} = 6 N_k j kappa(A) instead of the constant c."""
     o = ascg_options_default()
     o.method = _METHODS[method] if isinstance(method, str) else int(method)
     o.basis = _BASES[basis] if isinstance(basis, str) else int(basis)
@@ -334,6 +337,9 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
     o.max_iters = int(max_iters)
     o.check_in_loop = 1 if check_in_loop else 0
     o.flags = (ASCG_FLAG_TIMING if timing else 0) | (ASCG_FLAG_GRAM_FP64 if gram_fp64 else 0)
+    if c_formula is not None:
+        o.flags |= ASCG_FLAG_C_FORMULA
+        o.kappa_A, o.norm_A = float(c_formula[0]), float(c_formula[1])
     if res_hist is not None:
         o.res_hist = res_hist.ctypes.data_as(C.POINTER(C.c_double))
         o.res_hist_cap = len(res_hist)

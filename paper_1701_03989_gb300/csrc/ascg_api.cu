@@ -117,6 +117,7 @@ struct Workspace {
 struct ascg_op_s {
   int64_t n = 0, nnz = 0;
   int device = 0;
+  int max_row_nnz = 0;  // N_A (Sec. 3.1): most nonzeros in a row of A
   // A in sliced ELL form (SpMV, residual, classical CG)
   int64_t* a_ptr = nullptr;
   int32_t* a_col = nullptr;
@@ -259,6 +260,57 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
   return ASCG_OK;
 }
 
+// ||B_{k,s}||_2 of eq. (AVVB) for the basis coefficients th, sg, gm. B is
+// block diagonal; its R block is a submatrix of its P block (the same
+// coefficients, one column fewer), so the norm is that of the P block:
+// (s+1) x (s+1), column j < s holding sg[j-1] above, th[j] on and gm[j]
+// below the diagonal. The largest eigenvalue of P^T P comes from cyclic
+// Jacobi rotations (a standard dense symmetric eigenvalue method).
+double norm_B(int s, const double* th, const double* sg, const double* gm) {
+  const int m = s + 1;
+  double Bp[kMaxS + 1][kMaxS + 1] = {};
+  for (int j = 0; j < s; ++j) {
+    Bp[j][j] = th[j];
+    Bp[j + 1][j] = gm[j];
+    if (j >= 1) Bp[j - 1][j] = sg[j - 1];
+  }
+  double M[kMaxS + 1][kMaxS + 1];
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) {
+      double acc = 0.0;
+      for (int r = 0; r < m; ++r) acc += Bp[r][a] * Bp[r][b];
+      M[a][b] = acc;
+    }
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int a = 0; a < m; ++a) {
+      diag += M[a][a] * M[a][a];
+      for (int b = a + 1; b < m; ++b) off += M[a][b] * M[a][b];
+    }
+    if (off <= 1e-32 * diag || off == 0.0) break;
+    for (int p = 0; p < m; ++p)
+      for (int q = p + 1; q < m; ++q) {
+        if (M[p][q] == 0.0) continue;
+        const double theta = (M[q][q] - M[p][p]) / (2.0 * M[p][q]);
+        const double t = (theta >= 0.0 ? 1.0 : -1.0) / (std::fabs(theta) + std::sqrt(theta * theta + 1.0));
+        const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+        for (int r = 0; r < m; ++r) {  // M <- M J
+          const double mp = M[r][p], mq = M[r][q];
+          M[r][p] = c * mp - sn * mq;
+          M[r][q] = sn * mp + c * mq;
+        }
+        for (int r = 0; r < m; ++r) {  // M <- J^T M
+          const double mp = M[p][r], mq = M[q][r];
+          M[p][r] = c * mp - sn * mq;
+          M[q][r] = sn * mp + c * mq;
+        }
+      }
+  }
+  double lmax = 0.0;
+  for (int a = 0; a < m; ++a) lmax = std::max(lmax, M[a][a]);
+  return std::sqrt(lmax);
+}
+
 ascg_status check_opts(const ascg_options& o) {
   if (o.method != ASCG_CLASSICAL && o.method != ASCG_FIXED_S && o.method != ASCG_ADAPTIVE &&
       o.method != ASCG_VARIABLE_S)
@@ -280,6 +332,11 @@ ascg_status check_opts(const ascg_options& o) {
       const int nw = o.newton_warmup > 0 ? o.newton_warmup : 2 * o.s_max;
       if (nw < o.s_max || nw > 32) return fail(ASCG_ERR_INVALID, "newton_warmup must be in s_max..32");
     }
+  }
+  if (o.flags & ASCG_FLAG_C_FORMULA) {
+    if (o.method != ASCG_ADAPTIVE) return fail(ASCG_ERR_INVALID, "ASCG_FLAG_C_FORMULA needs ASCG_ADAPTIVE");
+    if (!(o.kappa_A >= 1.0 && std::isfinite(o.kappa_A)) || !(o.norm_A > 0.0 && std::isfinite(o.norm_A)))
+      return fail(ASCG_ERR_INVALID, "ASCG_FLAG_C_FORMULA needs finite kappa_A >= 1 and norm_A > 0");
   }
   if (!(o.eps_target >= 0.0)) return fail(ASCG_ERR_INVALID, "eps_target must be >= 0");
   if (!(o.c > 0.0)) return fail(ASCG_ERR_INVALID, "c must be > 0");
@@ -478,6 +535,11 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     }
     const DevSplit Asplit = op->split();
     const double sqrt_n = std::sqrt((double)n);
+    // ASCG_FLAG_C_FORMULA: c_{k,j} = 6 N_k j kappa(A), N_k = 7 + 2 N_A + 14 ||B_k|| / ||A||
+    double c_step_of[kMaxS + 1] = {};
+    if (o.flags & ASCG_FLAG_C_FORMULA)
+      for (int sb = 1; sb <= o.s_max; ++sb)
+        c_step_of[sb] = 6.0 * (7.0 + 2.0 * op->max_row_nnz + 14.0 * norm_B(sb, th, sg, gm) / o.norm_A) * o.kappa_A;
     int k = 0, s_prev = 0;
     int nb_info = 0;
     while (!done) {
@@ -493,6 +555,8 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       hb.k = k;
       hb.eps_star = eps_star;
       hb.c = o.c;
+      hb.c_step = c_step_of[sbar];
+      hb.c_smax = o.s_max;
       hb.bnorm = bnorm;
       hb.sqrt_n = sqrt_n;
       hb.active = 1;
@@ -693,6 +757,7 @@ ascg_status ascg_op_create_csr(int64_t n, int64_t nnz, const int64_t* rowptr, co
   ascg_op op = new ascg_op_s();
   op->n = n;
   op->nnz = nnz;
+  for (int64_t i = 0; i < n; ++i) op->max_row_nnz = std::max<int>(op->max_row_nnz, (int)(hrp[i + 1] - hrp[i]));
   op->o_len = (int64_t)ho.val.size();
   cudaGetDevice(&op->device);
   ascg_status st = upload(&op->a_ptr, ha.ptr);
@@ -789,6 +854,8 @@ ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const*
   const ascg_options o = *opts;
   ASCG_TRY(check_opts(o));
   if (o.method == ASCG_CLASSICAL) return fail(ASCG_ERR_INVALID, "batched solves run an s-step method");
+  if (o.flags & ASCG_FLAG_C_FORMULA)
+    return fail(ASCG_ERR_INVALID, "ASCG_FLAG_C_FORMULA needs one system's kappa(A) and ||A||: use ascg_solve");
   if (o.basis != ASCG_MONOMIAL) return fail(ASCG_ERR_INVALID, "batched solves use the monomial basis");
   if ((o.res_hist && o.res_hist_cap < 1) || (o.block_hist && o.block_hist_cap < 1))
     return fail(ASCG_ERR_INVALID, "history capacities must be >= 1");

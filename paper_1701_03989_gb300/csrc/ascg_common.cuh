@@ -198,7 +198,10 @@ struct BlockState {
   int m;               // iterations before this block
   int k;               // block index
   double eps_star;
-  double c;
+  double c;            // c_{k,j} when c_step is 0
+  double c_step;       // > 0: c_{k,j} = c_step * j, and c_step * c_smax in eq. (condy)
+  int c_smax;
+  int pad2_;
   double bnorm;
   double sqrt_n;       // sqrt(length of the basis vectors)
   int active;          // batched solves: 0 skips this system's block (single solves: 1)

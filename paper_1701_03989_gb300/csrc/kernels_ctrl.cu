@@ -406,7 +406,9 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
   if (t == 0) {
     // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
     const double rnorm = sqrt(fmax(Gs[1][1], 0.0));
-    const double T = rnorm > 0.0 ? eps_star / (cc * kEps * rnorm) : CUDART_INF;
+    // eq. (condy) takes c_{k,s_max}
+    const double c_condy = st->c_step > 0.0 ? st->c_step * st->c_smax : cc;
+    const double T = rnorm > 0.0 ? eps_star / (c_condy * kEps * rnorm) : CUDART_INF;
     int stilde;
     double gamma;
     if (adaptive) {
@@ -503,8 +505,9 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
         if (rnn <= eps_star) {
           fl = ASCG_STOP_CONVERGED;
         } else if (adaptive && st->check_in_loop) {
-          // eq. (check): break when gamma >= eps* / (c eps (r'^T G r')^(1/2))
-          const double Tj = rnn > 0.0 ? eps_star / (cc * kEps * rnn) : CUDART_INF;
+          // eq. (check): break when gamma >= eps* / (c_{k,j} eps (r'^T G r')^(1/2))
+          const double cj = st->c_step > 0.0 ? st->c_step * j : cc;
+          const double Tj = rnn > 0.0 ? eps_star / (cj * kEps * rnn) : CUDART_INF;
           if (gamma >= Tj) fl = ASCG_STOP_BREAK;
         }
         s_beta = beta;

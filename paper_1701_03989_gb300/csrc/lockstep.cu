@@ -857,6 +857,8 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   const ascg_options o = *opts;
   LS_TRY(check_options(o));
   if (o.method == ASCG_CLASSICAL) return lfail(ASCG_ERR_INVALID, "the server runs an s-step method");
+  if (o.flags & ASCG_FLAG_C_FORMULA)
+    return lfail(ASCG_ERR_INVALID, "ASCG_FLAG_C_FORMULA needs one system's kappa(A) and ||A||: use ascg_solve");
   if (o.basis != ASCG_MONOMIAL) return lfail(ASCG_ERR_INVALID, "the server uses the monomial basis");
   if (o.res_hist || o.block_hist || o.alpha_hist || o.beta_hist)
     return lfail(ASCG_ERR_INVALID, "the server keeps no histories: the history buffers must be NULL");

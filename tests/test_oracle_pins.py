@@ -437,3 +437,70 @@ def test_paper_observations_sec5():
     loose = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-6)
     late = [bl["s_k"] for bl in loose.blocks[:-1] if bl["m"] >= 8]
     assert late and all(s == 8 for s in late)
+
+
+def _laplacian_1d(n):
+    """tridiag(-1/2, 1, -1/2): the 1D Dirichlet Laplacian, equilibrated (Sec. 5).
+    Eigenvalues 1 - cos(k pi/(n+1)), k = 1..n (closed form)."""
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        for j, v in ((i - 1, -0.5), (i, 1.0), (i + 1, -0.5)):
+            if 0 <= j < n:
+                rows.append(i)
+                cols.append(j)
+                vals.append(v)
+    rowptr = np.zeros(n + 1, np.int64)
+    np.add.at(rowptr, np.array(rows) + 1, 1)
+    return O.Operator(n, np.cumsum(rowptr), np.array(cols), np.array(vals))
+
+
+def test_c_formula_mode_closed_form():
+    """c_{k,j} = 6 N_k j kappa(A) (eq. (fb)) on the 1D Laplacian, where every
+    ingredient is known without the oracle: N_A = 3 nonzeros per row, ||B|| = 1
+    for the monomial basis (a shift), kappa(A) = cot^2(pi/(2(n+1))) and
+    ||A|| = 1 + cos(pi/(n+1)). Each block's eq. (condy) threshold must use
+    c_{k,s_max}, and the run must still reach its target."""
+    n, s_max, eps = 40, 6, 1e-10
+    A = _laplacian_1d(n)
+    th = math.pi / (n + 1)
+    kA = 1.0 / math.tan(th / 2) ** 2
+    nA = 1.0 + math.cos(th)
+    assert A.N_A == 3
+    b = W.rhs_uniform(n, np.random.default_rng(0))
+    res = O.adaptive_sstep_cg(A, b, np.zeros(n), s_max=s_max, eps_target=eps, c_formula=(kA, nA))
+    c_step = 6 * (7 + 2 * 3 + 14 * 1.0 / nA) * kA
+    for blk in res.blocks:
+        assert blk["c_condy"] == pytest.approx(c_step * s_max, rel=1e-13)
+        assert blk["threshold"] == pytest.approx(eps / (c_step * s_max * EPS * blk["rnorm"]), rel=1e-13)
+    assert res.converged and res.true_res <= 2 * eps
+
+
+def test_c_formula_is_more_conservative():
+    """The bound's c_{k,j} is far above 1, so eq. (condy) admits smaller bases
+    than with c = 1 (Sec. 3.2: the bound overestimates the error); the method
+    still converges, to the requested accuracy."""
+    c = W.poisson2d_32()
+    A = O.Operator.from_csr(c["A"])
+    lo, hi = W.poisson_eig_bounds(2, 32)
+    base = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-10)
+    form = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-10, c_formula=(hi / lo, hi))
+    assert form.converged and form.true_res <= 2e-10
+    mean = lambda r: r.iters / len(r.blocks)
+    assert mean(form) < mean(base)
+    assert len(form.blocks) > len(base.blocks)
+
+
+def test_c_formula_uses_the_bases_B_norm():
+    """tau_k = ||B_{k,sbar}|| / ||A||: for a Chebyshev basis ||B|| is not 1, and
+    the recorded c_{k,s_max} follows the 2-norm of the block's B."""
+    c = W.poisson2d_32()
+    A = O.Operator.from_csr(c["A"])
+    lo, hi = W.poisson_eig_bounds(2, 32)
+    res = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-10, basis="chebyshev", lam=(lo, hi),
+                              c_formula=(hi / lo, hi))
+    bp = O.chebyshev_params(lo, hi, 8)
+    for blk in res.blocks:
+        nb = np.linalg.svd(O.basis_change_matrix(blk["sbar"], bp), compute_uv=False)[0]
+        assert nb != pytest.approx(1.0, rel=1e-3)
+        assert blk["c_condy"] == pytest.approx(6 * (7 + 2 * A.N_A + 14 * nb / hi) * (hi / lo) * 8, rel=1e-12)
+    assert res.converged

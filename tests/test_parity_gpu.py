@@ -395,6 +395,13 @@ SOLVES = [
     ("banded_3001", dict(method="adaptive", basis="chebyshev", s_max=10), 1e-12),
     # the same Chebyshev solve with the Gram matrix formed by FP64 FMAs instead of the tensor cores
     ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_fp64=True), 1e-12),
+    # c_{k,j} = 6 N_k j kappa(A) (eq. (fb)) from closed-form kappa(A) and ||A|| of the Poisson matrices
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8,
+                          c_formula=(W.poisson_eig_bounds(2, 32)[1] / W.poisson_eig_bounds(2, 32)[0],
+                                     W.poisson_eig_bounds(2, 32)[1])), 1e-10),
+    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16,
+                          c_formula=(W.poisson_eig_bounds(3, 23)[1] / W.poisson_eig_bounds(3, 23)[0],
+                                     W.poisson_eig_bounds(3, 23)[1])), 1e-12),
     # Alg. 3: block sizes from a given sequence (Fibonacci-type growth capped at s_max)
     ("poisson2d_32", dict(method="variable", basis="monomial", s_max=5, s_seq=W.fibonacci_s_sequence(5, 8)), 1e-10),
     ("poisson3d_23", dict(method="variable", basis="chebyshev", s_max=12, s_seq=W.fibonacci_s_sequence(12, 9)), 1e-12),
@@ -441,7 +448,8 @@ def run_oracle(A, b, x1, kw, eps, lam, max_iters=20000):
         return O.variable_sstep_cg(Ao, b, x1, kw["s_seq"], bp, eps_target=eps, max_iters=max_iters)
     return O.adaptive_sstep_cg(Ao, b, x1, s_max=s, s0=kw.get("s0"), f=kw.get("f"), eps_target=eps,
                                basis=kw.get("basis", "monomial"), lam=lam, newton_warmup=kw.get("newton_warmup"),
-                               check_in_loop=kw.get("check_in_loop", True), max_iters=max_iters)
+                               check_in_loop=kw.get("check_in_loop", True), max_iters=max_iters,
+                               c_formula=kw.get("c_formula"))
 
 
 @pytest.mark.parametrize("name,kw,eps", SOLVES)
@@ -460,6 +468,8 @@ def test_solve_parity(env, name, kw, eps):
     if kw["method"] == "adaptive":
         exempt, bad = parity.compare_block_sequences(blocks, orc.blocks, A.n, orc.res_hist, eps)
         assert not bad, bad
+        if "c_formula" in kw:  # the eq. (condy) threshold with c_{k,s_max}: ||B||, N_A and the factors
+            assert abs(blocks[0]["threshold"] - orc.blocks[0]["threshold"]) <= 1e-12 * orc.blocks[0]["threshold"]
     else:
         exempt = None
         if kw["method"] in ("fixed", "variable"):
@@ -482,6 +492,29 @@ def test_solve_parity(env, name, kw, eps):
     NA = int(np.max(np.diff(A.rowptr)))
     tol = 2 * gamma_n(NA + 1) * np.linalg.norm(absAx) / np.linalg.norm(b)
     assert abs(O.norm2(O.residual(Ao, b, x)) / np.linalg.norm(b) - res.rel_res_true) <= tol
+
+
+def test_c_formula_argument_checks(env):
+    """ASCG_FLAG_C_FORMULA needs ASCG_ADAPTIVE, kappa_A >= 1 and norm_A > 0, and is
+    refused by batched solves and the server (one system's estimates only)."""
+    P, torch = env
+    A = MATRICES["poisson2d_32"]()
+    op = make_op(P, A)
+    b = dev(torch, W.rhs_uniform(A.n, np.random.default_rng(0)))
+    x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    for kw in (dict(method="fixed", c_formula=(10.0, 2.0)), dict(c_formula=(0.5, 2.0)),
+               dict(c_formula=(10.0, 0.0)), dict(c_formula=(float("inf"), 2.0))):
+        with pytest.raises(P.AscgError) as e:
+            P.ascg_solve(op, b, x, P.make_options(**kw))
+        assert e.value.status == P.ASCG_ERR_INVALID
+    o = P.make_options(c_formula=(10.0, 2.0))
+    with pytest.raises(P.AscgError) as e:
+        P.ascg_solve_batch([op], [b], [x], o)
+    assert e.value.status == P.ASCG_ERR_INVALID
+    with pytest.raises(P.AscgError) as e:
+        P.ascg_server_create(o, 1 << 20, 2)
+    assert e.value.status == P.ASCG_ERR_INVALID
+    P.ascg_op_destroy(op)
 
 
 def test_solve_is_deterministic(env):
