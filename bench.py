@@ -143,11 +143,18 @@ class ClockSampler:
 # roofline traffic from a committed ncu summary (bytes per launch), if current
 # ---------------------------------------------------------------------------
 
-def kernel_source_hash(name="kernels_mpk.cu"):
-    h = hashlib.sha256()
-    with open(os.path.join(ROOT, "paper_1701_03989_gb300", "csrc", name), "rb") as f:
-        h.update(f.read())
-    return h.hexdigest()[:16]
+MPK_KERNEL_TEXT = ("template <bool EMAX>", "// col_emax[c] = max over the warp entries")
+
+
+def kernel_source_hash(name="kernels_mpk.cu", span=MPK_KERNEL_TEXT, text=None):
+    """Hash of a kernel's own source text (from span[0] up to span[1]), so that
+    edits elsewhere in the file keep a committed ncu figure valid."""
+    if text is None:
+        with open(os.path.join(ROOT, "paper_1701_03989_gb300", "csrc", name)) as f:
+            text = f.read()
+    a = text.index(span[0])
+    b = text.index(span[1], a)
+    return hashlib.sha256(text[a:b].encode()).hexdigest()[:16]
 
 
 def committed_traffic():

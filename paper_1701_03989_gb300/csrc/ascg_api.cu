@@ -65,6 +65,7 @@ struct Workspace {
   int wcols = 0;
   int64_t ldY = 0;
   double* Y = nullptr;
+  double* Y2 = nullptr;     // second basis buffer: blocks alternate, so x += Y x' can run late
   double* b = nullptr;      // for host-buffer solves
   double* x = nullptr;      // for host-buffer solves
   double* q = nullptr;      // classical CG: A p; also a scratch vector
@@ -94,9 +95,11 @@ struct Workspace {
   double* h_scal = nullptr;
   cudaEvent_t ev[8] = {};
   bool events = false;
+  cudaStream_t side = nullptr;  // x += Y x' of the previous block
+  cudaEvent_t ev_gram = nullptr, ev_x[2] = {};
 
   void release() {
-    dev_free(Y); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(emax_part); dev_free(counter);
+    dev_free(Y); dev_free(Y2); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(emax_part); dev_free(counter);
     dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
     dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
     dev_free(dtils); dev_free(oscaled[0]); dev_free(oscaled[1]);
@@ -105,9 +108,16 @@ struct Workspace {
     if (h_cgs) cudaFreeHost(h_cgs);
     if (h_scal) cudaFreeHost(h_scal);
     h_bst = nullptr; h_cgs = nullptr; h_scal = nullptr;
-    if (events)
+    if (events) {
       for (auto& e : ev) cudaEventDestroy(e);
+      cudaEventDestroy(ev_gram);
+      for (auto& e : ev_x) cudaEventDestroy(e);
+      if (side) cudaStreamDestroy(side);
+    }
     events = false;
+    side = nullptr;
+    ev_gram = nullptr;
+    ev_x[0] = ev_x[1] = nullptr;
     n = 0; wcols = 0; ldY = 0; partials_cap = 0; res_cap = 0; ab_cap = 0; emax_ld = 0;
   }
 };
@@ -208,7 +218,7 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     ASCG_TRY(dev_alloc(&w.counter, 1));
     ASCG_CUDA(cudaMemset(w.counter, 0, sizeof(unsigned)));
     ASCG_TRY(dev_alloc(&w.G, kMaxW * kMaxW));
-    ASCG_TRY(dev_alloc(&w.coords, 3 * kMaxW));
+    ASCG_TRY(dev_alloc(&w.coords, 6 * kMaxW));  // two blocks' x', r', p'  
     ASCG_TRY(dev_alloc(&w.params, 3 * kMaxS));
     ASCG_TRY(dev_alloc(&w.scal, 4));
     ASCG_TRY(dev_alloc(&w.shifts, 32));
@@ -218,13 +228,17 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     ASCG_CUDA(cudaMallocHost((void**)&w.h_cgs, sizeof(CGState)));
     ASCG_CUDA(cudaMallocHost((void**)&w.h_scal, 4 * sizeof(double)));
     for (auto& e : w.ev) ASCG_CUDA(cudaEventCreate(&e));
+    ASCG_CUDA(cudaEventCreateWithFlags(&w.ev_gram, cudaEventDisableTiming));
+    for (auto& e : w.ev_x) ASCG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ASCG_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
     w.events = true;
   }
   if (w.n != n || w.wcols < wcols) {
-    dev_free(w.Y); dev_free(w.q);
+    dev_free(w.Y); dev_free(w.Y2); dev_free(w.q);
     const int64_t ld = round_up(n, 32);  // 256-byte aligned columns
     const int cols = wcols > 2 ? wcols : 2;
     ASCG_TRY(dev_alloc(&w.Y, (size_t)(cols * ld)));
+    if (wcols > 2) ASCG_TRY(dev_alloc(&w.Y2, (size_t)(cols * ld)));
     ASCG_TRY(dev_alloc(&w.q, (size_t)n));
     w.ldY = ld;
     w.wcols = cols;
@@ -542,9 +556,21 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         c_step_of[sb] = 6.0 * (7.0 + 2.0 * op->max_row_nnz + 14.0 * norm_B(sb, th, sg, gm) / o.norm_A) * o.kappa_A;
     int k = 0, s_prev = 0;
     int nb_info = 0;
+    // Blocks alternate between two basis buffers. Block k recovers r and p
+    // into the other buffer; its x += Y x' waits until block k+1's Gram is
+    // done and then runs on the side stream beside block k+1's condition
+    // estimates and controller, which leave most SMs idle. Block k+1's own
+    // recovery overwrites columns 0 and 1 of block k's buffer, so it waits for
+    // that update first.
+    double* Ybuf[2] = {w.Y, w.Y2};
+    double* cbuf[2] = {w.coords, w.coords + 3 * kMaxW};
+    int cur = 0, pend = -1, pend_w = 0;
+    bool x_out[2] = {false, false};  // an x update reading buffer b is queued on the side stream
+    const int x_ctas = std::max(1, gram_grid() - 24);
     while (!done) {
       const int sbar = block_sbar(o, k, s_prev);
       const int wb = 2 * sbar + 1;
+      double* const Yc = Ybuf[cur];
       BlockState& hb = *w.h_bst;
       std::memset(&hb, 0, sizeof(hb));
       hb.sbar = sbar;
@@ -564,9 +590,9 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
       // the steps also record each basis column's largest exponent for the tensor-core Gram
-      const bool tc_gram = !gram_fp64 && gram_tc_applies(wb) && gram_tc_aligned(w.Y, w.ldY);
+      const bool tc_gram = !gram_fp64 && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY);
       for (int j = 0; j < sbar; ++j) {
-        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], w.Y, w.ldY, j, 1, j < sbar - 1,
+        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], Yc, w.ldY, j, 1, j < sbar - 1,
                                         tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
       }
       if (tc_gram) {
@@ -577,19 +603,36 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
       // Gram: the block's one grid-wide reduction
       int nparts = 0;
-      ASCG_CUDA(launch_gram_any(n, wb, w.Y, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
+      ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
       ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
       res->launches += 2;
       res->grid_reductions += 1;
+      if (pend >= 0) {  // the previous block's x += Y x', beside this block's kappa and controller
+        ASCG_CUDA(cudaEventRecord(w.ev_gram, s));
+        ASCG_CUDA(cudaStreamWaitEvent(w.side, w.ev_gram, 0));
+        ASCG_CUDA(launch_recover_x(n, pend_w, Ybuf[pend], w.ldY, cbuf[pend], x, x_ctas, w.side));
+        ASCG_CUDA(cudaEventRecord(w.ev_x[pend], w.side));
+        x_out[pend] = true;
+        pend = -1;
+        res->launches += 1;
+      }
       if (o.method == ASCG_ADAPTIVE) {
         ASCG_CUDA(launch_kappa(w.G, w.bst, sbar, s));
         res->launches += 1;
       }
-      ASCG_CUDA(launch_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, w.coords, nullptr,
+      ASCG_CUDA(launch_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, cbuf[cur], nullptr,
                             w.res_hist, w.res_cap, w.ab_hist, w.ab_cap, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[4], s));
-      ASCG_CUDA(launch_recover(n, wb, w.Y, w.ldY, w.coords, x, r, p, s));
+      // r and p into columns 1 and 0 of the other buffer, once the update that reads it is done
+      if (x_out[cur ^ 1]) {
+        ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[cur ^ 1], 0));
+        x_out[cur ^ 1] = false;
+      }
+      ASCG_CUDA(launch_recover_rp(n, wb, Yc, w.ldY, cbuf[cur], Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s));
+      pend = cur;
+      pend_w = wb;
+      cur ^= 1;
       res->launches += 2;
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[5], s));
       ASCG_CUDA(cudaMemcpyAsync(w.h_bst, w.bst, sizeof(BlockState), cudaMemcpyDeviceToHost, s));
@@ -613,8 +656,9 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         const double nchains = 2.0 * sbar - 1.0;
         res->mpk_flops += nchains * 2.0 * (double)op->nnz;
         res->mpk_bytes += (double)sbar * (12.0 * op->nnz + 4.0 * (n + 1)) + nchains * 16.0 * n + 8.0 * n;
-        res->recover_flops += 3.0 * 2.0 * wb * (double)n;
-        res->recover_bytes += 8.0 * (wb + 1) * (double)n + 24.0 * n;
+        // the timed part: r = Y r', p = Y p' (x += Y x' runs later, on the side stream)
+        res->recover_flops += 2.0 * 2.0 * wb * (double)n;
+        res->recover_bytes += 8.0 * wb * (double)n + 16.0 * n;
       }
       const BlockState& out = *w.h_bst;
       if (o.block_hist && nb_info < o.block_hist_cap) {
@@ -646,6 +690,13 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         final_status = ASCG_NOT_CONVERGED;
         break;
       }
+    }
+    // the last block's x update, after any still on the side stream
+    for (int bq = 0; bq < 2; ++bq)
+      if (x_out[bq]) ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[bq], 0));
+    if (pend >= 0) {
+      ASCG_CUDA(launch_recover_x(n, pend_w, Ybuf[pend], w.ldY, cbuf[pend], x, x_ctas, s));
+      res->launches += 1;
     }
     res->blocks = k;
   }

@@ -187,6 +187,14 @@ cudaError_t launch_recover_items(int W, const SysDesc* descs, const RowItem* ite
 // Recovery (eq. coords).
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
                            double* x, double* r, double* p, cudaStream_t s);
+// The recovery in two parts with the same bits: r = Y r', p = Y p' (r and p
+// must not alias Y), and x += Y x' on `ctas` CTAs of which no two share an SM
+// and none shares an SM with a kernel holding more than ~6 KB of shared
+// memory.
+cudaError_t launch_recover_rp(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* r,
+                              double* p, cudaStream_t s);
+cudaError_t launch_recover_x(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
+                             int ctas, cudaStream_t s);
 
 // Block controller state shared by the controller kernels and the host driver.
 struct BlockState {

@@ -174,6 +174,73 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
   return cudaGetLastError();
 }
 
+// The recovery split in two, with the same sums as recover_kernel (so the
+// same bits): r = Y r', p = Y p' (written to another buffer: Y stays intact),
+// and x += Y x', which the next block does not need and which the solver
+// runs later, beside the next block's condition estimates and controller.
+template <int W>
+__global__ void __launch_bounds__(256) recover_rp_kernel(int64_t n, const double* __restrict__ Y, int64_t ldY,
+                                                         const double* __restrict__ coords, double* __restrict__ r,
+                                                         double* __restrict__ p) {
+  __shared__ double cr[W], cp[W];
+  if (threadIdx.x < W) {
+    cr[threadIdx.x] = coords[W + threadIdx.x];
+    cp[threadIdx.x] = coords[2 * W + threadIdx.x];
+  }
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double y[W];
+#pragma unroll
+    for (int c = 0; c < W; ++c) y[c] = Y[(int64_t)c * ldY + i];
+    double sr = 0.0, sp = 0.0;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      sr = fma(y[c], cr[c], sr);
+      sp = fma(y[c], cp[c], sp);
+    }
+    r[i] = sr;
+    p[i] = sp;
+  }
+}
+
+// x += Y x'. One CTA per SM at most, each reserving most of the SM's shared
+// memory (kXReserve of the 228 KB): the CTAs then never share an SM with the
+// condition estimate and controller CTAs (about 11 KB each), whose FP64 issue
+// they would otherwise slow.
+constexpr int kXThreads = 512;
+constexpr int kXReserve = 220 * 1024;
+template <int W>
+__global__ void __launch_bounds__(kXThreads, 1) recover_x_kernel(int64_t n, const double* __restrict__ Y,
+                                                                 int64_t ldY, const double* __restrict__ coords,
+                                                                 double* __restrict__ x) {
+  __shared__ double cx[W];
+  if (threadIdx.x < W) cx[threadIdx.x] = coords[threadIdx.x];
+  __syncthreads();
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double sx = 0.0;
+#pragma unroll
+    for (int c = 0; c < W; ++c) sx = fma(Y[(int64_t)c * ldY + i], cx[c], sx);
+    x[i] = x[i] + sx;
+  }
+}
+
+template <int W>
+cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
+                            double* p, int x_ctas, cudaStream_t s) {
+  if (x) {
+    static bool attr = false;  // once per process: the attribute is per function
+    if (!attr) {
+      cudaError_t e = cudaFuncSetAttribute(recover_x_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXReserve);
+      if (e != cudaSuccess) return e;
+      attr = true;
+    }
+    recover_x_kernel<W><<<x_ctas, kXThreads, kXReserve, s>>>(n, Y, ldY, coords, x);
+  } else {
+    recover_rp_kernel<W><<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, Y, ldY, coords, r, p);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
@@ -200,6 +267,35 @@ cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, doubl
                                cudaStream_t s) {
   shift_scale_kernel<<<grid_for(n, 256, 152 * 16), 256, 0, s>>>(src, n, theta, scale, dst);
   return cudaGetLastError();
+}
+
+cudaError_t launch_recover_rp(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* r,
+                              double* p, cudaStream_t s) {
+  switch (w) {
+#define ASCG_RS(W) \
+  case W:          \
+    return recover_split_w<W>(n, Y, ldY, coords, nullptr, r, p, 0, s);
+    ASCG_RS(1) ASCG_RS(3) ASCG_RS(5) ASCG_RS(7) ASCG_RS(9) ASCG_RS(11) ASCG_RS(13) ASCG_RS(15) ASCG_RS(17)
+    ASCG_RS(19) ASCG_RS(21) ASCG_RS(23) ASCG_RS(25) ASCG_RS(27) ASCG_RS(29) ASCG_RS(31) ASCG_RS(33)
+#undef ASCG_RS
+    default:
+      return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_recover_x(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
+                             int ctas, cudaStream_t s) {
+  if (ctas < 1) ctas = 1;
+  switch (w) {
+#define ASCG_RX(W) \
+  case W:          \
+    return recover_split_w<W>(n, Y, ldY, coords, x, nullptr, nullptr, ctas, s);
+    ASCG_RX(1) ASCG_RX(3) ASCG_RX(5) ASCG_RX(7) ASCG_RX(9) ASCG_RX(11) ASCG_RX(13) ASCG_RX(15) ASCG_RX(17)
+    ASCG_RX(19) ASCG_RX(21) ASCG_RX(23) ASCG_RX(25) ASCG_RX(27) ASCG_RX(29) ASCG_RX(31) ASCG_RX(33)
+#undef ASCG_RX
+    default:
+      return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
