@@ -79,6 +79,7 @@ struct Workspace {
   double* coords = nullptr; // 3 kMaxW
   double* params = nullptr; // theta, sigma, gamma: 3 kMaxS
   double* scal = nullptr;   // 4 scalars
+  double* spec = nullptr;   // speculative coordinate steps of a block (kSpecDoubles)
   double* shifts = nullptr; // 32
   BlockState* bst = nullptr;
   CGState* cgs = nullptr;
@@ -100,7 +101,7 @@ struct Workspace {
 
   void release() {
     dev_free(Y); dev_free(Y2); dev_free(b); dev_free(x); dev_free(q); dev_free(partials); dev_free(expp); dev_free(emax_part); dev_free(counter);
-    dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(shifts);
+    dev_free(G); dev_free(coords); dev_free(params); dev_free(scal); dev_free(spec); dev_free(shifts);
     dev_free(bst); dev_free(cgs); dev_free(res_hist); dev_free(ab_hist);
     dev_free(dtils); dev_free(oscaled[0]); dev_free(oscaled[1]);
     steps_ready = false;
@@ -215,8 +216,9 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
   Workspace& w = op->ws;
   const int64_t n = op->n;
   if (!w.counter) {
-    ASCG_TRY(dev_alloc(&w.counter, 1));
-    ASCG_CUDA(cudaMemset(w.counter, 0, sizeof(unsigned)));
+    ASCG_TRY(dev_alloc(&w.counter, 2));  // [0]: reductions, [1]: the block controller's ticket
+    ASCG_CUDA(cudaMemset(w.counter, 0, 2 * sizeof(unsigned)));
+    ASCG_TRY(dev_alloc(&w.spec, kSpecDoubles));
     ASCG_TRY(dev_alloc(&w.G, kMaxW * kMaxW));
     ASCG_TRY(dev_alloc(&w.coords, 6 * kMaxW));  // two blocks' x', r', p'  
     ASCG_TRY(dev_alloc(&w.params, 3 * kMaxS));
@@ -617,12 +619,9 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         pend = -1;
         res->launches += 1;
       }
-      if (o.method == ASCG_ADAPTIVE) {
-        ASCG_CUDA(launch_kappa(w.G, w.bst, sbar, s));
-        res->launches += 1;
-      }
-      ASCG_CUDA(launch_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, cbuf[cur], nullptr,
-                            w.res_hist, w.res_cap, w.ab_hist, w.ab_cap, s));
+      ASCG_CUDA(launch_block_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, sbar,
+                                  o.method == ASCG_ADAPTIVE, cbuf[cur], nullptr, w.res_hist, w.res_cap, w.ab_hist,
+                                  w.ab_cap, w.spec, w.counter + 1, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[4], s));
       // r and p into columns 1 and 0 of the other buffer, once the update that reads it is done
       if (x_out[cur ^ 1]) {
@@ -986,12 +985,18 @@ ascg_status ascg_block_step(int sbar, const double* G, int method, const double*
   BlockState* bst = nullptr;
   double* dpar = nullptr;
   double* dhist = nullptr;
+  double* dspec = nullptr;
+  unsigned* dcnt = nullptr;
   ASCG_TRY(dev_alloc(&bst, 1));
   ascg_status st = dev_alloc(&dpar, 3 * kMaxS);
   if (st == ASCG_OK) st = dev_alloc(&dhist, 3 * kMaxS);
+  if (st == ASCG_OK) st = dev_alloc(&dspec, kSpecDoubles);
+  if (st == ASCG_OK) st = dev_alloc(&dcnt, 1);
   if (st != ASCG_OK) {
     cudaFree(bst);
     cudaFree(dpar);
+    cudaFree(dhist);
+    cudaFree(dspec);
     return st;
   }
   BlockState hb;
@@ -1014,15 +1019,18 @@ ascg_status ascg_block_step(int sbar, const double* G, int method, const double*
   double hh[3 * kMaxS];
   cudaError_t e = cudaMemcpyAsync(bst, &hb, sizeof(hb), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(dpar, hp, sizeof(hp), cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && method == ASCG_ADAPTIVE) e = launch_kappa(G, bst, sbar, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(dcnt, 0, sizeof(unsigned), s);
   if (e == cudaSuccess)
-    e = launch_ctrl(G, dpar, dpar + kMaxS, dpar + 2 * kMaxS, bst, coords, dhist, nullptr, 0, nullptr, 0, s);
+    e = launch_block_ctrl(G, dpar, dpar + kMaxS, dpar + 2 * kMaxS, bst, sbar, method == ASCG_ADAPTIVE, coords, dhist,
+                          nullptr, 0, nullptr, 0, dspec, dcnt, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, bst, sizeof(hb), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(hh, dhist, sizeof(hh), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(bst);
   cudaFree(dpar);
   cudaFree(dhist);
+  cudaFree(dspec);
+  cudaFree(dcnt);
   if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("block step: ") + cudaGetErrorString(e));
   std::memset(info, 0, sizeof(*info));
   info->sbar = sbar;

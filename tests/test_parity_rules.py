@@ -108,5 +108,21 @@ def test_final_residual_rule_after_a_flipped_stop():
     assert parity.final_residual_ok(4.7e-9, 9.87e-9, 1e-8, 3)
     assert parity.final_residual_ok(1.9e-8, 9.87e-9, 1e-8, 3)
     assert not parity.final_residual_ok(2.1e-8, 9.87e-9, 1e-8, 3)
-    assert not parity.final_residual_ok(4.7e-9, 9.87e-9, 1e-8, None)
+    assert parity.final_residual_ok(4.7e-9, 9.87e-9, 1e-8, None)      # 2x lower, under the target
+    assert not parity.final_residual_ok(4.7e-9, 9.87e-9, 1e-9, None)  # 2x lower, above the target
+    assert not parity.final_residual_ok(2.1e-8, 1.0e-8, 1e-7, None)   # more than 2x higher
     assert math.isfinite(parity.kappa_uncertainty(10.0, 5, 100))
+
+
+def test_stop_decision_after_finite_termination_is_exempt(run):
+    """A stop decision after n iterations (finite termination) is on rounding
+    noise: exempt whatever the residuals."""
+    A, r = run
+    g = as_gpu(r.blocks)
+    last = r.blocks[-1]
+    extra = dict(g[-1], m=last["m"] + last["s_k"])
+    i = last["m"] + last["s_k"]
+    exempt, bad = parity.compare_block_sequences(g + [extra], r.blocks, i, r.res_hist, r.res_hist[i] * 100)
+    assert exempt == len(r.blocks) - 1 and not bad
+    exempt, bad = parity.compare_block_sequences(g + [extra], r.blocks, i + 1, r.res_hist, r.res_hist[i] * 100)
+    assert bad
