@@ -68,6 +68,8 @@ def parse():
                     help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--moment-gram", action="store_true",
+                    help="batch and served workloads: G from the monomial basis' moments (a variant)")
     ap.add_argument("--requests", type=int, default=200, help="served workload: requests in the open-loop run")
     ap.add_argument("--load", type=float, default=0.7, help="served workload: arrival rate / saturation throughput")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served workload: device-memory budget (GB)")
@@ -452,7 +454,8 @@ def batch_arm(args):
     bs = [torch.from_numpy(s["b"]).cuda() for s in systems]
     xs = [torch.zeros(s["A"].n, dtype=torch.float64, device="cuda") for s in systems]
     eps = [s["eps"] for s in systems]
-    o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=20000)
+    o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=20000,
+                       moment_gram=args.moment_gram)
     stream = torch.cuda.current_stream()
 
     def batch_once():
@@ -499,7 +502,8 @@ def batch_arm(args):
                                "in [1e3, 2e5], eps* 1e-8 or 1e-12 at p = 1/2, seed 1004; adaptive monomial s_max=10",
                    "rows_total": int(sum(s["A"].n for s in systems)),
                    "nnz_total": int(sum(s["A"].nnz for s in systems)),
-                   "gram": "FP64 FMAs (per-system row items)"},
+                   "gram": ("Hankel moments of the monomial basis, FP64 (a variant)" if args.moment_gram else
+                            "FP64 FMAs (per-system row items; tensor cores for lanes of 2^18 rows or more)")},
         "status_ok": ok, "iters_per_batch": iters, "lockstep_blocks": res[0].launches,
         "worst_true_res_over_target": worst_true,
         "sequential": {"ms": seq_ms, "iters": seq_iters, "iters_per_s": seq_iters / (seq_ms * 1e-3),
@@ -556,7 +560,8 @@ def serve_arm(args):
 
     bs = [rhs(i) for i in range(nreq)]
     xs = [torch.zeros_like(b) for b in bs]
-    o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=60000)
+    o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=60000,
+                       moment_gram=args.moment_gram)
     stream = torch.cuda.current_stream()
     budget = int(args.budget_gb * 1e9)
     slots = 256
@@ -662,7 +667,8 @@ def serve_arm(args):
                                "8..64; n at log-uniform quantiles of [1e4, 4e6]), eps* uniform over {1e-6, 1e-8, "
                                "1e-10, 1e-12}, Poisson arrivals, seed 1005; adaptive monomial s_max=10; budget "
                                "%.0f GB, %d slots" % (nreq, args.budget_gb, slots),
-                   "pool_n": nop, "pool_nnz": [int(p["A"].nnz) for p in pool]},
+                   "pool_n": nop, "pool_nnz": [int(p["A"].nnz) for p in pool],
+                   "gram": "Hankel moments (a variant)" if args.moment_gram else "Y^T Y"},
         "p50_ms": _pct(lat_ms, 50), "p99_ms": _pct(lat_ms, 99), "max_ms": max(lat_ms),
         "throughput_rps": nreq / wall, "arrival_rps": lam, "saturation_rps": mu,
         "saturation_wall_s": sat_wall, "saturation_peak_running": sat_peak, "peak_running": peak,

@@ -124,6 +124,9 @@ typedef struct {
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
 #define ASCG_FLAG_GRAM_FP64 2 /* Gram by FP64 FMAs on the CUDA cores for every w,
                                  instead of the tensor-core kernel (w >= 9)      */
+#define ASCG_FLAG_MOMENT_GRAM 8 /* monomial basis only: G from 6 sbar moments
+                                 (ascg_gram_moments) instead of Y^T Y; a
+                                 variant that rounds differently            */
 #define ASCG_FLAG_C_FORMULA 4 /* c_{k,j} = 6 N_k j kappa(A), the factor of the gap
                                  bound eq. (fb), instead of the constant c:
                                  N_k = 7 + 2 N_A + 14 ||B_k|| / ||A||, N_A = most
@@ -262,6 +265,21 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
  * (m = CTAs + 7); a column holding Inf or NaN gives NaN in its row and
  * column. */
 ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
+
+/* Gram matrix of a monomial basis from its moments (a variant of ascg_gram;
+ * the paper forms Y^T Y). With A symmetric and rho_j(z) = z^j, the blocks
+ * P^T P, P^T R and R^T R of G depend on i + j only (Hankel matrices), so
+ * 6s dot products replace w(w+1)/2, w = 2s + 1. Y: device, interleaved
+ * columns as above (P_j = column 2j, R_j = column 2j+1), n rows, ldY >= n;
+ * 1 <= s <= 16. The moments are
+ *   mu_pp[k] = P_floor(k/2)^T P_ceil(k/2),  k = 0 .. 2s
+ *   mu_pr[k] = P_ceil(k/2)^T R_floor(k/2),  k = 0 .. 2s-1
+ *   mu_rr[k] = R_floor(k/2)^T R_ceil(k/2),  k = 0 .. 2s-2
+ * each an FP64 dot product summed in a fixed order (error <= gamma_n
+ * |y_a|^T |y_b|), and G[2i+a][2j+b] = mu_(ab)[i+j] (device, row-major w x w).
+ * In exact arithmetic this is Y^T Y; in floating point it differs from it by
+ * the rounding of the basis recurrence. Synchronises the stream. */
+ascg_status ascg_gram_moments(int64_t n, int s, const double* Y, int64_t ldY, double* G, void* cuda_stream);
 
 /* One block controller step on a given Gram matrix (Alg. 4 from "Determine
  * s~_k" to the end of the inner loop). G: device double[(2 sbar+1)^2],

@@ -212,6 +212,50 @@ def gram(Y):
     return Y.T @ Y
 
 
+def gram_moments(Y, s: int):
+    """G_{k,s} of the monomial basis from 6s dot products (a variant of the Gram
+    step; the paper forms Y^T Y).
+
+    With A symmetric and rho_j(z) = z^j, P_i^T P_j = p^T A^(i+j) p,
+    P_i^T R_j = p^T A^(i+j) r and R_i^T R_j = r^T A^(i+j) r depend on i + j
+    only: each block of G is a Hankel matrix of moments. Reading (one pair of
+    columns per moment, the most balanced one):
+      mu_pp[k] = <P_floor(k/2), P_ceil(k/2)>,  k = 0 .. 2s
+      mu_pr[k] = <P_ceil(k/2), R_floor(k/2)>,  k = 0 .. 2s-1
+      mu_rr[k] = <R_floor(k/2), R_ceil(k/2)>,  k = 0 .. 2s-2
+    In exact arithmetic this is Y^T Y. In floating point it differs from it by
+    the rounding of the basis recurrence, which the other products of the
+    same moment would see differently. Y: P columns then R columns (s+1, s).
+    """
+    P = Y[:, : s + 1]
+    R = Y[:, s + 1:]
+    mpp = [P[:, k // 2] @ P[:, (k + 1) // 2] for k in range(2 * s + 1)]
+    mpr = [P[:, (k + 1) // 2] @ R[:, k // 2] for k in range(2 * s)]
+    mrr = [R[:, k // 2] @ R[:, (k + 1) // 2] for k in range(2 * s - 1)]
+    w = 2 * s + 1
+    G = np.zeros((w, w), dtype=np.asarray(Y).dtype)
+    for i in range(s + 1):
+        for j in range(s + 1):
+            G[i, j] = mpp[i + j]
+        for j in range(s):
+            G[i, s + 1 + j] = mpr[i + j]
+            G[s + 1 + j, i] = mpr[i + j]
+    for i in range(s):
+        for j in range(s):
+            G[s + 1 + i, s + 1 + j] = mrr[i + j]
+    return G
+
+
+def gram_of(Y, s: int, gram_mode: str):
+    """G by gram_mode: "plain" (Y^T Y, the paper's step) or "moments" (gram_moments;
+    monomial basis only)."""
+    if gram_mode == "plain":
+        return gram(Y)
+    if gram_mode == "moments":
+        return gram_moments(Y, s)
+    raise ValueError(gram_mode)
+
+
 def basis_change_matrix(s: int, bp: BasisParams, dtype=np.float64):
     """B_{k,s} with A * Yunder_{k,s} = Y_{k,s} * B_{k,s}, eq. (AVVB).
 
@@ -493,7 +537,7 @@ def classical_cg(A: Operator, b, x1, eps_target: float = 1e-10, max_iters: int =
 
 
 def variable_sstep_cg(A: Operator, b, x1, s_seq, bp: BasisParams, eps_target: float = 1e-10,
-                      max_iters: int = 10000, exact: bool = False):
+                      max_iters: int = 10000, exact: bool = False, gram_mode: str = "plain"):
     """Variable s-step CG, Alg. 3 (Alg. 2 when every s_k is the same).
 
     Block k: Y_{k,s_k} (eq. cg-krylovbasis), G = Y^T Y, B (eq. AVVB), s_k
@@ -515,7 +559,7 @@ def variable_sstep_cg(A: Operator, b, x1, s_seq, bp: BasisParams, eps_target: fl
     while not converged and m < max_iters:
         s = int(s_seq[min(k, len(s_seq) - 1)])
         Y = matrix_powers(A, p, r, s, bp)
-        G = gram(Y)
+        G = gram_of(Y, s, gram_mode)
         B = basis_change_matrix(s, bp, dtype=G.dtype)
         nsteps = min(s, max_iters - m)
 
@@ -551,11 +595,12 @@ def fixed_sstep_cg(A: Operator, b, x1, s: int, bp: BasisParams, **kw):
 def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, f: int | None = None,
                       eps_target: float = 1e-10, c: float = 1.0, basis: str = "monomial",
                       lam=None, newton_warmup: int | None = None, check_in_loop: bool = True,
-                      max_iters: int = 10000, trace: bool = False, c_formula=None):
+                      max_iters: int = 10000, trace: bool = False, c_formula=None, gram_mode: str = "plain"):
     """Adaptive s-step CG, Alg. 4.
 
     c_{k,j}: the constant c, or with c_formula = (kappa(A), ||A||) the bound's
-    own c_{k,j} = 6 N_k j kappa(A) (see formula_c_step).
+    own c_{k,j} = 6 N_k j kappa(A) (see formula_c_step). gram_mode "moments"
+    forms G from moments (gram_moments; monomial basis only).
 
     Per block k:
       sbar_k = s0 for k = 0, else min(s_{k-1} + f, s_max);
@@ -576,6 +621,8 @@ def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, 
     Lanczos tridiagonal, Leja-ordered). The warm-up iterations count toward
     the iteration total and the residual history.
     """
+    if gram_mode == "moments" and basis != "monomial":
+        raise ValueError("the moment Gram needs the monomial basis")
     s0 = s_max if s0 is None else s0
     f = s_max if f is None else f
     x = x1.copy()
@@ -614,7 +661,7 @@ def adaptive_sstep_cg(A: Operator, b, x1, *, s_max: int, s0: int | None = None, 
     while not converged and m < max_iters:
         sbar = s0 if k == 0 else min(s_prev + f, s_max)
         Y = matrix_powers(A, p, r, sbar, bp)
-        G = gram(Y)
+        G = gram_of(Y, sbar, gram_mode)
         c_step = None
         if c_formula is not None:
             c_step = formula_c_step(A, basis_change_matrix(sbar, bp), c_formula[0], c_formula[1])

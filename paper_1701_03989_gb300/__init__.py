@@ -34,6 +34,7 @@ ASCG_STOP_DONE, ASCG_STOP_CONVERGED, ASCG_STOP_BREAK, ASCG_STOP_BREAKDOWN, ASCG_
 ASCG_FLAG_TIMING = 1
 ASCG_FLAG_GRAM_FP64 = 2
 ASCG_FLAG_C_FORMULA = 4
+ASCG_FLAG_MOMENT_GRAM = 8
 
 
 class ascg_block_info(C.Structure):
@@ -99,6 +100,7 @@ def _load():
         "ascg_matrix_powers": (C.c_int, [P, C.c_int, P, P, P, P, I64, P]),
         "ascg_gram": (C.c_int, [I64, C.c_int, P, I64, P, P]),
         "ascg_gram_noalloc": (C.c_int, [I64, C.c_int, P, I64, P, P]),
+        "ascg_gram_moments": (C.c_int, [I64, C.c_int, P, I64, P, P]),
         "ascg_block_step": (C.c_int, [C.c_int, P, C.c_int, P, P, P, I64, C.c_double, C.c_double, C.c_int,
                                       C.c_int, C.c_double, P, C.POINTER(ascg_block_info), P, P]),
         "ascg_recover": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
@@ -272,6 +274,11 @@ def ascg_gram(n, w, Y, ldY, G, stream=None):
     _check(_lib.ascg_gram(int(n), int(w), _ptr(Y), int(ldY), _ptr(G), _stream(stream)), "ascg_gram")
 
 
+def ascg_gram_moments(n, s, Y, ldY, G, stream=None):
+    """Gram matrix of a monomial basis of size s from its 6s moments (see include/ascg.h)."""
+    _check(_lib.ascg_gram_moments(int(n), int(s), _ptr(Y), int(ldY), _ptr(G), _stream(stream)), "ascg_gram_moments")
+
+
 def ascg_gram_noalloc(n, w, Y, ldY, G, stream=None):
     """As ascg_gram, but with no device allocation (static scratch; see include/ascg.h).
     Enqueues only: synchronise the stream before reading G."""
@@ -317,12 +324,13 @@ _BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CH
 def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
-                 gram_fp64=False, s_seq=None, c_formula=None) -> ascg_options:
+                 gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
     the options object keeps its own copy alive. c_formula = (kappa(A), ||A||):
-    c_{k,j} = 6 N_k j kappa(A) instead of the constant c."""
+    c_{k,j} = 6 N_k j kappa(A) instead of the constant c. moment_gram: G from
+    the monomial basis' moments (ascg_gram_moments)."""
     o = ascg_options_default()
     o.method = _METHODS[method] if isinstance(method, str) else int(method)
     o.basis = _BASES[basis] if isinstance(basis, str) else int(basis)
@@ -337,6 +345,8 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
     o.max_iters = int(max_iters)
     o.check_in_loop = 1 if check_in_loop else 0
     o.flags = (ASCG_FLAG_TIMING if timing else 0) | (ASCG_FLAG_GRAM_FP64 if gram_fp64 else 0)
+    if moment_gram:
+        o.flags |= ASCG_FLAG_MOMENT_GRAM
     if c_formula is not None:
         o.flags |= ASCG_FLAG_C_FORMULA
         o.kappa_A, o.norm_A = float(c_formula[0]), float(c_formula[1])
@@ -364,7 +374,7 @@ def block_infos(count: int):
 
 
 EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
-            "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc",
+            "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc", "ascg_gram_moments",
             "ascg_block_step", "ascg_recover",
             "ascg_newton_shifts", "ascg_server_create", "ascg_server_submit", "ascg_server_step",
             "ascg_server_info", "ascg_server_destroy", "ascg_last_error"]

@@ -349,6 +349,8 @@ ascg_status check_opts(const ascg_options& o) {
       if (nw < o.s_max || nw > 32) return fail(ASCG_ERR_INVALID, "newton_warmup must be in s_max..32");
     }
   }
+  if ((o.flags & ASCG_FLAG_MOMENT_GRAM) && (o.method == ASCG_CLASSICAL || o.basis != ASCG_MONOMIAL))
+    return fail(ASCG_ERR_INVALID, "ASCG_FLAG_MOMENT_GRAM needs an s-step method with the monomial basis");
   if (o.flags & ASCG_FLAG_C_FORMULA) {
     if (o.method != ASCG_ADAPTIVE) return fail(ASCG_ERR_INVALID, "ASCG_FLAG_C_FORMULA needs ASCG_ADAPTIVE");
     if (!(o.kappa_A >= 1.0 && std::isfinite(o.kappa_A)) || !(o.norm_A > 0.0 && std::isfinite(o.norm_A)))
@@ -466,6 +468,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
   ASCG_TRY(ensure(op, wmax, o.max_iters + 2));
   const bool timing = (o.flags & ASCG_FLAG_TIMING) != 0;
   const bool gram_fp64 = (o.flags & ASCG_FLAG_GRAM_FP64) != 0;
+  const bool gram_mom = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
   if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
 
   // ||b||, r_1 = b - A x_1, p_1 = r_1 (Alg. 1/4 first line). p = column 0 and
@@ -592,7 +595,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
       // the steps also record each basis column's largest exponent for the tensor-core Gram
-      const bool tc_gram = !gram_fp64 && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY);
+      const bool tc_gram = !gram_fp64 && !gram_mom && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY);
       for (int j = 0; j < sbar; ++j) {
         ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], Yc, w.ldY, j, 1, j < sbar - 1,
                                         tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
@@ -605,9 +608,15 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
       // Gram: the block's one grid-wide reduction
       int nparts = 0;
-      ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
+      if (gram_mom)
+        ASCG_CUDA(launch_gram_moments(n, wb, Yc, w.ldY, w.partials, &nparts, s));
+      else
+        ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
-      ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
+      if (gram_mom)
+        ASCG_CUDA(launch_gram_moment_finalize(wb, w.partials, nparts, w.G, s));
+      else
+        ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
       res->launches += 2;
       res->grid_reductions += 1;
       if (pend >= 0) {  // the previous block's x += Y x', beside this block's kappa and controller
@@ -648,7 +657,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         res->t_recover_ms += d2;
         res->gram_launches += 1;
         res->mpk_launches += sbar;
-        res->gram_flops += 2.0 * (double)wb * (wb + 1) / 2.0 * (double)n;
+        res->gram_flops += 2.0 * (gram_mom ? 3.0 * (wb - 1) : (double)wb * (wb + 1) / 2.0) * (double)n;
         res->gram_bytes += 8.0 * (double)wb * (double)n;
         // per step and chain: the SpMV's 2 nnz flops (the folded shift, scale and
         // sigma terms are not counted)
@@ -969,6 +978,22 @@ ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G,
   cudaFree(partials);
   cudaFree(expp);
   if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("gram: ") + cudaGetErrorString(e));
+  return ASCG_OK;
+}
+
+ascg_status ascg_gram_moments(int64_t n, int s_, const double* Y, int64_t ldY, double* G, void* cuda_stream) {
+  g_err.clear();
+  if (!Y || !G || n < 1 || s_ < 1 || s_ > ASCG_MAX_S || ldY < n) return fail(ASCG_ERR_INVALID, "bad argument");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  double* partials = nullptr;
+  ASCG_TRY(dev_alloc(&partials, (size_t)gram_grid() * kMomSlots));
+  int parts = 0;
+  const int w = 2 * s_ + 1;
+  cudaError_t e = launch_gram_moments(n, w, Y, ldY, partials, &parts, s);
+  if (e == cudaSuccess) e = launch_gram_moment_finalize(w, partials, parts, G, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(partials);
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("gram moments: ") + cudaGetErrorString(e));
   return ASCG_OK;
 }
 

@@ -128,10 +128,22 @@ constexpr int kGramItemRowsMin = 1024;
 // changes no result. partials: nitems x W(W+1)/2.
 struct SysDesc;
 cudaError_t launch_gram_items(int W, const SysDesc* descs, const GramItem* items, int nitems, const int* sys_w,
-                              double* partials, int pair_groups, cudaStream_t s);
+                              double* partials, int pair_groups, bool moments, cudaStream_t s);
 // G of each active system q (w_q = sys_w[q] x w_q, stride w_q) at G + q * g_stride.
 cudaError_t launch_gram_items_finalize(int W, const double* partials, const int* sys_item0, const int* sys_nitems,
-                                       const int* sys_w, int count, double* G, int64_t g_stride, cudaStream_t s);
+                                       const int* sys_w, int count, double* G, int64_t g_stride, bool moments,
+                                       cudaStream_t s);
+// Hankel-moment Gram of the monomial basis (interleaved columns P_j = 2j,
+// R_j = 2j + 1, w = 2s + 1 odd >= 3): the 6s dot products
+// mu_pp[k] = <P_floor(k/2), P_ceil(k/2)>, mu_pr[k] = <P_ceil(k/2), R_floor(k/2)>,
+// mu_rr[k] = <R_floor(k/2), R_ceil(k/2)>, each in the FP64 kernel's fixed
+// order, and G = [mu_(ab)[i + j]]. Partials: kMomSlots per CTA (or per item
+// with moments = true above); slot = family * kMomFam + k.
+constexpr int kMomFam = 2 * kMaxS + 1;
+constexpr int kMomSlots = 3 * kMomFam;
+cudaError_t launch_gram_moments(int64_t n, int w, const double* Y, int64_t ldY, double* partials, int* nparts,
+                                cudaStream_t s);
+cudaError_t launch_gram_moment_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
 
 // Tensor-core Gram (split-bf16 operands, exact integer sums) for
 // kGramTcMinW <= w <= kMaxW. Below that width the FP64 kernel is faster.

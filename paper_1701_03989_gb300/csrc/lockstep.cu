@@ -208,7 +208,8 @@ class Lockstep {
     rcap_ = rcap;
     abcap_ = abcap;
     wcols_ = 2 * o.s_max + 1;
-    npw_ = wcols_ * (wcols_ + 1) / 2;
+    moments_ = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
+    npw_ = (int)partials_per_item(o.s_max, moments_);
     LS_TRY(dalloc(&d_desc_, lanes));
     LS_TRY(dalloc(&d_bst_, lanes));
     LS_TRY(dalloc(&d_G_, (size_t)lanes * kGStride));
@@ -252,10 +253,15 @@ class Lockstep {
   static size_t basis_bytes(int s_max, int64_t n) {
     return (size_t)(2 * s_max + 1) * round_up(n, kSlice) * sizeof(double);
   }
+  // Gram partials per item: the pairs' upper triangle, or the moment slots.
+  static int64_t partials_per_item(int s_max, bool moments) {
+    const int64_t w = 2 * s_max + 1, np = w * (w + 1) / 2;
+    return moments ? std::max<int64_t>(kMomSlots, np) : np;
+  }
   // Device bytes one system holds while it runs: its basis and its Gram partials.
-  static size_t footprint(int s_max, int64_t n) {
-    const int64_t w = 2 * s_max + 1;
-    return Arena::rounded(basis_bytes(s_max, n)) + (size_t)gram_items_of(n) * (w * (w + 1) / 2) * sizeof(double);
+  static size_t footprint(int s_max, int64_t n, bool moments) {
+    return Arena::rounded(basis_bytes(s_max, n)) +
+           (size_t)gram_items_of(n) * partials_per_item(s_max, moments) * sizeof(double);
   }
 
   // Validates a system and fills its descriptor (all but Y).
@@ -381,7 +387,7 @@ class Lockstep {
       const int w = 2 * sbar + 1;
       h_steps[q] = sbar;
       h_w[q] = w;
-      const bool tc = L.d.n >= kTcLaneRows && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
+      const bool tc = !moments_ && L.d.n >= kTcLaneRows && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
       h_wi[q] = tc ? 0 : w;
       if (tc) tc_lanes_.push_back(q);
       max_sbar = std::max(max_sbar, sbar);
@@ -403,8 +409,8 @@ class Lockstep {
     if ((int)tc_lanes_.size() < count_active()) {
       // pair groups: enough CTAs to cover the SMs twice
       const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
-      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, s_));
-      LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, s_));
+      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
+      LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
       nl += 2;
     }
     for (int q : tc_lanes_) {  // one lane at a time: the lanes share the partials buffer in stream order
@@ -643,6 +649,7 @@ class Lockstep {
   cudaStream_t s_ = nullptr;
   int lanes_ = 0, nused_ = 0, hi_ = 0, rcap_ = 0, abcap_ = 0, wcols_ = 0, npw_ = 0;
   bool dirty_ = true;
+  bool moments_ = false;  // Hankel-moment Gram (monomial basis)
   int64_t super_blocks_ = 0, launches_ = 0;
   std::vector<LaneSys> lane_;
   std::vector<char> used_;
@@ -880,7 +887,8 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   // least 1024 rows against (2 s_max + 1) 1024 doubles of basis: set them
   // aside out of the budget for the most rows the budget can hold, plus one
   // item per system.
-  const int64_t wcols = 2 * o.s_max + 1, npw = wcols * (wcols + 1) / 2;
+  const int64_t wcols = 2 * o.s_max + 1;
+  const int64_t npw = Lockstep::partials_per_item(o.s_max, (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0);
   const int64_t rows_max = hbm_budget / (wcols * (int64_t)sizeof(double));
   const int64_t gitems = rows_max / kGramItemRowsMin + max_systems;
   const int64_t part_bytes = gitems * npw * (int64_t)sizeof(double);
@@ -920,7 +928,8 @@ ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, dou
   if (!srv) return lfail(ASCG_ERR_INVALID, "srv is NULL");
   LaneSys L;
   LS_TRY(Lockstep::prepare(srv->o.s_max, op, b, x, eps_target, tag, &L));
-  if (Lockstep::footprint(srv->o.s_max, L.d.n) > srv->budget || Arena::rounded(L.bytes) > srv->arena.size())
+  if (Lockstep::footprint(srv->o.s_max, L.d.n, (srv->o.flags & ASCG_FLAG_MOMENT_GRAM) != 0) > srv->budget ||
+      Arena::rounded(L.bytes) > srv->arena.size())
     return lfail(ASCG_ERR_INVALID, "the system needs more device memory than the server's budget");
   LS_CUDA(cudaEventCreateWithFlags(&L.ready, cudaEventDisableTiming));
   cudaError_t e = cudaEventRecord(L.ready, srv->user);

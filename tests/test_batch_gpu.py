@@ -36,7 +36,8 @@ def make_op(P, A):
                                 np.ascontiguousarray(A.colind, np.int32), np.ascontiguousarray(A.val, np.float64), 0)
 
 
-def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None, s_seq=None):
+def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None, s_seq=None,
+              moment_gram=False):
     count = len(systems)
     ops = [make_op(P, s["A"]) for s in systems]
     bs = [dev(torch, s["b"]) for s in systems]
@@ -44,7 +45,7 @@ def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", 
     res_hist = np.zeros((count, max_iters + 2))
     infos = P.block_infos(count * (max_iters + 2))
     o = P.make_options(method=method, basis="monomial", s_max=s_max, eps_target=1e-10, max_iters=max_iters,
-                       res_hist=res_hist.reshape(-1), block_hist=infos, s_seq=s_seq)
+                       res_hist=res_hist.reshape(-1), block_hist=infos, s_seq=s_seq, moment_gram=moment_gram)
     o.res_hist_cap = max_iters + 2
     o.block_hist_cap = max_iters + 2
     epsv = [s["eps"] for s in systems] if eps is None else eps
@@ -116,6 +117,30 @@ def test_batch_tensor_gram_lane(env):
         assert np.all(np.abs(g["hist"][:nwin] - ho) <= tau), s["name"]
         assert parity.final_residual_ok(g["res"].rel_res_true, orc.true_res, s["eps"], exempt), (
             s["name"], g["res"].rel_res_true, orc.true_res)
+
+
+def test_batch_moment_gram(env):
+    """Batched solves with the Hankel-moment Gram (monomial basis): parity with the
+    oracle's moment-Gram solves, and each system bitwise the same alone."""
+    P, torch = env
+    systems = small_batch(seed=15, count=5)
+    out, st = run_batch(P, torch, systems, moment_gram=True)
+    assert st == P.ASCG_OK
+    for s, g in zip(systems, out):
+        orc = O.adaptive_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], s_max=S_MAX, eps_target=s["eps"],
+                                  basis="monomial", max_iters=CAP, gram_mode="moments")
+        assert g["res"].status == P.ASCG_OK and orc.converged, s["name"]
+        exempt, bad = parity.compare_block_sequences(g["blocks"], orc.blocks, s["A"].n, orc.res_hist, s["eps"])
+        assert not bad, (s["name"], bad)
+        nwin = min(parity.history_window(g["blocks"], orc.blocks, exempt, iters=20), len(g["hist"]),
+                   len(orc.res_hist), s["A"].n)
+        ho = np.asarray(orc.res_hist[:nwin])
+        tau = parity.history_tolerance(orc.blocks, ho, nwin)
+        assert np.all(np.abs(g["hist"][:nwin] - ho) <= tau), s["name"]
+        assert parity.final_residual_ok(g["res"].rel_res_true, orc.true_res, s["eps"], exempt), (
+            s["name"], g["res"].rel_res_true, orc.true_res)
+    alone, _ = run_batch(P, torch, [systems[2]], moment_gram=True)
+    assert np.array_equal(alone[0]["x"], out[2]["x"]) and np.array_equal(alone[0]["hist"], out[2]["hist"])
 
 
 def test_batch_result_same_alone_and_in_mix(env):

@@ -504,3 +504,41 @@ def test_c_formula_uses_the_bases_B_norm():
         assert nb != pytest.approx(1.0, rel=1e-3)
         assert blk["c_condy"] == pytest.approx(6 * (7 + 2 * A.N_A + 14 * nb / hi) * (hi / lo) * 8, rel=1e-12)
     assert res.converged
+
+
+# ---------------------------------------------------------------------------
+# the Hankel-moment Gram of the monomial basis (a variant of the Gram step)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 2, 4])
+def test_gram_moments_equal_gram_in_exact_arithmetic(s):
+    """With A symmetric the monomial basis' Gram blocks are Hankel matrices of
+    moments: in exact (rational) arithmetic the moment form equals Y^T Y
+    entry for entry, for every block (P^T P, P^T R, R^T R)."""
+    D = small_int_spd(7, 5)
+    A = O.Operator.from_dense(frac_array(D))
+    p = frac_array(np.array([1, -2, 0, 3, 1, -1, 2]))
+    r = frac_array(np.array([2, 1, -1, 0, 1, 3, -2]))
+    Y = O.matrix_powers(A, p, r, s, O.monomial_params(s, one=Fraction(1), zero=Fraction(0)))
+    Gm = O.gram_moments(Y, s)
+    Gp = O.gram(Y)
+    assert all(Gm[i, j] == Gp[i, j] for i in range(2 * s + 1) for j in range(2 * s + 1))
+    if s == 1:  # every entry is its own moment: the forms agree for any Y
+        return
+    # from s = 2 on, a basis that is not a Krylov sequence of one symmetric matrix breaks the identity
+    Y2 = Y.copy()
+    Y2[0, 1] += Fraction(1)
+    G2 = O.gram_moments(Y2, s)
+    assert any(G2[i, j] != O.gram(Y2)[i, j] for i in range(2 * s + 1) for j in range(2 * s + 1))
+
+
+def test_gram_moments_solve_reaches_target():
+    """Adaptive s-step CG with the moment Gram converges to the requested
+    accuracy on the 2D Poisson problem, with an s_k sequence close to the
+    plain Gram's."""
+    c = W.poisson2d_32()
+    A = O.Operator.from_csr(c["A"])
+    plain = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-10)
+    mom = O.adaptive_sstep_cg(A, c["b"], c["x1"], s_max=8, eps_target=1e-10, gram_mode="moments")
+    assert mom.converged and mom.true_res <= 2e-10
+    assert abs(mom.iters - plain.iters) <= plain.iters // 10

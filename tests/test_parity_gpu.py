@@ -160,6 +160,48 @@ def test_gram_parity(env, n, w):
     assert torch.equal(G, G2)   # fixed reduction order: bitwise reproducible
 
 
+@pytest.mark.parametrize("s", [1, 3, 8, 16])
+@pytest.mark.parametrize("name", ["poisson2d_32", "poisson3d_23"])
+def test_gram_moments_parity(env, name, s):
+    """The Hankel-moment Gram of a monomial basis (ascg_gram_moments) against the
+    oracle's gram_moments on the same basis, entry by entry: each moment is one
+    FP64 dot product of the same pair of columns on both sides, so they differ
+    by at most 2 gamma_n |y_a|^T |y_b| of that pair."""
+    P, torch = env
+    A = MATRICES[name]()
+    rng = np.random.default_rng(100 + s)
+    p, r = rng.standard_normal(A.n), rng.standard_normal(A.n)
+    Yo = O.matrix_powers(O.Operator.from_csr(A), p, r, s, O.monomial_params(s))  # P then R columns
+    w = 2 * s + 1
+    order = [j // 2 if j % 2 == 0 else s + 1 + j // 2 for j in range(w)]  # interleaved -> oracle column
+    Yi = Yo[:, order]
+    ld = A.n + (32 - A.n % 32) % 32
+    Yd = torch.zeros(w * ld, dtype=torch.float64, device="cuda")
+    for c in range(w):
+        Yd[c * ld:c * ld + A.n] = dev(torch, Yi[:, c])
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram_moments(A.n, s, Yd, ld, G)
+    Gg = G.cpu().numpy().reshape(w, w)
+    Go = O.gram_moments(Yo, s)[np.ix_(order, order)]
+    absY = np.abs(Yo)
+
+    def pair(fam, k):  # the columns (oracle order) whose product gives the moment
+        if fam == 0:
+            return k // 2, (k + 1) // 2
+        if fam == 1:
+            return (k + 1) // 2, s + 1 + k // 2
+        return s + 1 + k // 2, s + 1 + (k + 1) // 2
+
+    bound = np.zeros((w, w))
+    for a in range(w):
+        for b in range(w):
+            fam = (a & 1) + (b & 1)
+            ca, cb = pair(fam, a // 2 + b // 2)
+            bound[a, b] = 2 * gamma_n(A.n) * (absY[:, ca] @ absY[:, cb])
+    assert np.all(np.abs(Gg - Go) <= bound), np.max(np.abs(Gg - Go) / bound)
+    assert np.array_equal(Gg, Gg.T)
+
+
 def tc_gram_bound(Y, parts=160):
     """Error bound of the tensor-core Gram (w >= 9): entries of column a are
     truncated to the grid 2^(E_a - 55), 2^(E_a - 1) <= max|y_a| < 2^E_a, the digit
@@ -402,6 +444,9 @@ SOLVES = [
     ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16,
                           c_formula=(W.poisson_eig_bounds(3, 23)[1] / W.poisson_eig_bounds(3, 23)[0],
                                      W.poisson_eig_bounds(3, 23)[1])), 1e-12),
+    # G from the monomial basis' moments (Hankel blocks) instead of Y^T Y
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8, moment_gram=True), 1e-10),
+    ("banded_3001", dict(method="adaptive", basis="monomial", s_max=10, moment_gram=True), 1e-8),
     # Alg. 3: block sizes from a given sequence (Fibonacci-type growth capped at s_max)
     ("poisson2d_32", dict(method="variable", basis="monomial", s_max=5, s_seq=W.fibonacci_s_sequence(5, 8)), 1e-10),
     ("poisson3d_23", dict(method="variable", basis="chebyshev", s_max=12, s_seq=W.fibonacci_s_sequence(12, 9)), 1e-12),
@@ -449,7 +494,8 @@ def run_oracle(A, b, x1, kw, eps, lam, max_iters=20000):
     return O.adaptive_sstep_cg(Ao, b, x1, s_max=s, s0=kw.get("s0"), f=kw.get("f"), eps_target=eps,
                                basis=kw.get("basis", "monomial"), lam=lam, newton_warmup=kw.get("newton_warmup"),
                                check_in_loop=kw.get("check_in_loop", True), max_iters=max_iters,
-                               c_formula=kw.get("c_formula"))
+                               c_formula=kw.get("c_formula"),
+                               gram_mode="moments" if kw.get("moment_gram") else "plain")
 
 
 @pytest.mark.parametrize("name,kw,eps", SOLVES)
@@ -503,7 +549,9 @@ def test_c_formula_argument_checks(env):
     b = dev(torch, W.rhs_uniform(A.n, np.random.default_rng(0)))
     x = torch.zeros(A.n, dtype=torch.float64, device="cuda")
     for kw in (dict(method="fixed", c_formula=(10.0, 2.0)), dict(c_formula=(0.5, 2.0)),
-               dict(c_formula=(10.0, 0.0)), dict(c_formula=(float("inf"), 2.0))):
+               dict(c_formula=(10.0, 0.0)), dict(c_formula=(float("inf"), 2.0)),
+               dict(basis="chebyshev", lam=(0.01, 2.0), moment_gram=True),
+               dict(method="classical", moment_gram=True)):
         with pytest.raises(P.AscgError) as e:
             P.ascg_solve(op, b, x, P.make_options(**kw))
         assert e.value.status == P.ASCG_ERR_INVALID
