@@ -399,33 +399,75 @@ class Lockstep {
     int* d_item0 = d_int_ + kItem0 * lanes_;
     int* d_nitems = d_int_ + kNItems * lanes_;
     const int nr = (int)ritems_.size(), ng = (int)gitems_.size();
-    LS_CUDA(cudaMemcpyAsync(d_bst_, h_bst_, sizeof(BlockState) * hi_, cudaMemcpyHostToDevice, s_));
-    LS_CUDA(cudaMemcpyAsync(d_steps, h_steps, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
-    LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
-    LS_CUDA(cudaMemcpyAsync(d_wi, h_wi, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
-    for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
+    const bool item_gram = (int)tc_lanes_.size() < count_active();
     const int Wb = 2 * max_sbar + 1;
-    int nl = max_sbar;
-    if ((int)tc_lanes_.size() < count_active()) {
-      // pair groups: enough CTAs to cover the SMs twice
-      const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
-      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
-      LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
-      nl += 2;
+    int nl = max_sbar + 2 + (item_gram ? 2 : 0) + 3 * (int)tc_lanes_.size();
+    // The block's work: the state records in, the matrix powers steps, the
+    // Gram (item launch and tensor-core lanes), the controller, the recovery,
+    // the state records out. The host fills the pinned records before each
+    // launch; a captured graph reads them when it runs.
+    auto enqueue = [&]() -> ascg_status {
+      LS_CUDA(cudaMemcpyAsync(d_bst_, h_bst_, sizeof(BlockState) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_steps, h_steps, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_wi, h_wi, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
+      if (item_gram) {
+        // pair groups: enough CTAs to cover the SMs twice
+        const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
+        LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
+        LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
+      }
+      for (int q : tc_lanes_) {  // one lane at a time: the lanes share the partials buffer in stream order
+        const LaneSys& L = lane_[q];
+        int parts = 0;
+        LS_CUDA(launch_gram_any(L.d.n, h_w[q], L.d.Y, L.d.ldY, false, d_tc_exp_, false, d_tc_partials_, &parts, s_));
+        LS_CUDA(launch_gram_finalize(h_w[q], d_tc_partials_, parts, d_G_ + (int64_t)q * kGStride, s_));
+      }
+      LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_,
+                                      hi_, max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_,
+                                      rcap_, d_ab_hist_, abcap_, d_spec_, d_tickets_, s_));
+      LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
+      LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
+      return ASCG_OK;
+    };
+    // A block of the same shape (tables, sbar_max, Gram schedule) replays a
+    // captured graph: one launch instead of about twenty calls.
+    std::vector<int> key = {tables_version_, max_sbar, item_gram ? 1 : 0};
+    for (int q : tc_lanes_) {
+      key.push_back(q);
+      key.push_back(h_w[q]);
     }
-    for (int q : tc_lanes_) {  // one lane at a time: the lanes share the partials buffer in stream order
-      const LaneSys& L = lane_[q];
-      int parts = 0;
-      LS_CUDA(launch_gram_any(L.d.n, h_w[q], L.d.Y, L.d.ldY, false, d_tc_exp_, false, d_tc_partials_, &parts, s_));
-      LS_CUDA(launch_gram_finalize(h_w[q], d_tc_partials_, parts, d_G_ + (int64_t)q * kGStride, s_));
-      nl += 3;  // column exponents, tensor-core kernel, finalize
+    cudaGraphExec_t exec = nullptr;
+    auto it = graphs_.find(key);
+    if (it != graphs_.end()) {
+      exec = it->second;
+    } else if (capturable_) {
+      if (cudaStreamBeginCapture(s_, cudaStreamCaptureModeRelaxed) == cudaSuccess) {
+        const ascg_status st = enqueue();
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(s_, &g);
+        if (st != ASCG_OK || e != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          if (st != ASCG_OK) return st;
+          return lfail(ASCG_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&exec, g, 0);
+        cudaGraphDestroy(g);
+        LS_CUDA(ei);
+        if (graphs_.size() >= kMaxGraphs) drop_graphs();
+        graphs_[key] = exec;
+      } else {
+        cudaGetLastError();
+        capturable_ = false;  // e.g. the legacy default stream: launch directly
+      }
     }
-    LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_, hi_,
-                                    max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_, rcap_,
-                                    d_ab_hist_, abcap_, d_spec_, d_tickets_, s_));
-    LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
-    LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
-    launches_ += nl + 2;
+    if (exec)
+      LS_CUDA(cudaGraphLaunch(exec, s_));
+    else
+      LS_TRY(enqueue());
+    launches_ += nl;
     *launched = true;
     return ASCG_OK;
   }
@@ -634,10 +676,19 @@ class Lockstep {
       LS_CUDA(cudaMemcpyAsync(d_int_ + kNItems * lanes_, h_nitems, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     }
     dirty_ = false;
+    ++tables_version_;
+    if (graphs_.size() >= kMaxGraphs) drop_graphs();
     return ASCG_OK;
   }
 
+  static constexpr size_t kMaxGraphs = 64;
+  void drop_graphs() {
+    for (auto& kv : graphs_) cudaGraphExecDestroy(kv.second);
+    graphs_.clear();
+  }
+
   void release() {
+    drop_graphs();
     dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
     dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
     dfree(d_tc_partials_); dfree(d_tc_exp_); dfree(d_spec_); dfree(d_tickets_);
@@ -650,6 +701,9 @@ class Lockstep {
   int lanes_ = 0, nused_ = 0, hi_ = 0, rcap_ = 0, abcap_ = 0, wcols_ = 0, npw_ = 0;
   bool dirty_ = true;
   bool moments_ = false;  // Hankel-moment Gram (monomial basis)
+  bool capturable_ = true;
+  int tables_version_ = 0;
+  std::map<std::vector<int>, cudaGraphExec_t> graphs_;  // captured blocks by shape
   int64_t super_blocks_ = 0, launches_ = 0;
   std::vector<LaneSys> lane_;
   std::vector<char> used_;
@@ -681,9 +735,38 @@ class Lockstep {
 
 // Batched solves: every system admitted at once, blocks until none is
 // active, then the true residuals.
+namespace {
+// A stream of the call's own (blocks on it can be captured as graphs, which
+// the legacy default stream does not allow), ordered after the caller's
+// stream on entry and before it on exit.
+struct OwnStream {
+  cudaStream_t user = nullptr, s = nullptr;
+  cudaEvent_t ev = nullptr;
+  ascg_status open(cudaStream_t u) {
+    user = u;
+    LS_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    LS_CUDA(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    LS_CUDA(cudaEventRecord(ev, user));
+    LS_CUDA(cudaStreamWaitEvent(s, ev, 0));
+    return ASCG_OK;
+  }
+  ~OwnStream() {
+    if (s) {
+      if (ev && cudaEventRecord(ev, s) == cudaSuccess) cudaStreamWaitEvent(user, ev, 0);
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+    if (ev) cudaEventDestroy(ev);
+  }
+};
+}  // namespace
+
 ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
                                  const double* eps_target, const ascg_options& o, ascg_result* results,
-                                 cudaStream_t s) {
+                                 cudaStream_t user_stream) {
+  OwnStream own;
+  LS_TRY(own.open(user_stream));
+  const cudaStream_t s = own.s;
   std::vector<LaneSys> sys(count);
   size_t y_bytes = 0;
   int64_t gi = 0, ri = 0;
@@ -693,7 +776,7 @@ ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* co
     gi += Lockstep::gram_items_of(sys[q].d.n);
     ri += Lockstep::row_items_of(sys[q].d.n);
   }
-  Arena arena;
+  Arena arena;  // destroyed after the engine and its stream's work (declaration order)
   LS_TRY(arena.init(y_bytes));
   for (int q = 0; q < count; ++q) {
     if (!arena.take(sys[q].bytes, &sys[q].off)) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
