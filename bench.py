@@ -68,6 +68,8 @@ def parse():
                     help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batch workload: measure the Gram schedule threshold first (ascg_tune_gram_schedule)")
     ap.add_argument("--moment-gram", action="store_true",
                     help="batch and served workloads: G from the monomial basis' moments (a variant)")
     ap.add_argument("--requests", type=int, default=200, help="served workload: requests in the open-loop run")
@@ -454,8 +456,12 @@ def batch_arm(args):
     bs = [torch.from_numpy(s["b"]).cuda() for s in systems]
     xs = [torch.zeros(s["A"].n, dtype=torch.float64, device="cuda") for s in systems]
     eps = [s["eps"] for s in systems]
+    tuned = None
+    if args.autotune:
+        thr, table = P.ascg_tune_gram_schedule(10)
+        tuned = {"tc_lane_rows": thr, "table_us": [[int(r[0]), round(r[1], 1), round(r[2], 1)] for r in table]}
     o = P.make_options(method="adaptive", basis="monomial", s_max=10, eps_target=1e-10, max_iters=20000,
-                       moment_gram=args.moment_gram)
+                       moment_gram=args.moment_gram, tc_lane_rows=tuned["tc_lane_rows"] if tuned else 0)
     stream = torch.cuda.current_stream()
 
     def batch_once():
@@ -508,7 +514,7 @@ def batch_arm(args):
         "worst_true_res_over_target": worst_true,
         "sequential": {"ms": seq_ms, "iters": seq_iters, "iters_per_s": seq_iters / (seq_ms * 1e-3),
                        "batch_speedup": seq_ms / (ms / args.steps)},
-        "setup_s": t_gen, "clocks": clocks,
+        "setup_s": t_gen, "clocks": clocks, "gram_schedule": tuned or {"tc_lane_rows": 1 << 18, "source": "default"},
     }
     print(json.dumps(line), flush=True)
     for op in ops:

@@ -119,6 +119,11 @@ typedef struct {
   /* ASCG_FLAG_C_FORMULA (ASCG_ADAPTIVE, ascg_solve only): estimates of
      kappa(A) (>= 1) and ||A||_2 (> 0) for c_{k,j} = 6 N_k j kappa(A) */
   double kappa_A, norm_A;
+  /* batched solves and the server: rows from which a system's Gram runs on
+     the tensor cores (w >= 9) instead of in the shared FP64 launch; 0: 2^18;
+     < 0: never. ascg_tune_gram_schedule measures a value for this GPU. The
+     two kernels round differently: keep it fixed for reproducible results. */
+  int64_t tc_lane_rows;
 } ascg_options;
 
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
@@ -427,6 +432,21 @@ ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* stats);
  * yet completed are dropped (their x holds whatever iterate was reached).
  * NULL is accepted. */
 ascg_status ascg_server_destroy(ascg_server srv);
+
+/* Autotuner of the batched Gram schedule. For w = 2 s_max + 1 and sizes
+ * n = 2^12, 2^13, ..., 2^22, times on this GPU the Gram of one system of n
+ * rows (random basis) in the FP64 item launch and on the tensor cores
+ * (column exponents, kernel, finalize), each the median of several runs. In
+ * a batch the FP64 items of all systems share one launch that fills the GPU,
+ * so a system's FP64 cost is taken as n times the per-row cost at the
+ * largest size. Writes to *tc_lane_rows the smallest n of the grid from
+ * which the tensor cores are faster at that size and every larger one (or
+ * -1 if they never are), for ascg_options.tc_lane_rows. table (host, may be NULL): up to table_cap rows
+ * of (n, FP64 us, tensor-core us). *rows: rows written. 1 <= s_max <= 16.
+ * Uses about (2 s_max + 1) x 32 MB of device memory while it runs.
+ * Synchronises the stream. */
+ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* table, int table_cap, int* rows,
+                                    void* cuda_stream);
 
 /* Message of the last error on this thread ("" if none). */
 const char* ascg_last_error(void);

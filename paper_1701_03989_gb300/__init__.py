@@ -54,7 +54,7 @@ class ascg_options(C.Structure):
                 ("alpha_hist", C.POINTER(C.c_double)), ("beta_hist", C.POINTER(C.c_double)),
                 ("coef_hist_cap", C.c_int), ("pad4_", C.c_int),
                 ("s_seq", C.POINTER(C.c_int)), ("s_seq_len", C.c_int), ("pad5_", C.c_int),
-                ("kappa_A", C.c_double), ("norm_A", C.c_double)]
+                ("kappa_A", C.c_double), ("norm_A", C.c_double), ("tc_lane_rows", C.c_int64)]
 
 
 class ascg_result(C.Structure):
@@ -111,6 +111,7 @@ def _load():
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "ascg_server_info": (C.c_int, [P, C.POINTER(ascg_server_stats)]),
         "ascg_server_destroy": (C.c_int, [P]),
+        "ascg_tune_gram_schedule": (C.c_int, [C.c_int, C.POINTER(I64), P, C.c_int, C.POINTER(C.c_int), P]),
         "ascg_last_error": (C.c_char_p, []),
     }
     for name, (res, args) in sig.items():
@@ -245,6 +246,17 @@ def ascg_server_info(srv):
     return st
 
 
+def ascg_tune_gram_schedule(s_max, stream=None):
+    """Measured Gram schedule threshold for batched solves: returns (tc_lane_rows,
+    table as a list of (n, fp64_us, tensor_us))."""
+    thr = C.c_int64()
+    buf = np.zeros((16, 3))
+    rows = C.c_int()
+    _check(_lib.ascg_tune_gram_schedule(int(s_max), C.byref(thr), buf.ctypes.data, 16, C.byref(rows), _stream(stream)),
+           "ascg_tune_gram_schedule")
+    return thr.value, [tuple(buf[i]) for i in range(rows.value)]
+
+
 def ascg_server_destroy(srv):
     _check(_lib.ascg_server_destroy(srv), "ascg_server_destroy")
 
@@ -324,7 +336,8 @@ _BASES = {"monomial": ASCG_MONOMIAL, "newton": ASCG_NEWTON, "chebyshev": ASCG_CH
 def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, eps_target=1e-10, c=1.0,
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
-                 gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False) -> ascg_options:
+                 gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False,
+                 tc_lane_rows=0) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
@@ -345,6 +358,7 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
     o.max_iters = int(max_iters)
     o.check_in_loop = 1 if check_in_loop else 0
     o.flags = (ASCG_FLAG_TIMING if timing else 0) | (ASCG_FLAG_GRAM_FP64 if gram_fp64 else 0)
+    o.tc_lane_rows = int(tc_lane_rows)
     if moment_gram:
         o.flags |= ASCG_FLAG_MOMENT_GRAM
     if c_formula is not None:
@@ -377,4 +391,4 @@ EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "as
             "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc", "ascg_gram_moments",
             "ascg_block_step", "ascg_recover",
             "ascg_newton_shifts", "ascg_server_create", "ascg_server_submit", "ascg_server_step",
-            "ascg_server_info", "ascg_server_destroy", "ascg_last_error"]
+            "ascg_server_info", "ascg_server_destroy", "ascg_tune_gram_schedule", "ascg_last_error"]

@@ -192,6 +192,8 @@ cudaError_t launch_residual_items(const SysDesc* descs, const RowItem* items, in
 // out[q] = sum of squares (fixed order) of b (which 0) or Y column `which` of the systems in list.
 cudaError_t launch_seg_sumsq(const SysDesc* descs, const int* list, int nlist, int which, double* out,
                              cudaStream_t s);
+// count values in [-1, 1) from a hash of (seed, index) (timing data).
+cudaError_t launch_fill_uniform(double* v, int64_t count, uint64_t seed, cudaStream_t s);
 // Recovery of every system with w_q = sys_w[q] > 0 (W >= max w_q), coordinates at coords + q * c_stride.
 cudaError_t launch_recover_items(int W, const SysDesc* descs, const RowItem* items, int nitems, const int* sys_w,
                                  const double* coords, int64_t c_stride, cudaStream_t s);

@@ -135,7 +135,26 @@ __global__ void __launch_bounds__(kRowItem) recover_items_kernel(const SysDesc* 
   d.Y[row] = sp;
 }
 
+// v[i] in [-1, 1) from a 64-bit mix of (seed, i) (the SplitMix64 finaliser of
+// Steele, Lea and Flood, "Fast splittable pseudorandom number generators",
+// OOPSLA 2014): synthetic data for the autotuner's timings.
+__global__ void fill_uniform_kernel(double* __restrict__ v, int64_t count, uint64_t seed) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = seed + (uint64_t)i * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    v[i] = (double)(int64_t)(z >> 11) * 0x1.0p-52 - 1.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_fill_uniform(double* v, int64_t count, uint64_t seed, cudaStream_t s) {
+  if (count < 1) return cudaSuccess;
+  fill_uniform_kernel<<<grid_for(count, 256, 152 * 16), 256, 0, s>>>(v, count, seed);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_mpk_items(const SysDesc* descs, const RowItem* items, int nitems, const int* sys_steps, int j,
                              cudaStream_t s) {

@@ -24,7 +24,9 @@
 // Gram schedule per lane, fixed by the lane's own size: lanes of at least
 // kTcLaneRows rows (and w >= 9) take the tensor-core Gram kernel, one launch
 // per lane; all other lanes share one launch of the FP64 item kernel.
+#include <algorithm>
 #include <chrono>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <deque>
@@ -185,8 +187,9 @@ struct LaneSys {
 };
 
 // Rows from which a lane's Gram runs on the tensor cores (one launch per
-// lane); below it the lane joins the shared FP64 item launch, which keeps the
-// whole GPU busy with many small lanes at once.
+// lane) by default; below it the lane joins the shared FP64 item launch,
+// which keeps the whole GPU busy with many small lanes at once. The
+// options can set another value (ascg_tune_gram_schedule measures one).
 constexpr int64_t kTcLaneRows = (int64_t)1 << 18;
 
 class Lockstep {
@@ -209,6 +212,7 @@ class Lockstep {
     abcap_ = abcap;
     wcols_ = 2 * o.s_max + 1;
     moments_ = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
+    tc_rows_ = o.tc_lane_rows == 0 ? kTcLaneRows : (o.tc_lane_rows < 0 ? INT64_MAX : o.tc_lane_rows);
     npw_ = (int)partials_per_item(o.s_max, moments_);
     LS_TRY(dalloc(&d_desc_, lanes));
     LS_TRY(dalloc(&d_bst_, lanes));
@@ -387,7 +391,7 @@ class Lockstep {
       const int w = 2 * sbar + 1;
       h_steps[q] = sbar;
       h_w[q] = w;
-      const bool tc = !moments_ && L.d.n >= kTcLaneRows && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
+      const bool tc = !moments_ && L.d.n >= tc_rows_ && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
       h_wi[q] = tc ? 0 : w;
       if (tc) tc_lanes_.push_back(q);
       max_sbar = std::max(max_sbar, sbar);
@@ -702,6 +706,7 @@ class Lockstep {
   bool dirty_ = true;
   bool moments_ = false;  // Hankel-moment Gram (monomial basis)
   bool capturable_ = true;
+  int64_t tc_rows_ = kTcLaneRows;  // lanes of at least this many rows: tensor-core Gram
   int tables_version_ = 0;
   std::map<std::vector<int>, cudaGraphExec_t> graphs_;  // captured blocks by shape
   int64_t super_blocks_ = 0, launches_ = 0;
@@ -1086,6 +1091,105 @@ ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, in
   if (ndone) *ndone = nd;
   if (nactive) *nactive = srv->running;
   if (npending) *npending = (int)std::min<size_t>(srv->queue.size() + srv->ready.size(), 0x7fffffff);
+  return ASCG_OK;
+}
+
+ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* table, int table_cap, int* rows,
+                                    void* cuda_stream) {
+  set_last_error("");
+  if (!tc_lane_rows || s_max < 1 || s_max > ASCG_MAX_S || table_cap < 0 || (table_cap > 0 && !table))
+    return lfail(ASCG_ERR_INVALID, "bad argument");
+  *tc_lane_rows = -1;
+  if (rows) *rows = 0;
+  const int w = 2 * s_max + 1;
+  if (!gram_tc_applies(w)) return ASCG_OK;  // narrow bases always take the FP64 kernel
+  const cudaStream_t s = (cudaStream_t)cuda_stream;
+  constexpr int kLogMin = 12, kLogMax = 22, kReps = 5;
+  const int64_t ld = (int64_t)1 << kLogMax;
+  struct Bufs {
+    double *Y = nullptr, *G = nullptr, *part = nullptr, *tcp = nullptr;
+    int *ints = nullptr, *exps = nullptr;
+    SysDesc* desc = nullptr;
+    GramItem* items = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~Bufs() {
+      dfree(Y); dfree(G); dfree(part); dfree(tcp); dfree(ints); dfree(exps); dfree(desc); dfree(items);
+      if (e0) cudaEventDestroy(e0);
+      if (e1) cudaEventDestroy(e1);
+    }
+  } B;
+  const int64_t max_items = ld / kGramItemRowsMin + 1;
+  const int64_t np = (int64_t)w * (w + 1) / 2;
+  LS_TRY(dalloc(&B.Y, (size_t)w * ld));
+  LS_TRY(dalloc(&B.G, (size_t)kMaxW * kMaxW));
+  LS_TRY(dalloc(&B.part, (size_t)max_items * np));
+  LS_TRY(dalloc(&B.tcp, (size_t)gram_grid() * kMaxPairs));
+  LS_TRY(dalloc(&B.exps, (size_t)gram_grid() * kMaxW));
+  LS_TRY(dalloc(&B.ints, 3));
+  LS_TRY(dalloc(&B.desc, 1));
+  LS_TRY(dalloc(&B.items, (size_t)max_items));
+  LS_CUDA(cudaEventCreate(&B.e0));
+  LS_CUDA(cudaEventCreate(&B.e1));
+  LS_CUDA(launch_fill_uniform(B.Y, (int64_t)w * ld, 0x5eed5eedull, s));
+  const int hint[3] = {w, 0, 0};  // sys_w, item0, nitems (set per size)
+  std::vector<double> t_fp(kLogMax + 1), t_tc(kLogMax + 1);
+  int nrow = 0;
+  for (int lg = kLogMin; lg <= kLogMax; ++lg) {
+    const int64_t n = (int64_t)1 << lg;
+    SysDesc d{};
+    d.n = n;
+    d.Y = B.Y;
+    d.ldY = ld;
+    std::vector<GramItem> items;
+    const int64_t gr = gram_item_rows(n);
+    for (int64_t r = 0; r < n; r += gr) items.push_back(GramItem{r, (int)std::min<int64_t>(gr, n - r), 0});
+    const int ng = (int)items.size();
+    const int ints[3] = {hint[0], 0, ng};
+    LS_CUDA(cudaMemcpyAsync(B.desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
+    LS_CUDA(cudaMemcpyAsync(B.items, items.data(), sizeof(GramItem) * ng, cudaMemcpyHostToDevice, s));
+    LS_CUDA(cudaMemcpyAsync(B.ints, ints, sizeof(ints), cudaMemcpyHostToDevice, s));
+    LS_CUDA(cudaStreamSynchronize(s));  // the host arrays above are locals
+    const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / ng));
+    std::vector<float> a(kReps), b(kReps);
+    for (int rep = 0; rep < kReps + 1; ++rep) {  // the first run of each is a warm-up
+      LS_CUDA(cudaEventRecord(B.e0, s));
+      LS_CUDA(launch_gram_items(w, B.desc, B.items, ng, B.ints, B.part, groups, false, s));
+      LS_CUDA(launch_gram_items_finalize(w, B.part, B.ints + 1, B.ints + 2, B.ints, 1, B.G, kMaxW * kMaxW, false, s));
+      LS_CUDA(cudaEventRecord(B.e1, s));
+      LS_CUDA(cudaEventSynchronize(B.e1));
+      float ms = 0.f;
+      LS_CUDA(cudaEventElapsedTime(&ms, B.e0, B.e1));
+      if (rep > 0) a[rep - 1] = ms;
+      int parts = 0;
+      LS_CUDA(cudaEventRecord(B.e0, s));
+      LS_CUDA(launch_gram_any(n, w, B.Y, ld, false, B.exps, false, B.tcp, &parts, s));
+      LS_CUDA(launch_gram_finalize(w, B.tcp, parts, B.G, s));
+      LS_CUDA(cudaEventRecord(B.e1, s));
+      LS_CUDA(cudaEventSynchronize(B.e1));
+      LS_CUDA(cudaEventElapsedTime(&ms, B.e0, B.e1));
+      if (rep > 0) b[rep - 1] = ms;
+    }
+    std::sort(a.begin(), a.end());
+    std::sort(b.begin(), b.end());
+    t_fp[lg] = 1e3 * a[kReps / 2];
+    t_tc[lg] = 1e3 * b[kReps / 2];
+    if (nrow < table_cap) {
+      table[3 * nrow] = (double)n;
+      table[3 * nrow + 1] = t_fp[lg];
+      table[3 * nrow + 2] = t_tc[lg];
+      ++nrow;
+    }
+  }
+  if (rows) *rows = nrow;
+  // In a batch the FP64 items of every lane share one launch that fills the
+  // GPU, so a lane's FP64 cost is its rows times the per-row cost at full
+  // load (taken at the largest size); a tensor-core lane runs alone. The
+  // threshold is the smallest size from which the tensor cores win at every
+  // larger size.
+  const double per_row = t_fp[kLogMax] / (double)((int64_t)1 << kLogMax);
+  int from = kLogMax + 1;
+  for (int lg = kLogMax; lg >= kLogMin && t_tc[lg] < per_row * (double)((int64_t)1 << lg); --lg) from = lg;
+  *tc_lane_rows = from <= kLogMax ? ((int64_t)1 << from) : -1;
   return ASCG_OK;
 }
 

@@ -37,7 +37,7 @@ def make_op(P, A):
 
 
 def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", eps=None, s_seq=None,
-              moment_gram=False):
+              moment_gram=False, tc_lane_rows=0):
     count = len(systems)
     ops = [make_op(P, s["A"]) for s in systems]
     bs = [dev(torch, s["b"]) for s in systems]
@@ -45,7 +45,8 @@ def run_batch(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", 
     res_hist = np.zeros((count, max_iters + 2))
     infos = P.block_infos(count * (max_iters + 2))
     o = P.make_options(method=method, basis="monomial", s_max=s_max, eps_target=1e-10, max_iters=max_iters,
-                       res_hist=res_hist.reshape(-1), block_hist=infos, s_seq=s_seq, moment_gram=moment_gram)
+                       res_hist=res_hist.reshape(-1), block_hist=infos, s_seq=s_seq, moment_gram=moment_gram,
+                       tc_lane_rows=tc_lane_rows)
     o.res_hist_cap = max_iters + 2
     o.block_hist_cap = max_iters + 2
     epsv = [s["eps"] for s in systems] if eps is None else eps
@@ -246,3 +247,25 @@ def test_batch_rejects_unsupported(env):
         P.ascg_solve_batch([op], [b], [x], o)
     assert e.value.status == P.ASCG_ERR_INVALID
     P.ascg_op_destroy(op)
+
+
+def test_gram_schedule_autotuner(env):
+    """ascg_tune_gram_schedule times both Gram kernels over its size grid and
+    returns a power of two in it (or -1); a batch run with that threshold meets
+    the parity rules (the tensor-core lanes among them)."""
+    P, torch = env
+    thr, table = P.ascg_tune_gram_schedule(S_MAX)
+    assert len(table) == 11 and [int(r[0]) for r in table] == [1 << k for k in range(12, 23)]
+    assert all(r[1] > 0 and r[2] > 0 for r in table)
+    assert thr == -1 or (thr & (thr - 1)) == 0 and (1 << 12) <= thr <= (1 << 22)
+    assert P.ascg_tune_gram_schedule(3)[0] == -1  # w = 7 < 9: always the FP64 kernel
+    systems = small_batch(seed=16, count=4)
+    lo = min(s["A"].n for s in systems)
+    out, st = run_batch(P, torch, systems, tc_lane_rows=lo)  # every lane on the tensor cores
+    assert st == P.ASCG_OK
+    for s, g in zip(systems, out):
+        orc = O.adaptive_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], s_max=S_MAX, eps_target=s["eps"],
+                                  basis="monomial", max_iters=CAP)
+        exempt, bad = parity.compare_block_sequences(g["blocks"], orc.blocks, s["A"].n, orc.res_hist, s["eps"])
+        assert not bad, (s["name"], bad)
+        assert parity.final_residual_ok(g["res"].rel_res_true, orc.true_res, s["eps"], exempt), s["name"]
