@@ -119,8 +119,8 @@ typedef struct {
   /* ASCG_FLAG_C_FORMULA (ASCG_ADAPTIVE, ascg_solve only): estimates of
      kappa(A) (>= 1) and ||A||_2 (> 0) for c_{k,j} = 6 N_k j kappa(A) */
   double kappa_A, norm_A;
-  /* batched solves and the server: rows from which a system's Gram runs on
-     the tensor cores (w >= 9) instead of in the shared FP64 launch; 0: 2^18;
+  /* batched solves and the server: rows from which a system's Gram runs in
+     the tensor-core launch (w >= 9) instead of the FP64 one; 0: 1024;
      < 0: never. ascg_tune_gram_schedule measures a value for this GPU. The
      two kernels round differently: keep it fixed for reproducible results. */
   int64_t tc_lane_rows;
@@ -435,13 +435,14 @@ ascg_status ascg_server_destroy(ascg_server srv);
 
 /* Autotuner of the batched Gram schedule. For w = 2 s_max + 1 and sizes
  * n = 2^12, 2^13, ..., 2^22, times on this GPU the Gram of one system of n
- * rows (random basis) in the FP64 item launch and on the tensor cores
- * (column exponents, kernel, finalize), each the median of several runs. In
- * a batch the FP64 items of all systems share one launch that fills the GPU,
- * so a system's FP64 cost is taken as n times the per-row cost at the
- * largest size. Writes to *tc_lane_rows the smallest n of the grid from
- * which the tensor cores are faster at that size and every larger one (or
- * -1 if they never are), for ascg_options.tc_lane_rows. table (host, may be NULL): up to table_cap rows
+ * rows (random basis) in the FP64 item launch and in the tensor-core item
+ * launch (column exponents, kernel, finalize), each the median of several
+ * runs. In a batch each launch covers all its systems and fills the GPU, so
+ * a system costs the per-row rate at full load (taken at the largest size)
+ * times the rows read: n in FP64, round_up(n, 1024) on the tensor cores.
+ * Writes to *tc_lane_rows the smallest power of two >= 256 from which the
+ * tensor cores cost less at every larger size (or -1 if they never do), for
+ * ascg_options.tc_lane_rows. table (host, may be NULL): up to table_cap rows
  * of (n, FP64 us, tensor-core us). *rows: rows written. 1 <= s_max <= 16.
  * Uses about (2 s_max + 1) x 32 MB of device memory while it runs.
  * Synchronises the stream. */

@@ -159,6 +159,15 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
                            double* partials, cudaStream_t s);
 // Partials of G with the kernel for this width (FP64 when force_fp64); returns
 // the number of partials through *nparts.
+// Tensor-core Gram of many systems whose bases are row ranges of one matrix
+// Y (rows x w used, leading dimension ldY, rows a multiple of 1024): items
+// are whole 1024-row chunks of one system each (GramItem rows in Y, nrows a
+// multiple of 1024, at most 8 chunks); items of systems with sys_w 0 skip.
+// Each item gets its system's column exponents (emax_all: nsys x 33 ints,
+// zeroed and filled here) and writes w(w+1)/2 partials.
+cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t rows, const GramItem* items,
+                                 int nitems, const int* sys_w, int nsys, int* emax_all, double* partials,
+                                 cudaStream_t s);
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s);
 

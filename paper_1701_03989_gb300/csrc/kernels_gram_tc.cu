@@ -475,9 +475,13 @@ __device__ __forceinline__ bool drain_chunk(uint32_t c, int w, int half, int qua
   return true;
 }
 
-__global__ void __launch_bounds__(kTcThreads, 1)
-    gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
-                   double* __restrict__ partials) {
+// The Gram partial of the chunks ch = c_lo, c_lo + c_step, ... < c_hi of the
+// rows [row_base, row_base + n_local) of the tensor map's matrix (chunk ch
+// starts at row row_base + ch * kTChunk), with the column exponents col_emax,
+// written to out[w (w + 1) / 2]. Run by a whole CTA of kTcThreads.
+__device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, int64_t row_base, int64_t c_lo,
+                                             int64_t c_hi, int64_t c_step, int64_t n_local,
+                                             const int* __restrict__ col_emax, double* __restrict__ out) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* dstage = smem + kDOff;
   unsigned char* fstage = smem + kFOff;
@@ -525,7 +529,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
-  const int64_t chunks = (n + kTChunk - 1) / kTChunk;
+  const int64_t n = n_local;
   uint32_t armed = 0;   // loader: stages whose copies were issued
   uint32_t issued = 0;  // MMA issuer: stages whose MMAs were issued
 
@@ -535,7 +539,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int half = warp >> 2, quarter = warp & 3;
     const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16);
     uint32_t t = 0, cu = 0, drained = 0;
-    for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x, ++cu) {
+    for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
       const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
       const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
       for (int sub = 0; sub < nsub; ++sub, ++t) {
@@ -563,14 +567,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- loader: one tensor copy per stage ----
     if (lane == 0) {
       uint32_t t = 0;
-      for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x) {
+      for (int64_t ch = c_lo; ch < c_hi; ch += c_step) {
         const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
         const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
         for (int sub = 0; sub < nsub; ++sub, ++t) {
           const int fs = (int)(t % kFStages);
           if (t >= kFStages && !bar_wait(f_empty + fs, (t / kFStages - 1) & 1, s_err)) goto done;
           bar_expect_tx(f_full + fs, kFBoxBytes);
-          tensor_g2s(fstage + fs * kFStageBytes, &ymap, (int)(ch * kTChunk + (int64_t)sub * kSub), f_full + fs);
+          tensor_g2s(fstage + fs * kFStageBytes, ymap_p, (int)(row_base + ch * kTChunk + (int64_t)sub * kSub),
+                     f_full + fs);
           armed = t + 1;
         }
       }
@@ -579,7 +584,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // ---- MMA issue ----
     if (lane == 0) {
       uint32_t t = 0, cu = 0;
-      for (int64_t ch = blockIdx.x; ch < chunks; ch += gridDim.x, ++cu) {
+      for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
         const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
         const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
         const uint32_t p = cu & 1;
@@ -635,13 +640,36 @@ done:
       const double s = ldexp((double)hi, -24) + ldexp((double)lo, -56);
       v = ldexp(s, s_emax[a] + s_emax[b] - 2058);
     }
-    partials[(int64_t)blockIdx.x * np + p] = v;
+    out[p] = v;
   }
   if (warp == kMmaWarp) {
     __syncwarp();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tbase));
   }
+}
+
+// One matrix: CTA b takes the chunks b, b + gridDim.x, ... of the n rows.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
+                   double* __restrict__ partials) {
+  gram_tc_body(&ymap, w, 0, blockIdx.x, (n + kTChunk - 1) / kTChunk, gridDim.x, n, col_emax,
+               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2));
+}
+
+// Many systems whose bases are row ranges of one matrix (the tensor map's):
+// CTA q takes item q, whole chunks of one system (rows [row0, row0 + nrows),
+// nrows a multiple of kTChunk), with that system's column exponents
+// (emax_all + sys * kTW). Items of systems with sys_w 0 skip.
+__global__ void __launch_bounds__(kTcThreads, 1)
+    gram_tc_items_kernel(const __grid_constant__ CUtensorMap ymap, int w, const GramItem* __restrict__ items,
+                         const int* __restrict__ sys_w, const int* __restrict__ emax_all,
+                         double* __restrict__ partials) {
+  const GramItem it = items[blockIdx.x];
+  if (sys_w[it.sys] == 0) return;  // uniform over the CTA, before any barrier
+  const int64_t nch = it.nrows / kTChunk;
+  gram_tc_body(&ymap, w, it.row0, 0, nch, 1, nch * kTChunk, emax_all + (int64_t)it.sys * kTW,
+               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2));
 }
 
 // Largest biased exponent of each column, reduced into col_emax (zeroed
@@ -682,6 +710,42 @@ __global__ void __launch_bounds__(256) col_exponent_kernel(int64_t n, int w, con
     unsigned m = 0;
     for (int g = 0; g < 8; ++g) m = max(m, red[g][threadIdx.x]);
     if (m > 0) atomicMax(col_emax + threadIdx.x, (int)m);
+  }
+}
+
+// Column exponents of many systems: CTA q takes item q (the rows of one
+// system) and folds the largest biased exponent of each of its w columns into
+// emax_all[sys * kTW + c] (zeroed before the launch).
+__global__ void __launch_bounds__(256) tc_items_exponent_kernel(int w, const double* __restrict__ Y, int64_t ldY,
+                                                                const GramItem* __restrict__ items,
+                                                                const int* __restrict__ sys_w,
+                                                                int* __restrict__ emax_all) {
+  __shared__ unsigned red[8][kTW];
+  const GramItem it = items[blockIdx.x];
+  if (sys_w[it.sys] == 0) return;  // uniform over the CTA
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  auto ex = [](double v) { return ((unsigned)__double2hiint(v) >> 20) & 0x7ffu; };
+  for (int a = 0; a < w; ++a) {
+    const double2* col = reinterpret_cast<const double2*>(Y + (int64_t)a * ldY + it.row0);
+    unsigned m0 = 0, m1 = 0;
+    int64_t q = threadIdx.x;
+    for (; q + 256 < it.nrows / 2; q += 512) {
+      const double2 v0 = __ldcs(col + q), v1 = __ldcs(col + q + 256);
+      m0 = max(m0, max(ex(v0.x), ex(v0.y)));
+      m1 = max(m1, max(ex(v1.x), ex(v1.y)));
+    }
+    for (; q < it.nrows / 2; q += 256) {
+      const double2 v = __ldcs(col + q);
+      m0 = max(m0, max(ex(v.x), ex(v.y)));
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, max(m0, m1));
+    if (lane == 0) red[warp][a] = m;
+  }
+  __syncthreads();
+  if (threadIdx.x < w) {
+    unsigned m = 0;
+    for (int g = 0; g < 8; ++g) m = max(m, red[g][threadIdx.x]);
+    if (m > 0) atomicMax(emax_all + (int64_t)it.sys * kTW + threadIdx.x, (int)m);
   }
 }
 
@@ -752,6 +816,34 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
     if (e != cudaSuccess) return e;
   }
   gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t rows, const GramItem* items,
+                                 int nitems, const int* sys_w, int nsys, int* emax_all, double* partials,
+                                 cudaStream_t s) {
+  if (nitems < 1) return cudaSuccess;
+  if (!gram_tc_applies(w) || !gram_tc_aligned(Y, ldY) || rows < 1 || rows > 0x7fffffffll || rows > ldY ||
+      (rows % kTChunk) != 0)
+    return cudaErrorInvalidValue;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  static int attr_dev = -1;
+  if (attr_dev != dev) {
+    e = cudaFuncSetAttribute(gram_tc_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
+    if (e != cudaSuccess) return e;
+    attr_dev = dev;
+  }
+  CUtensorMap map;
+  e = encode_map(&map, Y, rows, w, ldY);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(emax_all, 0, sizeof(int) * kTW * nsys, s);
+  if (e != cudaSuccess) return e;
+  tc_items_exponent_kernel<<<nitems, 256, 0, s>>>(w, Y, ldY, items, sys_w, emax_all);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  gram_tc_items_kernel<<<nitems, kTcThreads, kTcSmem, s>>>(map, w, items, sys_w, emax_all, partials);
   return cudaGetLastError();
 }
 

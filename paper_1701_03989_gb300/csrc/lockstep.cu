@@ -109,63 +109,72 @@ double now_ms() {
   return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
 }
 
-// First-fit allocator over one device allocation. Blocks are multiples of
-// kAlign bytes; a freed block merges with free neighbours.
+// The bases of all held systems are row ranges of one matrix of wcols
+// columns and R rows (column-major, leading dimension R): a system of n rows
+// holds rows [r0, r0 + round_up(n, 1024)) of every column. One leading
+// dimension for all lets one tensor map, and so one tensor-core Gram launch,
+// cover every system. First-fit over row ranges; a freed range merges with
+// its free neighbours. Ranges start and end on 1024-row boundaries, the
+// chunks of the tensor-core Gram.
 class Arena {
  public:
-  static constexpr size_t kAlign = 256;
+  static constexpr int64_t kRowAlign = 1024;
   ~Arena() { dfree(base_); }
-  ascg_status init(size_t bytes) {
-    size_ = (size_t)round_up((int64_t)bytes, kAlign);
-    if (size_ > 0) {
-      LS_TRY(dalloc(&base_, size_));
-      free_[0] = size_;
+  ascg_status init(int wcols, int64_t rows) {
+    wcols_ = wcols;
+    rows_ = rows > 0 ? round_up(rows, kRowAlign) : 0;
+    if (rows_ > 0) {
+      LS_TRY(dalloc(&base_, (size_t)wcols * rows_));
+      free_[0] = rows_;
     }
     return ASCG_OK;
   }
-  static size_t rounded(size_t bytes) { return (size_t)round_up((int64_t)bytes, kAlign); }
-  bool take(size_t bytes, size_t* off) {
-    bytes = rounded(bytes);
+  static int64_t rounded(int64_t n) { return round_up(n > 0 ? n : 1, kRowAlign); }
+  bool take(int64_t n, int64_t* r0) {
+    const int64_t need = rounded(n);
     for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < bytes) continue;
-      *off = it->first;
-      const size_t rest = it->second - bytes, next = it->first + bytes;
+      if (it->second < need) continue;
+      *r0 = it->first;
+      const int64_t rest = it->second - need, next = it->first + need;
       free_.erase(it);
       if (rest) free_[next] = rest;
-      live_[*off] = bytes;
-      used_ += bytes;
+      live_[*r0] = need;
+      used_ += need;
       return true;
     }
     return false;
   }
-  void give(size_t off) {
-    auto l = live_.find(off);
+  void give(int64_t r0) {
+    auto l = live_.find(r0);
     if (l == live_.end()) return;
-    size_t bytes = l->second;
+    int64_t len = l->second;
     live_.erase(l);
-    used_ -= bytes;
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && nx->first == off + bytes) {
-      bytes += nx->second;
+    used_ -= len;
+    auto nx = free_.lower_bound(r0);
+    if (nx != free_.end() && nx->first == r0 + len) {
+      len += nx->second;
       nx = free_.erase(nx);
     }
     if (nx != free_.begin()) {
       auto pv = std::prev(nx);
-      if (pv->first + pv->second == off) {
-        pv->second += bytes;
+      if (pv->first + pv->second == r0) {
+        pv->second += len;
         return;
       }
     }
-    free_[off] = bytes;
+    free_[r0] = len;
   }
-  double* at(size_t off) const { return (double*)(base_ + off); }
-  size_t size() const { return size_; }
-  size_t used() const { return used_; }
+  double* row(int64_t r0) const { return base_ + r0; }  // column 0 at row r0
+  double* base() const { return base_; }
+  int64_t ld() const { return rows_; }
+  size_t bytes_total() const { return (size_t)wcols_ * rows_ * sizeof(double); }
+  size_t bytes_used() const { return (size_t)wcols_ * used_ * sizeof(double); }
 
  private:
-  char* base_ = nullptr;
-  size_t size_ = 0, used_ = 0;
-  std::map<size_t, size_t> free_, live_;  // offset -> bytes
+  double* base_ = nullptr;
+  int wcols_ = 0;
+  int64_t rows_ = 0, used_ = 0;
+  std::map<int64_t, int64_t> free_, live_;  // first row -> rows
 };
 
 }  // namespace
@@ -176,7 +185,8 @@ struct LaneSys {
   SysDesc d{};
   double eps_target = 0.0;
   int64_t tag = 0;
-  size_t off = 0, bytes = 0;
+  int64_t off = 0;   // first row of the system's range in the shared basis matrix
+  size_t bytes = 0;  // basis bytes: (2 s_max + 1) 8 round_up(n, 1024)
   int m = 0, kb = 0, s_prev = 0, nb_info = 0, wasted = 0, sbar = 0;
   double bnorm = 0.0, eps_star = 0.0, rel_upd = 0.0, rnorm0 = 0.0, rel_true = 0.0;
   bool active = false, done = false;
@@ -186,11 +196,12 @@ struct LaneSys {
   cudaEvent_t ready = nullptr;  // server: b and x_1 written on the caller's stream
 };
 
-// Rows from which a lane's Gram runs on the tensor cores (one launch per
-// lane) by default; below it the lane joins the shared FP64 item launch,
-// which keeps the whole GPU busy with many small lanes at once. The
-// options can set another value (ascg_tune_gram_schedule measures one).
-constexpr int64_t kTcLaneRows = (int64_t)1 << 18;
+// Rows from which a lane's Gram runs on the tensor cores (all such lanes in
+// one launch over the shared basis matrix) by default; below it the lane
+// joins the FP64 item launch: a tensor-core lane reads whole 1024-row chunks,
+// so a very small system costs less in FP64. The options can set another
+// value (ascg_tune_gram_schedule measures one).
+constexpr int64_t kTcLaneRows = (int64_t)1 << 10;
 
 class Lockstep {
  public:
@@ -200,8 +211,10 @@ class Lockstep {
   // item capacities (they grow on demand); rcap, abcap: history capacities
   // per lane (0: none). All work is ordered on stream s.
   ascg_status init(const ascg_options& o, int lanes, int64_t gitems, int64_t ritems, int rcap, int abcap,
-                   cudaStream_t s) {
+                   double* basis, int64_t basis_ld, cudaStream_t s) {
     o_ = o;
+    ybase_ = basis;
+    yld_ = basis_ld;
     if (o.method == ASCG_VARIABLE_S) {  // keep a copy: the caller's array may go
       seq_.assign(o.s_seq, o.s_seq + o.s_seq_len);
       o_.s_seq = seq_.data();
@@ -213,6 +226,7 @@ class Lockstep {
     wcols_ = 2 * o.s_max + 1;
     moments_ = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
     tc_rows_ = o.tc_lane_rows == 0 ? kTcLaneRows : (o.tc_lane_rows < 0 ? INT64_MAX : o.tc_lane_rows);
+    tcnp_ = wcols_ * (wcols_ + 1) / 2;
     npw_ = (int)partials_per_item(o.s_max, moments_);
     LS_TRY(dalloc(&d_desc_, lanes));
     LS_TRY(dalloc(&d_bst_, lanes));
@@ -222,9 +236,8 @@ class Lockstep {
     LS_TRY(dalloc(&d_sums_, (size_t)2 * lanes));
     LS_TRY(dalloc(&d_params_, (size_t)3 * kMaxS));
     LS_TRY(dalloc(&d_spec_, (size_t)lanes * kSpecDoubles));
+    LS_TRY(dalloc(&d_emax_, (size_t)lanes * kMaxW));
     LS_TRY(dalloc(&d_tickets_, (size_t)lanes));
-    LS_TRY(dalloc(&d_tc_partials_, (size_t)gram_grid() * kMaxPairs));
-    LS_TRY(dalloc(&d_tc_exp_, (size_t)gram_grid() * kMaxW));
     if (rcap_) LS_TRY(dalloc(&d_res_hist_, (size_t)lanes * rcap_));
     if (abcap_) LS_TRY(dalloc(&d_ab_hist_, (size_t)lanes * 2 * abcap_));
     LS_TRY(halloc(&h_desc_, lanes));
@@ -253,9 +266,12 @@ class Lockstep {
 
   static int64_t gram_items_of(int64_t n) { return (n + gram_item_rows(n) - 1) / gram_item_rows(n); }
   static int64_t row_items_of(int64_t n) { return (n + kRowItem - 1) / kRowItem; }
-  // Basis bytes of a system of n rows: 2 s_max + 1 columns of round_up(n, 32).
+  // Tensor-core Gram items: up to kTcItemRows rows (whole 1024-row chunks) each.
+  static constexpr int64_t kTcItemRows = 8192;
+  static int64_t tc_items_of(int64_t n) { return (Arena::rounded(n) + kTcItemRows - 1) / kTcItemRows; }
+  // Basis bytes of a system of n rows: 2 s_max + 1 columns of round_up(n, 1024).
   static size_t basis_bytes(int s_max, int64_t n) {
-    return (size_t)(2 * s_max + 1) * round_up(n, kSlice) * sizeof(double);
+    return (size_t)(2 * s_max + 1) * Arena::rounded(n) * sizeof(double);
   }
   // Gram partials per item: the pairs' upper triangle, or the moment slots.
   static int64_t partials_per_item(int s_max, bool moments) {
@@ -264,8 +280,9 @@ class Lockstep {
   }
   // Device bytes one system holds while it runs: its basis and its Gram partials.
   static size_t footprint(int s_max, int64_t n, bool moments) {
-    return Arena::rounded(basis_bytes(s_max, n)) +
-           (size_t)gram_items_of(n) * partials_per_item(s_max, moments) * sizeof(double);
+    const int64_t w = 2 * s_max + 1;
+    return basis_bytes(s_max, n) + (size_t)gram_items_of(n) * partials_per_item(s_max, moments) * sizeof(double) +
+           (size_t)tc_items_of(n) * (w * (w + 1) / 2) * sizeof(double);
   }
 
   // Validates a system and fills its descriptor (all but Y).
@@ -281,7 +298,7 @@ class Lockstep {
     out->op = op;
     out->d.b = b;
     out->d.x = x;
-    out->d.ldY = round_up(out->d.n, kSlice);
+    out->d.ldY = 0;  // set at admission: the shared basis matrix's leading dimension
     out->eps_target = eps_target;
     out->tag = tag;
     out->bytes = basis_bytes(s_max, out->d.n);
@@ -308,6 +325,15 @@ class Lockstep {
     }
     if (lanes_out) *lanes_out = fresh;
     if (fresh.empty()) return ASCG_OK;
+    // rows n .. round_up(n, 1024) of every column are zero: the tensor-core
+    // Gram reads whole 1024-row chunks
+    for (int q : fresh) {
+      const LaneSys& L = lane_[q];
+      const int64_t pad = Arena::rounded(L.d.n) - L.d.n;
+      if (pad > 0)
+        LS_CUDA(cudaMemset2DAsync(L.d.Y + L.d.n, (size_t)L.d.ldY * sizeof(double), 0, (size_t)pad * sizeof(double),
+                                  (size_t)wcols_, s_));
+    }
     LS_TRY(rebuild_tables());
     int* h_sel = h_int_ + kSel * lanes_;
     int* h_list = h_int_ + kList * lanes_;
@@ -363,8 +389,8 @@ class Lockstep {
     int* h_steps = h_int_ + kSteps * lanes_;
     int* h_w = h_int_ + kW * lanes_;
     int* h_wi = h_int_ + kWItems * lanes_;
-    int max_sbar = 0;
-    tc_lanes_.clear();
+    int* h_wtc = h_int_ + kWTc * lanes_;
+    int max_sbar = 0, n_tc = 0;
     for (int q = 0; q < hi_; ++q) {
       BlockState& hb = h_bst_[q];
       std::memset(&hb, 0, sizeof(hb));
@@ -373,6 +399,7 @@ class Lockstep {
         h_steps[q] = 0;
         h_w[q] = 0;
         h_wi[q] = 0;
+        h_wtc[q] = 0;
         continue;
       }
       const int sbar = block_sbar(o_, L.kb, L.s_prev);
@@ -393,7 +420,8 @@ class Lockstep {
       h_w[q] = w;
       const bool tc = !moments_ && L.d.n >= tc_rows_ && gram_tc_applies(w) && gram_tc_aligned(L.d.Y, L.d.ldY);
       h_wi[q] = tc ? 0 : w;
-      if (tc) tc_lanes_.push_back(q);
+      h_wtc[q] = tc ? w : 0;
+      n_tc += tc;
       max_sbar = std::max(max_sbar, sbar);
     }
     if (max_sbar == 0) return ASCG_OK;
@@ -402,10 +430,14 @@ class Lockstep {
     int* d_wi = d_int_ + kWItems * lanes_;
     int* d_item0 = d_int_ + kItem0 * lanes_;
     int* d_nitems = d_int_ + kNItems * lanes_;
-    const int nr = (int)ritems_.size(), ng = (int)gitems_.size();
-    const bool item_gram = (int)tc_lanes_.size() < count_active();
+    int* d_wtc = d_int_ + kWTc * lanes_;
+    int* d_tc0 = d_int_ + kTcItem0 * lanes_;
+    int* d_tcn = d_int_ + kTcNItems * lanes_;
+    const int nr = (int)ritems_.size(), ng = (int)gitems_.size(), nt = (int)titems_.size();
+    const bool item_gram = n_tc < count_active();
+    const bool tc_gram = n_tc > 0;
     const int Wb = 2 * max_sbar + 1;
-    int nl = max_sbar + 2 + (item_gram ? 2 : 0) + 3 * (int)tc_lanes_.size();
+    int nl = max_sbar + 2 + (item_gram ? 2 : 0) + (tc_gram ? 3 : 0);
     // The block's work: the state records in, the matrix powers steps, the
     // Gram (item launch and tensor-core lanes), the controller, the recovery,
     // the state records out. The host fills the pinned records before each
@@ -415,6 +447,7 @@ class Lockstep {
       LS_CUDA(cudaMemcpyAsync(d_steps, h_steps, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_wi, h_wi, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_wtc, h_wtc, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
       if (item_gram) {
         // pair groups: enough CTAs to cover the SMs twice
@@ -422,11 +455,9 @@ class Lockstep {
         LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
         LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
       }
-      for (int q : tc_lanes_) {  // one lane at a time: the lanes share the partials buffer in stream order
-        const LaneSys& L = lane_[q];
-        int parts = 0;
-        LS_CUDA(launch_gram_any(L.d.n, h_w[q], L.d.Y, L.d.ldY, false, d_tc_exp_, false, d_tc_partials_, &parts, s_));
-        LS_CUDA(launch_gram_finalize(h_w[q], d_tc_partials_, parts, d_G_ + (int64_t)q * kGStride, s_));
+      if (tc_gram) {  // every tensor-core lane in one launch over the shared basis matrix
+        LS_CUDA(launch_gram_tc_items(Wb, ybase_, yld_, yld_, d_titems_, nt, d_wtc, hi_, d_emax_, d_tpart_, s_));
+        LS_CUDA(launch_gram_items_finalize(Wb, d_tpart_, d_tc0, d_tcn, d_wtc, hi_, d_G_, kGStride, false, s_));
       }
       LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_,
                                       hi_, max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_,
@@ -437,11 +468,7 @@ class Lockstep {
     };
     // A block of the same shape (tables, sbar_max, Gram schedule) replays a
     // captured graph: one launch instead of about twenty calls.
-    std::vector<int> key = {tables_version_, max_sbar, item_gram ? 1 : 0};
-    for (int q : tc_lanes_) {
-      key.push_back(q);
-      key.push_back(h_w[q]);
-    }
+    const std::vector<int> key = {tables_version_, max_sbar, item_gram ? 1 : 0, tc_gram ? 1 : 0};
     cudaGraphExec_t exec = nullptr;
     auto it = graphs_.find(key);
     if (it != graphs_.end()) {
@@ -623,12 +650,24 @@ class Lockstep {
   static constexpr int64_t kGStride = (int64_t)kMaxW * kMaxW;
   static constexpr int64_t kCStride = 3 * kMaxW;
   // int arrays of lanes entries each, in d_int_ and h_int_
-  enum { kSteps = 0, kW, kSel, kList, kItem0, kNItems, kWItems, kIntArrays };
+  enum { kSteps = 0, kW, kSel, kList, kItem0, kNItems, kWItems, kWTc, kTcItem0, kTcNItems, kIntArrays };
 
   int count_active() const {
     int c = 0;
     for (int q = 0; q < hi_; ++q) c += used_[q] && lane_[q].active;
     return c;
+  }
+
+  ascg_status grow_titems(int64_t titems) {
+    if (titems > tcap_items_) {
+      LS_CUDA(cudaStreamSynchronize(s_));
+      dfree(d_titems_);
+      dfree(d_tpart_);
+      tcap_items_ = std::max<int64_t>(titems, 2 * tcap_items_);
+      LS_TRY(dalloc(&d_titems_, (size_t)tcap_items_));
+      LS_TRY(dalloc(&d_tpart_, (size_t)tcap_items_ * tcnp_));
+    }
+    return ASCG_OK;
   }
 
   ascg_status grow_items(int64_t ritems, int64_t gitems) {
@@ -656,12 +695,23 @@ class Lockstep {
   ascg_status rebuild_tables() {
     ritems_.clear();
     gitems_.clear();
+    titems_.clear();
     int* h_item0 = h_int_ + kItem0 * lanes_;
     int* h_nitems = h_int_ + kNItems * lanes_;
+    int* h_tc0 = h_int_ + kTcItem0 * lanes_;
+    int* h_tcn = h_int_ + kTcNItems * lanes_;
     for (int q = 0; q < hi_; ++q) {
       h_item0[q] = (int)gitems_.size();
       h_nitems[q] = 0;
+      h_tc0[q] = (int)titems_.size();
+      h_tcn[q] = 0;
       if (!used_[q]) continue;
+      {  // whole 1024-row chunks of the lane's range in the shared basis matrix
+        const int64_t rows = Arena::rounded(lane_[q].d.n), first = lane_[q].off;
+        for (int64_t r = 0; r < rows; r += kTcItemRows)
+          titems_.push_back(GramItem{first + r, (int)std::min<int64_t>(kTcItemRows, rows - r), q});
+        h_tcn[q] = (int)titems_.size() - h_tc0[q];
+      }
       const int64_t n = lane_[q].d.n;
       for (int64_t r = 0; r < n; r += kRowItem)
         ritems_.push_back(RowItem{q, (int)r, (int)std::min<int64_t>(kRowItem, n - r), 0});
@@ -670,6 +720,9 @@ class Lockstep {
       h_nitems[q] = (int)gitems_.size() - h_item0[q];
     }
     LS_TRY(grow_items((int64_t)ritems_.size(), (int64_t)gitems_.size()));
+    LS_TRY(grow_titems((int64_t)titems_.size()));
+    if (!titems_.empty())
+      LS_CUDA(cudaMemcpyAsync(d_titems_, titems_.data(), sizeof(GramItem) * titems_.size(), cudaMemcpyHostToDevice, s_));
     if (!ritems_.empty())
       LS_CUDA(cudaMemcpyAsync(d_ritems_, ritems_.data(), sizeof(RowItem) * ritems_.size(), cudaMemcpyHostToDevice, s_));
     if (!gitems_.empty())
@@ -678,6 +731,8 @@ class Lockstep {
       LS_CUDA(cudaMemcpyAsync(d_desc_, h_desc_, sizeof(SysDesc) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_int_ + kItem0 * lanes_, h_item0, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_int_ + kNItems * lanes_, h_nitems, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + kTcItem0 * lanes_, h_tc0, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
+      LS_CUDA(cudaMemcpyAsync(d_int_ + kTcNItems * lanes_, h_tcn, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
     }
     dirty_ = false;
     ++tables_version_;
@@ -695,7 +750,7 @@ class Lockstep {
     drop_graphs();
     dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
     dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
-    dfree(d_tc_partials_); dfree(d_tc_exp_); dfree(d_spec_); dfree(d_tickets_);
+    dfree(d_titems_); dfree(d_tpart_); dfree(d_emax_); dfree(d_spec_); dfree(d_tickets_);
     hfree(h_desc_); hfree(h_bst_); hfree(h_int_); hfree(h_sums_);
   }
 
@@ -714,7 +769,7 @@ class Lockstep {
   std::vector<char> used_;
   std::vector<RowItem> ritems_;
   std::vector<GramItem> gitems_;
-  std::vector<int> tc_lanes_;
+  std::vector<GramItem> titems_;
   int64_t rcap_items_ = 0, gcap_items_ = 0;
   SysDesc* d_desc_ = nullptr;
   BlockState* d_bst_ = nullptr;
@@ -728,8 +783,13 @@ class Lockstep {
   RowItem* d_ritems_ = nullptr;
   GramItem* d_gitems_ = nullptr;
   double* d_partials_ = nullptr;
-  double* d_tc_partials_ = nullptr;
-  int* d_tc_exp_ = nullptr;
+  double* ybase_ = nullptr;  // the shared basis matrix (leading dimension yld_)
+  int64_t yld_ = 0;
+  GramItem* d_titems_ = nullptr;  // tensor-core Gram items (row ranges in the shared matrix)
+  double* d_tpart_ = nullptr;     // their partials, tcnp_ each
+  int* d_emax_ = nullptr;         // per-lane column exponents, kMaxW each
+  int64_t tcap_items_ = 0;
+  int tcnp_ = 0;
   double* d_spec_ = nullptr;      // speculative coordinate steps, kSpecDoubles per lane
   unsigned* d_tickets_ = nullptr;  // the block controller's ticket counters, one per lane
   SysDesc* h_desc_ = nullptr;
@@ -773,24 +833,25 @@ ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* co
   LS_TRY(own.open(user_stream));
   const cudaStream_t s = own.s;
   std::vector<LaneSys> sys(count);
-  size_t y_bytes = 0;
-  int64_t gi = 0, ri = 0;
+  int64_t y_rows = 0, gi = 0, ri = 0;
   for (int q = 0; q < count; ++q) {
     LS_TRY(Lockstep::prepare(o.s_max, ops[q], b[q], x[q], eps_target ? eps_target[q] : o.eps_target, q, &sys[q]));
-    y_bytes += Arena::rounded(sys[q].bytes);
+    y_rows += Arena::rounded(sys[q].d.n);
     gi += Lockstep::gram_items_of(sys[q].d.n);
     ri += Lockstep::row_items_of(sys[q].d.n);
   }
+  if (y_rows > 0x7fffffffll) return lfail(ASCG_ERR_INVALID, "the batch exceeds 2^31 rows");
   Arena arena;  // destroyed after the engine and its stream's work (declaration order)
-  LS_TRY(arena.init(y_bytes));
+  LS_TRY(arena.init(2 * o.s_max + 1, y_rows));
   for (int q = 0; q < count; ++q) {
-    if (!arena.take(sys[q].bytes, &sys[q].off)) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
-    sys[q].d.Y = arena.at(sys[q].off);
+    if (!arena.take(sys[q].d.n, &sys[q].off)) return lfail(ASCG_ERR_OOM, "the batch does not fit its own arena");
+    sys[q].d.Y = arena.row(sys[q].off);
+    sys[q].d.ldY = arena.ld();
   }
   const int rcap = o.res_hist ? std::max(o.res_hist_cap, 1) : 0;
   const int abcap = (o.alpha_hist && o.beta_hist) ? std::max(o.coef_hist_cap, 1) : 0;
   Lockstep eng;
-  LS_TRY(eng.init(o, count, gi, ri, rcap, abcap, s));
+  LS_TRY(eng.init(o, count, gi, ri, rcap, abcap, arena.base(), arena.ld(), s));
   LS_TRY(eng.admit(sys, nullptr));
   for (int q = 0; q < count; ++q)
     if (eng.lane(q).status == ASCG_ERR_INVALID) return lfail(ASCG_ERR_INVALID, "b or x_1 is not finite");
@@ -912,11 +973,12 @@ struct ascg_server_s {
         continue;
       }
       if (running >= max_systems) break;
-      size_t off = 0;
-      if (!arena.take(it->bytes, &off)) break;
+      int64_t off = 0;
+      if (!arena.take(it->d.n, &off)) break;
       LaneSys L = *it;
       L.off = off;
-      L.d.Y = arena.at(off);
+      L.d.Y = arena.row(off);
+      L.d.ldY = arena.ld();
       if (L.ready) {
         LS_CUDA(cudaStreamWaitEvent(g.stream, L.ready, 0));
         cudaEventDestroy(L.ready);
@@ -979,13 +1041,17 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   const int64_t npw = Lockstep::partials_per_item(o.s_max, (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0);
   const int64_t rows_max = hbm_budget / (wcols * (int64_t)sizeof(double));
   const int64_t gitems = rows_max / kGramItemRowsMin + max_systems;
-  const int64_t part_bytes = gitems * npw * (int64_t)sizeof(double);
-  const int64_t y_bytes = std::max<int64_t>(hbm_budget - part_bytes, 0);
+  const int64_t titems = rows_max / Lockstep::kTcItemRows + max_systems;
+  const int64_t part_bytes = (gitems * npw + titems * (wcols * (wcols + 1) / 2)) * (int64_t)sizeof(double);
+  const int64_t y_rows = std::min<int64_t>(std::max<int64_t>(hbm_budget - part_bytes, 0) /
+                                               (wcols * (int64_t)sizeof(double)) / Arena::kRowAlign *
+                                               Arena::kRowAlign,
+                                           0x7fffffffll / Arena::kRowAlign * Arena::kRowAlign);
   auto fail_free = [&](ascg_status st) {
     delete srv;
     return st;
   };
-  ascg_status st = srv->arena.init((size_t)y_bytes);
+  ascg_status st = srv->arena.init((int)wcols, y_rows);
   if (st != ASCG_OK) return fail_free(st);
   // Stream priorities: the smallest class highest, so that as the CTAs of a
   // large class's kernels retire, the SMs go to waiting small-class CTAs first.
@@ -997,7 +1063,7 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
     cudaError_t e = cudaStreamCreateWithPriority(&g.stream, cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&g.done, cudaEventDisableTiming);
     if (e != cudaSuccess) return fail_free(lfail(ASCG_ERR_CUDA, std::string("stream: ") + cudaGetErrorString(e)));
-    st = g.eng.init(o, max_systems, gitems / kGroups + 1, 1024, 0, 0, g.stream);
+    st = g.eng.init(o, max_systems, gitems / kGroups + 1, 1024, 0, 0, srv->arena.base(), srv->arena.ld(), g.stream);
     if (st != ASCG_OK) return fail_free(st);
   }
   *out = srv;
@@ -1017,7 +1083,7 @@ ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, dou
   LaneSys L;
   LS_TRY(Lockstep::prepare(srv->o.s_max, op, b, x, eps_target, tag, &L));
   if (Lockstep::footprint(srv->o.s_max, L.d.n, (srv->o.flags & ASCG_FLAG_MOMENT_GRAM) != 0) > srv->budget ||
-      Arena::rounded(L.bytes) > srv->arena.size())
+      L.bytes > srv->arena.bytes_total())
     return lfail(ASCG_ERR_INVALID, "the system needs more device memory than the server's budget");
   LS_CUDA(cudaEventCreateWithFlags(&L.ready, cudaEventDisableTiming));
   cudaError_t e = cudaEventRecord(L.ready, srv->user);
@@ -1107,31 +1173,32 @@ ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* ta
   constexpr int kLogMin = 12, kLogMax = 22, kReps = 5;
   const int64_t ld = (int64_t)1 << kLogMax;
   struct Bufs {
-    double *Y = nullptr, *G = nullptr, *part = nullptr, *tcp = nullptr;
-    int *ints = nullptr, *exps = nullptr;
+    double *Y = nullptr, *G = nullptr, *part = nullptr, *tpart = nullptr;
+    int *ints = nullptr, *emax = nullptr;
     SysDesc* desc = nullptr;
-    GramItem* items = nullptr;
+    GramItem *items = nullptr, *titems = nullptr;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     ~Bufs() {
-      dfree(Y); dfree(G); dfree(part); dfree(tcp); dfree(ints); dfree(exps); dfree(desc); dfree(items);
+      dfree(Y); dfree(G); dfree(part); dfree(tpart); dfree(ints); dfree(emax); dfree(desc); dfree(items);
+      dfree(titems);
       if (e0) cudaEventDestroy(e0);
       if (e1) cudaEventDestroy(e1);
     }
   } B;
-  const int64_t max_items = ld / kGramItemRowsMin + 1;
+  const int64_t max_items = ld / kGramItemRowsMin + 1, max_titems = ld / Lockstep::kTcItemRows + 1;
   const int64_t np = (int64_t)w * (w + 1) / 2;
   LS_TRY(dalloc(&B.Y, (size_t)w * ld));
   LS_TRY(dalloc(&B.G, (size_t)kMaxW * kMaxW));
   LS_TRY(dalloc(&B.part, (size_t)max_items * np));
-  LS_TRY(dalloc(&B.tcp, (size_t)gram_grid() * kMaxPairs));
-  LS_TRY(dalloc(&B.exps, (size_t)gram_grid() * kMaxW));
-  LS_TRY(dalloc(&B.ints, 3));
+  LS_TRY(dalloc(&B.tpart, (size_t)max_titems * np));
+  LS_TRY(dalloc(&B.emax, (size_t)kMaxW));
+  LS_TRY(dalloc(&B.ints, 5));
   LS_TRY(dalloc(&B.desc, 1));
   LS_TRY(dalloc(&B.items, (size_t)max_items));
+  LS_TRY(dalloc(&B.titems, (size_t)max_titems));
   LS_CUDA(cudaEventCreate(&B.e0));
   LS_CUDA(cudaEventCreate(&B.e1));
   LS_CUDA(launch_fill_uniform(B.Y, (int64_t)w * ld, 0x5eed5eedull, s));
-  const int hint[3] = {w, 0, 0};  // sys_w, item0, nitems (set per size)
   std::vector<double> t_fp(kLogMax + 1), t_tc(kLogMax + 1);
   int nrow = 0;
   for (int lg = kLogMin; lg <= kLogMax; ++lg) {
@@ -1140,13 +1207,17 @@ ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* ta
     d.n = n;
     d.Y = B.Y;
     d.ldY = ld;
-    std::vector<GramItem> items;
+    std::vector<GramItem> items, titems;
     const int64_t gr = gram_item_rows(n);
     for (int64_t r = 0; r < n; r += gr) items.push_back(GramItem{r, (int)std::min<int64_t>(gr, n - r), 0});
-    const int ng = (int)items.size();
-    const int ints[3] = {hint[0], 0, ng};
+    const int64_t padded = Arena::rounded(n);
+    for (int64_t r = 0; r < padded; r += Lockstep::kTcItemRows)
+      titems.push_back(GramItem{r, (int)std::min<int64_t>(Lockstep::kTcItemRows, padded - r), 0});
+    const int ng = (int)items.size(), nt = (int)titems.size();
+    const int ints[5] = {w, 0, ng, 0, nt};  // sys_w, item0, nitems, tc item0, tc nitems
     LS_CUDA(cudaMemcpyAsync(B.desc, &d, sizeof(d), cudaMemcpyHostToDevice, s));
     LS_CUDA(cudaMemcpyAsync(B.items, items.data(), sizeof(GramItem) * ng, cudaMemcpyHostToDevice, s));
+    LS_CUDA(cudaMemcpyAsync(B.titems, titems.data(), sizeof(GramItem) * nt, cudaMemcpyHostToDevice, s));
     LS_CUDA(cudaMemcpyAsync(B.ints, ints, sizeof(ints), cudaMemcpyHostToDevice, s));
     LS_CUDA(cudaStreamSynchronize(s));  // the host arrays above are locals
     const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / ng));
@@ -1160,10 +1231,9 @@ ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* ta
       float ms = 0.f;
       LS_CUDA(cudaEventElapsedTime(&ms, B.e0, B.e1));
       if (rep > 0) a[rep - 1] = ms;
-      int parts = 0;
       LS_CUDA(cudaEventRecord(B.e0, s));
-      LS_CUDA(launch_gram_any(n, w, B.Y, ld, false, B.exps, false, B.tcp, &parts, s));
-      LS_CUDA(launch_gram_finalize(w, B.tcp, parts, B.G, s));
+      LS_CUDA(launch_gram_tc_items(w, B.Y, ld, ld, B.titems, nt, B.ints, 1, B.emax, B.tpart, s));
+      LS_CUDA(launch_gram_items_finalize(w, B.tpart, B.ints + 3, B.ints + 4, B.ints, 1, B.G, kMaxW * kMaxW, false, s));
       LS_CUDA(cudaEventRecord(B.e1, s));
       LS_CUDA(cudaEventSynchronize(B.e1));
       LS_CUDA(cudaEventElapsedTime(&ms, B.e0, B.e1));
@@ -1181,15 +1251,21 @@ ascg_status ascg_tune_gram_schedule(int s_max, int64_t* tc_lane_rows, double* ta
     }
   }
   if (rows) *rows = nrow;
-  // In a batch the FP64 items of every lane share one launch that fills the
-  // GPU, so a lane's FP64 cost is its rows times the per-row cost at full
-  // load (taken at the largest size); a tensor-core lane runs alone. The
-  // threshold is the smallest size from which the tensor cores win at every
-  // larger size.
-  const double per_row = t_fp[kLogMax] / (double)((int64_t)1 << kLogMax);
-  int from = kLogMax + 1;
-  for (int lg = kLogMax; lg >= kLogMin && t_tc[lg] < per_row * (double)((int64_t)1 << lg); --lg) from = lg;
-  *tc_lane_rows = from <= kLogMax ? ((int64_t)1 << from) : -1;
+  // In a batch both kinds of Gram run as one launch over all lanes that fills
+  // the GPU, so each costs its per-row rate at full load (taken at the largest
+  // size) times the rows it reads: n for the FP64 items, round_up(n, 1024) for
+  // the tensor cores. The threshold is the smallest power of two n >= 2^8 from
+  // which the tensor cores cost less at every larger size.
+  const double c_fp = t_fp[kLogMax] / (double)ld, c_tc = t_tc[kLogMax] / (double)ld;
+  int from = 31;
+  for (int lg = 30; lg >= 8; --lg) {
+    const int64_t m = (int64_t)1 << lg;
+    if (c_tc * (double)Arena::rounded(m) < c_fp * (double)m)
+      from = lg;
+    else
+      break;
+  }
+  *tc_lane_rows = from <= 30 ? ((int64_t)1 << from) : -1;
   return ASCG_OK;
 }
 
@@ -1197,8 +1273,8 @@ ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* st) {
   if (!srv || !st) return lfail(ASCG_ERR_INVALID, "bad argument");
   std::memset(st, 0, sizeof(*st));
   st->budget_bytes = (int64_t)srv->budget;
-  st->basis_bytes_used = (int64_t)srv->arena.used();
-  st->basis_bytes_total = (int64_t)srv->arena.size();
+  st->basis_bytes_used = (int64_t)srv->arena.bytes_used();
+  st->basis_bytes_total = (int64_t)srv->arena.bytes_total();
   st->systems_running = srv->running;
   st->max_systems = srv->max_systems;
   st->queued = (int64_t)srv->queue.size();

@@ -47,10 +47,12 @@ def gram_item_rows(n):
 
 
 def footprint(n, s_max=S_MAX):
+    """Device bytes the server counts for a system: basis rows rounded to 1024,
+    FP64 Gram partials per item and tensor-core Gram partials per 8192 rows."""
     w = 2 * s_max + 1
-    ld = (n + 31) // 32 * 32
-    y = (w * ld * 8 + 255) // 256 * 256
-    return y + -(-n // gram_item_rows(n)) * (w * (w + 1) // 2) * 8
+    rows = -(-n // 1024) * 1024
+    np_ = w * (w + 1) // 2
+    return w * rows * 8 + -(-n // gram_item_rows(n)) * np_ * 8 + -(-rows // 8192) * np_ * 8
 
 
 def solve_alone(P, torch, op, b, x1, eps, max_iters=4000):
