@@ -1,29 +1,32 @@
 // Lockstep engine: many independent SPD systems, each running Alg. 4 (or
-// Alg. 2) on its own operator, advance one block at a time together. It is
-// the engine behind ascg_solve_batch and the solve server (ascg_server_*).
+// Alg. 2, Alg. 3) on its own operator, advance one block at a time together.
+// It is the engine behind ascg_solve_batch and the solve server
+// (ascg_server_*).
 //
 // Every system sits in a lane. A lane holds the system's descriptor (its
 // operator, its basis Y, x and b), its controller state and its Gram and
 // coordinate slots. One "super-block" runs one block of every active lane:
 //   sbar_max matrix powers steps  (mpk_items_kernel, one row item per CTA)
-//   Gram partials and their fixed-order sum  (gram_items_kernel, finalize)
-//   condition estimates, controller  (kappa_kernel, ctrl_kernel, per lane)
+//   Gram: tensor-core lanes in one launch (gram_tc_items_kernel), the other
+//         lanes in one FP64 launch (gram_items_kernel), fixed-order sums
+//   condition estimates and coordinate steps  (block_ctrl_kernel, per lane)
 //   recovery  (recover_items_kernel)
-// so a super-block is the same dozen launches for any number of systems.
-// The host reads back one BlockState per lane, since the next block's basis
-// size sbar_k = min(s_{k-1} + f, s_max) depends on it (Alg. 4).
+// so a super-block is the same dozen launches for any number of systems,
+// replayed as one captured graph while its shape stays the same. The host
+// reads back one BlockState per lane, since the next block's basis size
+// sbar_k = min(s_{k-1} + f, s_max) depends on it (Alg. 4).
 //
 // Each lane's arithmetic reads that lane's data only, in an order fixed by
 // its own size: a system's result is bitwise the same alone and in any mix,
 // whichever lane it lands in and whoever else is running.
 //
-// The bases live in one device arena (first-fit, merging free neighbours)
-// owned by the caller of the engine, so admitting and retiring systems
-// allocates nothing from CUDA.
+// The bases are row ranges of one shared matrix (first-fit over 1024-row
+// chunks) owned by the caller of the engine: admitting and retiring systems
+// allocates nothing from CUDA, and one tensor map covers every lane.
 //
 // Gram schedule per lane, fixed by the lane's own size: lanes of at least
-// kTcLaneRows rows (and w >= 9) take the tensor-core Gram kernel, one launch
-// per lane; all other lanes share one launch of the FP64 item kernel.
+// tc_lane_rows rows (default 1024) with w >= 9 take the tensor-core launch;
+// the others the FP64 one.
 #include <algorithm>
 #include <chrono>
 #include <climits>
