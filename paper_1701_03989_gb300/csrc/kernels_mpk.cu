@@ -241,11 +241,14 @@ template <int W>
 cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
                             double* p, int x_ctas, cudaStream_t s) {
   if (x) {
-    static bool attr = false;  // once per process: the attribute is per function
-    if (!attr) {
-      cudaError_t e = cudaFuncSetAttribute(recover_x_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXReserve);
+    static int attr_dev = -1;  // the attribute is set once per device and instance
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (attr_dev != dev) {
+      e = cudaFuncSetAttribute(recover_x_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXReserve);
       if (e != cudaSuccess) return e;
-      attr = true;
+      attr_dev = dev;
     }
     recover_x_kernel<W><<<x_ctas, kXThreads, kXReserve, s>>>(n, Y, ldY, coords, x);
   } else {
