@@ -82,6 +82,21 @@ def parse():
     return ap.parse_args()
 
 
+def job_totals(elapsed, units, world, device):
+    """Whole-job figures over the ranks (replicas): the slowest rank's elapsed
+    time and the sum of all ranks' units of work."""
+    if world == 1:
+        return float(elapsed), float(units)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed), float(units)], dtype=torch.float64, device=device)
+    tmax = t.clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    tsum = t.clone()
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[1])
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -298,15 +313,7 @@ def our_arm(args):
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
     iters = sum(r.iters for r in results)
-    if world > 1:
-        t = torch.tensor([ms, float(iters)], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
-        tsum = t.clone()
-        dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
-        ms_job, iters_job = float(tmax[0]), float(tsum[1])
-    else:
-        ms_job, iters_job = ms, float(iters)
+    ms_job, iters_job = job_totals(ms, iters, world, "cuda")
     value = iters_job / (ms_job * 1e-3)
     ok = all(r.status == P.ASCG_OK for r in results)
 
@@ -348,13 +355,7 @@ def our_arm(args):
         e2e_iters += r.iters
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s, float(e2e_iters)], dtype=torch.float64, device="cuda")
-        tm = t.clone()
-        dist.all_reduce(tm, op=dist.ReduceOp.MAX)
-        ts = t.clone()
-        dist.all_reduce(ts, op=dist.ReduceOp.SUM)
-        e2e_s, e2e_iters = float(tm[0]), float(ts[1])
+    e2e_s, e2e_iters = job_totals(e2e_s, e2e_iters, world, "cuda")
     e2e_value = e2e_iters / e2e_s
 
     # classical CG on the same GPU, same problem, same target
