@@ -269,3 +269,43 @@ def test_gram_schedule_autotuner(env):
         exempt, bad = parity.compare_block_sequences(g["blocks"], orc.blocks, s["A"].n, orc.res_hist, s["eps"])
         assert not bad, (s["name"], bad)
         assert parity.final_residual_ok(g["res"].rel_res_true, orc.true_res, s["eps"], exempt), s["name"]
+
+
+def test_full_size_batch_workload(env):
+    """The batched workload at full size, as the bench runs it (256 systems, n
+    log-uniform in [1e3, 2e5], seed 1004, adaptive monomial s_max = 10): every
+    system converges with its true residual near its target; the five smallest
+    systems meet the history and final-residual rules against the oracle; the
+    largest system's x is bitwise the same solved alone."""
+    P, torch = env
+    systems = W.batch_systems(256)
+    cap = 20000
+    ops = [make_op(P, s["A"]) for s in systems]
+    bs = [dev(torch, s["b"]) for s in systems]
+    xs = [torch.zeros(s["A"].n, dtype=torch.float64, device="cuda") for s in systems]
+    res_hist = np.zeros((len(systems), cap + 2))
+    o = P.make_options(method="adaptive", basis="monomial", s_max=S_MAX, eps_target=1e-10, max_iters=cap,
+                       res_hist=res_hist.reshape(-1))
+    o.res_hist_cap = cap + 2
+    results, st = P.ascg_solve_batch(ops, bs, xs, o, eps_targets=[s["eps"] for s in systems])
+    assert st == P.ASCG_OK and all(r.status == P.ASCG_OK for r in results)
+    for s, r in zip(systems, results):
+        assert r.rel_res_updated <= s["eps"] and r.rel_res_true <= 4 * s["eps"], (s["name"], r.rel_res_true)
+    order = sorted(range(len(systems)), key=lambda q: systems[q]["A"].n)
+    for q in order[:5]:
+        s = systems[q]
+        orc = O.adaptive_sstep_cg(O.Operator.from_csr(s["A"]), s["b"], s["x1"], s_max=S_MAX, eps_target=s["eps"],
+                                  basis="monomial", max_iters=cap)
+        k = min(21, results[q].iters + 1, len(orc.res_hist), s["A"].n)
+        ho = np.asarray(orc.res_hist[:k])
+        tau = parity.history_tolerance(orc.blocks, ho, k)
+        assert np.all(np.abs(res_hist[q, :k] - ho) <= tau), s["name"]
+        exempt = None if results[q].iters == orc.iters else 0
+        assert parity.final_residual_ok(results[q].rel_res_true, orc.true_res, s["eps"], exempt), s["name"]
+    big = order[-1]
+    x_alone = torch.zeros_like(xs[big])
+    oa = P.make_options(method="adaptive", basis="monomial", s_max=S_MAX, eps_target=1e-10, max_iters=cap)
+    P.ascg_solve_batch([ops[big]], [bs[big]], [x_alone], oa, eps_targets=[systems[big]["eps"]])
+    assert torch.equal(x_alone, xs[big])
+    for op in ops:
+        P.ascg_op_destroy(op)

@@ -261,3 +261,37 @@ def test_server_iteration_cap(env):
     r, xa = solve_alone(P, torch, op, s["b"], s["x1"], s["eps"], max_iters=9)
     assert np.array_equal(x, xa)
     P.ascg_op_destroy(op)
+
+
+def test_served_stream_full_size_pool(env):
+    """Requests drawn from the served workload's operator pool (sizes at
+    log-uniform quantiles of [1e4, 4e6]) and targets, all submitted at once to a
+    server with the default budget split: every request converges, and the
+    three smallest are bitwise the same solved alone."""
+    P, torch = env
+    pool = W.serve_pool()
+    req = W.serve_requests(24)
+    ops = [make_op(P, p["A"]) for p in pool]
+    nop = [p["A"].n for p in pool]
+    rng = np.random.default_rng(99)
+    systems = []
+    for i in range(len(req["op"])):
+        n = nop[req["op"][i]]
+        systems.append(dict(name=f"req{i}_{n}", A=pool[req["op"][i]]["A"], b=W.rhs_uniform(n, rng), x1=np.zeros(n),
+                            eps=float(req["eps"][i])))
+    sys_ops = [ops[req["op"][i]] for i in range(len(systems))]
+    srv = P.ascg_server_create(opts(P, max_iters=60000), 40 * (1 << 30), 64)
+    try:
+        served, _ = serve(P, torch, srv, systems, sys_ops, [(list(range(len(systems))), 0)])
+    finally:
+        P.ascg_server_destroy(srv)
+    for q, s in enumerate(systems):
+        c, _ = served[q]
+        assert c.result.status == P.ASCG_OK, s["name"]
+        assert c.result.rel_res_updated <= s["eps"] and c.result.rel_res_true <= 4 * s["eps"], s["name"]
+    for q in sorted(range(len(systems)), key=lambda q: systems[q]["A"].n)[:3]:
+        r, xa = solve_alone(P, torch, sys_ops[q], systems[q]["b"], systems[q]["x1"], systems[q]["eps"],
+                            max_iters=60000)
+        assert np.array_equal(served[q][1], xa), systems[q]["name"]
+    for op in ops:
+        P.ascg_op_destroy(op)
