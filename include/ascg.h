@@ -223,19 +223,24 @@ ascg_status ascg_solve_host(ascg_op op, const double* b, double* x, const ascg_o
  *    eps_target[q] ||b_q||), or NULL for opts->eps_target.
  *  - opts: method ASCG_ADAPTIVE, ASCG_FIXED_S or ASCG_VARIABLE_S, basis
  *    ASCG_MONOMIAL (the other bases need per-system parameters and are not
- *    batched); s_max, s0, f, s_seq, c, check_in_loop and max_iters apply to
- *    every system. Histories are per
- *    system: res_hist is count x res_hist_cap, block_hist count x
- *    block_hist_cap, alpha_hist and beta_hist count x coef_hist_cap (row q is
- *    system q); the caps must be >= 1 when the arrays are given.
+ *    batched); s_max, s0, f, s_seq, c, check_in_loop, max_iters,
+ *    tc_lane_rows and ASCG_FLAG_MOMENT_GRAM apply to every system
+ *    (ASCG_FLAG_C_FORMULA is refused). Histories are per system: res_hist is
+ *    count x res_hist_cap, block_hist count x block_hist_cap, alpha_hist and
+ *    beta_hist count x coef_hist_cap (row q is system q); the caps must be
+ *    >= 1 when the arrays are given.
  *  - results: host ascg_result[count] or NULL: per system status, iters,
  *    blocks, wasted_vecs, bnorm, rel_res_updated, rel_res_true; launches holds
  *    the number of lockstep blocks of the whole call. Device times are not
  *    recorded.
- * Temporary device memory: (2 s_max + 1) 8 round_up(n_q, 32) bytes of basis
- * per system plus (2 s_max + 1)(s_max + 1) 8 bytes of Gram partials per Gram
- * item (items of 1024 to 8192 rows: about n_q/16 as a power of two). Returns ASCG_OK when every system converged, else ASCG_NOT_CONVERGED
- * or ASCG_ERR_BREAKDOWN (the worst over the systems; results[q].status tells
+ * Temporary device memory: the bases, (2 s_max + 1) 8 round_up(n_q, 1024)
+ * bytes per system as row ranges of one shared matrix, plus (2 s_max + 1)
+ * (s_max + 1) 8 bytes of Gram partials per FP64 Gram item (1024 to 8192
+ * rows: about n_q/16 as a power of two) and per tensor-core Gram item (8192
+ * rows). n_tot = the sum of round_up(n_q, 1024) must be < 2^31. Runs on a
+ * stream of its own, ordered after the caller's stream's earlier work.
+ * Returns ASCG_OK when every system converged, else ASCG_NOT_CONVERGED or
+ * ASCG_ERR_BREAKDOWN (the worst over the systems; results[q].status tells
  * which); ASCG_ERR_INVALID if some b or x_1 is not finite. Synchronises the
  * stream. */
 ascg_status ascg_solve_batch(int count, const ascg_op* ops, const double* const* b, double* const* x,
@@ -385,13 +390,14 @@ typedef struct {
 
 /* Creates a server. opts: as for ascg_solve_batch (an s-step method, the
  * MONOMIAL basis; s_seq is copied), history buffers NULL; eps_target is per
- * request. hbm_budget:
- * device bytes the server may hold for running systems. A system of n rows
- * holds (2 s_max + 1) 8 round_up(n, 32) bytes of basis plus (2 s_max + 1)
- * (s_max + 1) 8 bytes of Gram partials per Gram item (1024 to 8192 rows,
- * about n/16 as a power of two); the whole budget is
- * allocated here, as one arena for the bases and one buffer for the
- * partials (plus about 16 bytes per 256 rows of row tables outside it).
+ * request. hbm_budget: device bytes the server may hold for running
+ * systems. A system of n rows holds (2 s_max + 1) 8 round_up(n, 1024) bytes
+ * of basis (a row range of one shared matrix) plus (2 s_max + 1)(s_max + 1)
+ * 8 bytes of Gram partials per FP64 Gram item (1024 to 8192 rows, about n/16
+ * as a power of two) and per tensor-core Gram item (8192 rows). The basis
+ * matrix takes the budget less the partials' share and is allocated here;
+ * the partial and row-table buffers (about 16 bytes per 256 rows) grow on
+ * demand within that share.
  * max_systems: most systems running at once (1 .. 2^20). cuda_stream: the
  * caller's stream, which orders submissions after the caller's work; the
  * server runs its blocks on streams of its own. The operators are the
