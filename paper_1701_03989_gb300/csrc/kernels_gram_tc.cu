@@ -231,15 +231,7 @@ __device__ __forceinline__ void split_z(double y, int emax, uint32_t& zlo, uint3
   const uint32_t Mlo = lo << 3;
   int s = emax + 1 - (e > 1 ? e : 1);
   s = s < 63 ? s : 63;
-  uint32_t ylo, yhi;
-  if (s < 32) {
-    ylo = __funnelshift_r(Mlo, Mhi, s);
-    yhi = Mhi >> s;
-  } else {
-    ylo = Mhi >> (s - 32);
-    yhi = 0u;
-  }
-  unsigned long long Y = ((unsigned long long)yhi << 32) | ylo;
+  unsigned long long Y = (((unsigned long long)Mhi << 32) | Mlo) >> s;
   if (hi < 0) Y = 0ull - Y;
   const unsigned long long Z = Y + 0x0080808080808080ull;
   zlo = (uint32_t)Z;
@@ -264,52 +256,67 @@ __device__ __forceinline__ uint32_t digit_pair(uint32_t zlo0, uint32_t zhi0, uin
   return *reinterpret_cast<const uint32_t*>(&h);
 }
 
-// Operand row of digit i of column a (see the layout above).
-__device__ __forceinline__ int digit_row(int i, int a) {
-  if (i <= 3) return a <= 31 ? 32 * i + a : 128 + i;
-  return a <= 31 ? 144 + 32 * (i - 4) + a : 132 + (i - 4);
+// The conversion work of one worker thread, the same in every stage. Thread
+// t < 528 takes rows 4 g .. 4 g + 3 of column a, with t = 66 q + 2 a + (g & 1)
+// and q = g >> 1: a warp covers 16 columns for both halves g & 1 of a
+// core-matrix row, so its digit stores fill whole 128-byte rows of the
+// operand (no bank conflicts), and its staging loads (column stride 528 B)
+// spread over all banks. Digit i of the item goes to byte offset
+// base + i * 4096 (+ 2048 for i >= 4) of the stage when a <= 31 (operand rows
+// 32 i + a, or 32 i + 16 + a for i >= 4), and to base + 16 i when a = 32
+// (row 128 + i); see the layout above. Three registers stay live.
+struct ConvItem {
+  uint32_t src;   // byte offset of the item's four values in an FP64 stage; ~0u: no item
+  int ex;         // column a's largest biased exponent, plus 1 << 16 when a = 32
+  uint32_t base;  // byte offset of digit 0 in a digit stage
+};
+
+__device__ __forceinline__ ConvItem conv_item(int ptid, int w, const int* s_emax) {
+  ConvItem c;
+  const int q = ptid / 66, rem = ptid - 66 * q;
+  const int a = rem >> 1, g = 2 * q + (rem & 1);
+  const bool on = ptid < 16 * kTW && a < w;
+  const int aa = on ? a : 0;
+  c.src = on ? (uint32_t)(aa * kColStride + g * 32) : ~0u;
+  c.ex = s_emax[aa] | (aa == 32 ? 1 << 16 : 0);
+  const uint32_t gb = (uint32_t)((g >> 1) * kLBO + (g & 1) * 8);
+  c.base = aa <= 31 ? gb + (uint32_t)((aa >> 3) * kSBO + (aa & 7) * 16) : gb + 16 * kSBO;
+  return c;
 }
 
-// Converts one stage: rows [row0, row0 + 64) of Y from the FP64 staging box
-// (column a at a * 528 B; zeros past n) into the digit operand. Item (g, a):
-// rows 4 g .. 4 g + 3 of column a, i.e. half a core-matrix row (8 bytes) per
-// digit. Consecutive threads take consecutive columns, so the staging loads
-// (stride 528 B) and the digit stores (consecutive operand rows) do not
-// collide in the shared-memory banks.
-__device__ __forceinline__ void convert_stage(unsigned char* dst, const unsigned char* fst, int w, const int* s_emax,
-                                              int ptid) {
-  const int items = 16 * w;
-  for (int it = ptid; it < items; it += kWorkWarps * 32) {
-    const int g = it / w;
-    const int a = it - g * w;
-    const double2* src = reinterpret_cast<const double2*>(fst + a * kColStride + g * 32);
-    const int emax = s_emax[a];
-    const double2 t0 = src[0], t1 = src[1];
-    uint32_t zlo[4], zhi[4];
-    split_z(t0.x, emax, zlo[0], zhi[0]);
-    split_z(t0.y, emax, zlo[1], zhi[1]);
-    split_z(t1.x, emax, zlo[2], zhi[2]);
-    split_z(t1.y, emax, zlo[3], zhi[3]);
-    unsigned char* base = dst + (g >> 1) * kLBO + (g & 1) * 8;
+// Converts the thread's item of one stage: rows [row0, row0 + 64) of Y from
+// the FP64 staging box (column a at a * 528 B; zeros past n) into the digit
+// operand.
+__device__ __forceinline__ void convert_item(unsigned char* dst, const unsigned char* fst, const ConvItem& c) {
+  const double2* src = reinterpret_cast<const double2*>(fst + c.src);
+  const int emax = c.ex & 0xFFFF;
+  const bool last = c.ex >= (1 << 16);
+  const uint32_t stride = last ? 16u : 4u * kSBO;
+  const uint32_t base_hi = last ? c.base : c.base + 2u * kSBO;
+  const double2 t0 = src[0], t1 = src[1];
+  uint32_t zlo[4], zhi[4];
+  split_z(t0.x, emax, zlo[0], zhi[0]);
+  split_z(t0.y, emax, zlo[1], zhi[1]);
+  split_z(t1.x, emax, zlo[2], zhi[2]);
+  split_z(t1.y, emax, zlo[3], zhi[3]);
 #pragma unroll
-    for (int i = 0; i < kDig; ++i) {  // digit i (most significant first) is c_(6-i)
-      uint32_t wd[2];
+  for (int i = 0; i < kDig; ++i) {  // digit i (most significant first) is c_(6-i)
+    uint32_t wd[2];
 #pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const uint32_t a0 = zlo[2 * p], b0 = zhi[2 * p], a1 = zlo[2 * p + 1], b1 = zhi[2 * p + 1];
-        switch (6 - i) {
-          case 6: wd[p] = digit_pair<6>(a0, b0, a1, b1); break;
-          case 5: wd[p] = digit_pair<5>(a0, b0, a1, b1); break;
-          case 4: wd[p] = digit_pair<4>(a0, b0, a1, b1); break;
-          case 3: wd[p] = digit_pair<3>(a0, b0, a1, b1); break;
-          case 2: wd[p] = digit_pair<2>(a0, b0, a1, b1); break;
-          case 1: wd[p] = digit_pair<1>(a0, b0, a1, b1); break;
-          default: wd[p] = digit_pair<0>(a0, b0, a1, b1); break;
-        }
+    for (int p = 0; p < 2; ++p) {
+      const uint32_t a0 = zlo[2 * p], b0 = zhi[2 * p], a1 = zlo[2 * p + 1], b1 = zhi[2 * p + 1];
+      switch (6 - i) {
+        case 6: wd[p] = digit_pair<6>(a0, b0, a1, b1); break;
+        case 5: wd[p] = digit_pair<5>(a0, b0, a1, b1); break;
+        case 4: wd[p] = digit_pair<4>(a0, b0, a1, b1); break;
+        case 3: wd[p] = digit_pair<3>(a0, b0, a1, b1); break;
+        case 2: wd[p] = digit_pair<2>(a0, b0, a1, b1); break;
+        case 1: wd[p] = digit_pair<1>(a0, b0, a1, b1); break;
+        default: wd[p] = digit_pair<0>(a0, b0, a1, b1); break;
       }
-      const int R = digit_row(i, a);
-      *reinterpret_cast<uint2*>(base + (R >> 3) * kSBO + (R & 7) * 16) = make_uint2(wd[0], wd[1]);
     }
+    const uint32_t off = (i < 4 ? c.base : base_hi) + (uint32_t)i * stride;
+    *reinterpret_cast<uint2*>(dst + off) = make_uint2(wd[0], wd[1]);
   }
 }
 
@@ -538,6 +545,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
     const bool drains = warp < kDrainWarps;
     const int half = warp >> 2, quarter = warp & 3;
     const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16);
+    const ConvItem item = conv_item(tid, w, s_emax);
     uint32_t t = 0, cu = 0, drained = 0;
     for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
       const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
@@ -546,7 +554,7 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         const int fs = (int)(t % kFStages), ds = (int)(t % kDStages);
         if (!bar_wait(f_full + fs, (t / kFStages) & 1, s_err)) goto done;
         if (t >= kDStages && !bar_wait(d_empty + ds, (t / kDStages - 1) & 1, s_err)) goto done;
-        convert_stage(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, w, s_emax, tid);
+        if (item.src != ~0u) convert_item(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, item);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
