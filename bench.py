@@ -510,12 +510,13 @@ def batch_arm(args):
                    "rows_total": int(sum(s["A"].n for s in systems)),
                    "nnz_total": int(sum(s["A"].nnz for s in systems)),
                    "gram": ("Hankel moments of the monomial basis, FP64 (a variant)" if args.moment_gram else
-                            "FP64 FMAs (per-system row items; tensor cores for lanes of 2^18 rows or more)")},
+                            "tensor cores for lanes of tc_lane_rows rows or more (whole 1024-row chunks, one launch), "
+                            "FP64 FMAs on per-system row items below")},
         "status_ok": ok, "iters_per_batch": iters, "lockstep_blocks": res[0].launches,
         "worst_true_res_over_target": worst_true,
         "sequential": {"ms": seq_ms, "iters": seq_iters, "iters_per_s": seq_iters / (seq_ms * 1e-3),
                        "batch_speedup": seq_ms / (ms / args.steps)},
-        "setup_s": t_gen, "clocks": clocks, "gram_schedule": tuned or {"tc_lane_rows": 1 << 18, "source": "default"},
+        "setup_s": t_gen, "clocks": clocks, "gram_schedule": tuned or {"tc_lane_rows": 1 << 10, "source": "default"},
     }
     print(json.dumps(line), flush=True)
     for op in ops:
