@@ -418,7 +418,9 @@ ascg_status prepare_steps(ascg_op op, const double* th, const double* sg, const 
       ++*launches;
       dt = dst;
     }
-    out[j] = StepOp{ov, dt, j >= 1 ? sg[j - 1] * inv : 0.0};
+    // sig_j = sigma_{j-1} / gamma_j, exactly 1 when the two are equal (Chebyshev)
+    const double sj = j < 1 ? 0.0 : (sg[j - 1] == gm[j] ? 1.0 : sg[j - 1] * inv);
+    out[j] = StepOp{ov, dt, sj};
   }
   return ASCG_OK;
 }

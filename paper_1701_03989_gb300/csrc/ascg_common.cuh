@@ -80,7 +80,8 @@ struct DevSplit {
 //   rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1},
 //   Dt_j = (D - theta_j) / gamma_j,  Ot_j = O / gamma_j,  sig_j = sigma_{j-1} / gamma_j.
 // One multiply for the diagonal, one FMA per off-diagonal nonzero and one FMA for
-// the sigma term per row: nnz_row + 1 FP64 instructions instead of nnz_row + 3.
+// the sigma term per row: nnz_row + 1 FP64 instructions instead of nnz_row + 3,
+// and nnz_row when sig_j = 1 (the negated rho_{j-1} starts the sum).
 struct StepOp {
   const double* oval;   // values of Ot_j (O's sliced ELL layout)
   const double* dtil;   // Dt_j, n values

@@ -13,7 +13,8 @@
 //
 // The basis coefficients are folded into the operator beforehand. A is kept
 // as D + O, and step j uses Dt_j = (D - theta_j)/gamma_j and O/gamma_j, so a
-// row costs nnz_row + 1 FP64 instructions rather than nnz_row + 3. That spends
+// row costs nnz_row + 1 FP64 instructions rather than nnz_row + 3 (nnz_row
+// when sig_j = 1: the sigma term is the start value of the sum). That spends
 // HBM capacity, of which a GB300 has plenty, to save FP64 work, which it lacks.
 #include "ascg_common.cuh"
 
@@ -30,14 +31,18 @@ __device__ __forceinline__ unsigned biased_exp(double v) { return ((unsigned)__d
 // tensor-core Gram.
 // EMAX: record exponents (emax_part). The entries of a row go in pairs: both
 // index and value loads, then the four gathers, then the FMAs, so each warp
-// keeps more loads in flight (the kernel waits mostly on its gathers); the
-// sums run in the same order as one entry at a time. 6 CTAs per SM (up to 40
-// registers) measured faster than 8 at 32 registers with this structure.
-template <bool EMAX>
+// keeps more loads in flight (the kernel waits mostly on its gathers). 6 CTAs
+// per SM (up to 40 registers) measured faster than 8 at 32 registers with
+// this structure.
+// SIG: 0 no sigma term (j = 0 or sig_j = 0); 1 sig_j = 1 exactly (the
+// Chebyshev basis, where sigma_{j-1} = gamma_j); 2 any other sig_j. The sum
+// starts from -sig_j rho_{j-1} and takes the diagonal term as its first FMA,
+// so with SIG = 1 a row costs nnz_row FP64 instructions per chain.
+template <bool EMAX, int SIG>
 __global__ void __launch_bounds__(kSpmvRows, 6) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
                                                                    const double* __restrict__ dtil, double sig,
-                                                                   int use_sig, double* __restrict__ Y, int64_t ldY,
-                                                                   int j, int do_p, int do_r, int* emax_part,
+                                                                   double* __restrict__ Y, int64_t ldY, int j,
+                                                                   int do_p, int do_r, int* emax_part,
                                                                    int64_t emax_ld) {
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   unsigned e_op = 0, e_or = 0;
@@ -51,9 +56,22 @@ __global__ void __launch_bounds__(kSpmvRows, 6) mpk_split_step_kernel(DevSell O,
     const double* v = oval + b + l;
     const int32_t* c = O.col + b + l;
     const double dt = dtil[row];
-    double tp = dt * pj[row];
+    // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
+    double tp;
+    if (SIG == 0) {
+      tp = dt * pj[row];
+    } else {
+      const double z = Y[(int64_t)(2 * j - 2) * ldY + row];
+      tp = fma(dt, pj[row], SIG == 1 ? -z : -sig * z);
+    }
     if (do_r) {
-      double tr = dt * rj[row];
+      double tr;
+      if (SIG == 0) {
+        tr = dt * rj[row];
+      } else {
+        const double z = Y[(int64_t)(2 * j - 1) * ldY + row];
+        tr = fma(dt, rj[row], SIG == 1 ? -z : -sig * z);
+      }
       int k = 0;
       for (; k + 2 <= width; k += 2) {
         const int c0 = __ldg(c + kSlice * k), c1 = __ldg(c + kSlice * (k + 1));
@@ -70,16 +88,10 @@ __global__ void __launch_bounds__(kSpmvRows, 6) mpk_split_step_kernel(DevSell O,
         tp = fma(a, __ldg(pj + cc), tp);
         tr = fma(a, __ldg(rj + cc), tr);
       }
-      // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
-      if (use_sig) {  // integer test: a double compare would take an FP64 issue slot per row
-        tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
-        tr = fma(-sig, Y[(int64_t)(2 * j - 1) * ldY + row], tr);
-      }
       Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
       if (EMAX) e_or = biased_exp(tr);
     } else {
       for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
-      if (use_sig) tp = fma(-sig, Y[(int64_t)(2 * j - 2) * ldY + row], tp);
     }
     if (do_p) {
       Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
@@ -262,13 +274,20 @@ cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const doubl
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
                                   int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s) {
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
-  const int use_sig = (op.sig != 0.0 && j >= 1) ? 1 : 0;
-  if (emax_part)
-    mpk_split_step_kernel<true><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p,
-                                                        do_r, emax_part, emax_ld);
-  else
-    mpk_split_step_kernel<false><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, use_sig, Y, ldY, j, do_p,
-                                                         do_r, nullptr, 0);
+  const int sig_mode = (op.sig == 0.0 || j < 1) ? 0 : (op.sig == 1.0 ? 1 : 2);
+#define ASCG_MPK(E, S)                                                                                     \
+  mpk_split_step_kernel<E, S><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r, \
+                                                      E ? emax_part : nullptr, E ? emax_ld : 0)
+  if (emax_part) {
+    if (sig_mode == 0) ASCG_MPK(true, 0);
+    else if (sig_mode == 1) ASCG_MPK(true, 1);
+    else ASCG_MPK(true, 2);
+  } else {
+    if (sig_mode == 0) ASCG_MPK(false, 0);
+    else if (sig_mode == 1) ASCG_MPK(false, 1);
+    else ASCG_MPK(false, 2);
+  }
+#undef ASCG_MPK
   return cudaGetLastError();
 }
 

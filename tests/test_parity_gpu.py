@@ -82,6 +82,11 @@ def basis_for(kind, s, lam):
         return O.monomial_params(s)
     if kind == "chebyshev":
         return O.chebyshev_params(lam[0], lam[1], s)
+    if kind == "three_term":
+        # a three-term recurrence with sigma_{j-1} != gamma_j (the general sigma
+        # path of the matrix powers step; the Chebyshev basis has them equal)
+        c, h = (lam[0] + lam[1]) / 2, (lam[1] - lam[0]) / 2
+        return O.BasisParams([c] * s, [0.3 * h] * s, [h] + [0.7 * h] * (s - 1), "three_term")
     return O.newton_params(list(np.linspace(1.9, 0.05, s)), s)
 
 
@@ -98,7 +103,7 @@ def abs_bound_columns(A, v, ncols, bp):
     return cols
 
 
-@pytest.mark.parametrize("kind", ["monomial", "chebyshev", "newton"])
+@pytest.mark.parametrize("kind", ["monomial", "chebyshev", "newton", "three_term"])
 @pytest.mark.parametrize("s", [1, 4, 8, 16])
 @pytest.mark.parametrize("name", ["poisson2d_32", "poisson3d_23", "banded_3001"])
 def test_matrix_powers_parity(env, kind, s, name):
