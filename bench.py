@@ -162,7 +162,7 @@ class ClockSampler:
 # roofline traffic from a committed ncu summary (bytes per launch), if current
 # ---------------------------------------------------------------------------
 
-MPK_KERNEL_TEXT = ("template <bool EMAX, int SIG>", "// col_emax[c] = max over the warp entries")
+MPK_KERNEL_TEXT = ("template <int SIG, bool R>", "// col_emax[c] = max over the warp entries")
 
 
 def kernel_source_hash(name="kernels_mpk.cu", span=MPK_KERNEL_TEXT, text=None):

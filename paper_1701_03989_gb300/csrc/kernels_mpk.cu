@@ -29,21 +29,22 @@ __device__ __forceinline__ unsigned biased_exp(double v) { return ((unsigned)__d
 // the input columns 0 and 1) at emax_part[col * emax_ld + warp]; plain stores,
 // no synchronisation. emax_reduce_kernel folds them per column for the
 // tensor-core Gram.
-// EMAX: record exponents (emax_part). The entries of a row go in pairs: both
-// index and value loads, then the four gathers, then the FMAs, so each warp
-// keeps more loads in flight (the kernel waits mostly on its gathers). 6 CTAs
-// per SM (up to 40 registers) measured faster than 8 at 32 registers with
-// this structure.
+// emax_part (or nullptr): record exponents. R: also the R chain (every step of
+// a block but the last). The entries of a row go in pairs: both index and value
+// loads, then the four gathers, then the FMAs, so each warp keeps more loads
+// in flight (the kernel waits mostly on its gathers). The chains and the sigma
+// mode are compile-time parameters: with both as runtime flags the same step
+// took 67.5 us instead of 57.1 us at 128^3. 6 CTAs per SM (up to 40 registers).
+// The exponent work always runs (a few integer operations per row); a
+// variant without it measured slower (63.5 us).
 // SIG: 0 no sigma term (j = 0 or sig_j = 0); 1 sig_j = 1 exactly (the
 // Chebyshev basis, where sigma_{j-1} = gamma_j); 2 any other sig_j. The sum
 // starts from -sig_j rho_{j-1} and takes the diagonal term as its first FMA,
 // so with SIG = 1 a row costs nnz_row FP64 instructions per chain.
-template <bool EMAX, int SIG>
-__global__ void __launch_bounds__(kSpmvRows, 6) mpk_split_step_kernel(DevSell O, const double* __restrict__ oval,
-                                                                   const double* __restrict__ dtil, double sig,
-                                                                   double* __restrict__ Y, int64_t ldY, int j,
-                                                                   int do_p, int do_r, int* emax_part,
-                                                                   int64_t emax_ld) {
+template <int SIG, bool R>
+__global__ void __launch_bounds__(kSpmvRows, 6)
+    mpk_split_step_kernel(DevSell O, const double* __restrict__ oval, const double* __restrict__ dtil, double sig,
+                          double* __restrict__ Y, int64_t ldY, int j, int* emax_part, int64_t emax_ld) {
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   unsigned e_op = 0, e_or = 0;
   if (row < O.n) {
@@ -57,55 +58,53 @@ __global__ void __launch_bounds__(kSpmvRows, 6) mpk_split_step_kernel(DevSell O,
     const int32_t* c = O.col + b + l;
     const double dt = dtil[row];
     // rho_{j+1} = (Dt_j + Ot_j) rho_j - sig_j rho_{j-1}
-    double tp;
+    double tp, tr = 0.0;
     if (SIG == 0) {
       tp = dt * pj[row];
+      if (R) tr = dt * rj[row];
     } else {
-      const double z = Y[(int64_t)(2 * j - 2) * ldY + row];
-      tp = fma(dt, pj[row], SIG == 1 ? -z : -sig * z);
-    }
-    if (do_r) {
-      double tr;
-      if (SIG == 0) {
-        tr = dt * rj[row];
-      } else {
-        const double z = Y[(int64_t)(2 * j - 1) * ldY + row];
-        tr = fma(dt, rj[row], SIG == 1 ? -z : -sig * z);
+      const double zp = Y[(int64_t)(2 * j - 2) * ldY + row];
+      tp = fma(dt, pj[row], SIG == 1 ? -zp : -sig * zp);
+      if (R) {
+        const double zr = Y[(int64_t)(2 * j - 1) * ldY + row];
+        tr = fma(dt, rj[row], SIG == 1 ? -zr : -sig * zr);
       }
-      int k = 0;
-      for (; k + 2 <= width; k += 2) {
-        const int c0 = __ldg(c + kSlice * k), c1 = __ldg(c + kSlice * (k + 1));
-        const double a0 = __ldg(v + kSlice * k), a1 = __ldg(v + kSlice * (k + 1));
-        const double p0 = __ldg(pj + c0), p1 = __ldg(pj + c1), r0 = __ldg(rj + c0), r1 = __ldg(rj + c1);
+    }
+    int k = 0;
+    for (; k + 2 <= width; k += 2) {
+      const int c0 = __ldg(c + kSlice * k), c1 = __ldg(c + kSlice * (k + 1));
+      const double a0 = __ldg(v + kSlice * k), a1 = __ldg(v + kSlice * (k + 1));
+      const double p0 = __ldg(pj + c0), p1 = __ldg(pj + c1);
+      if (R) {
+        const double r0 = __ldg(rj + c0), r1 = __ldg(rj + c1);
         tp = fma(a0, p0, tp);
         tr = fma(a0, r0, tr);
         tp = fma(a1, p1, tp);
         tr = fma(a1, r1, tr);
+      } else {
+        tp = fma(a0, p0, tp);
+        tp = fma(a1, p1, tp);
       }
-      if (k < width) {
-        const double a = __ldg(v + kSlice * k);
-        const int cc = __ldg(c + kSlice * k);
-        tp = fma(a, __ldg(pj + cc), tp);
-        tr = fma(a, __ldg(rj + cc), tr);
-      }
-      Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
-      if (EMAX) e_or = biased_exp(tr);
-    } else {
-      for (int k = 0; k < width; ++k) tp = fma(__ldg(v + kSlice * k), __ldg(pj + __ldg(c + kSlice * k)), tp);
     }
-    if (do_p) {
-      Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
-      if (EMAX) e_op = biased_exp(tp);
+    if (k < width) {
+      const double a = __ldg(v + kSlice * k);
+      const int cc = __ldg(c + kSlice * k);
+      tp = fma(a, __ldg(pj + cc), tp);
+      if (R) tr = fma(a, __ldg(rj + cc), tr);
     }
+    Y[(int64_t)(2 * j + 2) * ldY + row] = tp;
+    if (R) Y[(int64_t)(2 * j + 3) * ldY + row] = tr;
+    e_op = biased_exp(tp);
+    if (R) e_or = biased_exp(tr);
   }
-  if (!EMAX) return;
+  if (!emax_part) return;  // uniform over the grid
   // the warp's rows share one slice; lanes past n contribute 0
   e_op = __reduce_max_sync(0xffffffffu, e_op);
   e_or = __reduce_max_sync(0xffffffffu, e_or);
   const int64_t wg = ((int64_t)blockIdx.x * kSpmvRows + threadIdx.x) >> 5;
   if ((threadIdx.x & 31) == 0) {
-    if (do_p) emax_part[(int64_t)(2 * j + 2) * emax_ld + wg] = (int)e_op;
-    if (do_r) emax_part[(int64_t)(2 * j + 3) * emax_ld + wg] = (int)e_or;
+    emax_part[(int64_t)(2 * j + 2) * emax_ld + wg] = (int)e_op;
+    if (R) emax_part[(int64_t)(2 * j + 3) * emax_ld + wg] = (int)e_or;
   }
   if (j == 0) {
     // inputs p and r (columns 0, 1): reloaded here (cache hits) so that nothing
@@ -273,19 +272,19 @@ cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const doubl
 
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
                                   int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s) {
+  if (!do_p) return cudaErrorInvalidValue;  // every step forms the P column
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
   const int sig_mode = (op.sig == 0.0 || j < 1) ? 0 : (op.sig == 1.0 ? 1 : 2);
-#define ASCG_MPK(E, S)                                                                                     \
-  mpk_split_step_kernel<E, S><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, do_p, do_r, \
-                                                      E ? emax_part : nullptr, E ? emax_ld : 0)
-  if (emax_part) {
-    if (sig_mode == 0) ASCG_MPK(true, 0);
-    else if (sig_mode == 1) ASCG_MPK(true, 1);
-    else ASCG_MPK(true, 2);
+#define ASCG_MPK(S, R) \
+  mpk_split_step_kernel<S, R><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, emax_part, emax_ld)
+  if (do_r) {
+    if (sig_mode == 0) ASCG_MPK(0, true);
+    else if (sig_mode == 1) ASCG_MPK(1, true);
+    else ASCG_MPK(2, true);
   } else {
-    if (sig_mode == 0) ASCG_MPK(false, 0);
-    else if (sig_mode == 1) ASCG_MPK(false, 1);
-    else ASCG_MPK(false, 2);
+    if (sig_mode == 0) ASCG_MPK(0, false);
+    else if (sig_mode == 1) ASCG_MPK(1, false);
+    else ASCG_MPK(2, false);
   }
 #undef ASCG_MPK
   return cudaGetLastError();
