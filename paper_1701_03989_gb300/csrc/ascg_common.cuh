@@ -87,7 +87,8 @@ struct StepOp {
   const double* dtil;   // Dt_j, n values
   double sig;           // sig_j (0 for j = 0)
 };
-// Forms column 2(j+1) from 2j, 2(j-1) if do_p, and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
+// Forms column 2(j+1) from 2j, 2(j-1), and column 2(j+1)+1 from 2j+1, 2j-1 if do_r.
+// do_p must be 1 (cudaErrorInvalidValue otherwise): every step forms the P column.
 // emax_part (device int[kMaxW * emax_ld] or nullptr, emax_ld >= ceil(n/32), a
 // multiple of 4, entries past ceil(n/32) zero):
 // per warp of 32 rows, the largest biased exponent of each column written (for
