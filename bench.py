@@ -46,16 +46,27 @@ SM_MAX_MHZ = 2070.0
 FP64_FMA_PER_CLK_SM = 2.0   # nominal: 1.25 TFLOP/s FP64 = 2 DFMA/clk/SM x 152 SMs x 2.07 GHz x 2
 
 
-def _measured_bf16_tflops():
-    """Dense bf16 burst peak from MEASURED_PEAKS.json (driver-written), else the fallback."""
+def _measured_peak(key, fallback):
+    """A peak from MEASURED_PEAKS.json (driver-written), else the fallback figure."""
     try:
         with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["bf16_tflops"])
+            return float(json.load(f)[key]), "measured"
     except (OSError, KeyError, ValueError):
-        return 1900.0
+        return fallback, "fallback"
 
 
-BF16_PEAK_TF = _measured_bf16_tflops()
+BF16_PEAK_TF, BF16_PEAK_SRC = _measured_peak("bf16_tflops", 1900.0)
+HBM_PEAK_GBS, HBM_PEAK_SRC = _measured_peak("hbm_gbs", 6800.0)
+
+
+def hbm_view(nbytes, ms):
+    """Algorithmic bytes over a kernel's device time against the HBM copy peak:
+    the bandwidth side of a kernel that another unit bounds."""
+    if not ms or ms <= 0:
+        return None
+    gbs = nbytes / (ms * 1e-3) / 1e9
+    return {"achieved": gbs, "peak": HBM_PEAK_GBS, "unit": "GB/s", "frac": gbs / HBM_PEAK_GBS,
+            "peak_source": f"{HBM_PEAK_SRC} copy bandwidth"}
 
 
 def parse():
@@ -419,13 +430,15 @@ def our_arm(args):
                          "flops_per_launch": per_launch_mpk,
                          "peak_source": "derived: FP64 DFMA 2 per clock per SM (nominal 1.25 TFLOP/s) x 152 SMs x "
                                         "2070 MHz max clock; FP64 is the binding unit (not HBM); the MEASURED_PEAKS "
-                                        "file has no FP64 figure"},
+                                        "file has no FP64 figure",
+                         "hbm": hbm_view(sum(r.mpk_bytes for r in results), t_mpk)},
             "roofline_gram": {"bound": "tensor", "kernel": "gram_tc_kernel (+ column exponents)",
                               "achieved": achieved_tc, "peak": BF16_PEAK_TF, "unit": "TFLOP/s",
                               "frac": (achieved_tc / BF16_PEAK_TF) if achieved_tc and BF16_PEAK_TF else None,
                               "flops_per_launch": 2.0 * 128 * (240 + 16) * n,
                               "fp64_equiv_tflops": achieved_tf,
-                              "peak_source": "measured dense bf16 burst (fp16 runs at the same rate)"},
+                              "peak_source": f"{BF16_PEAK_SRC} dense bf16 burst (fp16 runs at the same rate)",
+                              "hbm": hbm_view(sum(r.gram_bytes for r in results), t_gram)},
             "vs_classical": classical,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 8 * n},
