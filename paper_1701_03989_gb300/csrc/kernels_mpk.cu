@@ -167,9 +167,9 @@ __global__ void shift_scale_kernel(const double* __restrict__ src, int64_t n, do
 // All recovery kernels load a row's entries in groups of kRecGroup columns
 // (streaming loads, which also keep the compiler from hoisting every load of
 // the row) and add them in column order: the same sums (and bits) in every
-// kernel, with about 40 registers, so 6 CTAs fit on an SM. Holding the whole row in
-// registers (166 for W = 33) left one CTA per SM and took 279 us instead of
-// 238 us for r and p at 128^3.
+// kernel, with about 40 registers, so 6 CTAs fit on an SM. Holding the whole
+// row in registers (166 for W = 33) left one CTA per SM and took 279 us
+// instead of 238 us for r and p at 128^3.
 constexpr int kRecGroup = 8;
 
 template <int W>
