@@ -6,6 +6,7 @@
 // keep every lane busy and count FP64 instructions, not bytes.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <string>
 #include <cuda_runtime.h>
@@ -41,6 +42,22 @@ __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// Raises a kernel's dynamic shared-memory limit to `bytes` on the current
+// device, once per device (devices 0..63; others every call). The device's
+// flag is set only after the attribute call succeeded, so a caller that sees
+// it may launch; two threads may both make the call, which is harmless.
+template <typename K>
+inline cudaError_t smem_limit_once(std::atomic<uint64_t>& done, K* kernel, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const uint64_t bit = (dev >= 0 && dev < 64) ? (uint64_t)1 << dev : 0;
+  if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_release);
+  return e;
 }
 
 // Number of blocks for a grid-stride kernel over n items.

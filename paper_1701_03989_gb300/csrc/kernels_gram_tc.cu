@@ -782,7 +782,7 @@ cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int6
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-int g_tc_attr_dev = -1;
+std::atomic<uint64_t> g_tc_smem_set{0}, g_tc_items_smem_set{0};
 
 }  // namespace
 
@@ -804,14 +804,8 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
   const int parts = gram_tc_parts(n);
   // a sliced sum takes <= 10 additions per chunk: at most 2^11 chunks per CTA
   if ((n + kTChunk - 1) / kTChunk > (int64_t)parts * 2048) return cudaErrorInvalidValue;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = smem_limit_once(g_tc_smem_set, gram_tc_kernel, (int)kTcSmem);
   if (e != cudaSuccess) return e;
-  if (g_tc_attr_dev != dev) {
-    e = cudaFuncSetAttribute(gram_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    if (e != cudaSuccess) return e;
-    g_tc_attr_dev = dev;
-  }
   CUtensorMap map;
   e = encode_map(&map, Y, n, w, ldY);
   if (e != cudaSuccess) return e;
@@ -834,15 +828,8 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
   if (!gram_tc_applies(w) || !gram_tc_aligned(Y, ldY) || rows < 1 || rows > 0x7fffffffll || rows > ldY ||
       (rows % kTChunk) != 0)
     return cudaErrorInvalidValue;
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  cudaError_t e = smem_limit_once(g_tc_items_smem_set, gram_tc_items_kernel, (int)kTcSmem);
   if (e != cudaSuccess) return e;
-  static int attr_dev = -1;
-  if (attr_dev != dev) {
-    e = cudaFuncSetAttribute(gram_tc_items_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem);
-    if (e != cudaSuccess) return e;
-    attr_dev = dev;
-  }
   CUtensorMap map;
   e = encode_map(&map, Y, rows, w, ldY);
   if (e != cudaSuccess) return e;

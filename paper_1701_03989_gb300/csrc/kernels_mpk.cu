@@ -283,15 +283,9 @@ template <int W>
 cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
                             double* p, int x_ctas, cudaStream_t s) {
   if (x) {
-    static int attr_dev = -1;  // the attribute is set once per device and instance
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    static std::atomic<uint64_t> smem_set{0};  // one flag set per instance
+    const cudaError_t e = smem_limit_once(smem_set, recover_x_kernel<W>, kXReserve);
     if (e != cudaSuccess) return e;
-    if (attr_dev != dev) {
-      e = cudaFuncSetAttribute(recover_x_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kXReserve);
-      if (e != cudaSuccess) return e;
-      attr_dev = dev;
-    }
     recover_x_kernel<W><<<x_ctas, kXThreads, kXReserve, s>>>(n, Y, ldY, coords, x);
   } else {
     recover_rp_kernel<W><<<rec_grid(n), 256, 0, s>>>(n, Y, ldY, coords, r, p);
