@@ -439,6 +439,33 @@ def test_paper_observations_sec5():
     assert late and all(s == 8 for s in late)
 
 
+@pytest.mark.parametrize("s_max", [8, 10])
+@pytest.mark.parametrize("family", ["poisson2d_32", "poisson3d_12"])
+def test_sk_monotone_while_residual_decreases(family, s_max):
+    """Sec. 5 observation: where the residual 2-norm decreases monotonically, the
+    chosen s_k increase monotonically (the threshold of (condy) grows as the
+    residual shrinks). Checked on the Poisson stand-ins at a tight target: the
+    block-start residuals must fall, and s_k must not decrease, up to the last
+    block, which is cut short by convergence."""
+    if family == "poisson2d_32":
+        c = W.poisson2d_32()
+        A, b, x1 = O.Operator.from_csr(c["A"]), c["b"], c["x1"]
+    else:
+        A = O.Operator.from_csr(W.poisson3d(12))
+        rng = np.random.default_rng(5)
+        b = rng.uniform(-1.0, 1.0, A.n)
+        b /= np.linalg.norm(b)
+        x1 = np.zeros(A.n)
+    ad = O.adaptive_sstep_cg(A, b, x1, s_max=s_max, eps_target=1e-13, max_iters=3000)
+    assert ad.converged
+    rn = [bl["rnorm"] for bl in ad.blocks]
+    assert all(rn[i + 1] <= rn[i] for i in range(len(rn) - 1))
+    body = [bl["s_k"] for bl in ad.blocks if bl["stop"] != "converged"]
+    assert len(body) >= 5
+    assert all(body[i + 1] >= body[i] for i in range(len(body) - 1)), body
+    assert body[-1] > body[0]
+
+
 def _laplacian_1d(n):
     """tridiag(-1/2, 1, -1/2): the 1D Dirichlet Laplacian, equilibrated (Sec. 5).
     Eigenvalues 1 - cos(k pi/(n+1)), k = 1..n (closed form)."""
