@@ -74,6 +74,30 @@ def test_struct_layouts_match_header(P):
                     P.ascg_server_stats.steps.offset]
 
 
+def test_every_struct_field_offset_matches_header(P):
+    """Every field of every struct the binding mirrors sits at the header's
+    offset, with the header's size (the C compiler is the judge)."""
+    structs = {"ascg_options": P.ascg_options, "ascg_result": P.ascg_result,
+               "ascg_block_info": P.ascg_block_info, "ascg_completion": P.ascg_completion,
+               "ascg_server_stats": P.ascg_server_stats}
+    lines, expect = [], []
+    for cname, ct in structs.items():
+        lines.append(f'printf("%zu\\n", sizeof({cname}));')
+        expect.append(C.sizeof(ct))
+        for fname, _ in ct._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {fname}));')
+            expect.append(getattr(ct, fname).offset)
+    src = ("#include <stdio.h>\n#include <stddef.h>\n#include \"ascg.h\"\nint main(void) {\n" +
+           "\n".join(lines) + "\nreturn 0;\n}\n")
+    with tempfile.TemporaryDirectory() as d:
+        cfile = os.path.join(d, "off.c")
+        exe = os.path.join(d, "off")
+        open(cfile, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), cfile, "-o", exe], check=True)
+        got = [int(v) for v in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    assert got == expect
+
+
 def test_options_default(P):
     o = P.ascg_options_default()
     assert o.method == P.ASCG_ADAPTIVE and o.basis == P.ASCG_MONOMIAL
