@@ -72,7 +72,7 @@ def test_classical_cg_exact_finite_termination():
 
 
 @pytest.mark.parametrize("seq", [[1], [2], [3], [5], [2, 1, 3], [1, 4], [3, 2, 1]])
-@pytest.mark.parametrize("basis", ["monomial", "chebyshev", "newton"])
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev", "newton", "three_term"])
 def test_sstep_equals_classical_exact(seq, basis):
     """s-step CG (Alg. 2) and variable s-step CG (Alg. 3) give the classical iterates exactly.
 
@@ -89,9 +89,15 @@ def test_sstep_equals_classical_exact(seq, basis):
         bp = O.monomial_params(smax, one=Fraction(1), zero=Fraction(0))
     elif basis == "chebyshev":
         bp = O.chebyshev_params(Fraction(1, 2), Fraction(40), smax)
-    else:
+    elif basis == "newton":
         bp = O.BasisParams([Fraction(k + 1, 3) for k in range(smax)], [Fraction(0)] * smax,
                            [Fraction(1)] * smax, "newton")
+    else:
+        # a general three-term recurrence: theta_j, sigma_j and gamma_j all differ
+        # with j, so an index slip anywhere in the recurrence or in B shows
+        bp = O.BasisParams([Fraction(2 * k + 1, 5) for k in range(smax)],
+                           [Fraction(k + 2, 7) for k in range(smax)],
+                           [Fraction(k + 3, 4) for k in range(smax)], "three_term")
     total = n - 1   # stop before r = 0 exactly (finite termination at step n)
     ss = O.variable_sstep_cg(A, b, x1, seq, bp, max_iters=total, exact=True)
     assert ss.iters == total
@@ -161,7 +167,7 @@ def _exact_residual_norm(Ad, Yu, Y, B):
     return np.linalg.norm(E.astype(np.float64), 2)
 
 
-@pytest.mark.parametrize("basis", ["monomial", "chebyshev", "newton"])
+@pytest.mark.parametrize("basis", ["monomial", "chebyshev", "newton", "three_term"])
 def test_basis_recurrence_bound_E(basis):
     """||A Yunder - Y B|| <= eps((3+N_A)||A|| ||Yunder|| + 4 ||Y|| ||B||), eq. (E)."""
     c = W.scaled("poisson2d", 6, 5)
@@ -171,8 +177,12 @@ def test_basis_recurrence_bound_E(basis):
         bp = O.monomial_params(s)
     elif basis == "chebyshev":
         bp = O.chebyshev_params(c["lam"][0], c["lam"][1], s)
-    else:
+    elif basis == "newton":
         bp = O.newton_params(np.linspace(1.9, 0.1, s), s)
+    else:
+        lo, hi = c["lam"]
+        bp = O.BasisParams([(lo + hi) / 2 + 0.1 * k for k in range(s)], [0.2 + 0.05 * k for k in range(s)],
+                           [0.6 + 0.1 * k for k in range(s)], "three_term")
     rng = np.random.default_rng(4)
     p = rng.standard_normal(A.n)
     r = rng.standard_normal(A.n)
@@ -464,6 +474,27 @@ def test_sk_monotone_while_residual_decreases(family, s_max):
     assert len(body) >= 5
     assert all(body[i + 1] >= body[i] for i in range(len(body) - 1)), body
     assert body[-1] > body[0]
+
+
+@pytest.mark.parametrize("n,hbw", [(800, 20), (1500, 40)])
+def test_in_loop_check_cuts_blocks_short(n, hbw):
+    """Eq. (check) inside the block (Alg. 4): where the coordinate residual grows
+    within a block, the threshold eps*/(c eps ||r'||) falls below the basis'
+    condition estimate gamma and the block stops before s~ steps. On banded
+    SPD matrices (whose CG residual norms oscillate) at eps* = 1e-12 some blocks
+    must stop that way. In each, gamma lies below every earlier step's threshold
+    and at or above the last one's."""
+    A = O.Operator.from_csr(W.banded_spd(n, hbw, np.random.default_rng(n)))
+    b = W.rhs_uniform(A.n, np.random.default_rng(1))
+    ad = O.adaptive_sstep_cg(A, b, np.zeros(A.n), s_max=10, eps_target=1e-12, max_iters=20000)
+    assert ad.converged
+    cut = [bl for bl in ad.blocks if bl["stop"] == "break" and bl["s_k"] < bl["stilde"]]
+    assert cut
+    for bl in cut:
+        thresholds = [t for _, t in bl["checks"]]
+        assert len(thresholds) == bl["s_k"]
+        assert all(bl["gamma"] < t for t in thresholds[:-1])
+        assert bl["gamma"] >= thresholds[-1]
 
 
 def _laplacian_1d(n):
