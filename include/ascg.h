@@ -47,7 +47,9 @@ typedef enum {
   ASCG_ERR_CUDA = 3,         /* a CUDA runtime call failed                       */
   ASCG_ERR_BREAKDOWN = 4,    /* a block could not take a single inner step       */
   ASCG_NOT_CONVERGED = 5,    /* max_iters reached before the target              */
-  ASCG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up               */
+  ASCG_ERR_TIMEOUT = 6,      /* a bounded device-side wait gave up: a wait of the
+                                tensor-core Gram (about 2 s) ran out, its CTA
+                                gave up cleanly and the GPU context stays usable */
   ASCG_ERR_NOT_SPD = 7       /* a diagonal entry is missing or not positive      */
 } ascg_status;
 
@@ -132,6 +134,16 @@ typedef struct {
 #define ASCG_FLAG_MOMENT_GRAM 8 /* monomial basis only: G from 6 sbar moments
                                  (ascg_gram_moments) instead of Y^T Y; a
                                  variant that rounds differently            */
+#define ASCG_FLAG_TEST_GRAM_STALL 16 /* failure-path test only (ascg_solve with
+                                 an s-step method): in the first block, the
+                                 tensor-core Gram's first CTA never issues its
+                                 first tensor copy and every wait is limited
+                                 to a few milliseconds, so a wait runs out by
+                                 construction. The CTA gives up cleanly (its
+                                 copies and MMAs land, its tensor memory is
+                                 freed) and the solve returns ASCG_ERR_TIMEOUT
+                                 with x = x_1. No effect when the block's Gram
+                                 takes the FP64 kernel (w < 9).              */
 #define ASCG_FLAG_C_FORMULA 4 /* c_{k,j} = 6 N_k j kappa(A), the factor of the gap
                                  bound eq. (fb), instead of the constant c:
                                  N_k = 7 + 2 N_A + 14 ||B_k|| / ||A||, N_A = most
@@ -273,7 +285,8 @@ ascg_status ascg_matrix_powers(ascg_op op, int s, const double* theta, const dou
  * digit products are summed exactly in integers. Per entry the error is at
  * most 2^-51 (max|y_a| ||y_b||_1 + max|y_b| ||y_a||_1) + gamma_(m) |y_a|^T |y_b|
  * (m = CTAs + 7); a column holding Inf or NaN gives NaN in its row and
- * column. */
+ * column. If a bounded wait of the tensor-core kernel runs out (about 2 s),
+ * G is NaN and the call returns ASCG_ERR_TIMEOUT. */
 ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
 
 /* Gram matrix of a monomial basis from its moments (a variant of ascg_gram;
@@ -346,7 +359,10 @@ ascg_status ascg_newton_shifts(const double* alphas, const double* betas, int k,
  *    (for example on two streams at once) race and give wrong results:
  *    order them on one stream.
  *  - Returns once the work is enqueued on the stream (it does not
- *    synchronise). */
+ *    synchronise), so it cannot report a device-side timeout: if a bounded
+ *    wait of the tensor-core kernel runs out (about 2 s), every entry of G
+ *    that the giving-up CTA contributes to is NaN. NaN in G with finite Y
+ *    means exactly that. */
 ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int64_t ldY, double* G, void* cuda_stream);
 
 /* --- solve server (continuous batching) ------------------------------------

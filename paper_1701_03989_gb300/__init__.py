@@ -35,6 +35,7 @@ ASCG_FLAG_TIMING = 1
 ASCG_FLAG_GRAM_FP64 = 2
 ASCG_FLAG_C_FORMULA = 4
 ASCG_FLAG_MOMENT_GRAM = 8
+ASCG_FLAG_TEST_GRAM_STALL = 16
 
 
 class ascg_block_info(C.Structure):
@@ -337,7 +338,7 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
                  gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False,
-                 tc_lane_rows=0) -> ascg_options:
+                 tc_lane_rows=0, test_gram_stall=False) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
@@ -361,6 +362,8 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
     o.tc_lane_rows = int(tc_lane_rows)
     if moment_gram:
         o.flags |= ASCG_FLAG_MOMENT_GRAM
+    if test_gram_stall:
+        o.flags |= ASCG_FLAG_TEST_GRAM_STALL
     if c_formula is not None:
         o.flags |= ASCG_FLAG_C_FORMULA
         o.kappa_A, o.norm_A = float(c_formula[0]), float(c_formula[1])

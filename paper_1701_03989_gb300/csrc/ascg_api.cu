@@ -471,6 +471,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
   const bool timing = (o.flags & ASCG_FLAG_TIMING) != 0;
   const bool gram_fp64 = (o.flags & ASCG_FLAG_GRAM_FP64) != 0;
   const bool gram_mom = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
+  const bool stall_test = (o.flags & ASCG_FLAG_TEST_GRAM_STALL) != 0;
   if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
 
   // ||b||, r_1 = b - A x_1, p_1 = r_1 (Alg. 1/4 first line). p = column 0 and
@@ -502,6 +503,10 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     ASCG_TRY(run_classical(op, x, r, p, eps_star, bnorm, o.max_iters, 0, s, res, timing));
     m = w.h_cgs->iter;
     final_status = w.h_cgs->converged ? ASCG_OK : ASCG_NOT_CONVERGED;
+    if (w.h_cgs->breakdown) {
+      final_status = ASCG_ERR_BREAKDOWN;
+      g_err = "breakdown: p^T A p was not positive and finite";
+    }
     res->rel_res_updated = std::sqrt(std::max(w.h_cgs->rr, 0.0)) / bnorm;
   } else {
     double th[kMaxS], sg[kMaxS], gm[kMaxS];
@@ -529,6 +534,11 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       m = w.h_cgs->iter;
       res->rel_res_updated = std::sqrt(std::max(w.h_cgs->rr, 0.0)) / bnorm;
       if (w.h_cgs->converged) done = true;
+      if (!done && w.h_cgs->breakdown) {
+        done = true;
+        final_status = ASCG_ERR_BREAKDOWN;
+        g_err = "breakdown: p^T A p was not positive and finite in the Newton warm-up";
+      }
       if (!done && m >= o.max_iters) {
         done = true;
         final_status = ASCG_NOT_CONVERGED;
@@ -597,7 +607,8 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
       // the steps also record each basis column's largest exponent for the tensor-core Gram
-      const bool tc_gram = !gram_fp64 && !gram_mom && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY);
+      const bool tc_gram =
+          !gram_fp64 && !gram_mom && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY) && gram_tc_fits(n);
       for (int j = 0; j < sbar; ++j) {
         ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], Yc, w.ldY, j, 1, j < sbar - 1,
                                         tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
@@ -613,7 +624,8 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       if (gram_mom)
         ASCG_CUDA(launch_gram_moments(n, wb, Yc, w.ldY, w.partials, &nparts, s));
       else
-        ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s));
+        ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s,
+                                  &w.bst->status, stall_test && k == 0));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
       if (gram_mom)
         ASCG_CUDA(launch_gram_moment_finalize(wb, w.partials, nparts, w.G, s));
@@ -686,6 +698,13 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       }
       ++nb_info;
       res->wasted_vecs += 2 * (sbar - out.s_k);
+      if (out.status == ASCG_ERR_TIMEOUT) {
+        // a bounded wait of the tensor-core Gram ran out; its CTA gave up
+        // cleanly and the block's G is NaN, so no step was taken
+        final_status = ASCG_ERR_TIMEOUT;
+        g_err = "timeout: a bounded wait of the tensor-core Gram ran out";
+        break;
+      }
       if (out.s_k == 0) {
         final_status = ASCG_ERR_BREAKDOWN;
         g_err = "breakdown: a block could not take an inner step";
@@ -969,17 +988,23 @@ ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G,
   int* expp = nullptr;
   int parts = 0;
   ASCG_TRY(dev_alloc(&partials, (size_t)gram_grid() * kMaxPairs));
-  ascg_status rs = dev_alloc(&expp, (size_t)gram_grid() * kMaxW);
+  // column exponents, then one error word of the tensor-core kernel
+  const size_t nexp = (size_t)gram_grid() * kMaxW;
+  ascg_status rs = dev_alloc(&expp, nexp + 1);
   if (rs != ASCG_OK) {
     cudaFree(partials);
     return rs;
   }
-  cudaError_t e = launch_gram_any(n, w, Y, ldY, false, expp, false, partials, &parts, s);
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(expp + nexp, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_gram_any(n, w, Y, ldY, false, expp, false, partials, &parts, s, expp + nexp);
   if (e == cudaSuccess) e = launch_gram_finalize(w, partials, parts, G, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, expp + nexp, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   cudaFree(partials);
   cudaFree(expp);
   if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("gram: ") + cudaGetErrorString(e));
+  if (herr == ASCG_ERR_TIMEOUT) return fail(ASCG_ERR_TIMEOUT, "gram: a bounded wait of the tensor-core kernel ran out");
   return ASCG_OK;
 }
 

@@ -171,11 +171,26 @@ int gram_tc_parts(int64_t n);   // CTAs (= partials) of the tensor-core Gram
 bool gram_tc_applies(int w);
 // The tensor-core Gram needs 16-byte aligned columns: Y 16-byte aligned, ldY even.
 bool gram_tc_aligned(const double* Y, int64_t ldY);
+// Every mbarrier wait of the tensor-core Gram is bounded. A wait that runs out
+// makes the CTA give up: it lets the copies and MMAs it already issued land,
+// frees its tensor memory, writes NaN partials and, when err is given, sets
+// *err = ASCG_ERR_TIMEOUT (device int). stall_stage >= 0 is the stall test:
+// CTA 0 never issues the copy of that stage, so a wait runs out by
+// construction; wait_limit is then a few milliseconds.
+struct TcGuard {
+  long long wait_limit;
+  int stall_stage;
+  int* err;
+};
 // col_emax: device int[kMaxW], the largest biased exponent of each column;
 // computed here unless emax_ready (then it already holds them, e.g. from the
-// matrix powers kernel). partials as for launch_gram_partial.
+// matrix powers kernel). partials as for launch_gram_partial. err: as in
+// TcGuard (may be nullptr); stall_test: run the stall test (see TcGuard).
 cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, bool emax_ready,
-                           double* partials, cudaStream_t s);
+                           double* partials, cudaStream_t s, int* err = nullptr, bool stall_test = false);
+// True when the tensor-core Gram can take n rows (at most 2^31 - 1 rows and
+// 2048 chunks of 1024 rows per CTA); larger bases take the FP64 kernel.
+bool gram_tc_fits(int64_t n);
 // Partials of G with the kernel for this width (FP64 when force_fp64); returns
 // the number of partials through *nparts.
 // Tensor-core Gram of many systems whose bases are row ranges of one matrix
@@ -188,7 +203,8 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
                                  int nitems, const int* sys_w, int nsys, int* emax_all, double* partials,
                                  cudaStream_t s);
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
-                            bool emax_ready, double* partials, int* nparts, cudaStream_t s);
+                            bool emax_ready, double* partials, int* nparts, cudaStream_t s, int* err = nullptr,
+                            bool stall_test = false);
 
 // Many systems in lockstep (kernels_batch.cu): a device table of per-system
 // descriptors and row items of one system each (up to kRowItem rows starting
@@ -310,7 +326,7 @@ struct CGState {
   int done;         // 1 once converged or capped
   int converged;
   int active;       // 1 if the current iteration runs (set by the SpMV kernel)
-  int pad_;
+  int breakdown;    // 1 once p^T A p was not positive and finite (the solve stops)
 };
 // q = A p, state.pAp; the last CTA sets alpha.
 cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st,

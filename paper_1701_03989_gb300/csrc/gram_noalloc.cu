@@ -50,14 +50,18 @@ extern "C" ascg_status ascg_gram_noalloc(int64_t n, int w, const double* Y, int6
   if (w < 1 || w > kMaxW)
     return fail(ASCG_ERR_INVALID,
                 "ascg_gram_noalloc: w must be in 1..33 (the static scratch holds 33-column Grams at most)");
-  const int parts = gram_tc_applies(w) && gram_tc_aligned(Y, ldY) ? gram_tc_parts(n) : gram_parts(n);
+  const int parts =
+      gram_tc_applies(w) && gram_tc_aligned(Y, ldY) && gram_tc_fits(n) ? gram_tc_parts(n) : gram_parts(n);
   if (parts > kScratchParts)
     return fail(ASCG_ERR_INVALID, "ascg_gram_noalloc: this GPU would use " + std::to_string(parts) +
                                       " CTAs, more than the 160 the static scratch holds");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+  if (e != cudaSuccess)
     return fail(ASCG_ERR_CUDA, std::string("ascg_gram_noalloc: cudaGetDevice: ") + cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices)
+    return fail(ASCG_ERR_INVALID, "ascg_gram_noalloc: device " + std::to_string(dev) +
+                                      " is beyond the 64 devices whose scratch addresses this library keeps");
   double* scratch = nullptr;
   int* exp_scratch = nullptr;
   {

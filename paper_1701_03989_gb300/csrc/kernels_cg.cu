@@ -124,7 +124,16 @@ __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const
     const double pq = sum_partials(partials, gridDim.x, red);
     if (threadIdx.x == 0) {
       st->pAp = pq;
-      st->alpha = st->rr / pq;  // Alg. 1: alpha_i = r^T r / p^T A p
+      if (pq > 0.0 && isfinite(pq)) {
+        st->alpha = st->rr / pq;  // Alg. 1: alpha_i = r^T r / p^T A p
+      } else {
+        // breakdown (A is not SPD, or the data is not finite): this iteration
+        // is skipped and the solve stops with x, r and p as they were
+        st->alpha = 0.0;
+        st->breakdown = 1;
+        st->done = 1;
+        st->active = 0;
+      }
       *counter = 0u;
     }
   }
@@ -191,6 +200,7 @@ __global__ void cg_init_kernel(CGState* st, double eps_star, double bnorm, int m
     st->done = st->converged || iter0 >= max_iters;
     st->alpha = st->beta = st->pAp = 0.0;
     st->active = 0;
+    st->breakdown = 0;
   }
 }
 

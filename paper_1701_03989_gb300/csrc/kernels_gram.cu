@@ -25,7 +25,8 @@ constexpr int kGramWarps = 16;
 constexpr int kGramThreads = kGramWarps * 32;
 constexpr int kChunk = 32;  // rows per chunk = lanes
 
-int g_gram_grid = 0;
+// SM count of each device (0: not looked up yet), for devices 0..63.
+std::atomic<int> g_gram_grid[64];
 
 // Partial Gram of 32-row chunks [c0, c1) of rows [0, n) of Y into out[NP]
 // (row-major upper triangle). Called by every thread of a CTA of kGramThreads.
@@ -302,13 +303,20 @@ cudaError_t gram_w(int64_t n, const double* Y, int64_t ldY, double* partials, in
 }  // namespace
 
 int gram_grid() {
-  if (g_gram_grid == 0) {
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    g_gram_grid = sms > 0 ? sms : 1;
+  // the current device's SM count, looked up once per device (each thread may
+  // look it up the first time; the value is the same)
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) dev = -1;
+  const bool cached = dev >= 0 && dev < 64;
+  if (cached) {
+    const int v = g_gram_grid[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
   }
-  return g_gram_grid;
+  const bool ok = dev >= 0 && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+                  sms > 0;
+  if (!ok) return 1;
+  if (cached) g_gram_grid[dev].store(sms, std::memory_order_relaxed);
+  return sms;
 }
 
 int gram_parts(int64_t n) {

@@ -53,7 +53,8 @@
 //  - one thread issues tcgen05.mma kind::f16 (f16 x f16 -> f32) into one of
 //    two TMEM buffers (tile 0 at 256 p + 0..239, tile 1 at 256 p + 240..255),
 //    so a chunk is drained while the next one is multiplied.
-// All waits are bounded; a wait that runs out writes NaN partials.
+// All waits are bounded; a wait that runs out writes NaN partials and reports
+// ASCG_ERR_TIMEOUT through the launch's error word, when one is given.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_fp16.h>
@@ -88,6 +89,7 @@ constexpr int kLoadWarp = 17, kMmaWarp = 18;
 constexpr int kTcThreads = 19 * 32;
 constexpr int kDrainLag = 2;         // drain chunk c after converting 3 stages of chunk c+1
 constexpr long long kWaitLimit = 1ll << 20;  // polls; with the suspend hint a wait ends within ~2 s
+constexpr long long kTestWaitLimit = 1ll << 12;  // the stall test's limit: a few milliseconds
 
 // dynamic shared memory layout
 constexpr size_t kDOff = 0;
@@ -170,9 +172,9 @@ __device__ __forceinline__ int bar_try(uint32_t a, uint32_t parity) {
 
 // Waits until the phase of the given parity has completed. Gives up after
 // kWaitLimit polls or once another role has given up; returns 0 then.
-__device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile int* err) {
+__device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile int* err, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kWaitLimit; ++it) {
+  for (long long it = 0; it < limit; ++it) {
     if (bar_try(a, parity)) return 1;
     if ((it & 15) == 15 && *err) return 0;
   }
@@ -182,9 +184,9 @@ __device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile
 
 // Bounded wait that ignores the error flag: lets copies and MMAs already
 // issued finish before the CTA exits after an error.
-__device__ __forceinline__ void bar_drain(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ void bar_drain(uint64_t* bar, uint32_t parity, long long limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < kWaitLimit; ++it)
+  for (long long it = 0; it < limit; ++it)
     if (bar_try(a, parity)) return;
 }
 
@@ -444,9 +446,9 @@ __device__ __forceinline__ void drain_t1(uint32_t taddr, uint32_t cb, int R, lon
 // (acc_hi, acc_lo). Lanes of a warp have distinct a, so their entries differ.
 __device__ __forceinline__ bool drain_chunk(uint32_t c, int w, int half, int quarter, int lane, uint32_t taddr,
                                             uint64_t* acc_full, uint64_t* acc_empty, volatile int* s_err,
-                                            uint32_t* acc_hi, uint32_t* acc_lo) {
+                                            long long limit, uint32_t* acc_hi, uint32_t* acc_lo) {
   const uint32_t p = c & 1;
-  if (!bar_wait(acc_full + p, (c >> 1) & 1, s_err)) return false;
+  if (!bar_wait(acc_full + p, (c >> 1) & 1, s_err, limit)) return false;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t cb = 256u * p;
   const int a = lane;
@@ -485,10 +487,13 @@ __device__ __forceinline__ bool drain_chunk(uint32_t c, int w, int half, int qua
 // The Gram partial of the chunks ch = c_lo, c_lo + c_step, ... < c_hi of the
 // rows [row_base, row_base + n_local) of the tensor map's matrix (chunk ch
 // starts at row row_base + ch * kTChunk), with the column exponents col_emax,
-// written to out[w (w + 1) / 2]. Run by a whole CTA of kTcThreads.
+// written to out[w (w + 1) / 2]. Run by a whole CTA of kTcThreads. guard: the
+// wait limit, where a wait that ran out is reported, and the stall test's
+// stage (see TcGuard).
 __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, int64_t row_base, int64_t c_lo,
                                              int64_t c_hi, int64_t c_step, int64_t n_local,
-                                             const int* __restrict__ col_emax, double* __restrict__ out) {
+                                             const int* __restrict__ col_emax, double* __restrict__ out,
+                                             const TcGuard guard) {
   extern __shared__ __align__(1024) unsigned char smem[];
   unsigned char* dstage = smem + kDOff;
   unsigned char* fstage = smem + kFOff;
@@ -537,6 +542,8 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
   const int64_t n = n_local;
+  const long long lim = guard.wait_limit;
+  const bool stall_here = guard.stall_stage >= 0 && blockIdx.x == 0;
   uint32_t armed = 0;   // loader: stages whose copies were issued
   uint32_t issued = 0;  // MMA issuer: stages whose MMAs were issued
 
@@ -552,8 +559,8 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
       const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
       for (int sub = 0; sub < nsub; ++sub, ++t) {
         const int fs = (int)(t % kFStages), ds = (int)(t % kDStages);
-        if (!bar_wait(f_full + fs, (t / kFStages) & 1, s_err)) goto done;
-        if (t >= kDStages && !bar_wait(d_empty + ds, (t / kDStages - 1) & 1, s_err)) goto done;
+        if (!bar_wait(f_full + fs, (t / kFStages) & 1, s_err, lim)) goto done;
+        if (t >= kDStages && !bar_wait(d_empty + ds, (t / kDStages - 1) & 1, s_err, lim)) goto done;
         if (item.src != ~0u) convert_item(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, item);
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
@@ -563,13 +570,14 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         }
         if (drains && sub == kDrainLag)
           for (; drained < cu; ++drained)
-            if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, acc_hi, acc_lo))
+            if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, lim, acc_hi,
+                             acc_lo))
               goto done;
       }
     }
     if (drains)
       for (; drained < cu; ++drained)
-        if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, acc_hi, acc_lo))
+        if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, lim, acc_hi, acc_lo))
           goto done;
   } else if (warp == kLoadWarp) {
     // ---- loader: one tensor copy per stage ----
@@ -580,11 +588,12 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
         for (int sub = 0; sub < nsub; ++sub, ++t) {
           const int fs = (int)(t % kFStages);
-          if (t >= kFStages && !bar_wait(f_empty + fs, (t / kFStages - 1) & 1, s_err)) goto done;
+          if (t >= kFStages && !bar_wait(f_empty + fs, (t / kFStages - 1) & 1, s_err, lim)) goto done;
+          armed = t + 1;
+          if (stall_here && t == (uint32_t)guard.stall_stage) continue;  // the stall test: never armed
           bar_expect_tx(f_full + fs, kFBoxBytes);
           tensor_g2s(fstage + fs * kFStageBytes, ymap_p, (int)(row_base + ch * kTChunk + (int64_t)sub * kSub),
                      f_full + fs);
-          armed = t + 1;
         }
       }
     }
@@ -596,12 +605,12 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
         const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
         const uint32_t p = cu & 1;
-        if (cu >= 2 && !bar_wait(acc_empty + p, ((cu >> 1) - 1) & 1, s_err)) goto done;
+        if (cu >= 2 && !bar_wait(acc_empty + p, ((cu >> 1) - 1) & 1, s_err, lim)) goto done;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t d0 = tbase + 256u * p;
         for (int sub = 0; sub < nsub; ++sub, ++t) {
           const int ds = (int)(t % kDStages);
-          if (!bar_wait(d_full + ds, (t / kDStages) & 1, s_err)) goto done;
+          if (!bar_wait(d_full + ds, (t / kDStages) & 1, s_err, lim)) goto done;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t sb = smem_u32(dstage + ds * kDStageBytes);
 #pragma unroll
@@ -624,13 +633,14 @@ done:
     // error path: let the copies and MMAs already in flight land first
     if (warp == kLoadWarp && lane == 0)
       for (uint32_t k = armed > (uint32_t)kFStages ? armed - kFStages : 0; k < armed; ++k)
-        bar_drain(f_full + k % kFStages, (k / kFStages) & 1);
+        bar_drain(f_full + k % kFStages, (k / kFStages) & 1, lim);
     if (warp == kMmaWarp && lane == 0 && issued > 0)
-      bar_drain(d_empty + (issued - 1) % kDStages, ((issued - 1) / kDStages) & 1);
+      bar_drain(d_empty + (issued - 1) % kDStages, ((issued - 1) / kDStages) & 1, lim);
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   const int ok = !*s_err;
+  if (!ok && tid == 0 && guard.err) atomicExch(guard.err, (int)ASCG_ERR_TIMEOUT);
   const int np = w * (w + 1) / 2;
   for (int p = tid; p < np; p += kTcThreads) {
     int a = 0, rem = p;
@@ -660,9 +670,9 @@ done:
 // One matrix: CTA b takes the chunks b, b + gridDim.x, ... of the n rows.
 __global__ void __launch_bounds__(kTcThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
-                   double* __restrict__ partials) {
+                   double* __restrict__ partials, const TcGuard guard) {
   gram_tc_body(&ymap, w, 0, blockIdx.x, (n + kTChunk - 1) / kTChunk, gridDim.x, n, col_emax,
-               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2));
+               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), guard);
 }
 
 // Many systems whose bases are row ranges of one matrix (the tensor map's):
@@ -677,7 +687,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (sys_w[it.sys] == 0) return;  // uniform over the CTA, before any barrier
   const int64_t nch = it.nrows / kTChunk;
   gram_tc_body(&ymap, w, it.row0, 0, nch, 1, nch * kTChunk, emax_all + (int64_t)it.sys * kTW,
-               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2));
+               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), TcGuard{kWaitLimit, -1, nullptr});
 }
 
 // Largest biased exponent of each column, reduced into col_emax (zeroed
@@ -798,12 +808,15 @@ bool gram_tc_aligned(const double* Y, int64_t ldY) {
   return (reinterpret_cast<uintptr_t>(Y) & 15) == 0 && (ldY & 1) == 0;
 }
 
-cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, bool emax_ready,
-                           double* partials, cudaStream_t s) {
-  if (w < 1 || w > kTW || n < 1 || n > 0x7fffffffll || !gram_tc_aligned(Y, ldY)) return cudaErrorInvalidValue;
-  const int parts = gram_tc_parts(n);
+bool gram_tc_fits(int64_t n) {
   // a sliced sum takes <= 10 additions per chunk: at most 2^11 chunks per CTA
-  if ((n + kTChunk - 1) / kTChunk > (int64_t)parts * 2048) return cudaErrorInvalidValue;
+  return n >= 1 && n <= 0x7fffffffll && (n + kTChunk - 1) / kTChunk <= (int64_t)gram_tc_parts(n) * 2048;
+}
+
+cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, bool emax_ready,
+                           double* partials, cudaStream_t s, int* err, bool stall_test) {
+  if (w < 1 || w > kTW || !gram_tc_fits(n) || !gram_tc_aligned(Y, ldY)) return cudaErrorInvalidValue;
+  const int parts = gram_tc_parts(n);
   cudaError_t e = smem_limit_once(g_tc_smem_set, gram_tc_kernel, (int)kTcSmem);
   if (e != cudaSuccess) return e;
   CUtensorMap map;
@@ -817,7 +830,8 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials);
+  const TcGuard guard{stall_test ? kTestWaitLimit : kWaitLimit, stall_test ? 0 : -1, err};
+  gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials, guard);
   return cudaGetLastError();
 }
 
@@ -843,10 +857,11 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
 }
 
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
-                            bool emax_ready, double* partials, int* nparts, cudaStream_t s) {
-  if (!force_fp64 && gram_tc_applies(w) && gram_tc_aligned(Y, ldY)) {
+                            bool emax_ready, double* partials, int* nparts, cudaStream_t s, int* err,
+                            bool stall_test) {
+  if (!force_fp64 && gram_tc_applies(w) && gram_tc_aligned(Y, ldY) && gram_tc_fits(n)) {
     *nparts = gram_tc_parts(n);
-    return launch_gram_tc(n, w, Y, ldY, exp_parts, emax_ready, partials, s);
+    return launch_gram_tc(n, w, Y, ldY, exp_parts, emax_ready, partials, s, err, stall_test);
   }
   *nparts = gram_parts(n);
   return launch_gram_partial(n, w, Y, ldY, partials, s);

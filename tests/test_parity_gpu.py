@@ -304,6 +304,34 @@ def block_inputs(name, kind, sbar, warm):
     return A, bp, b, O.gram(Y)
 
 
+def _far_threshold_eps(blk, eps, n):
+    """A target eps* whose eq. (condy) threshold lies midway (geometrically)
+    between two of the oracle's sqrt(kappa(G_{k,i})), far from all of them, so
+    that the s~ decision cannot be within rounding of the threshold. The
+    threshold is eps* / (c eps ||r_{m+1}||) with c = 1, so eps* scales with it."""
+    T = blk["threshold"]
+    finite = sorted(s for _i, s, _u in blk["kappas"] if math.isfinite(s))
+    if not finite:
+        return eps
+    below = [s for s in finite if s < T]
+    above = [s for s in finite if s >= T]
+    if below and above:
+        T2 = math.sqrt(below[-1] * above[0])
+    elif above:
+        T2 = above[0] / 16.0
+    else:
+        T2 = below[-1] * 16.0
+    return eps * T2 / T
+
+
+def _block_step(P, torch, A, bp, Gi, sbar, eps):
+    w = 2 * sbar + 1
+    coords = torch.zeros(3 * w, dtype=torch.float64, device="cuda")
+    info, hist = P.ascg_block_step(sbar, dev(torch, Gi.ravel()), P.ASCG_ADAPTIVE, bp.theta[:sbar], bp.sigma[:sbar],
+                                   bp.gamma[:sbar], A.n, eps, 1.0, 1, 1000, 1.0, coords)
+    return info, hist, coords
+
+
 @pytest.mark.parametrize("name,kind,sbar,warm,eps", [
     ("poisson2d_32", "monomial", 8, 20, 1e-10),
     ("poisson2d_32", "monomial", 8, 0, 1e-10),       # first block: p = r, rank deficient
@@ -313,21 +341,32 @@ def block_inputs(name, kind, sbar, warm):
     ("poisson3d_23", "newton", 12, 30, 1e-10),
 ])
 def test_block_step_parity(env, name, kind, sbar, warm, eps):
+    """One block controller step on the same G on both sides. When the s~
+    decision at the given target lies within the rounding uncertainty of its
+    threshold, the same G is compared again at a target whose threshold lies
+    far from every sqrt(kappa(G_{k,i})), so every case asserts the decision."""
     P, torch = env
     A, bp, b, G = block_inputs(name, kind, sbar, warm)
     w = 2 * sbar + 1
     perm = interleave_perm(sbar)
     Gi = G[np.ix_(perm, perm)]
-    coords = torch.zeros(3 * w, dtype=torch.float64, device="cuda")
-    info, hist = P.ascg_block_step(sbar, dev(torch, Gi.ravel()), P.ASCG_ADAPTIVE, bp.theta[:sbar], bp.sigma[:sbar],
-                                   bp.gamma[:sbar], A.n, eps, 1.0, 1, 1000, 1.0, coords)
+    info, hist, coords = _block_step(P, torch, A, bp, Gi, sbar, eps)
     blk, inner, idx = O.adaptive_block(G, sbar, bp, eps, 1.0, A.n, True, 1000)
     sk_g = [info.sqrt_kappa[i] for i in range(sbar)]
     gblk = dict(sbar=sbar, stilde=info.stilde, s_k=info.s_k, sqrt_kappa=sk_g, threshold=info.threshold)
     exempt, bad = parity.compare_block_sequences([gblk], [blk], A.n)
     assert not bad, bad
     if exempt is not None:
-        pytest.skip("decision within rounding uncertainty of its threshold")
+        eps2 = _far_threshold_eps(blk, eps, A.n)
+        print(f"decision at eps* = {eps:g} within rounding of its threshold; compared at eps* = {eps2:g}")
+        eps = eps2
+        info, hist, coords = _block_step(P, torch, A, bp, Gi, sbar, eps)
+        blk, inner, idx = O.adaptive_block(G, sbar, bp, eps, 1.0, A.n, True, 1000)
+        sk_g = [info.sqrt_kappa[i] for i in range(sbar)]
+        gblk = dict(sbar=sbar, stilde=info.stilde, s_k=info.s_k, sqrt_kappa=sk_g, threshold=info.threshold)
+        exempt, bad = parity.compare_block_sequences([gblk], [blk], A.n)
+        assert not bad and exempt is None, (bad, exempt)
+    assert info.stilde == blk["stilde"] and info.s_k == blk["s_k"]
     assert abs(info.threshold - blk["threshold"]) <= 1e-12 * blk["threshold"]
     for i, s_o, unc in blk["kappas"]:
         s_g = sk_g[i - 1]
@@ -503,8 +542,40 @@ def run_oracle(A, b, x1, kw, eps, lam, max_iters=20000):
                                gram_mode="moments" if kw.get("moment_gram") else "plain")
 
 
+def _gram_sequential(Y):
+    """Y^T Y with every entry summed row by row in index order: a valid
+    summation order other than the oracle's BLAS product (as in
+    tests/test_tolerances.py)."""
+    w = Y.shape[1]
+    G = np.empty((w, w))
+    for a in range(w):
+        for c in range(a, w):
+            G[a, c] = G[c, a] = np.cumsum(Y[:, a] * Y[:, c])[-1]
+    return G
+
+
+def oracle_spread(monkeypatch, A, b, x1, kw, eps, lam, base):
+    """The oracle run again with its Gram summed in another valid order
+    (sequentially for Y^T Y; over reversed rows for the moment Gram). Returns
+    its residual history and the number of leading entries produced by the
+    same block sequence as the base run (after that the two runs may take
+    different, equally valid, s_k decisions)."""
+    orig_gram, orig_moments = O.gram, O.gram_moments
+    with monkeypatch.context() as m:
+        m.setattr(O, "gram", _gram_sequential)
+        m.setattr(O, "gram_moments", lambda Y, s: orig_moments(Y[::-1], s))
+        alt = run_oracle(A, b, x1, kw, eps, lam)
+    assert O.gram is orig_gram
+    limit = min(len(alt.res_hist), len(base.res_hist))
+    for bo, ba in zip(base.blocks, alt.blocks):
+        if (bo["sbar"], bo["stilde"], bo["s_k"]) != (ba["sbar"], ba["stilde"], ba["s_k"]):
+            limit = min(limit, bo["m"] + 1)
+            break
+    return np.asarray(alt.res_hist), limit
+
+
 @pytest.mark.parametrize("name,kw,eps", SOLVES)
-def test_solve_parity(env, name, kw, eps):
+def test_solve_parity(env, monkeypatch, record_property, name, kw, eps):
     P, torch = env
     A = MATRICES[name]()
     b = W.rhs_uniform(A.n, np.random.default_rng(1001))
@@ -516,9 +587,12 @@ def test_solve_parity(env, name, kw, eps):
     res, hist, blocks, x = run_gpu(P, torch, A, b, x1, kwg, eps)
     orc = run_oracle(A, b, x1, kw, eps, lam)
     assert res.status == P.ASCG_OK and orc.converged, (res.status, orc.status)
+    reason = None
     if kw["method"] == "adaptive":
         exempt, bad = parity.compare_block_sequences(blocks, orc.blocks, A.n, orc.res_hist, eps)
         assert not bad, bad
+        if exempt is not None:
+            reason = f"block {exempt} (m = {orc.blocks[exempt]['m']}) is exempt: its decision lies within rounding"
         if "c_formula" in kw:  # the eq. (condy) threshold with c_{k,s_max}: ||B||, N_A and the factors
             assert abs(blocks[0]["threshold"] - orc.blocks[0]["threshold"]) <= 1e-12 * orc.blocks[0]["threshold"]
     else:
@@ -531,8 +605,27 @@ def test_solve_parity(env, name, kw, eps):
         nwin = max(nwin, min(25, len(hist)))   # the classical warm-up is compared too
     hg, ho = np.asarray(hist[:nwin]), np.asarray(orc.res_hist[:nwin])
     assert len(hg) == len(ho)
+    # every comparison covers the first 20 iterations (21 entries with the initial
+    # residual), unless a logged exempt decision ends it earlier
+    full = min(21, len(orc.res_hist), len(hist))
+    print(f"{name} {kw}: history entries compared {len(hg)}" + (f" ({reason})" if reason else ""))
+    record_property("history_entries", len(hg))
+    assert len(hg) >= full or reason is not None, (len(hg), full)
     tau = parity.history_tolerance(getattr(orc, "blocks", []) if kw["method"] == "adaptive" else [], ho, nwin)
     assert np.all(np.abs(hg - ho) <= tau), (np.abs(hg - ho) / tau).max()
+    wide = tau > 1e-10
+    if np.any(wide):
+        # the widened tolerance must earn its use: the GPU moves from the oracle
+        # by no more than a small multiple of what the oracle itself moves under
+        # another valid summation order of G, on the same solve
+        halt, lim = oracle_spread(monkeypatch, A, b, x1, kw, eps, lam, orc)
+        sel = np.flatnonzero(wide[:lim])
+        if sel.size:
+            spread = np.max(np.abs(halt[sel] - ho[sel]))
+            gdev = np.max(np.abs(hg[sel] - ho[sel]))
+            print(f"  widened entries {sel.size}: gpu deviation {gdev:.3g}, oracle spread {spread:.3g}")
+            record_property("gpu_dev_over_oracle_spread", float(gdev / max(spread, 1e-300)))
+            assert gdev <= max(10.0 * spread, 1e-10), (gdev, spread)
     if exempt is None and kw["method"] == "adaptive":
         assert len(blocks) == len(orc.blocks) and res.iters == orc.iters
     assert parity.final_residual_ok(res.rel_res_true, orc.true_res, eps, exempt), (res.rel_res_true, orc.true_res)
@@ -672,16 +765,41 @@ def test_full_size_poisson3d_128(env):
     P.ascg_op_destroy(op)
 
 
-def test_full_size_diffusion_2048_warmup_and_shifts(env):
-    """2D diffusion 2048^2, Newton basis: the 24 warm-up iterations and the shifts."""
+def test_full_size_diffusion_2048(env, record_property):
+    """2D diffusion 2048^2 (log-normal sigma = 2 coefficients), adaptive Newton
+    basis, s_max = 12, 24 warm-up iterations, target 1e-10: solved to
+    convergence at full size. Against the oracle: the 24 warm-up iterations and
+    the first 20 s-step iterations after them, the s_k sequence of the two
+    blocks that cover them (oracle capped at 48 iterations), and the Newton
+    shifts. The oracle's whole
+    solve (about 11,700 iterations of a 4.2M-row system in numpy) takes hours,
+    so the final true residual is held to 2x the target instead of 2x the
+    oracle's."""
     P, torch = env
     cfg = W.diffusion2d_2048()
     A, b = cfg["A"], cfg["b"]
     kw = dict(method="adaptive", basis="newton", s_max=12, newton_warmup=24)
-    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-10, max_iters=60)
+    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), kw, 1e-10, max_iters=60000)
+    assert res.status == P.ASCG_OK, res.status
+    assert res.rel_res_true <= 2e-10, res.rel_res_true
     Ao = O.Operator.from_csr(A)
-    cl = O.classical_cg(Ao, b, np.zeros(A.n), eps_target=1e-10, max_iters=24)
-    assert np.all(np.abs(hist[:25] - np.asarray(cl.res_hist[:25])) <= 1e-10)
-    want = O.leja_order(O.ritz_values(cl.alphas, cl.betas))[:12]
-    got = P.ascg_newton_shifts(cl.alphas, cl.betas, 24, 12)
+    cap = 24 + 24
+    orc = O.adaptive_sstep_cg(Ao, b, np.zeros(A.n), s_max=12, eps_target=1e-10, basis="newton", newton_warmup=24,
+                              max_iters=cap)
+    # blocks the oracle's iteration cap did not cut short
+    whole = [o for o in orc.blocks if o["m"] + o["s_k"] < cap or o["s_k"] == o["stilde"]]
+    assert len(whole) >= 1
+    exempt, bad = parity.compare_block_sequences(blocks, whole, A.n)
+    assert not bad, bad
+    nwin = parity.history_window(blocks, orc.blocks, exempt, iters=24 + 20)
+    print(f"diffusion 2048^2: {res.iters} iterations in {res.blocks} blocks, true residual {res.rel_res_true:.3e}; "
+          f"history entries compared {nwin}, s_k of {len(whole)} blocks")
+    record_property("history_entries", nwin)
+    assert nwin == 24 + 20 + 1 or exempt is not None, (nwin, exempt)
+    tau = parity.history_tolerance(orc.blocks, np.asarray(orc.res_hist), nwin)
+    assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= tau), \
+        (np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) / tau).max()
+    assert all(bg["sbar"] == 12 for bg in blocks)
+    want = O.leja_order(O.ritz_values(orc.alphas[:24], orc.betas[:24]))[:12]
+    got = P.ascg_newton_shifts(orc.alphas[:24], orc.betas[:24], 24, 12)
     assert np.allclose(got, want, rtol=0, atol=1e-12 * max(abs(v) for v in want))
