@@ -100,6 +100,8 @@ def parse():
                     help="solver timed as the step (classical CG is the comparison baseline)")
     ap.add_argument("--no-classical", action="store_true", help="skip the classical-CG comparison solves")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-sequential", action="store_true",
+                    help="batch workload: skip the one-by-one adaptive solves of the same systems")
     ap.add_argument("--no-all-cores", action="store_true",
                     help="skip the all-host-cores oracle baseline (one replica per core)")
     ap.add_argument("--autotune", action="store_true",
@@ -109,6 +111,10 @@ def parse():
     ap.add_argument("--requests", type=int, default=200, help="served workload: requests in the open-loop run")
     ap.add_argument("--load", type=float, default=0.7, help="served workload: arrival rate / saturation throughput")
     ap.add_argument("--budget-gb", type=float, default=150.0, help="served workload: device-memory budget (GB)")
+    ap.add_argument("--policy", default="sjf", choices=["fifo", "sjf"],
+                    help="served workload: admission order (submission order, or shortest estimated work first)")
+    ap.add_argument("--large-cap", type=int, default=1,
+                    help="served workload: most systems of >= 2^19 rows running at once (0: no cap)")
     ap.add_argument("--workload", default="poisson3d_128",
                     choices=list(SINGLE_WORKLOADS) + ["batch", "serve"],
                     help="a single-solve workload, or batch: 256 uneven systems solved by ascg_solve_batch (one "
@@ -610,19 +616,49 @@ def batch_arm(args):
     value = iters * args.steps / (ms * 1e-3)
     ok = all(r.status == P.ASCG_OK for r in res)
     worst_true = max(r.rel_res_true / e for r, e in zip(res, eps))
-    # the same systems one by one through ascg_solve (tensor-core Gram where w >= 9)
-    seq_iters = 0
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    s0.record(stream)
-    for q in range(len(systems)):
-        xs[q].zero_()
-        oq = P.ascg_options.from_buffer_copy(o)
-        oq.eps_target = eps[q]
-        r = P.ascg_solve(ops[q], bs[q], xs[q], oq, stream=stream)
-        seq_iters += r.iters
-    s1.record(stream)
-    torch.cuda.synchronize()
-    seq_ms = s0.elapsed_time(s1)
+    def one_by_one(opts):
+        """The same systems solved one by one through ascg_solve with opts."""
+        its = 0
+        s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        for q in range(len(systems)):
+            xs[q].zero_()
+            oq = P.ascg_options.from_buffer_copy(opts)
+            oq.eps_target = eps[q]
+            r = P.ascg_solve(ops[q], bs[q], xs[q], oq, stream=stream)
+            its += r.iters
+        s1.record(stream)
+        torch.cuda.synchronize()
+        return s0.elapsed_time(s1), its
+
+    seq_ms = seq_iters = None
+    classical = None
+    if not args.no_sequential:
+        # the same systems one by one through ascg_solve (tensor-core Gram where w >= 9)
+        seq_ms, seq_iters = one_by_one(o)
+    if not args.no_classical:
+        # classical CG (Alg. 1) on the same systems and targets: one by one through
+        # ascg_solve, and batched in the same lockstep engine as s-step CG with
+        # s = 1 (Alg. 2 with s = 1 equals classical CG in exact arithmetic, one
+        # global reduction per iteration)
+        oc = P.make_options(method="classical", eps_target=1e-10, max_iters=200000)
+        c_ms, c_its = one_by_one(oc)
+        o1 = P.make_options(method="fixed", basis="monomial", s_max=1, eps_target=1e-10, max_iters=200000)
+        for x in xs:
+            x.zero_()
+        torch.cuda.synchronize()
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        r1, _st1 = P.ascg_solve_batch(ops, bs, xs, o1, eps_targets=eps, stream=stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        s1_ms = b0.elapsed_time(b1)
+        classical = {"one_by_one_ms": c_ms, "one_by_one_iters": c_its,
+                     "s1_batched_ms": s1_ms, "s1_batched_iters": sum(r.iters for r in r1),
+                     "s1_batched_ok": all(r.status == P.ASCG_OK for r in r1),
+                     "adaptive_batched_ms": ms / args.steps,
+                     "speedup_vs_classical_one_by_one": c_ms / (ms / args.steps),
+                     "speedup_vs_s1_batched": s1_ms / (ms / args.steps)}
     line = {
         "metric": "batched CG iters/s (256 uneven SPD systems, one ascg_solve_batch call per step)",
         "value": value, "unit": "iters/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -637,8 +673,10 @@ def batch_arm(args):
                             "FP64 FMAs on per-system row items below")},
         "status_ok": ok, "iters_per_batch": iters, "lockstep_blocks": res[0].launches,
         "worst_true_res_over_target": worst_true,
-        "sequential": {"ms": seq_ms, "iters": seq_iters, "iters_per_s": seq_iters / (seq_ms * 1e-3),
-                       "batch_speedup": seq_ms / (ms / args.steps)},
+        "sequential": None if seq_ms is None else {
+            "ms": seq_ms, "iters": seq_iters, "iters_per_s": seq_iters / (seq_ms * 1e-3),
+            "batch_speedup": seq_ms / (ms / args.steps)},
+        "vs_classical": classical,
         "setup_s": t_gen, "clocks": clocks, "gram_schedule": tuned or {"tc_lane_rows": 1 << 10, "source": "default"},
     }
     print(json.dumps(line), flush=True)
@@ -678,8 +716,9 @@ def serve_arm(args):
     ops = [P.ascg_op_create_csr(p["A"].n, p["A"].nnz, p["A"].rowptr, p["A"].colind, p["A"].val, 0) for p in pool]
     nop = [p["A"].n for p in pool]
     nreq = max(int(args.requests), 8)
-    nwarm = max(4, nreq // 10)
-    ne2e = max(8, nreq // 4)
+    nwarm = max(4, min(nreq // 10, 40))
+    ne2e = max(8, min(nreq // 4, 100))
+    nsat = min(nreq, 300)   # the saturation sample: the first requests of the stream
     req = W.serve_requests(nreq)
     t_gen = time.perf_counter() - t_gen
 
@@ -697,6 +736,8 @@ def serve_arm(args):
     budget = int(args.budget_gb * 1e9)
     slots = 256
     srv = P.ascg_server_create(o, budget, slots, stream)
+    order = P.ASCG_ADMIT_SHORTEST_FIRST if args.policy == "sjf" else P.ASCG_ADMIT_FIFO
+    P.ascg_server_set_policy(srv, order, args.large_cap)
 
     def run(idx, arrivals, host_io=False):
         """Serves requests idx arriving at `arrivals` (seconds from the start).
@@ -743,10 +784,10 @@ def serve_arm(args):
         wall = time.perf_counter() - t0
         return lat, comp, wall, peak, P.ascg_server_info(srv).steps - steps0
 
-    # (1) saturation: the stream's requests, all submitted at once
+    # (1) saturation: the stream's first requests, all submitted at once
     run(np.arange(nwarm), np.zeros(nwarm))  # warm-up
-    _, _, sat_wall, sat_peak, _ = run(np.arange(nreq), np.zeros(nreq))
-    mu = nreq / sat_wall
+    _, _, sat_wall, sat_peak, _ = run(np.arange(nsat), np.zeros(nsat))
+    mu = nsat / sat_wall
     lam = args.load * mu
     # (2) open loop at load x saturation
     idx = np.arange(nreq)
@@ -764,6 +805,12 @@ def serve_arm(args):
     iters = sum(comp[i].result.iters for i in range(nreq))
     ok = all(comp[i].result.status == P.ASCG_OK for i in range(nreq))
     worst = max(comp[i].result.rel_res_true / req["eps"][i] for i in range(nreq))
+    # latency by request size (rows): thirds of the log-uniform range
+    edges = [0, 1e5, 1e6, float("inf")]
+    by_size = {}
+    for lo_, hi_ in zip(edges[:-1], edges[1:]):
+        sel = [lat_ms[i] for i in range(nreq) if lo_ <= nop[req["op"][i]] < hi_]
+        by_size[f"n<{hi_:g}"] = {"count": len(sel), "p50_ms": _pct(sel, 50), "p99_ms": _pct(sel, 99)}
     # (3) FIFO sequential classical CG on the same arrivals, from measured service times
     oc = P.make_options(method="classical", eps_target=1e-10, max_iters=200000)
     service = {}
@@ -778,11 +825,15 @@ def serve_arm(args):
         c1.record(stream)
         torch.cuda.synchronize()
         service[key] = c0.elapsed_time(c1) * 1e-3
-    fin, fifo = 0.0, []
+    fin, fifo, fifo_of = 0.0, [], {}
     for k in np.argsort(arrivals, kind="stable"):
         fin = max(arrivals[k], fin) + service[(int(req["op"][k]), float(req["eps"][k]))]
         fifo.append(1e3 * (fin - arrivals[k]))
+        fifo_of[int(k)] = fifo[-1]
     fifo_wall = fin - arrivals.min()
+    for lo_, hi_ in zip(edges[:-1], edges[1:]):
+        sel = [fifo_of[i] for i in range(nreq) if lo_ <= nop[req["op"][i]] < hi_]
+        by_size[f"n<{hi_:g}"].update({"classical_fifo_p50_ms": _pct(sel, 50), "classical_fifo_p99_ms": _pct(sel, 99)})
     # (4) end to end: host right-hand sides in, solutions out
     e_idx = np.arange(ne2e)
     elat, _, ewall, _, _ = run(e_idx, arrivals[:ne2e], host_io=True)
@@ -801,6 +852,8 @@ def serve_arm(args):
                    "pool_n": nop, "pool_nnz": [int(p["A"].nnz) for p in pool],
                    "gram": "Hankel moments (a variant)" if args.moment_gram else "Y^T Y"},
         "p50_ms": _pct(lat_ms, 50), "p99_ms": _pct(lat_ms, 99), "max_ms": max(lat_ms),
+        "policy": {"admit": args.policy, "large_class_cap": args.large_cap}, "by_size": by_size,
+        "saturation_sample": nsat,
         "throughput_rps": nreq / wall, "arrival_rps": lam, "saturation_rps": mu,
         "saturation_wall_s": sat_wall, "saturation_peak_running": sat_peak, "peak_running": peak,
         "server_steps": steps, "iters_per_s": iters / wall, "status_ok": ok, "worst_true_res_over_target": worst,

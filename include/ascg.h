@@ -130,7 +130,14 @@ typedef struct {
 
 #define ASCG_FLAG_TIMING 1   /* time the Gram kernel and phases with CUDA events  */
 #define ASCG_FLAG_GRAM_FP64 2 /* Gram by FP64 FMAs on the CUDA cores for every w,
-                                 instead of the tensor-core kernel (w >= 9)      */
+                                 instead of the tensor-core kernel. By default
+                                 ascg_solve runs the Gram on the tensor cores
+                                 when w >= 9 and n w(w+1)/2 >= 2^25 (below
+                                 that the FP64 kernel costs less than the
+                                 tensor-core kernel's fixed cost)               */
+#define ASCG_FLAG_GRAM_TC 32  /* ascg_solve: the tensor-core Gram for every
+                                 block with w >= 9, whatever n (excludes
+                                 ASCG_FLAG_GRAM_FP64 and ASCG_FLAG_MOMENT_GRAM) */
 #define ASCG_FLAG_MOMENT_GRAM 8 /* monomial basis only: G from 6 sbar moments
                                  (ascg_gram_moments) instead of Y^T Y; a
                                  variant that rounds differently            */
@@ -143,7 +150,7 @@ typedef struct {
                                  copies and MMAs land, its tensor memory is
                                  freed) and the solve returns ASCG_ERR_TIMEOUT
                                  with x = x_1. No effect when the block's Gram
-                                 takes the FP64 kernel (w < 9).              */
+                                 takes the FP64 kernel (see ASCG_FLAG_GRAM_TC). */
 #define ASCG_FLAG_C_FORMULA 4 /* c_{k,j} = 6 N_k j kappa(A), the factor of the gap
                                  bound eq. (fb), instead of the constant c:
                                  N_k = 7 + 2 N_A + 14 ||B_k|| / ||A||, N_A = most
@@ -304,8 +311,8 @@ ascg_status ascg_gram(int64_t n, int w, const double* Y, int64_t ldY, double* G,
  * the rounding of the basis recurrence. Synchronises the stream. */
 ascg_status ascg_gram_moments(int64_t n, int s, const double* Y, int64_t ldY, double* G, void* cuda_stream);
 
-/* One block controller step on a given Gram matrix (Alg. 4 from "Determine
- * s~_k" to the end of the inner loop). G: device double[(2 sbar+1)^2],
+/* One block controller step on a given Gram matrix (Alg. 4, Sec. 3.2: the
+ * choice of s~_k by eq. (condy), then the inner loop). G: device double[(2 sbar+1)^2],
  * interleaved order as above. method: ASCG_ADAPTIVE (eq. (condy) and, if
  * check_in_loop, eq. (check)) or ASCG_FIXED_S (s~ = sbar, no test).
  * nrows: length n of the basis vectors (sets the certification floor
@@ -446,6 +453,27 @@ ascg_status ascg_server_submit(ascg_server srv, ascg_op op, const double* b, dou
  * still run on the GPU when it returns. */
 ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, int* ndone, int* nactive,
                              int* npending);
+
+/* Admission policy of a server. */
+typedef enum {
+  ASCG_ADMIT_FIFO = 0,            /* the scan visits requests in submission order
+                                     (the default)                               */
+  ASCG_ADMIT_SHORTEST_FIRST = 1   /* in increasing estimated work: rows times the
+                                     decimal digits of the target (n *
+                                     max(1, -log10 eps_target)); ties in
+                                     submission order                            */
+} ascg_admit_order;
+
+/* Sets the server's admission policy (host; takes effect at the next
+ * ascg_server_step). admit_order: ascg_admit_order. large_class_cap > 0: at
+ * most that many systems run at once in the largest size class (n >= 2^19),
+ * whose kernels cover the whole GPU by themselves, so that running more of
+ * them at once only shares the GPU among them; 0: no cap. The other rules of
+ * ascg_server_step stay: a class in the middle of a block admits nothing,
+ * and the first request that finds no slot or no memory stops the scan. A
+ * system's arithmetic does not depend on the policy. ASCG_ERR_INVALID for an
+ * unknown order or a negative cap. */
+ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap);
 
 /* Counters of the server (host). */
 ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* stats);

@@ -416,7 +416,7 @@ def formula_c_step(A: Operator, B, kappa_A: float, norm_A: float) -> float:
 def adaptive_block(G, sbar: int, bp: BasisParams, eps_star: float, c: float, nrows: int,
                    check_in_loop: bool = True, max_steps: int | None = None, trace: bool = False,
                    c_step: float | None = None, s_max: int | None = None):
-    """One block of Alg. 4 after G is formed: "Determine s~_k" to the end of the inner loop.
+    """One block of Alg. 4 (Sec. 3.2) after G is formed: the choice of s~_k, then the inner loop.
 
     ||r_{m+1}|| = sqrt(G[i_s, i_s]) (column i_s is r since rho_0 = 1);
     threshold = eps* / (c_{k,s_max} eps ||r_{m+1}||); s~ by eq. (condy); gamma =

@@ -36,6 +36,7 @@ ASCG_FLAG_GRAM_FP64 = 2
 ASCG_FLAG_C_FORMULA = 4
 ASCG_FLAG_MOMENT_GRAM = 8
 ASCG_FLAG_TEST_GRAM_STALL = 16
+ASCG_FLAG_GRAM_TC = 32
 
 
 class ascg_block_info(C.Structure):
@@ -111,6 +112,7 @@ def _load():
         "ascg_server_step": (C.c_int, [P, C.POINTER(ascg_completion), C.c_int, C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "ascg_server_info": (C.c_int, [P, C.POINTER(ascg_server_stats)]),
+        "ascg_server_set_policy": (C.c_int, [P, C.c_int, C.c_int]),
         "ascg_server_destroy": (C.c_int, [P]),
         "ascg_tune_gram_schedule": (C.c_int, [C.c_int, C.POINTER(I64), P, C.c_int, C.POINTER(C.c_int), P]),
         "ascg_last_error": (C.c_char_p, []),
@@ -241,6 +243,13 @@ def ascg_server_step(srv, cap=64):
     return [buf[i] for i in range(nd.value)], na.value, npd.value
 
 
+ASCG_ADMIT_FIFO, ASCG_ADMIT_SHORTEST_FIRST = 0, 1
+
+
+def ascg_server_set_policy(srv, admit_order, large_class_cap=0):
+    _check(_lib.ascg_server_set_policy(srv, int(admit_order), int(large_class_cap)), "ascg_server_set_policy")
+
+
 def ascg_server_info(srv):
     st = ascg_server_stats()
     _check(_lib.ascg_server_info(srv, C.byref(st)), "ascg_server_info")
@@ -338,7 +347,7 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
                  gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False,
-                 tc_lane_rows=0, test_gram_stall=False) -> ascg_options:
+                 tc_lane_rows=0, test_gram_stall=False, gram_tc=False) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
@@ -364,6 +373,8 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
         o.flags |= ASCG_FLAG_MOMENT_GRAM
     if test_gram_stall:
         o.flags |= ASCG_FLAG_TEST_GRAM_STALL
+    if gram_tc:
+        o.flags |= ASCG_FLAG_GRAM_TC
     if c_formula is not None:
         o.flags |= ASCG_FLAG_C_FORMULA
         o.kappa_A, o.norm_A = float(c_formula[0]), float(c_formula[1])
@@ -394,4 +405,5 @@ EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "as
             "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc", "ascg_gram_moments",
             "ascg_block_step", "ascg_recover",
             "ascg_newton_shifts", "ascg_server_create", "ascg_server_submit", "ascg_server_step",
-            "ascg_server_info", "ascg_server_destroy", "ascg_tune_gram_schedule", "ascg_last_error"]
+            "ascg_server_info", "ascg_server_set_policy", "ascg_server_destroy", "ascg_tune_gram_schedule",
+            "ascg_last_error"]

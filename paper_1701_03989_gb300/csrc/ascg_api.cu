@@ -210,6 +210,11 @@ namespace {
 
 int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// Products n w(w+1)/2 from which a single solve's Gram runs on the tensor
+// cores by default (measured on GB300: the tensor-core kernel costs about
+// 40 us at n = 1024, w = 17, where the FP64 kernel takes a few).
+constexpr double kTcSolveProducts = 33554432.0;  // 2^25
+
 // Ensures the workspace can hold n rows, wcols basis columns and histories of
 // res_cap entries.
 ascg_status ensure(ascg_op op, int wcols, int res_cap) {
@@ -349,6 +354,8 @@ ascg_status check_opts(const ascg_options& o) {
       if (nw < o.s_max || nw > 32) return fail(ASCG_ERR_INVALID, "newton_warmup must be in s_max..32");
     }
   }
+  if ((o.flags & ASCG_FLAG_GRAM_TC) && (o.flags & (ASCG_FLAG_GRAM_FP64 | ASCG_FLAG_MOMENT_GRAM)))
+    return fail(ASCG_ERR_INVALID, "ASCG_FLAG_GRAM_TC excludes ASCG_FLAG_GRAM_FP64 and ASCG_FLAG_MOMENT_GRAM");
   if ((o.flags & ASCG_FLAG_MOMENT_GRAM) && (o.method == ASCG_CLASSICAL || o.basis != ASCG_MONOMIAL))
     return fail(ASCG_ERR_INVALID, "ASCG_FLAG_MOMENT_GRAM needs an s-step method with the monomial basis");
   if (o.flags & ASCG_FLAG_C_FORMULA) {
@@ -470,6 +477,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
   ASCG_TRY(ensure(op, wmax, o.max_iters + 2));
   const bool timing = (o.flags & ASCG_FLAG_TIMING) != 0;
   const bool gram_fp64 = (o.flags & ASCG_FLAG_GRAM_FP64) != 0;
+  const bool gram_tc_force = (o.flags & ASCG_FLAG_GRAM_TC) != 0;
   const bool gram_mom = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
   const bool stall_test = (o.flags & ASCG_FLAG_TEST_GRAM_STALL) != 0;
   if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
@@ -607,8 +615,13 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
       // the steps also record each basis column's largest exponent for the tensor-core Gram
-      const bool tc_gram =
-          !gram_fp64 && !gram_mom && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY) && gram_tc_fits(n);
+      // The tensor cores take the Gram when its FP64 work, n w(w+1)/2 products,
+      // is large enough to pay for the kernel's fixed cost (tensor memory,
+      // barriers, pipeline fill: about 40 us on GB300, against about 1 us per
+      // 2^20 products in FP64), or when ASCG_FLAG_GRAM_TC asks for them.
+      const bool tc_big = gram_tc_force || (double)n * wb * (wb + 1) / 2.0 >= kTcSolveProducts;
+      const bool tc_gram = !gram_fp64 && !gram_mom && tc_big && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY) &&
+                           gram_tc_fits(n);
       for (int j = 0; j < sbar; ++j) {
         ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], Yc, w.ldY, j, 1, j < sbar - 1,
                                         tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
@@ -624,7 +637,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       if (gram_mom)
         ASCG_CUDA(launch_gram_moments(n, wb, Yc, w.ldY, w.partials, &nparts, s));
       else
-        ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, gram_fp64, w.expp, tc_gram, w.partials, &nparts, s,
+        ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, !tc_gram, w.expp, tc_gram, w.partials, &nparts, s,
                                   &w.bst->status, stall_test && k == 0));
       if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
       if (gram_mom)

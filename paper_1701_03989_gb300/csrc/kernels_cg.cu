@@ -14,7 +14,10 @@ namespace ascg {
 
 namespace {
 
-// sum_j a_ij x_j for row i (i < A.n) in stored order, starting from 0.
+// sum_j a_ij x_j for row i (i < A.n) in stored order, starting from 0. The
+// values and column indices of A are read once per pass: they are loaded with
+// the evict-first (streaming) policy, so that the vectors of the iteration,
+// which every pass reads again, keep their place in L2.
 __device__ __forceinline__ double sell_row(const DevSell& A, int64_t i, const double* __restrict__ x) {
   const int64_t s = i >> 5;
   const int l = (int)(i & 31);
@@ -23,7 +26,7 @@ __device__ __forceinline__ double sell_row(const DevSell& A, int64_t i, const do
   const double* v = A.val + b + l;
   const int32_t* c = A.col + b + l;
   double t = 0.0;
-  for (int j = 0; j < width; ++j) t = fma(__ldg(v + kSlice * j), __ldg(x + __ldg(c + kSlice * j)), t);
+  for (int j = 0; j < width; ++j) t = fma(__ldcs(v + kSlice * j), __ldg(x + __ldcs(c + kSlice * j)), t);
   return t;
 }
 

@@ -94,34 +94,45 @@ __device__ __forceinline__ int sturm_unrolled(const double (&d)[M], const double
   return cnt;
 }
 
-// 33-way multisection (one warp) for the smallest x with count(x) >= target on
-// [lo, hi]. geo0: the first round uses the points hi * 2^-(32-t), t = 0..31.
-// Returns through lo/hi; stop_below: if the first geometric bracket lies at or
-// below this value, sets *below and stops.
+// 65-way multisection by a pair of warps (64 evaluation points per round, 32
+// per warp, the pair synchronised by the named barrier bar_id of 64 threads),
+// for the smallest x with count(x) >= target on [lo, hi]. half: the warp's
+// place in the pair. geo0: the first round uses the points hi * 2^(k - 64),
+// k = 0..63. stop_below: if the first geometric bracket lies at or below this
+// value, sets *below and stops. Both warps compute the same brackets.
 template <int M>
-__device__ void multisect_warp(const double* ds, const double* e2s, int target, int rounds, bool geo0,
-                               double stop_below, double* lo_io, double* hi_io, int* below) {
+__device__ void multisect_pair(const double* ds, const double* e2s, int target, int rounds, bool geo0,
+                               double stop_below, double* lo_io, double* hi_io, int* below, int half, int bar_id,
+                               unsigned* s_mask) {
   const int lane = threadIdx.x & 31;
+  const int k = lane + 32 * half;
   double d[M], e2[M];
 #pragma unroll
-  for (int k = 0; k < M; ++k) {
-    d[k] = ds[k];
-    e2[k] = k + 1 < M ? e2s[k] : 0.0;
+  for (int q = 0; q < M; ++q) {
+    d[q] = ds[q];
+    e2[q] = q + 1 < M ? e2s[q] : 0.0;
   }
-  const double kStep = 1.0 / 33.0;
+  const double kStep = 1.0 / 65.0;
   double lo = *lo_io, hi = *hi_io;
   for (int round = 0; round < rounds; ++round) {
     const bool geo = geo0 && round == 0;
-    const double x = geo ? ldexp(hi, lane - 32) : lo + (hi - lo) * ((double)(lane + 1) * kStep);
+    const double x = geo ? ldexp(hi, k - 64) : lo + (hi - lo) * ((double)(k + 1) * kStep);
     const unsigned mk = __ballot_sync(kFull, sturm_unrolled<M>(d, e2, x) >= target);
+    if (lane == 0) s_mask[half] = mk;
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+    const unsigned long long both = (unsigned long long)s_mask[0] | ((unsigned long long)s_mask[1] << 32);
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");  // both masks read before the next round
+    // the point k' of either warp, recomputed from the shared bracket
+    auto point = [&](int kk) {
+      return geo ? ldexp(hi, kk - 64) : lo + (hi - lo) * ((double)(kk + 1) * kStep);
+    };
     double nlo = lo, nhi = hi;
-    if (mk == 0u) {
-      nlo = __shfl_sync(kFull, x, 31);
+    if (both == 0ull) {
+      nlo = point(63);
     } else {
-      const int f = __ffs(mk) - 1;
-      nhi = __shfl_sync(kFull, x, f);
-      const double below_pt = __shfl_sync(kFull, x, f > 0 ? f - 1 : 0);
-      nlo = f > 0 ? below_pt : (geo ? 0.0 : lo);
+      const int f = __ffsll((long long)both) - 1;
+      nhi = point(f);
+      nlo = f > 0 ? point(f - 1) : (geo ? 0.0 : lo);
     }
     if (geo && nhi <= stop_below) {
       *below = 1;
@@ -134,16 +145,17 @@ __device__ void multisect_warp(const double* ds, const double* e2s, int target, 
   *hi_io = hi;
 }
 
-__device__ void multisect_dispatch(int m, const double* ds, const double* e2s, int target, int rounds, bool geo0,
-                                   double stop_below, double* lo, double* hi, int* below) {
+__device__ void multisect_pair_dispatch(int m, const double* ds, const double* e2s, int target, int rounds,
+                                        bool geo0, double stop_below, double* lo, double* hi, int* below, int half,
+                                        int bar_id, unsigned* s_mask) {
   switch (m) {
-#define ASCG_MS(M) \
-  case M:          \
-    multisect_warp<M>(ds, e2s, target, rounds, geo0, stop_below, lo, hi, below); \
+#define ASCG_MP(M)                                                                                          \
+  case M:                                                                                                   \
+    multisect_pair<M>(ds, e2s, target, rounds, geo0, stop_below, lo, hi, below, half, bar_id, s_mask); \
     break;
-    ASCG_MS(3) ASCG_MS(5) ASCG_MS(7) ASCG_MS(9) ASCG_MS(11) ASCG_MS(13) ASCG_MS(15) ASCG_MS(17)
-    ASCG_MS(19) ASCG_MS(21) ASCG_MS(23) ASCG_MS(25) ASCG_MS(27) ASCG_MS(29) ASCG_MS(31) ASCG_MS(33)
-#undef ASCG_MS
+    ASCG_MP(3) ASCG_MP(5) ASCG_MP(7) ASCG_MP(9) ASCG_MP(11) ASCG_MP(13) ASCG_MP(15) ASCG_MP(17)
+    ASCG_MP(19) ASCG_MP(21) ASCG_MP(23) ASCG_MP(25) ASCG_MP(27) ASCG_MP(29) ASCG_MP(31) ASCG_MP(33)
+#undef ASCG_MP
     default:
       break;
   }
@@ -167,11 +179,18 @@ __device__ __forceinline__ double warp_max(double v) {
 // reflection's scalars (norm, square root, one division) and publishes them
 // in shared memory. Only the O(len^2) product and rank-2 update are split by
 // columns over the four warps. The tridiagonal is then scaled to unit norm.
-// Warp 0 brackets lambda_min and warp 1 lambda_max with 32 Sturm counts per
-// round for a fixed 11 rounds. For lambda_min, the first round is on the powers
-// of two 2^-32..2^-1 times min d, which finds its magnitude and decides
-// certification (is it below the floor (2i+1) sqrt(n) eps lambda_max?).
-constexpr int kKappaRounds = 11;
+// Warps 0 and 1 bracket lambda_min and warps 2 and 3 lambda_max, each pair
+// with 64 Sturm counts per round (the four warps sit on the SM's four
+// sub-partitions, so the pairs' FP64 work runs side by side) for a fixed 6
+// rounds. For lambda_min, the first round is on the powers of two
+// 2^-64..2^-1 times min d, which finds its magnitude within a factor 2 and
+// decides certification (is it below the floor (2i+1) sqrt(n) eps
+// lambda_max?); five more rounds of 65 subintervals leave a bracket of
+// relative width < 1e-9. lambda_max starts from [max d, Gershgorin bound], at
+// most 2 lambda_max wide, and six rounds leave < 2e-10 of it. kappa is thus
+// known to about 1e-9, far inside the 1e-6 to which rounding in G already
+// makes decisions near a threshold uncertain.
+constexpr int kKappaRounds = 6;
 
 // Run by a whole CTA of 128 threads: sqrt(kappa(G_{k,i})) into st->sqrt_kappa[i-1]
 // (G: the system's w x w Gram matrix, w = 2 sbar + 1).
@@ -185,6 +204,7 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
   __shared__ double lo_s[2], hi_s[2];
   __shared__ double beta_s, floor_s;
   __shared__ int go_s, uncert_s;
+  __shared__ unsigned s_mask[2][2];
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -284,14 +304,15 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
     }
   }
   __syncthreads();
-  if (warp < 2) {
-    const int pair = warp;  // 0: lambda_min (geometric first round), 1: lambda_max
+  {
+    const int pair = warp >> 1, half = warp & 1;  // pair 0: lambda_min (geometric first round), 1: lambda_max
     double lo = lo_s[pair], hi = hi_s[pair];
     int below = 0;
-    if (!(pair == 0 && uncert_s))
-      multisect_dispatch(m, d, e2, pair == 0 ? 1 : m, kKappaRounds, pair == 0, pair == 0 ? floor_s : -1.0, &lo, &hi,
-                         &below);
-    if (lane == 0) {
+    if (!(pair == 0 && uncert_s))  // uniform over the pair
+      multisect_pair_dispatch(m, d, e2, pair == 0 ? 1 : m, kKappaRounds, pair == 0, pair == 0 ? floor_s : -1.0, &lo,
+                              &hi, &below, half, 1 + pair, s_mask[pair]);
+    __syncthreads();  // every warp has read lo_s, hi_s and uncert_s
+    if (lane == 0 && half == 0) {
       lo_s[pair] = lo;
       hi_s[pair] = hi;
       if (below) uncert_s = 1;
@@ -467,19 +488,27 @@ __device__ void spec_steps(const double* __restrict__ G, const double* __restric
 // Applies eq. (condy) and eq. (check) to the kappa values and the step
 // records (one CTA; the other CTAs' writes are read with L1-bypassing loads),
 // writes the block's outcome, the histories of the steps taken and their
-// coordinates.
+// coordinates. All loads are issued at once by the CTA's threads into shared
+// memory; thread 0 then decides on shared values only, so the decision does
+// not wait on a chain of dependent global loads.
 __device__ void select_steps(const double* __restrict__ G, BlockState* st, const double* __restrict__ rec,
                              double* __restrict__ coords, double* __restrict__ hist, double* __restrict__ res_hist,
                              int res_cap, double* __restrict__ ab_hist, int ab_cap) {
   __shared__ int s_steps;
+  __shared__ double s_sk[kMaxS], s_step[kMaxS][3], s_g11, s_done;
   const int t = threadIdx.x;
   const int sbar = st->sbar;
   const int w = 2 * sbar + 1;
+  if (t < 3 * sbar) s_step[t / 3][t % 3] = __ldcg(rec + (int64_t)(t / 3) * kSpecRow + 3 * kMaxW + t % 3);
+  if (t >= 64 && t < 64 + sbar) s_sk[t - 64] = __ldcg(&st->sqrt_kappa[t - 64]);
+  if (t == 96) s_g11 = __ldcg(G + 1 * w + 1);
+  if (t == 97) s_done = __ldcg(rec + kSpecDone);
+  __syncthreads();
   if (t == 0) {
     const int adaptive = st->method == ASCG_ADAPTIVE;
     const double eps_star = st->eps_star, cc = st->c, bnorm = st->bnorm;
     // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
-    const double rnorm = sqrt(fmax(__ldcg(G + 1 * w + 1), 0.0));
+    const double rnorm = sqrt(fmax(s_g11, 0.0));
     // eq. (condy) takes c_{k,s_max}
     const double c_condy = st->c_step > 0.0 ? st->c_step * st->c_smax : cc;
     const double T = rnorm > 0.0 ? eps_star / (c_condy * kEps * rnorm) : CUDART_INF;
@@ -489,18 +518,18 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
       // eq. (condy): largest prefix i with sqrt(kappa(G_{k,i})) <= T; none -> 1
       stilde = 0;
       for (int i = 1; i <= sbar; ++i) {
-        if (__ldcg(&st->sqrt_kappa[i - 1]) <= T)
+        if (s_sk[i - 1] <= T)
           stilde = i;
         else
           break;
       }
       if (stilde < 1) stilde = 1;
-      gamma = __ldcg(&st->sqrt_kappa[stilde - 1]);
+      gamma = s_sk[stilde - 1];
     } else {
       stilde = sbar;
       gamma = 0.0;
     }
-    const int done = (int)__ldcg(rec + kSpecDone);
+    const int done = (int)s_done;
     const int nmax = min(stilde, st->max_steps);
     int steps = 0, stop = ASCG_STOP_DONE;
     for (int j = 1; j <= nmax; ++j) {
@@ -509,7 +538,7 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
         break;
       }
       steps = j;
-      const double rnn = __ldcg(rec + (int64_t)(j - 1) * kSpecRow + 3 * kMaxW + 2);
+      const double rnn = s_step[j - 1][2];
       if (rnn <= eps_star) {
         stop = ASCG_STOP_CONVERGED;
         break;
@@ -525,24 +554,7 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
       }
     }
     if (stop == ASCG_STOP_DONE && steps < stilde) stop = ASCG_STOP_MAXITER;
-    const int m0 = st->m;
-    double relres = sqrt(fmax(__ldcg(G + 1 * w + 1), 0.0)) / bnorm;
-    for (int j = 1; j <= steps; ++j) {
-      const double* r = rec + (int64_t)(j - 1) * kSpecRow + 3 * kMaxW;
-      const double alpha = __ldcg(r), beta = __ldcg(r + 1);
-      relres = __ldcg(r + 2) / bnorm;
-      const int it = m0 + j;  // 1-based iteration index
-      if (res_hist && it < res_cap) res_hist[it] = relres;
-      if (ab_hist && it - 1 < ab_cap) {
-        ab_hist[it - 1] = alpha;
-        ab_hist[ab_cap + it - 1] = beta;
-      }
-      if (hist) {
-        hist[3 * (j - 1)] = alpha;
-        hist[3 * (j - 1) + 1] = beta;
-        hist[3 * (j - 1) + 2] = relres;
-      }
-    }
+    const double rel0 = rnorm / bnorm;
     st->rnorm = rnorm;
     st->threshold = T;
     st->stilde = stilde;
@@ -550,11 +562,27 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
     st->s_k = steps;
     st->stop = stop;
     st->converged = stop == ASCG_STOP_CONVERGED;
-    st->rel_res = relres;
+    st->rel_res = steps > 0 ? s_step[steps - 1][2] / bnorm : rel0;
     s_steps = steps;
   }
   __syncthreads();
   const int steps = s_steps;
+  // histories of the steps taken: step j (1-based) is iteration m + j
+  if (t < steps) {
+    const int j = t + 1;
+    const double alpha = s_step[t][0], beta = s_step[t][1], relres = s_step[t][2] / st->bnorm;
+    const int it = st->m + j;
+    if (res_hist && it < res_cap) res_hist[it] = relres;
+    if (ab_hist && it - 1 < ab_cap) {
+      ab_hist[it - 1] = alpha;
+      ab_hist[ab_cap + it - 1] = beta;
+    }
+    if (hist) {
+      hist[3 * t] = alpha;
+      hist[3 * t + 1] = beta;
+      hist[3 * t + 2] = relres;
+    }
+  }
   const double* r = rec + (int64_t)(steps - 1) * kSpecRow;
   for (int c = t; c < w; c += blockDim.x) {
     if (steps > 0) {

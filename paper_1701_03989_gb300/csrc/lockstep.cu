@@ -309,6 +309,7 @@ class Lockstep {
   }
 
   int free_lanes() const { return lanes_ - nused_; }
+  int active_lanes() const { return nused_; }
 
   // Admits systems whose basis Y the caller has placed (each into the lowest
   // free lane; the caller checks free_lanes()), computes ||b||, r_1 = b - A x_1
@@ -911,6 +912,8 @@ struct ascg_server_s {
   size_t budget = 0;
   int max_systems = 0;
   int running = 0;
+  int admit_order = ASCG_ADMIT_FIFO;
+  int large_cap = 0;  // > 0: most systems running at once in the largest size class
   cudaStream_t user = nullptr;
   Arena arena;
   Group group[kGroups];
@@ -962,23 +965,37 @@ struct ascg_server_s {
     return ASCG_OK;
   }
 
-  // Admission in submission order: a request whose size class is in the
-  // middle of a block waits for it (later requests of idle classes may go
-  // ahead); the first request that finds no slot or no memory stops the scan.
+  // Estimated work of a request: its rows times the decimal digits of
+  // accuracy it asks for (CG iterations grow with both).
+  static double work_of(const LaneSys& L) {
+    const double digits = L.eps_target > 0.0 ? -std::log10(L.eps_target) : 16.0;
+    return (double)L.d.n * (digits > 1.0 ? digits : 1.0);
+  }
+
+  // Admission scan, in submission order (ASCG_ADMIT_FIFO) or in increasing
+  // estimated work (ASCG_ADMIT_SHORTEST_FIRST, ties in submission order). A
+  // request whose size class is in the middle of a block waits for it (later
+  // requests of idle classes may go ahead), as does one whose class is at its
+  // cap; the first request that finds no slot or no memory stops the scan.
   ascg_status admit() {
     std::vector<LaneSys> pick[kGroups];
     int taken[kGroups] = {0, 0, 0};
-    for (auto it = queue.begin(); it != queue.end();) {
-      const int gi = group_of(it->d.n);
+    std::vector<size_t> order(queue.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    if (admit_order == ASCG_ADMIT_SHORTEST_FIRST)
+      std::stable_sort(order.begin(), order.end(),
+                       [&](size_t a, size_t b) { return work_of(queue[a]) < work_of(queue[b]); });
+    std::vector<char> gone(queue.size(), 0);
+    for (size_t k = 0; k < order.size(); ++k) {
+      LaneSys& Q = queue[order[k]];
+      const int gi = group_of(Q.d.n);
       Group& g = group[gi];
-      if (g.in_flight || g.eng.free_lanes() - taken[gi] <= 0) {
-        ++it;
-        continue;
-      }
+      if (g.in_flight || g.eng.free_lanes() - taken[gi] <= 0) continue;
+      if (large_cap > 0 && gi == kGroups - 1 && g.eng.active_lanes() + taken[gi] >= large_cap) continue;
       if (running >= max_systems) break;
       int64_t off = 0;
-      if (!arena.take(it->d.n, &off)) break;
-      LaneSys L = *it;
+      if (!arena.take(Q.d.n, &off)) break;
+      LaneSys L = Q;
       L.off = off;
       L.d.Y = arena.row(off);
       L.d.ldY = arena.ld();
@@ -990,7 +1007,13 @@ struct ascg_server_s {
       pick[gi].push_back(L);
       ++taken[gi];
       ++running;
-      it = queue.erase(it);
+      gone[order[k]] = 1;
+    }
+    if (!order.empty()) {
+      std::deque<LaneSys> rest;
+      for (size_t i = 0; i < queue.size(); ++i)
+        if (!gone[i]) rest.push_back(queue[i]);
+      queue.swap(rest);
     }
     for (int gi = 0; gi < kGroups; ++gi) {
       if (pick[gi].empty()) continue;
@@ -1070,6 +1093,17 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
     if (st != ASCG_OK) return fail_free(st);
   }
   *out = srv;
+  return ASCG_OK;
+}
+
+ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap) {
+  set_last_error("");
+  if (!srv) return lfail(ASCG_ERR_INVALID, "srv is NULL");
+  if (admit_order != ASCG_ADMIT_FIFO && admit_order != ASCG_ADMIT_SHORTEST_FIRST)
+    return lfail(ASCG_ERR_INVALID, "unknown admission order");
+  if (large_class_cap < 0) return lfail(ASCG_ERR_INVALID, "large_class_cap must be >= 0");
+  srv->admit_order = admit_order;
+  srv->large_cap = large_class_cap;
   return ASCG_OK;
 }
 

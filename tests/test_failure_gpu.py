@@ -50,10 +50,11 @@ def _solve(P, torch, op, b, kw, raise_on=None):
 
 def test_gram_wait_runs_out_and_context_survives(env):
     P, torch = env
-    A = W.poisson3d(23)                      # w = 33 in the first block: the tensor-core Gram
+    A = W.poisson3d(23)                      # w = 33 in the first block
     b = W.rhs_uniform(A.n, np.random.default_rng(11))
     lam = W.poisson_eig_bounds(3, 23)
-    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=lam, eps_target=1e-12, max_iters=5000)
+    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=lam, eps_target=1e-12, max_iters=5000,
+              gram_tc=True)                  # the tensor-core Gram at this size too
     op = _op(P, A)
     ref, xref = _solve(P, torch, op, b, kw)
     assert ref.status == P.ASCG_OK

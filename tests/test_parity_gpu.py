@@ -479,8 +479,10 @@ SOLVES = [
     ("diffusion_63", dict(method="adaptive", basis="newton", s_max=12, newton_warmup=24), 1e-10),
     ("banded_3001", dict(method="adaptive", basis="monomial", s_max=10), 1e-8),
     ("banded_3001", dict(method="adaptive", basis="chebyshev", s_max=10), 1e-12),
-    # the same Chebyshev solve with the Gram matrix formed by FP64 FMAs instead of the tensor cores
-    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_fp64=True), 1e-12),
+    # the same Chebyshev solve with the Gram matrix on the tensor cores (at this size the
+    # solver takes the FP64 kernel by default), and the monomial one
+    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_tc=True), 1e-12),
+    ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8, gram_tc=True), 1e-10),
     # c_{k,j} = 6 N_k j kappa(A) (eq. (fb)) from closed-form kappa(A) and ||A|| of the Poisson matrices
     ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8,
                           c_formula=(W.poisson_eig_bounds(2, 32)[1] / W.poisson_eig_bounds(2, 32)[0],

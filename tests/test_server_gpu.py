@@ -133,6 +133,63 @@ def test_served_results_equal_alone(env):
         P.ascg_op_destroy(op)
 
 
+def test_shortest_first_admission_and_large_cap(env):
+    """ASCG_ADMIT_SHORTEST_FIRST: with room for one system at a time, the
+    waiting requests are admitted in increasing estimated work (rows times
+    target digits), and every result is still bitwise the same as alone. A
+    large-class cap of 1 keeps two large systems from running at once."""
+    P, torch = env
+    rng = np.random.default_rng(33)
+    mats = [W.poisson2d(60), W.poisson2d(20), W.banded_spd(2000, 12, rng), W.poisson2d(30)]
+    epss = [1e-10, 1e-8, 1e-6, 1e-12]
+    systems = [dict(name=f"s{i}_{A.n}", A=A, b=W.rhs_uniform(A.n, rng), x1=np.zeros(A.n), eps=e)
+               for i, (A, e) in enumerate(zip(mats, epss))]
+    ops = [make_op(P, s["A"]) for s in systems]
+    srv = P.ascg_server_create(opts(P), 1 << 30, 1)      # one slot: requests wait their turn
+    P.ascg_server_set_policy(srv, P.ASCG_ADMIT_SHORTEST_FIRST, 0)
+    try:
+        # the first request takes the slot at once; the other three wait and are
+        # then admitted shortest first
+        served, order = serve(P, torch, srv, systems, ops, [([0], 1), ([1, 2, 3], 0)])
+    finally:
+        P.ascg_server_destroy(srv)
+    work = {q: systems[q]["A"].n * max(1.0, -np.log10(systems[q]["eps"])) for q in range(4)}
+    waiting = sorted([1, 2, 3], key=lambda q: work[q])
+    adm = [served[q][0].step_admitted for q in waiting]
+    assert adm == sorted(adm) and len(set(adm)) == 3, (adm, waiting)
+    for q, s in enumerate(systems):
+        c, x = served[q]
+        r, xa = solve_alone(P, torch, ops[q], s["b"], s["x1"], s["eps"])
+        assert c.result.status == P.ASCG_OK == r.status and np.array_equal(x, xa), s["name"]
+    # large-class cap: two systems of >= 2^19 rows never run at once
+    big = [W.poisson3d(81), W.poisson3d(82)]
+    assert all(A.n >= 1 << 19 for A in big)
+    bsys = [dict(name=f"big{i}", A=A, b=W.rhs_uniform(A.n, rng), x1=np.zeros(A.n), eps=1e-6)
+            for i, A in enumerate(big)]
+    bops = [make_op(P, s["A"]) for s in bsys]
+    srv = P.ascg_server_create(opts(P), 1 << 32, 8)
+    P.ascg_server_set_policy(srv, P.ASCG_ADMIT_FIFO, 1)
+    log = []
+    try:
+        bserved, _ = serve(P, torch, srv, bsys, bops, [([0, 1], 0)], log)
+    finally:
+        P.ascg_server_destroy(srv)
+    assert max(st.systems_running for st in log) == 1
+    assert bserved[1][0].step_admitted >= bserved[0][0].step_done
+    for q, s in enumerate(bsys):
+        c, x = bserved[q]
+        r, xa = solve_alone(P, torch, bops[q], s["b"], s["x1"], s["eps"])
+        assert c.result.status == P.ASCG_OK == r.status and np.array_equal(x, xa), s["name"]
+    with pytest.raises(P.AscgError):
+        srv2 = P.ascg_server_create(opts(P), 1 << 20, 2)
+        try:
+            P.ascg_server_set_policy(srv2, 7, 0)
+        finally:
+            P.ascg_server_destroy(srv2)
+    for op in ops + bops:
+        P.ascg_op_destroy(op)
+
+
 def test_served_size_classes_equal_alone(env):
     """Systems in all three size classes (n < 2^16, < 2^19, larger), each class
     stepping on its own stream: every result equals its solve alone, bit for
