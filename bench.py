@@ -115,6 +115,8 @@ def parse():
                     help="served workload: admission order (submission order, or shortest estimated work first)")
     ap.add_argument("--large-cap", type=int, default=1,
                     help="served workload: most systems of >= 2^19 rows running at once (0: no cap)")
+    ap.add_argument("--no-yield", dest="yield_large", action="store_false",
+                    help="served workload: the largest size class does not wait for the smaller ones")
     ap.add_argument("--workload", default="poisson3d_128",
                     choices=list(SINGLE_WORKLOADS) + ["batch", "serve"],
                     help="a single-solve workload, or batch: 256 uneven systems solved by ascg_solve_batch (one "
@@ -737,7 +739,7 @@ def serve_arm(args):
     slots = 256
     srv = P.ascg_server_create(o, budget, slots, stream)
     order = P.ASCG_ADMIT_SHORTEST_FIRST if args.policy == "sjf" else P.ASCG_ADMIT_FIFO
-    P.ascg_server_set_policy(srv, order, args.large_cap)
+    P.ascg_server_set_policy(srv, order, args.large_cap, args.yield_large)
 
     def run(idx, arrivals, host_io=False):
         """Serves requests idx arriving at `arrivals` (seconds from the start).
@@ -852,7 +854,8 @@ def serve_arm(args):
                    "pool_n": nop, "pool_nnz": [int(p["A"].nnz) for p in pool],
                    "gram": "Hankel moments (a variant)" if args.moment_gram else "Y^T Y"},
         "p50_ms": _pct(lat_ms, 50), "p99_ms": _pct(lat_ms, 99), "max_ms": max(lat_ms),
-        "policy": {"admit": args.policy, "large_class_cap": args.large_cap}, "by_size": by_size,
+        "policy": {"admit": args.policy, "large_class_cap": args.large_cap, "yield_large": args.yield_large},
+        "by_size": by_size,
         "saturation_sample": nsat,
         "throughput_rps": nreq / wall, "arrival_rps": lam, "saturation_rps": mu,
         "saturation_wall_s": sat_wall, "saturation_peak_running": sat_peak, "peak_running": peak,

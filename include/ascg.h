@@ -464,16 +464,19 @@ typedef enum {
                                      submission order                            */
 } ascg_admit_order;
 
-/* Sets the server's admission policy (host; takes effect at the next
+/* Sets the server's scheduling policy (host; takes effect at the next
  * ascg_server_step). admit_order: ascg_admit_order. large_class_cap > 0: at
  * most that many systems run at once in the largest size class (n >= 2^19),
  * whose kernels cover the whole GPU by themselves, so that running more of
- * them at once only shares the GPU among them; 0: no cap. The other rules of
+ * them at once only shares the GPU among them; 0: no cap. yield_large != 0:
+ * the largest class starts no block while a smaller class has systems
+ * running, so that small and medium requests get the whole GPU (large
+ * requests wait meanwhile: their latency grows). The other rules of
  * ascg_server_step stay: a class in the middle of a block admits nothing,
  * and the first request that finds no slot or no memory stops the scan. A
  * system's arithmetic does not depend on the policy. ASCG_ERR_INVALID for an
  * unknown order or a negative cap. */
-ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap);
+ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap, int yield_large);
 
 /* Counters of the server (host). */
 ascg_status ascg_server_info(ascg_server srv, ascg_server_stats* stats);

@@ -112,7 +112,7 @@ def _load():
         "ascg_server_step": (C.c_int, [P, C.POINTER(ascg_completion), C.c_int, C.POINTER(C.c_int),
                                        C.POINTER(C.c_int), C.POINTER(C.c_int)]),
         "ascg_server_info": (C.c_int, [P, C.POINTER(ascg_server_stats)]),
-        "ascg_server_set_policy": (C.c_int, [P, C.c_int, C.c_int]),
+        "ascg_server_set_policy": (C.c_int, [P, C.c_int, C.c_int, C.c_int]),
         "ascg_server_destroy": (C.c_int, [P]),
         "ascg_tune_gram_schedule": (C.c_int, [C.c_int, C.POINTER(I64), P, C.c_int, C.POINTER(C.c_int), P]),
         "ascg_last_error": (C.c_char_p, []),
@@ -246,8 +246,9 @@ def ascg_server_step(srv, cap=64):
 ASCG_ADMIT_FIFO, ASCG_ADMIT_SHORTEST_FIRST = 0, 1
 
 
-def ascg_server_set_policy(srv, admit_order, large_class_cap=0):
-    _check(_lib.ascg_server_set_policy(srv, int(admit_order), int(large_class_cap)), "ascg_server_set_policy")
+def ascg_server_set_policy(srv, admit_order, large_class_cap=0, yield_large=False):
+    _check(_lib.ascg_server_set_policy(srv, int(admit_order), int(large_class_cap), 1 if yield_large else 0),
+           "ascg_server_set_policy")
 
 
 def ascg_server_info(srv):

@@ -59,6 +59,9 @@ void dev_free(T*& p) {
   p = nullptr;
 }
 
+// Records of the blocks in flight: block j uses slot j % kRing.
+constexpr int kRing = 4;
+
 // Device workspace owned by an operator; grows on demand.
 struct Workspace {
   int64_t n = 0;
@@ -95,6 +98,8 @@ struct Workspace {
   CGState* h_cgs = nullptr;
   double* h_scal = nullptr;
   cudaEvent_t ev[8] = {};
+  cudaEvent_t ev_blk[kRing][5] = {};  // per record slot: the phase boundaries of a block (timing)
+  cudaEvent_t ev_rec[kRing] = {};     // per record slot: the block's record is on the host
   bool events = false;
   cudaStream_t side = nullptr;  // x += Y x' of the previous block
   cudaEvent_t ev_gram = nullptr, ev_x[2] = {};
@@ -111,6 +116,9 @@ struct Workspace {
     h_bst = nullptr; h_cgs = nullptr; h_scal = nullptr;
     if (events) {
       for (auto& e : ev) cudaEventDestroy(e);
+      for (auto& row : ev_blk)
+        for (auto& e : row) cudaEventDestroy(e);
+      for (auto& e : ev_rec) cudaEventDestroy(e);
       cudaEventDestroy(ev_gram);
       for (auto& e : ev_x) cudaEventDestroy(e);
       if (side) cudaStreamDestroy(side);
@@ -229,12 +237,15 @@ ascg_status ensure(ascg_op op, int wcols, int res_cap) {
     ASCG_TRY(dev_alloc(&w.params, 3 * kMaxS));
     ASCG_TRY(dev_alloc(&w.scal, 4));
     ASCG_TRY(dev_alloc(&w.shifts, 32));
-    ASCG_TRY(dev_alloc(&w.bst, 1));
+    ASCG_TRY(dev_alloc(&w.bst, kRing));
     ASCG_TRY(dev_alloc(&w.cgs, 1));
-    ASCG_CUDA(cudaMallocHost((void**)&w.h_bst, sizeof(BlockState)));
+    ASCG_CUDA(cudaMallocHost((void**)&w.h_bst, 2 * kRing * sizeof(BlockState)));
     ASCG_CUDA(cudaMallocHost((void**)&w.h_cgs, sizeof(CGState)));
     ASCG_CUDA(cudaMallocHost((void**)&w.h_scal, 4 * sizeof(double)));
     for (auto& e : w.ev) ASCG_CUDA(cudaEventCreate(&e));
+    for (auto& row : w.ev_blk)
+      for (auto& e : row) ASCG_CUDA(cudaEventCreate(&e));
+    for (auto& e : w.ev_rec) ASCG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     ASCG_CUDA(cudaEventCreateWithFlags(&w.ev_gram, cudaEventDisableTiming));
     for (auto& e : w.ev_x) ASCG_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     ASCG_CUDA(cudaStreamCreateWithFlags(&w.side, cudaStreamNonBlocking));
@@ -445,7 +456,7 @@ ascg_status run_classical(ascg_op op, double* x, double* r, double* p, double ep
   int batch = 8;
   for (;;) {
     for (int i = 0; i < batch; ++i) {
-      ASCG_CUDA(launch_cg_spmv_dot(A, p, w.q, w.cgs, w.partials, w.counter, s));
+      ASCG_CUDA(launch_cg_spmv_dot(A, op->nnz, p, w.q, w.cgs, w.partials, w.counter, s));
       ASCG_CUDA(launch_cg_update(n, x, r, p, w.q, w.cgs, w.partials, w.counter, w.res_hist, w.res_cap,
                                  w.ab_hist, w.ab_hist + w.ab_cap, w.ab_cap, s));
       ASCG_CUDA(launch_cg_pupdate(n, r, p, w.cgs, s));
@@ -589,21 +600,35 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     // that update first.
     double* Ybuf[2] = {w.Y, w.Y2};
     double* cbuf[2] = {w.coords, w.coords + 3 * kMaxW};
-    int cur = 0, pend = -1, pend_w = 0;
     bool x_out[2] = {false, false};  // an x update reading buffer b is queued on the side stream
     const int x_ctas = std::max(1, gram_grid() - 24);
-    while (!done) {
-      const int sbar = block_sbar(o, k, s_prev);
+    // Block j uses basis buffer j & 1, coordinates cbuf[j & 1] and record slot
+    // j % kRing (device w.bst[slot], pinned host w.h_bst[slot] going in and
+    // w.h_bst[kRing + slot] coming back). When block j+1's basis size does not
+    // depend on block j's outcome (Alg. 2, Alg. 3, and Alg. 4 with f >= s_max - 1,
+    // where sbar_k = s_max for every k >= 1), block j+1 is enqueued before the
+    // host reads block j's record: the GPU never waits for the host between
+    // blocks. A device kernel carries m, k and the iteration budget from
+    // block to block and clears block j+1's flag when block j ended the solve;
+    // every kernel of a block then returns at once.
+    const bool ahead = o.method == ASCG_FIXED_S || o.method == ASCG_VARIABLE_S ||
+                       (o.method == ASCG_ADAPTIVE && o.f >= o.s_max - 1);
+    int wb_of[kRing] = {};
+    int sbar_of[kRing] = {};
+    auto enqueue = [&](int j, int sbar) -> ascg_status {
+      const int slot = j % kRing, cur = j & 1;
       const int wb = 2 * sbar + 1;
       double* const Yc = Ybuf[cur];
-      BlockState& hb = *w.h_bst;
+      BlockState* const dst = w.bst + slot;
+      const int* const gate = &dst->active;
+      BlockState& hb = w.h_bst[slot];
       std::memset(&hb, 0, sizeof(hb));
       hb.sbar = sbar;
       hb.method = o.method;
       hb.check_in_loop = o.check_in_loop;
-      hb.max_steps = o.max_iters - m;
+      hb.max_steps = o.max_iters - m;  // block 0; later blocks: set on the device
       hb.m = m;
-      hb.k = k;
+      hb.k = j;
       hb.eps_star = eps_star;
       hb.c = o.c;
       hb.c_step = c_step_of[sbar];
@@ -611,73 +636,101 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       hb.bnorm = bnorm;
       hb.sqrt_n = sqrt_n;
       hb.active = 1;
-      ASCG_CUDA(cudaMemcpyAsync(w.bst, &hb, sizeof(BlockState), cudaMemcpyHostToDevice, s));
+      ASCG_CUDA(cudaMemcpyAsync(dst, &hb, sizeof(BlockState), cudaMemcpyHostToDevice, s));
+      if (j > 0) {
+        ASCG_CUDA(launch_block_advance(w.bst + (j - 1) % kRing, dst, o.max_iters, s));
+        res->launches += 1;
+      }
+      wb_of[slot] = wb;
+      sbar_of[slot] = sbar;
+      cudaEvent_t* ev = w.ev_blk[slot];
       // matrix powers: P columns 1..sbar, R columns 1..sbar-1 (eq. cg-krylovbasis)
-      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[1], s));
-      // the steps also record each basis column's largest exponent for the tensor-core Gram
+      if (timing) ASCG_CUDA(cudaEventRecord(ev[0], s));
       // The tensor cores take the Gram when its FP64 work, n w(w+1)/2 products,
       // is large enough to pay for the kernel's fixed cost (tensor memory,
       // barriers, pipeline fill: about 40 us on GB300, against about 1 us per
-      // 2^20 products in FP64), or when ASCG_FLAG_GRAM_TC asks for them.
+      // 2^20 products in FP64), or when ASCG_FLAG_GRAM_TC asks for them. The
+      // matrix powers steps then also record each column's largest exponent.
       const bool tc_big = gram_tc_force || (double)n * wb * (wb + 1) / 2.0 >= kTcSolveProducts;
       const bool tc_gram = !gram_fp64 && !gram_mom && tc_big && gram_tc_applies(wb) && gram_tc_aligned(Yc, w.ldY) &&
                            gram_tc_fits(n);
-      for (int j = 0; j < sbar; ++j) {
-        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[j], Yc, w.ldY, j, 1, j < sbar - 1,
-                                        tc_gram ? w.emax_part : nullptr, w.emax_ld, s));
+      for (int q = 0; q < sbar; ++q) {
+        ASCG_CUDA(launch_mpk_split_step(Asplit, steps[q], Yc, w.ldY, q, 1, q < sbar - 1,
+                                        tc_gram ? w.emax_part : nullptr, w.emax_ld, s, gate));
       }
       if (tc_gram) {
-        ASCG_CUDA(launch_emax_reduce(w.emax_part, w.emax_ld, n, wb, w.expp, s));
+        ASCG_CUDA(launch_emax_reduce(w.emax_part, w.emax_ld, n, wb, w.expp, s, gate));
         res->launches += 1;
       }
       res->launches += sbar;
-      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[2], s));
+      if (timing) ASCG_CUDA(cudaEventRecord(ev[1], s));
       // Gram: the block's one grid-wide reduction
       int nparts = 0;
       if (gram_mom)
-        ASCG_CUDA(launch_gram_moments(n, wb, Yc, w.ldY, w.partials, &nparts, s));
+        ASCG_CUDA(launch_gram_moments(n, wb, Yc, w.ldY, w.partials, &nparts, s, gate));
       else
         ASCG_CUDA(launch_gram_any(n, wb, Yc, w.ldY, !tc_gram, w.expp, tc_gram, w.partials, &nparts, s,
-                                  &w.bst->status, stall_test && k == 0));
-      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[3], s));
+                                  &dst->status, stall_test && j == 0, gate));
+      if (timing) ASCG_CUDA(cudaEventRecord(ev[2], s));
       if (gram_mom)
-        ASCG_CUDA(launch_gram_moment_finalize(wb, w.partials, nparts, w.G, s));
+        ASCG_CUDA(launch_gram_moment_finalize(wb, w.partials, nparts, w.G, s, gate));
       else
-        ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s));
+        ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s, gate));
       res->launches += 2;
-      res->grid_reductions += 1;
-      if (pend >= 0) {  // the previous block's x += Y x', beside this block's kappa and controller
+      if (j > 0) {  // block j-1's x += Y x', beside this block's kappa and controller
+        const int ps = (j - 1) % kRing;
         ASCG_CUDA(cudaEventRecord(w.ev_gram, s));
         ASCG_CUDA(cudaStreamWaitEvent(w.side, w.ev_gram, 0));
-        ASCG_CUDA(launch_recover_x(n, pend_w, Ybuf[pend], w.ldY, cbuf[pend], x, x_ctas, w.side));
-        ASCG_CUDA(cudaEventRecord(w.ev_x[pend], w.side));
-        x_out[pend] = true;
-        pend = -1;
+        ASCG_CUDA(launch_recover_x(n, wb_of[ps], Ybuf[cur ^ 1], w.ldY, cbuf[cur ^ 1], x, x_ctas, w.side,
+                                   &w.bst[ps].active));
+        ASCG_CUDA(cudaEventRecord(w.ev_x[cur ^ 1], w.side));
+        x_out[cur ^ 1] = true;
         res->launches += 1;
       }
-      ASCG_CUDA(launch_block_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, w.bst, sbar,
+      ASCG_CUDA(launch_block_ctrl(w.G, w.params, w.params + kMaxS, w.params + 2 * kMaxS, dst, sbar,
                                   o.method == ASCG_ADAPTIVE, cbuf[cur], nullptr, w.res_hist, w.res_cap, w.ab_hist,
                                   w.ab_cap, w.spec, w.counter + 1, s));
-      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[4], s));
+      if (timing) ASCG_CUDA(cudaEventRecord(ev[3], s));
       // r and p into columns 1 and 0 of the other buffer, once the update that reads it is done
       if (x_out[cur ^ 1]) {
         ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[cur ^ 1], 0));
         x_out[cur ^ 1] = false;
       }
-      ASCG_CUDA(launch_recover_rp(n, wb, Yc, w.ldY, cbuf[cur], Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s));
-      pend = cur;
-      pend_w = wb;
-      cur ^= 1;
+      ASCG_CUDA(launch_recover_rp(n, wb, Yc, w.ldY, cbuf[cur], Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s, gate));
       res->launches += 2;
-      if (timing) ASCG_CUDA(cudaEventRecord(w.ev[5], s));
-      ASCG_CUDA(cudaMemcpyAsync(w.h_bst, w.bst, sizeof(BlockState), cudaMemcpyDeviceToHost, s));
-      ASCG_CUDA(cudaStreamSynchronize(s));
+      if (timing) ASCG_CUDA(cudaEventRecord(ev[4], s));
+      ASCG_CUDA(cudaMemcpyAsync(w.h_bst + kRing + slot, dst, sizeof(BlockState), cudaMemcpyDeviceToHost, s));
+      ASCG_CUDA(cudaEventRecord(w.ev_rec[slot], s));
+      return ASCG_OK;
+    };
+    // block sizes known without the previous block's outcome
+    auto sbar_ahead = [&](int j, int* sbar) {
+      if (!ahead || j == 0) return false;
+      *sbar = o.method == ASCG_ADAPTIVE ? o.s_max : block_sbar(o, j, 1);
+      return true;
+    };
+    int enq = 0;  // blocks enqueued
+    if (!done) {
+      ASCG_TRY(enqueue(0, block_sbar(o, 0, 0)));
+      enq = 1;
+    }
+    while (!done) {
+      int sb_next = 0;
+      if (enq == k + 1 && sbar_ahead(k + 1, &sb_next)) {
+        ASCG_TRY(enqueue(k + 1, sb_next));
+        enq = k + 2;
+      }
+      const int slot = k % kRing;
+      const int sbar = sbar_of[slot];
+      const int wb = wb_of[slot];
+      ASCG_CUDA(cudaEventSynchronize(w.ev_rec[slot]));
       if (timing) {
+        cudaEvent_t* ev = w.ev_blk[slot];
         float a = 0.f, b2 = 0.f, c2 = 0.f, d2 = 0.f;
-        ASCG_CUDA(cudaEventElapsedTime(&a, w.ev[1], w.ev[2]));
-        ASCG_CUDA(cudaEventElapsedTime(&b2, w.ev[2], w.ev[3]));
-        ASCG_CUDA(cudaEventElapsedTime(&c2, w.ev[3], w.ev[4]));
-        ASCG_CUDA(cudaEventElapsedTime(&d2, w.ev[4], w.ev[5]));
+        ASCG_CUDA(cudaEventElapsedTime(&a, ev[0], ev[1]));
+        ASCG_CUDA(cudaEventElapsedTime(&b2, ev[1], ev[2]));
+        ASCG_CUDA(cudaEventElapsedTime(&c2, ev[2], ev[3]));
+        ASCG_CUDA(cudaEventElapsedTime(&d2, ev[3], ev[4]));
         res->t_mpk_ms += a;
         res->t_gram_ms += b2;
         res->t_ctrl_ms += c2;
@@ -695,7 +748,8 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         res->recover_flops += 2.0 * 2.0 * wb * (double)n;
         res->recover_bytes += 8.0 * wb * (double)n + 16.0 * n;
       }
-      const BlockState& out = *w.h_bst;
+      const BlockState& out = w.h_bst[kRing + slot];
+      res->grid_reductions += 1;
       if (o.block_hist && nb_info < o.block_hist_cap) {
         ascg_block_info& bi = o.block_hist[nb_info];
         std::memset(&bi, 0, sizeof(bi));
@@ -732,12 +786,20 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         final_status = ASCG_NOT_CONVERGED;
         break;
       }
+      if (enq == k) {
+        ASCG_TRY(enqueue(k, block_sbar(o, k, s_prev)));
+        enq = k + 1;
+      }
     }
-    // the last block's x update, after any still on the side stream
+    // the x update of the last block enqueued (block enq-1: it returns at once
+    // if that block was enqueued ahead and had nothing to do), after any still
+    // on the side stream
     for (int bq = 0; bq < 2; ++bq)
       if (x_out[bq]) ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[bq], 0));
-    if (pend >= 0) {
-      ASCG_CUDA(launch_recover_x(n, pend_w, Ybuf[pend], w.ldY, cbuf[pend], x, x_ctas, s));
+    if (enq > 0) {
+      const int last = enq - 1, ls = last % kRing;
+      ASCG_CUDA(launch_recover_x(n, wb_of[ls], Ybuf[last & 1], w.ldY, cbuf[last & 1], x, x_ctas, s,
+                                 &w.bst[ls].active));
       res->launches += 1;
     }
     res->blocks = k;

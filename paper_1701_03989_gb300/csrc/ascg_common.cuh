@@ -110,11 +110,15 @@ struct StepOp {
 // multiple of 4, entries past ceil(n/32) zero):
 // per warp of 32 rows, the largest biased exponent of each column written (for
 // j = 0 also of columns 0 and 1), at [col * emax_ld + warp].
+// gate (device int, or nullptr): every kernel of a solver block takes the
+// block's flag, and returns at once when it is 0 (a block enqueued ahead of the
+// host's reading of the previous one, which ended the solve).
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
-                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s);
+                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s,
+                                  const int* gate = nullptr);
 // col_emax[c] = max_k emax_part[c * emax_ld + k] for c < w, k < ceil(n/32).
 cudaError_t launch_emax_reduce(const int* emax_part, int64_t emax_ld, int64_t n, int w, int* col_emax,
-                               cudaStream_t s);
+                               cudaStream_t s, const int* gate = nullptr);
 // dst[i] = (src[i] - theta) * scale, for i < n
 cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, double scale, double* dst,
                                cudaStream_t s);
@@ -123,9 +127,10 @@ cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, doubl
 int gram_grid();                // CTAs per launch at most (the SM count)
 int gram_parts(int64_t n);      // CTAs (= partials) used for n rows
 cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, double* partials,
-                                cudaStream_t s);
+                                cudaStream_t s, const int* gate = nullptr);
 // Sum the partials in a fixed order; G row-major w x w, both halves.
-cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
+cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s,
+                                 const int* gate = nullptr);
 
 // Batched solves: one Gram item = rows [row0, row0 + nrows) of system sys.
 struct GramItem {
@@ -161,8 +166,9 @@ cudaError_t launch_gram_items_finalize(int W, const double* partials, const int*
 constexpr int kMomFam = 2 * kMaxS + 1;
 constexpr int kMomSlots = 3 * kMomFam;
 cudaError_t launch_gram_moments(int64_t n, int w, const double* Y, int64_t ldY, double* partials, int* nparts,
-                                cudaStream_t s);
-cudaError_t launch_gram_moment_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s);
+                                cudaStream_t s, const int* gate = nullptr);
+cudaError_t launch_gram_moment_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s,
+                                        const int* gate = nullptr);
 
 // Tensor-core Gram (split-bf16 operands, exact integer sums) for
 // kGramTcMinW <= w <= kMaxW. Below that width the FP64 kernel is faster.
@@ -181,13 +187,15 @@ struct TcGuard {
   long long wait_limit;
   int stall_stage;
   int* err;
+  const int* gate;  // see launch_mpk_split_step
 };
 // col_emax: device int[kMaxW], the largest biased exponent of each column;
 // computed here unless emax_ready (then it already holds them, e.g. from the
 // matrix powers kernel). partials as for launch_gram_partial. err: as in
 // TcGuard (may be nullptr); stall_test: run the stall test (see TcGuard).
 cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, bool emax_ready,
-                           double* partials, cudaStream_t s, int* err = nullptr, bool stall_test = false);
+                           double* partials, cudaStream_t s, int* err = nullptr, bool stall_test = false,
+                           const int* gate = nullptr);
 // True when the tensor-core Gram can take n rows (at most 2^31 - 1 rows and
 // 2048 chunks of 1024 rows per CTA); larger bases take the FP64 kernel.
 bool gram_tc_fits(int64_t n);
@@ -204,7 +212,7 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
                                  cudaStream_t s);
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s, int* err = nullptr,
-                            bool stall_test = false);
+                            bool stall_test = false, const int* gate = nullptr);
 
 // Many systems in lockstep (kernels_batch.cu): a device table of per-system
 // descriptors and row items of one system each (up to kRowItem rows starting
@@ -250,9 +258,9 @@ cudaError_t launch_recover(int64_t n, int w, const double* Y, int64_t ldY, const
 // and none shares an SM with a kernel holding more than ~6 KB of shared
 // memory.
 cudaError_t launch_recover_rp(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* r,
-                              double* p, cudaStream_t s);
+                              double* p, cudaStream_t s, const int* gate = nullptr);
 cudaError_t launch_recover_x(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
-                             int ctas, cudaStream_t s);
+                             int ctas, cudaStream_t s, const int* gate = nullptr);
 
 // Block controller state shared by the controller kernels and the host driver.
 struct BlockState {
@@ -308,6 +316,10 @@ cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const dou
                                     double* coords, int64_t c_stride, double* res_hist, int res_cap, double* ab_hist,
                                     int ab_cap, double* spec, unsigned* counters, cudaStream_t s);
 
+// Block j+1 of a single solve from block j's record (m, k, iteration budget,
+// and the flag that gates every kernel of block j+1).
+cudaError_t launch_block_advance(const BlockState* prev, BlockState* cur, int max_iters, cudaStream_t s);
+
 // Newton shifts: Ritz values of the CG tridiagonal, Leja order. alphas, betas:
 // device; shifts: device double[k].
 cudaError_t launch_newton_shifts(const double* alphas, const double* betas, int k, double* shifts,
@@ -328,8 +340,9 @@ struct CGState {
   int active;       // 1 if the current iteration runs (set by the SpMV kernel)
   int breakdown;    // 1 once p^T A p was not positive and finite (the solve stops)
 };
-// q = A p, state.pAp; the last CTA sets alpha.
-cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st,
+// q = A p, state.pAp; the last CTA sets alpha. nnz: A's nonzeros (a large A
+// is streamed past L2, see sell_row).
+cudaError_t launch_cg_spmv_dot(const DevSell& A, int64_t nnz, const double* p, double* q, CGState* st,
                                double* partials, unsigned* counter, cudaStream_t s);
 // x += alpha p, r -= alpha q, rr_new; the last CTA sets beta, records histories,
 // tests convergence.

@@ -14,10 +14,12 @@ namespace ascg {
 
 namespace {
 
-// sum_j a_ij x_j for row i (i < A.n) in stored order, starting from 0. The
-// values and column indices of A are read once per pass: they are loaded with
-// the evict-first (streaming) policy, so that the vectors of the iteration,
-// which every pass reads again, keep their place in L2.
+// sum_j a_ij x_j for row i (i < A.n) in stored order, starting from 0. With
+// STREAM, the values and column indices of A, read once per pass, are loaded
+// with the evict-first (streaming) policy, so that the vectors of an
+// iteration, which every pass reads again, keep their place in L2: worth it
+// when A does not fit in L2 beside them. A small A is better left in L2.
+template <bool STREAM = false>
 __device__ __forceinline__ double sell_row(const DevSell& A, int64_t i, const double* __restrict__ x) {
   const int64_t s = i >> 5;
   const int l = (int)(i & 31);
@@ -26,7 +28,11 @@ __device__ __forceinline__ double sell_row(const DevSell& A, int64_t i, const do
   const double* v = A.val + b + l;
   const int32_t* c = A.col + b + l;
   double t = 0.0;
-  for (int j = 0; j < width; ++j) t = fma(__ldcs(v + kSlice * j), __ldg(x + __ldcs(c + kSlice * j)), t);
+  if (STREAM) {
+    for (int j = 0; j < width; ++j) t = fma(__ldcs(v + kSlice * j), __ldg(x + __ldcs(c + kSlice * j)), t);
+  } else {
+    for (int j = 0; j < width; ++j) t = fma(__ldg(v + kSlice * j), __ldg(x + __ldg(c + kSlice * j)), t);
+  }
   return t;
 }
 
@@ -108,6 +114,7 @@ __global__ void __launch_bounds__(256) dot_kernel(const double* __restrict__ u, 
 // Grid-stride over rows with a bounded grid: every CTA ends in one block
 // reduction and one atomic ticket, so few CTAs keep that overhead small. Each
 // warp-wide FP64 add costs a full FP64 issue slot, however few lanes need it.
+template <bool STREAM>
 __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const double* __restrict__ p,
                                                                 double* __restrict__ q, CGState* st,
                                                                 double* partials, unsigned* counter) {
@@ -118,7 +125,7 @@ __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const
   if (done) return;
   double part = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x; i < A.n; i += (int64_t)gridDim.x * kSpmvRows) {
-    const double v = sell_row(A, i, p);
+    const double v = sell_row<STREAM>(A, i, p);
     q[i] = v;
     part = fma(p[i], v, part);
   }
@@ -228,10 +235,15 @@ cudaError_t launch_dot(const double* u, const double* v, int64_t n, double* out,
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_spmv_dot(const DevSell& A, const double* p, double* q, CGState* st, double* partials,
-                               unsigned* counter, cudaStream_t s) {
+cudaError_t launch_cg_spmv_dot(const DevSell& A, int64_t nnz, const double* p, double* q, CGState* st,
+                               double* partials, unsigned* counter, cudaStream_t s) {
   const int g = grid_for(A.n, kSpmvRows, 152 * 8);
-  cg_spmv_dot_kernel<<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
+  // A's values and columns (12 bytes per entry) beyond a quarter of the 129 MB
+  // L2: stream them past it
+  if (12 * nnz > ((int64_t)32 << 20))
+    cg_spmv_dot_kernel<true><<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
+  else
+    cg_spmv_dot_kernel<false><<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
   return cudaGetLastError();
 }
 

@@ -198,65 +198,82 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
   const int m = 2 * i + 1;
   const int w = 2 * sbar + 1;
   __shared__ double A[kMaxW][kMaxW];  // odd row stride: conflict-free column access
-  __shared__ double v[32], wv[32];
+  __shared__ double vb[2][32];         // Householder vectors of steps k (slot k & 1) and k + 1
   __shared__ double part[4][32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
   __shared__ double lo_s[2], hi_s[2];
-  __shared__ double beta_s, floor_s;
-  __shared__ int go_s, uncert_s;
+  __shared__ double beta_s[2], floor_s;
+  __shared__ int go_s[2], uncert_s;
   __shared__ unsigned s_mask[2][2];
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  // The reflection that zeroes column kk below its subdiagonal (run by warp 0):
+  // v = x - alpha e_1 over rows kk+1 .. m-1, alpha = -sign(x_0) ||x||, and
+  // beta = 2 / v^T v = 1 / (s2 + |x_0| ||x||) (v^T v = 2 (s2 + |x_0| ||x||)).
+  auto reflector = [&](int kk, int slot) {
+    const int len_ = m - kk - 1;
+    const bool on_ = lane < len_;
+    const double xi = on_ ? A[kk + 1 + lane][kk] : 0.0;
+    const double s2 = warp_sum(xi * xi);
+    const double x0 = __shfl_sync(kFull, xi, 0);
+    const int go = s2 > 0.0;
+    double alpha = 0.0, vv = 0.0;
+    if (go) {
+      const double r = sqrt(s2);
+      alpha = -copysign(r, x0);
+      vv = on_ ? (lane == 0 ? x0 - alpha : xi) : 0.0;
+      if (lane == 0) beta_s[slot] = 1.0 / (s2 + fabs(x0) * r);
+    }
+    vb[slot][lane] = vv;
+    if (lane == 0) {
+      go_s[slot] = go;
+      e[kk] = alpha;  // s2 == 0: the column is already zero
+    }
+  };
+  // Householder tridiagonalisation with look-ahead: in step k every warp
+  // forms the product p = A22 v (columns split evenly), then, redundantly in
+  // each warp, w = beta p - (beta^2 v^T p / 2) v, and applies the rank-2
+  // update to its columns. Warp 0 owns only the first trailing column (column
+  // k+1), so it can form the next step's reflection while warps 1..3 update
+  // the rest. Two barriers per step; the arithmetic, and so every bit, is the
+  // same as updating in turn.
+  if (warp == 0 && m >= 3) reflector(0, 0);
+  __syncthreads();
   for (int k = 0; k + 2 < m; ++k) {
     const int len = m - k - 1;  // rows k+1 .. m-1, at most 32
     const int row = k + 1 + lane;
     const bool on = lane < len;
-    const int c0 = (len * warp) >> 2, c1 = (len * (warp + 1)) >> 2;
-    double vi = 0.0;
-    if (warp == 0) {
-      const double xi = on ? A[row][k] : 0.0;
-      const double s2 = warp_sum(xi * xi);
-      const double x0 = __shfl_sync(kFull, xi, 0);
-      const int go = s2 > 0.0;
-      double alpha = 0.0;
-      if (go) {
-        const double r = sqrt(s2);
-        alpha = -copysign(r, x0);
-        vi = on ? (lane == 0 ? x0 - alpha : xi) : 0.0;
-        // v^T v = 2 (s2 + |x0| r), so beta = 2 / v^T v without another reduction
-        if (lane == 0) beta_s = 1.0 / (s2 + fabs(x0) * r);
+    const int sl = k & 1;
+    if (go_s[sl]) {  // uniform
+      const double vi = on ? vb[sl][lane] : 0.0;
+      const double beta = beta_s[sl];
+      const int c0 = (len * warp) >> 2, c1 = (len * (warp + 1)) >> 2;
+      double p0 = 0.0, p1 = 0.0;
+      if (on) {
+        int c = c0;
+        for (; c + 1 < c1; c += 2) {
+          p0 = fma(A[row][k + 1 + c], vb[sl][c], p0);
+          p1 = fma(A[row][k + 2 + c], vb[sl][c + 1], p1);
+        }
+        if (c < c1) p0 = fma(A[row][k + 1 + c], vb[sl][c], p0);
       }
-      v[lane] = vi;
-      if (lane == 0) {
-        go_s = go;
-        e[k] = alpha;  // s2 == 0: the column is already zero
-      }
-    }
-    __syncthreads();
-    if (!go_s) continue;  // uniform
-    if (warp != 0) vi = on ? v[lane] : 0.0;
-    double p0 = 0.0, p1 = 0.0;
-    if (on) {
-      int c = c0;
-      for (; c + 1 < c1; c += 2) {
-        p0 = fma(A[row][k + 1 + c], v[c], p0);
-        p1 = fma(A[row][k + 2 + c], v[c + 1], p1);
-      }
-      if (c < c1) p0 = fma(A[row][k + 1 + c], v[c], p0);
-    }
-    part[warp][lane] = p0 + p1;
-    __syncthreads();
-    if (warp == 0) {
-      const double beta = beta_s;
+      part[warp][lane] = p0 + p1;
+      __syncthreads();
       const double pi = beta * ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane]));
       const double K = 0.5 * beta * warp_sum(vi * pi);
-      wv[lane] = pi - K * vi;
+      const double wi = pi - K * vi;
+      // rank-2 update of this warp's columns: warp 0 column 0, warps 1..3 the rest
+      const int g0 = warp == 0 ? 0 : 1 + (((len - 1) * (warp - 1)) / 3);
+      const int g1 = warp == 0 ? 1 : 1 + (((len - 1) * warp) / 3);
+      for (int c = g0; c < g1; ++c) {
+        const double vc = __shfl_sync(kFull, vi, c), wc = __shfl_sync(kFull, wi, c);
+        if (on) A[row][k + 1 + c] = fma(-vi, wc, fma(-wi, vc, A[row][k + 1 + c]));
+      }
     }
-    __syncthreads();
-    if (on) {
-      const double wi = wv[lane];
-      for (int c = c0; c < c1; ++c) A[row][k + 1 + c] = fma(-vi, wv[c], fma(-wi, v[c], A[row][k + 1 + c]));
+    if (warp == 0 && k + 3 < m) {
+      __syncwarp();
+      reflector(k + 1, sl ^ 1);
     }
     __syncthreads();
   }
@@ -504,7 +521,11 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
   if (t == 96) s_g11 = __ldcg(G + 1 * w + 1);
   if (t == 97) s_done = __ldcg(rec + kSpecDone);
   __syncthreads();
-  if (t == 0) {
+  if (t < 32) {
+    // warp 0, lane j - 1 for step j and submatrix i = j: the same scalar
+    // formulas as a serial scan, evaluated for all j at once (an FP64
+    // instruction costs the same for 1 or 32 lanes), then ballots
+    const int lane = t;
     const int adaptive = st->method == ASCG_ADAPTIVE;
     const double eps_star = st->eps_star, cc = st->c, bnorm = st->bnorm;
     // ||r_{m+1}|| from G: column 1 is rho_0(A) r = r
@@ -516,13 +537,8 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
     double gamma;
     if (adaptive) {
       // eq. (condy): largest prefix i with sqrt(kappa(G_{k,i})) <= T; none -> 1
-      stilde = 0;
-      for (int i = 1; i <= sbar; ++i) {
-        if (s_sk[i - 1] <= T)
-          stilde = i;
-        else
-          break;
-      }
+      const unsigned ok = __ballot_sync(kFull, lane < sbar && s_sk[lane < sbar ? lane : 0] <= T);
+      stilde = __ffs(~ok) - 1;
       if (stilde < 1) stilde = 1;
       gamma = s_sk[stilde - 1];
     } else {
@@ -531,39 +547,46 @@ __device__ void select_steps(const double* __restrict__ G, BlockState* st, const
     }
     const int done = (int)s_done;
     const int nmax = min(stilde, st->max_steps);
-    int steps = 0, stop = ASCG_STOP_DONE;
-    for (int j = 1; j <= nmax; ++j) {
-      if (j > done) {  // the step's denominators were not positive and finite
+    // step j ends the loop: breakdown (j > done), convergence, or eq. (check),
+    // a break when gamma >= eps* / (c_{k,j} eps (r'^T G r')^(1/2))
+    const int j = lane + 1;
+    const double rnn = s_step[lane < kMaxS ? lane : 0][2];
+    const bool bd = j > done;
+    const bool conv = !bd && rnn <= eps_star;
+    bool brk = false;
+    if (!bd && !conv && adaptive && st->check_in_loop) {
+      const double cj = st->c_step > 0.0 ? st->c_step * j : cc;
+      const double Tj = rnn > 0.0 ? eps_star / (cj * kEps * rnn) : CUDART_INF;
+      brk = gamma >= Tj;
+    }
+    const unsigned ev = __ballot_sync(kFull, j <= nmax && (bd || conv || brk));
+    const unsigned cv = __ballot_sync(kFull, conv);
+    const unsigned bdm = __ballot_sync(kFull, bd);
+    int steps, stop;
+    if (ev == 0u) {
+      steps = nmax;
+      stop = steps < stilde ? ASCG_STOP_MAXITER : ASCG_STOP_DONE;
+    } else {
+      const int f = __ffs(ev) - 1;  // step f + 1 ends the loop
+      if ((bdm >> f) & 1u) {
+        steps = f;
         stop = ASCG_STOP_BREAKDOWN;
-        break;
-      }
-      steps = j;
-      const double rnn = s_step[j - 1][2];
-      if (rnn <= eps_star) {
-        stop = ASCG_STOP_CONVERGED;
-        break;
-      }
-      if (adaptive && st->check_in_loop) {
-        // eq. (check): break when gamma >= eps* / (c_{k,j} eps (r'^T G r')^(1/2))
-        const double cj = st->c_step > 0.0 ? st->c_step * j : cc;
-        const double Tj = rnn > 0.0 ? eps_star / (cj * kEps * rnn) : CUDART_INF;
-        if (gamma >= Tj) {
-          stop = ASCG_STOP_BREAK;
-          break;
-        }
+      } else {
+        steps = f + 1;
+        stop = ((cv >> f) & 1u) ? ASCG_STOP_CONVERGED : ASCG_STOP_BREAK;
       }
     }
-    if (stop == ASCG_STOP_DONE && steps < stilde) stop = ASCG_STOP_MAXITER;
-    const double rel0 = rnorm / bnorm;
-    st->rnorm = rnorm;
-    st->threshold = T;
-    st->stilde = stilde;
-    st->gamma = gamma;
-    st->s_k = steps;
-    st->stop = stop;
-    st->converged = stop == ASCG_STOP_CONVERGED;
-    st->rel_res = steps > 0 ? s_step[steps - 1][2] / bnorm : rel0;
-    s_steps = steps;
+    if (lane == 0) {
+      st->rnorm = rnorm;
+      st->threshold = T;
+      st->stilde = stilde;
+      st->gamma = gamma;
+      st->s_k = steps;
+      st->stop = stop;
+      st->converged = stop == ASCG_STOP_CONVERGED;
+      st->rel_res = steps > 0 ? s_step[steps - 1][2] / bnorm : rnorm / bnorm;
+      s_steps = steps;
+    }
   }
   __syncthreads();
   const int steps = s_steps;
@@ -639,6 +662,21 @@ __global__ void __launch_bounds__(128) block_ctrl_kernel(const double* __restric
   __threadfence();
   select_steps(G, st, spec, coords, hist, res_hist, res_cap, ab_hist, ab_cap);
   if (threadIdx.x == 0) *counters = 0u;
+}
+
+// Carries a single solve from block j to block j+1 on the device: m, k and the
+// iteration budget of block j+1 from block j's outcome, and block j+1's flag,
+// cleared when block j ended the solve (converged, no step, a wait that ran
+// out, or the iteration cap reached), so that a block enqueued ahead does
+// nothing.
+__global__ void block_advance_kernel(const BlockState* __restrict__ prev, BlockState* __restrict__ cur,
+                                     int max_iters) {
+  if (threadIdx.x != 0) return;
+  const int m = prev->m + prev->s_k;
+  cur->m = m;
+  cur->k = prev->k + 1;
+  cur->max_steps = max_iters - m;
+  cur->active = prev->active && prev->s_k > 0 && !prev->converged && prev->status == ASCG_OK && m < max_iters;
 }
 
 // Ritz values of the CG tridiagonal (k <= 32), one lane per eigenvalue index by
@@ -727,6 +765,11 @@ cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const dou
   block_ctrl_kernel<<<dim3(adaptive ? max_sbar + 1 : 1, count), 128, 0, s>>>(
       G, theta, sigma, gamma, st, coords, nullptr, res_hist, res_cap, ab_hist, ab_cap, g_stride, c_stride, spec,
       counters);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_block_advance(const BlockState* prev, BlockState* cur, int max_iters, cudaStream_t s) {
+  block_advance_kernel<<<1, 32, 0, s>>>(prev, cur, max_iters);
   return cudaGetLastError();
 }
 

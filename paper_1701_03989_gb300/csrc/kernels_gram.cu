@@ -153,7 +153,9 @@ __device__ __forceinline__ void gram_chunks(int64_t n, const double* __restrict_
 
 template <int W, bool MOM = false>
 __global__ void __launch_bounds__(kGramThreads, 1) gram_partial_kernel(int64_t n, const double* __restrict__ Y,
-                                                                        int64_t ldY, double* __restrict__ partials) {
+                                                                        int64_t ldY, double* __restrict__ partials,
+                                                                        const int* __restrict__ gate) {
+  if (gate && !*gate) return;  // uniform: a block enqueued ahead that has nothing to do
   constexpr int NP = MOM ? kMomSlots : W * (W + 1) / 2;
   const int64_t nchunks = (n + kChunk - 1) / kChunk;
   gram_chunks<W, MOM>(n, Y, ldY, nchunks * blockIdx.x / gridDim.x, nchunks * (blockIdx.x + 1) / gridDim.x,
@@ -190,7 +192,9 @@ __device__ __forceinline__ void moments_to_gram(const double* mu, int w, double*
 // The moments of one system from nparts partials (kMomSlots each), each
 // summed over the partials in index order, then G.
 __global__ void __launch_bounds__(128) gram_moment_finalize_kernel(int w, const double* __restrict__ partials,
-                                                                   int nparts, double* __restrict__ G) {
+                                                                   int nparts, double* __restrict__ G,
+                                                                   const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   __shared__ double mu[kMomSlots];
   const int S = (w - 1) / 2;
   for (int sl = threadIdx.x; sl < kMomSlots; sl += blockDim.x) {
@@ -234,7 +238,8 @@ __global__ void __launch_bounds__(128) gram_items_moment_finalize_kernel(const d
 // then the four sums combine as (s0 + s1) + (s2 + s3). Fixed order: the result
 // is bitwise reproducible.
 __global__ void __launch_bounds__(128) gram_finalize_kernel(int w, const double* __restrict__ partials, int nparts,
-                                                            double* __restrict__ G) {
+                                                            double* __restrict__ G, const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   const int np = w * (w + 1) / 2;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
   const int p = gt >> 2, t = gt & 3;
@@ -295,8 +300,9 @@ __global__ void __launch_bounds__(256) gram_items_finalize_kernel(int W, const d
 }
 
 template <int W>
-cudaError_t gram_w(int64_t n, const double* Y, int64_t ldY, double* partials, int grid, cudaStream_t s) {
-  gram_partial_kernel<W><<<grid, kGramThreads, 0, s>>>(n, Y, ldY, partials);
+cudaError_t gram_w(int64_t n, const double* Y, int64_t ldY, double* partials, int grid, cudaStream_t s,
+                   const int* gate) {
+  gram_partial_kernel<W><<<grid, kGramThreads, 0, s>>>(n, Y, ldY, partials, gate);
   return cudaGetLastError();
 }
 
@@ -324,12 +330,13 @@ int gram_parts(int64_t n) {
   return (int)(chunks < gram_grid() ? chunks : gram_grid());
 }
 
-cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, double* partials, cudaStream_t s) {
+cudaError_t launch_gram_partial(int64_t n, int w, const double* Y, int64_t ldY, double* partials, cudaStream_t s,
+                                const int* gate) {
   const int grid = gram_parts(n);
   switch (w) {
 #define ASCG_GW(W) \
   case W:          \
-    return gram_w<W>(n, Y, ldY, partials, grid, s);
+    return gram_w<W>(n, Y, ldY, partials, grid, s, gate);
     ASCG_GW(1) ASCG_GW(2) ASCG_GW(3) ASCG_GW(4) ASCG_GW(5) ASCG_GW(6) ASCG_GW(7) ASCG_GW(8) ASCG_GW(9)
     ASCG_GW(10) ASCG_GW(11) ASCG_GW(12) ASCG_GW(13) ASCG_GW(14) ASCG_GW(15) ASCG_GW(16) ASCG_GW(17)
     ASCG_GW(18) ASCG_GW(19) ASCG_GW(20) ASCG_GW(21) ASCG_GW(22) ASCG_GW(23) ASCG_GW(24) ASCG_GW(25)
@@ -373,13 +380,13 @@ cudaError_t launch_gram_items_finalize(int W, const double* partials, const int*
 }
 
 cudaError_t launch_gram_moments(int64_t n, int w, const double* Y, int64_t ldY, double* partials, int* nparts,
-                                cudaStream_t s) {
+                                cudaStream_t s, const int* gate) {
   const int grid = gram_parts(n);
   *nparts = grid;
   switch (w) {
 #define ASCG_GM(W)                                                                       \
   case W:                                                                                \
-    gram_partial_kernel<W, true><<<grid, kGramThreads, 0, s>>>(n, Y, ldY, partials);     \
+    gram_partial_kernel<W, true><<<grid, kGramThreads, 0, s>>>(n, Y, ldY, partials, gate); \
     return cudaGetLastError();
     ASCG_GM(3) ASCG_GM(5) ASCG_GM(7) ASCG_GM(9) ASCG_GM(11) ASCG_GM(13) ASCG_GM(15) ASCG_GM(17) ASCG_GM(19)
     ASCG_GM(21) ASCG_GM(23) ASCG_GM(25) ASCG_GM(27) ASCG_GM(29) ASCG_GM(31) ASCG_GM(33)
@@ -389,14 +396,16 @@ cudaError_t launch_gram_moments(int64_t n, int w, const double* Y, int64_t ldY, 
   }
 }
 
-cudaError_t launch_gram_moment_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s) {
-  gram_moment_finalize_kernel<<<1, 128, 0, s>>>(w, partials, nparts, G);
+cudaError_t launch_gram_moment_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s,
+                                        const int* gate) {
+  gram_moment_finalize_kernel<<<1, 128, 0, s>>>(w, partials, nparts, G, gate);
   return cudaGetLastError();
 }
 
-cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s) {
+cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s,
+                                 const int* gate) {
   const int np = w * (w + 1) / 2;
-  gram_finalize_kernel<<<(4 * np + 127) / 128, 128, 0, s>>>(w, partials, nparts, G);
+  gram_finalize_kernel<<<(4 * np + 127) / 128, 128, 0, s>>>(w, partials, nparts, G, gate);
   return cudaGetLastError();
 }
 

@@ -671,6 +671,7 @@ done:
 __global__ void __launch_bounds__(kTcThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
                    double* __restrict__ partials, const TcGuard guard) {
+  if (guard.gate && !*guard.gate) return;  // uniform, before any barrier or tensor memory
   gram_tc_body(&ymap, w, 0, blockIdx.x, (n + kTChunk - 1) / kTChunk, gridDim.x, n, col_emax,
                partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), guard);
 }
@@ -687,7 +688,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (sys_w[it.sys] == 0) return;  // uniform over the CTA, before any barrier
   const int64_t nch = it.nrows / kTChunk;
   gram_tc_body(&ymap, w, it.row0, 0, nch, 1, nch * kTChunk, emax_all + (int64_t)it.sys * kTW,
-               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), TcGuard{kWaitLimit, -1, nullptr});
+               partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), TcGuard{kWaitLimit, -1, nullptr, nullptr});
 }
 
 // Largest biased exponent of each column, reduced into col_emax (zeroed
@@ -814,7 +815,7 @@ bool gram_tc_fits(int64_t n) {
 }
 
 cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* exp_parts, bool emax_ready,
-                           double* partials, cudaStream_t s, int* err, bool stall_test) {
+                           double* partials, cudaStream_t s, int* err, bool stall_test, const int* gate) {
   if (w < 1 || w > kTW || !gram_tc_fits(n) || !gram_tc_aligned(Y, ldY)) return cudaErrorInvalidValue;
   const int parts = gram_tc_parts(n);
   cudaError_t e = smem_limit_once(g_tc_smem_set, gram_tc_kernel, (int)kTcSmem);
@@ -830,7 +831,7 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
-  const TcGuard guard{stall_test ? kTestWaitLimit : kWaitLimit, stall_test ? 0 : -1, err};
+  const TcGuard guard{stall_test ? kTestWaitLimit : kWaitLimit, stall_test ? 0 : -1, err, gate};
   gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials, guard);
   return cudaGetLastError();
 }
@@ -858,13 +859,13 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
 
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* exp_parts,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s, int* err,
-                            bool stall_test) {
+                            bool stall_test, const int* gate) {
   if (!force_fp64 && gram_tc_applies(w) && gram_tc_aligned(Y, ldY) && gram_tc_fits(n)) {
     *nparts = gram_tc_parts(n);
-    return launch_gram_tc(n, w, Y, ldY, exp_parts, emax_ready, partials, s, err, stall_test);
+    return launch_gram_tc(n, w, Y, ldY, exp_parts, emax_ready, partials, s, err, stall_test, gate);
   }
   *nparts = gram_parts(n);
-  return launch_gram_partial(n, w, Y, ldY, partials, s);
+  return launch_gram_partial(n, w, Y, ldY, partials, s, gate);
 }
 
 }  // namespace ascg

@@ -44,7 +44,9 @@ __device__ __forceinline__ unsigned biased_exp(double v) { return ((unsigned)__d
 template <int SIG, bool R>
 __global__ void __launch_bounds__(kSpmvRows, 6)
     mpk_split_step_kernel(DevSell O, const double* __restrict__ oval, const double* __restrict__ dtil, double sig,
-                          double* __restrict__ Y, int64_t ldY, int j, int* emax_part, int64_t emax_ld) {
+                          double* __restrict__ Y, int64_t ldY, int j, int* emax_part, int64_t emax_ld,
+                          const int* __restrict__ gate) {
+  if (gate && !*gate) return;  // uniform: a block enqueued ahead that has nothing to do
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   unsigned e_op = 0, e_or = 0;
   if (row < O.n) {
@@ -127,7 +129,8 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
 // per column, 16-byte loads, four in flight per thread. emax_ld is a multiple
 // of 4 and entries past the warp count are zero.
 __global__ void __launch_bounds__(1024) emax_reduce_kernel(const int* __restrict__ emax_part, int64_t emax_ld,
-                                                           int* __restrict__ col_emax) {
+                                                           int* __restrict__ col_emax, const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   const int c = blockIdx.x;
   const int4* src = reinterpret_cast<const int4*>(emax_part + (int64_t)c * emax_ld);
   const int64_t n4 = emax_ld / 4;
@@ -223,7 +226,9 @@ cudaError_t recover_w(int64_t n, const double* Y, int64_t ldY, const double* coo
 template <int W>
 __global__ void __launch_bounds__(256, 6) recover_rp_kernel(int64_t n, const double* __restrict__ Y, int64_t ldY,
                                                             const double* __restrict__ coords,
-                                                            double* __restrict__ r, double* __restrict__ p) {
+                                                            double* __restrict__ r, double* __restrict__ p,
+                                                            const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   __shared__ double cr[W], cp[W];
   if (threadIdx.x < W) {
     cr[threadIdx.x] = coords[W + threadIdx.x];
@@ -259,7 +264,8 @@ constexpr int kXReserve = 220 * 1024;
 template <int W>
 __global__ void __launch_bounds__(kXThreads, 1) recover_x_kernel(int64_t n, const double* __restrict__ Y,
                                                                  int64_t ldY, const double* __restrict__ coords,
-                                                                 double* __restrict__ x) {
+                                                                 double* __restrict__ x, const int* __restrict__ gate) {
+  if (gate && !*gate) return;
   __shared__ double cx[W];
   if (threadIdx.x < W) cx[threadIdx.x] = coords[threadIdx.x];
   __syncthreads();
@@ -281,14 +287,14 @@ __global__ void __launch_bounds__(kXThreads, 1) recover_x_kernel(int64_t n, cons
 
 template <int W>
 cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const double* coords, double* x, double* r,
-                            double* p, int x_ctas, cudaStream_t s) {
+                            double* p, int x_ctas, cudaStream_t s, const int* gate) {
   if (x) {
     static std::atomic<uint64_t> smem_set{0};  // one flag set per instance
     const cudaError_t e = smem_limit_once(smem_set, recover_x_kernel<W>, kXReserve);
     if (e != cudaSuccess) return e;
-    recover_x_kernel<W><<<x_ctas, kXThreads, kXReserve, s>>>(n, Y, ldY, coords, x);
+    recover_x_kernel<W><<<x_ctas, kXThreads, kXReserve, s>>>(n, Y, ldY, coords, x, gate);
   } else {
-    recover_rp_kernel<W><<<rec_grid(n), 256, 0, s>>>(n, Y, ldY, coords, r, p);
+    recover_rp_kernel<W><<<rec_grid(n), 256, 0, s>>>(n, Y, ldY, coords, r, p, gate);
   }
   return cudaGetLastError();
 }
@@ -296,12 +302,13 @@ cudaError_t recover_split_w(int64_t n, const double* Y, int64_t ldY, const doubl
 }  // namespace
 
 cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y, int64_t ldY, int j, int do_p,
-                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s) {
+                                  int do_r, int* emax_part, int64_t emax_ld, cudaStream_t s, const int* gate) {
   if (!do_p) return cudaErrorInvalidValue;  // every step forms the P column
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
   const int sig_mode = (op.sig == 0.0 || j < 1) ? 0 : (op.sig == 1.0 ? 1 : 2);
 #define ASCG_MPK(S, R) \
-  mpk_split_step_kernel<S, R><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, emax_part, emax_ld)
+  mpk_split_step_kernel<S, R><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, emax_part, emax_ld, \
+                                                      gate)
   if (do_r) {
     if (sig_mode == 0) ASCG_MPK(0, true);
     else if (sig_mode == 1) ASCG_MPK(1, true);
@@ -316,9 +323,9 @@ cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y
 }
 
 cudaError_t launch_emax_reduce(const int* emax_part, int64_t emax_ld, int64_t n, int w, int* col_emax,
-                               cudaStream_t s) {
+                               cudaStream_t s, const int* gate) {
   (void)n;
-  emax_reduce_kernel<<<w, 1024, 0, s>>>(emax_part, emax_ld, col_emax);
+  emax_reduce_kernel<<<w, 1024, 0, s>>>(emax_part, emax_ld, col_emax, gate);
   return cudaGetLastError();
 }
 
@@ -329,11 +336,11 @@ cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, doubl
 }
 
 cudaError_t launch_recover_rp(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* r,
-                              double* p, cudaStream_t s) {
+                              double* p, cudaStream_t s, const int* gate) {
   switch (w) {
 #define ASCG_RS(W) \
   case W:          \
-    return recover_split_w<W>(n, Y, ldY, coords, nullptr, r, p, 0, s);
+    return recover_split_w<W>(n, Y, ldY, coords, nullptr, r, p, 0, s, gate);
     ASCG_RS(1) ASCG_RS(3) ASCG_RS(5) ASCG_RS(7) ASCG_RS(9) ASCG_RS(11) ASCG_RS(13) ASCG_RS(15) ASCG_RS(17)
     ASCG_RS(19) ASCG_RS(21) ASCG_RS(23) ASCG_RS(25) ASCG_RS(27) ASCG_RS(29) ASCG_RS(31) ASCG_RS(33)
 #undef ASCG_RS
@@ -343,12 +350,12 @@ cudaError_t launch_recover_rp(int64_t n, int w, const double* Y, int64_t ldY, co
 }
 
 cudaError_t launch_recover_x(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
-                             int ctas, cudaStream_t s) {
+                             int ctas, cudaStream_t s, const int* gate) {
   if (ctas < 1) ctas = 1;
   switch (w) {
 #define ASCG_RX(W) \
   case W:          \
-    return recover_split_w<W>(n, Y, ldY, coords, x, nullptr, nullptr, ctas, s);
+    return recover_split_w<W>(n, Y, ldY, coords, x, nullptr, nullptr, ctas, s, gate);
     ASCG_RX(1) ASCG_RX(3) ASCG_RX(5) ASCG_RX(7) ASCG_RX(9) ASCG_RX(11) ASCG_RX(13) ASCG_RX(15) ASCG_RX(17)
     ASCG_RX(19) ASCG_RX(21) ASCG_RX(23) ASCG_RX(25) ASCG_RX(27) ASCG_RX(29) ASCG_RX(31) ASCG_RX(33)
 #undef ASCG_RX

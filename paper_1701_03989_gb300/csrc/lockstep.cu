@@ -206,6 +206,95 @@ struct LaneSys {
 // value (ascg_tune_gram_schedule measures one).
 constexpr int64_t kTcLaneRows = (int64_t)1 << 10;
 
+// A lane's running state on the device, for batched solves whose block loop
+// runs on the GPU (Lockstep::run_on_device): the fields the host loop keeps
+// in LaneSys, updated from each block's record exactly as complete_block
+// does on the host.
+struct LaneRun {
+  int active, started, m, kb, s_prev, wasted, status, tc_ok;
+  double rel_upd, eps_star, bnorm, sqrt_n;
+};
+struct LoopParams {
+  int method, s_max, s0, f, check_in_loop, max_iters, seq_len, iter_cap;
+  double c;
+  const int* seq;
+};
+
+// One CTA: for every lane, the outcome of its last block (as complete_block),
+// then its next block's record and table entries (as launch_block), or zeros
+// when it has finished; then the loop's condition: another block while any
+// lane runs and fewer than iter_cap blocks have been taken. Every block takes
+// at least one step of every running lane or ends it, so the loop ends within
+// max_iters + 1 blocks; iter_cap bounds it in any case.
+__global__ void __launch_bounds__(1024) lanes_advance_kernel(BlockState* __restrict__ bst, LaneRun* __restrict__ run,
+                                                             int nl, int* __restrict__ steps, int* __restrict__ w,
+                                                             int* __restrict__ wi, int* __restrict__ wtc,
+                                                             const LoopParams P, int* __restrict__ iter,
+                                                             cudaGraphConditionalHandle cond) {
+  int any = 0;
+  for (int q = threadIdx.x; q < nl; q += blockDim.x) {
+    LaneRun R = run[q];
+    BlockState& B = bst[q];
+    if (R.active && R.started) {
+      R.wasted += 2 * (B.sbar - B.s_k);
+      if (B.s_k == 0) {
+        R.status = ASCG_ERR_BREAKDOWN;
+        R.active = 0;
+      } else {
+        R.rel_upd = B.rel_res;
+        R.m += B.s_k;
+        R.s_prev = B.s_k;
+        ++R.kb;
+        if (B.converged) {
+          R.active = 0;
+        } else if (R.m >= P.max_iters) {
+          R.status = ASCG_NOT_CONVERGED;
+          R.active = 0;
+        }
+      }
+    }
+    R.started = 1;
+    int sb = 0;
+    if (R.active) {
+      if (P.method == ASCG_FIXED_S)
+        sb = P.s_max;
+      else if (P.method == ASCG_VARIABLE_S)
+        sb = P.seq[R.kb < P.seq_len ? R.kb : P.seq_len - 1];
+      else
+        sb = R.kb == 0 ? P.s0 : (R.s_prev + P.f < P.s_max ? R.s_prev + P.f : P.s_max);
+      BlockState nb;
+      memset(&nb, 0, sizeof(nb));
+      nb.sbar = sb;
+      nb.method = P.method;
+      nb.check_in_loop = P.check_in_loop;
+      nb.max_steps = P.max_iters - R.m;
+      nb.m = R.m;
+      nb.k = R.kb;
+      nb.eps_star = R.eps_star;
+      nb.c = P.c;
+      nb.bnorm = R.bnorm;
+      nb.sqrt_n = R.sqrt_n;
+      nb.active = 1;
+      B = nb;
+    } else {
+      B.active = 0;
+    }
+    const int ww = sb > 0 ? 2 * sb + 1 : 0;
+    const bool tc = R.tc_ok && ww >= kGramTcMinW;
+    steps[q] = sb;
+    w[q] = ww;
+    wi[q] = tc ? 0 : ww;
+    wtc[q] = tc ? ww : 0;
+    run[q] = R;
+    any |= R.active;
+  }
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) {
+    const int it = ++*iter;
+    cudaGraphSetConditional(cond, (any && it <= P.iter_cap) ? 1u : 0u);
+  }
+}
+
 class Lockstep {
  public:
   ~Lockstep() { release(); }
@@ -452,21 +541,7 @@ class Lockstep {
       LS_CUDA(cudaMemcpyAsync(d_w, h_w, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_wi, h_wi, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
       LS_CUDA(cudaMemcpyAsync(d_wtc, h_wtc, sizeof(int) * hi_, cudaMemcpyHostToDevice, s_));
-      for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
-      if (item_gram) {
-        // pair groups: enough CTAs to cover the SMs twice
-        const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
-        LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
-        LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
-      }
-      if (tc_gram) {  // every tensor-core lane in one launch over the shared basis matrix
-        LS_CUDA(launch_gram_tc_items(Wb, ybase_, yld_, yld_, d_titems_, nt, d_wtc, hi_, d_emax_, d_tpart_, s_));
-        LS_CUDA(launch_gram_items_finalize(Wb, d_tpart_, d_tc0, d_tcn, d_wtc, hi_, d_G_, kGStride, false, s_));
-      }
-      LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_,
-                                      hi_, max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_,
-                                      rcap_, d_ab_hist_, abcap_, d_spec_, d_tickets_, s_));
-      LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
+      LS_TRY(block_kernels(max_sbar, item_gram, tc_gram));
       LS_CUDA(cudaMemcpyAsync(h_bst_, d_bst_, sizeof(BlockState) * hi_, cudaMemcpyDeviceToHost, s_));
       return ASCG_OK;
     };
@@ -504,6 +579,157 @@ class Lockstep {
       LS_TRY(enqueue());
     launches_ += nl;
     *launched = true;
+    return ASCG_OK;
+  }
+
+  // The kernels of one block of every lane whose table entries (steps, w,
+  // wi, wtc) and record are set: the matrix powers steps, the Gram (item
+  // launch and tensor-core lanes), the controller, the recovery.
+  ascg_status block_kernels(int max_sbar, bool item_gram, bool tc_gram) {
+    int* d_steps = d_int_ + kSteps * lanes_;
+    int* d_w = d_int_ + kW * lanes_;
+    int* d_wi = d_int_ + kWItems * lanes_;
+    int* d_item0 = d_int_ + kItem0 * lanes_;
+    int* d_nitems = d_int_ + kNItems * lanes_;
+    int* d_wtc = d_int_ + kWTc * lanes_;
+    int* d_tc0 = d_int_ + kTcItem0 * lanes_;
+    int* d_tcn = d_int_ + kTcNItems * lanes_;
+    const int nr = (int)ritems_.size(), ng = (int)gitems_.size(), nt = (int)titems_.size();
+    const int Wb = 2 * max_sbar + 1;
+    for (int j = 0; j < max_sbar; ++j) LS_CUDA(launch_mpk_items(d_desc_, d_ritems_, nr, d_steps, j, s_));
+    if (item_gram) {
+      // pair groups: enough CTAs to cover the SMs twice
+      const int groups = std::max(1, std::min(16, (2 * gram_grid() + ng - 1) / std::max(ng, 1)));
+      LS_CUDA(launch_gram_items(Wb, d_desc_, d_gitems_, ng, d_wi, d_partials_, groups, moments_, s_));
+      LS_CUDA(launch_gram_items_finalize(Wb, d_partials_, d_item0, d_nitems, d_wi, hi_, d_G_, kGStride, moments_, s_));
+    }
+    if (tc_gram) {  // every tensor-core lane in one launch over the shared basis matrix
+      LS_CUDA(launch_gram_tc_items(Wb, ybase_, yld_, yld_, d_titems_, nt, d_wtc, hi_, d_emax_, d_tpart_, s_));
+      LS_CUDA(launch_gram_items_finalize(Wb, d_tpart_, d_tc0, d_tcn, d_wtc, hi_, d_G_, kGStride, false, s_));
+    }
+    LS_CUDA(launch_block_ctrl_batch(d_G_, kGStride, d_params_, d_params_ + kMaxS, d_params_ + 2 * kMaxS, d_bst_,
+                                    hi_, max_sbar, o_.method == ASCG_ADAPTIVE, d_coords_, kCStride, d_res_hist_,
+                                    rcap_, d_ab_hist_, abcap_, d_spec_, d_tickets_, s_));
+    LS_CUDA(launch_recover_items(Wb, d_desc_, d_ritems_, nr, d_w, d_coords_, kCStride, s_));
+    return ASCG_OK;
+  }
+
+  // The whole block loop of the held lanes as one launch: a graph whose
+  // while-node body is lanes_advance_kernel (which decides, on the device,
+  // each lane's next block or its end, and whether to go on) followed by the
+  // block's kernels for s_max steps (lanes with fewer steps skip the rest, as
+  // in a host-driven block with a larger s of another lane). The host takes
+  // no part between blocks and reads each lane's outcome once at the end.
+  // Each lane's arithmetic is the same as in the host-driven loop. *ran =
+  // false (nothing done) when the stream cannot be captured or the graph
+  // cannot be built, and the caller then drives the blocks from the host.
+  ascg_status run_on_device(bool* ran) {
+    *ran = false;
+    if (!capturable_ || hi_ == 0) return ASCG_OK;
+    if (!d_run_) {
+      LS_TRY(dalloc(&d_run_, (size_t)lanes_));
+      LS_TRY(dalloc(&d_iter_, 1));
+      LS_TRY(dalloc(&d_seq_, (size_t)std::max<size_t>(seq_.size(), 1)));
+    }
+    std::vector<LaneRun> hr(hi_);
+    bool any_tc = false;
+    for (int q = 0; q < hi_; ++q) {
+      const LaneSys& L = lane_[q];
+      LaneRun& R = hr[q];
+      std::memset(&R, 0, sizeof(R));
+      R.active = used_[q] && L.active;
+      R.m = L.m;
+      R.kb = L.kb;
+      R.s_prev = L.s_prev;
+      R.wasted = L.wasted;
+      R.status = L.status;
+      R.tc_ok = used_[q] && !moments_ && L.d.n >= tc_rows_ && gram_tc_aligned(L.d.Y, L.d.ldY);
+      R.rel_upd = L.rel_upd;
+      R.eps_star = L.eps_star;
+      R.bnorm = L.bnorm;
+      R.sqrt_n = std::sqrt((double)L.d.n);
+      any_tc = any_tc || (R.active && R.tc_ok && gram_tc_applies(2 * o_.s_max + 1));
+    }
+    LS_CUDA(cudaMemcpyAsync(d_run_, hr.data(), sizeof(LaneRun) * hi_, cudaMemcpyHostToDevice, s_));
+    LS_CUDA(cudaMemsetAsync(d_iter_, 0, sizeof(int), s_));
+    if (!seq_.empty())
+      LS_CUDA(cudaMemcpyAsync(d_seq_, seq_.data(), sizeof(int) * seq_.size(), cudaMemcpyHostToDevice, s_));
+    LoopParams lp;
+    lp.method = o_.method;
+    lp.s_max = o_.s_max;
+    lp.s0 = o_.s0;
+    lp.f = o_.f;
+    lp.check_in_loop = o_.check_in_loop;
+    lp.max_iters = o_.max_iters;
+    lp.seq_len = (int)seq_.size();
+    lp.iter_cap = o_.max_iters + 2;
+    lp.c = o_.c;
+    lp.seq = d_seq_;
+    // the graph: one while node whose body is captured from the stream
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    auto fail_build = [&](cudaError_t e) {
+      if (exec) cudaGraphExecDestroy(exec);
+      if (g) cudaGraphDestroy(g);
+      cudaGetLastError();
+      (void)e;
+      return ASCG_OK;  // *ran stays false: the host loop takes over
+    };
+    cudaError_t e = cudaGraphCreate(&g, 0);
+    if (e != cudaSuccess) return fail_build(e);
+    cudaGraphConditionalHandle cond;
+    e = cudaGraphConditionalHandleCreate(&cond, g, 1, cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return fail_build(e);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node = nullptr;
+    e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np);
+    if (e != cudaSuccess) return fail_build(e);
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    e = cudaStreamBeginCaptureToGraph(s_, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail_build(e);
+    int* d_steps = d_int_ + kSteps * lanes_;
+    int* d_w = d_int_ + kW * lanes_;
+    int* d_wi = d_int_ + kWItems * lanes_;
+    int* d_wtc = d_int_ + kWTc * lanes_;
+    lanes_advance_kernel<<<1, 1024, 0, s_>>>(d_bst_, d_run_, hi_, d_steps, d_w, d_wi, d_wtc, lp, d_iter_, cond);
+    ascg_status st = cudaGetLastError() == cudaSuccess ? ASCG_OK : ASCG_ERR_CUDA;
+    if (st == ASCG_OK) st = block_kernels(o_.s_max, true, any_tc);
+    cudaGraph_t captured = nullptr;
+    e = cudaStreamEndCapture(s_, &captured);
+    if (st != ASCG_OK || e != cudaSuccess) return fail_build(e);
+    e = cudaGraphInstantiate(&exec, g, 0);
+    if (e != cudaSuccess) return fail_build(e);
+    int iters = 0;
+    e = cudaGraphLaunch(exec, s_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), d_run_, sizeof(LaneRun) * hi_, cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&iters, d_iter_, sizeof(int), cudaMemcpyDeviceToHost, s_);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s_);
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(g);
+    LS_CUDA(e);
+    for (int q = 0; q < hi_; ++q) {
+      if (!used_[q]) continue;
+      LaneSys& L = lane_[q];
+      const LaneRun& R = hr[q];
+      L.m = R.m;
+      L.kb = R.kb;
+      L.s_prev = R.s_prev;
+      L.wasted = R.wasted;
+      L.status = (ascg_status)R.status;
+      L.rel_upd = R.rel_upd;
+      if (R.active) {  // the block cap ended the loop (cannot happen: each block advances every lane)
+        L.status = ASCG_NOT_CONVERGED;
+      }
+      L.active = false;
+      L.done = true;
+    }
+    super_blocks_ += std::max(iters - 1, 0);  // the last pass found no lane running
+    launches_ += 1;
+    *ran = true;
     return ASCG_OK;
   }
 
@@ -755,6 +981,7 @@ class Lockstep {
     dfree(d_desc_); dfree(d_bst_); dfree(d_G_); dfree(d_coords_); dfree(d_int_); dfree(d_sums_); dfree(d_params_);
     dfree(d_res_hist_); dfree(d_ab_hist_); dfree(d_ritems_); dfree(d_gitems_); dfree(d_partials_);
     dfree(d_titems_); dfree(d_tpart_); dfree(d_emax_); dfree(d_spec_); dfree(d_tickets_);
+    dfree(d_run_); dfree(d_iter_); dfree(d_seq_);
     hfree(h_desc_); hfree(h_bst_); hfree(h_int_); hfree(h_sums_);
   }
 
@@ -794,6 +1021,9 @@ class Lockstep {
   int* d_emax_ = nullptr;         // per-lane column exponents, kMaxW each
   int64_t tcap_items_ = 0;
   int tcnp_ = 0;
+  LaneRun* d_run_ = nullptr;      // device-driven block loop: the lanes' running state
+  int* d_iter_ = nullptr;         // its block counter
+  int* d_seq_ = nullptr;          // Alg. 3's block sizes
   double* d_spec_ = nullptr;      // speculative coordinate steps, kSpecDoubles per lane
   unsigned* d_tickets_ = nullptr;  // the block controller's ticket counters, one per lane
   SysDesc* h_desc_ = nullptr;
@@ -859,7 +1089,12 @@ ascg_status lockstep_solve_batch(int count, const ascg_op* ops, const double* co
   LS_TRY(eng.admit(sys, nullptr));
   for (int q = 0; q < count; ++q)
     if (eng.lane(q).status == ASCG_ERR_INVALID) return lfail(ASCG_ERR_INVALID, "b or x_1 is not finite");
-  while (eng.any_active()) LS_TRY(eng.super_block(o.block_hist, o.block_hist_cap));
+  // Without per-block records to return, the whole block loop runs on the
+  // device as one graph launch; otherwise (or if the graph cannot be built)
+  // the host drives it block by block.
+  bool on_device = false;
+  if (!o.block_hist && eng.any_active()) LS_TRY(eng.run_on_device(&on_device));
+  while (!on_device && eng.any_active()) LS_TRY(eng.super_block(o.block_hist, o.block_hist_cap));
   std::vector<int> all(count);
   for (int q = 0; q < count; ++q) all[q] = q;
   LS_TRY(eng.finish(all));
@@ -913,7 +1148,8 @@ struct ascg_server_s {
   int max_systems = 0;
   int running = 0;
   int admit_order = ASCG_ADMIT_FIFO;
-  int large_cap = 0;  // > 0: most systems running at once in the largest size class
+  int large_cap = 0;       // > 0: most systems running at once in the largest size class
+  bool yield_large = false;  // the largest class starts no block while a smaller class has systems
   cudaStream_t user = nullptr;
   Arena arena;
   Group group[kGroups];
@@ -1096,7 +1332,7 @@ ascg_status ascg_server_create(const ascg_options* opts, int64_t hbm_budget, int
   return ASCG_OK;
 }
 
-ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap) {
+ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_class_cap, int yield_large) {
   set_last_error("");
   if (!srv) return lfail(ASCG_ERR_INVALID, "srv is NULL");
   if (admit_order != ASCG_ADMIT_FIFO && admit_order != ASCG_ADMIT_SHORTEST_FIRST)
@@ -1104,6 +1340,7 @@ ascg_status ascg_server_set_policy(ascg_server srv, int admit_order, int large_c
   if (large_class_cap < 0) return lfail(ASCG_ERR_INVALID, "large_class_cap must be >= 0");
   srv->admit_order = admit_order;
   srv->large_cap = large_class_cap;
+  srv->yield_large = yield_large != 0;
   return ASCG_OK;
 }
 
@@ -1161,10 +1398,14 @@ ascg_status ascg_server_step(ascg_server srv, ascg_completion* done, int cap, in
       const size_t before = srv->ready.size();
       if (!srv->queue.empty()) LS_TRY(srv->admit());
       progressed = progressed || srv->ready.size() > before;
-      // 3. the next block of every idle group with work
-      bool in_flight = false;
-      for (Group& g : srv->group) {
-        if (!g.in_flight) {
+      // 3. the next block of every idle group with work (the largest class
+      // waits while a smaller one has systems, when it yields)
+      bool in_flight = false, smaller_busy = false;
+      for (int gi = 0; gi < kGroups; ++gi) {
+        Group& g = srv->group[gi];
+        const bool yield = srv->yield_large && gi == kGroups - 1 && smaller_busy;
+        smaller_busy = smaller_busy || g.eng.active_lanes() > 0;
+        if (!g.in_flight && !yield) {
           LS_TRY(g.eng.refresh());
           bool launched = false;
           LS_TRY(g.eng.launch_block(&launched));

@@ -151,7 +151,7 @@ def test_server_argument_checks(P):
     assert P._lib.ascg_server_step(None, None, 0, None, None, None) == P.ASCG_ERR_INVALID
     assert P._lib.ascg_server_submit(None, None, None, None, 1e-8, 0) == P.ASCG_ERR_INVALID
     assert P._lib.ascg_server_info(None, None) == P.ASCG_ERR_INVALID
-    assert P._lib.ascg_server_set_policy(None, 0, 0) == P.ASCG_ERR_INVALID
+    assert P._lib.ascg_server_set_policy(None, 0, 0, 0) == P.ASCG_ERR_INVALID
     o = P.ascg_options_default()
     h = C.c_void_p()
     assert P._lib.ascg_server_create(C.byref(o), 1 << 20, 4, None, None) == P.ASCG_ERR_INVALID

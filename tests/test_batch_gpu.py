@@ -158,6 +158,51 @@ def test_batch_result_same_alone_and_in_mix(env):
         assert a["blocks"] == m["blocks"], systems[q]["name"]
 
 
+def run_batch_device_loop(P, torch, systems, s_max=S_MAX, max_iters=CAP, method="adaptive", s_seq=None,
+                          moment_gram=False):
+    """As run_batch, without per-block records: the whole block loop then runs
+    on the device as one graph launch (a while node over the blocks)."""
+    ops = [make_op(P, s["A"]) for s in systems]
+    bs = [dev(torch, s["b"]) for s in systems]
+    xs = [dev(torch, s["x1"]) for s in systems]
+    res_hist = np.zeros((len(systems), max_iters + 2))
+    o = P.make_options(method=method, basis="monomial", s_max=s_max, eps_target=1e-10, max_iters=max_iters,
+                       res_hist=res_hist.reshape(-1), s_seq=s_seq, moment_gram=moment_gram)
+    o.res_hist_cap = max_iters + 2
+    results, st = P.ascg_solve_batch(ops, bs, xs, o, eps_targets=[s["eps"] for s in systems])
+    out = [dict(res=results[q], hist=res_hist[q, :results[q].iters + 1].copy(), x=xs[q].cpu().numpy())
+           for q in range(len(systems))]
+    for op in ops:
+        P.ascg_op_destroy(op)
+    return out, st
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(method="variable", s_max=5, s_seq=[1, 1, 2, 3, 5]),
+                                dict(moment_gram=True), dict(max_iters=9)])
+def test_batch_device_loop_equals_host_loop(env, kw):
+    """The device-driven block loop (no per-block records asked for) and the
+    host-driven one give every system the same status, iterations, blocks,
+    residual history and x, bit for bit; the iteration cap ends systems alike."""
+    P, torch = env
+    A = W.poisson3d(40)   # a tensor-core lane beside the small FP64 ones
+    systems = small_batch(seed=14, count=5) + [
+        dict(name="poisson3d_40", A=A, b=W.rhs_uniform(A.n, np.random.default_rng(6)), x1=np.zeros(A.n), eps=1e-8)]
+    host_kw = dict(kw)
+    cap = host_kw.pop("max_iters", CAP)
+    host, st_h = run_batch(P, torch, systems, max_iters=cap, **host_kw)
+    devl, st_d = run_batch_device_loop(P, torch, systems, max_iters=cap, **host_kw)
+    assert st_h == st_d
+    for s, h, d in zip(systems, host, devl):
+        assert d["res"].status == h["res"].status, s["name"]
+        assert d["res"].iters == h["res"].iters and d["res"].blocks == h["res"].blocks, s["name"]
+        assert d["res"].rel_res_true == h["res"].rel_res_true, s["name"]
+        assert d["res"].rel_res_updated == h["res"].rel_res_updated, s["name"]
+        assert d["res"].wasted_vecs == h["res"].wasted_vecs, s["name"]
+        assert np.array_equal(d["hist"], h["hist"]) and np.array_equal(d["x"], h["x"]), s["name"]
+    if cap == 9:
+        assert any(h["res"].status == P.ASCG_NOT_CONVERGED for h in host)
+
+
 def test_batch_edge_cases(env):
     """A zero right-hand side (x = 0, no block), a system whose start is already
     the solution, an iteration cap that stops one system, and fixed s."""

@@ -180,6 +180,25 @@ def test_shortest_first_admission_and_large_cap(env):
         c, x = bserved[q]
         r, xa = solve_alone(P, torch, bops[q], s["b"], s["x1"], s["eps"])
         assert c.result.status == P.ASCG_OK == r.status and np.array_equal(x, xa), s["name"]
+    # yield: with a small system running, the large class starts no block, so
+    # the small system, submitted with the large one, finishes first
+    ysys = [dict(name="big", A=big[0], b=W.rhs_uniform(big[0].n, rng), x1=np.zeros(big[0].n), eps=1e-6),
+            dict(name="small", A=W.poisson2d(30), b=None, x1=None, eps=1e-8)]
+    ysys[1]["b"], ysys[1]["x1"] = W.rhs_uniform(900, rng), np.zeros(900)
+    yops = [make_op(P, q["A"]) for q in ysys]
+    srv = P.ascg_server_create(opts(P), 1 << 32, 8)
+    P.ascg_server_set_policy(srv, P.ASCG_ADMIT_FIFO, 0, True)
+    try:
+        yserved, _ = serve(P, torch, srv, ysys, yops, [([0, 1], 0)])
+    finally:
+        P.ascg_server_destroy(srv)
+    assert yserved[1][0].step_done < yserved[0][0].step_done
+    for q, sy in enumerate(ysys):
+        c, x = yserved[q]
+        r, xa = solve_alone(P, torch, yops[q], sy["b"], sy["x1"], sy["eps"])
+        assert c.result.status == P.ASCG_OK == r.status and np.array_equal(x, xa), sy["name"]
+    for op in yops:
+        P.ascg_op_destroy(op)
     with pytest.raises(P.AscgError):
         srv2 = P.ascg_server_create(opts(P), 1 << 20, 2)
         try:
