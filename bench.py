@@ -90,6 +90,27 @@ def hbm_view(nbytes, ms):
             "peak_source": f"{HBM_PEAK_SRC} copy bandwidth"}
 
 
+def fp64_dgemm_tflops(torch, size=4096, reps=5):
+    """FP64 rate of cuBLAS DGEMM (torch.matmul in float64) on this GPU, best of
+    `reps`: a measured companion to the derived FP64 peak (DGEMM on GB300 uses
+    the same FP64 units as DFMA)."""
+    a = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    b = torch.randn(size, size, dtype=torch.float64, device="cuda")
+    torch.matmul(a, b)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        best = ms if best is None else min(best, ms)
+    del a, b
+    return 2.0 * size ** 3 / (best * 1e-3) / 1e12
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -501,6 +522,8 @@ def our_arm(args):
             classical["fixed_s4_ms_per_solve"] = fms / args.steps
             classical["fixed_s4_iters_per_solve"] = sum(r.iters for r in fres) / args.steps
 
+    dgemm_tf = fp64_dgemm_tflops(torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
         ci, cs, cb = oracle_sample(spec, cfg, 12.0)
@@ -549,6 +572,8 @@ def our_arm(args):
                          "peak_source": "derived: FP64 DFMA 2 per clock per SM (nominal 1.25 TFLOP/s) x 152 SMs x "
                                         "2070 MHz max clock; FP64 is the binding unit (not HBM); the MEASURED_PEAKS "
                                         "file has no FP64 figure",
+                         "fp64_dgemm_measured_tflops": dgemm_tf,
+                         "frac_of_dgemm": (achieved_mpk / dgemm_tf) if achieved_mpk and dgemm_tf else None,
                          "hbm": hbm_view(sum(r.mpk_bytes for r in results), t_mpk)},
             "roofline_gram": {"bound": "tensor", "kernel": "gram_tc_kernel (+ column exponents)",
                               "achieved": achieved_tc, "peak": BF16_PEAK_TF, "unit": "TFLOP/s",

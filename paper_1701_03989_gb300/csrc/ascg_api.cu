@@ -601,7 +601,10 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     double* Ybuf[2] = {w.Y, w.Y2};
     double* cbuf[2] = {w.coords, w.coords + 3 * kMaxW};
     bool x_out[2] = {false, false};  // an x update reading buffer b is queued on the side stream
-    const int x_ctas = std::max(1, gram_grid() - 24);
+    // the x update runs beside the controller, whose CTAs (one per condition
+    // estimate plus one for the steps: s_max + 1 at most) keep their SMs; the
+    // x update takes every other SM, one CTA each
+    const int x_ctas = std::max(1, gram_grid() - (o.method == ASCG_ADAPTIVE ? o.s_max + 1 : 1));
     // Block j uses basis buffer j & 1, coordinates cbuf[j & 1] and record slot
     // j % kRing (device w.bst[slot], pinned host w.h_bst[slot] going in and
     // w.h_bst[kRing + slot] coming back). When block j+1's basis size does not
