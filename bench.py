@@ -499,9 +499,9 @@ def our_arm(args):
         cit = sum(r.iters for r in cres) / args.steps
         ams = ms / args.steps
         # classical CG's own floor per iteration: max(FP64 instructions, HBM bytes) of
-        # its three kernels (SpMV + p^T A p; x, r and r^T r; p = r + beta p)
+        # its three kernels (SpMV + p^T A p; r and r^T r; x += alpha p and p = r + beta p)
         c_flops = 2.0 * (A.nnz + n) + 2.0 * 3 * n + 2.0 * n
-        c_bytes = 12.0 * A.nnz + 4.0 * (n + 1) + 8.0 * n * (2 + 6 + 3)
+        c_bytes = 12.0 * A.nnz + 4.0 * (n + 1) + 8.0 * n * (2 + 3 + 5)
         floor_us = 1e6 * max(c_flops / (peak_tf * 1e12), c_bytes / (HBM_PEAK_GBS * 1e9))
         per_it_us = 1e3 * cms / max(cit, 1)
         classical = {"iters_per_s": cit / (cms * 1e-3), "iters_per_solve": cit, "ms_per_solve": cms,
@@ -513,9 +513,9 @@ def our_arm(args):
                      "us_per_iteration": per_it_us,
                      "floor_us_per_iteration": floor_us,
                      "roofline_frac": floor_us / per_it_us,
-                     "floor_note": "max(FP64: 2(nnz+n) SpMV + 2n p^T A p + 6n update + 2n p update flops at the "
-                                   "FP64 peak; HBM: 12 nnz + 4(n+1) bytes of A + 11 vector passes of 8n bytes at "
-                                   "the measured copy peak)"}
+                     "floor_note": "max(FP64: 2(nnz+n) SpMV + 2n p^T A p + 4n r update + 4n x and p update "
+                                   "flops at the FP64 peak; HBM: 12 nnz + 4(n+1) bytes of A + 10 vector passes of "
+                                   "8n bytes at the measured copy peak)"}
         if args.workload == "poisson2d_32":
             of = P.make_options(method="fixed", basis="monomial", s_max=4, eps_target=eps, max_iters=max_it)
             fms, fres = _timed_solves(P, torch, op, bd, xd, of, args.steps, stream, flush)

@@ -457,9 +457,9 @@ ascg_status run_classical(ascg_op op, double* x, double* r, double* p, double ep
   for (;;) {
     for (int i = 0; i < batch; ++i) {
       ASCG_CUDA(launch_cg_spmv_dot(A, op->nnz, p, w.q, w.cgs, w.partials, w.counter, s));
-      ASCG_CUDA(launch_cg_update(n, x, r, p, w.q, w.cgs, w.partials, w.counter, w.res_hist, w.res_cap,
-                                 w.ab_hist, w.ab_hist + w.ab_cap, w.ab_cap, s));
-      ASCG_CUDA(launch_cg_pupdate(n, r, p, w.cgs, s));
+      ASCG_CUDA(launch_cg_update(n, r, w.q, w.cgs, w.partials, w.counter, w.res_hist, w.res_cap, w.ab_hist,
+                                 w.ab_hist + w.ab_cap, w.ab_cap, s));
+      ASCG_CUDA(launch_cg_pupdate(n, x, r, p, w.cgs, s));
     }
     res->launches += 3 * batch;
     ASCG_CUDA(cudaMemcpyAsync(w.h_cgs, w.cgs, sizeof(CGState), cudaMemcpyDeviceToHost, s));

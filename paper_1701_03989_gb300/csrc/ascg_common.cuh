@@ -344,14 +344,13 @@ struct CGState {
 // is streamed past L2, see sell_row).
 cudaError_t launch_cg_spmv_dot(const DevSell& A, int64_t nnz, const double* p, double* q, CGState* st,
                                double* partials, unsigned* counter, cudaStream_t s);
-// x += alpha p, r -= alpha q, rr_new; the last CTA sets beta, records histories,
-// tests convergence.
-cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q,
-                             CGState* st, double* partials, unsigned* counter, double* res_hist,
-                             int res_cap, double* alpha_hist, double* beta_hist, int ab_cap,
-                             cudaStream_t s);
-// p = r + beta p
-cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGState* st, cudaStream_t s);
+// r -= alpha q, rr_new; the last CTA sets beta, records histories, tests
+// convergence.
+cudaError_t launch_cg_update(int64_t n, double* r, const double* q, CGState* st, double* partials,
+                             unsigned* counter, double* res_hist, int res_cap, double* alpha_hist, double* beta_hist,
+                             int ab_cap, cudaStream_t s);
+// x += alpha p (the iteration's p), then p = r + beta p
+cudaError_t launch_cg_pupdate(int64_t n, double* x, const double* r, double* p, const CGState* st, cudaStream_t s);
 // CG state init from rr = r^T r computed into st->rr.
 cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
                            double* res_hist, int res_cap, cudaStream_t s);

@@ -149,18 +149,20 @@ __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const
   }
 }
 
-__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __restrict__ x, double* __restrict__ r,
-                                                        const double* __restrict__ p, const double* __restrict__ q,
-                                                        CGState* st, double* partials, unsigned* counter,
-                                                        double* res_hist, int res_cap, double* alpha_hist,
-                                                        double* beta_hist, int ab_cap) {
+// r -= alpha A p and r^T r. x is not needed until the iteration's end: its
+// update x += alpha p (the same FMA) runs in cg_pupdate_kernel, which reads p
+// anyway, one pass over x and p fewer per iteration.
+__global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __restrict__ r,
+                                                        const double* __restrict__ q, CGState* st,
+                                                        double* partials, unsigned* counter, double* res_hist,
+                                                        int res_cap, double* alpha_hist, double* beta_hist,
+                                                        int ab_cap) {
   __shared__ double red[32];
   __shared__ int flag;
   if (!st->active) return;
   const double alpha = st->alpha;
   double s = 0.0;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
-    x[i] = fma(alpha, p[i], x[i]);          // x += q, q = alpha p
     const double ri = fma(-alpha, q[i], r[i]);  // r -= A q = alpha (A p)
     r[i] = ri;
     s = fma(ri, ri, s);
@@ -189,12 +191,16 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __res
   }
 }
 
-__global__ void __launch_bounds__(256) cg_pupdate_kernel(int64_t n, const double* __restrict__ r,
-                                                         double* __restrict__ p, const CGState* st) {
+__global__ void __launch_bounds__(256) cg_pupdate_kernel(int64_t n, double* __restrict__ x,
+                                                         const double* __restrict__ r, double* __restrict__ p,
+                                                         const CGState* st) {
   if (!st->active) return;  // this iteration was skipped (solve already done)
-  const double beta = st->beta;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-    p[i] = fma(beta, p[i], r[i]);            // p = r + beta p
+  const double alpha = st->alpha, beta = st->beta;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double pi = p[i];
+    x[i] = fma(alpha, pi, x[i]);             // x += q, q = alpha p (the iteration's p)
+    p[i] = fma(beta, pi, r[i]);              // p = r + beta p
+  }
 }
 
 __global__ void cg_init_kernel(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,
@@ -247,18 +253,18 @@ cudaError_t launch_cg_spmv_dot(const DevSell& A, int64_t nnz, const double* p, d
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_update(int64_t n, double* x, double* r, const double* p, const double* q, CGState* st,
-                             double* partials, unsigned* counter, double* res_hist, int res_cap,
-                             double* alpha_hist, double* beta_hist, int ab_cap, cudaStream_t s) {
+cudaError_t launch_cg_update(int64_t n, double* r, const double* q, CGState* st, double* partials,
+                             unsigned* counter, double* res_hist, int res_cap, double* alpha_hist, double* beta_hist,
+                             int ab_cap, cudaStream_t s) {
   // HBM-bound axpys: 8 CTAs per SM keep enough loads in flight (partials hold one
   // slot per 256-row block, so any grid up to n/256 fits)
-  cg_update_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, x, r, p, q, st, partials, counter, res_hist,
-                                                                res_cap, alpha_hist, beta_hist, ab_cap);
+  cg_update_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, r, q, st, partials, counter, res_hist, res_cap,
+                                                                alpha_hist, beta_hist, ab_cap);
   return cudaGetLastError();
 }
 
-cudaError_t launch_cg_pupdate(int64_t n, const double* r, double* p, const CGState* st, cudaStream_t s) {
-  cg_pupdate_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(n, r, p, st);
+cudaError_t launch_cg_pupdate(int64_t n, double* x, const double* r, double* p, const CGState* st, cudaStream_t s) {
+  cg_pupdate_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(n, x, r, p, st);
   return cudaGetLastError();
 }
 

@@ -202,7 +202,7 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
   __shared__ double part[4][32];
   __shared__ double d[kMaxW], e[kMaxW], e2[kMaxW];
   __shared__ double lo_s[2], hi_s[2];
-  __shared__ double beta_s[2], floor_s;
+  __shared__ double den_s[2], floor_s;
   __shared__ int go_s[2], uncert_s;
   __shared__ unsigned s_mask[2][2];
   for (int idx = threadIdx.x; idx < m * m; idx += blockDim.x) A[idx / m][idx % m] = G[(idx / m) * w + (idx % m)];
@@ -210,7 +210,8 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // The reflection that zeroes column kk below its subdiagonal (run by warp 0):
   // v = x - alpha e_1 over rows kk+1 .. m-1, alpha = -sign(x_0) ||x||, and
-  // beta = 2 / v^T v = 1 / (s2 + |x_0| ||x||) (v^T v = 2 (s2 + |x_0| ||x||)).
+  // beta = 2 / v^T v = 1 / (s2 + |x_0| ||x||) (v^T v = 2 (s2 + |x_0| ||x||));
+  // warp 0 publishes the denominator and every warp divides for itself.
   auto reflector = [&](int kk, int slot) {
     const int len_ = m - kk - 1;
     const bool on_ = lane < len_;
@@ -223,7 +224,7 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
       const double r = sqrt(s2);
       alpha = -copysign(r, x0);
       vv = on_ ? (lane == 0 ? x0 - alpha : xi) : 0.0;
-      if (lane == 0) beta_s[slot] = 1.0 / (s2 + fabs(x0) * r);
+      if (lane == 0) den_s[slot] = s2 + fabs(x0) * r;  // beta = 1 / den, formed by each warp when needed
     }
     vb[slot][lane] = vv;
     if (lane == 0) {
@@ -247,7 +248,7 @@ __device__ void kappa_body(const double* __restrict__ G, BlockState* st, int i, 
     const int sl = k & 1;
     if (go_s[sl]) {  // uniform
       const double vi = on ? vb[sl][lane] : 0.0;
-      const double beta = beta_s[sl];
+      const double beta = 1.0 / den_s[sl];  // off warp 0's path: it overlaps this warp's product below
       const int c0 = (len * warp) >> 2, c1 = (len * (warp + 1)) >> 2;
       double p0 = 0.0, p1 = 0.0;
       if (on) {

@@ -200,15 +200,6 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
       : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, uint32_t (&r)[4]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];\n"
-      "tcgen05.wait::ld.sync.aligned;\n"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-      : "r"(taddr)
-      : "memory");
-}
-
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
@@ -349,16 +340,35 @@ __device__ __forceinline__ void level_add(long long& hi, long long& lo, int L, u
     lo += d << (8 * (7 - L));
 }
 
-// Drain of 4 columns of tile 0 at TMEM column col, whose operand rows are
-// digits (J, B0 + t), t = 0..3. The thread is T0 digit (i, a); for column b
-// its product stands for ((i,a),(J,b)), counted when a <= b, and, when (J,b)
-// is not in T0 (FAR), also for ((J,b),(i,a)), counted when b <= a. Either way
-// it belongs to the entry (min(a,b), max(a,b)), summed in slot t.
+// The four columns of tile 0 for each of the seven digit levels J of entries
+// b = B0 .. B0 + 3 (TMEM columns t0 + {0, 32, 64, 96, 144, 176, 208}): seven
+// loads, then one wait, so the warp waits for tensor memory once per pass
+// instead of seven times.
+__device__ __forceinline__ void tmem_ld4x7(uint32_t t0, uint32_t (&r)[7][4]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%28];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%4,%5,%6,%7}, [%29];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%8,%9,%10,%11}, [%30];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%12,%13,%14,%15}, [%31];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%16,%17,%18,%19}, [%32];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%20,%21,%22,%23}, [%33];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%24,%25,%26,%27}, [%34];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]),
+        "=r"(r[1][3]), "=r"(r[2][0]), "=r"(r[2][1]), "=r"(r[2][2]), "=r"(r[2][3]), "=r"(r[3][0]), "=r"(r[3][1]),
+        "=r"(r[3][2]), "=r"(r[3][3]), "=r"(r[4][0]), "=r"(r[4][1]), "=r"(r[4][2]), "=r"(r[4][3]), "=r"(r[5][0]),
+        "=r"(r[5][1]), "=r"(r[5][2]), "=r"(r[5][3]), "=r"(r[6][0]), "=r"(r[6][1]), "=r"(r[6][2]), "=r"(r[6][3])
+      : "r"(t0), "r"(t0 + 32), "r"(t0 + 64), "r"(t0 + 96), "r"(t0 + 144), "r"(t0 + 176), "r"(t0 + 208)
+      : "memory");
+}
+
+// Level J of the four columns held in r: the thread is T0 digit (i, a); for
+// column b its product stands for ((i,a),(J,b)), counted when a <= b, and,
+// when (J,b) is not in T0 (FAR), also for ((J,b),(i,a)), counted when b <= a.
+// Either way it belongs to the entry (min(a,b), max(a,b)), summed in slot t.
 template <int J, int B0, bool FAR>
-__device__ __forceinline__ void drain_cols(uint32_t taddr, uint32_t col, int i, int a, long long (&hi)[4],
+__device__ __forceinline__ void drain_cols(const uint32_t (&r)[4], int i, int a, long long (&hi)[4],
                                           long long (&lo)[4]) {
-  uint32_t r[4];
-  tmem_ld4(taddr + col, r);
   const int L = i + J;
   if (L > 7) return;
 #pragma unroll
@@ -377,13 +387,15 @@ __device__ __forceinline__ void drain_t0_pass(uint32_t taddr, uint32_t cb, int i
   long long hi[4], lo[4];
 #pragma unroll
   for (int k = 0; k < 4; ++k) hi[k] = lo[k] = 0;
-  drain_cols<0, B0, false>(taddr, cb + 0 + B0, i, a, hi, lo);
-  drain_cols<1, B0, false>(taddr, cb + 32 + B0, i, a, hi, lo);
-  drain_cols<2, B0, false>(taddr, cb + 64 + B0, i, a, hi, lo);
-  drain_cols<3, B0, false>(taddr, cb + 96 + B0, i, a, hi, lo);
-  drain_cols<4, B0, true>(taddr, cb + 144 + B0, i, a, hi, lo);
-  drain_cols<5, B0, true>(taddr, cb + 176 + B0, i, a, hi, lo);
-  drain_cols<6, B0, true>(taddr, cb + 208 + B0, i, a, hi, lo);
+  uint32_t r[7][4];
+  tmem_ld4x7(taddr + cb + B0, r);
+  drain_cols<0, B0, false>(r[0], i, a, hi, lo);
+  drain_cols<1, B0, false>(r[1], i, a, hi, lo);
+  drain_cols<2, B0, false>(r[2], i, a, hi, lo);
+  drain_cols<3, B0, false>(r[3], i, a, hi, lo);
+  drain_cols<4, B0, true>(r[4], i, a, hi, lo);
+  drain_cols<5, B0, true>(r[5], i, a, hi, lo);
+  drain_cols<6, B0, true>(r[6], i, a, hi, lo);
   if (a < w) {
 #pragma unroll
     for (int t = 0; t < 4; ++t) {
