@@ -45,14 +45,20 @@
 // (i >= 4, a <= 31) i-major (144..239), zeros (240..255). Each TMEM load of
 // the drain is then one aligned 16-column block of a single digit level.
 //
-// Pipeline (PTX ISA, tcgen05 and cp.async.bulk.tensor), linked by mbarriers:
+// Pipeline (PTX ISA, tcgen05 and cp.async.bulk.tensor), linked by mbarriers,
+// 29 warps with fixed roles:
 //  - a loader thread issues one 2D tensor-map copy per stage (66 rows x 33
 //    columns of Y; rows past n and columns past w arrive as zeros);
-//  - 17 worker warps turn FP64 into digits (4 rows of a column per thread);
-//    8 of them also drain the TMEM accumulators of the previous chunk;
-//  - one thread issues tcgen05.mma kind::f16 (f16 x f16 -> f32) into one of
-//    two TMEM buffers (tile 0 at 256 p + 0..239, tile 1 at 256 p + 240..255),
-//    so a chunk is drained while the next one is multiplied.
+//  - two groups of 9 converter warps take alternate stages: 8 warps for
+//    columns 0..31, where a thread turns 8 rows of one column from FP64 into
+//    digits with one 16-byte store per digit, and one for column 32, 2 rows
+//    per thread;
+//  - two threads issue tcgen05.mma kind::f16 (f16 x f16 -> f32) into one of
+//    two TMEM buffers, one tile 0 (at 256 p + 0..239), the other tile 1 (at
+//    256 p + 240..255): a small MMA costs about as much as a large one, and
+//    issuing the two tiles from two threads overlaps them better;
+//  - 8 drain warps, two per TMEM lane quarter, fold a chunk's accumulators
+//    into the integer sums while the next chunk is multiplied.
 // All waits are bounded; a wait that runs out writes NaN partials and reports
 // ASCG_ERR_TIMEOUT through the launch's error word, when one is given.
 #include <cuda.h>
@@ -73,7 +79,7 @@ constexpr int kSub = 64;             // rows of Y per stage (MMA K)
 constexpr int kSubPerChunk = 16;
 constexpr int kTChunk = kSub * kSubPerChunk;  // 1024 rows per TMEM accumulation
 constexpr int kDStages = 3;          // digit operand stages
-constexpr int kFStages = 6;          // FP64 staging stages (tensor copies in flight)
+constexpr int kFStages = 6;          // FP64 staging stages (tensor copies in flight); even: a slot keeps its group
 constexpr int kBoxRows = 66;         // rows per tensor copy: column stride 528 B (bank offset)
 constexpr uint32_t kColStride = kBoxRows * 8;
 constexpr uint32_t kFStageBytes = ((kTW * kColStride + 127) / 128) * 128;
@@ -83,13 +89,15 @@ constexpr uint32_t kSBO = (kSub / 8) * 128;   // bytes between 8-row groups (102
 constexpr uint32_t kDStageBytes = 256 * kSub * 2;  // 32 KB: 256 digit rows x 64 fp16
 constexpr int kN0 = 240, kN1 = 16;   // MMA N of tiles 0 and 1
 constexpr int kTile1Col = 240;       // TMEM column of tile 1 within a buffer
-constexpr int kWorkWarps = 17;       // 544 threads: one 4-row item each (16 x 33 items)
-constexpr int kDrainWarps = 8;       // workers 0..7 also drain
-constexpr int kLoadWarp = 17, kMmaWarp = 18;
-constexpr int kTcThreads = 19 * 32;
-constexpr int kDrainLag = 2;         // drain chunk c after converting 3 stages of chunk c+1
+constexpr int kGroupWarps = 9;       // converters per group: 8 for columns 0..31, 1 for column 32
+constexpr int kConvWarps = 2 * kGroupWarps;
+constexpr int kDrainWarp0 = kConvWarps, kDrainWarps = 8;  // drain warp d: lane quarter d & 3, half d >> 2
+constexpr int kLoadWarp = kDrainWarp0 + kDrainWarps;
+constexpr int kMmaWarp = kLoadWarp + 1, kMma1Warp = kMmaWarp + 1;  // tile 0 and tile 1 issuers
+constexpr int kTcThreads = (kMma1Warp + 1) * 32;                   // 928
 constexpr long long kWaitLimit = 1ll << 20;  // polls; with the suspend hint a wait ends within ~2 s
 constexpr long long kTestWaitLimit = 1ll << 12;  // the stall test's limit: a few milliseconds
+static_assert(kFStages % 2 == 0, "a staging slot must belong to one converter group");
 
 // dynamic shared memory layout
 constexpr size_t kDOff = 0;
@@ -97,7 +105,7 @@ constexpr size_t kFOff = kDOff + (size_t)kDStages * kDStageBytes;
 constexpr int kSlices = 3;           // 17-bit slices of an int64 sum, one 32-bit word each
 constexpr size_t kAccOff = kFOff + (size_t)kFStages * kFStageBytes;  // u32 [2 (hi, lo)][3][33][33]
 constexpr size_t kBarOff = kAccOff + 2 * kSlices * 4 * kTW * kTW;
-constexpr int kNumBars = 2 * kFStages + 2 * kDStages + 4;
+constexpr int kNumBars = 2 * kFStages + 2 * kDStages + 6;
 constexpr size_t kSlotOff = kBarOff + 8 * kNumBars;
 constexpr size_t kEmaxOff = kSlotOff + 16;
 constexpr size_t kErrOff = kEmaxOff + 4 * kTW;
@@ -171,12 +179,13 @@ __device__ __forceinline__ int bar_try(uint32_t a, uint32_t parity) {
 }
 
 // Waits until the phase of the given parity has completed. Gives up after
-// kWaitLimit polls or once another role has given up; returns 0 then.
-__device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile int* err, long long limit) {
+// `limit` polls or once another role has given up; returns 0 then.
+__device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile int* err, uint32_t limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < limit; ++it) {
+  if (bar_try(a, parity)) return 1;
+  for (uint32_t it = 1; it < limit; ++it) {
     if (bar_try(a, parity)) return 1;
-    if ((it & 15) == 15 && *err) return 0;
+    if ((it & 15) == 0 && *err) return 0;
   }
   *err = 1;
   return 0;
@@ -184,9 +193,9 @@ __device__ __forceinline__ int bar_wait(uint64_t* bar, uint32_t parity, volatile
 
 // Bounded wait that ignores the error flag: lets copies and MMAs already
 // issued finish before the CTA exits after an error.
-__device__ __forceinline__ void bar_drain(uint64_t* bar, uint32_t parity, long long limit) {
+__device__ __forceinline__ void bar_drain(uint64_t* bar, uint32_t parity, uint32_t limit) {
   const uint32_t a = smem_u32(bar);
-  for (long long it = 0; it < limit; ++it)
+  for (uint32_t it = 0; it < limit; ++it)
     if (bar_try(a, parity)) return;
 }
 
@@ -211,9 +220,13 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
 
 // Balanced digits, step 1. With E = emax - 1022 for the column's largest
 // biased exponent emax, Y = trunc(y 2^(55 - E)) (|Y| < 2^55), and
-// Z = Y + sum_{k<7} 128 * 256^k. Byte k of Z (k < 6) is c_k + 128, and
-// Z >> 48 (9 bits) is c_6 + 128, where Y = sum_k c_k 256^k with c_k in
-// [-128, 127] (k < 6) and c_6 in [-128, 128]. Integer operations only.
+// Z = Y + sum_{k<7} 128 * 256^k + 0x6400 * 2^48. Byte k of Z (k < 6) is
+// c_k + 128, and the top 16 bits of Z are 0x6400 + c_6 + 128 (no carry out:
+// c_6 + 128 <= 256), the fp16 bit pattern of 1024 + c_6 + 128, where
+// Y = sum_k c_k 256^k with c_k in [-128, 127] (k < 6) and c_6 in
+// [-128, 128]. Integer operations only; any emax, zeros and subnormals
+// included.
+constexpr unsigned long long kZBias = 0x6480808080808080ull;
 __device__ __forceinline__ void split_z(double y, int emax, uint32_t& zlo, uint32_t& zhi) {
   const int hi = __double2hiint(y);
   const uint32_t lo = (uint32_t)__double2loint(y);
@@ -226,91 +239,136 @@ __device__ __forceinline__ void split_z(double y, int emax, uint32_t& zlo, uint3
   s = s < 63 ? s : 63;
   unsigned long long Y = (((unsigned long long)Mhi << 32) | Mlo) >> s;
   if (hi < 0) Y = 0ull - Y;
-  const unsigned long long Z = Y + 0x0080808080808080ull;
+  const unsigned long long Z = Y + kZBias;
   zlo = (uint32_t)Z;
   zhi = (uint32_t)(Z >> 32);
 }
 
-// Digit c_k of two entries as an fp16 pair (exact): fp16 0x6400 + t is 1024 + t,
-// minus 1152 gives t - 128.
-template <int K>
-__device__ __forceinline__ uint32_t digit_pair(uint32_t zlo0, uint32_t zhi0, uint32_t zlo1, uint32_t zhi1) {
-  uint32_t t;
-  if (K < 4) {
-    t = __byte_perm(zlo0, zlo1, 0x0400 | (K << 8) | K);  // byte K of each at positions 0, 2
-    t = (t & 0x00FF00FFu) | 0x64006400u;
-  } else if (K < 6) {
-    t = __byte_perm(zhi0, zhi1, 0x0400 | ((K - 4) << 8) | (K - 4));
-    t = (t & 0x00FF00FFu) | 0x64006400u;
-  } else {
-    t = (zhi0 >> 16) | (zhi1 & 0xFFFF0000u) | 0x64006400u;
-  }
-  const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&t), __floats2half2_rn(1152.0f, 1152.0f));
-  return *reinterpret_cast<const uint32_t*>(&h);
+// The same Z for a column with emax >= 55, in fewer operations:
+// Y = (m 4) >> (emax - e) with the implicit bit always set, which is
+// (m 8) >> (emax + 1 - e) for e >= 1; a zero or subnormal entry (e = 0) then
+// shifts by >= 55 and gives 0, as it must (its true Y is 0 below 2^-968).
+// The sign is applied as (Y ^ s) - s with s = 0 or all ones.
+constexpr int kFastSplitMinEmax = 55;
+__device__ __forceinline__ void split_z_fast(double y, int emax, uint32_t& zlo, uint32_t& zhi) {
+  const int hi = __double2hiint(y);
+  const uint32_t lo = (uint32_t)__double2loint(y);
+  const uint32_t t = (uint32_t)(emax - ((hi >> 20) & 0x7ff));
+  const uint32_t Mhi = (__funnelshift_l(lo, (uint32_t)hi, 2) & 0x3FFFFFu) | 0x400000u;
+  const unsigned long long M = ((unsigned long long)Mhi << 32) | (lo << 2);
+  unsigned long long Y;
+  asm("shr.b64 %0, %1, %2;" : "=l"(Y) : "l"(M), "r"(t));  // a shift of 64 or more gives 0
+  const unsigned long long sm = (unsigned long long)(long long)(hi >> 31);
+  const unsigned long long Z = (Y ^ sm) + kZBias - sm;
+  zlo = (uint32_t)Z;
+  zhi = (uint32_t)(Z >> 32);
 }
 
-// The conversion work of one worker thread, the same in every stage. Thread
-// t < 528 takes rows 4 g .. 4 g + 3 of column a, with t = 66 q + 2 a + (g & 1)
-// and q = g >> 1: a warp covers 16 columns for both halves g & 1 of a
-// core-matrix row, so its digit stores fill whole 128-byte rows of the
-// operand (no bank conflicts), and its staging loads (column stride 528 B)
-// spread over all banks. Digit i of the item goes to byte offset
-// base + i * 4096 (+ 2048 for i >= 4) of the stage when a <= 31 (operand rows
-// 32 i + a, or 32 i + 16 + a for i >= 4), and to base + 16 i when a = 32
-// (row 128 + i); see the layout above. Three registers stay live.
-struct ConvItem {
-  uint32_t src;   // byte offset of the item's four values in an FP64 stage; ~0u: no item
-  int ex;         // column a's largest biased exponent, plus 1 << 16 when a = 32
+// The seven digits of two entries as fp16 pairs (exact), w[i] holding digit
+// i = 0 (c_6, most significant) .. 6 (c_0) of entry 0 in the low half and of
+// entry 1 in the high half. Bytes k, k + 1 of both Z are first gathered into
+// one word; each fp16 pair is then 0x64 | byte (1024 + c + 128), minus 1152;
+// the top digit comes with its 0x64 already in place (kZBias).
+__device__ __forceinline__ void digit_words(uint32_t zl0, uint32_t zh0, uint32_t zl1, uint32_t zh1,
+                                            uint32_t (&w)[kDig]) {
+  const uint32_t x01 = __byte_perm(zl0, zl1, 0x5140);  // z0.b0 z1.b0 z0.b1 z1.b1
+  const uint32_t x23 = __byte_perm(zl0, zl1, 0x7362);  // z0.b2 z1.b2 z0.b3 z1.b3
+  const uint32_t x45 = __byte_perm(zh0, zh1, 0x5140);  // bytes 4, 5
+  uint32_t t[kDig];
+  t[0] = __byte_perm(x01, 0x64646464u, 0x4140);
+  t[1] = __byte_perm(x01, 0x64646464u, 0x4342);
+  t[2] = __byte_perm(x23, 0x64646464u, 0x4140);
+  t[3] = __byte_perm(x23, 0x64646464u, 0x4342);
+  t[4] = __byte_perm(x45, 0x64646464u, 0x4140);
+  t[5] = __byte_perm(x45, 0x64646464u, 0x4342);
+  t[6] = __byte_perm(zh0, zh1, 0x7632);  // the top 16 bits of each Z
+  const __half2 c = __floats2half2_rn(1152.0f, 1152.0f);
+#pragma unroll
+  for (int k = 0; k < kDig; ++k) {
+    const __half2 h = __hsub2(*reinterpret_cast<const __half2*>(&t[k]), c);
+    w[kDig - 1 - k] = *reinterpret_cast<const uint32_t*>(&h);
+  }
+}
+
+// A converter thread's task in every stage of its group. In converter warp
+// k < 8 of a group, lane l takes rows 8 g .. 8 g + 7 of column
+// a = 8 (k & 3) + (l & 7), g = 4 (k >> 2) + (l >> 3): the 8 lanes of a
+// quarter warp share g and cover 8 consecutive columns, so each 16-byte load
+// from the staging box (column stride 528 B) and each 16-byte digit store
+// (8 consecutive operand rows of one core matrix) is free of bank conflicts.
+// Warp 8 takes column 32, rows 2 l and 2 l + 1 in lane l.
+//
+// Digit i of column a <= 31 goes to operand row 32 i + a (i <= 3) or
+// 32 i + 16 + a (i >= 4), at byte (row >> 3) 1024 + g 128 + (row & 7) 16
+// of the stage, and of column 32 to row 128 + i; see the layout above.
+struct ConvTask {
+  uint32_t src;   // byte offset of the task's values in an FP64 stage; ~0u: no task
   uint32_t base;  // byte offset of digit 0 in a digit stage
+  int emax;       // the column's largest biased exponent
 };
 
-__device__ __forceinline__ ConvItem conv_item(int ptid, int w, const int* s_emax) {
-  ConvItem c;
-  const int q = ptid / 66, rem = ptid - 66 * q;
-  const int a = rem >> 1, g = 2 * q + (rem & 1);
-  const bool on = ptid < 16 * kTW && a < w;
-  const int aa = on ? a : 0;
-  c.src = on ? (uint32_t)(aa * kColStride + g * 32) : ~0u;
-  c.ex = s_emax[aa] | (aa == 32 ? 1 << 16 : 0);
-  const uint32_t gb = (uint32_t)((g >> 1) * kLBO + (g & 1) * 8);
-  c.base = aa <= 31 ? gb + (uint32_t)((aa >> 3) * kSBO + (aa & 7) * 16) : gb + 16 * kSBO;
+__device__ __forceinline__ ConvTask conv_task(int k, int lane, int w, const int* s_emax) {
+  ConvTask c;
+  int a;
+  if (k < 8) {
+    a = 8 * (k & 3) + (lane & 7);
+    const int g = 4 * (k >> 2) + (lane >> 3);
+    c.base = (uint32_t)((a >> 3) * kSBO + g * kLBO + (a & 7) * 16);
+    c.src = (uint32_t)(a * kColStride + g * 64);
+  } else {
+    a = 32;
+    c.base = (uint32_t)(16 * kSBO + (lane >> 2) * kLBO + (lane & 3) * 4);
+    c.src = (uint32_t)(a * kColStride + lane * 16);
+  }
+  const bool on = a < w;
+  if (!on) c.src = ~0u;
+  c.emax = s_emax[on ? a : 0];
   return c;
 }
 
-// Converts the thread's item of one stage: rows [row0, row0 + 64) of Y from
-// the FP64 staging box (column a at a * 528 B; zeros past n) into the digit
-// operand.
-__device__ __forceinline__ void convert_item(unsigned char* dst, const unsigned char* fst, const ConvItem& c) {
-  const double2* src = reinterpret_cast<const double2*>(fst + c.src);
-  const int emax = c.ex & 0xFFFF;
-  const bool last = c.ex >= (1 << 16);
-  const uint32_t stride = last ? 16u : 4u * kSBO;
-  const uint32_t base_hi = last ? c.base : c.base + 2u * kSBO;
-  const double2 t0 = src[0], t1 = src[1];
-  uint32_t zlo[4], zhi[4];
-  split_z(t0.x, emax, zlo[0], zhi[0]);
-  split_z(t0.y, emax, zlo[1], zhi[1]);
-  split_z(t1.x, emax, zlo[2], zhi[2]);
-  split_z(t1.y, emax, zlo[3], zhi[3]);
+template <int N>
+__device__ __forceinline__ void split_n(const double (&y)[N], int emax, uint32_t (&zl)[N], uint32_t (&zh)[N]) {
+  if (emax >= kFastSplitMinEmax) {
 #pragma unroll
-  for (int i = 0; i < kDig; ++i) {  // digit i (most significant first) is c_(6-i)
-    uint32_t wd[2];
+    for (int q = 0; q < N; ++q) split_z_fast(y[q], emax, zl[q], zh[q]);
+  } else {
 #pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const uint32_t a0 = zlo[2 * p], b0 = zhi[2 * p], a1 = zlo[2 * p + 1], b1 = zhi[2 * p + 1];
-      switch (6 - i) {
-        case 6: wd[p] = digit_pair<6>(a0, b0, a1, b1); break;
-        case 5: wd[p] = digit_pair<5>(a0, b0, a1, b1); break;
-        case 4: wd[p] = digit_pair<4>(a0, b0, a1, b1); break;
-        case 3: wd[p] = digit_pair<3>(a0, b0, a1, b1); break;
-        case 2: wd[p] = digit_pair<2>(a0, b0, a1, b1); break;
-        case 1: wd[p] = digit_pair<1>(a0, b0, a1, b1); break;
-        default: wd[p] = digit_pair<0>(a0, b0, a1, b1); break;
-      }
-    }
-    const uint32_t off = (i < 4 ? c.base : base_hi) + (uint32_t)i * stride;
-    *reinterpret_cast<uint2*>(dst + off) = make_uint2(wd[0], wd[1]);
+    for (int q = 0; q < N; ++q) split_z(y[q], emax, zl[q], zh[q]);
   }
+}
+
+// Converts the thread's task of one stage (zeros past n arrive as zeros):
+// columns 0..31, 8 rows into 7 digit rows of 8 fp16, one 16-byte store per
+// digit; column 32, 2 rows into 7 fp16 pairs.
+__device__ __forceinline__ void convert_main(unsigned char* dst, const unsigned char* fst, const ConvTask& c) {
+  const double2* src = reinterpret_cast<const double2*>(fst + c.src);
+  double y[8];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double2 v = src[q];
+    y[2 * q] = v.x;
+    y[2 * q + 1] = v.y;
+  }
+  uint32_t zl[8], zh[8];
+  split_n<8>(y, c.emax, zl, zh);
+  uint32_t wd[4][kDig];
+#pragma unroll
+  for (int p = 0; p < 4; ++p) digit_words(zl[2 * p], zh[2 * p], zl[2 * p + 1], zh[2 * p + 1], wd[p]);
+#pragma unroll
+  for (int i = 0; i < kDig; ++i) {
+    const uint32_t off = c.base + (uint32_t)i * 4u * kSBO + (i >= 4 ? 2u * kSBO : 0u);
+    *reinterpret_cast<uint4*>(dst + off) = make_uint4(wd[0][i], wd[1][i], wd[2][i], wd[3][i]);
+  }
+}
+
+__device__ __forceinline__ void convert_col32(unsigned char* dst, const unsigned char* fst, const ConvTask& c) {
+  const double2 v = *reinterpret_cast<const double2*>(fst + c.src);
+  const double y[2] = {v.x, v.y};
+  uint32_t zl[2], zh[2], wd[kDig];
+  split_n<2>(y, c.emax, zl, zh);
+  digit_words(zl[0], zh[0], zl[1], zh[1], wd);
+#pragma unroll
+  for (int i = 0; i < kDig; ++i) *reinterpret_cast<uint32_t*>(dst + c.base + 16u * i) = wd[i];
 }
 
 // Adds an int64 v (|v| < 2^50) to the CTA's sum at word index idx of the slice
@@ -331,19 +389,26 @@ __device__ __forceinline__ long long slice_value(const uint32_t* acc, int idx) {
          ((long long)acc[kPlane + idx] << 17) + (long long)acc[idx];
 }
 
-// Scales a product to its level L = i + j and adds it to the hi/lo sums.
-__device__ __forceinline__ void level_add(long long& hi, long long& lo, int L, uint32_t fbits, int times) {
-  const long long d = (long long)__float2int_rn(__uint_as_float(fbits)) * times;
-  if (L <= 3)
-    hi += d << (8 * (3 - L));
-  else if (L <= 7)
-    lo += d << (8 * (7 - L));
+// acc += d 2^k for an exact integer product sum d held as an fp32 (|d| <= 2^24):
+// one conversion and one wide multiply-add.
+template <int K>
+__device__ __forceinline__ void add_scaled(long long& acc, uint32_t fbits) {
+  const int d = __float2int_rn(__uint_as_float(fbits));
+  asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(acc) : "r"(d), "r"(1 << K));
+}
+
+// Product sum of level L = I + J into hi (L <= 3) or lo (4 <= L <= 7).
+template <int L>
+__device__ __forceinline__ void level_sum(long long& hi, long long& lo, uint32_t fbits) {
+  if constexpr (L <= 3)
+    add_scaled<8 * (3 - L)>(hi, fbits);
+  else if constexpr (L <= 7)
+    add_scaled<8 * (7 - L)>(lo, fbits);
 }
 
 // The four columns of tile 0 for each of the seven digit levels J of entries
 // b = B0 .. B0 + 3 (TMEM columns t0 + {0, 32, 64, 96, 144, 176, 208}): seven
-// loads, then one wait, so the warp waits for tensor memory once per pass
-// instead of seven times.
+// loads, then one wait.
 __device__ __forceinline__ void tmem_ld4x7(uint32_t t0, uint32_t (&r)[7][4]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%28];\n"
@@ -362,138 +427,112 @@ __device__ __forceinline__ void tmem_ld4x7(uint32_t t0, uint32_t (&r)[7][4]) {
       : "memory");
 }
 
-// Level J of the four columns held in r: the thread is T0 digit (i, a); for
-// column b its product stands for ((i,a),(J,b)), counted when a <= b, and,
-// when (J,b) is not in T0 (FAR), also for ((J,b),(i,a)), counted when b <= a.
-// Either way it belongs to the entry (min(a,b), max(a,b)), summed in slot t.
-template <int J, int B0, bool FAR>
-__device__ __forceinline__ void drain_cols(const uint32_t (&r)[4], int i, int a, long long (&hi)[4],
-                                          long long (&lo)[4]) {
-  const int L = i + J;
-  if (L > 7) return;
+// Level J of the four columns held in r, for the T0 digit (I, a) of the
+// lane: the product with (J, b) stands for ((I,a),(J,b)), counted when
+// a <= b, and, when (J, b) is not in T0 (J >= 4), also for ((J,b),(I,a)),
+// counted when b <= a. The sums keep the two kinds apart (near: J <= 3,
+// far: J >= 4) and weigh them per entry afterwards.
+template <int I, int J>
+__device__ __forceinline__ void drain_level(const uint32_t (&r)[4], long long (&hn)[4], long long (&ln)[4],
+                                           long long (&lf)[4]) {
 #pragma unroll
   for (int t = 0; t < 4; ++t) {
-    const int b = B0 + t;
-    const int times = (a <= b ? 1 : 0) + (FAR && b <= a ? 1 : 0);
-    level_add(hi[t], lo[t], L, r[t], times);
+    if constexpr (J <= 3)
+      level_sum<I + J>(hn[t], ln[t], r[t]);
+    else if constexpr (I + J <= 7)
+      add_scaled<8 * (7 - (I + J))>(lf[t], r[t]);
   }
 }
 
-// Entries b = B0 .. B0 + 3 of T0 digit (i, a): all seven digit levels j of b,
-// then one sliced addition per entry.
-template <int B0>
-__device__ __forceinline__ void drain_t0_pass(uint32_t taddr, uint32_t cb, int i, int a, int w, uint32_t* acc_hi,
-                                              uint32_t* acc_lo) {
-  long long hi[4], lo[4];
+// Drains the chunk in TMEM columns tq + 0..255 for a warp of lane quarter I:
+// half 0 takes tile 0's entries b = 0..15, half 1 entries b = 16..32 and
+// tile 1. Sums per entry in registers, then one sliced addition per entry
+// into the CTA's sums (acc_hi, acc_lo). Lanes of a warp have distinct a, so
+// their entries differ.
+template <int I>
+__device__ __forceinline__ void drain_quarter(uint32_t tq, int a, int w, uint32_t* acc_hi, uint32_t* acc_lo,
+                                              int half) {
+#pragma unroll 1
+  for (int B0 = 16 * half; B0 < 16 * half + 16; B0 += 4) {
+    uint32_t r[7][4];
+    tmem_ld4x7(tq + (uint32_t)B0, r);
+    long long hn[4], ln[4], lf[4];
 #pragma unroll
-  for (int k = 0; k < 4; ++k) hi[k] = lo[k] = 0;
-  uint32_t r[7][4];
-  tmem_ld4x7(taddr + cb + B0, r);
-  drain_cols<0, B0, false>(r[0], i, a, hi, lo);
-  drain_cols<1, B0, false>(r[1], i, a, hi, lo);
-  drain_cols<2, B0, false>(r[2], i, a, hi, lo);
-  drain_cols<3, B0, false>(r[3], i, a, hi, lo);
-  drain_cols<4, B0, true>(r[4], i, a, hi, lo);
-  drain_cols<5, B0, true>(r[5], i, a, hi, lo);
-  drain_cols<6, B0, true>(r[6], i, a, hi, lo);
-  if (a < w) {
+    for (int t = 0; t < 4; ++t) hn[t] = ln[t] = lf[t] = 0;
+    drain_level<I, 0>(r[0], hn, ln, lf);
+    drain_level<I, 1>(r[1], hn, ln, lf);
+    drain_level<I, 2>(r[2], hn, ln, lf);
+    drain_level<I, 3>(r[3], hn, ln, lf);
+    drain_level<I, 4>(r[4], hn, ln, lf);
+    drain_level<I, 5>(r[5], hn, ln, lf);
+    drain_level<I, 6>(r[6], hn, ln, lf);
+    if (a < w) {
 #pragma unroll
-    for (int t = 0; t < 4; ++t) {
-      const int b = B0 + t;
-      if (b >= w) continue;
-      const int idx = (a < b ? a : b) * kTW + (a < b ? b : a);
-      if (hi[t] != 0) slice_add(acc_hi, idx, hi[t]);
-      if (lo[t] != 0) slice_add(acc_lo, idx, lo[t]);
-    }
-  }
-}
-
-// Entry b = 32 of T0 digit (i, a): operand rows 128..134 hold digits (j, 32),
-// j = 0..6, and b = 32 > a.
-__device__ __forceinline__ void drain_t0_b32(uint32_t taddr, uint32_t cb, int i, int a, int w, uint32_t* acc_hi,
-                                             uint32_t* acc_lo) {
-  uint32_t r[8];
-  tmem_ld8(taddr + cb + 128, r);
-  long long hi = 0, lo = 0;
-#pragma unroll
-  for (int j = 0; j < 7; ++j) level_add(hi, lo, i + j, r[j], 1);
-  if (a < w && w == kTW) {
-    if (hi != 0) slice_add(acc_hi, a * kTW + 32, hi);
-    if (lo != 0) slice_add(acc_lo, a * kTW + 32, lo);
-  }
-}
-
-// Tile 1, operand row R = 128 + 32 quarter + lane: columns 0..3 hold
-// D[row, (j, 32)], j = 0..3. Row (i <= 3, 32): ((i,32),(j,32)) -> G_32,32.
-// Row (i >= 4, 32): also ((j,32),(i,32)), so twice. Row (i >= 4, a <= 31):
-// ((i,a),(j,32)) -> G_a,32. Slot 0 sums G_a,32, slot 1 sums G_32,32.
-__device__ __forceinline__ void drain_t1(uint32_t taddr, uint32_t cb, int R, long long (&hi2)[2],
-                                         long long (&lo2)[2]) {
-  uint32_t r[16];
-  tmem_ld16(taddr + cb + kTile1Col, r);
-  int i = 0, slot = -1, times = 1;
-  if (R < 132) {
-    i = R - 128;
-    slot = 1;
-  } else if (R < 135) {
-    i = 4 + (R - 132);
-    slot = 1;
-    times = 2;
-  } else if (R >= 144 && R < 240) {
-    i = 4 + (R - 144) / 32;
-    slot = 0;
-  }
-  if (slot < 0) return;
-#pragma unroll
-  for (int j = 0; j < 4; ++j) {
-    if (slot == 0)
-      level_add(hi2[0], lo2[0], i + j, r[j], times);
-    else
-      level_add(hi2[1], lo2[1], i + j, r[j], times);
-  }
-}
-
-// Drains the accumulators of chunk c (TMEM buffer c & 1): sums per entry in
-// registers, then one sliced addition per entry into the CTA's sums
-// (acc_hi, acc_lo). Lanes of a warp have distinct a, so their entries differ.
-__device__ __forceinline__ bool drain_chunk(uint32_t c, int w, int half, int quarter, int lane, uint32_t taddr,
-                                            uint64_t* acc_full, uint64_t* acc_empty, volatile int* s_err,
-                                            long long limit, uint32_t* acc_hi, uint32_t* acc_lo) {
-  const uint32_t p = c & 1;
-  if (!bar_wait(acc_full + p, (c >> 1) & 1, s_err, limit)) return false;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  const uint32_t cb = 256u * p;
-  const int a = lane;
-  if (half == 0) {
-    drain_t0_pass<0>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<4>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<8>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<12>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-  } else {
-    drain_t0_pass<16>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<20>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<24>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_pass<28>(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    drain_t0_b32(taddr, cb, quarter, a, w, acc_hi, acc_lo);
-    long long hi2[2] = {0, 0}, lo2[2] = {0, 0};
-    drain_t1(taddr, cb, 128 + quarter * 32 + lane, hi2, lo2);
-    if (w == kTW) {
-      const int R = 128 + quarter * 32 + lane;
-      if (R >= 144 && R < 240) {
-        const int a2 = (R - 144) % 32;
-        if (hi2[0] != 0) slice_add(acc_hi, a2 * kTW + 32, hi2[0]);
-        if (lo2[0] != 0) slice_add(acc_lo, a2 * kTW + 32, lo2[0]);
-      }
-      if (R < 135) {
-        if (hi2[1] != 0) slice_add(acc_hi, 32 * kTW + 32, hi2[1]);
-        if (lo2[1] != 0) slice_add(acc_lo, 32 * kTW + 32, lo2[1]);
+      for (int t = 0; t < 4; ++t) {
+        const int b = B0 + t;
+        if (b >= w) break;
+        const bool le = a <= b;
+        const long long hi = le ? hn[t] : 0;
+        const long long lo = (le ? ln[t] : 0) + (a == b ? 2 * lf[t] : lf[t]);
+        const int idx = le ? a * kTW + b : b * kTW + a;
+        if (hi != 0) slice_add(acc_hi, idx, hi);
+        if (lo != 0) slice_add(acc_lo, idx, lo);
       }
     }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-  __syncwarp();
-  if (lane == 0) bar_arrive(acc_empty + p);
-  return true;
+  if (half == 0) return;
+  // entry b = 32 (> a): TMEM columns 128..134 hold the digits (J, 32), J = 0..6
+  {
+    uint32_t r[8];
+    tmem_ld8(tq + 128, r);
+    long long hi = 0, lo = 0;
+    level_sum<I + 0>(hi, lo, r[0]);
+    level_sum<I + 1>(hi, lo, r[1]);
+    level_sum<I + 2>(hi, lo, r[2]);
+    level_sum<I + 3>(hi, lo, r[3]);
+    level_sum<I + 4>(hi, lo, r[4]);
+    level_sum<I + 5>(hi, lo, r[5]);
+    level_sum<I + 6>(hi, lo, r[6]);
+    if (a < w && w == kTW) {
+      if (hi != 0) slice_add(acc_hi, a * kTW + 32, hi);
+      if (lo != 0) slice_add(acc_lo, a * kTW + 32, lo);
+    }
+  }
+  // Tile 1, operand row R = 128 + 32 I + a: columns 0..3 hold D[R, (j, 32)],
+  // j = 0..3. Row (i <= 3, 32): ((i,32),(j,32)) -> G_32,32. Row (i >= 4, 32):
+  // also ((j,32),(i,32)), so twice. Row (i >= 4, a' <= 31): ((i,a'),(j,32))
+  // -> G_a',32.
+  if (w == kTW) {
+    uint32_t r[16];
+    tmem_ld16(tq + kTile1Col, r);
+    const int R = 128 + 32 * I + a;
+    int i = 0, times = 1, ent = -1;
+    if (R < 132) {
+      i = R - 128;
+      ent = 32 * kTW + 32;
+    } else if (R < 135) {
+      i = 4 + (R - 132);
+      times = 2;
+      ent = 32 * kTW + 32;
+    } else if (R >= 144 && R < 240) {
+      i = 4 + (R - 144) / 32;
+      ent = ((R - 144) % 32) * kTW + 32;
+    }
+    if (ent >= 0) {
+      long long hi = 0, lo = 0;
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int L = i + j;
+        const long long d = (long long)__float2int_rn(__uint_as_float(r[j])) * times;
+        if (L <= 3)
+          hi += d << (8 * (3 - L));
+        else if (L <= 7)
+          lo += d << (8 * (7 - L));
+      }
+      if (hi != 0) slice_add(acc_hi, ent, hi);
+      if (lo != 0) slice_add(acc_lo, ent, lo);
+    }
+  }
 }
 
 // The Gram partial of the chunks ch = c_lo, c_lo + c_step, ... < c_hi of the
@@ -513,11 +552,12 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
   uint32_t* acc_lo = acc_hi + kSlices * kTW * kTW;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kBarOff);
   uint64_t* f_full = bars;                  // tensor copy landed (tx count)
-  uint64_t* f_empty = bars + kFStages;      // workers done reading
-  uint64_t* d_full = bars + 2 * kFStages;   // workers done writing digits
+  uint64_t* f_empty = bars + kFStages;      // converters done reading
+  uint64_t* d_full = bars + 2 * kFStages;   // converters done writing digits
   uint64_t* d_empty = d_full + kDStages;    // MMAs done reading digits
   uint64_t* acc_full = d_empty + kDStages;  // [2] a chunk's MMAs are complete
   uint64_t* acc_empty = acc_full + 2;       // [2] its accumulators are drained
+  uint64_t* mma_done = acc_empty + 2;       // [2] per issuer: its MMAs are complete (error path)
   uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kSlotOff);
   int* s_emax = reinterpret_cast<int*>(smem + kEmaxOff);
   volatile int* s_err = reinterpret_cast<volatile int*>(smem + kErrOff);
@@ -532,15 +572,16 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
     *s_err = 0;
     for (int k = 0; k < kFStages; ++k) {
       bar_init(f_full + k, 1);
-      bar_init(f_empty + k, kWorkWarps);
+      bar_init(f_empty + k, kGroupWarps);
     }
     for (int k = 0; k < kDStages; ++k) {
-      bar_init(d_full + k, kWorkWarps);
-      bar_init(d_empty + k, 1);
+      bar_init(d_full + k, kGroupWarps);
+      bar_init(d_empty + k, 2);  // both issuers commit
     }
     for (int k = 0; k < 2; ++k) {
-      bar_init(acc_full + k, 1);
+      bar_init(acc_full + k, 2);
       bar_init(acc_empty + k, kDrainWarps);
+      bar_init(mma_done + k, 1);
     }
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -554,43 +595,70 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tbase = *tslot;
   const int64_t n = n_local;
-  const long long lim = guard.wait_limit;
+  const uint32_t lim = (uint32_t)(guard.wait_limit < 0xFFFFFFFFll ? guard.wait_limit : 0xFFFFFFFFll);
   const bool stall_here = guard.stall_stage >= 0 && blockIdx.x == 0;
   uint32_t armed = 0;   // loader: stages whose copies were issued
-  uint32_t issued = 0;  // MMA issuer: stages whose MMAs were issued
+  uint32_t issued = 0;  // MMA issuers: stages whose MMAs this thread issued
 
-  if (warp < kWorkWarps) {
-    // ---- workers: FP64 -> digits; warps 0..7 also drain the previous chunk ----
-    const bool drains = warp < kDrainWarps;
-    const int half = warp >> 2, quarter = warp & 3;
-    const uint32_t taddr = tbase + ((uint32_t)(quarter * 32) << 16);
-    const ConvItem item = conv_item(tid, w, s_emax);
-    uint32_t t = 0, cu = 0, drained = 0;
-    for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
+  if (warp < kConvWarps) {
+    // ---- converters: group G takes the stages t with t % 2 == G ----
+    const uint32_t G = warp >= kGroupWarps ? 1u : 0u;
+    const int k = warp - (int)G * kGroupWarps;
+    const ConvTask task = conv_task(k, lane, w, s_emax);
+    uint32_t T = 0;  // stages of this CTA
+    for (int64_t ch = c_lo; ch < c_hi; ch += c_step) {
       const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
-      const int nsub = left < kSubPerChunk ? (int)left : kSubPerChunk;
-      for (int sub = 0; sub < nsub; ++sub, ++t) {
-        const int fs = (int)(t % kFStages), ds = (int)(t % kDStages);
-        if (!bar_wait(f_full + fs, (t / kFStages) & 1, s_err, lim)) goto done;
-        if (t >= kDStages && !bar_wait(d_empty + ds, (t / kDStages - 1) & 1, s_err, lim)) goto done;
-        if (item.src != ~0u) convert_item(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, item);
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) {
-          bar_arrive(f_empty + fs);
-          bar_arrive(d_full + ds);
-        }
-        if (drains && sub == kDrainLag)
-          for (; drained < cu; ++drained)
-            if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, lim, acc_hi,
-                             acc_lo))
-              goto done;
+      T += (uint32_t)(left < kSubPerChunk ? left : kSubPerChunk);
+    }
+    // stage t: staging slot fs = t % kFStages of parity fpar = (t / kFStages) & 1,
+    // digit slot ds = t % kDStages with dq = t / kDStages
+    uint32_t fs = G, fpar = 0, ds = G, dq = 0;
+    for (uint32_t t = G; t < T; t += 2) {
+      if (!bar_wait(f_full + fs, fpar, s_err, lim)) goto done;
+      if (t >= kDStages && !bar_wait(d_empty + ds, (dq - 1) & 1, s_err, lim)) goto done;
+      if (task.src != ~0u) {
+        if (k < 8)
+          convert_main(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, task);
+        else
+          convert_col32(dstage + ds * kDStageBytes, fstage + fs * kFStageBytes, task);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        bar_arrive(f_empty + fs);
+        bar_arrive(d_full + ds);
+      }
+      fs += 2;
+      if (fs >= (uint32_t)kFStages) {
+        fs -= kFStages;
+        fpar ^= 1;
+      }
+      ds += 2;
+      if (ds >= (uint32_t)kDStages) {
+        ds -= kDStages;
+        ++dq;
       }
     }
-    if (drains)
-      for (; drained < cu; ++drained)
-        if (!drain_chunk(drained, w, half, quarter, lane, taddr, acc_full, acc_empty, s_err, lim, acc_hi, acc_lo))
-          goto done;
+  } else if (warp < kDrainWarp0 + kDrainWarps) {
+    // ---- drain: warp of lane quarter I folds each chunk into the sums ----
+    const int I = warp & 3;
+    const uint32_t tl = tbase + ((uint32_t)(I * 32) << 16);
+    uint32_t cu = 0;
+    for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
+      const uint32_t p = cu & 1;
+      if (!bar_wait(acc_full + p, (cu >> 1) & 1, s_err, lim)) goto done;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t tq = tl + 256u * p;
+      switch (I) {
+        case 0: drain_quarter<0>(tq, lane, w, acc_hi, acc_lo, (warp - kDrainWarp0) >> 2); break;
+        case 1: drain_quarter<1>(tq, lane, w, acc_hi, acc_lo, (warp - kDrainWarp0) >> 2); break;
+        case 2: drain_quarter<2>(tq, lane, w, acc_hi, acc_lo, (warp - kDrainWarp0) >> 2); break;
+        default: drain_quarter<3>(tq, lane, w, acc_hi, acc_lo, (warp - kDrainWarp0) >> 2); break;
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(acc_empty + p);
+    }
   } else if (warp == kLoadWarp) {
     // ---- loader: one tensor copy per stage ----
     if (lane == 0) {
@@ -609,9 +677,12 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         }
       }
     }
-  } else if (warp == kMmaWarp) {
-    // ---- MMA issue ----
+  } else if (warp == kMmaWarp || warp == kMma1Warp) {
+    // ---- MMA issue: tile 0 (rows 0..127 x 0..239) or tile 1 (rows 128..255 x 128..143) ----
     if (lane == 0) {
+      const bool t0 = warp == kMmaWarp;
+      const uint32_t aoff = t0 ? 0u : 16u * kSBO;  // operand row 0 or 128
+      const uint32_t idesc = t0 ? instr_desc(128, kN0) : instr_desc(128, kN1);
       uint32_t t = 0, cu = 0;
       for (int64_t ch = c_lo; ch < c_hi; ch += c_step, ++cu) {
         const int64_t left = (n - ch * kTChunk + kSub - 1) / kSub;
@@ -619,19 +690,16 @@ __device__ __forceinline__ void gram_tc_body(const CUtensorMap* ymap_p, int w, i
         const uint32_t p = cu & 1;
         if (cu >= 2 && !bar_wait(acc_empty + p, ((cu >> 1) - 1) & 1, s_err, lim)) goto done;
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d0 = tbase + 256u * p;
+        const uint32_t d0 = tbase + 256u * p + (t0 ? 0u : (uint32_t)kTile1Col);
         for (int sub = 0; sub < nsub; ++sub, ++t) {
           const int ds = (int)(t % kDStages);
           if (!bar_wait(d_full + ds, (t / kDStages) & 1, s_err, lim)) goto done;
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-          const uint32_t sb = smem_u32(dstage + ds * kDStageBytes);
+          const uint32_t sb = smem_u32(dstage + ds * kDStageBytes) + aoff;
 #pragma unroll
           for (int ks = 0; ks < kSub / 16; ++ks) {
-            const uint32_t acc = (sub > 0 || ks > 0) ? 1u : 0u;
-            const uint64_t rows0 = smem_desc(sb + ks * 2 * kLBO);               // operand rows 0..
-            const uint64_t rows128 = smem_desc(sb + 16 * kSBO + ks * 2 * kLBO);  // operand rows 128..
-            mma_f16(d0, rows0, rows0, instr_desc(128, kN0), acc);
-            mma_f16(d0 + kTile1Col, rows128, rows128, instr_desc(128, kN1), acc);
+            const uint64_t desc = smem_desc(sb + ks * 2 * kLBO);
+            mma_f16(d0, desc, desc, idesc, (sub > 0 || ks > 0) ? 1u : 0u);
           }
           mma_commit(d_empty + ds);
           issued = t + 1;
@@ -646,8 +714,10 @@ done:
     if (warp == kLoadWarp && lane == 0)
       for (uint32_t k = armed > (uint32_t)kFStages ? armed - kFStages : 0; k < armed; ++k)
         bar_drain(f_full + k % kFStages, (k / kFStages) & 1, lim);
-    if (warp == kMmaWarp && lane == 0 && issued > 0)
-      bar_drain(d_empty + (issued - 1) % kDStages, ((issued - 1) / kDStages) & 1, lim);
+    if ((warp == kMmaWarp || warp == kMma1Warp) && lane == 0 && issued > 0) {
+      mma_commit(mma_done + (warp - kMmaWarp));  // tracks this thread's MMAs only
+      bar_drain(mma_done + (warp - kMmaWarp), 0, lim);
+    }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
