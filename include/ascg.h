@@ -138,6 +138,11 @@ typedef struct {
 #define ASCG_FLAG_GRAM_TC 32  /* ascg_solve: the tensor-core Gram for every
                                  block with w >= 9, whatever n (excludes
                                  ASCG_FLAG_GRAM_FP64 and ASCG_FLAG_MOMENT_GRAM) */
+#define ASCG_FLAG_RECOVER_FP64 64 /* ascg_solve: the recovery (eq. coords) by
+                                 FP64 FMAs for every block. By default a block
+                                 whose Gram took the tensor cores also recovers
+                                 x, r and p on them, in one pass over Y (see
+                                 ascg_recover_tc for its error bound)          */
 #define ASCG_FLAG_MOMENT_GRAM 8 /* monomial basis only: G from 6 sbar moments
                                  (ascg_gram_moments) instead of Y^T Y; a
                                  variant that rounds differently            */
@@ -334,6 +339,25 @@ ascg_status ascg_block_step(int sbar, const double* G, int method, const double*
  * it is written). */
 ascg_status ascg_recover(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
                          double* x, double* r, double* p, void* cuda_stream);
+
+/* Recovery, eq. (coords), on the tensor cores, as the solver runs it for a
+ * block whose Gram took the tensor cores: x += Y x', r = Y r', p = Y p' in
+ * one pass over Y. Each column of Y becomes a 55-bit fixed-point integer
+ * relative to its largest entry (the Gram's digit split); each coefficient
+ * vector takes its columns' scales in and becomes a 55-bit fixed-point
+ * integer too; the digit products are summed exactly and each result is
+ * rounded once to FP64. Error against the exact sum_j Y_ij c_j: at most
+ * 2^-53 |result| + 2^-54 sum_j ||y_j||_inf |c_j| +
+ * (w + 2) 2^-52 max_j ||y_j||_inf |c_j| (normwise; ascg_recover's is
+ * componentwise), plus the rounding of x + (Y x')_i.
+ *  - n, w, Y, ldY, coords, x, r, p: as for ascg_recover, with
+ *    9 <= w <= 33, Y 16-byte aligned and ldY even (else ASCG_ERR_INVALID),
+ *    n <= 2^31 - 1. r and p may alias columns 1 and 0 of Y.
+ *  - Allocates 136 bytes of device memory for the column exponents and
+ *    synchronises the stream. ASCG_ERR_TIMEOUT: a bounded wait of the kernel
+ *    ran out (the outputs are then incomplete). */
+ascg_status ascg_recover_tc(int64_t n, int w, const double* Y, int64_t ldY, const double* coords,
+                            double* x, double* r, double* p, void* cuda_stream);
 
 /* Newton basis shifts: Ritz values of the Lanczos tridiagonal of k classical
  * CG steps (T_jj = 1/alpha_j + beta_{j-1}/alpha_{j-1}, T_{j,j+1} =

@@ -37,6 +37,7 @@ ASCG_FLAG_C_FORMULA = 4
 ASCG_FLAG_MOMENT_GRAM = 8
 ASCG_FLAG_TEST_GRAM_STALL = 16
 ASCG_FLAG_GRAM_TC = 32
+ASCG_FLAG_RECOVER_FP64 = 64
 
 
 class ascg_block_info(C.Structure):
@@ -106,6 +107,7 @@ def _load():
         "ascg_block_step": (C.c_int, [C.c_int, P, C.c_int, P, P, P, I64, C.c_double, C.c_double, C.c_int,
                                       C.c_int, C.c_double, P, C.POINTER(ascg_block_info), P, P]),
         "ascg_recover": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
+        "ascg_recover_tc": (C.c_int, [I64, C.c_int, P, I64, P, P, P, P, P]),
         "ascg_newton_shifts": (C.c_int, [P, P, C.c_int, C.c_int, P, P]),
         "ascg_server_create": (C.c_int, [C.POINTER(ascg_options), I64, C.c_int, P, C.POINTER(P)]),
         "ascg_server_submit": (C.c_int, [P, P, P, P, C.c_double, I64]),
@@ -328,6 +330,11 @@ def ascg_recover(n, w, Y, ldY, coords, x, r, p, stream=None):
                              _stream(stream)), "ascg_recover")
 
 
+def ascg_recover_tc(n, w, Y, ldY, coords, x, r, p, stream=None):
+    _check(_lib.ascg_recover_tc(int(n), int(w), _ptr(Y), int(ldY), _ptr(coords), _ptr(x), _ptr(r), _ptr(p),
+                                _stream(stream)), "ascg_recover_tc")
+
+
 def ascg_newton_shifts(alphas, betas, k, s, stream=None):
     al = np.ascontiguousarray(alphas, dtype=np.float64)
     be = np.ascontiguousarray(betas if len(betas) else [0.0], dtype=np.float64)
@@ -348,13 +355,14 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
                  lam=None, newton_warmup=0, max_iters=100000, check_in_loop=True, timing=False,
                  res_hist=None, block_hist=None, alpha_hist=None, beta_hist=None,
                  gram_fp64=False, s_seq=None, c_formula=None, moment_gram=False,
-                 tc_lane_rows=0, test_gram_stall=False, gram_tc=False) -> ascg_options:
+                 tc_lane_rows=0, test_gram_stall=False, gram_tc=False, recover_fp64=False) -> ascg_options:
     """ascg_options filled from keywords. History arrays are numpy (float64) or a
     ctypes array of ascg_block_info; the caller keeps them alive for the call.
     s_seq (method "variable"): the block sizes s_0, s_1, ... (the last repeats);
     the options object keeps its own copy alive. c_formula = (kappa(A), ||A||):
     c_{k,j} = 6 N_k j kappa(A) instead of the constant c. moment_gram: G from
-    the monomial basis' moments (ascg_gram_moments)."""
+    the monomial basis' moments (ascg_gram_moments). recover_fp64: the recovery by
+    FP64 FMAs even where the Gram took the tensor cores."""
     o = ascg_options_default()
     o.method = _METHODS[method] if isinstance(method, str) else int(method)
     o.basis = _BASES[basis] if isinstance(basis, str) else int(basis)
@@ -376,6 +384,8 @@ def make_options(method="adaptive", basis="monomial", s_max=8, s0=None, f=None, 
         o.flags |= ASCG_FLAG_TEST_GRAM_STALL
     if gram_tc:
         o.flags |= ASCG_FLAG_GRAM_TC
+    if recover_fp64:
+        o.flags |= ASCG_FLAG_RECOVER_FP64
     if c_formula is not None:
         o.flags |= ASCG_FLAG_C_FORMULA
         o.kappa_A, o.norm_A = float(c_formula[0]), float(c_formula[1])
@@ -404,7 +414,7 @@ def block_infos(count: int):
 
 EXPORTED = ["ascg_options_default", "ascg_op_create_csr", "ascg_op_destroy", "ascg_op_size", "ascg_solve",
             "ascg_solve_host", "ascg_solve_batch", "ascg_spmv", "ascg_matrix_powers", "ascg_gram", "ascg_gram_noalloc", "ascg_gram_moments",
-            "ascg_block_step", "ascg_recover",
+            "ascg_block_step", "ascg_recover", "ascg_recover_tc",
             "ascg_newton_shifts", "ascg_server_create", "ascg_server_submit", "ascg_server_step",
             "ascg_server_info", "ascg_server_set_policy", "ascg_server_destroy", "ascg_tune_gram_schedule",
             "ascg_last_error"]

@@ -490,6 +490,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
   const bool gram_fp64 = (o.flags & ASCG_FLAG_GRAM_FP64) != 0;
   const bool gram_tc_force = (o.flags & ASCG_FLAG_GRAM_TC) != 0;
   const bool gram_mom = (o.flags & ASCG_FLAG_MOMENT_GRAM) != 0;
+  const bool rec_fp64 = (o.flags & ASCG_FLAG_RECOVER_FP64) != 0;
   const bool stall_test = (o.flags & ASCG_FLAG_TEST_GRAM_STALL) != 0;
   if (timing) ASCG_CUDA(cudaEventRecord(w.ev[0], s));
 
@@ -617,6 +618,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     const bool ahead = o.method == ASCG_FIXED_S || o.method == ASCG_VARIABLE_S ||
                        (o.method == ASCG_ADAPTIVE && o.f >= o.s_max - 1);
     int wb_of[kRing] = {};
+    bool rec_tc_of[kRing] = {};  // the block's recovery ran on the tensor cores (x included)
     int sbar_of[kRing] = {};
     auto enqueue = [&](int j, int sbar) -> ascg_status {
       const int slot = j % kRing, cur = j & 1;
@@ -680,7 +682,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
       else
         ASCG_CUDA(launch_gram_finalize(wb, w.partials, nparts, w.G, s, gate));
       res->launches += 2;
-      if (j > 0) {  // block j-1's x += Y x', beside this block's kappa and controller
+      if (j > 0 && !rec_tc_of[(j - 1) % kRing]) {  // block j-1's x += Y x', beside this block's controller
         const int ps = (j - 1) % kRing;
         ASCG_CUDA(cudaEventRecord(w.ev_gram, s));
         ASCG_CUDA(cudaStreamWaitEvent(w.side, w.ev_gram, 0));
@@ -699,7 +701,16 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[cur ^ 1], 0));
         x_out[cur ^ 1] = false;
       }
-      ASCG_CUDA(launch_recover_rp(n, wb, Yc, w.ldY, cbuf[cur], Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s, gate));
+      // A block whose Gram took the tensor cores recovers x, r and p on them in
+      // one pass (its column exponents are in w.expp); otherwise r and p here
+      // and x during the next block.
+      const bool tc_rec = tc_gram && !rec_fp64;
+      rec_tc_of[slot] = tc_rec;
+      if (tc_rec)
+        ASCG_CUDA(launch_recover_tc(n, wb, Yc, w.ldY, w.expp, cbuf[cur], x, Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s,
+                                    &dst->status, gate));
+      else
+        ASCG_CUDA(launch_recover_rp(n, wb, Yc, w.ldY, cbuf[cur], Ybuf[cur ^ 1] + w.ldY, Ybuf[cur ^ 1], s, gate));
       res->launches += 2;
       if (timing) ASCG_CUDA(cudaEventRecord(ev[4], s));
       ASCG_CUDA(cudaMemcpyAsync(w.h_bst + kRing + slot, dst, sizeof(BlockState), cudaMemcpyDeviceToHost, s));
@@ -747,9 +758,11 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
         const double nchains = 2.0 * sbar - 1.0;
         res->mpk_flops += nchains * 2.0 * (double)op->nnz;
         res->mpk_bytes += (double)sbar * (12.0 * op->nnz + 4.0 * (n + 1)) + nchains * 16.0 * n + 8.0 * n;
-        // the timed part: r = Y r', p = Y p' (x += Y x' runs later, on the side stream)
-        res->recover_flops += 2.0 * 2.0 * wb * (double)n;
-        res->recover_bytes += 8.0 * wb * (double)n + 16.0 * n;
+        // the timed part: r = Y r', p = Y p', and x += Y x' on the tensor-core
+        // path (the FP64 path's x update runs later, on the side stream)
+        const double nvec = rec_tc_of[slot] ? 3.0 : 2.0;
+        res->recover_flops += 2.0 * nvec * wb * (double)n;
+        res->recover_bytes += 8.0 * wb * (double)n + (rec_tc_of[slot] ? 32.0 : 16.0) * n;
       }
       const BlockState& out = w.h_bst[kRing + slot];
       res->grid_reductions += 1;
@@ -799,7 +812,7 @@ ascg_status solve_device(ascg_op op, const double* b, double* x, const ascg_opti
     // on the side stream
     for (int bq = 0; bq < 2; ++bq)
       if (x_out[bq]) ASCG_CUDA(cudaStreamWaitEvent(s, w.ev_x[bq], 0));
-    if (enq > 0) {
+    if (enq > 0 && !rec_tc_of[(enq - 1) % kRing]) {
       const int last = enq - 1, ls = last % kRing;
       ASCG_CUDA(launch_recover_x(n, wb_of[ls], Ybuf[last & 1], w.ldY, cbuf[last & 1], x, x_ctas, s,
                                  &w.bst[ls].active));
@@ -1181,6 +1194,27 @@ ascg_status ascg_recover(int64_t n, int w, const double* Y, int64_t ldY, const d
   if (!Y || !coords || !x || !r || !p || n < 1 || w < 1 || w > ASCG_MAX_W || (w % 2) == 0 || ldY < n)
     return fail(ASCG_ERR_INVALID, "bad argument");
   ASCG_CUDA(launch_recover(n, w, Y, ldY, coords, x, r, p, (cudaStream_t)cuda_stream));
+  return ASCG_OK;
+}
+
+ascg_status ascg_recover_tc(int64_t n, int w, const double* Y, int64_t ldY, const double* coords, double* x,
+                            double* r, double* p, void* cuda_stream) {
+  g_err.clear();
+  if (!Y || !coords || !x || !r || !p || n < 1 || n > 0x7fffffffll || w < kGramTcMinW || w > ASCG_MAX_W || ldY < n)
+    return fail(ASCG_ERR_INVALID, "bad argument");
+  if (!gram_tc_aligned(Y, ldY)) return fail(ASCG_ERR_INVALID, "Y must be 16-byte aligned with an even ldY");
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  int* expp = nullptr;  // column exponents, then the kernel's error word
+  ASCG_TRY(dev_alloc(&expp, (size_t)kMaxW + 1));
+  int herr = 0;
+  cudaError_t e = cudaMemsetAsync(expp + kMaxW, 0, sizeof(int), s);
+  if (e == cudaSuccess) e = launch_col_exponents(n, w, Y, ldY, expp, s);
+  if (e == cudaSuccess) e = launch_recover_tc(n, w, Y, ldY, expp, coords, x, r, p, s, expp + kMaxW);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, expp + kMaxW, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(expp);
+  if (e != cudaSuccess) return fail(ASCG_ERR_CUDA, std::string("recover_tc: ") + cudaGetErrorString(e));
+  if (herr == ASCG_ERR_TIMEOUT) return fail(ASCG_ERR_TIMEOUT, "recover_tc: a bounded wait of the kernel ran out");
   return ASCG_OK;
 }
 

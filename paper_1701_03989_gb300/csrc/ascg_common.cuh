@@ -210,6 +210,18 @@ bool gram_tc_fits(int64_t n);
 cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t rows, const GramItem* items,
                                  int nitems, const int* sys_w, int nsys, int* emax_all, double* partials,
                                  cudaStream_t s);
+// Recovery (eq. coords) on the tensor cores: x += Y x', r = Y r', p = Y p' in
+// one pass, with the Gram's digit split of Y (col_emax: the Gram's column
+// exponents, device int[kMaxW]) and coefficients (coords: device double[3w],
+// x', r', p'). Each result is the FP64 rounding of a fixed-point sum, within a
+// normwise bound (kernels_gram_tc.cu). kGramTcMinW <= w <= kMaxW, Y aligned
+// as for the tensor-core Gram; r and p may be columns 1 and 0 of Y. err and
+// gate: as in TcGuard.
+cudaError_t launch_recover_tc(int64_t n, int w, const double* Y, int64_t ldY, const int* col_emax,
+                              const double* coords, double* x, double* r, double* p, cudaStream_t s,
+                              int* err = nullptr, const int* gate = nullptr);
+// The largest biased exponent of each column into col_emax (device int[kMaxW]).
+cudaError_t launch_col_exponents(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, cudaStream_t s);
 cudaError_t launch_gram_any(int64_t n, int w, const double* Y, int64_t ldY, bool force_fp64, int* col_emax,
                             bool emax_ready, double* partials, int* nparts, cudaStream_t s, int* err = nullptr,
                             bool stall_test = false, const int* gate = nullptr);

@@ -850,11 +850,327 @@ __global__ void __launch_bounds__(256) tc_items_exponent_kernel(int w, const dou
   }
 }
 
+// ---------------------------------------------------------------------------
+// Recovery (eq. coords) on the tensor cores: x += Y x', r = Y r', p = Y p' in
+// one pass over Y, with the digit split of the Gram.
+//
+// Per column j, Y_ij = Yt_ij 2^(E_j - 55), Yt the truncated 55-bit integer of
+// the Gram in seven balanced base-256 digits. The coefficients take the column
+// scale in, u_vj = c_vj 2^(E_j - 55) (exact), and get one exponent per vector
+// v (x', r', p'): u_vj = ut_vj 2^(F_v - 55), ut again a truncated 55-bit
+// integer in seven digits. Then sum_j Y_ij c_vj = 2^(F_v - 55) sum_j Yt_ij
+// ut_vj, and digit d of Yt times digit e of ut weighs 256^(12 - d - e).
+// One MMA chain per 128 rows of Y (M = 128, K = 231 = 33 columns x 7 digits
+// padded to 240, N = 24 = 3 vectors x 8 levels padded to 32) forms
+// D[i, (v, L)] = sum_{j, d} yt_ijd ut_vj(L-d): each sum holds the products of
+// one level L = d + e, exact in FP32 (|D| < 2^22). Levels L >= 8 are dropped
+// (below 2^-56 of the largest product). Per row and vector,
+// T = sum_{L <= 7} D_L 256^(7 - L) = T_hi 2^32 + T_lo (two int64), and the
+// result T 2^(F_v - 15) is rounded once to FP64 (one fma).
+// Error against the exact sum_j Y_ij c_vj: at most 2^-53 |result| +
+// 2^-54 sum_j ||y_j||_inf |c_vj| + (w + 2) 2^-52 max_j ||y_j||_inf |c_vj|, a
+// normwise bound like the Gram's (the FP64 recovery's is componentwise,
+// gamma_w sum_j |Y_ij c_vj|).
+//
+// Pipeline, 26 warps: a loader thread (one tensor-map copy of 128 rows x 33
+// columns per tile, two staging slots); 20 converter warps (16 take 8 columns
+// of one row each, 4 take column 32), two digit slots; one MMA thread, the
+// 15 K-steps of a tile alternating between two accumulators so that
+// consecutive MMAs do not wait on each other; 4 drain warps, one per TMEM
+// lane quarter, each lane one row. All waits are bounded, as in the Gram.
+constexpr int kRTile = 128;                         // rows of Y per tile (MMA M)
+constexpr int kRK = 240;                            // MMA K: 224 (digits x columns 0..31) + 7 (column 32) + 9 zeros
+constexpr uint32_t kRSBO = (kRK / 8) * 128;         // bytes between 8-row groups (3840)
+constexpr uint32_t kRABytes = (kRTile / 8) * kRSBO; // one digit tile (61440)
+constexpr uint32_t kRFBytes = kTW * kRTile * 8;     // one staging tile (33792)
+constexpr uint32_t kRBBytes = 4 * kRSBO;            // coefficient digits, 32 rows (15360)
+constexpr int kRN = 32;                             // MMA N: (v, L) = 8 v + L
+constexpr int kRConvWarps = 20, kRDrainWarp0 = 20, kRLoadWarp = 24, kRMmaWarp = 25;
+constexpr int kRThreads = 26 * 32;
+constexpr size_t kRAOff = 0;
+constexpr size_t kRFOff = kRAOff + 2 * (size_t)kRABytes;
+constexpr size_t kRBOff = kRFOff + 2 * (size_t)kRFBytes;
+constexpr size_t kRBarOff = kRBOff + kRBBytes;
+constexpr int kRNumBars = 13;
+constexpr size_t kRSlotOff = kRBarOff + 8 * kRNumBars;
+constexpr size_t kREmaxOff = kRSlotOff + 16;
+constexpr size_t kRFvOff = (kREmaxOff + 4 * kTW + 15) / 16 * 16;  // int[4]: per-vector exponents, a NaN flag
+constexpr size_t kRScaleOff = kRFvOff + 16;        // double[3]
+constexpr size_t kRErrOff = kRScaleOff + 24;
+constexpr size_t kRSmem = kRErrOff + 16;
+static_assert(kRFOff % 1024 == 0 && kRBOff % 1024 == 0 && kRBarOff % 8 == 0 && kRScaleOff % 8 == 0, "alignment");
+static_assert(kRSmem <= 227 * 1024, "shared memory per CTA");
+
+// Byte offset of operand row R, K index k (a multiple of 8), in a digit tile.
+__host__ __device__ constexpr uint32_t rec_off(int R, int k) {
+  return (uint32_t)((R >> 3) * kRSBO + (k >> 3) * 128 + (R & 7) * 16);
+}
+
+__device__ __forceinline__ uint64_t rec_desc(uint32_t saddr) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((128u >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((kRSBO >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+__device__ __forceinline__ void tmem_ld8x2(uint32_t a0, uint32_t a1, uint32_t (&r)[2][8]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%16];\n"
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%8,%9,%10,%11,%12,%13,%14,%15}, [%17];\n"
+      "tcgen05.wait::ld.sync.aligned;\n"
+      : "=r"(r[0][0]), "=r"(r[0][1]), "=r"(r[0][2]), "=r"(r[0][3]), "=r"(r[0][4]), "=r"(r[0][5]), "=r"(r[0][6]),
+        "=r"(r[0][7]), "=r"(r[1][0]), "=r"(r[1][1]), "=r"(r[1][2]), "=r"(r[1][3]), "=r"(r[1][4]), "=r"(r[1][5]),
+        "=r"(r[1][6]), "=r"(r[1][7])
+      : "r"(a0), "r"(a1)
+      : "memory");
+}
+
+// One row and vector: the levels L = 0..7 in two accumulators (e, o) to the
+// FP64 value T 2^(F_v - 15), scale = 2^(F_v - 15).
+__device__ __forceinline__ double rec_value(const uint32_t (&e)[8], const uint32_t (&o)[8], double scale) {
+  long long hi = 0, lo = 0;
+#pragma unroll
+  for (int L = 0; L < 8; ++L) {
+    const int d = __float2int_rn(__uint_as_float(e[L]) + __uint_as_float(o[L]));  // exact: |e|, |o| < 2^21
+    if (L <= 3)
+      asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(hi) : "r"(d), "r"(1 << (8 * (3 - L))));
+    else
+      asm("mad.wide.s32 %0, %1, %2, %0;" : "+l"(lo) : "r"(d), "r"(1 << (8 * (7 - L))));
+  }
+  // |hi|, |lo| < 2^47: both exact in FP64; one rounding in the fma
+  return fma((double)hi, 4294967296.0, (double)lo) * scale;
+}
+
+__global__ void __launch_bounds__(kRThreads, 1)
+    recover_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
+                      const double* __restrict__ coords, double* __restrict__ x, double* __restrict__ r,
+                      double* __restrict__ p, const TcGuard guard) {
+  // uniform, before any barrier or tensor memory: a block enqueued ahead with
+  // nothing to do, or one whose Gram already failed (its error word is set),
+  // leaves x, r and p alone
+  if ((guard.gate && !*guard.gate) || (guard.err && *guard.err != 0)) return;
+  extern __shared__ __align__(1024) unsigned char smem[];
+  unsigned char* astage = smem + kRAOff;
+  unsigned char* fstage = smem + kRFOff;
+  unsigned char* bop = smem + kRBOff;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + kRBarOff);
+  uint64_t* f_full = bars;          // [2] tensor copy landed
+  uint64_t* f_empty = bars + 2;     // [2] converters done reading
+  uint64_t* a_full = bars + 4;      // [2] digits written
+  uint64_t* a_empty = bars + 6;     // [2] MMAs done reading them
+  uint64_t* acc_full = bars + 8;    // [2] a tile's MMAs complete
+  uint64_t* acc_empty = bars + 10;  // [2] its accumulators drained
+  uint64_t* mma_done = bars + 12;   // the MMA thread's MMAs complete (error path)
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + kRSlotOff);
+  int* s_emax = reinterpret_cast<int*>(smem + kREmaxOff);
+  int* s_fv = reinterpret_cast<int*>(smem + kRFvOff);
+  double* s_scale = reinterpret_cast<double*>(smem + kRScaleOff);
+  volatile int* s_err = reinterpret_cast<volatile int*>(smem + kRErrOff);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+  // digit tiles and coefficient digits start at zero (padding stays zero)
+  for (uint32_t o = tid * 16; o < 2 * kRABytes; o += kRThreads * 16)
+    *reinterpret_cast<uint4*>(astage + o) = make_uint4(0, 0, 0, 0);
+  for (uint32_t o = tid * 16; o < kRBBytes; o += kRThreads * 16)
+    *reinterpret_cast<uint4*>(bop + o) = make_uint4(0, 0, 0, 0);
+  if (tid < kTW) s_emax[tid] = tid < w ? col_emax[tid] : 0;
+  if (tid < 4) s_fv[tid] = 0;
+  if (tid == 0) {
+    *s_err = 0;
+    for (int k = 0; k < 2; ++k) {
+      bar_init(f_full + k, 1);
+      bar_init(f_empty + k, kRConvWarps);
+      bar_init(a_full + k, kRConvWarps);
+      bar_init(a_empty + k, 1);
+      bar_init(acc_full + k, 1);
+      bar_init(acc_empty + k, 4);
+    }
+    bar_init(mma_done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == kRMmaWarp) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(smem_u32(tslot)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  __syncthreads();
+  // coefficients: u_vj = c_vj 2^(E_j - 55), E_j = emax_j - 1022; per vector the
+  // largest biased exponent f_v; a NaN or infinite column or coefficient
+  // makes every result NaN
+  const int cv = tid / kTW, cj = tid % kTW;
+  const bool cthr = tid < 3 * kTW && cj < w;
+  double u = 0.0;
+  if (cthr) {
+    // a zero column (emax 0) takes no part: its digits are all zero
+    u = s_emax[cj] == 0 ? 0.0 : ldexp(coords[cv * w + cj], s_emax[cj] - 1077);
+    const int eu = (__double2hiint(u) >> 20) & 0x7ff;
+    atomicMax(s_fv + cv, eu);
+    if (eu == 0x7ff || s_emax[cj] == 0x7ff) atomicMax(s_fv + 3, 1);
+  }
+  __syncthreads();
+  if (cthr) {
+    // B[(v, L), (j, d)] = digit L - d of ut_vj: column j <= 31 at K = 32 d + j,
+    // column 32 at K = 224 + d
+    uint32_t zl, zh, dw[kDig];
+    split_z(u, s_fv[cv], zl, zh);
+    digit_words(zl, zh, zl, zh, dw);
+    unsigned short* b16 = reinterpret_cast<unsigned short*>(bop);
+#pragma unroll
+    for (int d = 0; d < kDig; ++d)
+#pragma unroll
+      for (int e = 0; e < kDig; ++e) {
+        if (d + e > 7) continue;
+        const int R = 8 * cv + d + e, k = cj <= 31 ? 32 * d + cj : 224 + d;
+        b16[(rec_off(R, k & ~7) + (k & 7) * 2) / 2] = (unsigned short)(dw[e] & 0xFFFFu);
+      }
+  }
+  if (tid < 3) s_scale[tid] = ldexp(1.0, s_fv[tid] - 1037);
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tbase = *tslot;
+  const int64_t ntiles = (n + kRTile - 1) / kRTile;
+  const uint32_t T = ntiles > blockIdx.x ? (uint32_t)((ntiles - 1 - blockIdx.x) / gridDim.x + 1) : 0u;
+  const uint32_t lim = (uint32_t)(guard.wait_limit < 0xFFFFFFFFll ? guard.wait_limit : 0xFFFFFFFFll);
+  uint32_t armed = 0, issued = 0;
+
+  if (warp < kRConvWarps) {
+    // ---- converters: warp k < 16 takes columns 8 (k & 3) .. + 7 of row
+    // 32 (k >> 2) + lane; warps 16..19 column 32 of row 32 (k - 16) + lane ----
+    const bool col32 = warp >= 16;
+    const int jb = warp & 3;
+    const int row = col32 ? 32 * (warp - 16) + lane : 32 * (warp >> 2) + lane;
+    const bool on = col32 ? w == kTW : 8 * jb < w;
+    for (uint32_t t = 0; t < T; ++t) {
+      const uint32_t s = t & 1, par = (t >> 1) & 1;
+      if (!bar_wait(f_full + s, par, s_err, lim)) goto rdone;
+      if (t >= 2 && !bar_wait(a_empty + s, par ^ 1, s_err, lim)) goto rdone;
+      if (on) {
+        const double* f = reinterpret_cast<const double*>(fstage + s * kRFBytes);
+        unsigned char* dst = astage + s * kRABytes;
+        if (!col32) {
+          double y[8];
+          uint32_t zl[8], zh[8];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) y[c] = f[(8 * jb + c) * kRTile + row];
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int em = s_emax[8 * jb + c];  // the same in every lane
+            if (em >= kFastSplitMinEmax)
+              split_z_fast(y[c], em, zl[c], zh[c]);
+            else
+              split_z(y[c], em, zl[c], zh[c]);
+          }
+          uint32_t wd[4][kDig];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) digit_words(zl[2 * q], zh[2 * q], zl[2 * q + 1], zh[2 * q + 1], wd[q]);
+#pragma unroll
+          for (int d = 0; d < kDig; ++d)
+            *reinterpret_cast<uint4*>(dst + rec_off(row, 32 * d + 8 * jb)) =
+                make_uint4(wd[0][d], wd[1][d], wd[2][d], wd[3][d]);
+        } else {
+          const double y = f[32 * kRTile + row];
+          uint32_t zl, zh, dw[kDig];
+          const int em = s_emax[32];
+          if (em >= kFastSplitMinEmax)
+            split_z_fast(y, em, zl, zh);
+          else
+            split_z(y, em, zl, zh);
+          digit_words(zl, zh, zl, zh, dw);
+          // digits 0..6 at K = 224..230, K = 231 zero
+          *reinterpret_cast<uint4*>(dst + rec_off(row, 224)) =
+              make_uint4(__byte_perm(dw[0], dw[1], 0x5410), __byte_perm(dw[2], dw[3], 0x5410),
+                         __byte_perm(dw[4], dw[5], 0x5410), dw[6] & 0xFFFFu);
+        }
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        bar_arrive(f_empty + s);
+        bar_arrive(a_full + s);
+      }
+    }
+  } else if (warp < kRDrainWarp0 + 4) {
+    // ---- drain: lane quarter q, one row per lane ----
+    const int q = warp & 3;
+    const bool bad = s_fv[3] != 0;
+    const double sc0 = s_scale[0], sc1 = s_scale[1], sc2 = s_scale[2];
+    for (uint32_t t = 0; t < T; ++t) {
+      const uint32_t b = t & 1;
+      if (!bar_wait(acc_full + b, (t >> 1) & 1, s_err, lim)) goto rdone;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t ta = tbase + ((uint32_t)(32 * q) << 16) + 64u * b;
+      uint32_t v0[2][8], v1[2][8], v2[2][8];
+      tmem_ld8x2(ta + 0, ta + 32, v0);
+      tmem_ld8x2(ta + 8, ta + 40, v1);
+      tmem_ld8x2(ta + 16, ta + 48, v2);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) bar_arrive(acc_empty + b);
+      const int64_t i = ((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * kRTile + 32 * q + lane;
+      if (i < n) {
+        double dx = rec_value(v0[0], v0[1], sc0), dr = rec_value(v1[0], v1[1], sc1),
+               dp = rec_value(v2[0], v2[1], sc2);
+        if (bad) dx = dr = dp = CUDART_NAN;
+        x[i] = x[i] + dx;
+        r[i] = dr;
+        p[i] = dp;
+      }
+    }
+  } else if (warp == kRLoadWarp) {
+    if (lane == 0) {
+      for (uint32_t t = 0; t < T; ++t) {
+        const uint32_t s = t & 1;
+        if (t >= 2 && !bar_wait(f_empty + s, ((t >> 1) & 1) ^ 1, s_err, lim)) goto rdone;
+        armed = t + 1;
+        bar_expect_tx(f_full + s, kRFBytes);
+        tensor_g2s(fstage + s * kRFBytes, &ymap, (int)(((int64_t)blockIdx.x + (int64_t)t * gridDim.x) * kRTile),
+                   f_full + s);
+      }
+    }
+  } else if (warp == kRMmaWarp) {
+    if (lane == 0) {
+      const uint32_t idesc = instr_desc(128, kRN);
+      const uint32_t bbase = smem_u32(bop);
+      for (uint32_t t = 0; t < T; ++t) {
+        const uint32_t s = t & 1, b = t & 1;
+        if (!bar_wait(a_full + s, (t >> 1) & 1, s_err, lim)) goto rdone;
+        if (t >= 2 && !bar_wait(acc_empty + b, ((t >> 1) & 1) ^ 1, s_err, lim)) goto rdone;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t abase = smem_u32(astage + s * kRABytes);
+        const uint32_t d0 = tbase + 64u * b;
+#pragma unroll
+        for (int ks = 0; ks < kRK / 16; ++ks)
+          mma_f16(d0 + 32u * (ks & 1), rec_desc(abase + 256u * ks), rec_desc(bbase + 256u * ks), idesc,
+                  ks >= 2 ? 1u : 0u);
+        mma_commit(a_empty + s);
+        mma_commit(acc_full + b);
+        issued = t + 1;
+      }
+    }
+  }
+rdone:
+  if (*s_err) {
+    if (warp == kRLoadWarp && lane == 0)
+      for (uint32_t k = armed > 2u ? armed - 2u : 0u; k < armed; ++k) bar_drain(f_full + (k & 1), (k >> 1) & 1, lim);
+    if (warp == kRMmaWarp && lane == 0 && issued > 0) {
+      mma_commit(mma_done);
+      bar_drain(mma_done, 0, lim);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (*s_err && tid == 0 && guard.err) atomicExch(guard.err, (int)ASCG_ERR_TIMEOUT);
+  if (warp == kRMmaWarp) {
+    __syncwarp();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tbase));
+  }
+}
+
 // cuTensorMapEncodeTiled, looked up once through the runtime.
 PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 std::mutex g_encode_mu;
 
-cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int64_t ldY) {
+cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int64_t ldY, int box_rows = kBoxRows) {
   {
     std::lock_guard<std::mutex> lock(g_encode_mu);
     if (!g_encode) {
@@ -867,7 +1183,7 @@ cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int6
   }
   const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)w};
   const cuuint64_t strides[1] = {(cuuint64_t)ldY * sizeof(double)};
-  const cuuint32_t box[2] = {(cuuint32_t)kBoxRows, (cuuint32_t)kTW};
+  const cuuint32_t box[2] = {(cuuint32_t)box_rows, (cuuint32_t)kTW};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, const_cast<double*>(Y), dims, strides, box,
                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -875,7 +1191,7 @@ cudaError_t encode_map(CUtensorMap* map, const double* Y, int64_t n, int w, int6
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-std::atomic<uint64_t> g_tc_smem_set{0}, g_tc_items_smem_set{0};
+std::atomic<uint64_t> g_tc_smem_set{0}, g_tc_items_smem_set{0}, g_rec_smem_set{0};
 
 }  // namespace
 
@@ -936,6 +1252,32 @@ cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t ro
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   gram_tc_items_kernel<<<nitems, kTcThreads, kTcSmem, s>>>(map, w, items, sys_w, emax_all, partials);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_recover_tc(int64_t n, int w, const double* Y, int64_t ldY, const int* col_emax,
+                              const double* coords, double* x, double* r, double* p, cudaStream_t s, int* err,
+                              const int* gate) {
+  if (!gram_tc_applies(w) || !gram_tc_aligned(Y, ldY) || n < 1 || n > 0x7fffffffll) return cudaErrorInvalidValue;
+  cudaError_t e = smem_limit_once(g_rec_smem_set, recover_tc_kernel, (int)kRSmem);
+  if (e != cudaSuccess) return e;
+  CUtensorMap map;
+  e = encode_map(&map, Y, n, w, ldY, kRTile);
+  if (e != cudaSuccess) return e;
+  const int64_t tiles = (n + kRTile - 1) / kRTile;
+  const int g = gram_grid();
+  const TcGuard guard{kWaitLimit, -1, err, gate};
+  recover_tc_kernel<<<(int)(tiles < g ? tiles : g), kRThreads, kRSmem, s>>>(map, n, w, col_emax, coords, x, r, p,
+                                                                           guard);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_col_exponents(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, cudaStream_t s) {
+  if (w < 1 || w > kTW || n < 1) return cudaErrorInvalidValue;
+  cudaError_t e = cudaMemsetAsync(col_emax, 0, sizeof(int) * kTW, s);
+  if (e != cudaSuccess) return e;
+  const int64_t eb = (n + 255) / 256;
+  col_exponent_kernel<<<(int)(eb < kExpBlocks ? eb : kExpBlocks), 256, 0, s>>>(n, w, Y, ldY, col_emax);
   return cudaGetLastError();
 }
 

@@ -142,6 +142,8 @@ def test_null_arguments_are_errors(P):
     assert P._lib.ascg_op_destroy(None) == P.ASCG_OK
     assert P._lib.ascg_gram(0, 3, None, 0, None, None) == P.ASCG_ERR_INVALID
     assert P._lib.ascg_recover(10, 4, 1, 10, 1, 1, 1, 1, None) == P.ASCG_ERR_INVALID  # even w
+    assert P._lib.ascg_recover_tc(10, 7, 1, 10, 1, 1, 1, 1, None) == P.ASCG_ERR_INVALID  # w < 9
+    assert P._lib.ascg_recover_tc(10, 9, 1, 10, 1, 1, 1, 1, None) == P.ASCG_ERR_INVALID  # unaligned Y
     assert P._lib.ascg_newton_shifts(None, None, 0, 0, None, None) == P.ASCG_ERR_INVALID
 
 

@@ -8,6 +8,7 @@ its rounding uncertainty, see parity.py) and the final true residual (within
 a factor 2).
 """
 import math
+from fractions import Fraction
 
 import numpy as np
 import pytest
@@ -444,6 +445,101 @@ def test_recover_in_place_on_basis(env):
     _, ro, po = O.recover(Y.T, np.zeros(n), cf[:w], cf[w:2 * w], cf[2 * w:])
     got = Yd.cpu().numpy().reshape(w, n)
     assert np.allclose(got[1], ro, rtol=1e-13, atol=1e-13) and np.allclose(got[0], po, rtol=1e-13, atol=1e-13)
+
+
+def _bexp(v):
+    return (int(np.float64(v).view(np.uint64)) >> 52) & 0x7FF
+
+
+def _digits55(v, emax):
+    """Seven balanced base-256 digits, most significant first, of the integer
+    trunc(v 2^(55 - E)), E = emax - 1022 (|digit| <= 128)."""
+    t = int(Fraction(float(v)) * Fraction(2) ** (55 - (emax - 1022)))
+    z = t + sum(128 << (8 * k) for k in range(7))
+    d = [((z >> (8 * k)) & 0xFF) - 128 for k in range(6)] + [(z >> 48) - 128]
+    return d[::-1]
+
+
+def recover_tc_model(Y, cf, x):
+    """The arithmetic ascg_recover_tc documents, in exact integers: columns of Y
+    (w x n) and the scaled coefficients u_vj = c_vj 2^(E_j - 55) in 55-bit fixed
+    point, digit products of levels d + e <= 7 summed exactly, one rounding to
+    FP64, then x + (Y x')_i."""
+    w, n = Y.shape
+    emax = [max(_bexp(v) for v in Y[j]) for j in range(w)]
+    yd = [[_digits55(Y[j, i], emax[j]) for i in range(n)] for j in range(w)]
+    outs = []
+    for v in range(3):
+        u = [0.0 if emax[j] == 0 else math.ldexp(float(cf[v * w + j]), emax[j] - 1077) for j in range(w)]
+        fv = max(_bexp(t) for t in u)
+        ud = [_digits55(u[j], fv) for j in range(w)]
+        col = np.empty(n)
+        for i in range(n):
+            T = 0
+            for j in range(w):
+                a, b = yd[j][i], ud[j]
+                for d in range(7):
+                    if a[d]:
+                        for e in range(min(7, 8 - d)):
+                            T += a[d] * b[e] << (8 * (7 - d - e))
+            col[i] = float(T) * 2.0 ** (fv - 1037)
+        outs.append(col)
+    return x + outs[0], outs[1], outs[2]
+
+
+def _krylov_like(rng, w, n):
+    """Columns of growing scale with entries spread over a few decades, one zero
+    column: the shape of a scaled Krylov basis."""
+    Y = rng.standard_normal((w, n)) * 10.0 ** rng.uniform(-3, 0, (w, n)) * np.logspace(0, 6, w)[:, None]
+    Y[w // 2] = 0.0
+    return Y
+
+
+@pytest.mark.parametrize("n,w", [(300, 33), (1025, 17), (129, 9), (260, 25)])
+def test_recover_tc_parity(env, n, w):
+    """Tensor-core recovery: bit for bit the fixed-point arithmetic it documents
+    (a model in exact integers), and within its derived normwise bound of the
+    FP64 oracle of eq. (coords); ragged n (not a multiple of the 128-row tile)."""
+    P, torch = env
+    rng = np.random.default_rng(7 * n + w)
+    Y = _krylov_like(rng, w, n)
+    x = rng.standard_normal(n)
+    cf = rng.standard_normal(3 * w) * 10.0 ** rng.uniform(-2, 2, 3 * w)
+    ld = n + (n % 2)
+    Yd = _gram_dev(torch, Y, ld)
+    xd = dev(torch, x)
+    r = torch.empty(n, dtype=torch.float64, device="cuda")
+    p = torch.empty(n, dtype=torch.float64, device="cuda")
+    P.ascg_recover_tc(n, w, Yd, ld, dev(torch, cf), xd, r, p)
+    got = (xd.cpu().numpy(), r.cpu().numpy(), p.cpu().numpy())
+    model = recover_tc_model(Y, cf, x)
+    for g, m in zip(got, model):
+        assert np.array_equal(g, m)
+    # against the oracle: the kernel's normwise bound plus the oracle's own FP64 error
+    xo, ro, po = O.recover(Y.T, x, cf[:w], cf[w:2 * w], cf[2 * w:])
+    ninf = np.abs(Y).max(axis=1)
+    for k, (g, o) in enumerate(zip(got, (xo, ro, po))):
+        c = np.abs(cf[k * w:(k + 1) * w])
+        tc = 2.0 ** -54 * (ninf @ c) + (w + 2) * 2.0 ** -52 * np.max(ninf * c)
+        own = 2 * gamma_n(w + 1) * (np.abs(Y.T) @ c + (np.abs(x) if k == 0 else 0.0))
+        assert np.all(np.abs(g - o) <= 2.0 ** -52 * np.abs(g) + tc + own)
+
+
+def test_recover_tc_in_place_on_basis(env):
+    """r and p may be columns 1 and 0 of Y itself (each 128-row tile is read
+    into shared memory before its results are written)."""
+    P, torch = env
+    n, w = 700, 33
+    rng = np.random.default_rng(11)
+    Y = _krylov_like(rng, w, n)
+    cf = rng.standard_normal(3 * w)
+    Yd = _gram_dev(torch, Y, n)
+    x = torch.zeros(n, dtype=torch.float64, device="cuda")
+    P.ascg_recover_tc(n, w, Yd, n, dev(torch, cf), x, Yd[n:].data_ptr(), Yd.data_ptr())
+    _, rm, pm = recover_tc_model(Y, cf, np.zeros(n))
+    got = Yd[:w * n].cpu().numpy().reshape(w, n)
+    assert np.array_equal(got[1], rm) and np.array_equal(got[0], pm)
+    assert np.array_equal(got[2:], Y[2:])
 
 
 # ---------------------------------------------------------------------------
