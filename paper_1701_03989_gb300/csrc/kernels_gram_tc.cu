@@ -1039,6 +1039,13 @@ __global__ void __launch_bounds__(kRThreads, 1)
     const int jb = warp & 3;
     const int row = col32 ? 32 * (warp - 16) + lane : 32 * (warp >> 2) + lane;
     const bool on = col32 ? w == kTW : 8 * jb < w;
+    // the columns' exponents, the same in every lane of the warp
+    int em[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) em[c] = s_emax[col32 ? 32 : 8 * jb + c];
+    bool all_fast = true;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) all_fast = all_fast && em[c] >= kFastSplitMinEmax;
     for (uint32_t t = 0; t < T; ++t) {
       const uint32_t s = t & 1, par = (t >> 1) & 1;
       if (!bar_wait(f_full + s, par, s_err, lim)) goto rdone;
@@ -1051,13 +1058,12 @@ __global__ void __launch_bounds__(kRThreads, 1)
           uint32_t zl[8], zh[8];
 #pragma unroll
           for (int c = 0; c < 8; ++c) y[c] = f[(8 * jb + c) * kRTile + row];
+          if (all_fast) {
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int em = s_emax[8 * jb + c];  // the same in every lane
-            if (em >= kFastSplitMinEmax)
-              split_z_fast(y[c], em, zl[c], zh[c]);
-            else
-              split_z(y[c], em, zl[c], zh[c]);
+            for (int c = 0; c < 8; ++c) split_z_fast(y[c], em[c], zl[c], zh[c]);
+          } else {
+#pragma unroll
+            for (int c = 0; c < 8; ++c) split_z(y[c], em[c], zl[c], zh[c]);
           }
           uint32_t wd[4][kDig];
 #pragma unroll
@@ -1069,11 +1075,10 @@ __global__ void __launch_bounds__(kRThreads, 1)
         } else {
           const double y = f[32 * kRTile + row];
           uint32_t zl, zh, dw[kDig];
-          const int em = s_emax[32];
-          if (em >= kFastSplitMinEmax)
-            split_z_fast(y, em, zl, zh);
+          if (all_fast)
+            split_z_fast(y, em[0], zl, zh);
           else
-            split_z(y, em, zl, zh);
+            split_z(y, em[0], zl, zh);
           digit_words(zl, zh, zl, zh, dw);
           // digits 0..6 at K = 224..230, K = 231 zero
           *reinterpret_cast<uint4*>(dst + rec_off(row, 224)) =
