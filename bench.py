@@ -582,6 +582,11 @@ def our_arm(args):
                               "fp64_equiv_tflops": achieved_tf,
                               "peak_source": f"{BF16_PEAK_SRC} dense bf16 burst (fp16 runs at the same rate)",
                               "hbm": hbm_view(sum(r.gram_bytes for r in results), t_gram)},
+            # the recovery of x, r and p (on the tensor cores where the Gram took them):
+            # its algorithmic bytes, 8 w n + 32 n per block (r and p only, 8 w n + 16 n,
+            # on the FP64 path), against the measured copy peak
+            "roofline_recovery": (lambda h: dict(h, bound="hbm", kernel="recover_tc_kernel") if h else None)(
+                hbm_view(sum(r.recover_bytes for r in results), t_rec)),
             "vs_classical": classical,
             "e2e": {"value": e2e_value, "unit": "iters/s", "h2d_bytes_per_step": 16 * n,
                     "d2h_bytes_per_step": 8 * n},
