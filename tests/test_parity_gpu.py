@@ -8,13 +8,13 @@ its rounding uncertainty, see parity.py) and the final true residual (within
 a factor 2).
 """
 import math
-from fractions import Fraction
 
 import numpy as np
 import pytest
 
 import parity
 import workloads as W
+from tc_models import gram_tc_model, recover_tc_model
 from oracle import ascg_oracle as O
 
 pytestmark = pytest.mark.gpu
@@ -223,6 +223,25 @@ def _gram_dev(torch, Y, ld):
     for c in range(w):
         Yd[c * ld:c * ld + n] = dev(torch, Y[c])
     return Yd
+
+
+@pytest.mark.parametrize("n,w", [(300001, 33), (5000, 25), (37, 17), (1025, 9)])
+def test_gram_tensor_bit_exact(env, n, w):
+    """The tensor-core Gram equals, bit for bit, the fixed-point arithmetic it
+    documents (an exact model in integers: 55-bit columns, digit levels <= 7,
+    per-CTA partials, the finalize kernel's summation order), on columns that
+    span 60 orders of magnitude with zeros and denormals."""
+    P, torch = env
+    rng = np.random.default_rng(3 * n + w)
+    Y = rng.standard_normal((w, n)) * 10.0 ** rng.uniform(-30, 30, (1, n)) * np.logspace(0, 8, w)[:, None]
+    Y[0, ::3] = 0.0
+    Y[1, :] = rng.standard_normal(n) * 1e-310
+    ld = n + (n % 2)
+    Yd = _gram_dev(torch, Y, ld)
+    G = torch.empty(w * w, dtype=torch.float64, device="cuda")
+    P.ascg_gram(n, w, Yd, ld, G)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    assert np.array_equal(G.cpu().numpy().reshape(w, w), gram_tc_model(Y, sms))
 
 
 @pytest.mark.parametrize("n,w", [(300001, 33), (37, 17), (1025, 9), (65, 33)])
@@ -445,46 +464,6 @@ def test_recover_in_place_on_basis(env):
     _, ro, po = O.recover(Y.T, np.zeros(n), cf[:w], cf[w:2 * w], cf[2 * w:])
     got = Yd.cpu().numpy().reshape(w, n)
     assert np.allclose(got[1], ro, rtol=1e-13, atol=1e-13) and np.allclose(got[0], po, rtol=1e-13, atol=1e-13)
-
-
-def _bexp(v):
-    return (int(np.float64(v).view(np.uint64)) >> 52) & 0x7FF
-
-
-def _digits55(v, emax):
-    """Seven balanced base-256 digits, most significant first, of the integer
-    trunc(v 2^(55 - E)), E = emax - 1022 (|digit| <= 128)."""
-    t = int(Fraction(float(v)) * Fraction(2) ** (55 - (emax - 1022)))
-    z = t + sum(128 << (8 * k) for k in range(7))
-    d = [((z >> (8 * k)) & 0xFF) - 128 for k in range(6)] + [(z >> 48) - 128]
-    return d[::-1]
-
-
-def recover_tc_model(Y, cf, x):
-    """The arithmetic ascg_recover_tc documents, in exact integers: columns of Y
-    (w x n) and the scaled coefficients u_vj = c_vj 2^(E_j - 55) in 55-bit fixed
-    point, digit products of levels d + e <= 7 summed exactly, one rounding to
-    FP64, then x + (Y x')_i."""
-    w, n = Y.shape
-    emax = [max(_bexp(v) for v in Y[j]) for j in range(w)]
-    yd = [[_digits55(Y[j, i], emax[j]) for i in range(n)] for j in range(w)]
-    outs = []
-    for v in range(3):
-        u = [0.0 if emax[j] == 0 else math.ldexp(float(cf[v * w + j]), emax[j] - 1077) for j in range(w)]
-        fv = max(_bexp(t) for t in u)
-        ud = [_digits55(u[j], fv) for j in range(w)]
-        col = np.empty(n)
-        for i in range(n):
-            T = 0
-            for j in range(w):
-                a, b = yd[j][i], ud[j]
-                for d in range(7):
-                    if a[d]:
-                        for e in range(min(7, 8 - d)):
-                            T += a[d] * b[e] << (8 * (7 - d - e))
-            col[i] = float(T) * 2.0 ** (fv - 1037)
-        outs.append(col)
-    return x + outs[0], outs[1], outs[2]
 
 
 def _krylov_like(rng, w, n):
