@@ -60,6 +60,36 @@ inline cudaError_t smem_limit_once(std::atomic<uint64_t>& done, K* kernel, int b
   return e;
 }
 
+// Programmatic dependent launch: the kernel may be scheduled while the
+// previous kernel in the stream is still finishing, and waits for it (all its
+// memory operations visible) with pdl_wait() before touching anything that
+// kernel wrote. pdl_release() lets the next such kernel be scheduled as soon
+// as every CTA of this one has started. Without the launch attribute both are
+// no-ops, so the kernels stay correct under any launch. Every kernel launched
+// this way calls pdl_wait() at entry: a kernel that returned before its
+// predecessor finished would let its own successor overtake that predecessor.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl_ex(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                 Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t s, Args... args) {
+  return launch_pdl_ex(kernel, dim3((unsigned)grid), dim3((unsigned)block), 0, s, args...);
+}
+
 // Number of blocks for a grid-stride kernel over n items.
 inline int grid_for(int64_t n, int threads, int cap) {
   int64_t g = (n + threads - 1) / threads;

@@ -120,6 +120,8 @@ __global__ void __launch_bounds__(kSpmvRows) cg_spmv_dot_kernel(DevSell A, const
                                                                 double* partials, unsigned* counter) {
   __shared__ double red[32];
   __shared__ int flag;
+  pdl_wait();     // the previous kernel's p and state
+  pdl_release();
   const int done = st->done;  // uniform: written by an earlier kernel
   if (blockIdx.x == 0 && threadIdx.x == 0) st->active = !done;  // read by the next two kernels
   if (done) return;
@@ -159,6 +161,8 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __res
                                                         int ab_cap) {
   __shared__ double red[32];
   __shared__ int flag;
+  pdl_wait();     // q and alpha from the SpMV
+  pdl_release();
   if (!st->active) return;
   const double alpha = st->alpha;
   double s = 0.0;
@@ -194,6 +198,8 @@ __global__ void __launch_bounds__(256) cg_update_kernel(int64_t n, double* __res
 __global__ void __launch_bounds__(256) cg_pupdate_kernel(int64_t n, double* __restrict__ x,
                                                          const double* __restrict__ r, double* __restrict__ p,
                                                          const CGState* st) {
+  pdl_wait();     // r and beta from the update
+  pdl_release();
   if (!st->active) return;  // this iteration was skipped (solve already done)
   const double alpha = st->alpha, beta = st->beta;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
@@ -247,10 +253,8 @@ cudaError_t launch_cg_spmv_dot(const DevSell& A, int64_t nnz, const double* p, d
   // A's values and columns (12 bytes per entry) beyond a quarter of the 129 MB
   // L2: stream them past it
   if (12 * nnz > ((int64_t)32 << 20))
-    cg_spmv_dot_kernel<true><<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
-  else
-    cg_spmv_dot_kernel<false><<<g, kSpmvRows, 0, s>>>(A, p, q, st, partials, counter);
-  return cudaGetLastError();
+    return launch_pdl(cg_spmv_dot_kernel<true>, g, kSpmvRows, s, A, p, q, st, partials, counter);
+  return launch_pdl(cg_spmv_dot_kernel<false>, g, kSpmvRows, s, A, p, q, st, partials, counter);
 }
 
 cudaError_t launch_cg_update(int64_t n, double* r, const double* q, CGState* st, double* partials,
@@ -258,14 +262,12 @@ cudaError_t launch_cg_update(int64_t n, double* r, const double* q, CGState* st,
                              int ab_cap, cudaStream_t s) {
   // HBM-bound axpys: 8 CTAs per SM keep enough loads in flight (partials hold one
   // slot per 256-row block, so any grid up to n/256 fits)
-  cg_update_kernel<<<grid_for(n, 256, 152 * 8), 256, 0, s>>>(n, r, q, st, partials, counter, res_hist, res_cap,
-                                                                alpha_hist, beta_hist, ab_cap);
-  return cudaGetLastError();
+  return launch_pdl(cg_update_kernel, grid_for(n, 256, 152 * 8), 256, s, n, r, q, st, partials, counter, res_hist,
+                    res_cap, alpha_hist, beta_hist, ab_cap);
 }
 
 cudaError_t launch_cg_pupdate(int64_t n, double* x, const double* r, double* p, const CGState* st, cudaStream_t s) {
-  cg_pupdate_kernel<<<grid_for(n, 256, 4096), 256, 0, s>>>(n, x, r, p, st);
-  return cudaGetLastError();
+  return launch_pdl(cg_pupdate_kernel, grid_for(n, 256, 4096), 256, s, n, x, r, p, st);
 }
 
 cudaError_t launch_cg_init(CGState* st, double eps_star, double bnorm, int max_iters, int iter0,

@@ -636,6 +636,8 @@ __global__ void __launch_bounds__(128) block_ctrl_kernel(const double* __restric
                                                          double* __restrict__ ab_hist, int ab_cap, int64_t g_stride,
                                                          int64_t c_stride, double* __restrict__ spec,
                                                          unsigned* counters) {
+  pdl_wait();
+  pdl_release();
   const int q = blockIdx.y;
   G += (int64_t)q * g_stride;
   st += q;
@@ -672,6 +674,8 @@ __global__ void __launch_bounds__(128) block_ctrl_kernel(const double* __restric
 // nothing.
 __global__ void block_advance_kernel(const BlockState* __restrict__ prev, BlockState* __restrict__ cur,
                                      int max_iters) {
+  pdl_wait();
+  pdl_release();
   if (threadIdx.x != 0) return;
   const int m = prev->m + prev->s_k;
   cur->m = m;
@@ -752,10 +756,8 @@ cudaError_t launch_block_ctrl(const double* G, const double* theta, const double
                               BlockState* st, int sbar, int adaptive, double* coords, double* hist, double* res_hist,
                               int res_cap, double* ab_hist, int ab_cap, double* spec, unsigned* counter,
                               cudaStream_t s) {
-  block_ctrl_kernel<<<dim3(adaptive ? sbar + 1 : 1, 1), 128, 0, s>>>(G, theta, sigma, gamma, st, coords, hist,
-                                                                      res_hist, res_cap, ab_hist, ab_cap, 0, 0, spec,
-                                                                      counter);
-  return cudaGetLastError();
+  return launch_pdl_ex(block_ctrl_kernel, dim3(adaptive ? sbar + 1 : 1, 1), dim3(128), 0, s, G, theta, sigma, gamma,
+                       st, coords, hist, res_hist, res_cap, ab_hist, ab_cap, (int64_t)0, (int64_t)0, spec, counter);
 }
 
 cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const double* theta, const double* sigma,
@@ -770,8 +772,7 @@ cudaError_t launch_block_ctrl_batch(const double* G, int64_t g_stride, const dou
 }
 
 cudaError_t launch_block_advance(const BlockState* prev, BlockState* cur, int max_iters, cudaStream_t s) {
-  block_advance_kernel<<<1, 32, 0, s>>>(prev, cur, max_iters);
-  return cudaGetLastError();
+  return launch_pdl(block_advance_kernel, 1, 32, s, prev, cur, max_iters);
 }
 
 cudaError_t launch_newton_shifts(const double* alphas, const double* betas, int k, double* shifts,

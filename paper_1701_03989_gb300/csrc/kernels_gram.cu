@@ -239,6 +239,8 @@ __global__ void __launch_bounds__(128) gram_items_moment_finalize_kernel(const d
 // is bitwise reproducible.
 __global__ void __launch_bounds__(128) gram_finalize_kernel(int w, const double* __restrict__ partials, int nparts,
                                                             double* __restrict__ G, const int* __restrict__ gate) {
+  pdl_wait();
+  pdl_release();
   if (gate && !*gate) return;
   const int np = w * (w + 1) / 2;
   const int gt = blockIdx.x * blockDim.x + threadIdx.x;
@@ -405,8 +407,7 @@ cudaError_t launch_gram_moment_finalize(int w, const double* partials, int npart
 cudaError_t launch_gram_finalize(int w, const double* partials, int nparts, double* G, cudaStream_t s,
                                  const int* gate) {
   const int np = w * (w + 1) / 2;
-  gram_finalize_kernel<<<(4 * np + 127) / 128, 128, 0, s>>>(w, partials, nparts, G, gate);
-  return cudaGetLastError();
+  return launch_pdl(gram_finalize_kernel, (4 * np + 127) / 128, 128, s, w, partials, nparts, G, gate);
 }
 
 }  // namespace ascg

@@ -753,6 +753,8 @@ done:
 __global__ void __launch_bounds__(kTcThreads, 1)
     gram_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
                    double* __restrict__ partials, const TcGuard guard) {
+  pdl_wait();
+  pdl_release();
   if (guard.gate && !*guard.gate) return;  // uniform, before any barrier or tensor memory
   gram_tc_body(&ymap, w, 0, blockIdx.x, (n + kTChunk - 1) / kTChunk, gridDim.x, n, col_emax,
                partials + (int64_t)blockIdx.x * (w * (w + 1) / 2), guard);
@@ -943,6 +945,8 @@ __global__ void __launch_bounds__(kRThreads, 1)
     recover_tc_kernel(const __grid_constant__ CUtensorMap ymap, int64_t n, int w, const int* __restrict__ col_emax,
                       const double* __restrict__ coords, double* __restrict__ x, double* __restrict__ r,
                       double* __restrict__ p, const TcGuard guard) {
+  pdl_wait();
+  pdl_release();
   // uniform, before any barrier or tensor memory: a block enqueued ahead with
   // nothing to do, or one whose Gram already failed (its error word is set),
   // leaves x, r and p alone
@@ -1235,8 +1239,8 @@ cudaError_t launch_gram_tc(int64_t n, int w, const double* Y, int64_t ldY, int* 
     if (e != cudaSuccess) return e;
   }
   const TcGuard guard{stall_test ? kTestWaitLimit : kWaitLimit, stall_test ? 0 : -1, err, gate};
-  gram_tc_kernel<<<parts, kTcThreads, kTcSmem, s>>>(map, n, w, exp_parts, partials, guard);
-  return cudaGetLastError();
+  return launch_pdl_ex(gram_tc_kernel, dim3(parts), dim3(kTcThreads), kTcSmem, s, map, n, w, exp_parts, partials,
+                       guard);
 }
 
 cudaError_t launch_gram_tc_items(int w, const double* Y, int64_t ldY, int64_t rows, const GramItem* items,
@@ -1272,9 +1276,8 @@ cudaError_t launch_recover_tc(int64_t n, int w, const double* Y, int64_t ldY, co
   const int64_t tiles = (n + kRTile - 1) / kRTile;
   const int g = gram_grid();
   const TcGuard guard{kWaitLimit, -1, err, gate};
-  recover_tc_kernel<<<(int)(tiles < g ? tiles : g), kRThreads, kRSmem, s>>>(map, n, w, col_emax, coords, x, r, p,
-                                                                           guard);
-  return cudaGetLastError();
+  return launch_pdl_ex(recover_tc_kernel, dim3((unsigned)(tiles < g ? tiles : g)), dim3(kRThreads), kRSmem, s, map, n,
+                       w, col_emax, coords, x, r, p, guard);
 }
 
 cudaError_t launch_col_exponents(int64_t n, int w, const double* Y, int64_t ldY, int* col_emax, cudaStream_t s) {

@@ -46,6 +46,8 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
     mpk_split_step_kernel(DevSell O, const double* __restrict__ oval, const double* __restrict__ dtil, double sig,
                           double* __restrict__ Y, int64_t ldY, int j, int* emax_part, int64_t emax_ld,
                           const int* __restrict__ gate) {
+  pdl_wait();     // the previous step's columns (and the gate) are written by the kernel before
+  pdl_release();  // the next step may be scheduled once every CTA of this one has started
   if (gate && !*gate) return;  // uniform: a block enqueued ahead that has nothing to do
   const int64_t row = (int64_t)blockIdx.x * kSpmvRows + threadIdx.x;
   unsigned e_op = 0, e_or = 0;
@@ -130,6 +132,8 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
 // of 4 and entries past the warp count are zero.
 __global__ void __launch_bounds__(1024) emax_reduce_kernel(const int* __restrict__ emax_part, int64_t emax_ld,
                                                            int* __restrict__ col_emax, const int* __restrict__ gate) {
+  pdl_wait();
+  pdl_release();
   if (gate && !*gate) return;
   const int c = blockIdx.x;
   const int4* src = reinterpret_cast<const int4*>(emax_part + (int64_t)c * emax_ld);
@@ -306,9 +310,9 @@ cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y
   if (!do_p) return cudaErrorInvalidValue;  // every step forms the P column
   const int g = (int)((O.O.n + kSpmvRows - 1) / kSpmvRows);
   const int sig_mode = (op.sig == 0.0 || j < 1) ? 0 : (op.sig == 1.0 ? 1 : 2);
-#define ASCG_MPK(S, R) \
-  mpk_split_step_kernel<S, R><<<g, kSpmvRows, 0, s>>>(O.O, op.oval, op.dtil, op.sig, Y, ldY, j, emax_part, emax_ld, \
-                                                      gate)
+#define ASCG_MPK(S, R)                                                                                        \
+  return launch_pdl(mpk_split_step_kernel<S, R>, g, kSpmvRows, s, O.O, op.oval, op.dtil, op.sig, Y, ldY, j, emax_part, \
+                    emax_ld, gate)
   if (do_r) {
     if (sig_mode == 0) ASCG_MPK(0, true);
     else if (sig_mode == 1) ASCG_MPK(1, true);
@@ -325,8 +329,7 @@ cudaError_t launch_mpk_split_step(const DevSplit& O, const StepOp& op, double* Y
 cudaError_t launch_emax_reduce(const int* emax_part, int64_t emax_ld, int64_t n, int w, int* col_emax,
                                cudaStream_t s, const int* gate) {
   (void)n;
-  emax_reduce_kernel<<<w, 1024, 0, s>>>(emax_part, emax_ld, col_emax, gate);
-  return cudaGetLastError();
+  return launch_pdl(emax_reduce_kernel, w, 1024, s, emax_part, emax_ld, col_emax, gate);
 }
 
 cudaError_t launch_shift_scale(const double* src, int64_t n, double theta, double scale, double* dst,

@@ -474,7 +474,7 @@ def _krylov_like(rng, w, n):
     return Y
 
 
-@pytest.mark.parametrize("n,w", [(300, 33), (1025, 17), (129, 9), (260, 25)])
+@pytest.mark.parametrize("n,w", [(300, 33), (1025, 17), (129, 9), (260, 25), (37, 11)])
 def test_recover_tc_parity(env, n, w):
     """Tensor-core recovery: bit for bit the fixed-point arithmetic it documents
     (a model in exact integers), and within its derived normwise bound of the
@@ -558,6 +558,8 @@ SOLVES = [
     # solver takes the FP64 kernel by default), and the monomial one
     ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_tc=True), 1e-12),
     ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8, gram_tc=True), 1e-10),
+    # the same, with the recovery kept on the FP64 path (ASCG_FLAG_RECOVER_FP64)
+    ("poisson3d_23", dict(method="adaptive", basis="chebyshev", s_max=16, gram_tc=True, recover_fp64=True), 1e-12),
     # c_{k,j} = 6 N_k j kappa(A) (eq. (fb)) from closed-form kappa(A) and ||A|| of the Poisson matrices
     ("poisson2d_32", dict(method="adaptive", basis="monomial", s_max=8,
                           c_formula=(W.poisson_eig_bounds(2, 32)[1] / W.poisson_eig_bounds(2, 32)[0],
