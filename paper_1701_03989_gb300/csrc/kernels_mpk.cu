@@ -27,7 +27,10 @@ __device__ __forceinline__ unsigned biased_exp(double v) { return ((unsigned)__d
 // emax_part (optional, int[kMaxW][emax_ld]): lane 0 of each warp stores the
 // warp's largest biased exponent of each column written (and, for j = 0, of
 // the input columns 0 and 1) at emax_part[col * emax_ld + warp]; plain stores,
-// no synchronisation. emax_reduce_kernel folds them per column for the
+// no synchronisation. A warp past the last 32-row slice stores nothing: a row
+// holds the ceil(n / 32) slices rounded up to 4, fewer than the grid's warps
+// when n is not a multiple of 256, and such a store would land on the next
+// column's first slices. emax_reduce_kernel folds them per column for the
 // tensor-core Gram.
 // emax_part (or nullptr): record exponents. R: also the R chain (every step of
 // a block but the last). The entries of a row go in pairs: both index and value
@@ -101,11 +104,11 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
     e_op = biased_exp(tp);
     if (R) e_or = biased_exp(tr);
   }
-  if (!emax_part) return;  // uniform over the grid
+  const int64_t wg = ((int64_t)blockIdx.x * kSpmvRows + threadIdx.x) >> 5;
+  if (!emax_part || wg * kSlice >= O.n) return;  // uniform over the warp
   // the warp's rows share one slice; lanes past n contribute 0
   e_op = __reduce_max_sync(0xffffffffu, e_op);
   e_or = __reduce_max_sync(0xffffffffu, e_or);
-  const int64_t wg = ((int64_t)blockIdx.x * kSpmvRows + threadIdx.x) >> 5;
   if ((threadIdx.x & 31) == 0) {
     emax_part[(int64_t)(2 * j + 2) * emax_ld + wg] = (int)e_op;
     if (R) emax_part[(int64_t)(2 * j + 3) * emax_ld + wg] = (int)e_or;

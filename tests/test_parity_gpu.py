@@ -810,6 +810,40 @@ def test_small_n_large_s(env):
     assert res.status == P.ASCG_OK and res.rel_res_true <= 2e-12
 
 
+def test_ragged_n_tensor_core_exponents(env):
+    """n = 46^3 = 97336, not a multiple of 256, on the tensor-core Gram and
+    recovery. The matrix powers steps record each 32-row slice's largest
+    exponent per column, and the Gram and recovery scale every column by the
+    maximum of those records; a record written past the last slice would land
+    on the next column's first slices. The right-hand side puts the largest
+    entries of the early basis columns in those first slices, so an
+    under-stated column exponent would drop them from the digit split. The
+    first iterations are held to the oracle and the solve to its target, and
+    the same solve with the FP64 Gram and recovery takes the same blocks."""
+    P, torch = env
+    m = 46
+    A = W.poisson3d(m)
+    assert A.n % 256 != 0
+    rng = np.random.default_rng(11)
+    b = 1e-3 * W.rhs_uniform(A.n, rng)
+    b[:96] = rng.uniform(0.5, 1.0, 96)
+    b /= np.linalg.norm(b)
+    lam = W.poisson_eig_bounds(3, m)
+    kw = dict(method="adaptive", basis="chebyshev", s_max=16, lam=lam)
+    res, hist, blocks, x = run_gpu(P, torch, A, b, np.zeros(A.n), dict(kw, gram_tc=True), 1e-10)
+    assert res.status == P.ASCG_OK and res.rel_res_true <= 2e-10
+    ref, href, bref, _ = run_gpu(P, torch, A, b, np.zeros(A.n), dict(kw, gram_fp64=True), 1e-10)
+    assert ref.status == P.ASCG_OK and abs(res.iters - ref.iters) <= 16
+    orc = O.adaptive_sstep_cg(O.Operator.from_csr(A), b, np.zeros(A.n), s_max=16, eps_target=1e-10,
+                              basis="chebyshev", lam=lam, max_iters=40)
+    exempt, bad = parity.compare_block_sequences(blocks, orc.blocks[:-1], A.n)
+    assert not bad, bad
+    nwin = parity.history_window(blocks, orc.blocks, exempt, iters=20)
+    assert nwin > 1  # the first block's Gram (w = 33, on the tensor cores) decides entry 1
+    tau = parity.history_tolerance(orc.blocks, np.asarray(orc.res_hist), nwin)
+    assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= tau)
+
+
 # ---------------------------------------------------------------------------
 # full sizes: sampled outputs and the first iterations against the oracle
 # ---------------------------------------------------------------------------
