@@ -844,6 +844,97 @@ def test_ragged_n_tensor_core_exponents(env):
     assert np.all(np.abs(hist[:nwin] - np.asarray(orc.res_hist[:nwin])) <= tau)
 
 
+def _solve_on(P, torch, A, b, kw, stream=None):
+    """One solve of A x = b from x = 0 with options kw on `stream` (None: the
+    default stream) and a fresh operator; returns (result, x on the host,
+    residual history)."""
+    op = make_op(P, A)
+    bd = dev(torch, b)
+    xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+    hist = np.zeros(kw["max_iters"] + 2)
+    o = P.make_options(res_hist=hist, **kw)
+    torch.cuda.synchronize()
+    res = P.ascg_solve(op, bd, xd, o, stream=stream)
+    torch.cuda.synchronize()
+    x = xd.cpu().numpy()
+    P.ascg_op_destroy(op)
+    return res, x, hist[:res.iters + 1].copy()
+
+
+def test_solve_on_own_stream_matches_default(env):
+    """The kernels of a block wait for their predecessor on the solve's own
+    stream (programmatic dependent launch): a solve on a stream of the
+    caller's gives the bits of the same solve on the default stream, on the
+    tensor-core path (n = 46^3) and on the FP64 one (n = 23^3)."""
+    P, torch = env
+    for m in (46, 23):
+        A = W.poisson3d(m)
+        b = W.rhs_uniform(A.n, np.random.default_rng(12))
+        o = dict(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=W.poisson_eig_bounds(3, m),
+                 max_iters=20000)
+        r0, x0, h0 = _solve_on(P, torch, A, b, o)
+        r1, x1, h1 = _solve_on(P, torch, A, b, o, stream=torch.cuda.Stream())
+        assert r0.status == P.ASCG_OK and r1.status == P.ASCG_OK
+        assert r0.iters == r1.iters and r0.blocks == r1.blocks
+        assert np.array_equal(x0, x1) and np.array_equal(h0, h1)
+
+
+def test_concurrent_solves_on_two_streams(env):
+    """Two operators solved at the same time from two host threads, each on a
+    stream of its own (one on the tensor-core Gram and recovery, one on the
+    FP64 kernels, Newton basis): each gives the bits it gives alone."""
+    import threading
+    P, torch = env
+    A1 = W.poisson3d(46)
+    b1 = W.rhs_uniform(A1.n, np.random.default_rng(13))
+    o1 = dict(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=W.poisson_eig_bounds(3, 46),
+              max_iters=20000)
+    A2 = W.fv_diffusion2d(127, 2.0, np.random.default_rng(14))
+    b2 = W.rhs_uniform(A2.n, np.random.default_rng(15))
+    o2 = dict(method="adaptive", basis="newton", s_max=8, eps_target=1e-10, max_iters=20000)
+    solo = [_solve_on(P, torch, A1, b1, o1), _solve_on(P, torch, A2, b2, o2)]
+    out = [None, None]
+    errors = []
+
+    def run(i, A, b, o):
+        try:
+            out[i] = _solve_on(P, torch, A, b, o, stream=torch.cuda.Stream())
+        except Exception as e:  # reported below, in the main thread
+            errors.append(e)
+
+    ts = [threading.Thread(target=run, args=(0, A1, b1, o1)), threading.Thread(target=run, args=(1, A2, b2, o2))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    assert not errors, errors
+    for (rs, xs, hs), (rc, xc, hc) in zip(solo, out):
+        assert rs.status == P.ASCG_OK and rc.status == P.ASCG_OK
+        assert rs.iters == rc.iters and np.array_equal(xs, xc) and np.array_equal(hs, hc)
+
+
+def test_alternating_gram_paths_on_one_operator(env):
+    """One operator solved with the tensor-core Gram and recovery, then with
+    the FP64 Gram, then with the FP64 recovery beside the tensor-core Gram,
+    then with the tensor cores again: the last solve repeats the first bit for
+    bit (nothing in the shared workspace carries over), and each converges."""
+    P, torch = env
+    m = 46
+    A = W.poisson3d(m)
+    b = W.rhs_uniform(A.n, np.random.default_rng(16))
+    op = make_op(P, A)
+    bd = dev(torch, b)
+    base = dict(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=W.poisson_eig_bounds(3, m))
+    runs = []
+    for extra in (dict(gram_tc=True), dict(gram_fp64=True), dict(gram_tc=True, recover_fp64=True), dict(gram_tc=True)):
+        xd = torch.zeros(A.n, dtype=torch.float64, device="cuda")
+        res = P.ascg_solve(op, bd, xd, P.make_options(**base, **extra))
+        assert res.status == P.ASCG_OK and res.rel_res_true <= 2e-12
+        runs.append((res.iters, xd.cpu().numpy()))
+    P.ascg_op_destroy(op)
+    assert runs[0][0] == runs[3][0] and np.array_equal(runs[0][1], runs[3][1])
+
+
 # ---------------------------------------------------------------------------
 # full sizes: sampled outputs and the first iterations against the oracle
 # ---------------------------------------------------------------------------
