@@ -36,3 +36,18 @@ def test_kernel_source_hash_tracks_the_kernel_text():
     assert h != bench.kernel_source_hash(text=text.replace("body A", "body B"), span=span)
     # the committed kernel still contains the span bench.py hashes
     assert len(bench.kernel_source_hash()) == 16
+
+
+def test_timed_solves_run_without_phase_events():
+    """The timed solves run with the library's per-phase timing off (its
+    events break the chain of dependent launches); everything else in the
+    options is the phase pass's."""
+    P = pytest.importorskip("paper_1701_03989_gb300")
+    o = P.make_options(method="adaptive", basis="chebyshev", s_max=16, eps_target=1e-12, lam=(0.01, 1.0),
+                       timing=True, gram_fp64=True)
+    u = bench.untimed(P, o)
+    assert o.flags & P.ASCG_FLAG_TIMING
+    assert not u.flags & P.ASCG_FLAG_TIMING
+    assert u.flags == o.flags & ~P.ASCG_FLAG_TIMING
+    assert (u.method, u.basis, u.s_max, u.eps_target) == (o.method, o.basis, o.s_max, o.eps_target)
+    assert o.flags & P.ASCG_FLAG_TIMING  # the original is left as it was
