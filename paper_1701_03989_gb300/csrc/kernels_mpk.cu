@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
     }
     int k = 0;
     for (; k + 2 <= width; k += 2) {
-      const int c0 = __ldg(c + kSlice * k), c1 = __ldg(c + kSlice * (k + 1));
-      const double a0 = __ldg(v + kSlice * k), a1 = __ldg(v + kSlice * (k + 1));
+      const int c0 = __ldcs(c + kSlice * k), c1 = __ldcs(c + kSlice * (k + 1));
+      const double a0 = __ldcs(v + kSlice * k), a1 = __ldcs(v + kSlice * (k + 1));
       const double p0 = __ldg(pj + c0), p1 = __ldg(pj + c1);
       if (R) {
         const double r0 = __ldg(rj + c0), r1 = __ldg(rj + c1);
@@ -94,8 +94,8 @@ __global__ void __launch_bounds__(kSpmvRows, 6)
       }
     }
     if (k < width) {
-      const double a = __ldg(v + kSlice * k);
-      const int cc = __ldg(c + kSlice * k);
+      const double a = __ldcs(v + kSlice * k);
+      const int cc = __ldcs(c + kSlice * k);
       tp = fma(a, __ldg(pj + cc), tp);
       if (R) tr = fma(a, __ldg(rj + cc), tr);
     }
